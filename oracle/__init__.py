@@ -1,0 +1,136 @@
+"""FP64 CPU oracle of the spin-based Bloch simulation (§5.1.1, Eq. 4.1).
+
+TEST INFRASTRUCTURE ONLY: the reference that the CUDA library is checked
+against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import it; the library never does.  It shares no code with
+the CUDA path: the arithmetic lives in ``mrsim_oracle.c`` (plain C, libm,
+OpenMP over spins), this module only marshals arrays.
+
+Inputs are plain numpy arrays (or any object with the seven phantom fields and
+an ``events`` record array of 64-byte events); nothing here imports the
+library package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mrsim_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lib = None
+
+# Same byte layout as the library's event record (the interface, not shared code).
+EVENT_DTYPE = np.dtype(
+    [
+        ("dt", "<f8"),
+        ("gx", "<f8"),
+        ("gy", "<f8"),
+        ("gz", "<f8"),
+        ("rf_flip", "<f8"),
+        ("rf_phase", "<f8"),
+        ("adc_phase", "<f8"),
+        ("adc", "<i4"),
+        ("reserved", "<i4"),
+    ]
+)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP) into oracle/lib/liboracle.so."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _bind(path):
+    lib = ctypes.CDLL(path)
+    d = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_simulate.restype = ctypes.c_int
+    lib.oracle_simulate.argtypes = [ctypes.c_int64] + [d] * 7 + [d, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_double, d, ctypes.c_int64, d, ctypes.c_int]
+    lib.oracle_max_threads.restype = ctypes.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = _bind(_LIB)
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def simulate(phantom, events, gamma_hz_per_t, m_init=None, want_signal=True, want_state=False, n_threads=0, lib=None):
+    """Run the oracle.  Returns (signal complex128[n_adc] or None, state float64[n,3] or None)."""
+    lib = _load() if lib is None else lib
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    arrs = [np.ascontiguousarray(getattr(phantom, k), dtype=np.float64) for k in ("x", "y", "z", "rho", "t1", "t2", "dw")]
+    n = arrs[0].shape[0]
+    n_adc = int(np.count_nonzero(ev["adc"]))
+    sig = np.zeros(2 * n_adc, dtype=np.float64) if want_signal else None
+    st = np.zeros(3 * n, dtype=np.float64) if want_state else None
+    mi = None
+    if m_init is not None:
+        mi = np.ascontiguousarray(np.asarray(m_init, dtype=np.float64).reshape(-1))
+        if mi.shape[0] != 3 * n:
+            raise ValueError("m_init must have 3 values per spin")
+    rc = lib.oracle_simulate(
+        n, *[_dp(a) for a in arrs], _dp(mi), ev.shape[0], ev.ctypes.data_as(ctypes.c_void_p),
+        float(gamma_hz_per_t), _dp(sig), n_adc, _dp(st), int(n_threads)
+    )
+    if rc != 0:
+        raise RuntimeError(f"oracle_simulate failed with code {rc}")
+    out_sig = sig.view(np.complex128) if sig is not None else None
+    out_st = st.reshape(n, 3) if st is not None else None
+    return out_sig, out_st
+
+
+def signal(workload_or_phantom, sequence=None, n_threads=0):
+    """Convenience: complex signal of a workload (or phantom + sequence)."""
+    if sequence is None:
+        ph, seq = workload_or_phantom.phantom, workload_or_phantom.sequence
+    else:
+        ph, seq = workload_or_phantom, sequence
+    s, _ = simulate(ph, seq.events, seq.gamma_hz_per_t, n_threads=n_threads)
+    return s
+
+
+class Variant:
+    """The oracle compiled from another C source (used to check that the pins catch planted mistakes)."""
+
+    def __init__(self, c_source: str, workdir: str):
+        os.makedirs(workdir, exist_ok=True)
+        src = os.path.join(workdir, "variant.c")
+        so = os.path.join(workdir, "libvariant.so")
+        with open(src, "w") as f:
+            f.write(c_source)
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", so, src, "-lm"], check=True)
+        self.lib = _bind(so)
+
+    def simulate(self, *args, **kw):
+        return simulate(*args, lib=self.lib, **kw)
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
