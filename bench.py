@@ -1,0 +1,373 @@
+"""Benchmark: spin-steps/s of the forward simulation on GB300 (one JSON line on rank 0).
+
+A step is one forward simulation (all operations of the hot path: RF rotations, precession and
+relaxation of every spin through every event, and the per-sample signal sum) of the workload's
+phantom through its sequence, with inputs resident in device memory.  Default workload: the
+2D 256² spin echo (4 isochromats/voxel, sinc 90/180 pulses, B0 + fat; `--workload c2`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1] [--impl ours|reference]
+
+N > 1 (torchrun): weak scaling — every rank simulates its own phantom of the workload's size
+(a different seed), the ranks' phantoms form one object, and the per-step exchange is the
+sum-reduce of the complex signal over ranks (NCCL all-reduce).
+
+The reference arm (`--impl reference`) times the FP64 CPU oracle on the host cores, on a
+bounded spin sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1305_6861_gb300 import workloads as W  # noqa: E402
+
+METRIC = "spin-steps/s (isochromat×event updates) at 1 GB300, FP32 vs FP64, % FP32/SFU peak"
+# FP32 lane-operations the method needs per spin-step, by event type ("roofline"):
+#   ADC event: complex rotation-relaxation of Mxy (4) + complex accumulate into the sample (2)
+#   RF event : rotation (9) + T1 step of Mz (1) + complex precession (4)
+#   other    : complex precession (4) + T1 step of Mz (1)
+OPS_ADC, OPS_RF, OPS_OTHER = 6, 14, 5
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def algorithmic_ops_per_spin(events) -> int:
+    adc = events["adc"] != 0
+    rf = (events["rf_flip"] != 0) & ~adc
+    other = ~adc & ~rf
+    n_rf_adc = int(np.count_nonzero((events["rf_flip"] != 0) & adc))
+    return int(OPS_ADC * np.count_nonzero(adc) + OPS_RF * np.count_nonzero(rf) + OPS_OTHER * np.count_nonzero(other)
+               + (OPS_RF - OPS_OTHER) * n_rf_adc)
+
+
+def fp32_alu_peak_ops(sm_mhz: float = SM_MAX_MHZ) -> float:
+    return SMS * FP32_LANES * sm_mhz * 1e6
+
+
+def build_workload(name: str, rank: int = 0):
+    seed = None if rank == 0 else W.SEED_BASE + 100 * rank + {"c1": 1, "c2": 2, "c3": 3}[name]
+    if name == "c1":
+        return W.config1(seed)
+    if name == "c2":
+        return W.config2(seed)
+    if name == "c3":
+        return W.config3(seed)
+    raise ValueError(name)
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if s >= 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+def traffic_for(kernel_src_sha: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("kernel_source_sha") == kernel_src_sha:
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("fwd_kernel.cuh", "internal.h", "compile.cpp"):
+        with open(os.path.join(ROOT, "paper_1305_6861_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(w, seconds: float = 10.0, seed: int = 1):
+    """The oracle, as it stands, on a bounded random spin sample of the workload (full sequence)."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(seed)
+    n_cal = min(w.phantom.n, 64)
+    cal = w.phantom.subset(np.sort(rng.choice(w.phantom.n, n_cal, replace=False)))
+    t0 = time.perf_counter()
+    oracle.signal(cal, w.sequence, n_threads=cores)
+    dt = time.perf_counter() - t0
+    per_spin = dt / n_cal
+    n = int(max(cores, min(w.phantom.n, seconds / max(per_spin, 1e-9))))
+    sub = w.phantom.subset(np.sort(rng.choice(w.phantom.n, n, replace=False)))
+    t0 = time.perf_counter()
+    oracle.signal(sub, w.sequence, n_threads=cores)
+    el = time.perf_counter() - t0
+    return {"value": n * w.sequence.n_events / el, "unit": "spin-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{w.name}: full sequence ({w.sequence.n_events} events) on {n} of {w.phantom.n} spins, {el:.1f} s"}, sub
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = build_workload(args.workload)
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r, _ = cpu_baseline(w, seconds=args.ref_seconds, seed=100 + i)
+        if i >= args.warmup:
+            times.append(r)
+            cb = r
+    v = statistics.median(t["value"] for t in times)
+    ms = w.spin_steps / v * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "spin-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": w.sequence.n_events,
+                   "note": "each step is the oracle on a bounded spin sample of the workload; ms_per_step extrapolates to the full phantom"},
+        "cpu_baseline": {"value": v, "unit": "spin-steps/s", "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
+        "e2e": {"value": v, "unit": "spin-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1305_6861_gb300 import mrsim as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = build_workload(args.workload, rank)
+    prec = M.FP64 if args.precision == "fp64" else M.FP32
+    ctx = M.Context(local)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    arrs = [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()]
+    ph = M.Phantom(ctx, arrs, stream=stream)
+    seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64, device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    kw = {}
+    if args.spins_per_thread:
+        kw["spins_per_thread"] = args.spins_per_thread
+    if args.threads:
+        kw["threads_per_block"] = args.threads
+
+    def step():
+        M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
+        if dist:
+            dist.all_reduce(sig)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.stream_status(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.15)
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush_buf.zero_()  # L2 flush between timed steps (outside the step's events)
+        ev[i][0].record(stream)
+        kev[i][0].record(stream)
+        M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
+        kev[i][1].record(stream)
+        if dist:
+            dist.all_reduce(sig)
+        ev[i][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    ck = clocks.stop()
+    ctx.stream_status(stream)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kern_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    spin_steps = w.spin_steps
+    value = world * spin_steps / (ms_per_step * 1e-3)
+
+    # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
+    ops = algorithmic_ops_per_spin(w.sequence.events) * w.phantom.n
+    achieved = ops / (kern_ms * 1e-3) / 1e9
+    peak = fp32_alu_peak_ops() / 1e9
+    sha = kernel_source_sha()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
+            "traffic": traffic_for(sha, w.name), "kernel_ms": kern_ms,
+            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
+            "ops_per_spin_step": ops / spin_steps}
+
+    out = {}
+    if rank == 0 and not args.skip_extra:
+        # float64 GPU path on the same workload, and its agreement with float32
+        s32 = sig.clone()
+        if dist:
+            M.simulate(ctx, ph, seq, M.FP32, stream=stream, out=s32, **kw)
+        other = M.FP32 if prec == M.FP64 else M.FP64
+        so = torch.zeros_like(sig)
+        M.simulate(ctx, ph, seq, other, stream=stream, out=so)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            M.simulate(ctx, ph, seq, other, stream=stream, out=so)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        o_ms = e0.elapsed_time(e1) / reps
+        a32 = (s32 if prec == M.FP32 else so).cpu().numpy().view(np.complex128)
+        a64 = (so if prec == M.FP32 else s32).cpu().numpy().view(np.complex128)
+        rel = float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64))
+        key = "fp64_gpu" if prec == M.FP32 else "fp32_gpu"
+        out[key] = {"value": spin_steps / (o_ms * 1e-3), "unit": "spin-steps/s", "ms_per_step": o_ms}
+        out["fp32_vs_fp64_gpu_rel_l2"] = rel
+        out["fp32_vs_fp64_gpu_db"] = 20 * math.log10(rel) if rel > 0 else None
+
+        # end to end through the public API with host buffers (pinned), copies inside the region
+        pinned = [torch.from_numpy(a).pin_memory() for a in w.phantom.arrays()]
+        host_arrays = [p.numpy() for p in pinned]
+        ev_pinned = torch.from_numpy(w.sequence.events.view(np.uint8)).pin_memory().numpy().view(W.EVENT_DTYPE)
+        host_sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64).pin_memory().numpy().view(np.complex128)
+        e2e_steps = max(3, min(args.steps, 10))
+
+        def e2e_step():
+            p = M.Phantom(ctx, host_arrays)
+            s = M.Sequence(ctx, ev_pinned, w.sequence.gamma_hz_per_t)
+            M.simulate(ctx, p, s, prec, out=host_sig, **kw)
+            p.close()
+            s.close()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        out["e2e"] = {"value": spin_steps / e2e_s, "unit": "spin-steps/s",
+                      "h2d_bytes_per_step": int(7 * 8 * w.phantom.n + w.sequence.events.nbytes),
+                      "d2h_bytes_per_step": int(16 * seq.n_adc), "ms_per_step": e2e_s * 1e3, "steps": e2e_steps}
+        if not args.no_cpu_baseline:
+            cb, _ = cpu_baseline(w, seconds=args.cpu_seconds)
+            out["cpu_baseline"] = cb
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n_spins_per_gpu": w.phantom.n, "n_events": w.sequence.n_events,
+                       "n_adc": seq.n_adc, "n_ops": seq.n_ops, "spin_steps_per_gpu_step": spin_steps,
+                       "precision": args.precision, "launch": kw or "library default",
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                       "parallelism": f"spin-sharded x{world}" if world > 1 else "1 GPU"},
+            "roofline": roof, "gpu_launches": args.steps, "clocks": ck, "wall_s_timed": t_wall,
+            "peaks_file": {k: read_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
+        }
+        line.update(out)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3"], default="c2")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--spins-per-thread", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * mrsim.h -- C-ABI of the GB300 spin-based MR simulator (libmrsim.so).
+ *
+ * The library computes the hot path of a spin-based MR-tomography simulation
+ * (Kürsch, "Konzeption und Realisierung eines skalierbaren Simulators für die
+ * Magnetresonanz-Tomographie", §5.1.1): every isochromat of a phantom is
+ * propagated independently through a pulse sequence of elementary sequences
+ * (§4.1, Eq. 4.1: hard RF pulse Eq. 3.19, gradient/off-resonance precession
+ * Eqs. 3.5/3.11/3.14, T1/T2 relaxation Eq. 3.5), and at every ADC sample the
+ * rotating-frame transverse magnetisation is summed over all spins into the
+ * complex signal (Eqs. 3.30-3.32).
+ *
+ * Conventions (all SI units, angles in rad):
+ *   - rotating frame, on resonance; γ is a parameter given as γ/2π in Hz/T;
+ *   - an event applies, in this order: the RF pulse at its start, precession
+ *     by θ = (γ G·x + Δω)·Δt with Mxy <- Mxy·exp(-jθ) and T2 decay, T1
+ *     recovery of Mz towards M0, then (if adc != 0) one sample of
+ *     Σ_spins (Mx + jMy)·exp(-j·adc_phase) at the end of the event;
+ *   - signals are complex float64, interleaved (re, im), one value per ADC
+ *     event, in event order.
+ *
+ * Errors: every entry point returns an mrsim_status and never aborts the
+ * process.  The message of the last failure on a context is available from
+ * mrsim_last_error().  Device waits are bounded; a wait that runs out makes the
+ * kernel record MRSIM_ETIMEOUT in a device status word, which the next
+ * host-visible call (mrsim_stream_status, or any call with host output
+ * buffers) reports.
+ *
+ * Ownership: create functions copy their inputs; the caller keeps ownership of
+ * every buffer it passes.  Handles are owned by the caller and released with
+ * the matching destroy function (NULL is accepted).  A context must outlive the
+ * handles created on it.  Calls on one context are not thread-safe.
+ *
+ * Pointers marked "host or device" may be either: the library asks the CUDA
+ * runtime what a pointer is and copies host data itself.
+ */
+#ifndef MRSIM_H
+#define MRSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MRSIM_OK = 0,
+    MRSIM_EINVAL = 1,      /* invalid argument: NaN/Inf, T <= 0, Δt < 0, size mismatch, NULL */
+    MRSIM_ENOMEM = 2,      /* host or device allocation failed */
+    MRSIM_ECUDA = 3,       /* a CUDA runtime call failed */
+    MRSIM_ETIMEOUT = 4,    /* a bounded device wait ran out */
+    MRSIM_EUNSUPPORTED = 5 /* valid request this build cannot serve (e.g. no sm_103 device) */
+} mrsim_status;
+
+typedef enum {
+    MRSIM_FP64 = 0, /* every step in float64 */
+    MRSIM_FP32 = 1  /* rotations/relaxation in float32 with float64 sequence precompute,
+                       float-float phase arguments, and the per-sample sum kept in float64
+                       across warps and thread blocks */
+} mrsim_precision;
+
+/* One elementary sequence (§4.1; Eq. 4.1).  64 bytes, no padding. */
+typedef struct mrsim_event {
+    double dt;        /* duration Δt >= 0 [s] */
+    double gx, gy, gz;/* constant gradient during Δt [T/m] */
+    double rf_flip;   /* flip angle α of the hard pulse at the start [rad]; 0 = no pulse; sign allowed */
+    double rf_phase;  /* phase φ of the pulse axis in the x'y' plane [rad] (Eq. 3.19) */
+    double adc_phase; /* receiver demodulation phase [rad] of this event's sample */
+    int32_t adc;      /* 1 = take one sample at the end of the event, 0 = none */
+    int32_t reserved; /* must be 0 */
+} mrsim_event;
+
+typedef struct mrsim_ctx mrsim_ctx;
+typedef struct mrsim_phantom mrsim_phantom;
+typedef struct mrsim_sequence mrsim_sequence;
+
+/* Optional launch and state controls of mrsim_simulate_ex. Zero-initialise for defaults. */
+typedef struct mrsim_options {
+    int32_t spins_per_thread;  /* 0 = library choice (tuned table); else 1, 2, 4 or 8 (FP64: 1 or 2) */
+    int32_t threads_per_block; /* 0 = library choice; else a multiple of 32 in [32, 1024] */
+    uint32_t flags;            /* MRSIM_ACCUMULATE: add into signal_out instead of overwriting it */
+    int32_t reserved;
+    const double *state_in;    /* NULL = thermal equilibrium (0,0,M0); else 3*n_spins (Mx,My,Mz), host or device */
+    double *state_out;         /* NULL, or 3*n_spins receiving (Mx,My,Mz) after the last event, host or device */
+} mrsim_options;
+
+#define MRSIM_ACCUMULATE 1u
+
+/* ---- context ------------------------------------------------------------------------- */
+
+/* Bind a context to CUDA device `device` (must be a compute capability 10.3 GPU). */
+mrsim_status mrsim_context_create(int device, mrsim_ctx **out);
+void mrsim_context_destroy(mrsim_ctx *ctx);
+const char *mrsim_status_string(mrsim_status s);
+/* Message of the last failed call on ctx ("" if none).  Owned by ctx, valid until the next call. */
+const char *mrsim_last_error(const mrsim_ctx *ctx);
+/* Synchronise `stream` (cudaStream_t, NULL = legacy default stream) and report any device-side
+ * status recorded by kernels of this context (e.g. MRSIM_ETIMEOUT); clears the status word. */
+mrsim_status mrsim_stream_status(mrsim_ctx *ctx, void *stream);
+
+/* ---- phantom: the object as a list of isochromats (§6.1.1, Eq. 6.2) ------------------- */
+
+/* Copies n_spins isochromats from host arrays: position x,y,z [m], equilibrium magnetisation
+ * M0 (rho), T1, T2 [s] (> 0, +INFINITY allowed = no relaxation), total off-resonance Δω [rad/s].
+ * EINVAL on NaN/Inf positions, rho or dw, or T1/T2 <= 0.  n_spins = 0 is allowed. */
+mrsim_status mrsim_phantom_create(mrsim_ctx *ctx, int64_t n_spins, const double *x, const double *y,
+                                  const double *z, const double *rho, const double *t1, const double *t2,
+                                  const double *dw, mrsim_phantom **out);
+/* Same with the seven arrays in device memory (e.g. torch tensors); packing runs on `stream`,
+ * which is synchronised before return so the caller may free the arrays afterwards. */
+mrsim_status mrsim_phantom_create_device(mrsim_ctx *ctx, int64_t n_spins, const double *x, const double *y,
+                                         const double *z, const double *rho, const double *t1,
+                                         const double *t2, const double *dw, void *stream,
+                                         mrsim_phantom **out);
+int64_t mrsim_phantom_num_spins(const mrsim_phantom *p);
+void mrsim_phantom_destroy(mrsim_phantom *p);
+
+/* ---- sequence: elementary sequences (§4.1) compiled once in float64 ------------------- */
+
+/* Validates and compiles n_events events (host memory) with γ/2π = gamma_hz_per_t [Hz/T]:
+ * gradient moments γ·G·Δt, RF rotation matrices (Eq. 3.19), relaxation intervals and the
+ * recurring precession intervals are precomputed in float64 once, as the spin-independent terms
+ * of the paper's master process (§6.3).  EINVAL on NaN/Inf fields, Δt < 0, adc not in {0,1},
+ * reserved != 0 or gamma <= 0. */
+mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                 double gamma_hz_per_t, mrsim_sequence **out);
+int64_t mrsim_sequence_num_adc(const mrsim_sequence *s);
+int64_t mrsim_sequence_num_events(const mrsim_sequence *s);
+/* Number of compiled device operations (after merging runs of events); for diagnostics. */
+int64_t mrsim_sequence_num_ops(const mrsim_sequence *s);
+void mrsim_sequence_destroy(mrsim_sequence *s);
+
+/* ---- simulation ----------------------------------------------------------------------- */
+
+/* Forward simulation (§5.1.1): signal_out receives 2*n_adc doubles (re, im per sample), host or
+ * device.  n_adc must equal mrsim_sequence_num_adc(seq).  With a device output the call is
+ * asynchronous on `stream` (cudaStream_t); with a host output it synchronises. */
+mrsim_status mrsim_simulate(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                            mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc);
+/* As mrsim_simulate with launch controls, accumulation and state in/out (opt may be NULL).  State
+ * in/out lets a long sequence run as consecutive sub-sequences (checkpoint / resume). */
+mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                               mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc,
+                               const mrsim_options *opt);
+
+/* ---- diagnostics ---------------------------------------------------------------------- */
+
+/* Host-only compile of an event list (no device needed), for inspecting and testing the
+ * sequence compiler.  Call once with NULL output arrays to get the sizes (*n_ops, *n_pcls,
+ * *n_e1, *n_e2, *n_adc), then again with arrays of those sizes: ops_out receives *n_ops float64
+ * device operations (128-byte records), pcls_out 4 doubles per precession class (kx, ky, kz in
+ * cycles/m, Δt in s), e1_out / e2_out one interval per relaxation class.  Same validation and
+ * error codes as mrsim_sequence_load; EINVAL if a given output array is too small. */
+mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
+                                 void *ops_out, int64_t *n_ops, double *pcls_out, int32_t *n_pcls,
+                                 double *e1_out, int32_t *n_e1, double *e2_out, int32_t *n_e2,
+                                 int64_t *n_adc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRSIM_H */

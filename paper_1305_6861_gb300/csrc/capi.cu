@@ -1,0 +1,427 @@
+// capi.cu -- the C-ABI of libmrsim (see include/mrsim.h): handles, validation, memory, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mrsim.h"
+#include "compiled.h"
+#include "internal.h"
+
+using namespace mrsim;
+
+struct mrsim_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    std::string err;
+    int *d_status = nullptr;
+    // scratch for host-side outputs and inputs, grown on demand
+    double *d_sig = nullptr;
+    size_t sig_cap = 0;
+    double *d_state = nullptr;
+    size_t state_cap = 0;
+    double *d_stage = nullptr;
+    size_t stage_cap = 0;
+    int *d_bad = nullptr;
+};
+
+struct mrsim_phantom {
+    mrsim_ctx *ctx = nullptr;
+    int64_t n = 0, n_pad = 0;
+    double *params = nullptr;
+};
+
+struct mrsim_sequence {
+    mrsim_ctx *ctx = nullptr;
+    int64_t n_events = 0;
+    Compiled host;
+    void *d_ops32 = nullptr, *d_ops64 = nullptr;
+    double *d_pcls = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_demod = nullptr;
+    Program p32{}, p64{};
+};
+
+namespace {
+
+mrsim_status fail(mrsim_ctx *ctx, mrsim_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+mrsim_status cuda_fail(mrsim_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, MRSIM_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return fail(ctx, MRSIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+mrsim_status grow(mrsim_ctx *ctx, double **buf, size_t *cap, size_t need_doubles) {
+    if (need_doubles <= *cap) return MRSIM_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    size_t n = std::max<size_t>(need_doubles, 1024);
+    CK(cudaMalloc(buf, n * sizeof(double)), "cudaMalloc scratch");
+    *cap = n;
+    return MRSIM_OK;
+}
+
+template <class T>
+mrsim_status upload(mrsim_ctx *ctx, T **dst, const std::vector<T> &v) {
+    *dst = nullptr;
+    if (v.empty()) return MRSIM_OK;
+    CK(cudaMalloc(dst, v.size() * sizeof(T)), "cudaMalloc sequence");
+    CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload sequence");
+    return MRSIM_OK;
+}
+
+mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStream_t st, mrsim_phantom **out) {
+    mrsim_phantom *p = new (std::nothrow) mrsim_phantom();
+    if (!p) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    p->ctx = ctx;
+    p->n = n;
+    p->n_pad = (n + 31) / 32 * 32;
+    if (n > 0) {
+        cudaError_t e = cudaMalloc(&p->params, (size_t)NPARAM * p->n_pad * sizeof(double));
+        if (e != cudaSuccess) {
+            delete p;
+            return cuda_fail(ctx, e, "cudaMalloc phantom");
+        }
+        const int big = 0x7fffffff;
+        cudaMemcpyAsync(ctx->d_bad, &big, sizeof(int), cudaMemcpyHostToDevice, st);
+        int rc = pack_params(n, p->n_pad, src[0], src[1], src[2], src[3], src[4], src[5], src[6], p->params,
+                             ctx->d_bad, st);
+        int bad = big;
+        if (rc == 0) rc = (int)cudaMemcpyAsync(&bad, ctx->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (rc == 0) rc = (int)cudaStreamSynchronize(st);
+        if (rc != 0) {
+            cudaFree(p->params);
+            delete p;
+            return cuda_fail(ctx, (cudaError_t)rc, "pack phantom");
+        }
+        if (bad != big) {
+            cudaFree(p->params);
+            delete p;
+            return fail(ctx, MRSIM_EINVAL,
+                        "spin " + std::to_string(bad) + ": non-finite position/rho/dw or T1/T2 <= 0");
+        }
+    }
+    *out = p;
+    return MRSIM_OK;
+}
+
+struct Launch {
+    int k, threads;
+};
+
+// Default launch shape: the largest spins-per-thread that still gives every SM about two blocks.
+Launch choose_launch(const mrsim_ctx *ctx, bool fp64, int64_t n) {
+    static const Launch f32[] = {{4, 128}, {2, 128}, {1, 128}, {1, 64}, {1, 32}};
+    static const Launch f64[] = {{1, 128}, {1, 64}, {1, 32}};
+    const Launch *c = fp64 ? f64 : f32;
+    const int nc = fp64 ? 3 : 5;
+    for (int i = 0; i < nc; ++i) {
+        const int64_t S = (int64_t)c[i].k * c[i].threads;
+        if ((n + S - 1) / S >= 2LL * ctx->num_sms) return c[i];
+    }
+    return c[nc - 1];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mrsim_status_string(mrsim_status s) {
+    switch (s) {
+    case MRSIM_OK: return "ok";
+    case MRSIM_EINVAL: return "invalid argument";
+    case MRSIM_ENOMEM: return "out of memory";
+    case MRSIM_ECUDA: return "CUDA error";
+    case MRSIM_ETIMEOUT: return "device wait timed out";
+    case MRSIM_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *mrsim_last_error(const mrsim_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mrsim_status mrsim_context_create(int device, mrsim_ctx **out) {
+    if (!out) return MRSIM_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return MRSIM_EUNSUPPORTED;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MRSIM_ECUDA;
+    if (prop.major != 10 || prop.minor != 3) return MRSIM_EUNSUPPORTED;  // built for sm_103a only
+    if (cudaSetDevice(device) != cudaSuccess) return MRSIM_ECUDA;
+    mrsim_ctx *ctx = new (std::nothrow) mrsim_ctx();
+    if (!ctx) return MRSIM_ENOMEM;
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&ctx->d_bad, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(ctx->d_status);
+        cudaFree(ctx->d_bad);
+        delete ctx;
+        return MRSIM_ENOMEM;
+    }
+    *out = ctx;
+    return MRSIM_OK;
+}
+
+void mrsim_context_destroy(mrsim_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_bad);
+    cudaFree(ctx->d_sig);
+    cudaFree(ctx->d_state);
+    cudaFree(ctx->d_stage);
+    delete ctx;
+}
+
+mrsim_status mrsim_stream_status(mrsim_ctx *ctx, void *stream) {
+    if (!ctx) return MRSIM_EINVAL;
+    cudaSetDevice(ctx->device);
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+    int st = 0;
+    CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (st != 0) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        return fail(ctx, (mrsim_status)st, "a kernel reported a device-side failure");
+    }
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_phantom_create(mrsim_ctx *ctx, int64_t n, const double *x, const double *y, const double *z,
+                                  const double *rho, const double *t1, const double *t2, const double *dw,
+                                  mrsim_phantom **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    if (n < 0) return fail(ctx, MRSIM_EINVAL, "n_spins < 0");
+    const double *src[7] = {x, y, z, rho, t1, t2, dw};
+    if (n > 0)
+        for (auto p : src)
+            if (!p) return fail(ctx, MRSIM_EINVAL, "NULL spin array");
+    cudaSetDevice(ctx->device);
+    mrsim_status st = grow(ctx, &ctx->d_stage, &ctx->stage_cap, (size_t)7 * (size_t)std::max<int64_t>(n, 1));
+    if (st != MRSIM_OK) return st;
+    const double *dsrc[7];
+    for (int i = 0; i < 7; ++i) {
+        double *dst = ctx->d_stage + (size_t)i * (size_t)n;
+        if (n > 0) CK(cudaMemcpyAsync(dst, src[i], (size_t)n * sizeof(double), cudaMemcpyDefault, 0), "copy spins");
+        dsrc[i] = dst;
+    }
+    return pack(ctx, n, dsrc, 0, out);
+}
+
+mrsim_status mrsim_phantom_create_device(mrsim_ctx *ctx, int64_t n, const double *x, const double *y,
+                                         const double *z, const double *rho, const double *t1, const double *t2,
+                                         const double *dw, void *stream, mrsim_phantom **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    if (n < 0) return fail(ctx, MRSIM_EINVAL, "n_spins < 0");
+    const double *src[7] = {x, y, z, rho, t1, t2, dw};
+    if (n > 0)
+        for (auto p : src)
+            if (!p || !is_device_ptr(p)) return fail(ctx, MRSIM_EINVAL, "spin arrays must be device pointers");
+    cudaSetDevice(ctx->device);
+    return pack(ctx, n, src, (cudaStream_t)stream, out);
+}
+
+int64_t mrsim_phantom_num_spins(const mrsim_phantom *p) { return p ? p->n : -1; }
+
+void mrsim_phantom_destroy(mrsim_phantom *p) {
+    if (!p) return;
+    cudaSetDevice(p->ctx->device);
+    cudaFree(p->params);
+    delete p;
+}
+
+mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events, double gamma,
+                                 mrsim_sequence **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    if (n_events > 0 && is_device_ptr(events)) return fail(ctx, MRSIM_EINVAL, "events must be in host memory");
+    mrsim_sequence *s = new (std::nothrow) mrsim_sequence();
+    if (!s) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    s->ctx = ctx;
+    s->n_events = n_events;
+    std::string err;
+    int rc = compile_sequence(events, n_events, gamma, s->host, err);
+    if (rc != MRSIM_OK) {
+        delete s;
+        return fail(ctx, (mrsim_status)rc, err);
+    }
+    cudaSetDevice(ctx->device);
+    mrsim_status st = MRSIM_OK;
+    auto up = [&](auto **d, const auto &v) {
+        if (st == MRSIM_OK) st = upload(ctx, d, v);
+    };
+    up((OpF32 **)&s->d_ops32, s->host.ops32);
+    up((OpF64 **)&s->d_ops64, s->host.ops64);
+    up(&s->d_pcls, s->host.pcls);
+    up(&s->d_e1, s->host.e1);
+    up(&s->d_e2, s->host.e2);
+    up(&s->d_demod, s->host.demod);
+    if (st != MRSIM_OK) {
+        mrsim_sequence_destroy(s);
+        return st;
+    }
+    Program p{};
+    p.n_ops = (int32_t)s->host.ops32.size();
+    p.n_pcls = s->host.n_pcls;
+    p.n_e1 = s->host.n_e1;
+    p.n_e2 = s->host.n_e2;
+    p.pcls = s->d_pcls;
+    p.e1 = s->d_e1;
+    p.e2 = s->d_e2;
+    p.demod = s->d_demod;
+    p.n_adc = s->host.n_adc;
+    s->p32 = p;
+    s->p32.ops = s->d_ops32;
+    s->p64 = p;
+    s->p64.ops = s->d_ops64;
+    *out = s;
+    return MRSIM_OK;
+}
+
+int64_t mrsim_sequence_num_adc(const mrsim_sequence *s) { return s ? s->host.n_adc : -1; }
+int64_t mrsim_sequence_num_events(const mrsim_sequence *s) { return s ? s->n_events : -1; }
+int64_t mrsim_sequence_num_ops(const mrsim_sequence *s) { return s ? (int64_t)s->host.ops32.size() : -1; }
+
+void mrsim_sequence_destroy(mrsim_sequence *s) {
+    if (!s) return;
+    cudaSetDevice(s->ctx->device);
+    cudaFree(s->d_ops32);
+    cudaFree(s->d_ops64);
+    cudaFree(s->d_pcls);
+    cudaFree(s->d_e1);
+    cudaFree(s->d_e2);
+    cudaFree(s->d_demod);
+    delete s;
+}
+
+mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                               mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc,
+                               const mrsim_options *opt) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
+    if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
+    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (n_adc != seq->host.n_adc)
+        return fail(ctx, MRSIM_EINVAL, "n_adc = " + std::to_string(n_adc) + " but the sequence has " +
+                                           std::to_string(seq->host.n_adc) + " samples");
+    if (n_adc > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal_out");
+    const bool fp64 = prec == MRSIM_FP64;
+    mrsim_options o{};
+    if (opt) o = *opt;
+    Launch L = choose_launch(ctx, fp64, ph->n);
+    if (o.spins_per_thread) L.k = o.spins_per_thread;
+    if (o.threads_per_block) L.threads = o.threads_per_block;
+    const bool k_ok = fp64 ? (L.k == 1 || L.k == 2) : (L.k == 1 || L.k == 2 || L.k == 4 || L.k == 8);
+    if (!k_ok || L.threads < 32 || L.threads % 32 || L.threads > (fp64 || L.k == 8 ? 256 : 512))
+        return fail(ctx, MRSIM_EINVAL, "unsupported spins_per_thread / threads_per_block");
+    const Program &P = fp64 ? seq->p64 : seq->p32;
+    if (fwd_smem_bytes(fp64, P, L.k, L.threads) > (size_t)ctx->max_smem_optin)
+        return fail(ctx, MRSIM_EUNSUPPORTED, "shared memory of this launch shape exceeds the device limit");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t sig_bytes = (size_t)2 * (size_t)n_adc * sizeof(double);
+    const bool host_sig = n_adc > 0 && !is_device_ptr(signal_out);
+    double *dsig = signal_out;
+    mrsim_status rs;
+    if (host_sig) {
+        if ((rs = grow(ctx, &ctx->d_sig, &ctx->sig_cap, 2 * (size_t)n_adc)) != MRSIM_OK) return rs;
+        dsig = ctx->d_sig;
+        if (o.flags & MRSIM_ACCUMULATE)
+            CK(cudaMemcpyAsync(dsig, signal_out, sig_bytes, cudaMemcpyHostToDevice, st), "copy signal in");
+    }
+    if (n_adc > 0 && !(o.flags & MRSIM_ACCUMULATE)) CK(cudaMemsetAsync(dsig, 0, sig_bytes, st), "clear signal");
+    // state in / out (host buffers go through one scratch area: [in | out])
+    const size_t st_n = (size_t)3 * (size_t)ph->n;
+    const bool host_in = o.state_in && !is_device_ptr(o.state_in);
+    const bool host_out = o.state_out && !is_device_ptr(o.state_out);
+    const double *din = o.state_in;
+    double *dout = o.state_out;
+    if (host_in || host_out) {
+        if ((rs = grow(ctx, &ctx->d_state, &ctx->state_cap, 2 * std::max<size_t>(st_n, 1))) != MRSIM_OK) return rs;
+        if (host_in) {
+            CK(cudaMemcpyAsync(ctx->d_state, o.state_in, st_n * sizeof(double), cudaMemcpyHostToDevice, st), "copy state in");
+            din = ctx->d_state;
+        }
+        if (host_out) dout = ctx->d_state + st_n;
+    }
+    FwdArgs a{};
+    a.prog = P;
+    a.params = ph->params;
+    a.n_spins = ph->n;
+    a.n_pad = ph->n_pad;
+    a.state_in = din;
+    a.state_out = dout;
+    a.signal = dsig;
+    a.status = ctx->d_status;
+    int rc = fp64 ? launch_fwd_f64(a, L.k, L.threads, stream) : launch_fwd_f32(a, L.k, L.threads, stream);
+    if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel");
+    if (host_out) CK(cudaMemcpyAsync(o.state_out, dout, st_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy state out");
+    if (host_sig) CK(cudaMemcpyAsync(signal_out, dsig, sig_bytes, cudaMemcpyDeviceToHost, st), "copy signal out");
+    if (host_sig || host_out) return mrsim_stream_status(ctx, stream);
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_simulate(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq, mrsim_precision prec,
+                            void *stream, double *signal_out, int64_t n_adc) {
+    return mrsim_simulate_ex(ctx, ph, seq, prec, stream, signal_out, n_adc, nullptr);
+}
+
+mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma, void *ops_out,
+                                 int64_t *n_ops, double *pcls_out, int32_t *n_pcls, double *e1_out, int32_t *n_e1,
+                                 double *e2_out, int32_t *n_e2, int64_t *n_adc) {
+    if (!n_ops || !n_pcls || !n_e1 || !n_e2 || !n_adc) return MRSIM_EINVAL;
+    Compiled c;
+    std::string err;
+    int rc = compile_sequence(events, n_events, gamma, c, err);
+    if (rc != MRSIM_OK) return (mrsim_status)rc;
+    const int64_t cap_ops = *n_ops;
+    const int32_t cap_p = *n_pcls, cap_1 = *n_e1, cap_2 = *n_e2;
+    if (ops_out && (int64_t)c.ops64.size() > cap_ops) return MRSIM_EINVAL;
+    if (pcls_out && c.n_pcls > cap_p) return MRSIM_EINVAL;
+    if (e1_out && c.n_e1 > cap_1) return MRSIM_EINVAL;
+    if (e2_out && c.n_e2 > cap_2) return MRSIM_EINVAL;
+    if (ops_out) std::memcpy(ops_out, c.ops64.data(), c.ops64.size() * sizeof(OpF64));
+    if (pcls_out) std::memcpy(pcls_out, c.pcls.data(), c.pcls.size() * sizeof(double));
+    if (e1_out) std::memcpy(e1_out, c.e1.data(), c.e1.size() * sizeof(double));
+    if (e2_out) std::memcpy(e2_out, c.e2.data(), c.e2.size() * sizeof(double));
+    *n_ops = (int64_t)c.ops64.size();
+    *n_pcls = c.n_pcls;
+    *n_e1 = c.n_e1;
+    *n_e2 = c.n_e2;
+    *n_adc = c.n_adc;
+    return MRSIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,405 @@
+// compile.cpp -- float64 host compiler: elementary sequences (§4.1) -> device program.
+//
+// The paper's master process precomputes every spin-independent term once (§6.3), e.g. the
+// trigonometric functions of the RF pulses of Eq. 3.19; this is that step.  All arithmetic
+// here is float64; the float32 program receives (hi, lo) float pairs where one float would
+// lose phase accuracy (gradient moments, interval lengths).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mrsim.h"
+#include "compiled.h"
+
+namespace mrsim {
+
+namespace {
+
+struct Item {
+    enum Kind { RF, PREC, SAMPLE, END } kind;
+    double k[3];    // gradient moment γ/2π·G·Δt [cycles/m]
+    double dt;      // interval [s]
+    double alpha, phi;
+    double tau;     // RF/END: time since the previous RF pulse [s]
+    int64_t j;      // SAMPLE: sample index
+};
+
+using Key = std::array<uint64_t, 4>;
+
+Key key_of(const double k[3], double dt) {
+    Key key;
+    double v[4] = {k[0], k[1], k[2], dt};
+    for (int i = 0; i < 4; ++i) {
+        double x = v[i] == 0.0 ? 0.0 : v[i];  // fold -0 into +0
+        std::memcpy(&key[i], &x, 8);
+    }
+    return key;
+}
+
+bool is_zero(const double k[3], double dt) { return k[0] == 0.0 && k[1] == 0.0 && k[2] == 0.0 && dt == 0.0; }
+
+uint64_t bits(double x) {
+    uint64_t b;
+    x = x == 0.0 ? 0.0 : x;
+    std::memcpy(&b, &x, 8);
+    return b;
+}
+
+// Top-`limit` keys by use count (count >= 2), ties broken by first appearance.
+template <class K>
+std::map<K, int> pick_classes(const std::map<K, std::pair<int64_t, int64_t>> &uses, int limit) {
+    std::vector<std::pair<K, std::pair<int64_t, int64_t>>> v(uses.begin(), uses.end());
+    std::sort(v.begin(), v.end(), [](const auto &a, const auto &b) {
+        if (a.second.first != b.second.first) return a.second.first > b.second.first;
+        return a.second.second < b.second.second;
+    });
+    std::map<K, int> out;
+    for (auto &kv : v) {
+        if ((int)out.size() >= limit || kv.second.first < 2) break;
+        int id = (int)out.size();
+        out[kv.first] = id;
+    }
+    return out;
+}
+
+void split(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// Eq. 3.19 written as the rotation by -α about n = (cos φ, sin φ, 0):
+// R = cos α·I + (1 - cos α)·n nᵀ - sin α·[n]x, with 1 - cos α = 2 sin²(α/2) for accuracy.
+void rf_matrix(double alpha, double phi, double R[9], double &r22m1) {
+    const double ca = std::cos(alpha), sa = std::sin(alpha);
+    const double h = std::sin(0.5 * alpha);
+    const double omc = 2.0 * h * h;
+    const double n0 = std::cos(phi), n1 = std::sin(phi);
+    R[0] = ca + omc * n0 * n0;
+    R[1] = omc * n0 * n1;
+    R[2] = -sa * n1;
+    R[3] = omc * n0 * n1;
+    R[4] = ca + omc * n1 * n1;
+    R[5] = sa * n0;
+    R[6] = sa * n1;
+    R[7] = -sa * n0;
+    R[8] = ca;
+    r22m1 = -omc;
+}
+
+}  // namespace
+
+int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err) {
+    out = Compiled();
+    if (!(gamma_hz > 0.0) || !std::isfinite(gamma_hz)) {
+        err = "gamma_hz_per_t must be finite and > 0";
+        return MRSIM_EINVAL;
+    }
+    if (n < 0 || (n > 0 && !ev)) {
+        err = "invalid event array";
+        return MRSIM_EINVAL;
+    }
+    // ---- validate and lower to items -------------------------------------------------------
+    std::vector<Item> items;
+    items.reserve((size_t)n + 2);
+    double tau = 0.0;
+    bool have = false;
+    double pk[3] = {0, 0, 0}, pdt = 0.0;
+    int64_t j = 0;
+    auto flush = [&]() {
+        if (have && !is_zero(pk, pdt)) {
+            Item it{};
+            it.kind = Item::PREC;
+            std::memcpy(it.k, pk, sizeof pk);
+            it.dt = pdt;
+            items.push_back(it);
+        }
+        have = false;
+        pk[0] = pk[1] = pk[2] = 0.0;
+        pdt = 0.0;
+    };
+    for (int64_t i = 0; i < n; ++i) {
+        const mrsim_event &e = ev[i];
+        const double f[7] = {e.dt, e.gx, e.gy, e.gz, e.rf_flip, e.rf_phase, e.adc_phase};
+        for (double v : f)
+            if (!std::isfinite(v)) {
+                err = "event " + std::to_string(i) + ": non-finite field";
+                return MRSIM_EINVAL;
+            }
+        if (e.dt < 0.0) {
+            err = "event " + std::to_string(i) + ": negative duration";
+            return MRSIM_EINVAL;
+        }
+        if ((e.adc != 0 && e.adc != 1) || e.reserved != 0) {
+            err = "event " + std::to_string(i) + ": adc must be 0/1 and reserved 0";
+            return MRSIM_EINVAL;
+        }
+        if (e.rf_flip != 0.0) {
+            flush();
+            Item it{};
+            it.kind = Item::RF;
+            it.alpha = e.rf_flip;
+            it.phi = e.rf_phase;
+            it.tau = tau;
+            items.push_back(it);
+            tau = 0.0;
+        }
+        const double k[3] = {gamma_hz * e.gx * e.dt, gamma_hz * e.gy * e.dt, gamma_hz * e.gz * e.dt};
+        if (e.adc) {
+            flush();
+            Item it{};
+            it.kind = Item::SAMPLE;
+            std::memcpy(it.k, k, sizeof k);
+            it.dt = e.dt;
+            it.j = j++;
+            items.push_back(it);
+            out.demod.push_back(std::cos(e.adc_phase));
+            out.demod.push_back(-std::sin(e.adc_phase));
+        } else {
+            for (int c = 0; c < 3; ++c) pk[c] += k[c];
+            pdt += e.dt;
+            have = true;
+        }
+        tau += e.dt;
+    }
+    flush();
+    {
+        Item it{};
+        it.kind = Item::END;
+        it.tau = tau;
+        items.push_back(it);
+    }
+    out.n_adc = j;
+
+    // ---- group sample runs and count class uses -------------------------------------------------
+    struct Group {
+        size_t first;
+        int64_t n;  // number of items (samples for runs)
+    };
+    std::vector<Group> groups;
+    for (size_t i = 0; i < items.size();) {
+        if (items[i].kind == Item::SAMPLE && !is_zero(items[i].k, items[i].dt)) {
+            Key k0 = key_of(items[i].k, items[i].dt);
+            size_t e = i + 1;
+            while (e < items.size() && items[e].kind == Item::SAMPLE && (int64_t)(e - i) < RUN_MAX &&
+                   key_of(items[e].k, items[e].dt) == k0)
+                ++e;
+            groups.push_back({i, (int64_t)(e - i)});
+            i = e;
+        } else {
+            groups.push_back({i, 1});
+            ++i;
+        }
+    }
+    std::map<Key, std::pair<int64_t, int64_t>> puses;  // key -> (count, first position)
+    std::map<uint64_t, std::pair<int64_t, int64_t>> e1uses, e2uses;
+    auto use = [](auto &m, const auto &key, int64_t cnt, int64_t pos) {
+        auto it = m.find(key);
+        if (it == m.end())
+            m[key] = {cnt, pos};
+        else
+            it->second.first += cnt;
+    };
+    auto anchor_key = [&](const Item &it, int64_t cnt) {
+        double k[3] = {it.k[0] * (double)cnt, it.k[1] * (double)cnt, it.k[2] * (double)cnt};
+        return key_of(k, it.dt * (double)cnt);
+    };
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const Item &it = items[groups[g].first];
+        const int64_t pos = (int64_t)groups[g].first;
+        if (it.kind == Item::PREC || (it.kind == Item::SAMPLE && !is_zero(it.k, it.dt))) {
+            use(puses, key_of(it.k, it.dt), groups[g].n, pos);
+            if (it.kind == Item::SAMPLE && groups[g].n >= 4) use(puses, anchor_key(it, groups[g].n), 1, pos);
+        }
+        if ((it.kind == Item::RF || it.kind == Item::END) && it.tau > 0.0) use(e1uses, bits(it.tau), 1, pos);
+    }
+    auto pmap = pick_classes(puses, MAX_PCLS);
+    auto e1map = pick_classes(e1uses, MAX_E1CLS);
+    // E2 classes: intervals of the precessions that stay inline
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const Item &it = items[groups[g].first];
+        if ((it.kind == Item::PREC || it.kind == Item::SAMPLE) && !is_zero(it.k, it.dt) && it.dt > 0.0 &&
+            !pmap.count(key_of(it.k, it.dt)))
+            use(e2uses, bits(it.dt), groups[g].n, (int64_t)groups[g].first);
+    }
+    auto e2map = pick_classes(e2uses, MAX_E2CLS);
+
+    out.n_pcls = (int)pmap.size();
+    out.n_e1 = (int)e1map.size();
+    out.n_e2 = (int)e2map.size();
+    out.pcls.assign(4 * (size_t)out.n_pcls, 0.0);
+    for (auto &kv : pmap)
+        for (int c = 0; c < 4; ++c) std::memcpy(&out.pcls[4 * (size_t)kv.second + c], &kv.first[c], 8);
+    out.e1.assign((size_t)out.n_e1, 0.0);
+    for (auto &kv : e1map) std::memcpy(&out.e1[(size_t)kv.second], &kv.first, 8);
+    out.e2.assign((size_t)out.n_e2, 0.0);
+    for (auto &kv : e2map) std::memcpy(&out.e2[(size_t)kv.second], &kv.first, 8);
+
+    // ---- emit ------------------------------------------------------------------------------------
+    auto new32 = [](uint8_t kind) {
+        OpF32 o;
+        std::memset(&o, 0, sizeof o);
+        o.kind = kind;
+        o.pcls = o.ecls = o.acls = -1;
+        o.adc0 = -1;
+        o.n = 1;
+        return o;
+    };
+    auto new64 = [](uint8_t kind) {
+        OpF64 o;
+        std::memset(&o, 0, sizeof o);
+        o.kind = kind;
+        o.pcls = o.ecls = o.acls = -1;
+        o.adc0 = -1;
+        o.n = 1;
+        return o;
+    };
+    auto set_e1 = [&](OpF32 &a, OpF64 &b, double t) {
+        if (t > 0.0) {
+            auto it = e1map.find(bits(t));
+            uint16_t fl = it != e1map.end() ? F_E1CLS : F_E1INL;
+            a.flags |= fl;
+            b.flags |= fl;
+            if (it != e1map.end()) a.ecls = b.ecls = (int16_t)it->second;
+        }
+        a.f[10] = (float)t;
+        b.f[10] = t;
+    };
+    auto set_inline_prec = [&](OpF32 &a, OpF64 &b, const Item &it) {
+        a.flags |= F_INLINE;
+        b.flags |= F_INLINE;
+        uint16_t terms = (it.k[0] != 0.0 ? F_KX : 0) | (it.k[1] != 0.0 ? F_KY : 0) |
+                         (it.k[2] != 0.0 ? F_KZ : 0) | (it.dt != 0.0 ? F_DT : 0);
+        a.flags |= terms;
+        b.flags |= terms;
+        for (int c = 0; c < 3; ++c) {
+            split(it.k[c], a.f[2 * c], a.f[2 * c + 1]);
+            b.f[c] = it.k[c];
+        }
+        split(it.dt, a.f[6], a.f[7]);
+        a.f[8] = (float)it.dt;
+        b.f[3] = it.dt;
+        auto e2 = e2map.find(bits(it.dt));
+        if (it.dt > 0.0 && e2 != e2map.end()) {
+            a.flags |= F_E2CLS;
+            b.flags |= F_E2CLS;
+            a.ecls = b.ecls = (int16_t)e2->second;
+        }
+    };
+    auto push = [&](const OpF32 &a, const OpF64 &b) {
+        out.ops32.push_back(a);
+        out.ops64.push_back(b);
+    };
+
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const Item &it = items[groups[g].first];
+        switch (it.kind) {
+        case Item::RF: {
+            OpF32 a = new32(OP_RF);
+            OpF64 b = new64(OP_RF);
+            double R[9], r22m1;
+            rf_matrix(it.alpha, it.phi, R, r22m1);
+            for (int c = 0; c < 9; ++c) {
+                a.f[c] = (float)R[c];
+                b.f[c] = R[c];
+            }
+            a.f[9] = (float)r22m1;
+            b.f[9] = r22m1;
+            set_e1(a, b, it.tau);
+            // fuse a following class precession (the sub-pulse trains of shaped pulses, Eq. 3.23)
+            if (g + 1 < groups.size()) {
+                const Item &nx = items[groups[g + 1].first];
+                if (nx.kind == Item::PREC) {
+                    auto pc = pmap.find(key_of(nx.k, nx.dt));
+                    if (pc != pmap.end()) {
+                        a.flags |= F_PCLS;
+                        b.flags |= F_PCLS;
+                        a.pcls = b.pcls = (int16_t)pc->second;
+                        ++g;
+                    }
+                }
+            }
+            push(a, b);
+            break;
+        }
+        case Item::PREC: {
+            OpF32 a = new32(OP_PREC);
+            OpF64 b = new64(OP_PREC);
+            auto pc = pmap.find(key_of(it.k, it.dt));
+            if (pc != pmap.end()) {
+                a.flags |= F_PCLS;
+                b.flags |= F_PCLS;
+                a.pcls = b.pcls = (int16_t)pc->second;
+            } else {
+                set_inline_prec(a, b, it);
+            }
+            push(a, b);
+            break;
+        }
+        case Item::SAMPLE: {
+            const int64_t cnt = groups[g].n;
+            if (is_zero(it.k, it.dt)) {
+                OpF32 a = new32(OP_PREC);
+                OpF64 b = new64(OP_PREC);
+                a.flags = b.flags = F_ADC;
+                a.adc0 = b.adc0 = (int32_t)it.j;
+                push(a, b);
+                break;
+            }
+            auto pc = pmap.find(key_of(it.k, it.dt));
+            if (pc != pmap.end() && cnt > 1) {
+                OpF32 a = new32(OP_RUN);
+                OpF64 b = new64(OP_RUN);
+                a.flags = b.flags = F_PCLS;
+                a.pcls = b.pcls = (int16_t)pc->second;
+                a.n = b.n = (int32_t)cnt;
+                a.adc0 = b.adc0 = (int32_t)it.j;
+                if (cnt >= 4) {
+                    auto an = pmap.find(anchor_key(it, cnt));
+                    if (an != pmap.end()) {
+                        a.flags |= F_ANCHOR;
+                        b.flags |= F_ANCHOR;
+                        a.acls = b.acls = (int16_t)an->second;
+                    }
+                }
+                push(a, b);
+            } else {
+                for (int64_t q = 0; q < cnt; ++q) {
+                    const Item &s = items[groups[g].first + (size_t)q];
+                    OpF32 a = new32(OP_PREC);
+                    OpF64 b = new64(OP_PREC);
+                    if (pc != pmap.end()) {
+                        a.flags |= F_PCLS;
+                        b.flags |= F_PCLS;
+                        a.pcls = b.pcls = (int16_t)pc->second;
+                    } else {
+                        set_inline_prec(a, b, s);
+                    }
+                    a.flags |= F_ADC;
+                    b.flags |= F_ADC;
+                    a.adc0 = b.adc0 = (int32_t)s.j;
+                    push(a, b);
+                }
+            }
+            break;
+        }
+        case Item::END: {
+            OpF32 a = new32(OP_END);
+            OpF64 b = new64(OP_END);
+            set_e1(a, b, it.tau);
+            push(a, b);
+            break;
+        }
+        }
+    }
+    if (out.n_adc > (int64_t)INT32_MAX) {
+        err = "too many ADC samples";
+        return MRSIM_EINVAL;
+    }
+    return MRSIM_OK;
+}
+
+}  // namespace mrsim

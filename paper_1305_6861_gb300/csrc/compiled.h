@@ -1,0 +1,26 @@
+// compiled.h -- host-side result of the sequence compiler (compile.cpp).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mrsim.h"
+#include "internal.h"
+
+namespace mrsim {
+
+struct Compiled {
+    std::vector<OpF32> ops32;
+    std::vector<OpF64> ops64;
+    std::vector<double> pcls;   // 4 per phasor class: kx, ky, kz [cycles/m], Δt [s]
+    std::vector<double> e1;     // τ per T1 class
+    std::vector<double> e2;     // Δt per T2 class
+    std::vector<double> demod;  // 2 per sample
+    int n_pcls = 0, n_e1 = 0, n_e2 = 0;
+    int64_t n_adc = 0;
+};
+
+// Returns an mrsim_status; on failure `err` says why.
+int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err);
+
+}  // namespace mrsim

@@ -1,0 +1,47 @@
+// fwd_f64.cu -- float64 instantiations of the forward kernel (K = spins per thread).
+#include "fwd_kernel.cuh"
+
+namespace mrsim {
+
+int launch_fwd_f64(const FwdArgs &a, int k, int threads, void *stream) {
+    switch (k) {
+    case 1: return dev::launch_one<double, 1, 256>(a, threads, stream);
+    case 2: return dev::launch_one<double, 2, 256>(a, threads, stream);
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+size_t fwd_smem_bytes(bool fp64, const Program &p, int k, int threads) {
+    return dev::smem_layout(fp64, p.n_pcls, p.n_e1, p.n_e2, k * threads, threads / 32).total;
+}
+
+// Validate and pack the seven float64 spin arrays into the parameter block (see internal.h).
+__global__ void pack_kernel(int64_t n, int64_t np, const double *x, const double *y, const double *z,
+                            const double *rho, const double *t1, const double *t2, const double *dw,
+                            double *params, int *bad) {
+    const double INV_TWO_PI = 0.15915494309189533577;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const double vx = x[s], vy = y[s], vz = z[s], vr = rho[s], v1 = t1[s], v2 = t2[s], vw = dw[s];
+        const bool ok = isfinite(vx) && isfinite(vy) && isfinite(vz) && isfinite(vr) && isfinite(vw) &&
+                        v1 > 0.0 && v2 > 0.0 && !isnan(v1) && !isnan(v2);
+        if (!ok) atomicMin(bad, (int)min(s, (int64_t)0x7ffffffe));
+        params[P_X * np + s] = vx;
+        params[P_Y * np + s] = vy;
+        params[P_Z * np + s] = vz;
+        params[P_DF * np + s] = vw * INV_TWO_PI;
+        params[P_RHO * np + s] = vr;
+        params[P_R1 * np + s] = isinf(v1) ? 0.0 : 1.0 / v1;
+        params[P_R2 * np + s] = isinf(v2) ? 0.0 : 1.0 / v2;
+    }
+}
+
+int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, const double *z, const double *rho,
+                const double *t1, const double *t2, const double *dw, double *params, int *bad, void *stream) {
+    if (n <= 0) return 0;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    pack_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, n_pad, x, y, z, rho, t1, t2, dw, params, bad);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mrsim

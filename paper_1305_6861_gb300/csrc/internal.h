@@ -1,0 +1,119 @@
+// internal.h -- device program format shared by the host sequence compiler and the kernels.
+//
+// A sequence of elementary sequences (§4.1) is compiled once, in float64, into a
+// stream of operations that every spin of a thread block executes in lock-step
+// (every thread sees the same operation, so branches on the operation never
+// diverge: the "codelet" idea of §6.3, one specialised code path per operation
+// kind).  Spin-independent work is done here once per sequence, as the paper's
+// master process does (§6.3):
+//   * gradient moments k = γ/2π · G · Δt in cycles/m;
+//   * RF rotation matrices (Eq. 3.19) and the accurate cos α − 1;
+//   * runs of events without RF and ADC merged into one precession
+//     (analytic solutions span long intervals in one step, §3.3);
+//   * T1 recovery applied lazily, once per RF pulse, over the time since the
+//     previous pulse (Mz only matters at the next pulse);
+//   * recurring precession intervals (same moment and Δt) become "classes"
+//     whose per-spin phasor E2·exp(-j2π(k·x + Δf·Δt)) each thread block
+//     evaluates once per spin in float64 and then reuses, e.g. for every
+//     sample of a constant-gradient readout.
+#pragma once
+#include <cstdint>
+
+namespace mrsim {
+
+enum OpKind : uint8_t {
+    OP_END = 0,   // final lazy T1 over f[10] (flags E1CLS/E1INL)
+    OP_RF = 1,    // lazy T1 over f[10], then rotation f[0..8] (row-major Eq. 3.19), f[9] = R22 - 1;
+                  // optionally fused precession by class pcls and a single sample
+    OP_PREC = 2,  // precession + T2 over one interval: class pcls (repeated n times) or inline
+    OP_RUN = 3,   // n consecutive samples, each after one precession by class pcls
+};
+
+enum OpFlags : uint16_t {
+    F_ADC = 1,      // one sample (index adc0) after the operation
+    F_PCLS = 2,     // precession by cached phasor class pcls
+    F_INLINE = 4,   // PREC: phase from the op's own moment and Δt
+    F_E1CLS = 8,    // RF/END: lazy T1 factor from cached class ecls
+    F_E1INL = 16,   // RF/END: lazy T1 factor computed from f[10]
+    F_E2CLS = 32,   // inline PREC: T2 factor from cached class ecls
+    F_ANCHOR = 64,  // RUN: state after the run = state before * phasor class acls (no drift)
+    F_KX = 128,     // inline PREC: which phase terms are non-zero
+    F_KY = 256,
+    F_KZ = 512,
+    F_DT = 1024,
+};
+
+// float32 program: 64 bytes.  Inline PREC payload: kx, ky, kz, Δt as (hi, lo) float pairs
+// (f[0..7]) and Δt in f[8].
+struct alignas(16) OpF32 {
+    uint8_t kind;
+    uint8_t rsv0;
+    uint16_t flags;
+    int32_t n;
+    int32_t adc0;
+    int16_t pcls, ecls;
+    int16_t acls, rsv1;
+    float f[11];
+};
+static_assert(sizeof(OpF32) == 64, "OpF32 must be 64 bytes");
+
+// float64 program: 128 bytes.  Inline PREC payload: kx, ky, kz, Δt in f[0..3].
+struct alignas(16) OpF64 {
+    uint8_t kind;
+    uint8_t rsv0;
+    uint16_t flags;
+    int32_t n;
+    int32_t adc0;
+    int16_t pcls, ecls;
+    int16_t acls, rsv1;
+    int32_t rsv2;
+    double f[13];
+};
+static_assert(sizeof(OpF64) == 128, "OpF64 must be 128 bytes");
+
+// Limits of the per-block class tables (shared memory grows with them).
+constexpr int MAX_PCLS = 8;
+constexpr int MAX_E1CLS = 4;
+constexpr int MAX_E2CLS = 4;
+// Samples held per block before they are summed across warps and added to global memory.
+constexpr int SAMPLE_WINDOW = 256;
+constexpr int RUN_MAX = SAMPLE_WINDOW;
+// Ops staged in shared memory per bulk copy (two buffers).
+constexpr int CHUNK_F32 = 128;
+constexpr int CHUNK_F64 = 64;
+
+// Per-spin parameter block on the device: 7 float64 SoA rows of n_pad values:
+// x, y, z [m], Δf = Δω/2π [Hz], M0, R1 = 1/T1, R2 = 1/T2 [1/s] (0 for T = ∞).
+constexpr int NPARAM = 7;
+enum ParamRow { P_X = 0, P_Y, P_Z, P_DF, P_RHO, P_R1, P_R2 };
+
+struct Program {
+    const void *ops;
+    int32_t n_ops;
+    int32_t n_pcls, n_e1, n_e2;
+    const double *pcls;  // 4 per class: kx, ky, kz [cycles/m], Δt [s]
+    const double *e1;    // τ [s] per class
+    const double *e2;    // Δt [s] per class
+    const double *demod; // 2 per sample: cos(adc_phase), -sin(adc_phase)
+    int64_t n_adc;
+};
+
+struct FwdArgs {
+    Program prog;
+    const double *params;  // NPARAM x n_pad
+    int64_t n_spins, n_pad;
+    const double *state_in;  // NULL or 3 per spin (device)
+    double *state_out;       // NULL or 3 per spin (device)
+    double *signal;          // 2 * n_adc (device), accumulated with atomics
+    int *status;             // device status word (0 = ok)
+};
+
+// Kernel launchers (fwd_f32.cu / fwd_f64.cu).  Return a cudaError_t value.
+int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
+int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
+size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
+int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, const double *z,
+                const double *rho, const double *t1, const double *t2, const double *dw,
+                double *params, int *bad, void *stream);
+
+}  // namespace mrsim

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libmrsim (include/mrsim.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA library.
+There is no CPU fallback — if ``lib/libmrsim.so`` is missing or no sm_103 GPU is
+present, the calls raise.  Arrays may be numpy arrays (host) or CUDA tensors
+(anything with ``data_ptr()`` and ``is_cuda``); streams are ``cudaStream_t``
+handles as integers (e.g. ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from enum import IntEnum
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmrsim.so")
+
+FP64 = 0
+FP32 = 1
+ACCUMULATE = 1
+
+EVENT_DTYPE = np.dtype(
+    [("dt", "<f8"), ("gx", "<f8"), ("gy", "<f8"), ("gz", "<f8"), ("rf_flip", "<f8"),
+     ("rf_phase", "<f8"), ("adc_phase", "<f8"), ("adc", "<i4"), ("reserved", "<i4")]
+)
+
+# Every symbol include/mrsim.h declares (checked by the CPU tests).
+EXPORTS = (
+    "mrsim_status_string", "mrsim_last_error", "mrsim_context_create", "mrsim_context_destroy",
+    "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
+    "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
+    "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
+    "mrsim_debug_compile",
+)
+
+
+class Status(IntEnum):
+    OK = 0
+    EINVAL = 1
+    ENOMEM = 2
+    ECUDA = 3
+    ETIMEOUT = 4
+    EUNSUPPORTED = 5
+
+
+class MrsimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{Status(status).name}: {msg}")
+        self.status = Status(status)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("spins_per_thread", ctypes.c_int32),
+        ("threads_per_block", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_int32),
+        ("state_in", ctypes.c_void_p),
+        ("state_out", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "mrsim_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "mrsim_last_error": (ctypes.c_char_p, [vp]),
+            "mrsim_context_create": (ctypes.c_int, [ctypes.c_int, P(vp)]),
+            "mrsim_context_destroy": (None, [vp]),
+            "mrsim_stream_status": (ctypes.c_int, [vp, vp]),
+            "mrsim_phantom_create": (ctypes.c_int, [vp, i64] + [vp] * 7 + [P(vp)]),
+            "mrsim_phantom_create_device": (ctypes.c_int, [vp, i64] + [vp] * 7 + [vp, P(vp)]),
+            "mrsim_phantom_num_spins": (i64, [vp]),
+            "mrsim_phantom_destroy": (None, [vp]),
+            "mrsim_sequence_load": (ctypes.c_int, [vp, i64, vp, dbl, P(vp)]),
+            "mrsim_sequence_num_adc": (i64, [vp]),
+            "mrsim_sequence_num_events": (i64, [vp]),
+            "mrsim_sequence_num_ops": (i64, [vp]),
+            "mrsim_sequence_destroy": (None, [vp]),
+            "mrsim_simulate": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
+            "mrsim_simulate_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64, P(Options)]),
+            "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, vp, P(i64), vp, P(i32), vp, P(i32), vp, P(i32), P(i64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a numpy array or CUDA tensor (None → NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        rc = lib().mrsim_context_create(int(device), ctypes.byref(h))
+        if rc != 0:
+            raise MrsimError(rc, f"mrsim_context_create(device={device}) failed")
+        self.h = h
+
+    def check(self, rc):
+        if rc != 0:
+            raise MrsimError(rc, lib().mrsim_last_error(self.h).decode())
+
+    def stream_status(self, stream=None):
+        self.check(lib().mrsim_stream_status(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Phantom:
+    """Spin list on the device.  `arrays` = (x, y, z, rho, t1, t2, dw), float64, host or CUDA."""
+
+    def __init__(self, ctx: Context, arrays, stream=None):
+        self.ctx = ctx
+        arrs = list(arrays)
+        n = int(arrs[0].shape[0])
+        h = ctypes.c_void_p()
+        if hasattr(arrs[0], "is_cuda") and arrs[0].is_cuda:
+            rc = lib().mrsim_phantom_create_device(ctx.h, n, *[_ptr(a) for a in arrs], _stream(stream), ctypes.byref(h))
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+            self._keep = arrs
+            rc = lib().mrsim_phantom_create(ctx.h, n, *[_ptr(a) for a in arrs], ctypes.byref(h))
+        ctx.check(rc)
+        self.h = h
+        self.n = n
+
+    @classmethod
+    def from_workload_phantom(cls, ctx, ph, stream=None):
+        return cls(ctx, ph.arrays(), stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_phantom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sequence:
+    """Compiled event list (host numpy array of EVENT_DTYPE records)."""
+
+    def __init__(self, ctx: Context, events, gamma_hz_per_t: float):
+        self.ctx = ctx
+        ev = np.ascontiguousarray(events)
+        if ev.dtype != EVENT_DTYPE:
+            ev = ev.astype(EVENT_DTYPE)
+        h = ctypes.c_void_p()
+        ctx.check(lib().mrsim_sequence_load(ctx.h, ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(h)))
+        self.h = h
+        self.n_adc = int(lib().mrsim_sequence_num_adc(h))
+        self.n_events = int(lib().mrsim_sequence_num_events(h))
+        self.n_ops = int(lib().mrsim_sequence_num_ops(h))
+
+    @classmethod
+    def from_workload_sequence(cls, ctx, seq):
+        return cls(ctx, seq.events, seq.gamma_hz_per_t)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_sequence_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None, out=None,
+             spins_per_thread: int = 0, threads_per_block: int = 0, accumulate: bool = False,
+             state_in=None, state_out=None):
+    """Run the forward simulation.  `out`: numpy complex128[n_adc] (host, returned when None) or a CUDA
+    buffer of 2*n_adc float64 (asynchronous on `stream`)."""
+    if out is None:
+        out = np.zeros(seq.n_adc, dtype=np.complex128)
+    opt = Options(int(spins_per_thread), int(threads_per_block), ACCUMULATE if accumulate else 0, 0,
+                  _ptr(state_in), _ptr(state_out))
+    rc = lib().mrsim_simulate_ex(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), _ptr(out), seq.n_adc,
+                                 ctypes.byref(opt))
+    ctx.check(rc)
+    return out
+
+
+def debug_compile(events, gamma_hz_per_t: float):
+    """Host-only compile of an event list (no GPU needed): returns the float64 device program
+    (op records as a structured array) and its class tables."""
+    L = lib()
+    ev = np.ascontiguousarray(events)
+    if ev.dtype != EVENT_DTYPE:
+        ev = ev.astype(EVENT_DTYPE)
+    n_ops = ctypes.c_int64()
+    n_p, n_1, n_2 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    n_adc = ctypes.c_int64()
+    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), None, ctypes.byref(n_ops), None,
+                               ctypes.byref(n_p), None, ctypes.byref(n_1), None, ctypes.byref(n_2), ctypes.byref(n_adc))
+    if rc != 0:
+        raise MrsimError(rc, "mrsim_debug_compile failed")
+    ops = np.zeros(n_ops.value, dtype=OP64_DTYPE)
+    pcls = np.zeros(4 * n_p.value)
+    e1 = np.zeros(n_1.value)
+    e2 = np.zeros(n_2.value)
+    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), _ptr(ops), ctypes.byref(n_ops),
+                               _ptr(pcls), ctypes.byref(n_p), _ptr(e1), ctypes.byref(n_1), _ptr(e2), ctypes.byref(n_2),
+                               ctypes.byref(n_adc))
+    if rc != 0:
+        raise MrsimError(rc, "mrsim_debug_compile failed")
+    return ops, pcls.reshape(-1, 4), e1, e2, int(n_adc.value)
+
+
+# Layout of one float64 device operation (128 bytes), for diagnostics.
+OP64_DTYPE = np.dtype(
+    [("kind", "u1"), ("rsv0", "u1"), ("flags", "<u2"), ("n", "<i4"), ("adc0", "<i4"), ("pcls", "<i2"),
+     ("ecls", "<i2"), ("acls", "<i2"), ("rsv1", "<i2"), ("rsv2", "<i4"), ("f", "<f8", (13,))]
+)
+assert OP64_DTYPE.itemsize == 128
+OP_END, OP_RF, OP_PREC, OP_RUN = 0, 1, 2, 3
+F_ADC, F_PCLS, F_INLINE, F_E1CLS, F_E1INL, F_E2CLS, F_ANCHOR = 1, 2, 4, 8, 16, 32, 64
+F_KX, F_KY, F_KZ, F_DT = 128, 256, 512, 1024

@@ -19,3 +19,12 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def mrsim_lib():
+    """Build libmrsim.so in-tree if needed (nvcc cross-compiles without a GPU) and load it."""
+    from paper_1305_6861_gb300 import build, mrsim
+
+    build.build()
+    return mrsim

@@ -1,0 +1,235 @@
+"""Forward-simulation parity of the CUDA library (through the C-ABI) against the CPU oracle.
+
+Tolerances (relative L2 error of the complex signal): 1e-12 for the float64 path, 2e-5 for
+the float32 path.  Sizes span several thread blocks with a ragged tail; the full-size
+workloads are checked on spin subsets (the signal is additive over spins, §5.3.2) in the
+launch shape the benchmark uses, plus properties that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1305_6861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0))
+
+
+def fp64_phase_tolerance(ph, seq):
+    """float64 floor for sequences with very large per-event phases (stress sequences).
+
+    An event turns a spin by θ = (γ G·x + Δω)·Δt; each implementation (oracle included)
+    represents θ with a relative rounding of ε = 2^-53, i.e. an absolute phase error of
+    about ε·|θ| per event, independently per event.  The signal error relative to the
+    signal is then of order ε·sqrt(Σ_e θ_e²) over the largest phases; 4x covers both
+    sides and the sin/cos evaluation.  For the paper's workloads this is below 1e-12.
+    """
+    ev = seq.events
+    g = 2 * math.pi * seq.gamma_hz_per_t
+    th = (g * (np.abs(ev["gx"]) * np.abs(ph.x).max() + np.abs(ev["gy"]) * np.abs(ph.y).max()
+               + np.abs(ev["gz"]) * np.abs(ph.z).max()) + np.abs(ph.dw).max()) * ev["dt"]
+    return max(TOL64, 4 * 2.0**-53 * float(np.sqrt(np.sum(th**2))))
+
+
+@pytest.fixture(scope="module")
+def M(mrsim_lib):
+    return mrsim_lib
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def run(M, ctx, ph, seq, prec, **kw):
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    s = M.Sequence.from_workload_sequence(ctx, seq)
+    out = M.simulate(ctx, p, s, prec, **kw)
+    ctx.stream_status()
+    return out
+
+
+def test_config1_parity(M, ctx, oracle_mod):
+    w = W.config1()
+    ref = oracle_mod.signal(w)
+    assert rel_l2(run(M, ctx, w.phantom, w.sequence, M.FP64), ref) <= TOL64
+    assert rel_l2(run(M, ctx, w.phantom, w.sequence, M.FP32), ref) <= TOL32
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_sequences_parity(M, ctx, oracle_mod, seed):
+    rng = np.random.default_rng(500 + seed)
+    ph = W.random_phantom(1000 + 777 * seed, rng)  # several blocks, ragged tail
+    seq = W.random_sequence(1500, rng, runs=True)
+    ref, ref_state = oracle_mod.simulate(ph, seq.events, seq.gamma_hz_per_t, want_state=True)
+    st64 = np.zeros((ph.n, 3))
+    s64 = run(M, ctx, ph, seq, M.FP64, state_out=st64)
+    tol = fp64_phase_tolerance(ph, seq)
+    assert rel_l2(s64, ref) <= tol
+    assert np.max(np.abs(st64 - ref_state)) <= tol * max(1.0, np.abs(ref_state).max())
+    st32 = np.zeros((ph.n, 3))
+    s32 = run(M, ctx, ph, seq, M.FP32, state_out=st32)
+    assert rel_l2(s32, ref) <= TOL32
+    assert np.max(np.abs(st32 - ref_state)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec,shapes", [
+    ("fp32", [(1, 32), (1, 64), (1, 512), (2, 128), (2, 512), (4, 96), (4, 512), (8, 64), (8, 256)]),
+    ("fp64", [(1, 32), (1, 256), (2, 64), (2, 256)]),
+])
+def test_launch_shapes_agree(M, ctx, oracle_mod, prec, shapes):
+    rng = np.random.default_rng(77)
+    ph = W.random_phantom(3001, rng)
+    seq = W.random_sequence(600, rng)
+    ref = oracle_mod.signal(ph, seq)
+    p = M.FP32 if prec == "fp32" else M.FP64
+    tol = TOL32 if prec == "fp32" else TOL64
+    tol = max(tol, fp64_phase_tolerance(ph, seq)) if p == M.FP64 else tol
+    ran = 0
+    for k, t in shapes:
+        try:
+            out = run(M, ctx, ph, seq, p, spins_per_thread=k, threads_per_block=t)
+        except M.MrsimError as e:  # the shape's shared memory exceeds the device limit
+            assert e.status == M.Status.EUNSUPPORTED, (k, t, e)
+            continue
+        assert rel_l2(out, ref) <= tol, (k, t)
+        ran += 1
+    assert ran >= len(shapes) - 2
+
+
+def test_state_resume_equals_single_run(M, ctx, oracle_mod):
+    """Checkpoint / resume: two consecutive sub-sequences chained through state_out → state_in."""
+    w = W.config1()
+    ev = w.sequence.events
+    cut = 67 * 23 + 30  # inside a readout
+    a = W.Sequence(ev[:cut], w.sequence.gamma_hz_per_t)
+    b = W.Sequence(ev[cut:], w.sequence.gamma_hz_per_t)
+    ref = oracle_mod.signal(w)
+    for prec, tol in ((M.FP64, TOL64), (M.FP32, TOL32)):
+        st = np.zeros((w.phantom.n, 3))
+        sa = run(M, ctx, w.phantom, a, prec, state_out=st)
+        sb = run(M, ctx, w.phantom, b, prec, state_in=st)
+        assert rel_l2(np.concatenate([sa, sb]), ref) <= tol
+
+
+def test_accumulate_over_spin_subsets(M, ctx):
+    """Domain decomposition (§5.3.2): the signal of the whole object is the sum over subsets."""
+    w = W.config1()
+    seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    full = M.simulate(ctx, M.Phantom.from_workload_phantom(ctx, w.phantom), seq, M.FP64)
+    idx = np.random.default_rng(3).permutation(w.phantom.n)
+    acc = np.zeros(seq.n_adc, dtype=complex)
+    for part in np.array_split(idx, 3):
+        M.simulate(ctx, M.Phantom.from_workload_phantom(ctx, w.phantom.subset(part)), seq, M.FP64, out=acc, accumulate=True)
+    assert rel_l2(acc, full) <= 1e-13
+
+
+def test_edge_cases(M, ctx, oracle_mod):
+    rng = np.random.default_rng(9)
+    seq = W.random_sequence(300, rng)
+    # zero spins: zero signal
+    empty = W.random_phantom(0, rng)
+    for p in (M.FP64, M.FP32):
+        out = run(M, ctx, empty, seq, p)
+        assert out.shape == (seq.n_adc,) and not np.any(out)
+    # one spin, T = inf, Δt = 0 events; a sequence without any sample
+    one = W.random_phantom(1, rng)
+    one.t1[:] = np.inf
+    one.t2[:] = np.inf
+    ev = np.concatenate([W.make_events([(0.0, 0, 0, 0, 1.0, 0.3, 1, 0.2), (0.0, 1e-3, 0, 0, 0, 0, 1, 0.0)]), seq.events])
+    s1 = W.Sequence(ev, W.GAMMA_BAR)
+    ref = oracle_mod.signal(one, s1)
+    assert rel_l2(run(M, ctx, one, s1, M.FP64), ref) <= TOL64
+    assert rel_l2(run(M, ctx, one, s1, M.FP32), ref) <= TOL32
+    noadc = W.Sequence(seq.events[seq.events["adc"] == 0], W.GAMMA_BAR)
+    st = np.zeros((one.n, 3))
+    out = run(M, ctx, one, noadc, M.FP64, state_out=st)
+    _, ref_st = oracle_mod.simulate(one, noadc.events, W.GAMMA_BAR, want_signal=False, want_state=True)
+    assert out.shape == (0,)
+    assert np.max(np.abs(st - ref_st)) <= 1e-12
+
+
+def test_invalid_inputs(M, ctx):
+    rng = np.random.default_rng(10)
+    ph = W.random_phantom(10, rng)
+    bad = ph.subset(np.arange(10))
+    bad.t1[3] = 0.0
+    with pytest.raises(M.MrsimError) as e:
+        M.Phantom.from_workload_phantom(ctx, bad)
+    assert e.value.status == M.Status.EINVAL
+    bad = ph.subset(np.arange(10))
+    bad.x[7] = np.nan
+    with pytest.raises(M.MrsimError):
+        M.Phantom.from_workload_phantom(ctx, bad)
+    seq = M.Sequence.from_workload_sequence(ctx, W.random_sequence(50, rng))
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    out = np.zeros(seq.n_adc + 1, dtype=complex)
+    import ctypes
+
+    rc = M.lib().mrsim_simulate(ctx.h, p.h, seq.h, M.FP32, None, ctypes.c_void_p(out.ctypes.data), seq.n_adc + 1)
+    assert rc == M.Status.EINVAL
+    with pytest.raises(M.MrsimError):
+        M.simulate(ctx, p, seq, M.FP32, spins_per_thread=3)
+
+
+def test_device_buffers_and_streams(M, ctx, oracle_mod):
+    torch = pytest.importorskip("torch")
+    w = W.config1()
+    dev = torch.device("cuda:0")
+    arrs = [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = M.Phantom(ctx, arrs, stream=s)
+        seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
+        out = torch.zeros(2 * seq.n_adc, dtype=torch.float64, device=dev)
+        M.simulate(ctx, p, seq, M.FP32, stream=s, out=out)
+    s.synchronize()
+    ctx.stream_status(s)
+    got = out.cpu().numpy().view(np.complex128)
+    assert rel_l2(got, oracle_mod.signal(w)) <= TOL32
+
+
+def test_config2_subset_parity(M, ctx, oracle_mod):
+    """Full C2 sequence (sinc 90/180, B0 + fat) on a random subset of its spins."""
+    w = W.config2()
+    idx = np.sort(np.random.default_rng(21).choice(w.phantom.n, 1500, replace=False))
+    sub = w.phantom.subset(idx)
+    ref = oracle_mod.signal(sub, w.sequence)
+    assert rel_l2(run(M, ctx, sub, w.sequence, M.FP64), ref) <= TOL64
+    assert rel_l2(run(M, ctx, sub, w.sequence, M.FP32), ref) <= TOL32
+
+
+def test_config2_full_size_fp32_vs_fp64(M, ctx):
+    """Full-size C2 in the benchmark's launch shape: float32 against the float64 GPU path, and
+    additivity of the float64 path over two disjoint halves of the spins."""
+    w = W.config2()
+    seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    p = M.Phantom.from_workload_phantom(ctx, w.phantom)
+    s64 = M.simulate(ctx, p, seq, M.FP64)
+    s32 = M.simulate(ctx, p, seq, M.FP32)
+    assert rel_l2(s32, s64) <= TOL32
+    half = w.phantom.n // 2
+    acc = np.zeros(seq.n_adc, dtype=complex)
+    for part in (np.arange(half), np.arange(half, w.phantom.n)):
+        M.simulate(ctx, M.Phantom.from_workload_phantom(ctx, w.phantom.subset(part)), seq, M.FP64, out=acc, accumulate=True)
+    assert rel_l2(acc, s64) <= 1e-13
+
+
+def test_config3_subset_parity(M, ctx, oracle_mod):
+    """Full C3 sequence (3D RF-spoiled GRE, 2.1 M events) on a random subset of its spins."""
+    w = W.config3()
+    idx = np.sort(np.random.default_rng(31).choice(w.phantom.n, 384, replace=False))
+    sub = w.phantom.subset(idx)
+    ref = oracle_mod.signal(sub, w.sequence)
+    assert rel_l2(run(M, ctx, sub, w.sequence, M.FP64), ref) <= TOL64
+    assert rel_l2(run(M, ctx, sub, w.sequence, M.FP32), ref) <= TOL32

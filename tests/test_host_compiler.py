@@ -1,0 +1,130 @@
+"""Host-side checks without a GPU: the library's exports, its input validation, and the
+sequence compiler (the compiled program, interpreted on the CPU, must reproduce the oracle)."""
+import math
+import re
+import os
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1305_6861_gb300 import workloads as W
+from program_interp import interpret
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def test_library_exports_every_declared_symbol(mrsim_lib):
+    header = open(os.path.join(ROOT, "include", "mrsim.h")).read()
+    declared = set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(mrsim_[a-z_0-9]+)\s*\(", header, re.M))
+    assert declared, "no declarations parsed"
+    assert declared == set(mrsim_lib.EXPORTS), f"header/binding drift: {declared ^ set(mrsim_lib.EXPORTS)}"
+    L = mrsim_lib.lib()
+    for name in declared:
+        assert hasattr(L, name), f"{name} not exported"
+
+
+def test_status_strings(mrsim_lib):
+    L = mrsim_lib.lib()
+    for s in range(6):
+        assert L.mrsim_status_string(s)
+
+
+def _compile_rc(events, gamma=W.GAMMA_BAR):
+    L = __import__("paper_1305_6861_gb300.mrsim", fromlist=["x"]).lib()
+    ev = np.ascontiguousarray(events, dtype=W.EVENT_DTYPE)
+    n = [ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()]
+    return L.mrsim_debug_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), float(gamma), None,
+                                 ctypes.byref(n[0]), None, ctypes.byref(n[1]), None, ctypes.byref(n[2]), None,
+                                 ctypes.byref(n[3]), ctypes.byref(n[4]))
+
+
+@pytest.mark.parametrize("field,value", [("dt", -1e-3), ("gx", np.nan), ("rf_flip", np.inf), ("adc", 2),
+                                         ("reserved", 1), ("adc_phase", np.nan)])
+def test_invalid_events_rejected(mrsim_lib, field, value):
+    ev = W.make_events([(1e-3, 0, 0, 0, 0.5, 0, 1, 0.0)] * 3)
+    ev[field][1] = value
+    assert _compile_rc(ev) == 1  # MRSIM_EINVAL
+
+
+def test_invalid_gamma_rejected(mrsim_lib):
+    ev = W.make_events([(1e-3, 0, 0, 0, 0.5, 0, 1, 0.0)])
+    assert _compile_rc(ev, 0.0) == 1
+    assert _compile_rc(ev, -1.0) == 1
+    assert _compile_rc(ev, np.nan) == 1
+    assert _compile_rc(ev[:0]) == 0
+
+
+def test_context_without_gpu_is_unsupported(mrsim_lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert mrsim_lib.lib().mrsim_context_create(0, ctypes.byref(h)) == 5  # MRSIM_EUNSUPPORTED
+
+
+def _check_structure(events, ops, n_adc):
+    from paper_1305_6861_gb300 import mrsim as M
+
+    assert len(ops) <= 2 * len(events) + 1  # an event with RF and a sample is two ops
+    assert ops[-1]["kind"] == M.OP_END
+    seen = []
+    for op in ops:
+        if op["kind"] == M.OP_RUN:
+            assert 1 <= op["n"] <= 256
+            seen.extend(range(op["adc0"], op["adc0"] + op["n"]))
+        elif op["flags"] & M.F_ADC:
+            seen.append(op["adc0"])
+    assert seen == list(range(n_adc)), "every sample exactly once, in order"
+
+
+CASES = {
+    "c1": lambda: W.config1(),
+    "c2_small": lambda: W.config2(n=32, iso=2),
+    "c3_small": lambda: W.config3(n=12, iso=1),
+    "c5_small": lambda: W.config5(n=24)[0],
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_compiled_program_matches_oracle(case, mrsim_lib, oracle_mod):
+    w = CASES[case]()
+    seq = w.sequence
+    sig, state, ops = interpret(seq.events, seq.gamma_hz_per_t, w.phantom)
+    ref, ref_state = oracle_mod.simulate(w.phantom, seq.events, seq.gamma_hz_per_t, want_state=True)
+    _check_structure(seq.events, ops, seq.n_adc)
+    assert rel_l2(sig, ref) < 1e-12
+    assert np.max(np.abs(state - ref_state)) < 1e-12 * max(1.0, np.max(np.abs(ref_state)))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_compiled_random_programs_match_oracle(seed, mrsim_lib, oracle_mod):
+    rng = np.random.default_rng(100 + seed)
+    ph = W.random_phantom(50, rng)
+    seq = W.random_sequence(400, rng, runs=seed % 3 != 0)
+    m0 = rng.normal(size=(ph.n, 3)) if seed % 2 else None
+    sig, state, ops = interpret(seq.events, seq.gamma_hz_per_t, ph, state_in=m0)
+    ref, ref_state = oracle_mod.simulate(ph, seq.events, seq.gamma_hz_per_t, m_init=m0, want_state=True)
+    _check_structure(seq.events, ops, seq.n_adc)
+    assert rel_l2(sig, ref) < 1e-11
+    assert np.max(np.abs(state - ref_state)) < 1e-11 * max(1.0, np.max(np.abs(ref_state)))
+
+
+def test_class_tables_bounded_and_used(mrsim_lib):
+    from paper_1305_6861_gb300 import mrsim as M
+
+    w = W.config2(n=32, iso=2)
+    ops, pcls, e1, e2, n_adc = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
+    assert len(pcls) <= 8 and len(e1) <= 4 and len(e2) <= 4
+    # the shaped-pulse sub-pulse trains are fused RF + class precession operations
+    rf = ops[ops["kind"] == M.OP_RF]
+    assert np.count_nonzero(rf["flags"] & M.F_PCLS) >= 0.99 * len(rf)
+    # every readout is one run with an anchor
+    runs = ops[ops["kind"] == M.OP_RUN]
+    assert len(runs) == 32 and np.all(runs["flags"] & M.F_ANCHOR)
