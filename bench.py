@@ -34,11 +34,11 @@ sys.path.insert(0, ROOT)
 from paper_1305_6861_gb300 import workloads as W  # noqa: E402
 
 METRIC = "spin-steps/s (isochromat×event updates) at 1 GB300, FP32 vs FP64, % FP32/SFU peak"
-# FP32 lane-operations the method needs per spin-step, by event type ("roofline"):
-#   ADC event: complex rotation-relaxation of Mxy (4) + complex accumulate into the sample (2)
-#   RF event : rotation (9) + T1 step of Mz (1) + complex precession (4)
-#   other    : complex precession (4) + T1 step of Mz (1)
-OPS_ADC, OPS_RF, OPS_OTHER = 6, 14, 5
+# FP32 lane-operations the method needs per spin-step, by event type (pulse-frame formulation):
+#   ADC event: precession-relaxation of Mxy, one complex product (4) + accumulate into the sample (2)
+#   RF event : hard pulse in its own frame (4) + T1 recovery of Mz (2) + precession (4)
+#   other    : precession (4); T1 recovery is folded into the next pulse
+OPS_ADC, OPS_RF, OPS_OTHER = 6, 10, 4
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -48,7 +48,7 @@ def algorithmic_ops_per_spin(events) -> int:
     other = ~adc & ~rf
     n_rf_adc = int(np.count_nonzero((events["rf_flip"] != 0) & adc))
     return int(OPS_ADC * np.count_nonzero(adc) + OPS_RF * np.count_nonzero(rf) + OPS_OTHER * np.count_nonzero(other)
-               + (OPS_RF - OPS_OTHER) * n_rf_adc)
+               + (OPS_RF - OPS_OTHER + 2) * n_rf_adc)
 
 
 def fp32_alu_peak_ops(sm_mhz: float = SM_MAX_MHZ) -> float:
@@ -211,6 +211,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     w = build_workload(args.workload, rank)
+    if args.events:  # profiling aid: a prefix of the sequence (whole repetitions), named in config
+        w = W.Workload(w.name + f"_first{args.events}ev", w.phantom,
+                       W.Sequence(w.sequence.events[: args.events], w.sequence.gamma_hz_per_t), w.note)
     prec = M.FP64 if args.precision == "fp64" else M.FP32
     ctx = M.Context(local)
     stream = torch.cuda.current_stream()
@@ -225,6 +228,11 @@ def run_ours(args):
         kw["spins_per_thread"] = args.spins_per_thread
     if args.threads:
         kw["threads_per_block"] = args.threads
+    tuned = None
+    if not kw and not args.no_tune:  # autotune the launch shape (part of warm-up, outside the timed region)
+        t0 = time.perf_counter()
+        tuned = M.autotune(ctx, ph, seq, prec, stream=stream)
+        tuned = {"spins_per_thread": tuned[0], "threads_per_block": tuned[1], "tune_s": time.perf_counter() - t0}
 
     def step():
         M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
@@ -334,7 +342,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
             "config": {"workload": w.name, "n_spins_per_gpu": w.phantom.n, "n_events": w.sequence.n_events,
                        "n_adc": seq.n_adc, "n_ops": seq.n_ops, "spin_steps_per_gpu_step": spin_steps,
-                       "precision": args.precision, "launch": kw or "library default",
+                       "precision": args.precision, "launch": kw or tuned or "library default",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "parallelism": f"spin-sharded x{world}" if world > 1 else "1 GPU"},
             "roofline": roof, "gpu_launches": args.steps, "clocks": ck, "wall_s_timed": t_wall,
@@ -361,6 +369,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--events", type=int, default=0, help="use only the first N events (profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

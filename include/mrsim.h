@@ -78,13 +78,15 @@ typedef struct mrsim_sequence mrsim_sequence;
 typedef struct mrsim_options {
     int32_t spins_per_thread;  /* 0 = library choice (tuned table); else 1, 2, 4 or 8 (FP64: 1 or 2) */
     int32_t threads_per_block; /* 0 = library choice; else a multiple of 32 in [32, 1024] */
-    uint32_t flags;            /* MRSIM_ACCUMULATE: add into signal_out instead of overwriting it */
+    uint32_t flags;            /* MRSIM_ACCUMULATE: add into signal_out instead of overwriting it;
+                                  MRSIM_TUNE: run mrsim_autotune first if this shape is not tuned yet */
     int32_t reserved;
     const double *state_in;    /* NULL = thermal equilibrium (0,0,M0); else 3*n_spins (Mx,My,Mz), host or device */
     double *state_out;         /* NULL, or 3*n_spins receiving (Mx,My,Mz) after the last event, host or device */
 } mrsim_options;
 
 #define MRSIM_ACCUMULATE 1u
+#define MRSIM_TUNE 2u /* autotune the launch shape on first use with this (precision, spin count) */
 
 /* ---- context ------------------------------------------------------------------------- */
 
@@ -149,12 +151,23 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
  * sequence compiler.  Call once with NULL output arrays to get the sizes (*n_ops, *n_pcls,
  * *n_e1, *n_e2, *n_adc), then again with arrays of those sizes: ops_out receives *n_ops float64
  * device operations (128-byte records), pcls_out 4 doubles per precession class (kx, ky, kz in
- * cycles/m, Δt in s), e1_out / e2_out one interval per relaxation class.  Same validation and
- * error codes as mrsim_sequence_load; EINVAL if a given output array is too small. */
+ * cycles/m, Δt in s), e1_out / e2_out one interval per relaxation class, demod_out 2 doubles per
+ * sample (the factor each sample's spin sum is multiplied by).  Same validation and error codes
+ * as mrsim_sequence_load; EINVAL if a given output array is too small. */
 mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
                                  void *ops_out, int64_t *n_ops, double *pcls_out, int32_t *n_pcls,
                                  double *e1_out, int32_t *n_e1, double *e2_out, int32_t *n_e2,
-                                 int64_t *n_adc);
+                                 double *demod_out, int64_t *n_adc);
+
+/* Autotuner: times every launch shape (spins per thread x threads per block) that fits the device
+ * on a prefix of the compiled program (about 3e9 spin-steps, at least 256 operations) on `stream`,
+ * and keeps the fastest in the context, keyed by precision, spin count and the compiled program's
+ * size and class tables; later mrsim_simulate / mrsim_simulate_ex calls without an explicit shape
+ * on any phantom/sequence with the same key use it.  Returns the shape in
+ * best->spins_per_thread / best->threads_per_block (other fields zeroed).  Synchronises `stream`;
+ * tuning again replaces the entry. */
+mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                            mrsim_precision prec, void *stream, mrsim_options *best);
 
 #ifdef __cplusplus
 }

@@ -2,9 +2,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mrsim.h"
@@ -13,7 +16,16 @@
 
 using namespace mrsim;
 
+struct TunedShape {
+    int k = 0, threads = 0;
+    float ms = 0.0f;
+};
+// Autotuned launch shapes are kept per context, keyed by what determines the kernel's cost:
+// precision, spin count and the compiled program's size and class-table sizes.
+using TuneKey = std::array<int64_t, 7>;
+
 struct mrsim_ctx {
+    std::map<TuneKey, TunedShape> tuned;
     int device = 0;
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -108,6 +120,7 @@ mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStr
             return cuda_fail(ctx, e, "cudaMalloc phantom");
         }
         const int big = 0x7fffffff;
+        cudaMemsetAsync(p->params, 0, (size_t)NPARAM * p->n_pad * sizeof(double), st);  // padding rows = 0
         cudaMemcpyAsync(ctx->d_bad, &big, sizeof(int), cudaMemcpyHostToDevice, st);
         int rc = pack_params(n, p->n_pad, src[0], src[1], src[2], src[3], src[4], src[5], src[6], p->params,
                              ctx->d_bad, st);
@@ -133,6 +146,11 @@ mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStr
 struct Launch {
     int k, threads;
 };
+
+TuneKey tune_key(mrsim_precision prec, const mrsim_phantom *ph, const mrsim_sequence *seq) {
+    const Compiled &c = seq->host;
+    return TuneKey{(int64_t)prec, ph->n, (int64_t)c.ops32.size(), c.n_pcls, c.n_e1, c.n_e2, c.n_adc};
+}
 
 // Default launch shape: the largest spins-per-thread that still gives every SM about two blocks.
 Launch choose_launch(const mrsim_ctx *ctx, bool fp64, int64_t n) {
@@ -340,7 +358,15 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     const bool fp64 = prec == MRSIM_FP64;
     mrsim_options o{};
     if (opt) o = *opt;
+    if ((o.flags & MRSIM_TUNE) && !o.spins_per_thread && !o.threads_per_block &&
+        !ctx->tuned.count(tune_key(prec, ph, seq))) {
+        mrsim_options t{};
+        mrsim_status ts = mrsim_autotune(ctx, ph, seq, prec, stream, &t);
+        if (ts != MRSIM_OK) return ts;
+    }
     Launch L = choose_launch(ctx, fp64, ph->n);
+    auto tu = ctx->tuned.find(tune_key(prec, ph, seq));
+    if (tu != ctx->tuned.end()) L = Launch{tu->second.k, tu->second.threads};
     if (o.spins_per_thread) L.k = o.spins_per_thread;
     if (o.threads_per_block) L.threads = o.threads_per_block;
     const bool k_ok = fp64 ? (L.k == 1 || L.k == 2) : (L.k == 1 || L.k == 2 || L.k == 4 || L.k == 8);
@@ -393,6 +419,78 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     return MRSIM_OK;
 }
 
+mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq, mrsim_precision prec,
+                            void *stream, mrsim_options *best) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (!ph || !seq || !best) return fail(ctx, MRSIM_EINVAL, "NULL argument");
+    if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
+    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    const bool fp64 = prec == MRSIM_FP64;
+    std::memset(best, 0, sizeof *best);
+    Launch def = choose_launch(ctx, fp64, ph->n);
+    if (ph->n == 0) {
+        best->spins_per_thread = def.k;
+        best->threads_per_block = def.threads;
+        return MRSIM_OK;
+    }
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // time a prefix of the program that is long enough to contain the sequence's structure
+    Program P = fp64 ? seq->p64 : seq->p32;
+    const double ev_per_op = (double)std::max<int64_t>(seq->n_events, 1) / (double)std::max(P.n_ops, 1);
+    const double target = 3e9;  // spin-steps per trial
+    int64_t nt = (int64_t)std::ceil(target / ((double)ph->n * ev_per_op));
+    nt = std::max<int64_t>(nt, std::min<int64_t>(P.n_ops, 256));
+    P.n_ops = (int32_t)std::min<int64_t>(nt, P.n_ops);
+    mrsim_status rs = grow(ctx, &ctx->d_sig, &ctx->sig_cap, 2 * (size_t)std::max<int64_t>(P.n_adc, 1));
+    if (rs != MRSIM_OK) return rs;
+    static const int f32k[] = {1, 2, 4, 8}, f64k[] = {1, 2};
+    static const int thr[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    TunedShape win;
+    win.ms = 1e30f;
+    for (int k : (fp64 ? std::vector<int>(f64k, f64k + 2) : std::vector<int>(f32k, f32k + 4))) {
+        for (int t : thr) {
+            if (t > (fp64 || k == 8 ? 256 : 512)) continue;
+            const size_t smem = fwd_smem_bytes(fp64, P, k, t);
+            if (smem > (size_t)ctx->max_smem_optin || fwd_blocks_per_sm(fp64, k, t, smem) == 0) continue;
+            FwdArgs a{};
+            a.prog = P;
+            a.params = ph->params;
+            a.n_spins = ph->n;
+            a.n_pad = ph->n_pad;
+            a.signal = ctx->d_sig;
+            a.status = ctx->d_status;
+            auto launch = [&]() { return fp64 ? launch_fwd_f64(a, k, t, stream) : launch_fwd_f32(a, k, t, stream); };
+            if (launch() != 0) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, st);
+            int rc = launch();
+            cudaEventRecord(e1, st);
+            if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < win.ms) win = TunedShape{k, t, ms};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mrsim_status ss = mrsim_stream_status(ctx, stream);
+    if (ss != MRSIM_OK) return ss;
+    if (win.k == 0) return fail(ctx, MRSIM_EUNSUPPORTED, "no launch shape fits this program on the device");
+    ctx->tuned[tune_key(prec, ph, seq)] = win;
+    best->spins_per_thread = win.k;
+    best->threads_per_block = win.threads;
+    return MRSIM_OK;
+}
+
 mrsim_status mrsim_simulate(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq, mrsim_precision prec,
                             void *stream, double *signal_out, int64_t n_adc) {
     return mrsim_simulate_ex(ctx, ph, seq, prec, stream, signal_out, n_adc, nullptr);
@@ -400,7 +498,7 @@ mrsim_status mrsim_simulate(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
 
 mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma, void *ops_out,
                                  int64_t *n_ops, double *pcls_out, int32_t *n_pcls, double *e1_out, int32_t *n_e1,
-                                 double *e2_out, int32_t *n_e2, int64_t *n_adc) {
+                                 double *e2_out, int32_t *n_e2, double *demod_out, int64_t *n_adc) {
     if (!n_ops || !n_pcls || !n_e1 || !n_e2 || !n_adc) return MRSIM_EINVAL;
     Compiled c;
     std::string err;
@@ -408,6 +506,8 @@ mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, do
     if (rc != MRSIM_OK) return (mrsim_status)rc;
     const int64_t cap_ops = *n_ops;
     const int32_t cap_p = *n_pcls, cap_1 = *n_e1, cap_2 = *n_e2;
+    const int64_t cap_adc = *n_adc;
+    if (demod_out && c.n_adc > cap_adc) return MRSIM_EINVAL;
     if (ops_out && (int64_t)c.ops64.size() > cap_ops) return MRSIM_EINVAL;
     if (pcls_out && c.n_pcls > cap_p) return MRSIM_EINVAL;
     if (e1_out && c.n_e1 > cap_1) return MRSIM_EINVAL;
@@ -416,6 +516,7 @@ mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, do
     if (pcls_out) std::memcpy(pcls_out, c.pcls.data(), c.pcls.size() * sizeof(double));
     if (e1_out) std::memcpy(e1_out, c.e1.data(), c.e1.size() * sizeof(double));
     if (e2_out) std::memcpy(e2_out, c.e2.data(), c.e2.size() * sizeof(double));
+    if (demod_out) std::memcpy(demod_out, c.demod.data(), c.demod.size() * sizeof(double));
     *n_ops = (int64_t)c.ops64.size();
     *n_pcls = c.n_pcls;
     *n_e1 = c.n_e1;

@@ -26,6 +26,7 @@ struct Item {
     double alpha, phi;
     double tau;     // RF/END: time since the previous RF pulse [s]
     int64_t j;      // SAMPLE: sample index
+    double adc_phase;
 };
 
 using Key = std::array<uint64_t, 4>;
@@ -69,25 +70,6 @@ std::map<K, int> pick_classes(const std::map<K, std::pair<int64_t, int64_t>> &us
 void split(double v, float &hi, float &lo) {
     hi = (float)v;
     lo = (float)(v - (double)hi);
-}
-
-// Eq. 3.19 written as the rotation by -α about n = (cos φ, sin φ, 0):
-// R = cos α·I + (1 - cos α)·n nᵀ - sin α·[n]x, with 1 - cos α = 2 sin²(α/2) for accuracy.
-void rf_matrix(double alpha, double phi, double R[9], double &r22m1) {
-    const double ca = std::cos(alpha), sa = std::sin(alpha);
-    const double h = std::sin(0.5 * alpha);
-    const double omc = 2.0 * h * h;
-    const double n0 = std::cos(phi), n1 = std::sin(phi);
-    R[0] = ca + omc * n0 * n0;
-    R[1] = omc * n0 * n1;
-    R[2] = -sa * n1;
-    R[3] = omc * n0 * n1;
-    R[4] = ca + omc * n1 * n1;
-    R[5] = sa * n0;
-    R[6] = sa * n1;
-    R[7] = -sa * n0;
-    R[8] = ca;
-    r22m1 = -omc;
 }
 
 }  // namespace
@@ -155,9 +137,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             std::memcpy(it.k, k, sizeof k);
             it.dt = e.dt;
             it.j = j++;
+            it.adc_phase = e.adc_phase;
             items.push_back(it);
-            out.demod.push_back(std::cos(e.adc_phase));
-            out.demod.push_back(-std::sin(e.adc_phase));
         } else {
             for (int c = 0; c < 3; ++c) pk[c] += k[c];
             pdt += e.dt;
@@ -239,6 +220,11 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     for (auto &kv : e2map) std::memcpy(&out.e2[(size_t)kv.second], &kv.first, 8);
 
     // ---- emit ------------------------------------------------------------------------------------
+    // Mirrors of the kernel's state: the frame angle ψ (phase of the latest pulse) and the
+    // register caches of the phasor class and the T1 class.
+    double psi = 0.0;
+    int pcache = -1, e1cache = -1;
+    out.demod.assign(2 * (size_t)out.n_adc, 0.0);
     auto new32 = [](uint8_t kind) {
         OpF32 o;
         std::memset(&o, 0, sizeof o);
@@ -257,24 +243,45 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         o.n = 1;
         return o;
     };
+    auto both = [](OpF32 &a, OpF64 &b, uint16_t fl) {
+        a.flags |= fl;
+        b.flags |= fl;
+    };
+    auto demod = [&](int64_t jj, double adc_phase) {
+        // sample sum in the frame ψ: Σ(u + jv) = e^{-jψ} Σ(Mx + jMy), so the factor is e^{-j(φ_adc - ψ)}
+        out.demod[2 * (size_t)jj] = std::cos(adc_phase - psi);
+        out.demod[2 * (size_t)jj + 1] = -std::sin(adc_phase - psi);
+    };
     auto set_e1 = [&](OpF32 &a, OpF64 &b, double t) {
         if (t > 0.0) {
             auto it = e1map.find(bits(t));
-            uint16_t fl = it != e1map.end() ? F_E1CLS : F_E1INL;
-            a.flags |= fl;
-            b.flags |= fl;
-            if (it != e1map.end()) a.ecls = b.ecls = (int16_t)it->second;
+            if (it != e1map.end()) {
+                both(a, b, F_E1CLS);
+                a.ecls = b.ecls = (int16_t)it->second;
+                if (e1cache != it->second) {
+                    both(a, b, F_E1LOAD);
+                    e1cache = it->second;
+                }
+            } else {
+                both(a, b, F_E1INL);
+            }
         }
         a.f[10] = (float)t;
         b.f[10] = t;
     };
+    auto use_pcls = [&](OpF32 &a, OpF64 &b, int c) {
+        both(a, b, F_PCLS);
+        a.pcls = b.pcls = (int16_t)c;
+        if (pcache != c) {
+            both(a, b, F_PLOAD);
+            pcache = c;
+        }
+    };
     auto set_inline_prec = [&](OpF32 &a, OpF64 &b, const Item &it) {
-        a.flags |= F_INLINE;
-        b.flags |= F_INLINE;
+        both(a, b, F_INLINE);
         uint16_t terms = (it.k[0] != 0.0 ? F_KX : 0) | (it.k[1] != 0.0 ? F_KY : 0) |
                          (it.k[2] != 0.0 ? F_KZ : 0) | (it.dt != 0.0 ? F_DT : 0);
-        a.flags |= terms;
-        b.flags |= terms;
+        both(a, b, terms);
         for (int c = 0; c < 3; ++c) {
             split(it.k[c], a.f[2 * c], a.f[2 * c + 1]);
             b.f[c] = it.k[c];
@@ -284,8 +291,7 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         b.f[3] = it.dt;
         auto e2 = e2map.find(bits(it.dt));
         if (it.dt > 0.0 && e2 != e2map.end()) {
-            a.flags |= F_E2CLS;
-            b.flags |= F_E2CLS;
+            both(a, b, F_E2CLS);
             a.ecls = b.ecls = (int16_t)e2->second;
         }
     };
@@ -300,28 +306,35 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         case Item::RF: {
             OpF32 a = new32(OP_RF);
             OpF64 b = new64(OP_RF);
-            double R[9], r22m1;
-            rf_matrix(it.alpha, it.phi, R, r22m1);
-            for (int c = 0; c < 9; ++c) {
-                a.f[c] = (float)R[c];
-                b.f[c] = R[c];
+            if (it.phi != psi) {
+                // turn the frame from ψ to φ: (u + jv) <- (u + jv)·exp(-jδ), δ = φ - ψ; the float32
+                // program gets (hi, lo) pairs so that the frame never drifts (it is uniform over spins)
+                const double d = it.phi - psi;
+                both(a, b, F_FRAME);
+                split(std::cos(d), a.f[2], a.f[3]);
+                split(std::sin(d), a.f[4], a.f[5]);
+                b.f[2] = std::cos(d);
+                b.f[3] = std::sin(d);
+                psi = it.phi;
             }
-            a.f[9] = (float)r22m1;
-            b.f[9] = r22m1;
             set_e1(a, b, it.tau);
+            a.f[0] = (float)std::cos(it.alpha);
+            a.f[1] = (float)std::sin(it.alpha);
+            b.f[0] = std::cos(it.alpha);
+            b.f[1] = std::sin(it.alpha);
             // fuse a following class precession (the sub-pulse trains of shaped pulses, Eq. 3.23)
             if (g + 1 < groups.size()) {
                 const Item &nx = items[groups[g + 1].first];
                 if (nx.kind == Item::PREC) {
                     auto pc = pmap.find(key_of(nx.k, nx.dt));
                     if (pc != pmap.end()) {
-                        a.flags |= F_PCLS;
-                        b.flags |= F_PCLS;
-                        a.pcls = b.pcls = (int16_t)pc->second;
+                        use_pcls(a, b, pc->second);
                         ++g;
                     }
                 }
             }
+            const uint16_t fast_mask = F_FRAME | F_E1LOAD | F_E1INL | F_PLOAD | F_ADC;
+            if ((a.flags & F_E1CLS) && (a.flags & F_PCLS) && !(a.flags & fast_mask)) a.kind = b.kind = OP_RF_FAST;
             push(a, b);
             break;
         }
@@ -329,22 +342,23 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             OpF32 a = new32(OP_PREC);
             OpF64 b = new64(OP_PREC);
             auto pc = pmap.find(key_of(it.k, it.dt));
-            if (pc != pmap.end()) {
-                a.flags |= F_PCLS;
-                b.flags |= F_PCLS;
-                a.pcls = b.pcls = (int16_t)pc->second;
-            } else {
+            if (pc != pmap.end())
+                use_pcls(a, b, pc->second);
+            else
                 set_inline_prec(a, b, it);
-            }
             push(a, b);
             break;
         }
         case Item::SAMPLE: {
             const int64_t cnt = groups[g].n;
+            for (int64_t q = 0; q < cnt; ++q) {
+                const Item &s = items[groups[g].first + (size_t)q];
+                demod(s.j, s.adc_phase);
+            }
             if (is_zero(it.k, it.dt)) {
                 OpF32 a = new32(OP_PREC);
                 OpF64 b = new64(OP_PREC);
-                a.flags = b.flags = F_ADC;
+                both(a, b, F_ADC);
                 a.adc0 = b.adc0 = (int32_t)it.j;
                 push(a, b);
                 break;
@@ -353,15 +367,13 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             if (pc != pmap.end() && cnt > 1) {
                 OpF32 a = new32(OP_RUN);
                 OpF64 b = new64(OP_RUN);
-                a.flags = b.flags = F_PCLS;
-                a.pcls = b.pcls = (int16_t)pc->second;
+                use_pcls(a, b, pc->second);
                 a.n = b.n = (int32_t)cnt;
                 a.adc0 = b.adc0 = (int32_t)it.j;
                 if (cnt >= 4) {
                     auto an = pmap.find(anchor_key(it, cnt));
                     if (an != pmap.end()) {
-                        a.flags |= F_ANCHOR;
-                        b.flags |= F_ANCHOR;
+                        both(a, b, F_ANCHOR);
                         a.acls = b.acls = (int16_t)an->second;
                     }
                 }
@@ -371,15 +383,11 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
                     const Item &s = items[groups[g].first + (size_t)q];
                     OpF32 a = new32(OP_PREC);
                     OpF64 b = new64(OP_PREC);
-                    if (pc != pmap.end()) {
-                        a.flags |= F_PCLS;
-                        b.flags |= F_PCLS;
-                        a.pcls = b.pcls = (int16_t)pc->second;
-                    } else {
+                    if (pc != pmap.end())
+                        use_pcls(a, b, pc->second);
+                    else
                         set_inline_prec(a, b, s);
-                    }
-                    a.flags |= F_ADC;
-                    b.flags |= F_ADC;
+                    both(a, b, F_ADC);
                     a.adc0 = b.adc0 = (int32_t)s.j;
                     push(a, b);
                 }
@@ -390,6 +398,11 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             OpF32 a = new32(OP_END);
             OpF64 b = new64(OP_END);
             set_e1(a, b, it.tau);
+            // back to the laboratory frame for the final state: (Mx + jMy) = (u + jv)·exp(+jψ)
+            a.f[0] = (float)std::cos(psi);
+            a.f[1] = (float)std::sin(psi);
+            b.f[0] = std::cos(psi);
+            b.f[1] = std::sin(psi);
             push(a, b);
             break;
         }

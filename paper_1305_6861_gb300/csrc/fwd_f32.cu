@@ -13,4 +13,24 @@ int launch_fwd_f32(const FwdArgs &a, int k, int threads, void *stream) {
     }
 }
 
+int fwd_blocks_per_sm_f32(int k, int threads, size_t smem) {
+    switch (k) {
+    case 1: return dev::blocks_per_sm<float, 1, 512>(threads, smem);
+    case 2: return dev::blocks_per_sm<float, 2, 512>(threads, smem);
+    case 4: return dev::blocks_per_sm<float, 4, 512>(threads, smem);
+    case 8: return dev::blocks_per_sm<float, 8, 256>(threads, smem);
+    default: return 0;
+    }
+}
+
+int fwd_regs_f32(int k) {
+    switch (k) {
+    case 1: return dev::regs_of<float, 1, 512>();
+    case 2: return dev::regs_of<float, 2, 512>();
+    case 4: return dev::regs_of<float, 4, 512>();
+    case 8: return dev::regs_of<float, 8, 256>();
+    default: return 0;
+    }
+}
+
 }  // namespace mrsim

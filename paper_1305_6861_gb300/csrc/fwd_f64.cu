@@ -11,6 +11,26 @@ int launch_fwd_f64(const FwdArgs &a, int k, int threads, void *stream) {
     }
 }
 
+int fwd_regs_f32(int k);
+int fwd_blocks_per_sm_f32(int k, int threads, size_t smem);
+int fwd_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
+    if (!fp64) return fwd_blocks_per_sm_f32(k, threads, smem);
+    switch (k) {
+    case 1: return dev::blocks_per_sm<double, 1, 256>(threads, smem);
+    case 2: return dev::blocks_per_sm<double, 2, 256>(threads, smem);
+    default: return 0;
+    }
+}
+
+int fwd_regs(bool fp64, int k) {
+    if (!fp64) return fwd_regs_f32(k);
+    switch (k) {
+    case 1: return dev::regs_of<double, 1, 256>();
+    case 2: return dev::regs_of<double, 2, 256>();
+    default: return 0;
+    }
+}
+
 size_t fwd_smem_bytes(bool fp64, const Program &p, int k, int threads) {
     return dev::smem_layout(fp64, p.n_pcls, p.n_e1, p.n_e2, k * threads, threads / 32).total;
 }

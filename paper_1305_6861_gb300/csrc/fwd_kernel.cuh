@@ -6,18 +6,17 @@
 // 0 stages into shared memory in chunks with bulk asynchronous copies (cp.async.bulk, completed
 // on an mbarrier) while the block computes on the previous chunk.
 //
-// Per operation (Eq. 4.1: M <- T_Relax·T_grad·T'_HF·M + T_Relax,z):
-//   RF   : lazy T1 over the time since the previous pulse, then the Eq. 3.19 rotation;
-//   PREC : Mxy <- Mxy·E2·exp(-j2πφ) with φ = k·x + Δf·Δt in cycles (Eqs. 3.5/3.11/3.14);
-//   RUN  : n samples of one constant-gradient readout, each Mxy <- Mxy·w (w cached per spin);
-//   samples: the sum Σ_spins Mxy (§5.1.1, Eq. 3.32) is reduced in-thread over the K spins,
+// Per operation (Eq. 4.1: M <- T_Relax·T_grad·T'_HF·M + T_Relax,z), with the transverse part
+// carried as u + jv = (Mx + jMy)·exp(-jψ) in the frame of the latest pulse phase ψ:
+//   RF   : lazy T1 recovery Mz <- Mz − ε1·(Mz − M0) over the time since the previous pulse
+//          (ε1 = 1 − exp(−τ/T1) evaluated accurately, never 1 − E1 in float32), then the
+//          Eq. 3.19 rotation, which in the pulse frame is a turn about the frame's x axis;
+//   PREC : u + jv <- (u + jv)·E2·exp(-j2πφ) with φ = k·x + Δf·Δt in cycles (Eqs. 3.5/3.11/3.14);
+//   RUN  : n samples of one constant-gradient readout, each (u + jv) <- (u + jv)·w;
+//   samples: Σ_spins (u + jv) (§5.1.1, Eq. 3.32) reduced in-thread over the K spins (tree),
 //            across the warp by a transposed butterfly (16 samples per pass: lane l ends up
-//            holding the warp total of value l), across warps in shared memory, and across
-//            blocks with float64 atomics after demodulation by exp(-j·adc_phase).
-//
-// Longitudinal magnetisation is carried as Dz = Mz − M0, so T1 recovery is Dz <- (1 − ε1)·Dz
-// with ε1 = 1 − exp(−τ/T1) evaluated accurately (expm1) even for the short sub-pulse spacing of
-// shaped pulses, where 1 − E1 would cancel in float32.
+//            with the warp total of value l), across warps in shared memory and across blocks
+//            with float64 atomics after multiplying by exp(-j(adc_phase − ψ)).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -74,7 +73,7 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t pari
     return true;
 }
 
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s for one 8 KB chunk: only a fault takes that long
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s for one 4 KB chunk: only a fault takes that long
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int RED_STRIDE = SAMPLE_WINDOW + 16;  // per-component row of the reduction window
 
@@ -93,6 +92,21 @@ __device__ __forceinline__ R transpose_reduce32(R (&v)[32], int lane) {
         }
     }
     return v[0];
+}
+
+// Pairwise (tree) sum of K values: log2(K) dependent adds instead of K − 1.
+template <typename R, int K>
+__device__ __forceinline__ R tree_sum(const R (&a)[K]) {
+    if constexpr (K == 1) {
+        return a[0];
+    } else if constexpr (K == 2) {
+        return a[0] + a[1];
+    } else if constexpr (K == 4) {
+        return (a[0] + a[1]) + (a[2] + a[3]);
+    } else {
+        static_assert(K == 8, "K must be 1, 2, 4 or 8");
+        return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    }
 }
 
 template <typename R>
@@ -118,8 +132,8 @@ __device__ __forceinline__ float ff_term(float kh, float kl, float xh, float xl,
 }
 __device__ __forceinline__ float wrap1(float t) { return t - rintf(t); }
 
-// Sum the sample window over warps (float64), demodulate by exp(-j·adc_phase) and add the
-// block's partial sums to the global signal.  Every thread of the block must call it.
+// Sum the sample window over warps (float64), multiply by the sample's demodulation factor and
+// add the block's partial sums to the global signal.  Every thread of the block must call it.
 template <typename R>
 __device__ __noinline__ void flush_window(const R *red, const double *demod, double *signal, int win_base,
                                           int win_end, int tid, int nthr, int nwarp) {
@@ -144,76 +158,94 @@ struct Spins {
     using Op = typename std::conditional<std::is_same<R, float>::value, OpF32, OpF64>::type;
     using V = typename V2<R>::T;
     static constexpr bool F64 = std::is_same<R, double>::value;
-    static constexpr int NPRM = F64 ? 6 : 10;  // per-spin rows kept in shared memory
 
-    R mx[K], my[K], dz[K], rho[K];
-    R wr[K], wi[K];
-    R e1v[K];
-    int cur_p, cur_e1;
+    R u[K], v[K], mz[K], rho[K];  // transverse part in the pulse frame, longitudinal, M0
+    R wr[K], wi[K];               // cached phasor class
+    R e1v[K];                     // cached T1 class ε1
     int win_base, win_end;
 
-    // shared-memory views
+    // shared-memory views and block geometry
     const V *cw;
     const R *ce1, *ce2, *prm;
     R *red;
     int S, nthr, tid, lane, warp, nwarp;
+    int64_t base, np, n_spins;
+    const double *params;
     const double *demod;
     double *signal;
 
     __device__ __forceinline__ int li(int i) const { return i * nthr + tid; }
 
     __device__ __forceinline__ void load_w(int c) {
-        if (c == cur_p) return;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const V w = cw[c * S + li(i)];
             wr[i] = w.x;
             wi[i] = w.y;
         }
-        cur_p = c;
     }
     __device__ __forceinline__ void rot_w() {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            const R nx = mx[i] * wr[i] - my[i] * wi[i];
-            const R ny = mx[i] * wi[i] + my[i] * wr[i];
-            mx[i] = nx;
-            my[i] = ny;
+            const R nu = u[i] * wr[i] - v[i] * wi[i];
+            const R nv = u[i] * wi[i] + v[i] * wr[i];
+            u[i] = nu;
+            v[i] = nv;
         }
+    }
+    __device__ __forceinline__ void t1_cached() {
+#pragma unroll
+        for (int i = 0; i < K; ++i) mz[i] = mz[i] - e1v[i] * (mz[i] - rho[i]);
     }
     // lazy T1 recovery over the interval since the previous pulse
     __device__ __forceinline__ void t1_relax(const Op &op) {
         if (op.flags & F_E1CLS) {
-            if (op.ecls != cur_e1) {
+            if (op.flags & F_E1LOAD) {
 #pragma unroll
                 for (int i = 0; i < K; ++i) e1v[i] = ce1[op.ecls * S + li(i)];
-                cur_e1 = op.ecls;
             }
-#pragma unroll
-            for (int i = 0; i < K; ++i) dz[i] = dz[i] - e1v[i] * dz[i];
+            t1_cached();
         } else if (op.flags & F_E1INL) {
-            const R tau = (R)op.f[10];
+            const double tau = (double)op.f[10];
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                const R r1 = prm[(NPRM - 2) * S + li(i)];
-                const R eps = -expm1(-tau * r1);
-                dz[i] = dz[i] - eps * dz[i];
+                const int64_t s = base + li(i);
+                const double r1 = s < n_spins ? params[P_R1 * np + s] : 0.0;
+                const R eps = (R)(-expm1(-tau * r1));
+                mz[i] = mz[i] - eps * (mz[i] - rho[i]);
             }
         }
     }
-    __device__ __forceinline__ void rf(const Op &op) {
-        const R r00 = (R)op.f[0], r01 = (R)op.f[1], r02 = (R)op.f[2];
-        const R r10 = (R)op.f[3], r11 = (R)op.f[4], r12 = (R)op.f[5];
-        const R r20 = (R)op.f[6], r21 = (R)op.f[7], r22 = (R)op.f[8], r22m1 = (R)op.f[9];
+    // hard pulse about the frame's x axis (Eq. 3.19 in the pulse frame)
+    __device__ __forceinline__ void rf_turn(R ca, R sa) {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            // (Mx, My, Dz + M0) rotated, Dz' = Mz' − M0 = r20 Mx + r21 My + r22 Dz + (r22 − 1) M0
-            const R nx = r00 * mx[i] + r01 * my[i] + r02 * dz[i] + r02 * rho[i];
-            const R ny = r10 * mx[i] + r11 * my[i] + r12 * dz[i] + r12 * rho[i];
-            const R nz = r20 * mx[i] + r21 * my[i] + r22 * dz[i] + r22m1 * rho[i];
-            mx[i] = nx;
-            my[i] = ny;
-            dz[i] = nz;
+            const R nv = ca * v[i] + sa * mz[i];
+            const R nz = ca * mz[i] - sa * v[i];
+            v[i] = nv;
+            mz[i] = nz;
+        }
+    }
+    // turn the frame by exp(-jδ) (uniform over spins); float32 uses (hi, lo) constants
+    __device__ __forceinline__ void frame_turn(const Op &op) {
+        if constexpr (F64) {
+            const double c = op.f[2], s = op.f[3];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const double nu = u[i] * c + v[i] * s;
+                const double nv = v[i] * c - u[i] * s;
+                u[i] = nu;
+                v[i] = nv;
+            }
+        } else {
+            const float ch = op.f[2], cl = op.f[3], sh = op.f[4], sl = op.f[5];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const float nu = fmaf(u[i], ch, fmaf(v[i], sh, fmaf(u[i], cl, v[i] * sl)));
+                const float nv = fmaf(v[i], ch, -fmaf(u[i], sh, fmaf(u[i], sl, -v[i] * cl)));
+                u[i] = nu;
+                v[i] = nv;
+            }
         }
     }
     // precession by the op's own moment and interval (not a cached class)
@@ -222,12 +254,15 @@ struct Spins {
         for (int i = 0; i < K; ++i) {
             const int l = li(i);
             R e2;
-            if (op.flags & F_E2CLS)
+            if (op.flags & F_E2CLS) {
                 e2 = ce2[op.ecls * S + l];
-            else if (op.flags & F_DT)
-                e2 = exp(-(R)op.f[F64 ? 3 : 8] * prm[(NPRM - 1) * S + l]);
-            else
+            } else if (op.flags & F_DT) {
+                const int64_t s = base + l;
+                const double r2 = s < n_spins ? params[P_R2 * np + s] : 0.0;
+                e2 = (R)exp(-(double)op.f[F64 ? 3 : 8] * r2);
+            } else {
                 e2 = (R)1;
+            }
             R sn, cs;
             if constexpr (F64) {
                 double th = 0.0;
@@ -244,13 +279,15 @@ struct Spins {
                 if (op.flags & F_KZ) t = wrap1(t + ff_term(op.f[4], op.f[5], prm[4 * S + l], prm[5 * S + l], err));
                 if (op.flags & F_DT) t = wrap1(t + ff_term(op.f[6], op.f[7], prm[6 * S + l], prm[7 * S + l], err));
                 t = wrap1(t + err);
-                __sincosf(6.283185307179586f * t, &sn, &cs);
+                // accurate sin/cos of the reduced angle (the hardware approximation's 2^-21 absolute
+                // error would accumulate over many inline intervals)
+                sincospif(2.0f * t, &sn, &cs);
             }
             const R ar = e2 * cs, ai = -e2 * sn;
-            const R nx = mx[i] * ar - my[i] * ai;
-            const R ny = mx[i] * ai + my[i] * ar;
-            mx[i] = nx;
-            my[i] = ny;
+            const R nu = u[i] * ar - v[i] * ai;
+            const R nv = u[i] * ai + v[i] * ar;
+            u[i] = nu;
+            v[i] = nv;
         }
     }
 
@@ -263,12 +300,7 @@ struct Spins {
 
     __device__ __forceinline__ void sample1(int j) {
         if (j + 1 - win_base > SAMPLE_WINDOW) flush();
-        R sx = mx[0], sy = my[0];
-#pragma unroll
-        for (int i = 1; i < K; ++i) {
-            sx += mx[i];
-            sy += my[i];
-        }
+        R sx = tree_sum<R, K>(u), sy = tree_sum<R, K>(v);
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
             sx += __shfl_xor_sync(FULL, sx, off);
@@ -281,42 +313,49 @@ struct Spins {
         win_end = j + 1;
     }
 
+    // one sample step of a run: rotate by the cached class, return the thread's sums
+    __device__ __forceinline__ void run_step(R &sx, R &sy) {
+        rot_w();
+        sx = tree_sum<R, K>(u);
+        sy = tree_sum<R, K>(v);
+    }
+
     __device__ __forceinline__ void run(const Op &op) {
         const int n = op.n, j0 = op.adc0;
-        load_w(op.pcls);
-        R ax[K], ay[K];
+        if (op.flags & F_PLOAD) load_w(op.pcls);
+        R au[K], av[K];
         const bool anchor = (op.flags & F_ANCHOR) != 0;
         if (anchor) {
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                ax[i] = mx[i];
-                ay[i] = my[i];
+                au[i] = u[i];
+                av[i] = v[i];
             }
         }
         if (j0 + n - win_base > SAMPLE_WINDOW) flush();
         R *r0 = red_row(0) + (j0 - win_base);
         R *r1 = red_row(1) + (j0 - win_base);
-        for (int t0 = 0; t0 < n; t0 += 16) {
-            const int tt = min(16, n - t0);
-            R v[32];
+        int t0 = 0;
+        for (; t0 + 16 <= n; t0 += 16) {  // full tiles: no guards
+            R vv[32];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) run_step(vv[2 * t], vv[2 * t + 1]);
+            const R tot = transpose_reduce32(vv, lane);
+            ((lane & 1) ? r1 : r0)[t0 + (lane >> 1)] = tot;
+        }
+        if (t0 < n) {  // ragged tail
+            const int tt = n - t0;
+            R vv[32];
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 if (t < tt) {
-                    rot_w();
-                    R sx = mx[0], sy = my[0];
-#pragma unroll
-                    for (int i = 1; i < K; ++i) {
-                        sx += mx[i];
-                        sy += my[i];
-                    }
-                    v[2 * t] = sx;
-                    v[2 * t + 1] = sy;
+                    run_step(vv[2 * t], vv[2 * t + 1]);
                 } else {
-                    v[2 * t] = (R)0;
-                    v[2 * t + 1] = (R)0;
+                    vv[2 * t] = (R)0;
+                    vv[2 * t + 1] = (R)0;
                 }
             }
-            const R tot = transpose_reduce32(v, lane);
+            const R tot = transpose_reduce32(vv, lane);
             if (lane < 2 * tt) ((lane & 1) ? r1 : r0)[t0 + (lane >> 1)] = tot;
         }
         win_end = j0 + n;
@@ -324,27 +363,33 @@ struct Spins {
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const V w = cw[op.acls * S + li(i)];
-                mx[i] = ax[i] * w.x - ay[i] * w.y;
-                my[i] = ax[i] * w.y + ay[i] * w.x;
+                u[i] = au[i] * w.x - av[i] * w.y;
+                v[i] = au[i] * w.y + av[i] * w.x;
             }
         }
     }
 
     __device__ __forceinline__ void exec(const Op &op) {
         switch (op.kind) {
+        case OP_RF_FAST:  // sub-pulse of a shaped pulse: every cache already holds the right class
+            t1_cached();
+            rf_turn((R)op.f[0], (R)op.f[1]);
+            rot_w();
+            break;
         case OP_RF:
+            if (op.flags & F_FRAME) frame_turn(op);
             t1_relax(op);
-            rf(op);
+            rf_turn((R)op.f[0], (R)op.f[1]);
             if (op.flags & F_PCLS) {
-                load_w(op.pcls);
+                if (op.flags & F_PLOAD) load_w(op.pcls);
                 rot_w();
             }
             if (op.flags & F_ADC) sample1(op.adc0);
             break;
         case OP_PREC:
             if (op.flags & F_PCLS) {
-                load_w(op.pcls);
-                for (int r = 0; r < op.n; ++r) rot_w();
+                if (op.flags & F_PLOAD) load_w(op.pcls);
+                rot_w();
             } else if (op.flags & F_INLINE) {
                 prec_inline(op);
             }
@@ -369,7 +414,7 @@ __host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1
     SmemLayout L;
     const size_t rs = f64 ? 8 : 4;
     const size_t opb = f64 ? sizeof(OpF64) * 2 * CHUNK_F64 : sizeof(OpF32) * 2 * CHUNK_F32;
-    const int nprm = f64 ? 6 : 10;
+    const int nprm = f64 ? 4 : 8;
     size_t o = 0;
     L.ops = o;
     o += opb;
@@ -424,10 +469,12 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
     sp.red = reinterpret_cast<R *>(smem + L.red);
     sp.demod = P.demod;
     sp.signal = a.signal;
-    sp.cur_p = -1;
-    sp.cur_e1 = -1;
+    sp.params = a.params;
     sp.win_base = 0;
     sp.win_end = 0;
+    sp.base = (int64_t)blockIdx.x * S;
+    sp.np = a.n_pad;
+    sp.n_spins = a.n_spins;
 
     const Op *gops = reinterpret_cast<const Op *>(P.ops);
     const int n_ops = P.n_ops;
@@ -449,12 +496,11 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
     }
 
     // ---- per-spin set-up: parameters, class tables (float64 math), initial state -------------
-    const int64_t base = (int64_t)blockIdx.x * S;
     const int64_t np = a.n_pad;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const int l = sp.li(i);
-        const int64_t s = base + l;
+        const int64_t s = sp.base + l;
         const bool valid = s < a.n_spins;
         const double x = valid ? a.params[P_X * np + s] : 0.0;
         const double y = valid ? a.params[P_Y * np + s] : 0.0;
@@ -469,18 +515,14 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
             prm[1 * S + l] = y;
             prm[2 * S + l] = z;
             prm[3 * S + l] = df;
-            prm[4 * S + l] = r1;
-            prm[5 * S + l] = r2;
         } else {
-            const double v[4] = {x, y, z, df};
+            const double vals[4] = {x, y, z, df};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float h = (float)v[q];
+                const float h = (float)vals[q];
                 prm[(2 * q) * S + l] = h;
-                prm[(2 * q + 1) * S + l] = (float)(v[q] - (double)h);
+                prm[(2 * q + 1) * S + l] = (float)(vals[q] - (double)h);
             }
-            prm[8 * S + l] = (float)r1;
-            prm[9 * S + l] = (float)r2;
         }
         for (int c = 0; c < P.n_pcls; ++c) {
             const double kx = __ldg(P.pcls + 4 * c), ky = __ldg(P.pcls + 4 * c + 1);
@@ -497,15 +539,18 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
         }
         for (int c = 0; c < P.n_e1; ++c) ce1[c * S + l] = (R)(-expm1(-__ldg(P.e1 + c) * r1));
         for (int c = 0; c < P.n_e2; ++c) ce2[c * S + l] = (R)exp(-__ldg(P.e2 + c) * r2);
-        if (a.state_in && valid) {
-            sp.mx[i] = (R)a.state_in[3 * s];
-            sp.my[i] = (R)a.state_in[3 * s + 1];
-            sp.dz[i] = (R)(a.state_in[3 * s + 2] - m0);
+        if (a.state_in && valid) {  // laboratory frame = pulse frame ψ = 0 at the start
+            sp.u[i] = (R)a.state_in[3 * s];
+            sp.v[i] = (R)a.state_in[3 * s + 1];
+            sp.mz[i] = (R)a.state_in[3 * s + 2];
         } else {
-            sp.mx[i] = (R)0;
-            sp.my[i] = (R)0;
-            sp.dz[i] = (R)0;
+            sp.u[i] = (R)0;
+            sp.v[i] = (R)0;
+            sp.mz[i] = (R)m0;
         }
+        sp.wr[i] = (R)1;
+        sp.wi[i] = (R)0;
+        sp.e1v[i] = (R)0;
     }
     __syncthreads();
 
@@ -519,7 +564,8 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
         }
         __syncthreads();
         if (*abort_flag) {
-            if (sp.tid == 0 && c + 1 < n_chunks) mbar_wait_bounded(&bars[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1), WAIT_LIMIT_NS);
+            if (sp.tid == 0 && c + 1 < n_chunks)
+                mbar_wait_bounded(&bars[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1), WAIT_LIMIT_NS);
             return;
         }
         const Op *ops = opbuf + (c & 1) * CH;
@@ -531,13 +577,18 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
     if (sp.win_end > sp.win_base) sp.flush();
 
     if (a.state_out) {
+        // the final OP_END carries the frame angle: (Mx + jMy) = (u + jv)·(cos ψ + j sin ψ)
+        const Op &last = gops[n_ops - 1];
+        const bool end = last.kind == OP_END;
+        const double cps = end ? (double)last.f[0] : 1.0, sps = end ? (double)last.f[1] : 0.0;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            const int64_t s = base + sp.li(i);
+            const int64_t s = sp.base + sp.li(i);
             if (s < a.n_spins) {
-                a.state_out[3 * s] = (double)sp.mx[i];
-                a.state_out[3 * s + 1] = (double)sp.my[i];
-                a.state_out[3 * s + 2] = (double)sp.dz[i] + (double)a.params[P_RHO * np + s];
+                const double uu = (double)sp.u[i], vv = (double)sp.v[i];
+                a.state_out[3 * s] = uu * cps - vv * sps;
+                a.state_out[3 * s + 1] = uu * sps + vv * cps;
+                a.state_out[3 * s + 2] = (double)sp.mz[i];
             }
         }
     }
@@ -556,6 +607,29 @@ int launch_one(const FwdArgs &a, int threads, void *stream) {
     if (grid > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
     kern<<<(unsigned)grid, threads, L.total, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
+}
+
+template <typename R, int K, int MAXT>
+int blocks_per_sm(int threads, size_t smem) {
+    if (threads <= 0 || threads > MAXT || threads % 32) return 0;
+    auto kern = fwd_kernel<R, K, MAXT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <typename R, int K, int MAXT>
+int regs_of() {
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, fwd_kernel<R, K, MAXT>) != cudaSuccess) return 0;
+    return at.numRegs;
 }
 
 }  // namespace dev

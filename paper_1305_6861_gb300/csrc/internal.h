@@ -7,40 +7,51 @@
 // kind).  Spin-independent work is done here once per sequence, as the paper's
 // master process does (§6.3):
 //   * gradient moments k = γ/2π · G · Δt in cycles/m;
-//   * RF rotation matrices (Eq. 3.19) and the accurate cos α − 1;
 //   * runs of events without RF and ADC merged into one precession
 //     (analytic solutions span long intervals in one step, §3.3);
 //   * T1 recovery applied lazily, once per RF pulse, over the time since the
 //     previous pulse (Mz only matters at the next pulse);
+//   * the transverse magnetisation is carried in a frame rotated about z by
+//     the phase ψ of the most recent RF pulse, u + jv = (Mx + jMy)·exp(-jψ).
+//     In that frame every hard pulse (Eq. 3.19) turns about the frame's x
+//     axis: u' = u, v' = cos α·v + sin α·Mz, Mz' = cos α·Mz − sin α·v.
+//     A pulse with another phase first turns the frame (one complex product by
+//     a constant); precession commutes with the frame; the frame angle at each
+//     sample is folded into the sample's demodulation factor;
 //   * recurring precession intervals (same moment and Δt) become "classes"
 //     whose per-spin phasor E2·exp(-j2π(k·x + Δf·Δt)) each thread block
 //     evaluates once per spin in float64 and then reuses, e.g. for every
-//     sample of a constant-gradient readout.
+//     sample of a constant-gradient readout.  The host tracks which class the
+//     kernel holds in registers and marks the operations that must reload it.
 #pragma once
 #include <cstdint>
 
 namespace mrsim {
 
 enum OpKind : uint8_t {
-    OP_END = 0,   // final lazy T1 over f[10] (flags E1CLS/E1INL)
-    OP_RF = 1,    // lazy T1 over f[10], then rotation f[0..8] (row-major Eq. 3.19), f[9] = R22 - 1;
-                  // optionally fused precession by class pcls and a single sample
-    OP_PREC = 2,  // precession + T2 over one interval: class pcls (repeated n times) or inline
-    OP_RUN = 3,   // n consecutive samples, each after one precession by class pcls
+    OP_END = 0,      // lazy T1 over f[10]; f[0], f[1] = cos ψ, sin ψ of the final frame
+    OP_RF = 1,       // general pulse: [frame turn f[2],f[3]] [lazy T1] rotation f[0]=cos α, f[1]=sin α
+                     // [fused class precession] [single sample]
+    OP_RF_FAST = 2,  // sub-pulse of a train: lazy T1 with the cached class, rotation, cached precession
+    OP_PREC = 3,     // precession + T2 over one interval: cached class or inline; [single sample]
+    OP_RUN = 4,      // n consecutive samples, each after one precession by the cached class
 };
 
 enum OpFlags : uint16_t {
-    F_ADC = 1,      // one sample (index adc0) after the operation
-    F_PCLS = 2,     // precession by cached phasor class pcls
-    F_INLINE = 4,   // PREC: phase from the op's own moment and Δt
-    F_E1CLS = 8,    // RF/END: lazy T1 factor from cached class ecls
-    F_E1INL = 16,   // RF/END: lazy T1 factor computed from f[10]
-    F_E2CLS = 32,   // inline PREC: T2 factor from cached class ecls
-    F_ANCHOR = 64,  // RUN: state after the run = state before * phasor class acls (no drift)
-    F_KX = 128,     // inline PREC: which phase terms are non-zero
-    F_KY = 256,
-    F_KZ = 512,
-    F_DT = 1024,
+    F_ADC = 1,       // one sample (index adc0) after the operation
+    F_PCLS = 2,      // precession by the cached phasor class
+    F_PLOAD = 4,     // load phasor class pcls into the register cache first
+    F_INLINE = 8,    // PREC: phase from the op's own moment and Δt
+    F_E1CLS = 16,    // RF/END: lazy T1 factor from the cached T1 class
+    F_E1LOAD = 32,   // load T1 class ecls into the register cache first
+    F_E1INL = 64,    // RF/END: lazy T1 factor computed from f[10]
+    F_E2CLS = 128,   // inline PREC: T2 factor from class ecls
+    F_ANCHOR = 256,  // RUN: state after the run = state before * phasor class acls (no drift)
+    F_FRAME = 512,   // RF: turn the frame by exp(-jδ), f[2] = cos δ, f[3] = sin δ
+    F_KX = 1024,     // inline PREC: which phase terms are non-zero
+    F_KY = 2048,
+    F_KZ = 4096,
+    F_DT = 8192,
 };
 
 // float32 program: 64 bytes.  Inline PREC payload: kx, ky, kz, Δt as (hi, lo) float pairs
@@ -79,8 +90,8 @@ constexpr int MAX_E2CLS = 4;
 constexpr int SAMPLE_WINDOW = 256;
 constexpr int RUN_MAX = SAMPLE_WINDOW;
 // Ops staged in shared memory per bulk copy (two buffers).
-constexpr int CHUNK_F32 = 128;
-constexpr int CHUNK_F64 = 64;
+constexpr int CHUNK_F32 = 64;
+constexpr int CHUNK_F64 = 32;
 
 // Per-spin parameter block on the device: 7 float64 SoA rows of n_pad values:
 // x, y, z [m], Δf = Δω/2π [Hz], M0, R1 = 1/T1, R2 = 1/T2 [1/s] (0 for T = ∞).
@@ -94,7 +105,7 @@ struct Program {
     const double *pcls;  // 4 per class: kx, ky, kz [cycles/m], Δt [s]
     const double *e1;    // τ [s] per class
     const double *e2;    // Δt [s] per class
-    const double *demod; // 2 per sample: cos(adc_phase), -sin(adc_phase)
+    const double *demod; // 2 per sample: exp(-j(adc_phase - ψ)) with ψ the frame at the sample
     int64_t n_adc;
 };
 
@@ -102,8 +113,8 @@ struct FwdArgs {
     Program prog;
     const double *params;  // NPARAM x n_pad
     int64_t n_spins, n_pad;
-    const double *state_in;  // NULL or 3 per spin (device)
-    double *state_out;       // NULL or 3 per spin (device)
+    const double *state_in;  // NULL or 3 per spin (device), laboratory frame
+    double *state_out;       // NULL or 3 per spin (device), laboratory frame
     double *signal;          // 2 * n_adc (device), accumulated with atomics
     int *status;             // device status word (0 = ok)
 };
@@ -112,6 +123,10 @@ struct FwdArgs {
 int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
+// Registers per thread of a kernel instance (0 if the shape does not exist).
+int fwd_regs(bool fp64, int spins_per_thread);
+// Resident blocks per SM of a launch shape with `smem` dynamic shared memory (0 = cannot launch).
+int fwd_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
 int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, const double *z,
                 const double *rho, const double *t1, const double *t2, const double *dw,
                 double *params, int *bad, void *stream);

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmrsim.so")
 FP64 = 0
 FP32 = 1
 ACCUMULATE = 1
+TUNE = 2
 
 EVENT_DTYPE = np.dtype(
     [("dt", "<f8"), ("gx", "<f8"), ("gy", "<f8"), ("gz", "<f8"), ("rf_flip", "<f8"),
@@ -32,7 +33,7 @@ EXPORTS = (
     "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
     "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
-    "mrsim_debug_compile",
+    "mrsim_debug_compile", "mrsim_autotune",
 )
 
 
@@ -91,7 +92,8 @@ def lib():
             "mrsim_sequence_destroy": (None, [vp]),
             "mrsim_simulate": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
             "mrsim_simulate_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64, P(Options)]),
-            "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, vp, P(i64), vp, P(i32), vp, P(i32), vp, P(i32), P(i64)]),
+            "mrsim_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, P(Options)]),
+            "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, vp, P(i64), vp, P(i32), vp, P(i32), vp, P(i32), vp, P(i64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -229,9 +231,18 @@ def simulate(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP3
     return out
 
 
+def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None):
+    """Time every launch shape on a prefix of the program; the winner is kept in the sequence
+    handle for this (precision, spin count).  Returns (spins_per_thread, threads_per_block)."""
+    opt = Options()
+    ctx.check(lib().mrsim_autotune(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), ctypes.byref(opt)))
+    return int(opt.spins_per_thread), int(opt.threads_per_block)
+
+
 def debug_compile(events, gamma_hz_per_t: float):
     """Host-only compile of an event list (no GPU needed): returns the float64 device program
-    (op records as a structured array) and its class tables."""
+    (op records as a structured array), its class tables and the per-sample demodulation
+    factors (complex, one per sample)."""
     L = lib()
     ev = np.ascontiguousarray(events)
     if ev.dtype != EVENT_DTYPE:
@@ -240,19 +251,21 @@ def debug_compile(events, gamma_hz_per_t: float):
     n_p, n_1, n_2 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     n_adc = ctypes.c_int64()
     rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), None, ctypes.byref(n_ops), None,
-                               ctypes.byref(n_p), None, ctypes.byref(n_1), None, ctypes.byref(n_2), ctypes.byref(n_adc))
+                               ctypes.byref(n_p), None, ctypes.byref(n_1), None, ctypes.byref(n_2), None,
+                               ctypes.byref(n_adc))
     if rc != 0:
         raise MrsimError(rc, "mrsim_debug_compile failed")
     ops = np.zeros(n_ops.value, dtype=OP64_DTYPE)
     pcls = np.zeros(4 * n_p.value)
     e1 = np.zeros(n_1.value)
     e2 = np.zeros(n_2.value)
+    demod = np.zeros(n_adc.value, dtype=np.complex128)
     rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), _ptr(ops), ctypes.byref(n_ops),
                                _ptr(pcls), ctypes.byref(n_p), _ptr(e1), ctypes.byref(n_1), _ptr(e2), ctypes.byref(n_2),
-                               ctypes.byref(n_adc))
+                               _ptr(demod), ctypes.byref(n_adc))
     if rc != 0:
         raise MrsimError(rc, "mrsim_debug_compile failed")
-    return ops, pcls.reshape(-1, 4), e1, e2, int(n_adc.value)
+    return ops, pcls.reshape(-1, 4), e1, e2, demod
 
 
 # Layout of one float64 device operation (128 bytes), for diagnostics.
@@ -261,6 +274,7 @@ OP64_DTYPE = np.dtype(
      ("ecls", "<i2"), ("acls", "<i2"), ("rsv1", "<i2"), ("rsv2", "<i4"), ("f", "<f8", (13,))]
 )
 assert OP64_DTYPE.itemsize == 128
-OP_END, OP_RF, OP_PREC, OP_RUN = 0, 1, 2, 3
-F_ADC, F_PCLS, F_INLINE, F_E1CLS, F_E1INL, F_E2CLS, F_ANCHOR = 1, 2, 4, 8, 16, 32, 64
-F_KX, F_KY, F_KZ, F_DT = 128, 256, 512, 1024
+OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN = 0, 1, 2, 3, 4
+F_ADC, F_PCLS, F_PLOAD, F_INLINE, F_E1CLS, F_E1LOAD, F_E1INL, F_E2CLS, F_ANCHOR, F_FRAME = (
+    1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
+F_KX, F_KY, F_KZ, F_DT = 1024, 2048, 4096, 8192

@@ -1,9 +1,10 @@
 """Test-side interpreter of the compiled float64 device program (host-compiler check, no GPU).
 
 It executes the operation stream that ``mrsim_debug_compile`` returns with numpy, with the
-semantics the kernels implement (lazy T1 per pulse, cached precession classes, sample runs
-with anchors), so that the host compiler's rewrites — merged intervals, fused sub-pulses,
-class selection, run grouping — can be compared with the oracle on the CPU.  It is test
+semantics the kernels implement (pulse frame, lazy T1 per pulse, cached precession and T1
+classes with explicit reloads, sample runs with anchors), so that the host compiler's
+rewrites — merged intervals, fused sub-pulses, frame tracking, class selection, cache
+bookkeeping, run grouping — can be compared with the oracle on the CPU.  It is test
 infrastructure, not a fallback: the library never calls it.
 """
 import math
@@ -14,7 +15,8 @@ from paper_1305_6861_gb300 import mrsim as M
 
 
 def interpret(events, gamma, ph, state_in=None):
-    ops, pcls, e1tab, e2tab, n_adc = M.debug_compile(events, gamma)
+    ops, pcls, e1tab, e2tab, demod = M.debug_compile(events, gamma)
+    n_adc = demod.shape[0]
     x, y, z, rho = ph.x, ph.y, ph.z, ph.rho
     df = ph.dw / (2 * math.pi)
     with np.errstate(divide="ignore"):
@@ -26,53 +28,78 @@ def interpret(events, gamma, ph, state_in=None):
     adc_phase = events["adc_phase"][events["adc"] != 0]
     sig = np.zeros(n_adc, dtype=complex)
     if state_in is None:
-        mxy = np.zeros(ph.n, dtype=complex)
-        dz = np.zeros(ph.n)
+        m = np.zeros(ph.n, dtype=complex)  # u + jv in the pulse frame (ψ = 0 at the start)
+        mz = rho.copy()
     else:
-        mxy = state_in[:, 0] + 1j * state_in[:, 1]
-        dz = state_in[:, 2] - rho
+        m = state_in[:, 0] + 1j * state_in[:, 1]
+        mz = state_in[:, 2].copy()
+    psi = 0.0  # frame angle, tracked here independently from the ops' frame turns
+    wc = None  # register caches of the kernel
+    e1c = None
 
     def sample(j, v):
-        sig[j] += v.sum() * np.exp(-1j * adc_phase[j])
+        # lab frame: Mx + jMy = (u + jv)·e^{jψ}; demodulate by e^{-j adc_phase}; the table the
+        # kernel uses must be exactly that factor
+        want = np.exp(1j * psi) * np.exp(-1j * adc_phase[j])
+        assert abs(demod[j] - want) < 1e-12, (j, demod[j], want)
+        sig[j] += v.sum() * demod[j]
 
     def t1(op):
-        nonlocal dz
+        nonlocal mz, e1c
         if op["flags"] & M.F_E1CLS:
-            dz = dz - E1[op["ecls"]] * dz
+            if op["flags"] & M.F_E1LOAD:
+                e1c = E1[op["ecls"]]
+            mz = mz - e1c * (mz - rho)
         elif op["flags"] & M.F_E1INL:
-            dz = dz - (-np.expm1(-op["f"][10] * r1)) * dz
+            mz = mz - (-np.expm1(-op["f"][10] * r1)) * (mz - rho)
+
+    def pcls_use(op):
+        nonlocal wc
+        if op["flags"] & M.F_PLOAD:
+            wc = W[op["pcls"]]
+        return wc
 
     for op in ops:
         k, fl, f = op["kind"], op["flags"], op["f"]
-        if k == M.OP_RF:
-            t1(op)
-            R = f[:9].reshape(3, 3)
-            v = np.stack([mxy.real, mxy.imag, dz + rho])
-            nv = R @ v
-            mxy = nv[0] + 1j * nv[1]
-            dz = nv[2] - rho
-            if fl & M.F_PCLS:
-                mxy = mxy * W[op["pcls"]]
+        if k in (M.OP_RF, M.OP_RF_FAST):
+            if fl & M.F_FRAME:
+                d = math.atan2(f[3], f[2])
+                m = m * np.exp(-1j * d)
+                psi += d
+            if k == M.OP_RF_FAST:
+                mz = mz - e1c * (mz - rho)
+            else:
+                t1(op)
+            ca, sa = f[0], f[1]
+            v = m.imag
+            nv = ca * v + sa * mz
+            mz = ca * mz - sa * v
+            m = m.real + 1j * nv
+            if k == M.OP_RF_FAST or fl & M.F_PCLS:
+                m = m * pcls_use(op)
             if fl & M.F_ADC:
-                sample(op["adc0"], mxy)
+                sample(op["adc0"], m)
         elif k == M.OP_PREC:
             if fl & M.F_PCLS:
                 for _ in range(op["n"]):
-                    mxy = mxy * W[op["pcls"]]
+                    m = m * pcls_use(op)
             elif fl & M.F_INLINE:
                 e2 = E2[op["ecls"]] if fl & M.F_E2CLS else np.exp(-f[3] * r2)
                 th = f[0] * x + f[1] * y + f[2] * z + f[3] * df
-                mxy = mxy * e2 * np.exp(-2j * math.pi * th)
+                m = m * e2 * np.exp(-2j * math.pi * th)
             if fl & M.F_ADC:
-                sample(op["adc0"], mxy)
+                sample(op["adc0"], m)
         elif k == M.OP_RUN:
-            start = mxy
+            start = m
+            w = pcls_use(op)
             for t in range(op["n"]):
-                mxy = mxy * W[op["pcls"]]
-                sample(op["adc0"] + t, mxy)
+                m = m * w
+                sample(op["adc0"] + t, m)
             if fl & M.F_ANCHOR:
-                mxy = start * W[op["acls"]]
+                m = start * W[op["acls"]]
         else:
             t1(op)
-    state = np.stack([mxy.real, mxy.imag, dz + rho], 1)
+            assert abs(math.atan2(f[1], f[0]) - math.atan2(math.sin(psi), math.cos(psi))) < 1e-9
+    lab = m * np.exp(1j * psi)
+    state = np.stack([lab.real, lab.imag, mz], 1)
     return sig, state, ops

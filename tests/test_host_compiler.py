@@ -42,7 +42,7 @@ def _compile_rc(events, gamma=W.GAMMA_BAR):
     n = [ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()]
     return L.mrsim_debug_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), float(gamma), None,
                                  ctypes.byref(n[0]), None, ctypes.byref(n[1]), None, ctypes.byref(n[2]), None,
-                                 ctypes.byref(n[3]), ctypes.byref(n[4]))
+                                 ctypes.byref(n[3]), None, ctypes.byref(n[4]))
 
 
 @pytest.mark.parametrize("field,value", [("dt", -1e-3), ("gx", np.nan), ("rf_flip", np.inf), ("adc", 2),
@@ -120,11 +120,16 @@ def test_class_tables_bounded_and_used(mrsim_lib):
     from paper_1305_6861_gb300 import mrsim as M
 
     w = W.config2(n=32, iso=2)
-    ops, pcls, e1, e2, n_adc = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
+    ops, pcls, e1, e2, demod = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
     assert len(pcls) <= 8 and len(e1) <= 4 and len(e2) <= 4
-    # the shaped-pulse sub-pulse trains are fused RF + class precession operations
-    rf = ops[ops["kind"] == M.OP_RF]
-    assert np.count_nonzero(rf["flags"] & M.F_PCLS) >= 0.99 * len(rf)
+    # the shaped-pulse sub-pulse trains are fused RF + class precession operations, and all but
+    # the first two sub-pulses of each train run as the branch-free fast codelet
+    rf = ops[(ops["kind"] == M.OP_RF) | (ops["kind"] == M.OP_RF_FAST)]
+    fused = (rf["kind"] == M.OP_RF_FAST) | ((rf["flags"] & M.F_PCLS) > 0)
+    # per TR only the excitation's last sub-pulse is not fused: its interval merges with the
+    # following prephase events into one (inline) precession
+    assert np.count_nonzero(fused) >= len(rf) - 32
+    assert np.count_nonzero(rf["kind"] == M.OP_RF_FAST) >= 0.97 * len(rf)
     # every readout is one run with an anchor
     runs = ops[ops["kind"] == M.OP_RUN]
     assert len(runs) == 32 and np.all(runs["flags"] & M.F_ANCHOR)
