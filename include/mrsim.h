@@ -148,16 +148,26 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
 /* ---- diagnostics ---------------------------------------------------------------------- */
 
 /* Host-only compile of an event list (no device needed), for inspecting and testing the
- * sequence compiler.  Call once with NULL output arrays to get the sizes (*n_ops, *n_pcls,
- * *n_e1, *n_e2, *n_adc), then again with arrays of those sizes: ops_out receives *n_ops float64
- * device operations (128-byte records), pcls_out 4 doubles per precession class (kx, ky, kz in
- * cycles/m, Δt in s), e1_out / e2_out one interval per relaxation class, demod_out 2 doubles per
- * sample (the factor each sample's spin sum is multiplied by).  Same validation and error codes
- * as mrsim_sequence_load; EINVAL if a given output array is too small. */
+ * sequence compiler.  On input each n_* field is the capacity of the matching array (ignored when
+ * the pointer is NULL); on output it is the size the program needs.  Call once with NULL arrays
+ * to get the sizes, then again with arrays of those sizes.  Same validation and error codes as
+ * mrsim_sequence_load; EINVAL if a given array is too small. */
+typedef struct mrsim_program_dump {
+    void *ops;      /* float64 device operations, 128-byte records */
+    int64_t n_ops;
+    double *pcls;   /* 4 per precession class: kx, ky, kz [cycles/m], Δt [s] */
+    int32_t n_pcls;
+    int32_t n_e1;
+    double *e1;     /* interval [s] per T1 class */
+    double *e2;     /* interval [s] per T2 class */
+    int32_t n_e2;
+    int32_t n_train;
+    double *train;  /* 2 per sub-pulse table entry: cos α, sin α */
+    double *demod;  /* 2 per sample: the factor each sample's spin sum is multiplied by */
+    int64_t n_adc;
+} mrsim_program_dump;
 mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
-                                 void *ops_out, int64_t *n_ops, double *pcls_out, int32_t *n_pcls,
-                                 double *e1_out, int32_t *n_e1, double *e2_out, int32_t *n_e2,
-                                 double *demod_out, int64_t *n_adc);
+                                 mrsim_program_dump *dump);
 
 /* Autotuner: times every launch shape (spins per thread x threads per block) that fits the device
  * on a prefix of the compiled program (about 3e9 spin-steps, at least 256 operations) on `stream`,

@@ -53,6 +53,9 @@ struct mrsim_sequence {
     Compiled host;
     void *d_ops32 = nullptr, *d_ops64 = nullptr;
     double *d_pcls = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_demod = nullptr;
+    float *d_demod32 = nullptr;
+    float *d_train32 = nullptr;
+    double *d_train64 = nullptr;
     Program p32{}, p64{};
 };
 
@@ -149,7 +152,8 @@ struct Launch {
 
 TuneKey tune_key(mrsim_precision prec, const mrsim_phantom *ph, const mrsim_sequence *seq) {
     const Compiled &c = seq->host;
-    return TuneKey{(int64_t)prec, ph->n, (int64_t)c.ops32.size(), c.n_pcls, c.n_e1, c.n_e2, c.n_adc};
+    return TuneKey{(int64_t)prec, ph->n, (int64_t)c.ops32.size(), c.n_pcls, c.n_e1, c.n_e2,
+                   c.n_adc * 4096 + (int64_t)c.train.size()};
 }
 
 // Default launch shape: the largest spins-per-thread that still gives every SM about two blocks.
@@ -306,6 +310,11 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     up(&s->d_e1, s->host.e1);
     up(&s->d_e2, s->host.e2);
     up(&s->d_demod, s->host.demod);
+    std::vector<float> d32(s->host.demod.begin(), s->host.demod.end());
+    up(&s->d_demod32, d32);
+    std::vector<float> t32(s->host.train.begin(), s->host.train.end());
+    up(&s->d_train32, t32);
+    up(&s->d_train64, s->host.train);
     if (st != MRSIM_OK) {
         mrsim_sequence_destroy(s);
         return st;
@@ -319,11 +328,15 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     p.e1 = s->d_e1;
     p.e2 = s->d_e2;
     p.demod = s->d_demod;
+    p.demod32 = s->d_demod32;
+    p.n_train = (int32_t)(s->host.train.size() / 2);
     p.n_adc = s->host.n_adc;
     s->p32 = p;
     s->p32.ops = s->d_ops32;
+    s->p32.train = s->d_train32;
     s->p64 = p;
     s->p64.ops = s->d_ops64;
+    s->p64.train = s->d_train64;
     *out = s;
     return MRSIM_OK;
 }
@@ -341,6 +354,9 @@ void mrsim_sequence_destroy(mrsim_sequence *s) {
     cudaFree(s->d_e1);
     cudaFree(s->d_e2);
     cudaFree(s->d_demod);
+    cudaFree(s->d_demod32);
+    cudaFree(s->d_train32);
+    cudaFree(s->d_train64);
     delete s;
 }
 
@@ -496,32 +512,29 @@ mrsim_status mrsim_simulate(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     return mrsim_simulate_ex(ctx, ph, seq, prec, stream, signal_out, n_adc, nullptr);
 }
 
-mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma, void *ops_out,
-                                 int64_t *n_ops, double *pcls_out, int32_t *n_pcls, double *e1_out, int32_t *n_e1,
-                                 double *e2_out, int32_t *n_e2, double *demod_out, int64_t *n_adc) {
-    if (!n_ops || !n_pcls || !n_e1 || !n_e2 || !n_adc) return MRSIM_EINVAL;
+mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma, mrsim_program_dump *d) {
+    if (!d) return MRSIM_EINVAL;
     Compiled c;
     std::string err;
     int rc = compile_sequence(events, n_events, gamma, c, err);
     if (rc != MRSIM_OK) return (mrsim_status)rc;
-    const int64_t cap_ops = *n_ops;
-    const int32_t cap_p = *n_pcls, cap_1 = *n_e1, cap_2 = *n_e2;
-    const int64_t cap_adc = *n_adc;
-    if (demod_out && c.n_adc > cap_adc) return MRSIM_EINVAL;
-    if (ops_out && (int64_t)c.ops64.size() > cap_ops) return MRSIM_EINVAL;
-    if (pcls_out && c.n_pcls > cap_p) return MRSIM_EINVAL;
-    if (e1_out && c.n_e1 > cap_1) return MRSIM_EINVAL;
-    if (e2_out && c.n_e2 > cap_2) return MRSIM_EINVAL;
-    if (ops_out) std::memcpy(ops_out, c.ops64.data(), c.ops64.size() * sizeof(OpF64));
-    if (pcls_out) std::memcpy(pcls_out, c.pcls.data(), c.pcls.size() * sizeof(double));
-    if (e1_out) std::memcpy(e1_out, c.e1.data(), c.e1.size() * sizeof(double));
-    if (e2_out) std::memcpy(e2_out, c.e2.data(), c.e2.size() * sizeof(double));
-    if (demod_out) std::memcpy(demod_out, c.demod.data(), c.demod.size() * sizeof(double));
-    *n_ops = (int64_t)c.ops64.size();
-    *n_pcls = c.n_pcls;
-    *n_e1 = c.n_e1;
-    *n_e2 = c.n_e2;
-    *n_adc = c.n_adc;
+    const int64_t n_train = (int64_t)c.train.size() / 2;
+    if ((d->ops && (int64_t)c.ops64.size() > d->n_ops) || (d->pcls && c.n_pcls > d->n_pcls) ||
+        (d->e1 && c.n_e1 > d->n_e1) || (d->e2 && c.n_e2 > d->n_e2) || (d->train && n_train > d->n_train) ||
+        (d->demod && c.n_adc > d->n_adc))
+        return MRSIM_EINVAL;
+    if (d->ops) std::memcpy(d->ops, c.ops64.data(), c.ops64.size() * sizeof(OpF64));
+    if (d->pcls) std::memcpy(d->pcls, c.pcls.data(), c.pcls.size() * sizeof(double));
+    if (d->e1) std::memcpy(d->e1, c.e1.data(), c.e1.size() * sizeof(double));
+    if (d->e2) std::memcpy(d->e2, c.e2.data(), c.e2.size() * sizeof(double));
+    if (d->train) std::memcpy(d->train, c.train.data(), c.train.size() * sizeof(double));
+    if (d->demod) std::memcpy(d->demod, c.demod.data(), c.demod.size() * sizeof(double));
+    d->n_ops = (int64_t)c.ops64.size();
+    d->n_pcls = c.n_pcls;
+    d->n_e1 = c.n_e1;
+    d->n_e2 = c.n_e2;
+    d->n_train = (int32_t)n_train;
+    d->n_adc = c.n_adc;
     return MRSIM_OK;
 }
 

@@ -408,6 +408,58 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         }
         }
     }
+    // ---- sub-pulse trains: runs of fast sub-pulses become one operation over a table of
+    // (cos α, sin α) pairs; identical trains (e.g. the same shaped pulse every TR) share entries.
+    {
+        std::vector<OpF32> o32;
+        std::vector<OpF64> o64;
+        o32.reserve(out.ops32.size());
+        o64.reserve(out.ops64.size());
+        std::map<std::vector<uint64_t>, int> seen;
+        for (size_t i = 0; i < out.ops32.size();) {
+            size_t e = i;
+            while (e < out.ops32.size() && out.ops32[e].kind == OP_RF_FAST && (int64_t)(e - i) < RUN_MAX) ++e;
+            const size_t n = e - i;
+            if (n >= 2) {
+                std::vector<uint64_t> key;
+                key.reserve(2 * n);
+                for (size_t q = i; q < e; ++q) {
+                    key.push_back(bits(out.ops64[q].f[0]));
+                    key.push_back(bits(out.ops64[q].f[1]));
+                }
+                auto it = seen.find(key);
+                int off = -1;
+                if (it != seen.end()) {
+                    off = it->second;
+                } else if ((int64_t)(out.train.size() / 2 + n) <= TRAIN_TABLE_MAX) {
+                    off = (int)(out.train.size() / 2);
+                    for (size_t q = i; q < e; ++q) {
+                        out.train.push_back(out.ops64[q].f[0]);
+                        out.train.push_back(out.ops64[q].f[1]);
+                    }
+                    seen[key] = off;
+                }
+                if (off >= 0) {
+                    OpF32 a = out.ops32[i];
+                    OpF64 b = out.ops64[i];
+                    a.kind = b.kind = OP_RF_TRAIN;
+                    a.n = b.n = (int32_t)n;
+                    a.adc0 = b.adc0 = off;
+                    o32.push_back(a);
+                    o64.push_back(b);
+                    i = e;
+                    continue;
+                }
+            }
+            for (size_t q = i; q < std::max(e, i + 1); ++q) {
+                o32.push_back(out.ops32[q]);
+                o64.push_back(out.ops64[q]);
+            }
+            i = std::max(e, i + 1);
+        }
+        out.ops32.swap(o32);
+        out.ops64.swap(o64);
+    }
     if (out.n_adc > (int64_t)INT32_MAX) {
         err = "too many ADC samples";
         return MRSIM_EINVAL;

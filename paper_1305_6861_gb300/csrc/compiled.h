@@ -16,6 +16,7 @@ struct Compiled {
     std::vector<double> e1;     // τ per T1 class
     std::vector<double> e2;     // Δt per T2 class
     std::vector<double> demod;  // 2 per sample
+    std::vector<double> train;  // 2 per sub-pulse table entry: cos α, sin α
     int n_pcls = 0, n_e1 = 0, n_e2 = 0;
     int64_t n_adc = 0;
 };

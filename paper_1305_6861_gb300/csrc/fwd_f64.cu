@@ -32,7 +32,7 @@ int fwd_regs(bool fp64, int k) {
 }
 
 size_t fwd_smem_bytes(bool fp64, const Program &p, int k, int threads) {
-    return dev::smem_layout(fp64, p.n_pcls, p.n_e1, p.n_e2, k * threads, threads / 32).total;
+    return dev::smem_layout(fp64, p.n_pcls, p.n_e1, p.n_e2, p.n_train, k * threads, threads / 32).total;
 }
 
 // Validate and pack the seven float64 spin arrays into the parameter block (see internal.h).

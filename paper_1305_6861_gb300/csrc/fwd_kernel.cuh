@@ -75,9 +75,43 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t pari
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s for one 4 KB chunk: only a fault takes that long
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int RED_STRIDE = SAMPLE_WINDOW + 16;  // per-component row of the reduction window
+constexpr int RED_STRIDE = SAMPLE_WINDOW_F64 + 16;  // float64: per-warp, per-component window row
+constexpr int WIN_STRIDE = SAMPLE_WINDOW_F32 + 16;  // float32: block-wide window, per component
+constexpr int TILE_STRIDE = 36;                     // float32: row of a warp's 32x32 transpose tile
 
-// Butterfly that leaves lane l with the warp-wide sum of v[l] (32 values per lane in, 1 out).
+__device__ __forceinline__ void red_shared_add(float *p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(su32(p)), "f"(v) : "memory");
+}
+
+// Shared-memory transpose that leaves lane l with the warp-wide sum of v[l]: every lane writes
+// its 32 values down tile column `lane` (32 conflict-free stores that nothing waits on), reads
+// tile row l as 8 conflict-free 16-byte loads and adds the 32 values as a tree: 71 instructions
+// instead of the 124 of a shuffle butterfly.
+__device__ __forceinline__ float tile_reduce32(float (&v)[32], int lane, float *tile) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) tile[i * TILE_STRIDE + lane] = v[i];
+    __syncwarp();
+    float a[32];
+    const float4 *row = reinterpret_cast<const float4 *>(tile + lane * TILE_STRIDE);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 t = row[q];
+        a[4 * q] = t.x;
+        a[4 * q + 1] = t.y;
+        a[4 * q + 2] = t.z;
+        a[4 * q + 3] = t.w;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+#pragma unroll
+        for (int i = 0; i < w; ++i) a[i] += a[i + w];
+    }
+    return a[0];
+}
+
+// Butterfly that leaves lane l with the warp-wide sum of v[l] (32 values per lane in, 1 out);
+// used by the float64 path.
 template <typename R>
 __device__ __forceinline__ R transpose_reduce32(R (&v)[32], int lane) {
 #pragma unroll
@@ -153,11 +187,30 @@ __device__ __noinline__ void flush_window(const R *red, const double *demod, dou
     __syncthreads();
 }
 
+// float32: multiply the block-wide window by the float32 demodulation factors, add it to the
+// global signal with float64 atomics and clear it.  Every thread of the block must call it.
+static __device__ __noinline__ void flush_window_f32(float *win, const float *demod32, double *signal, int win_base,
+                                             int win_end, int tid, int nthr) {
+    __syncthreads();
+    const int cnt = win_end - win_base;
+    for (int s = tid; s < cnt; s += nthr) {
+        const float re = win[s], im = win[WIN_STRIDE + s];
+        win[s] = 0.0f;
+        win[WIN_STRIDE + s] = 0.0f;
+        const int64_t j = (int64_t)win_base + s;
+        const float2 d = reinterpret_cast<const float2 *>(demod32)[j];
+        atomicAdd(signal + 2 * j, (double)(re * d.x - im * d.y));
+        atomicAdd(signal + 2 * j + 1, (double)(re * d.y + im * d.x));
+    }
+    __syncthreads();
+}
+
 template <typename R, int K>
 struct Spins {
     using Op = typename std::conditional<std::is_same<R, float>::value, OpF32, OpF64>::type;
     using V = typename V2<R>::T;
     static constexpr bool F64 = std::is_same<R, double>::value;
+    static constexpr int WIN = F64 ? SAMPLE_WINDOW_F64 : SAMPLE_WINDOW_F32;
 
     R u[K], v[K], mz[K], rho[K];  // transverse part in the pulse frame, longitudinal, M0
     R wr[K], wi[K];               // cached phasor class
@@ -166,12 +219,16 @@ struct Spins {
 
     // shared-memory views and block geometry
     const V *cw;
+    const V *train;  // sub-pulse table (cos α, sin α)
     const R *ce1, *ce2, *prm;
-    R *red;
+    R *red;       // float64: per-warp window rows
+    float *tile;  // float32: this warp's transpose tile
+    float *win;   // float32: block-wide window
     int S, nthr, tid, lane, warp, nwarp;
     int64_t base, np, n_spins;
     const double *params;
     const double *demod;
+    const float *demod32;
     double *signal;
 
     __device__ __forceinline__ int li(int i) const { return i * nthr + tid; }
@@ -294,12 +351,15 @@ struct Spins {
     __device__ __forceinline__ R *red_row(int comp) { return red + warp * 2 * RED_STRIDE + comp * RED_STRIDE; }
 
     __device__ __forceinline__ void flush() {
-        flush_window(red, demod, signal, win_base, win_end, tid, nthr, nwarp);
+        if constexpr (F64)
+            flush_window(red, demod, signal, win_base, win_end, tid, nthr, nwarp);
+        else
+            flush_window_f32(win, demod32, signal, win_base, win_end, tid, nthr);
         win_base = win_end;
     }
 
     __device__ __forceinline__ void sample1(int j) {
-        if (j + 1 - win_base > SAMPLE_WINDOW) flush();
+        if (j + 1 - win_base > WIN) flush();
         R sx = tree_sum<R, K>(u), sy = tree_sum<R, K>(v);
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
@@ -307,10 +367,29 @@ struct Spins {
             sy += __shfl_xor_sync(FULL, sy, off);
         }
         if (lane == 0) {
-            red_row(0)[j - win_base] = sx;
-            red_row(1)[j - win_base] = sy;
+            if constexpr (F64) {
+                red_row(0)[j - win_base] = sx;
+                red_row(1)[j - win_base] = sy;
+            } else {
+                red_shared_add(win + (j - win_base), sx);
+                red_shared_add(win + WIN_STRIDE + (j - win_base), sy);
+            }
         }
         win_end = j + 1;
+    }
+
+    // lane l holds the warp total of value l (sample l/2, component l%2) of a 16-sample tile
+    __device__ __forceinline__ R warp_tile_total(R (&vv)[32]) {
+        if constexpr (F64)
+            return transpose_reduce32(vv, lane);
+        else
+            return tile_reduce32(vv, lane, tile);
+    }
+    __device__ __forceinline__ void store_tile(int slot, R tot) {
+        if constexpr (F64)
+            red_row(lane & 1)[slot + (lane >> 1)] = tot;
+        else
+            red_shared_add(win + (lane & 1) * WIN_STRIDE + slot + (lane >> 1), tot);
     }
 
     // one sample step of a run: rotate by the cached class, return the thread's sums
@@ -332,16 +411,14 @@ struct Spins {
                 av[i] = v[i];
             }
         }
-        if (j0 + n - win_base > SAMPLE_WINDOW) flush();
-        R *r0 = red_row(0) + (j0 - win_base);
-        R *r1 = red_row(1) + (j0 - win_base);
+        if (j0 + n - win_base > WIN) flush();
+        const int slot0 = j0 - win_base;
         int t0 = 0;
         for (; t0 + 16 <= n; t0 += 16) {  // full tiles: no guards
             R vv[32];
 #pragma unroll
             for (int t = 0; t < 16; ++t) run_step(vv[2 * t], vv[2 * t + 1]);
-            const R tot = transpose_reduce32(vv, lane);
-            ((lane & 1) ? r1 : r0)[t0 + (lane >> 1)] = tot;
+            store_tile(slot0 + t0, warp_tile_total(vv));
         }
         if (t0 < n) {  // ragged tail
             const int tt = n - t0;
@@ -355,8 +432,8 @@ struct Spins {
                     vv[2 * t + 1] = (R)0;
                 }
             }
-            const R tot = transpose_reduce32(vv, lane);
-            if (lane < 2 * tt) ((lane & 1) ? r1 : r0)[t0 + (lane >> 1)] = tot;
+            const R tot = warp_tile_total(vv);
+            if (lane < 2 * tt) store_tile(slot0 + t0, tot);
         }
         win_end = j0 + n;
         if (anchor) {
@@ -369,8 +446,23 @@ struct Spins {
         }
     }
 
+    // n sub-pulses of a shaped pulse (Eq. 3.23): lazy T1 with the cached class, the pulse-frame
+    // turn with table entry i, precession by the cached class
+    __device__ __forceinline__ void train_run(int off, int n) {
+#pragma unroll 2
+        for (int i = 0; i < n; ++i) {
+            const V cs = train[off + i];
+            t1_cached();
+            rf_turn(cs.x, cs.y);
+            rot_w();
+        }
+    }
+
     __device__ __forceinline__ void exec(const Op &op) {
         switch (op.kind) {
+        case OP_RF_TRAIN:
+            train_run(op.adc0, op.n);
+            break;
         case OP_RF_FAST:  // sub-pulse of a shaped pulse: every cache already holds the right class
             t1_cached();
             rf_turn((R)op.f[0], (R)op.f[1]);
@@ -407,10 +499,11 @@ struct Spins {
 
 // Shared-memory layout (bytes) of one block; identical on host and device.
 struct SmemLayout {
-    size_t ops, bars, flag, cw, ce1, ce2, prm, red, total;
+    size_t ops, bars, flag, cw, ce1, ce2, prm, train, red, total;
 };
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-__host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1, int n_e2, int S, int nwarp) {
+__host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1, int n_e2, int n_train, int S,
+                                                  int nwarp) {
     SmemLayout L;
     const size_t rs = f64 ? 8 : 4;
     const size_t opb = f64 ? sizeof(OpF64) * 2 * CHUNK_F64 : sizeof(OpF32) * 2 * CHUNK_F32;
@@ -430,14 +523,19 @@ __host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1
     o = align_up(o + (size_t)n_e2 * S * rs, 16);
     L.prm = o;
     o = align_up(o + (size_t)nprm * S * rs, 16);
+    L.train = o;
+    o = align_up(o + (size_t)n_train * 2 * rs, 16);
     L.red = o;
-    o = align_up(o + (size_t)nwarp * 2 * RED_STRIDE * rs, 16);
+    if (f64)
+        o = align_up(o + (size_t)nwarp * 2 * RED_STRIDE * rs, 16);
+    else  // transpose tiles, then the block-wide window
+        o = align_up(o + (size_t)nwarp * 32 * TILE_STRIDE * 4 + (size_t)2 * WIN_STRIDE * 4, 16);
     L.total = o;
     return L;
 }
 
 template <typename R, int K, int MAXT>
-__global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
     using SP = Spins<R, K>;
     using Op = typename SP::Op;
     using V = typename SP::V;
@@ -454,7 +552,7 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
     sp.S = K * sp.nthr;
     const int S = sp.S;
     const Program &P = a.prog;
-    const SmemLayout L = smem_layout(F64, P.n_pcls, P.n_e1, P.n_e2, S, sp.nwarp);
+    const SmemLayout L = smem_layout(F64, P.n_pcls, P.n_e1, P.n_e2, P.n_train, S, sp.nwarp);
     Op *opbuf = reinterpret_cast<Op *>(smem + L.ops);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.flag);
@@ -463,11 +561,22 @@ __global__ void __launch_bounds__(MAXT) fwd_kernel(const FwdArgs a) {
     R *ce2 = reinterpret_cast<R *>(smem + L.ce2);
     R *prm = reinterpret_cast<R *>(smem + L.prm);
     sp.cw = cw;
+    {
+        V *tr = reinterpret_cast<V *>(smem + L.train);
+        const V *gtr = reinterpret_cast<const V *>(P.train);
+        for (int q = sp.tid; q < P.n_train; q += sp.nthr) tr[q] = gtr[q];
+        sp.train = tr;
+    }
     sp.ce1 = ce1;
     sp.ce2 = ce2;
     sp.prm = prm;
     sp.red = reinterpret_cast<R *>(smem + L.red);
+    sp.tile = reinterpret_cast<float *>(smem + L.red) + sp.warp * 32 * TILE_STRIDE;
+    sp.win = reinterpret_cast<float *>(smem + L.red) + sp.nwarp * 32 * TILE_STRIDE;
+    if constexpr (!F64)
+        for (int q = sp.tid; q < 2 * WIN_STRIDE; q += sp.nthr) sp.win[q] = 0.0f;
     sp.demod = P.demod;
+    sp.demod32 = P.demod32;
     sp.signal = a.signal;
     sp.params = a.params;
     sp.win_base = 0;
@@ -599,7 +708,8 @@ int launch_one(const FwdArgs &a, int threads, void *stream) {
     if (threads <= 0 || threads > MAXT || threads % 32) return (int)cudaErrorInvalidValue;
     if (a.n_spins <= 0) return 0;
     const int S = K * threads;
-    const SmemLayout L = smem_layout(std::is_same<R, double>::value, a.prog.n_pcls, a.prog.n_e1, a.prog.n_e2, S, threads / 32);
+    const SmemLayout L = smem_layout(std::is_same<R, double>::value, a.prog.n_pcls, a.prog.n_e1, a.prog.n_e2,
+                                     a.prog.n_train, S, threads / 32);
     auto kern = fwd_kernel<R, K, MAXT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return (int)e;

@@ -35,6 +35,7 @@ enum OpKind : uint8_t {
     OP_RF_FAST = 2,  // sub-pulse of a train: lazy T1 with the cached class, rotation, cached precession
     OP_PREC = 3,     // precession + T2 over one interval: cached class or inline; [single sample]
     OP_RUN = 4,      // n consecutive samples, each after one precession by the cached class
+    OP_RF_TRAIN = 5, // n fast sub-pulses whose (cos α, sin α) are train-table entries adc0 .. adc0+n-1
 };
 
 enum OpFlags : uint16_t {
@@ -86,9 +87,14 @@ static_assert(sizeof(OpF64) == 128, "OpF64 must be 128 bytes");
 constexpr int MAX_PCLS = 8;
 constexpr int MAX_E1CLS = 4;
 constexpr int MAX_E2CLS = 4;
-// Samples held per block before they are summed across warps and added to global memory.
-constexpr int SAMPLE_WINDOW = 256;
-constexpr int RUN_MAX = SAMPLE_WINDOW;
+// Samples held per block before they are added to global memory: float32 keeps one block-wide
+// window (warps add into it with shared-memory atomics), float64 one row per warp.
+constexpr int SAMPLE_WINDOW_F32 = 1024;
+constexpr int SAMPLE_WINDOW_F64 = 256;
+// Longest sample run of one operation (must fit either window).
+constexpr int RUN_MAX = 256;
+// Entries (cos α, sin α) of the de-duplicated sub-pulse table held in shared memory.
+constexpr int TRAIN_TABLE_MAX = 2048;
 // Ops staged in shared memory per bulk copy (two buffers).
 constexpr int CHUNK_F32 = 64;
 constexpr int CHUNK_F64 = 32;
@@ -106,6 +112,9 @@ struct Program {
     const double *e1;    // τ [s] per class
     const double *e2;    // Δt [s] per class
     const double *demod; // 2 per sample: exp(-j(adc_phase - ψ)) with ψ the frame at the sample
+    const float *demod32;  // the same factors rounded to float32 (float32 path)
+    const void *train;     // sub-pulse table: n_train (cos α, sin α) pairs, float2 or double2
+    int32_t n_train;
     int64_t n_adc;
 };
 

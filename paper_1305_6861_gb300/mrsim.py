@@ -52,6 +52,15 @@ class MrsimError(RuntimeError):
         self.status = Status(status)
 
 
+class ProgramDump(ctypes.Structure):
+    _fields_ = [
+        ("ops", ctypes.c_void_p), ("n_ops", ctypes.c_int64),
+        ("pcls", ctypes.c_void_p), ("n_pcls", ctypes.c_int32), ("n_e1", ctypes.c_int32),
+        ("e1", ctypes.c_void_p), ("e2", ctypes.c_void_p), ("n_e2", ctypes.c_int32), ("n_train", ctypes.c_int32),
+        ("train", ctypes.c_void_p), ("demod", ctypes.c_void_p), ("n_adc", ctypes.c_int64),
+    ]
+
+
 class Options(ctypes.Structure):
     _fields_ = [
         ("spins_per_thread", ctypes.c_int32),
@@ -93,7 +102,7 @@ def lib():
             "mrsim_simulate": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
             "mrsim_simulate_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64, P(Options)]),
             "mrsim_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, P(Options)]),
-            "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, vp, P(i64), vp, P(i32), vp, P(i32), vp, P(i32), vp, P(i64)]),
+            "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -240,32 +249,31 @@ def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP3
 
 
 def debug_compile(events, gamma_hz_per_t: float):
-    """Host-only compile of an event list (no GPU needed): returns the float64 device program
-    (op records as a structured array), its class tables and the per-sample demodulation
-    factors (complex, one per sample)."""
+    """Host-only compile of an event list (no GPU needed).  Returns a dict with the float64 device
+    program (op records), the class tables, the sub-pulse table and the per-sample demodulation
+    factors (complex)."""
     L = lib()
     ev = np.ascontiguousarray(events)
     if ev.dtype != EVENT_DTYPE:
         ev = ev.astype(EVENT_DTYPE)
-    n_ops = ctypes.c_int64()
-    n_p, n_1, n_2 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    n_adc = ctypes.c_int64()
-    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), None, ctypes.byref(n_ops), None,
-                               ctypes.byref(n_p), None, ctypes.byref(n_1), None, ctypes.byref(n_2), None,
-                               ctypes.byref(n_adc))
+    d = ProgramDump()
+    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(d))
     if rc != 0:
         raise MrsimError(rc, "mrsim_debug_compile failed")
-    ops = np.zeros(n_ops.value, dtype=OP64_DTYPE)
-    pcls = np.zeros(4 * n_p.value)
-    e1 = np.zeros(n_1.value)
-    e2 = np.zeros(n_2.value)
-    demod = np.zeros(n_adc.value, dtype=np.complex128)
-    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), _ptr(ops), ctypes.byref(n_ops),
-                               _ptr(pcls), ctypes.byref(n_p), _ptr(e1), ctypes.byref(n_1), _ptr(e2), ctypes.byref(n_2),
-                               _ptr(demod), ctypes.byref(n_adc))
+    out = {
+        "ops": np.zeros(d.n_ops, dtype=OP64_DTYPE),
+        "pcls": np.zeros((d.n_pcls, 4)),
+        "e1": np.zeros(d.n_e1),
+        "e2": np.zeros(d.n_e2),
+        "train": np.zeros((d.n_train, 2)),
+        "demod": np.zeros(d.n_adc, dtype=np.complex128),
+    }
+    for f in ("ops", "pcls", "e1", "e2", "train", "demod"):
+        setattr(d, f, out[f].ctypes.data)
+    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(d))
     if rc != 0:
         raise MrsimError(rc, "mrsim_debug_compile failed")
-    return ops, pcls.reshape(-1, 4), e1, e2, demod
+    return out
 
 
 # Layout of one float64 device operation (128 bytes), for diagnostics.
@@ -274,7 +282,7 @@ OP64_DTYPE = np.dtype(
      ("ecls", "<i2"), ("acls", "<i2"), ("rsv1", "<i2"), ("rsv2", "<i4"), ("f", "<f8", (13,))]
 )
 assert OP64_DTYPE.itemsize == 128
-OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN = 0, 1, 2, 3, 4
+OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN, OP_RF_TRAIN = 0, 1, 2, 3, 4, 5
 F_ADC, F_PCLS, F_PLOAD, F_INLINE, F_E1CLS, F_E1LOAD, F_E1INL, F_E2CLS, F_ANCHOR, F_FRAME = (
     1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
 F_KX, F_KY, F_KZ, F_DT = 1024, 2048, 4096, 8192

@@ -15,7 +15,8 @@ from paper_1305_6861_gb300 import mrsim as M
 
 
 def interpret(events, gamma, ph, state_in=None):
-    ops, pcls, e1tab, e2tab, demod = M.debug_compile(events, gamma)
+    prog = M.debug_compile(events, gamma)
+    ops, pcls, e1tab, e2tab, demod, train = (prog[k] for k in ("ops", "pcls", "e1", "e2", "demod", "train"))
     n_adc = demod.shape[0]
     x, y, z, rho = ph.x, ph.y, ph.z, ph.rho
     df = ph.dw / (2 * math.pi)
@@ -61,6 +62,15 @@ def interpret(events, gamma, ph, state_in=None):
 
     for op in ops:
         k, fl, f = op["kind"], op["flags"], op["f"]
+        if k == M.OP_RF_TRAIN:
+            w = wc
+            for ca, sa in train[op["adc0"] : op["adc0"] + op["n"]]:
+                mz = mz - e1c * (mz - rho)
+                v = m.imag
+                nv = ca * v + sa * mz
+                mz = ca * mz - sa * v
+                m = (m.real + 1j * nv) * w
+            continue
         if k in (M.OP_RF, M.OP_RF_FAST):
             if fl & M.F_FRAME:
                 d = math.atan2(f[3], f[2])

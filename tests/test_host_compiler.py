@@ -39,10 +39,10 @@ def test_status_strings(mrsim_lib):
 def _compile_rc(events, gamma=W.GAMMA_BAR):
     L = __import__("paper_1305_6861_gb300.mrsim", fromlist=["x"]).lib()
     ev = np.ascontiguousarray(events, dtype=W.EVENT_DTYPE)
-    n = [ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()]
-    return L.mrsim_debug_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), float(gamma), None,
-                                 ctypes.byref(n[0]), None, ctypes.byref(n[1]), None, ctypes.byref(n[2]), None,
-                                 ctypes.byref(n[3]), None, ctypes.byref(n[4]))
+    from paper_1305_6861_gb300 import mrsim as M
+
+    d = M.ProgramDump()
+    return L.mrsim_debug_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), float(gamma), ctypes.byref(d))
 
 
 @pytest.mark.parametrize("field,value", [("dt", -1e-3), ("gx", np.nan), ("rf_flip", np.inf), ("adc", 2),
@@ -76,6 +76,8 @@ def _check_structure(events, ops, n_adc):
     assert ops[-1]["kind"] == M.OP_END
     seen = []
     for op in ops:
+        if op["kind"] == M.OP_RF_TRAIN:
+            continue
         if op["kind"] == M.OP_RUN:
             assert 1 <= op["n"] <= 256
             seen.extend(range(op["adc0"], op["adc0"] + op["n"]))
@@ -120,16 +122,17 @@ def test_class_tables_bounded_and_used(mrsim_lib):
     from paper_1305_6861_gb300 import mrsim as M
 
     w = W.config2(n=32, iso=2)
-    ops, pcls, e1, e2, demod = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
-    assert len(pcls) <= 8 and len(e1) <= 4 and len(e2) <= 4
-    # the shaped-pulse sub-pulse trains are fused RF + class precession operations, and all but
-    # the first two sub-pulses of each train run as the branch-free fast codelet
-    rf = ops[(ops["kind"] == M.OP_RF) | (ops["kind"] == M.OP_RF_FAST)]
-    fused = (rf["kind"] == M.OP_RF_FAST) | ((rf["flags"] & M.F_PCLS) > 0)
-    # per TR only the excitation's last sub-pulse is not fused: its interval merges with the
-    # following prephase events into one (inline) precession
-    assert np.count_nonzero(fused) >= len(rf) - 32
-    assert np.count_nonzero(rf["kind"] == M.OP_RF_FAST) >= 0.97 * len(rf)
+    prog = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
+    ops = prog["ops"]
+    assert len(prog["pcls"]) <= 8 and len(prog["e1"]) <= 4 and len(prog["e2"]) <= 4
+    # every shaped pulse is a few general RF operations (frame turn, cache loads, the unfused last
+    # excitation sub-pulse) plus one train operation over the sub-pulse table; the two distinct
+    # pulse shapes (90° and 180°) are stored once and shared by all TRs
+    trains = ops[ops["kind"] == M.OP_RF_TRAIN]
+    assert len(trains) == 2 * 32
+    assert np.count_nonzero(ops["kind"] == M.OP_RF) <= 6 * 32
+    assert len(prog["train"]) == sum(sorted(set(zip(trains["adc0"], trains["n"])), key=lambda t: t[0])[i][1] for i in range(2))
+    assert len(prog["train"]) < 2 * 128
     # every readout is one run with an anchor
     runs = ops[ops["kind"] == M.OP_RUN]
     assert len(runs) == 32 and np.all(runs["flags"] & M.F_ANCHOR)
