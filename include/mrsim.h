@@ -145,6 +145,35 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
                                mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc,
                                const mrsim_options *opt);
 
+/* ---- batches: many phantoms with their own sequences in one persistent launch ---------- */
+
+/* A batch borrows n phantom/sequence pairs (they must outlive it) and one device signal buffer
+ * per pair (2*num_adc doubles each).  The work is split into tiles of spins (the paper's spin
+ * blocks, §5.3.2); one persistent kernel, sized to the device (SMs x resident blocks), lets every
+ * block pop (phantom, tile) items from a work queue, longest sequences first, until it is empty.
+ * Batches of uneven spin counts and sequence lengths therefore keep every SM busy. */
+typedef struct mrsim_batch mrsim_batch;
+mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
+                                const mrsim_sequence *const *seqs, mrsim_precision prec,
+                                double *const *signals_out, mrsim_batch **out);
+int64_t mrsim_batch_num_items(const mrsim_batch *b);
+/* Times every launch shape on a prefix of all programs (about 1e10 spin-steps in total) and keeps
+ * the fastest for this batch; returns it in best (other fields zeroed).  Synchronises `stream`. */
+mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *best);
+/* Sets the launch shape explicitly (EINVAL / EUNSUPPORTED as for mrsim_simulate_ex). */
+mrsim_status mrsim_batch_set_shape(mrsim_batch *b, int32_t spins_per_thread, int32_t threads_per_block);
+/* Enqueues on `stream`: zero the signal buffers, reset the work queue, run the persistent kernel.
+ * Asynchronous; may itself be captured into a CUDA graph by the caller. */
+mrsim_status mrsim_batch_launch(mrsim_batch *b, void *stream);
+/* Same work as one CUDA graph: captured on the first call (and again after the shape changes),
+ * replayed on `stream` afterwards. */
+mrsim_status mrsim_batch_launch_graph(mrsim_batch *b, void *stream);
+void mrsim_batch_destroy(mrsim_batch *b);
+/* One-shot convenience: create, launch, synchronise `stream`, destroy. */
+mrsim_status mrsim_simulate_batch(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
+                                  const mrsim_sequence *const *seqs, mrsim_precision prec, void *stream,
+                                  double *const *signals_out);
+
 /* ---- diagnostics ---------------------------------------------------------------------- */
 
 /* Host-only compile of an event list (no device needed), for inspecting and testing the

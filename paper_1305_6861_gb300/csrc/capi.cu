@@ -59,6 +59,23 @@ struct mrsim_sequence {
     Program p32{}, p64{};
 };
 
+struct mrsim_batch {
+    mrsim_ctx *ctx = nullptr;
+    mrsim_precision prec = MRSIM_FP32;
+    std::vector<const mrsim_phantom *> ph;
+    std::vector<const mrsim_sequence *> seq;
+    std::vector<FwdArgs> descs;
+    std::vector<BatchItem> items;
+    FwdArgs *d_descs = nullptr;
+    BatchItem *d_items = nullptr;
+    int *d_head = nullptr;  // work-queue counter
+    int k = 0, threads = 0, grid = 0;
+    size_t smem = 0;
+    int64_t spin_steps = 0;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t graph = nullptr;
+};
+
 namespace {
 
 mrsim_status fail(mrsim_ctx *ctx, mrsim_status st, const std::string &msg) {
@@ -536,6 +553,275 @@ mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, do
     d->n_train = (int32_t)n_train;
     d->n_adc = c.n_adc;
     return MRSIM_OK;
+}
+
+namespace {
+
+// Work items for tiles of S spins, longest sequences first (longest-processing-time order), and
+// the launch geometry of the persistent kernel.
+mrsim_status batch_layout(mrsim_batch *b, int k, int threads) {
+    mrsim_ctx *ctx = b->ctx;
+    const bool fp64 = b->prec == MRSIM_FP64;
+    const int64_t S = (int64_t)k * threads;
+    std::vector<int> order(b->descs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->seq[x]->n_events > b->seq[y]->n_events; });
+    std::vector<BatchItem> items;
+    size_t smem = 0;
+    for (int d : order) {
+        const int64_t tiles = (b->descs[d].n_spins + S - 1) / S;
+        if (tiles > INT32_MAX) return fail(ctx, MRSIM_EINVAL, "too many tiles");
+        for (int64_t t = 0; t < tiles; ++t) items.push_back(BatchItem{d, (int32_t)t});
+        smem = std::max(smem, fwd_smem_bytes(fp64, b->descs[d].prog, k, threads));
+    }
+    if (smem > (size_t)ctx->max_smem_optin) return fail(ctx, MRSIM_EUNSUPPORTED, "launch shape exceeds shared memory");
+    const int per_sm = batch_blocks_per_sm(fp64, k, threads, smem);
+    if (per_sm <= 0) return fail(ctx, MRSIM_EUNSUPPORTED, "launch shape cannot be resident");
+    if (items.size() > (size_t)INT32_MAX) return fail(ctx, MRSIM_EINVAL, "too many work items");
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    if (!items.empty()) {
+        CK(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)), "cudaMalloc batch items");
+        CK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice), "upload items");
+    }
+    b->items.swap(items);
+    b->k = k;
+    b->threads = threads;
+    b->smem = smem;
+    b->grid = (int)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, std::max<size_t>(b->items.size(), 1));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return MRSIM_OK;
+}
+
+// zero outputs, reset the queue, run the persistent kernel (all asynchronous on `st`)
+mrsim_status batch_enqueue(mrsim_batch *b, const FwdArgs *d_descs, cudaStream_t st) {
+    mrsim_ctx *ctx = b->ctx;
+    if (b->items.empty()) return MRSIM_OK;
+    int rc = zero_signals(d_descs, (int)b->descs.size(), st);
+    if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "zero batch signals");
+    CK(cudaMemsetAsync(b->d_head, 0, sizeof(int), st), "reset work queue");
+    BatchArgs a{};
+    a.descs = d_descs;
+    a.items = b->d_items;
+    a.n_items = (int32_t)b->items.size();
+    a.head = b->d_head;
+    rc = launch_batch(b->prec == MRSIM_FP64, a, b->k, b->threads, b->smem, b->grid, st);
+    if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch batch kernel");
+    return MRSIM_OK;
+}
+
+}  // namespace
+
+mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
+                                const mrsim_sequence *const *seqs, mrsim_precision prec, double *const *signals_out,
+                                mrsim_batch **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    if (n < 0 || (n > 0 && (!phantoms || !seqs || !signals_out)))
+        return fail(ctx, MRSIM_EINVAL, "invalid batch arrays");
+    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    cudaSetDevice(ctx->device);
+    mrsim_batch *b = new (std::nothrow) mrsim_batch();
+    if (!b) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    b->ctx = ctx;
+    b->prec = prec;
+    int64_t max_n = 0;
+    for (int i = 0; i < n; ++i) {
+        const mrsim_phantom *p = phantoms[i];
+        const mrsim_sequence *q = seqs[i];
+        if (!p || !q || p->ctx != ctx || q->ctx != ctx) {
+            delete b;
+            return fail(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": NULL handle or another context");
+        }
+        if (q->host.n_adc > 0 && !is_device_ptr(signals_out[i])) {
+            delete b;
+            return fail(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": signal buffer must be device memory");
+        }
+        FwdArgs a{};
+        a.prog = prec == MRSIM_FP64 ? q->p64 : q->p32;
+        a.params = p->params;
+        a.n_spins = p->n;
+        a.n_pad = p->n_pad;
+        a.signal = signals_out[i];
+        a.status = ctx->d_status;
+        b->ph.push_back(p);
+        b->seq.push_back(q);
+        b->descs.push_back(a);
+        b->spin_steps += p->n * q->n_events;
+        max_n = std::max(max_n, p->n);
+    }
+    auto bail = [&](mrsim_status st) {
+        mrsim_batch_destroy(b);
+        return st;
+    };
+    if (n > 0) {
+        cudaError_t e = cudaMalloc(&b->d_descs, b->descs.size() * sizeof(FwdArgs));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_descs, b->descs.data(), b->descs.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(int));
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "batch descriptors"));
+    }
+    // default shape: the single-phantom heuristic for the largest phantom, shrunk until it fits
+    Launch L = choose_launch(ctx, prec == MRSIM_FP64, max_n);
+    mrsim_status st = batch_layout(b, L.k, L.threads);
+    for (int t : {64, 32}) {
+        if (st != MRSIM_EUNSUPPORTED) break;
+        st = batch_layout(b, 1, t);
+    }
+    if (st != MRSIM_OK) return bail(st);
+    *out = b;
+    return MRSIM_OK;
+}
+
+int64_t mrsim_batch_num_items(const mrsim_batch *b) { return b ? (int64_t)b->items.size() : -1; }
+
+mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *best) {
+    if (!b) return MRSIM_EINVAL;
+    mrsim_ctx *ctx = b->ctx;
+    if (!best) return fail(ctx, MRSIM_EINVAL, "NULL best");
+    std::memset(best, 0, sizeof *best);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = b->prec == MRSIM_FP64;
+    if (b->descs.empty()) return MRSIM_OK;
+    // time a prefix of every program: the same fraction of each, about 5e9 spin-steps in all
+    // (warm-up launches run an 8-operation prefix so that each kernel is loaded before timing)
+    std::vector<FwdArgs> trunc = b->descs, warm = b->descs;
+    const double frac = std::min(1.0, 5e9 / (double)std::max<int64_t>(b->spin_steps, 1));
+    for (size_t i = 0; i < trunc.size(); ++i) {
+        FwdArgs &a = trunc[i];
+        int64_t nt = (int64_t)std::ceil(a.prog.n_ops * frac);
+        nt = std::max<int64_t>(nt, std::min<int64_t>(a.prog.n_ops, 64));
+        a.prog.n_ops = (int32_t)std::min<int64_t>(nt, a.prog.n_ops);
+        warm[i].prog.n_ops = std::min<int32_t>(a.prog.n_ops, 8);
+        a.signal = nullptr;  // filled below: the tuning runs write to scratch
+    }
+    size_t max_adc = 0;
+    for (auto &a : trunc) max_adc = std::max<size_t>(max_adc, (size_t)a.prog.n_adc);
+    mrsim_status rs = grow(ctx, &ctx->d_sig, &ctx->sig_cap, 2 * std::max<size_t>(max_adc, 1));
+    if (rs != MRSIM_OK) return rs;
+    for (auto &a : trunc) a.signal = ctx->d_sig;  // all phantoms add into one scratch buffer
+    for (auto &a : warm) a.signal = ctx->d_sig;
+    FwdArgs *d_trunc = nullptr;
+    CK(cudaMalloc(&d_trunc, 2 * trunc.size() * sizeof(FwdArgs)), "cudaMalloc tuning descriptors");
+    FwdArgs *d_warm = d_trunc + trunc.size();
+    CK(cudaMemcpy(d_trunc, trunc.data(), trunc.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice), "upload tuning descriptors");
+    CK(cudaMemcpy(d_warm, warm.data(), warm.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice), "upload tuning descriptors");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    static const int f32k[] = {1, 2, 4, 8}, f64k[] = {1, 2};
+    static const int thr[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
+    int bk = 0, bt = 0;
+    float bms = 1e30f;
+    for (int k : (fp64 ? std::vector<int>(f64k, f64k + 2) : std::vector<int>(f32k, f32k + 4))) {
+        for (int t : thr) {
+            if (t > (fp64 || k == 8 ? 256 : 512)) continue;
+            std::string keep = ctx->err;
+            if (batch_layout(b, k, t) != MRSIM_OK) {
+                ctx->err = keep;
+                continue;
+            }
+            if (batch_enqueue(b, d_warm, st) != MRSIM_OK) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, st);
+            mrsim_status q = batch_enqueue(b, d_trunc, st);
+            cudaEventRecord(e1, st);
+            if (q != MRSIM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < bms) {
+                bms = ms;
+                bk = k;
+                bt = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_trunc);
+    mrsim_status ss = mrsim_stream_status(ctx, stream);
+    if (ss != MRSIM_OK) return ss;
+    if (!bk) return fail(ctx, MRSIM_EUNSUPPORTED, "no launch shape fits this batch");
+    mrsim_status ls = batch_layout(b, bk, bt);
+    if (ls != MRSIM_OK) return ls;
+    best->spins_per_thread = bk;
+    best->threads_per_block = bt;
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_batch_set_shape(mrsim_batch *b, int32_t spins_per_thread, int32_t threads_per_block) {
+    if (!b) return MRSIM_EINVAL;
+    const bool fp64 = b->prec == MRSIM_FP64;
+    const int k = spins_per_thread, t = threads_per_block;
+    const bool ok = fp64 ? (k == 1 || k == 2) : (k == 1 || k == 2 || k == 4 || k == 8);
+    if (!ok || t < 32 || t % 32 || t > (fp64 || k == 8 ? 256 : 512))
+        return fail(b->ctx, MRSIM_EINVAL, "unsupported spins_per_thread / threads_per_block");
+    cudaSetDevice(b->ctx->device);
+    return batch_layout(b, k, t);
+}
+
+mrsim_status mrsim_batch_launch(mrsim_batch *b, void *stream) {
+    if (!b) return MRSIM_EINVAL;
+    cudaSetDevice(b->ctx->device);
+    return batch_enqueue(b, b->d_descs, (cudaStream_t)stream);
+}
+
+mrsim_status mrsim_batch_launch_graph(mrsim_batch *b, void *stream) {
+    if (!b) return MRSIM_EINVAL;
+    mrsim_ctx *ctx = b->ctx;
+    cudaSetDevice(ctx->device);
+    if (!b->graph) {
+        if (!b->capture) CK(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "create capture stream");
+        CK(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+        mrsim_status st = batch_enqueue(b, b->d_descs, b->capture);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+        if (st != MRSIM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return cuda_fail(ctx, e, "instantiate graph");
+        }
+    }
+    CK(cudaGraphLaunch(b->graph, (cudaStream_t)stream), "graph launch");
+    return MRSIM_OK;
+}
+
+void mrsim_batch_destroy(mrsim_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_head);
+    delete b;
+}
+
+mrsim_status mrsim_simulate_batch(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
+                                  const mrsim_sequence *const *seqs, mrsim_precision prec, void *stream,
+                                  double *const *signals_out) {
+    mrsim_batch *b = nullptr;
+    mrsim_status st = mrsim_batch_create(ctx, n, phantoms, seqs, prec, signals_out, &b);
+    if (st != MRSIM_OK) return st;
+    st = mrsim_batch_launch(b, stream);
+    if (st == MRSIM_OK) st = mrsim_stream_status(ctx, stream);
+    mrsim_batch_destroy(b);
+    return st;
 }
 
 }  // extern "C"

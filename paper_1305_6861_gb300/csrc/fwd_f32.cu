@@ -23,6 +23,26 @@ int fwd_blocks_per_sm_f32(int k, int threads, size_t smem) {
     }
 }
 
+int launch_batch_f32(const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream) {
+    switch (k) {
+    case 1: return dev::launch_batch_one<float, 1, 512>(b, threads, smem, grid, stream);
+    case 2: return dev::launch_batch_one<float, 2, 512>(b, threads, smem, grid, stream);
+    case 4: return dev::launch_batch_one<float, 4, 512>(b, threads, smem, grid, stream);
+    case 8: return dev::launch_batch_one<float, 8, 256>(b, threads, smem, grid, stream);
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int batch_blocks_per_sm_f32(int k, int threads, size_t smem) {
+    switch (k) {
+    case 1: return dev::batch_blocks_per_sm<float, 1, 512>(threads, smem);
+    case 2: return dev::batch_blocks_per_sm<float, 2, 512>(threads, smem);
+    case 4: return dev::batch_blocks_per_sm<float, 4, 512>(threads, smem);
+    case 8: return dev::batch_blocks_per_sm<float, 8, 256>(threads, smem);
+    default: return 0;
+    }
+}
+
 int fwd_regs_f32(int k) {
     switch (k) {
     case 1: return dev::regs_of<float, 1, 512>();

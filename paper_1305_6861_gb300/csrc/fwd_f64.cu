@@ -12,6 +12,26 @@ int launch_fwd_f64(const FwdArgs &a, int k, int threads, void *stream) {
 }
 
 int fwd_regs_f32(int k);
+int launch_batch_f32(const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream);
+int batch_blocks_per_sm_f32(int k, int threads, size_t smem);
+
+int launch_batch(bool fp64, const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream) {
+    if (!fp64) return launch_batch_f32(b, k, threads, smem, grid, stream);
+    switch (k) {
+    case 1: return dev::launch_batch_one<double, 1, 256>(b, threads, smem, grid, stream);
+    case 2: return dev::launch_batch_one<double, 2, 256>(b, threads, smem, grid, stream);
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int batch_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
+    if (!fp64) return batch_blocks_per_sm_f32(k, threads, smem);
+    switch (k) {
+    case 1: return dev::batch_blocks_per_sm<double, 1, 256>(threads, smem);
+    case 2: return dev::batch_blocks_per_sm<double, 2, 256>(threads, smem);
+    default: return 0;
+    }
+}
 int fwd_blocks_per_sm_f32(int k, int threads, size_t smem);
 int fwd_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
     if (!fp64) return fwd_blocks_per_sm_f32(k, threads, smem);
@@ -53,6 +73,22 @@ __global__ void pack_kernel(int64_t n, int64_t np, const double *x, const double
         params[P_R1 * np + s] = isinf(v1) ? 0.0 : 1.0 / v1;
         params[P_R2 * np + s] = isinf(v2) ? 0.0 : 1.0 / v2;
     }
+}
+
+// Zero the signal buffers of a batch (one launch instead of one memset per phantom).
+__global__ void zero_signals_kernel(const FwdArgs *descs, int n) {
+    for (int d = 0; d < n; ++d) {
+        double *sig = descs[d].signal;
+        const int64_t m = 2 * descs[d].prog.n_adc;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+            sig[i] = 0.0;
+    }
+}
+
+int zero_signals(const FwdArgs *descs, int n, void *stream) {
+    if (n <= 0) return 0;
+    zero_signals_kernel<<<152, 256, 0, (cudaStream_t)stream>>>(descs, n);
+    return (int)cudaGetLastError();
 }
 
 int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, const double *z, const double *rho,

@@ -534,14 +534,26 @@ __host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1
     return L;
 }
 
-template <typename R, int K, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
+// Barriers of the two op buffers; initialised once per block (thread 0).
+__device__ __forceinline__ void init_op_barriers(unsigned char *smem, bool f64) {
+    const SmemLayout L = smem_layout(f64, 0, 0, 0, 0, 0, 0);  // ops, bars and flag do not depend on the program
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+}
+
+// One tile of S = K·blockDim spins (spins tile·S ... tile·S + S − 1 of the phantom in `a`) through
+// the whole program.  `seq` counts the op chunks this block has staged so far (it selects the
+// buffer and the mbarrier phase, so consecutive tiles of a persistent block can reuse the
+// barriers).  Returns false if a bounded wait ran out (status recorded, block must stop).
+template <typename R, int K>
+__device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigned char *smem, uint32_t &seq) {
     using SP = Spins<R, K>;
     using Op = typename SP::Op;
     using V = typename SP::V;
     constexpr bool F64 = SP::F64;
     constexpr int CH = F64 ? CHUNK_F64 : CHUNK_F32;
-    extern __shared__ __align__(128) unsigned char smem[];
 
     SP sp;
     sp.nthr = blockDim.x;
@@ -581,24 +593,24 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
     sp.params = a.params;
     sp.win_base = 0;
     sp.win_end = 0;
-    sp.base = (int64_t)blockIdx.x * S;
+    sp.base = tile * S;
     sp.np = a.n_pad;
     sp.n_spins = a.n_spins;
 
     const Op *gops = reinterpret_cast<const Op *>(P.ops);
     const int n_ops = P.n_ops;
     const int n_chunks = (n_ops + CH - 1) / CH;
+    // chunk c of this tile is the block's chunk number seq + c: buffer (seq + c) & 1,
+    // mbarrier phase ((seq + c) >> 1) & 1
     auto issue = [&](int c) {
+        const uint32_t g = seq + (uint32_t)c;
         const int m = min(CH, n_ops - c * CH);
         const uint32_t bytes = (uint32_t)(m * (int)sizeof(Op));
         fence_proxy_async();
-        mbar_expect_tx(&bars[c & 1], bytes);
-        bulk_g2s(opbuf + (c & 1) * CH, gops + (size_t)c * CH, bytes, &bars[c & 1]);
+        mbar_expect_tx(&bars[g & 1], bytes);
+        bulk_g2s(opbuf + (g & 1) * CH, gops + (size_t)c * CH, bytes, &bars[g & 1]);
     };
     if (sp.tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
         *abort_flag = 0;
         if (n_chunks > 0) issue(0);
         if (n_chunks > 1) issue(1);
@@ -665,8 +677,9 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
 
     // ---- the operation stream ------------------------------------------------------------------
     for (int c = 0; c < n_chunks; ++c) {
+        const uint32_t g = seq + (uint32_t)c;
         if (sp.tid == 0) {
-            if (!mbar_wait_bounded(&bars[c & 1], (uint32_t)((c >> 1) & 1), WAIT_LIMIT_NS)) {
+            if (!mbar_wait_bounded(&bars[g & 1], (g >> 1) & 1u, WAIT_LIMIT_NS)) {
                 atomicCAS(a.status, 0, (int)MRSIM_ETIMEOUT);
                 *abort_flag = 1;
             }
@@ -674,15 +687,16 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
         __syncthreads();
         if (*abort_flag) {
             if (sp.tid == 0 && c + 1 < n_chunks)
-                mbar_wait_bounded(&bars[(c + 1) & 1], (uint32_t)(((c + 1) >> 1) & 1), WAIT_LIMIT_NS);
-            return;
+                mbar_wait_bounded(&bars[(g + 1) & 1], ((g + 1) >> 1) & 1u, WAIT_LIMIT_NS);
+            return false;
         }
-        const Op *ops = opbuf + (c & 1) * CH;
+        const Op *ops = opbuf + (g & 1) * CH;
         const int m = min(CH, n_ops - c * CH);
         for (int o = 0; o < m; ++o) sp.exec(ops[o]);
         __syncthreads();
         if (sp.tid == 0 && c + 2 < n_chunks) issue(c + 2);
     }
+    seq += (uint32_t)n_chunks;
     if (sp.win_end > sp.win_base) sp.flush();
 
     if (a.state_out) {
@@ -701,6 +715,37 @@ __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
             }
         }
     }
+    __syncthreads();  // the block's shared memory may be reused by the next tile
+    return true;
+}
+
+template <typename R, int K, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (threadIdx.x == 0) init_op_barriers(smem, std::is_same<R, double>::value);
+    uint32_t seq = 0;
+    run_tile<R, K>(a, (int64_t)blockIdx.x, smem, seq);
+}
+
+// Persistent batch kernel: each block pops (phantom, tile) work items from a global counter
+// (dynamic assignment of spin blocks, §5.3.2) until the queue is empty.  Items are ordered
+// longest first on the host.  No block waits on another.
+template <typename R, int K, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) batch_kernel(const BatchArgs b) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_item;
+    if (threadIdx.x == 0) init_op_barriers(smem, std::is_same<R, double>::value);
+    uint32_t seq = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(b.head, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= b.n_items) break;
+        const BatchItem item = b.items[it];
+        const FwdArgs a = b.descs[item.desc];
+        if (!run_tile<R, K>(a, (int64_t)item.tile, smem, seq)) return;
+    }
 }
 
 template <typename R, int K, int MAXT>
@@ -717,6 +762,32 @@ int launch_one(const FwdArgs &a, int threads, void *stream) {
     if (grid > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
     kern<<<(unsigned)grid, threads, L.total, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
+}
+
+template <typename R, int K, int MAXT>
+int launch_batch_one(const BatchArgs &b, int threads, size_t smem, int grid, void *stream) {
+    if (threads <= 0 || threads > MAXT || threads % 32 || grid <= 0) return (int)cudaErrorInvalidValue;
+    auto kern = batch_kernel<R, K, MAXT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    kern<<<grid, threads, smem, (cudaStream_t)stream>>>(b);
+    return (int)cudaGetLastError();
+}
+
+template <typename R, int K, int MAXT>
+int batch_blocks_per_sm(int threads, size_t smem) {
+    if (threads <= 0 || threads > MAXT || threads % 32) return 0;
+    auto kern = batch_kernel<R, K, MAXT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 template <typename R, int K, int MAXT>

@@ -128,7 +128,23 @@ struct FwdArgs {
     int *status;             // device status word (0 = ok)
 };
 
+// One work item of the persistent batch kernel: tile `tile` of the phantom of descriptor `desc`.
+struct BatchItem {
+    int32_t desc;
+    int32_t tile;
+};
+
+struct BatchArgs {
+    const FwdArgs *descs;    // one forward description per phantom (device)
+    const BatchItem *items;  // work items, longest first (device)
+    int32_t n_items;
+    int *head;               // work-queue counter, zero before the launch (device)
+};
+
 // Kernel launchers (fwd_f32.cu / fwd_f64.cu).  Return a cudaError_t value.
+int launch_batch(bool fp64, const BatchArgs &b, int spins_per_thread, int threads, size_t smem, int grid,
+                 void *stream);
+int batch_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
 int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
@@ -136,6 +152,7 @@ size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int thr
 int fwd_regs(bool fp64, int spins_per_thread);
 // Resident blocks per SM of a launch shape with `smem` dynamic shared memory (0 = cannot launch).
 int fwd_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
+int zero_signals(const FwdArgs *descs, int n, void *stream);
 int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, const double *z,
                 const double *rho, const double *t1, const double *t2, const double *dw,
                 double *params, int *bad, void *stream);

@@ -33,7 +33,9 @@ EXPORTS = (
     "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
     "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
-    "mrsim_debug_compile", "mrsim_autotune",
+    "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
+    "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
+    "mrsim_batch_destroy", "mrsim_simulate_batch",
 )
 
 
@@ -102,6 +104,14 @@ def lib():
             "mrsim_simulate": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
             "mrsim_simulate_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64, P(Options)]),
             "mrsim_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, P(Options)]),
+            "mrsim_batch_create": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, P(vp)]),
+            "mrsim_batch_num_items": (i64, [vp]),
+            "mrsim_batch_autotune": (ctypes.c_int, [vp, vp, P(Options)]),
+            "mrsim_batch_set_shape": (ctypes.c_int, [vp, i32, i32]),
+            "mrsim_batch_launch": (ctypes.c_int, [vp, vp]),
+            "mrsim_batch_launch_graph": (ctypes.c_int, [vp, vp]),
+            "mrsim_batch_destroy": (None, [vp]),
+            "mrsim_simulate_batch": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, vp]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
         }
         for name, (res, args) in sig.items():
@@ -238,6 +248,50 @@ def simulate(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP3
                                  ctypes.byref(opt))
     ctx.check(rc)
     return out
+
+
+class Batch:
+    """Many phantom/sequence pairs in one persistent launch.  `outs`: one CUDA buffer of 2*n_adc
+    float64 per pair (e.g. torch tensors); phantoms and sequences must outlive the batch."""
+
+    def __init__(self, ctx: Context, phantoms, seqs, precision: int = FP32, outs=None):
+        self.ctx = ctx
+        self._keep = (list(phantoms), list(seqs), list(outs))
+        n = len(self._keep[0])
+        ph = (ctypes.c_void_p * n)(*[p.h.value for p in phantoms])
+        sq = (ctypes.c_void_p * n)(*[q.h.value for q in seqs])
+        os_ = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
+        self._arrays = (ph, sq, os_)
+        h = ctypes.c_void_p()
+        ctx.check(lib().mrsim_batch_create(ctx.h, n, ph, sq, int(precision), os_, ctypes.byref(h)))
+        self.h = h
+
+    @property
+    def n_items(self) -> int:
+        return int(lib().mrsim_batch_num_items(self.h))
+
+    def autotune(self, stream=None):
+        opt = Options()
+        self.ctx.check(lib().mrsim_batch_autotune(self.h, _stream(stream), ctypes.byref(opt)))
+        return int(opt.spins_per_thread), int(opt.threads_per_block)
+
+    def set_shape(self, spins_per_thread: int, threads_per_block: int):
+        self.ctx.check(lib().mrsim_batch_set_shape(self.h, int(spins_per_thread), int(threads_per_block)))
+
+    def launch(self, stream=None, graph: bool = False):
+        f = lib().mrsim_batch_launch_graph if graph else lib().mrsim_batch_launch
+        self.ctx.check(f(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None):
