@@ -174,6 +174,32 @@ mrsim_status mrsim_simulate_batch(mrsim_ctx *ctx, int32_t n, const mrsim_phantom
                                   const mrsim_sequence *const *seqs, mrsim_precision prec, void *stream,
                                   double *const *signals_out);
 
+/* ---- batches without allocation ---------------------------------------------------------- */
+
+/* The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory when they simulate (a plug-in whose host application owns every device allocation, a
+ * real-time loop under a fixed memory budget).  It runs the same persistent batch kernel as
+ * mrsim_batch_launch for n phantom/sequence pairs (handles created earlier; device signal
+ * buffers of 2*num_adc doubles each, zeroed by the call), but allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  Its scratch (work-queue counter, per-phantom
+ * descriptors, work items) is one file-scope device array of MRSIM_STATIC_SCRATCH_BYTES that
+ * every GPU which loads the library holds until the process exits; the work list is staged
+ * through a host buffer of the same size.  Limits: at most
+ * (MRSIM_STATIC_SCRATCH_BYTES - 256) / sizeof(descriptor) phantoms and as many work items
+ * (tiles of spins_per_thread x threads_per_block spins, 8 bytes each) as fit after them;
+ * larger batches fail with MRSIM_EINVAL and a message saying which limit was hit.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Every call shares the one array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (other streams, other host threads'
+ * launches still running) race on it and must be serialised by the caller; host threads are
+ * serialised inside the call.  spins_per_thread / threads_per_block: 0 = library default.
+ * Asynchronous on `stream`; errors of the kernel surface through mrsim_stream_status. */
+#define MRSIM_STATIC_SCRATCH_BYTES (1u << 20)
+mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
+                                         const mrsim_sequence *const *seqs, mrsim_precision prec,
+                                         void *stream, double *const *signals_out,
+                                         int32_t spins_per_thread, int32_t threads_per_block);
+
 /* ---- diagnostics ---------------------------------------------------------------------- */
 
 /* Host-only compile of an event list (no device needed), for inspecting and testing the

@@ -12,69 +12,10 @@
 
 #include "../../include/mrsim.h"
 #include "compiled.h"
+#include "handles.h"
 #include "internal.h"
 
 using namespace mrsim;
-
-struct TunedShape {
-    int k = 0, threads = 0;
-    float ms = 0.0f;
-};
-// Autotuned launch shapes are kept per context, keyed by what determines the kernel's cost:
-// precision, spin count and the compiled program's size and class-table sizes.
-using TuneKey = std::array<int64_t, 7>;
-
-struct mrsim_ctx {
-    std::map<TuneKey, TunedShape> tuned;
-    int device = 0;
-    int num_sms = 0;
-    int max_smem_optin = 0;
-    std::string err;
-    int *d_status = nullptr;
-    // scratch for host-side outputs and inputs, grown on demand
-    double *d_sig = nullptr;
-    size_t sig_cap = 0;
-    double *d_state = nullptr;
-    size_t state_cap = 0;
-    double *d_stage = nullptr;
-    size_t stage_cap = 0;
-    int *d_bad = nullptr;
-};
-
-struct mrsim_phantom {
-    mrsim_ctx *ctx = nullptr;
-    int64_t n = 0, n_pad = 0;
-    double *params = nullptr;
-};
-
-struct mrsim_sequence {
-    mrsim_ctx *ctx = nullptr;
-    int64_t n_events = 0;
-    Compiled host;
-    void *d_ops32 = nullptr, *d_ops64 = nullptr;
-    double *d_pcls = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_demod = nullptr;
-    float *d_demod32 = nullptr;
-    float *d_train32 = nullptr;
-    double *d_train64 = nullptr;
-    Program p32{}, p64{};
-};
-
-struct mrsim_batch {
-    mrsim_ctx *ctx = nullptr;
-    mrsim_precision prec = MRSIM_FP32;
-    std::vector<const mrsim_phantom *> ph;
-    std::vector<const mrsim_sequence *> seq;
-    std::vector<FwdArgs> descs;
-    std::vector<BatchItem> items;
-    FwdArgs *d_descs = nullptr;
-    BatchItem *d_items = nullptr;
-    int *d_head = nullptr;  // work-queue counter
-    int k = 0, threads = 0, grid = 0;
-    size_t smem = 0;
-    int64_t spin_steps = 0;
-    cudaStream_t capture = nullptr;
-    cudaGraphExec_t graph = nullptr;
-};
 
 namespace {
 
@@ -163,28 +104,12 @@ mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStr
     return MRSIM_OK;
 }
 
-struct Launch {
-    int k, threads;
-};
-
 TuneKey tune_key(mrsim_precision prec, const mrsim_phantom *ph, const mrsim_sequence *seq) {
     const Compiled &c = seq->host;
     return TuneKey{(int64_t)prec, ph->n, (int64_t)c.ops32.size(), c.n_pcls, c.n_e1, c.n_e2,
                    c.n_adc * 4096 + (int64_t)c.train.size()};
 }
 
-// Default launch shape: the largest spins-per-thread that still gives every SM about two blocks.
-Launch choose_launch(const mrsim_ctx *ctx, bool fp64, int64_t n) {
-    static const Launch f32[] = {{4, 128}, {2, 128}, {1, 128}, {1, 64}, {1, 32}};
-    static const Launch f64[] = {{1, 128}, {1, 64}, {1, 32}};
-    const Launch *c = fp64 ? f64 : f32;
-    const int nc = fp64 ? 3 : 5;
-    for (int i = 0; i < nc; ++i) {
-        const int64_t S = (int64_t)c[i].k * c[i].threads;
-        if ((n + S - 1) / S >= 2LL * ctx->num_sms) return c[i];
-    }
-    return c[nc - 1];
-}
 
 }  // namespace
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
     "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
-    "mrsim_batch_destroy", "mrsim_simulate_batch",
+    "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
 )
 
 
@@ -112,6 +112,7 @@ def lib():
             "mrsim_batch_launch_graph": (ctypes.c_int, [vp, vp]),
             "mrsim_batch_destroy": (None, [vp]),
             "mrsim_simulate_batch": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, vp]),
+            "mrsim_simulate_batch_static": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, vp, i32, i32]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
         }
         for name, (res, args) in sig.items():
@@ -292,6 +293,19 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def simulate_batch_static(ctx: Context, phantoms, seqs, precision: int = FP32, outs=None, stream=None,
+                          spins_per_thread: int = 0, threads_per_block: int = 0):
+    """Batch launch that allocates no device memory (scratch in the library's fixed static array):
+    for callers that cannot call cudaMalloc.  `outs`: one CUDA buffer of 2*n_adc float64 per pair.
+    Asynchronous on `stream`; calls that overlap on the GPU share the scratch and must not overlap."""
+    n = len(phantoms)
+    ph = (ctypes.c_void_p * n)(*[p.h.value for p in phantoms])
+    sq = (ctypes.c_void_p * n)(*[q.h.value for q in seqs])
+    os_ = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
+    ctx.check(lib().mrsim_simulate_batch_static(ctx.h, n, ph, sq, int(precision), _stream(stream), os_,
+                                                int(spins_per_thread), int(threads_per_block)))
 
 
 def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None):
