@@ -59,6 +59,13 @@ def _bind(path):
     lib.oracle_simulate.argtypes = [ctypes.c_int64] + [d] * 7 + [d, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_double, d, ctypes.c_int64, d, ctypes.c_int]
     lib.oracle_max_threads.restype = ctypes.c_int
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.oracle_simulate_rf.restype = ctypes.c_int
+    lib.oracle_simulate_rf.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                       i32p, d, d, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_gradient.restype = ctypes.c_int
+    lib.oracle_gradient.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                    i32p, d, d, ctypes.c_int64, d, d, d, i32p, ctypes.c_int32, d, ctypes.c_int]
     return lib
 
 
@@ -103,6 +110,52 @@ def simulate(phantom, events, gamma_hz_per_t, m_init=None, want_signal=True, wan
     out_sig = sig.view(np.complex128) if sig is not None else None
     out_st = st.reshape(n, 3) if st is not None else None
     return out_sig, out_st
+
+
+def _ip(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def simulate_rf(phantom, events, gamma_hz_per_t, rf_param, rf_values, n_threads=0, lib=None):
+    """Forward signal where event e's flip angle is rf_values[rf_param[e]] (rf_param[e] >= 0)."""
+    lib = _load() if lib is None else lib
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    arrs = [np.ascontiguousarray(getattr(phantom, k), dtype=np.float64) for k in ("x", "y", "z", "rho", "t1", "t2", "dw")]
+    rp = np.ascontiguousarray(rf_param, dtype=np.int32)
+    rv = np.ascontiguousarray(rf_values, dtype=np.float64)
+    n_adc = int(np.count_nonzero(ev["adc"]))
+    sig = np.zeros(2 * n_adc)
+    rc = lib.oracle_simulate_rf(arrs[0].shape[0], *[_dp(a) for a in arrs], ev.shape[0], ev.ctypes.data_as(ctypes.c_void_p),
+                                float(gamma_hz_per_t), _ip(rp), _dp(rv), _dp(sig), n_adc, int(n_threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_simulate_rf failed with code {rc}")
+    return sig.view(np.complex128)
+
+
+def gradient(phantom, events, gamma_hz_per_t, h, rf_param=None, rf_values=None, sel=(), n_threads=0, lib=None):
+    """Forward-mode gradient of a loss whose gradient w.r.t. the signal is h (complex, per sample:
+    dL/dRe s + j dL/dIm s).  Returns (dL/dM0, dL/dT1, dL/dT2 per spin, dL/d rf_values[sel])."""
+    lib = _load() if lib is None else lib
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    arrs = [np.ascontiguousarray(getattr(phantom, k), dtype=np.float64) for k in ("x", "y", "z", "rho", "t1", "t2", "dw")]
+    n = arrs[0].shape[0]
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.complex128)).view(np.float64)
+    n_adc = int(np.count_nonzero(ev["adc"]))
+    if hh.shape[0] != 2 * n_adc:
+        raise ValueError("h must have one complex value per sample")
+    rp = None if rf_param is None else np.ascontiguousarray(rf_param, dtype=np.int32)
+    rv = None if rf_values is None else np.ascontiguousarray(rf_values, dtype=np.float64)
+    se = np.ascontiguousarray(np.asarray(sel, dtype=np.int32))
+    out = [np.zeros(n) for _ in range(3)]
+    dsel = np.zeros(max(len(se), 1))
+    rc = lib.oracle_gradient(n, *[_dp(a) for a in arrs], ev.shape[0], ev.ctypes.data_as(ctypes.c_void_p),
+                             float(gamma_hz_per_t), _ip(rp), _dp(rv), _dp(hh), n_adc, *[_dp(o) for o in out],
+                             _ip(se) if len(se) else None, len(se), _dp(dsel), int(n_threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_gradient failed with code {rc}")
+    return out[0], out[1], out[2], dsel[: len(se)]
 
 
 def signal(workload_or_phantom, sequence=None, n_threads=0):

@@ -172,6 +172,27 @@ int oracle_simulate(int64_t n_spins, const double *x, const double *y, const dou
     return 0;
 }
 
+/* Forward simulation with learnable flip angles: as oracle_simulate, but event e's flip angle is
+ * rf_values[rf_param[e]] wherever rf_param[e] >= 0. */
+int oracle_simulate_rf(int64_t n_spins, const double *x, const double *y, const double *z,
+                       const double *rho, const double *t1, const double *t2, const double *dw,
+                       int64_t n_events, const void *events, double gamma_hz_per_t,
+                       const int32_t *rf_param, const double *rf_values, double *signal, int64_t n_adc,
+                       int n_threads)
+{
+    const oracle_event *ev = (const oracle_event *)events;
+    oracle_event *copy = (oracle_event *)malloc(sizeof(oracle_event) * (size_t)(n_events > 0 ? n_events : 1));
+    if (!copy) return -2;
+    for (int64_t e = 0; e < n_events; ++e) {
+        copy[e] = ev[e];
+        if (rf_param && rf_param[e] >= 0) copy[e].rf_flip = rf_values[rf_param[e]];
+    }
+    int rc = oracle_simulate(n_spins, x, y, z, rho, t1, t2, dw, NULL, n_events, copy, gamma_hz_per_t, signal,
+                             n_adc, NULL, n_threads);
+    free(copy);
+    return rc;
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP
@@ -179,4 +200,144 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/*
+ * Gradient of a real loss L of the signal, by forward-mode differentiation of the same
+ * step-by-step simulation (tangent propagation; every step differentiated by hand from
+ * Eqs. 3.5 and 3.19).
+ *   h:        2*n_adc doubles, h_j = dL/dRe(s_j) + j dL/dIm(s_j) (gradient of L w.r.t. the signal)
+ *   rf_param: NULL or n_events ints; event e's flip angle is rf_values[rf_param[e]] when >= 0
+ *   rf_values:NULL or the learnable flip angles
+ *   d_rho, d_t1, d_t2: NULL or n_spins doubles, receive dL/dM0, dL/dT1, dL/dT2 per spin
+ *   sel, n_sel, d_sel: directional derivatives dL/d rf_values[sel[i]] into d_sel[i]
+ * dL/dp = sum_j Re(conj(h_j) ds_j/dp), s_j = sum_spins (Mx + jMy) exp(-j adc_phase_j).
+ */
+static double event_flip(const oracle_event *e, int64_t idx, const int32_t *rf_param, const double *rf_values)
+{
+    if (rf_param && rf_param[idx] >= 0) return rf_values[rf_param[idx]];
+    return e->rf_flip;
+}
+
+/* derivative of the Eq. 3.19 matrix with respect to the flip angle α */
+static void rf_rotation_dalpha(double alpha, double phi, double D[3][3])
+{
+    const double ca = cos(alpha), sa = sin(alpha);
+    const double cp = cos(phi), sp = sin(phi);
+    D[0][0] = -sp * sp * sa;
+    D[0][1] = sp * cp * sa;
+    D[0][2] = -sp * ca;
+    D[1][0] = sp * cp * sa;
+    D[1][1] = -cp * cp * sa;
+    D[1][2] = cp * ca;
+    D[2][0] = sp * ca;
+    D[2][1] = -cp * ca;
+    D[2][2] = -sa;
+}
+
+int oracle_gradient(int64_t n_spins, const double *x, const double *y, const double *z,
+                    const double *rho, const double *t1, const double *t2, const double *dw,
+                    int64_t n_events, const void *events, double gamma_hz_per_t,
+                    const int32_t *rf_param, const double *rf_values,
+                    const double *h, int64_t n_adc,
+                    double *d_rho, double *d_t1, double *d_t2,
+                    const int32_t *sel, int32_t n_sel, double *d_sel, int n_threads)
+{
+    const oracle_event *ev = (const oracle_event *)events;
+    if (count_adc(ev, n_events) != n_adc) return -1;
+    const double gamma = ORACLE_TWO_PI * gamma_hz_per_t;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+#endif
+    const int nd = 3 + n_sel; /* tangent directions per spin: M0, T1, T2, selected RF parameters */
+    double *part = (double *)calloc((size_t)nt * (size_t)(n_sel + 1), sizeof(double));
+    if (!part) return -2;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = part + (size_t)tid * (size_t)(n_sel + 1);
+        double *T = (double *)malloc(sizeof(double) * 3 * (size_t)nd);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t s = 0; s < n_spins; ++s) {
+            double M[3] = {0.0, 0.0, rho[s]};
+            for (int d = 0; d < 3 * nd; ++d) T[d] = 0.0;
+            T[0 * 3 + 2] = 1.0; /* dM/dM0 at equilibrium */
+            double g[3] = {0.0, 0.0, 0.0};
+            int64_t j = 0;
+            for (int64_t e = 0; e < n_events; ++e) {
+                const oracle_event *E = &ev[e];
+                const double alpha = event_flip(E, e, rf_param, rf_values);
+                if (alpha != 0.0) {
+                    double R[3][3], D[3][3];
+                    rf_rotation(alpha, E->rf_phase, R);
+                    rf_rotation_dalpha(alpha, E->rf_phase, D);
+                    const int p = rf_param ? rf_param[e] : -1;
+                    for (int d = 0; d < nd; ++d) {
+                        double *t = T + 3 * d;
+                        double u[3];
+                        for (int r = 0; r < 3; ++r) u[r] = R[r][0] * t[0] + R[r][1] * t[1] + R[r][2] * t[2];
+                        if (d >= 3 && p >= 0 && p == sel[d - 3])
+                            for (int r = 0; r < 3; ++r) u[r] += D[r][0] * M[0] + D[r][1] * M[1] + D[r][2] * M[2];
+                        t[0] = u[0]; t[1] = u[1]; t[2] = u[2];
+                    }
+                    double mx = R[0][0] * M[0] + R[0][1] * M[1] + R[0][2] * M[2];
+                    double my = R[1][0] * M[0] + R[1][1] * M[1] + R[1][2] * M[2];
+                    double mz = R[2][0] * M[0] + R[2][1] * M[1] + R[2][2] * M[2];
+                    M[0] = mx; M[1] = my; M[2] = mz;
+                }
+                const double theta = (gamma * (E->gx * x[s] + E->gy * y[s] + E->gz * z[s]) + dw[s]) * E->dt;
+                const double c = cos(theta), sn = sin(theta);
+                const double e2 = exp(-E->dt / t2[s]), e1 = exp(-E->dt / t1[s]);
+                /* d e2 / d T2 = e2 dt / T2^2, d e1 / d T1 = e1 dt / T1^2 (0 for T = inf) */
+                const double de2 = isinf(t2[s]) ? 0.0 : e2 * E->dt / (t2[s] * t2[s]);
+                const double de1 = isinf(t1[s]) ? 0.0 : e1 * E->dt / (t1[s] * t1[s]);
+                const double px = M[0] * c + M[1] * sn, py = -M[0] * sn + M[1] * c;
+                for (int d = 0; d < nd; ++d) {
+                    double *t = T + 3 * d;
+                    const double qx = t[0] * c + t[1] * sn, qy = -t[0] * sn + t[1] * c;
+                    double nx = e2 * qx, ny = e2 * qy, nz = e1 * t[2];
+                    if (d == 0) nz += 1.0 - e1;                 /* M0 */
+                    if (d == 1) nz += de1 * (M[2] - rho[s]);    /* T1 */
+                    if (d == 2) { nx += de2 * px; ny += de2 * py; } /* T2 */
+                    t[0] = nx; t[1] = ny; t[2] = nz;
+                }
+                M[0] = e2 * px;
+                M[1] = e2 * py;
+                M[2] = M[2] * e1 + rho[s] * (1.0 - e1);
+                if (E->adc) {
+                    const double cph = cos(E->adc_phase), sph = sin(E->adc_phase);
+                    const double hr = h[2 * j], hi = h[2 * j + 1];
+                    for (int d = 0; d < nd; ++d) {
+                        const double *t = T + 3 * d;
+                        /* ds = (tx + j ty) exp(-j phase); dL = Re(conj(h) ds) */
+                        const double dsr = t[0] * cph + t[1] * sph, dsi = t[1] * cph - t[0] * sph;
+                        const double dl = hr * dsr + hi * dsi;
+                        if (d < 3) g[d] += dl; else mine[d - 3] += dl;
+                    }
+                    ++j;
+                }
+            }
+            if (d_rho) d_rho[s] = g[0];
+            if (d_t1) d_t1[s] = g[1];
+            if (d_t2) d_t2[s] = g[2];
+        }
+        free(T);
+    }
+    for (int i = 0; i < n_sel; ++i) {
+        double acc = 0.0;
+        for (int t = 0; t < nt; ++t) acc += part[(size_t)t * (size_t)(n_sel + 1) + i];
+        if (d_sel) d_sel[i] = acc;
+    }
+    free(part);
+    return 0;
 }
