@@ -174,6 +174,35 @@ mrsim_status mrsim_simulate_batch(mrsim_ctx *ctx, int32_t n, const mrsim_phantom
                                   const mrsim_sequence *const *seqs, mrsim_precision prec, void *stream,
                                   double *const *signals_out);
 
+/* ---- differentiation: adjoint (backward-in-time) gradients ---------------------------------- */
+
+/* Gradients of a real loss L of the signal with respect to every spin's M0, T1, T2 and to
+ * learnable RF flip angles, by the adjoint recursion through the elementary sequences (Eq. 4.1 is
+ * affine in M, so the adjoint runs backward through the transposed steps: Eq. 3.19 rotations and
+ * Eq. 3.5 precession/relaxation).  float64 throughout.  The forward pass stores each spin's state
+ * every ckpt_every events; the backward pass recomputes the states between checkpoints.
+ *   rf_param: NULL or n_events indices; event e's flip angle is rf_values[rf_param[e]] when
+ *             rf_param[e] >= 0 (its rf_flip is then ignored), else the event's own rf_flip.
+ *   ckpt_every: events per checkpoint segment, 1..128 (0 = 64); storage is
+ *             ceil(n_events/ckpt_every) x 3 doubles per spin, allocated by the first forward call. */
+typedef struct mrsim_adjoint mrsim_adjoint;
+mrsim_status mrsim_adjoint_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                  double gamma_hz_per_t, const int32_t *rf_param, int32_t n_params,
+                                  int32_t ckpt_every, mrsim_adjoint **out);
+int64_t mrsim_adjoint_num_adc(const mrsim_adjoint *adj);
+/* Forward simulation that also stores the checkpoints.  rf_values: device array of n_params flip
+ * angles [rad] (may be NULL when n_params = 0); signal_out: device, 2*num_adc doubles.
+ * Asynchronous on `stream`. */
+mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, const double *rf_values,
+                                   void *stream, double *signal_out);
+/* Backward pass for the phantom and rf_values of the last forward call.  dl_dsignal: device,
+ * 2*num_adc doubles (dL/dRe s_j, dL/dIm s_j).  Outputs (device, NULL to skip): d_rho, d_t1, d_t2
+ * (n_spins each; dL/dT = 0 where T = INFINITY) and d_rf (n_params, overwritten).  Asynchronous. */
+mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph, const double *rf_values,
+                                    const double *dl_dsignal, void *stream, double *d_rho, double *d_t1,
+                                    double *d_t2, double *d_rf);
+void mrsim_adjoint_destroy(mrsim_adjoint *adj);
+
 /* ---- batches without allocation ---------------------------------------------------------- */
 
 /* The paper has no counterpart: this entry point exists for callers that cannot allocate device

@@ -1,0 +1,609 @@
+// adjoint.cu -- reverse-mode (adjoint, backward-in-time) gradient of a loss of the signal with
+// respect to every spin's M0, T1, T2 and to learnable RF flip angles.
+//
+// Every event is an affine map of a spin's magnetisation (Eq. 4.1): M' = P·R·M + (0, 0, M0(1−E1))
+// with R the hard pulse (Eq. 3.19) and P = diag(E2·rot(−θ), E1) (Eq. 3.5).  For a loss L whose
+// gradient with respect to the signal is h_j = ∂L/∂Re s_j + j ∂L/∂Im s_j, the adjoint λ of a spin's
+// state runs backward through the events: λ ← Rᵀ·Pᵀ·λ, plus conj(d_j)·h_j at the end of every
+// event that takes sample j (d_j = exp(−j·adc_phase_j), since s_j = Σ_spins (Mx + jMy)·d_j), and
+// the parameter gradients collect λ'ᵀ·∂M'/∂p along the way.  The backward pass needs the states
+// in reverse order: the forward pass stores every spin's state at the start of each segment of C
+// events (checkpoints); the backward pass restores a checkpoint, recomputes the segment's states
+// into a per-thread buffer and sweeps the segment backward.  Everything here is float64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mrsim.h"
+#include "handles.h"
+#include "internal.h"
+
+using namespace mrsim;
+
+namespace {
+
+constexpr int ADJ_MAX_CLASSES = 16;
+constexpr int ADJ_MAX_SEG = 128;  // events per checkpoint segment (per-thread state buffer size)
+constexpr int ADJ_THREADS = 128;
+
+enum AdjFlags : int32_t { A_RF = 1, A_ADC = 2, A_CLS = 4, A_INL = 8 };
+
+// One event of the differentiation program (64 bytes).
+struct AdjEvent {
+    int32_t flags;
+    int32_t rf;     // RF table entry (A_RF)
+    int32_t cls;    // precession/relaxation class (A_CLS)
+    int32_t adc;    // sample index (A_ADC)
+    double k[3];    // inline moment [cycles/m] (A_INL)
+    double dt;      // interval [s]
+    double pad[2];
+};
+static_assert(sizeof(AdjEvent) == 64, "AdjEvent must be 64 bytes");
+
+// The RF pulse of one RF event: its rotation R (Eq. 3.19) and dR/dα, rebuilt each launch from the
+// learnable flips; plus what they are built from.
+struct RfSpec {
+    double alpha, phi;
+    int32_t param, pad;
+};
+struct RfEntry {
+    double R[9];
+    double D[9];
+    int32_t param, pad;  // learnable parameter index or -1
+};
+
+}  // namespace
+
+struct mrsim_adjoint {
+    mrsim_ctx *ctx = nullptr;
+    int64_t n_events = 0, n_adc = 0;
+    int32_t n_params = 0, seg = 64, n_rf = 0, n_cls = 0;
+    AdjEvent *d_ev = nullptr;
+    RfSpec *d_spec = nullptr;
+    RfEntry *d_rf = nullptr;
+    double *d_cls = nullptr;    // 4 per class: kx, ky, kz, dt
+    double *d_demod = nullptr;  // 2 per sample: cos(adc_phase), -sin(adc_phase)
+    double *d_ckpt = nullptr;   // n_seg x 3 x n_spins
+    size_t ckpt_cap = 0;
+    const mrsim_phantom *last_ph = nullptr;
+    int64_t last_n = -1;
+};
+
+namespace {
+
+// Eq. 3.19 as the rotation by −α about n = (cos φ, sin φ, 0), and its derivative in α.
+__global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values, RfEntry *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const RfSpec s = spec[i];
+        const double a = s.param >= 0 ? values[s.param] : s.alpha;
+        double sa, ca, sp, cp;
+        sincos(a, &sa, &ca);
+        sincos(s.phi, &sp, &cp);
+        const double n0 = cp, n1 = sp;
+        const double omc = 1.0 - ca;
+        RfEntry e;
+        // R = cos α·I + (1 − cos α)·n nᵀ − sin α·[n]x
+        e.R[0] = ca + omc * n0 * n0;
+        e.R[1] = omc * n0 * n1;
+        e.R[2] = -sa * n1;
+        e.R[3] = omc * n0 * n1;
+        e.R[4] = ca + omc * n1 * n1;
+        e.R[5] = sa * n0;
+        e.R[6] = sa * n1;
+        e.R[7] = -sa * n0;
+        e.R[8] = ca;
+        // dR/dα = −sin α·I + sin α·n nᵀ − cos α·[n]x
+        e.D[0] = -sa + sa * n0 * n0;
+        e.D[1] = sa * n0 * n1;
+        e.D[2] = -ca * n1;
+        e.D[3] = sa * n0 * n1;
+        e.D[4] = -sa + sa * n1 * n1;
+        e.D[5] = ca * n0;
+        e.D[6] = ca * n1;
+        e.D[7] = -ca * n0;
+        e.D[8] = -sa;
+        e.param = s.param;
+        e.pad = 0;
+        out[i] = e;
+    }
+}
+
+struct AdjArgs {
+    const AdjEvent *ev;
+    int64_t n_events;
+    const RfEntry *rf;
+    const double *cls;
+    int32_t n_cls;
+    int32_t seg;
+    const double *demod;
+    const double *params;
+    int64_t n_spins, n_pad;
+    double *ckpt;     // n_seg x 3 x n_spins
+    double *signal;   // forward
+    const double *h;  // backward: dL/ds, 2 per sample
+    double *d_rho, *d_t1, *d_t2, *d_rf;
+    int32_t n_params;
+};
+
+struct SpinP {
+    double x, y, z, df, rho, r1, r2;
+};
+
+__device__ __forceinline__ SpinP load_spin(const AdjArgs &a, int64_t s) {
+    SpinP p{};
+    if (s < a.n_spins) {
+        const int64_t np = a.n_pad;
+        p.x = a.params[P_X * np + s];
+        p.y = a.params[P_Y * np + s];
+        p.z = a.params[P_Z * np + s];
+        p.df = a.params[P_DF * np + s];
+        p.rho = a.params[P_RHO * np + s];
+        p.r1 = a.params[P_R1 * np + s];
+        p.r2 = a.params[P_R2 * np + s];
+    }
+    return p;
+}
+
+// per-spin class table in shared memory: w (complex, with E2) and E1, per class
+__device__ __forceinline__ void fill_classes(const AdjArgs &a, const SpinP &p, double *tab) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int c = 0; c < a.n_cls; ++c) {
+        const double kx = a.cls[4 * c], ky = a.cls[4 * c + 1], kz = a.cls[4 * c + 2], dt = a.cls[4 * c + 3];
+        double th = kx * p.x + ky * p.y + kz * p.z + p.df * dt;
+        th -= rint(th);
+        double sn, cs;
+        sincospi(2.0 * th, &sn, &cs);
+        const double e2 = exp(-dt * p.r2);
+        tab[(3 * c + 0) * nt + t] = e2 * cs;
+        tab[(3 * c + 1) * nt + t] = -e2 * sn;
+        tab[(3 * c + 2) * nt + t] = exp(-dt * p.r1);
+    }
+}
+
+// precession + relaxation factors of one event for this spin: w = E2·exp(−j2πφ), E1
+__device__ __forceinline__ void factors(const AdjEvent &e, const SpinP &p, const double *tab, double &wr, double &wi,
+                                       double &e1) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (e.flags & A_CLS) {
+        wr = tab[(3 * e.cls + 0) * nt + t];
+        wi = tab[(3 * e.cls + 1) * nt + t];
+        e1 = tab[(3 * e.cls + 2) * nt + t];
+    } else if (e.flags & A_INL) {
+        double th = e.k[0] * p.x + e.k[1] * p.y + e.k[2] * p.z + p.df * e.dt;
+        th -= rint(th);
+        double sn, cs;
+        sincospi(2.0 * th, &sn, &cs);
+        const double e2 = exp(-e.dt * p.r2);
+        wr = e2 * cs;
+        wi = -e2 * sn;
+        e1 = exp(-e.dt * p.r1);
+    } else {
+        wr = 1.0;
+        wi = 0.0;
+        e1 = 1.0;
+    }
+}
+
+__device__ __forceinline__ void apply_rf(const double *R, double M[3]) {
+    const double x = R[0] * M[0] + R[1] * M[1] + R[2] * M[2];
+    const double y = R[3] * M[0] + R[4] * M[1] + R[5] * M[2];
+    const double z = R[6] * M[0] + R[7] * M[1] + R[8] * M[2];
+    M[0] = x;
+    M[1] = y;
+    M[2] = z;
+}
+
+// forward step of one event (Eq. 4.1)
+__device__ __forceinline__ void step(const AdjArgs &a, const AdjEvent &e, const SpinP &p, const double *tab,
+                                     double M[3]) {
+    if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, M);
+    double wr, wi, e1;
+    factors(e, p, tab, wr, wi, e1);
+    const double x = M[0] * wr - M[1] * wi;
+    const double y = M[0] * wi + M[1] * wr;
+    M[0] = x;
+    M[1] = y;
+    M[2] = e1 * M[2] + p.rho * (1.0 - e1);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// stage events [e0, e0 + m) of the program into shared memory (all threads)
+__device__ __forceinline__ void stage(const AdjArgs &a, int64_t e0, int m, AdjEvent *sev) {
+    __syncthreads();
+    const int4 *src = reinterpret_cast<const int4 *>(a.ev + e0);
+    int4 *dst = reinterpret_cast<int4 *>(sev);
+    for (int q = threadIdx.x; q < m * 4; q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ADJ_THREADS) adj_forward_kernel(const AdjArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    AdjEvent *sev = reinterpret_cast<AdjEvent *>(smem);
+    double *tab = reinterpret_cast<double *>(smem + sizeof(AdjEvent) * a.seg);
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const SpinP p = load_spin(a, s);
+    fill_classes(a, p, tab);
+    double M[3] = {0.0, 0.0, p.rho};
+    const int lane = threadIdx.x & 31;
+    for (int64_t e0 = 0, sg = 0; e0 < a.n_events; e0 += a.seg, ++sg) {
+        const int m = (int)min((int64_t)a.seg, a.n_events - e0);
+        stage(a, e0, m, sev);
+        if (s < a.n_spins) {
+            double *ck = a.ckpt + sg * 3 * a.n_spins;
+            ck[s] = M[0];
+            ck[a.n_spins + s] = M[1];
+            ck[2 * a.n_spins + s] = M[2];
+        }
+        for (int i = 0; i < m; ++i) {
+            const AdjEvent &e = sev[i];
+            step(a, e, p, tab, M);
+            if (e.flags & A_ADC) {
+                const double sx = warp_sum(M[0]), sy = warp_sum(M[1]);
+                if (lane == 0) {
+                    const double cr = a.demod[2 * e.adc], ci = a.demod[2 * e.adc + 1];
+                    atomicAdd(a.signal + 2 * e.adc, sx * cr - sy * ci);
+                    atomicAdd(a.signal + 2 * e.adc + 1, sx * ci + sy * cr);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    AdjEvent *sev = reinterpret_cast<AdjEvent *>(smem);
+    double *tab = reinterpret_cast<double *>(smem + sizeof(AdjEvent) * a.seg);
+    double *grf = tab + 3 * a.n_cls * blockDim.x;  // block's RF-parameter gradient
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const SpinP p = load_spin(a, s);
+    fill_classes(a, p, tab);
+    for (int q = threadIdx.x; q < a.n_params; q += blockDim.x) grf[q] = 0.0;
+    const int lane = threadIdx.x & 31;
+    const bool valid = s < a.n_spins;
+    double buf[ADJ_MAX_SEG][3];  // states at the start of each event of the segment
+    double L[3] = {0.0, 0.0, 0.0};
+    double g_rho = 0.0, g_r1 = 0.0, g_r2 = 0.0;
+    const int64_t n_seg = (a.n_events + a.seg - 1) / a.seg;
+    for (int64_t sg = n_seg - 1; sg >= 0; --sg) {
+        const int64_t e0 = sg * a.seg;
+        const int m = (int)min((int64_t)a.seg, a.n_events - e0);
+        stage(a, e0, m, sev);
+        double M[3];
+        if (valid) {
+            const double *ck = a.ckpt + sg * 3 * a.n_spins;
+            M[0] = ck[s];
+            M[1] = ck[a.n_spins + s];
+            M[2] = ck[2 * a.n_spins + s];
+        } else {
+            M[0] = M[1] = M[2] = 0.0;
+        }
+        for (int i = 0; i < m; ++i) {
+            buf[i][0] = M[0];
+            buf[i][1] = M[1];
+            buf[i][2] = M[2];
+            step(a, sev[i], p, tab, M);
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            const AdjEvent &e = sev[i];
+            if (e.flags & A_ADC) {  // λ += conj(d_j)·h_j
+                const double cr = a.demod[2 * e.adc], ci = -a.demod[2 * e.adc + 1];
+                const double hr = a.h[2 * e.adc], hi = a.h[2 * e.adc + 1];
+                L[0] += cr * hr - ci * hi;
+                L[1] += cr * hi + ci * hr;
+            }
+            // state before the event, and after its pulse
+            double Mn[3] = {buf[i][0], buf[i][1], buf[i][2]};
+            double Ma[3] = {Mn[0], Mn[1], Mn[2]};
+            if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, Ma);
+            double wr, wi, e1;
+            factors(e, p, tab, wr, wi, e1);
+            // parameter gradients through P (λ is the adjoint after the event)
+            const double mx = Ma[0] * wr - Ma[1] * wi, my = Ma[0] * wi + Ma[1] * wr;
+            g_r2 += -e.dt * (L[0] * mx + L[1] * my);
+            g_r1 += -e.dt * e1 * (Ma[2] - p.rho) * L[2];
+            g_rho += (1.0 - e1) * L[2];
+            // λ_a = Pᵀ λ: conj(w)·λ on the transverse part, E1 on z
+            const double lax = L[0] * wr + L[1] * wi, lay = -L[0] * wi + L[1] * wr, laz = e1 * L[2];
+            if (e.flags & A_RF) {
+                const RfEntry &rf = a.rf[e.rf];
+                if (rf.param >= 0) {
+                    // dL/dα = λ_aᵀ·(dR/dα)·M_n, reduced over the warp, then the block (shared atomics)
+                    const double *D = rf.D;
+                    const double dx = D[0] * Mn[0] + D[1] * Mn[1] + D[2] * Mn[2];
+                    const double dy = D[3] * Mn[0] + D[4] * Mn[1] + D[5] * Mn[2];
+                    const double dz = D[6] * Mn[0] + D[7] * Mn[1] + D[8] * Mn[2];
+                    const double g = warp_sum(lax * dx + lay * dy + laz * dz);
+                    if (lane == 0) atomicAdd(&grf[rf.param], g);
+                }
+                // λ_n = Rᵀ λ_a
+                L[0] = rf.R[0] * lax + rf.R[3] * lay + rf.R[6] * laz;
+                L[1] = rf.R[1] * lax + rf.R[4] * lay + rf.R[7] * laz;
+                L[2] = rf.R[2] * lax + rf.R[5] * lay + rf.R[8] * laz;
+            } else {
+                L[0] = lax;
+                L[1] = lay;
+                L[2] = laz;
+            }
+        }
+    }
+    g_rho += L[2];  // initial state (0, 0, M0)
+    __syncthreads();
+    if (a.d_rf)
+        for (int q = threadIdx.x; q < a.n_params; q += blockDim.x)
+            if (grf[q] != 0.0) atomicAdd(a.d_rf + q, grf[q]);
+    if (valid) {
+        // dL/dT = dL/dR · dR/dT = −dL/dR / T², i.e. −dL/dR · R²; T = ∞ (R = 0) gives 0
+        if (a.d_rho) a.d_rho[s] = g_rho;
+        if (a.d_t1) a.d_t1[s] = -g_r1 * p.r1 * p.r1;
+        if (a.d_t2) a.d_t2[s] = -g_r2 * p.r2 * p.r2;
+    }
+}
+
+}  // namespace
+
+namespace {
+
+mrsim_status afail(mrsim_ctx *ctx, mrsim_status st, const std::string &m) {
+    if (ctx) ctx->err = m;
+    return st;
+}
+
+bool dev_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t adj_smem(const mrsim_adjoint *adj, bool backward) {
+    return sizeof(AdjEvent) * adj->seg + sizeof(double) * 3 * adj->n_cls * ADJ_THREADS +
+           (backward ? sizeof(double) * (size_t)adj->n_params : 0);
+}
+
+AdjArgs adj_args(const mrsim_adjoint *adj, const mrsim_phantom *ph) {
+    AdjArgs a{};
+    a.ev = adj->d_ev;
+    a.n_events = adj->n_events;
+    a.rf = adj->d_rf;
+    a.cls = adj->d_cls;
+    a.n_cls = adj->n_cls;
+    a.seg = adj->seg;
+    a.demod = adj->d_demod;
+    a.params = ph->params;
+    a.n_spins = ph->n;
+    a.n_pad = ph->n_pad;
+    a.ckpt = adj->d_ckpt;
+    a.n_params = adj->n_params;
+    return a;
+}
+
+mrsim_status prepare_rf(mrsim_adjoint *adj, const double *rf_values, cudaStream_t st) {
+    mrsim_ctx *ctx = adj->ctx;
+    if (adj->n_params > 0 && !dev_ptr(rf_values)) return afail(ctx, MRSIM_EINVAL, "rf_values must be device memory");
+    if (adj->n_rf == 0) return MRSIM_OK;
+    rf_table_kernel<<<(adj->n_rf + 127) / 128, 128, 0, st>>>(adj->d_spec, adj->n_rf, rf_values, adj->d_rf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("rf table: ") + cudaGetErrorString(e));
+    return MRSIM_OK;
+}
+
+template <class T>
+cudaError_t put(T **d, const std::vector<T> &v) {
+    *d = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(d, v.size() * sizeof(T));
+    if (e == cudaSuccess) e = cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrsim_status mrsim_adjoint_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events, double gamma,
+                                  const int32_t *rf_param, int32_t n_params, int32_t ckpt_every,
+                                  mrsim_adjoint **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    // the forward compiler validates the event list with the same rules
+    {
+        Compiled c;
+        std::string err;
+        int rc = compile_sequence(events, n_events, gamma, c, err);
+        if (rc != MRSIM_OK) return afail(ctx, (mrsim_status)rc, err);
+    }
+    if (n_params < 0 || (n_params > 0 && !rf_param)) return afail(ctx, MRSIM_EINVAL, "invalid rf_param / n_params");
+    if (ckpt_every == 0) ckpt_every = 64;
+    if (ckpt_every < 1 || ckpt_every > ADJ_MAX_SEG)
+        return afail(ctx, MRSIM_EINVAL, "ckpt_every must be in [1, " + std::to_string(ADJ_MAX_SEG) + "]");
+    std::vector<AdjEvent> ev((size_t)n_events);
+    std::vector<RfSpec> spec;
+    std::vector<double> demod;
+    std::map<std::array<double, 4>, std::pair<int64_t, int64_t>> uses;
+    for (int64_t i = 0; i < n_events; ++i) {
+        const mrsim_event &e = events[i];
+        const std::array<double, 4> key = {gamma * e.gx * e.dt, gamma * e.gy * e.dt, gamma * e.gz * e.dt, e.dt};
+        if (e.dt > 0.0) {
+            auto it = uses.find(key);
+            if (it == uses.end())
+                uses[key] = {1, i};
+            else
+                ++it->second.first;
+        }
+    }
+    // up to 16 recurring intervals become per-spin classes (most frequent first)
+    std::vector<std::pair<std::array<double, 4>, std::pair<int64_t, int64_t>>> v(uses.begin(), uses.end());
+    std::sort(v.begin(), v.end(), [](const auto &a, const auto &b) {
+        return a.second.first != b.second.first ? a.second.first > b.second.first : a.second.second < b.second.second;
+    });
+    std::map<std::array<double, 4>, int> cls;
+    std::vector<double> ctab;
+    for (auto &kv : v) {
+        if ((int)cls.size() >= ADJ_MAX_CLASSES || kv.second.first < 2) break;
+        cls[kv.first] = (int)cls.size();
+        for (double x : kv.first) ctab.push_back(x);
+    }
+    int64_t j = 0;
+    for (int64_t i = 0; i < n_events; ++i) {
+        const mrsim_event &e = events[i];
+        AdjEvent a{};
+        const int32_t prm = rf_param ? rf_param[i] : -1;
+        if (prm >= n_params) return afail(ctx, MRSIM_EINVAL, "rf_param index out of range at event " + std::to_string(i));
+        if (e.rf_flip != 0.0 || prm >= 0) {
+            a.flags |= A_RF;
+            a.rf = (int32_t)spec.size();
+            spec.push_back(RfSpec{e.rf_flip, e.rf_phase, prm, 0});
+        }
+        const std::array<double, 4> key = {gamma * e.gx * e.dt, gamma * e.gy * e.dt, gamma * e.gz * e.dt, e.dt};
+        a.dt = e.dt;
+        if (e.dt > 0.0) {
+            auto c = cls.find(key);
+            if (c != cls.end()) {
+                a.flags |= A_CLS;
+                a.cls = c->second;
+            } else {
+                a.flags |= A_INL;
+                a.k[0] = key[0];
+                a.k[1] = key[1];
+                a.k[2] = key[2];
+            }
+        }
+        if (e.adc) {
+            a.flags |= A_ADC;
+            a.adc = (int32_t)j++;
+            demod.push_back(std::cos(e.adc_phase));
+            demod.push_back(-std::sin(e.adc_phase));
+        }
+        ev[(size_t)i] = a;
+    }
+    cudaSetDevice(ctx->device);
+    mrsim_adjoint *adj = new (std::nothrow) mrsim_adjoint();
+    if (!adj) return afail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    adj->ctx = ctx;
+    adj->n_events = n_events;
+    adj->n_adc = j;
+    adj->n_params = n_params;
+    adj->seg = ckpt_every;
+    adj->n_rf = (int32_t)spec.size();
+    adj->n_cls = (int32_t)cls.size();
+    cudaError_t e = put(&adj->d_ev, ev);
+    if (e == cudaSuccess) e = put(&adj->d_spec, spec);
+    if (e == cudaSuccess && !spec.empty()) e = cudaMalloc(&adj->d_rf, spec.size() * sizeof(RfEntry));
+    if (e == cudaSuccess) e = put(&adj->d_cls, ctab);
+    if (e == cudaSuccess) e = put(&adj->d_demod, demod);
+    if (e != cudaSuccess) {
+        mrsim_adjoint_destroy(adj);
+        return afail(ctx, MRSIM_ENOMEM, std::string("adjoint program: ") + cudaGetErrorString(e));
+    }
+    if (adj_smem(adj, true) > (size_t)ctx->max_smem_optin) {
+        mrsim_adjoint_destroy(adj);
+        return afail(ctx, MRSIM_EUNSUPPORTED, "adjoint program needs more shared memory than the device has");
+    }
+    *out = adj;
+    return MRSIM_OK;
+}
+
+int64_t mrsim_adjoint_num_adc(const mrsim_adjoint *adj) { return adj ? adj->n_adc : -1; }
+
+mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, const double *rf_values,
+                                   void *stream, double *signal_out) {
+    if (!adj) return MRSIM_EINVAL;
+    mrsim_ctx *ctx = adj->ctx;
+    if (!ph || ph->ctx != ctx) return afail(ctx, MRSIM_EINVAL, "NULL phantom or another context");
+    if (adj->n_adc > 0 && !dev_ptr(signal_out)) return afail(ctx, MRSIM_EINVAL, "signal_out must be device memory");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n_seg = (adj->n_events + adj->seg - 1) / adj->seg;
+    const size_t need = (size_t)std::max<int64_t>(n_seg, 1) * 3 * (size_t)std::max<int64_t>(ph->n, 1);
+    if (need > adj->ckpt_cap) {
+        cudaFree(adj->d_ckpt);
+        adj->d_ckpt = nullptr;
+        adj->ckpt_cap = 0;
+        cudaError_t e = cudaMalloc(&adj->d_ckpt, need * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return afail(ctx, MRSIM_ENOMEM, "checkpoint storage: " + std::to_string(need * 8) + " bytes");
+        }
+        adj->ckpt_cap = need;
+    }
+    mrsim_status rs = prepare_rf(adj, rf_values, st);
+    if (rs != MRSIM_OK) return rs;
+    if (adj->n_adc > 0) {
+        cudaError_t e = cudaMemsetAsync(signal_out, 0, 16 * (size_t)adj->n_adc, st);
+        if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, "clear signal");
+    }
+    adj->last_ph = ph;
+    adj->last_n = ph->n;
+    if (ph->n == 0) return MRSIM_OK;
+    AdjArgs a = adj_args(adj, ph);
+    a.signal = signal_out;
+    const size_t smem = adj_smem(adj, false);
+    cudaFuncSetAttribute(adj_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = (ph->n + ADJ_THREADS - 1) / ADJ_THREADS;
+    adj_forward_kernel<<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph, const double *rf_values,
+                                    const double *dl_dsignal, void *stream, double *d_rho, double *d_t1,
+                                    double *d_t2, double *d_rf) {
+    if (!adj) return MRSIM_EINVAL;
+    mrsim_ctx *ctx = adj->ctx;
+    if (!ph || ph != adj->last_ph || ph->n != adj->last_n)
+        return afail(ctx, MRSIM_EINVAL, "backward needs the phantom of the last forward call");
+    if (adj->n_adc > 0 && !dev_ptr(dl_dsignal)) return afail(ctx, MRSIM_EINVAL, "dl_dsignal must be device memory");
+    for (const double *q : {(const double *)d_rho, (const double *)d_t1, (const double *)d_t2, (const double *)d_rf})
+        if (q && !dev_ptr(q)) return afail(ctx, MRSIM_EINVAL, "gradient outputs must be device memory");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    mrsim_status rs = prepare_rf(adj, rf_values, st);
+    if (rs != MRSIM_OK) return rs;
+    if (d_rf && adj->n_params > 0) {
+        cudaError_t e = cudaMemsetAsync(d_rf, 0, sizeof(double) * (size_t)adj->n_params, st);
+        if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, "clear d_rf");
+    }
+    if (ph->n == 0) return MRSIM_OK;
+    AdjArgs a = adj_args(adj, ph);
+    a.h = dl_dsignal;
+    a.d_rho = d_rho;
+    a.d_t1 = d_t1;
+    a.d_t2 = d_t2;
+    a.d_rf = d_rf;
+    const size_t smem = adj_smem(adj, true);
+    cudaFuncSetAttribute(adj_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = (ph->n + ADJ_THREADS - 1) / ADJ_THREADS;
+    adj_backward_kernel<<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("adjoint backward: ") + cudaGetErrorString(e));
+    return MRSIM_OK;
+}
+
+void mrsim_adjoint_destroy(mrsim_adjoint *adj) {
+    if (!adj) return;
+    cudaSetDevice(adj->ctx->device);
+    cudaFree(adj->d_ev);
+    cudaFree(adj->d_spec);
+    cudaFree(adj->d_rf);
+    cudaFree(adj->d_cls);
+    cudaFree(adj->d_demod);
+    cudaFree(adj->d_ckpt);
+    delete adj;
+}
+
+}  // extern "C"

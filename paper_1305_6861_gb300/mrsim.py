@@ -36,6 +36,8 @@ EXPORTS = (
     "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
+    "mrsim_adjoint_create", "mrsim_adjoint_num_adc", "mrsim_adjoint_forward", "mrsim_adjoint_backward",
+    "mrsim_adjoint_destroy",
 )
 
 
@@ -113,6 +115,11 @@ def lib():
             "mrsim_batch_destroy": (None, [vp]),
             "mrsim_simulate_batch": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, vp]),
             "mrsim_simulate_batch_static": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, vp, i32, i32]),
+            "mrsim_adjoint_create": (ctypes.c_int, [vp, i64, vp, dbl, vp, i32, i32, P(vp)]),
+            "mrsim_adjoint_num_adc": (i64, [vp]),
+            "mrsim_adjoint_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+            "mrsim_adjoint_backward": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "mrsim_adjoint_destroy": (None, [vp]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
         }
         for name, (res, args) in sig.items():
@@ -306,6 +313,46 @@ def simulate_batch_static(ctx: Context, phantoms, seqs, precision: int = FP32, o
     os_ = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
     ctx.check(lib().mrsim_simulate_batch_static(ctx.h, n, ph, sq, int(precision), _stream(stream), os_,
                                                 int(spins_per_thread), int(threads_per_block)))
+
+
+class Adjoint:
+    """Compiled event list for differentiation (float64).  rf_param: None or one int per event
+    (index of the learnable flip angle that event uses, -1 = its own flip)."""
+
+    def __init__(self, ctx: Context, events, gamma_hz_per_t: float, rf_param=None, n_params: int = 0,
+                 ckpt_every: int = 64):
+        self.ctx = ctx
+        ev = np.ascontiguousarray(events)
+        if ev.dtype != EVENT_DTYPE:
+            ev = ev.astype(EVENT_DTYPE)
+        rp = None if rf_param is None else np.ascontiguousarray(rf_param, dtype=np.int32)
+        self._keep = (ev, rp)
+        h = ctypes.c_void_p()
+        ctx.check(lib().mrsim_adjoint_create(ctx.h, ev.shape[0], _ptr(ev), float(gamma_hz_per_t), _ptr(rp),
+                                             int(n_params), int(ckpt_every), ctypes.byref(h)))
+        self.h = h
+        self.n_params = int(n_params)
+        self.n_adc = int(lib().mrsim_adjoint_num_adc(h))
+
+    def forward(self, phantom: Phantom, rf_values=None, out=None, stream=None):
+        self.ctx.check(lib().mrsim_adjoint_forward(self.h, phantom.h, _ptr(rf_values), _stream(stream), _ptr(out)))
+        return out
+
+    def backward(self, phantom: Phantom, dl_dsignal, rf_values=None, d_rho=None, d_t1=None, d_t2=None, d_rf=None,
+                 stream=None):
+        self.ctx.check(lib().mrsim_adjoint_backward(self.h, phantom.h, _ptr(rf_values), _ptr(dl_dsignal),
+                                                    _stream(stream), _ptr(d_rho), _ptr(d_t1), _ptr(d_t2), _ptr(d_rf)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None):

@@ -1,0 +1,164 @@
+"""Adjoint (backward-in-time) gradients on the GPU against the oracle's forward-mode gradient and
+central finite differences (h = 1e-4 relative, float64), and the autograd.Function."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1305_6861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def M(mrsim_lib):
+    return mrsim_lib
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def shaped_case(seed, n_sp, n_rf=16, n_tr=3, n_read=8):
+    rng = np.random.default_rng(seed)
+    ph = W.random_phantom(n_sp, rng, inf_frac=0.1)
+    ph.dw[:] = 2 * math.pi * rng.uniform(-50, 50, n_sp)
+    base = W.sinc_pulse(0.6, n_rf, 4.0)
+    rows, params = [], []
+    for tr in range(n_tr):
+        for i, a in enumerate(base):
+            rows.append((20e-6, 0, 0, 2e-3, float(a), 0.3 * tr, 0, 0.0))
+            params.append(i)
+        rows.append((1e-3, -1e-3, 2e-3 * (tr - 1), 0, 0, 0, 0, 0.0))
+        rows += [(20e-6, 2e-3, 0, 0, 0, 0, 1, 0.3 * tr)] * n_read
+        params += [-1] * (1 + n_read)
+        rows.append((4e-3, 0, 0, 0, 0, 0, 0, 0.0))
+        params.append(-1)
+    ev = W.make_events(rows)
+    rf = np.array(base) * rng.uniform(0.8, 1.2, n_rf)
+    return ph, ev, np.array(params, dtype=np.int32), rf, rng
+
+
+def gpu_grads(M, ctx, torch, ph, ev, params, rf, h, ckpt=64):
+    adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf), ckpt_every=ckpt)
+    P = M.Phantom.from_workload_phantom(ctx, ph)
+    dev = torch.device("cuda:0")
+    rfd = torch.from_numpy(np.asarray(rf, dtype=np.float64)).to(dev)
+    sig = torch.zeros(2 * adj.n_adc, dtype=torch.float64, device=dev)
+    adj.forward(P, rfd, sig)
+    hd = torch.from_numpy(np.ascontiguousarray(np.asarray(h, dtype=np.complex128)).view(np.float64)).to(dev)
+    out = [torch.zeros(ph.n, dtype=torch.float64, device=dev) for _ in range(3)]
+    drf = torch.zeros(len(rf), dtype=torch.float64, device=dev)
+    adj.backward(P, hd, rfd, *out, drf)
+    torch.cuda.synchronize()
+    ctx.stream_status()
+    return sig.cpu().numpy().view(np.complex128), [o.cpu().numpy() for o in out], drf.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed,n_sp,ckpt", [(0, 40, 64), (1, 300, 7), (2, 1, 1), (3, 129, 128)])
+def test_adjoint_matches_oracle_gradient(M, ctx, torch, oracle_mod, seed, n_sp, ckpt):
+    ph, ev, params, rf, rng = shaped_case(seed, n_sp)
+    sig_ref = oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf)
+    target = oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf * 1.1) * 0.9
+    h = 2 * (sig_ref - target)
+    g_rho, g_t1, g_t2, g_rf = oracle_mod.gradient(ph, ev, W.GAMMA_BAR, h, params, rf, list(range(len(rf))))
+    sig, (a_rho, a_t1, a_t2), a_rf = gpu_grads(M, ctx, torch, ph, ev, params, rf, h, ckpt)
+    assert rel(sig, sig_ref) <= 1e-12
+    assert rel(a_rho, g_rho) <= 1e-10
+    assert rel(a_t1, g_t1) <= 1e-10
+    assert rel(a_t2, g_t2) <= 1e-10
+    assert rel(a_rf, g_rf) <= 1e-10
+
+
+def test_adjoint_config5_full_size(M, ctx, torch, oracle_mod):
+    """C5 (128² spins, 256 learnable sub-pulses, 49 408 events): the adjoint against the oracle's
+    gradient on sampled spins (per-spin gradients depend only on h and the spin) and against
+    central differences of the GPU float64 forward for sampled RF coordinates."""
+    w, tgt, rf0 = W.config5()
+    ev = w.sequence.events
+    params = np.full(len(ev), -1, dtype=np.int32)
+    idx = W.rf_event_index(w.sequence)
+    params[idx] = np.tile(np.arange(len(rf0), dtype=np.int32), idx.size // len(rf0))
+    dev = torch.device("cuda:0")
+    adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf0), ckpt_every=64)
+    P = M.Phantom.from_workload_phantom(ctx, w.phantom)
+    PT = M.Phantom.from_workload_phantom(ctx, tgt)
+    rfd = torch.from_numpy(rf0.copy()).to(dev)
+    sig = torch.zeros(2 * adj.n_adc, dtype=torch.float64, device=dev)
+    tsig = torch.zeros_like(sig)
+    adj.forward(PT, rfd, tsig)
+    adj.forward(P, rfd, sig)
+    torch.cuda.synchronize()
+    # the adjoint's forward equals the optimised forward path on the same sequence
+    seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    s_fast = M.simulate(ctx, P, seq, M.FP64)
+    s = sig.cpu().numpy().view(np.complex128)
+    assert rel(s, s_fast) <= 1e-12
+    t = tsig.cpu().numpy().view(np.complex128)
+    h = 2 * (s - t)
+    hd = torch.from_numpy(np.ascontiguousarray(h).view(np.float64)).to(dev)
+    out = [torch.zeros(w.phantom.n, dtype=torch.float64, device=dev) for _ in range(3)]
+    drf = torch.zeros(len(rf0), dtype=torch.float64, device=dev)
+    adj.backward(P, hd, rfd, *out, drf)
+    torch.cuda.synchronize()
+    ctx.stream_status()
+    a_rho, a_t1, a_t2 = [o.cpu().numpy() for o in out]
+    a_rf = drf.cpu().numpy()
+    sel = np.sort(np.random.default_rng(5).choice(w.phantom.n, 256, replace=False))
+    sub = w.phantom.subset(sel)
+    g_rho, g_t1, g_t2, _ = oracle_mod.gradient(sub, ev, W.GAMMA_BAR, h, params, rf0)
+    assert rel(a_rho[sel], g_rho) <= 1e-9
+    assert rel(a_t1[sel], g_t1) <= 1e-9
+    assert rel(a_t2[sel], g_t2) <= 1e-9
+    # central differences of L = |s - t|² in the RF coordinates, GPU float64 forward
+    def loss(rfv):
+        adj.forward(P, torch.from_numpy(rfv).to(dev), sig)
+        torch.cuda.synchronize()
+        return float(np.sum(np.abs(sig.cpu().numpy().view(np.complex128) - t) ** 2))
+    for p in (0, 100, 128, 200):
+        step = 1e-4 * max(abs(rf0[p]), 1e-3)
+        rp, rm = rf0.copy(), rf0.copy()
+        rp[p] += step
+        rm[p] -= step
+        fd = (loss(rp) - loss(rm)) / (2 * step)
+        assert abs(fd - a_rf[p]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(a_rf).max()), (p, fd, a_rf[p])
+
+
+def test_autograd_function(M, ctx, torch, oracle_mod):
+    from paper_1305_6861_gb300 import autograd as AG
+
+    ph, ev, params, rf, rng = shaped_case(9, 24)
+    dev = torch.device("cuda:0")
+    adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf))
+    geom = [torch.from_numpy(a).to(dev) for a in (ph.x, ph.y, ph.z, ph.dw)]
+    ph.t1[:] = np.minimum(ph.t1, 3.0)
+    ph.t2[:] = np.minimum(ph.t2, 0.5)
+    leaf = [torch.from_numpy(a.copy()).to(dev).requires_grad_(True) for a in (ph.rho, ph.t1, ph.t2, rf)]
+    target = torch.from_numpy(np.ascontiguousarray(oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf * 1.05))
+                              .view(np.float64).reshape(-1, 2)).to(dev)
+    s = AG.signal(adj, *geom, *leaf)
+    loss = ((s - target) ** 2).sum()
+    loss.backward()
+    h = 2 * (s.detach().cpu().numpy().view(np.complex128).ravel() - target.cpu().numpy().view(np.complex128).ravel())
+    g = oracle_mod.gradient(ph, ev, W.GAMMA_BAR, h, params, rf, list(range(len(rf))))
+    for got, want in zip([t.grad.cpu().numpy() for t in leaf], g):
+        assert rel(got, want) <= 1e-10
+    # torch's own numerical check on a few coordinates
+    small = [t.detach()[:3].clone().requires_grad_(True) for t in leaf[:3]] + [leaf[3].detach().clone().requires_grad_(True)]
+    geom3 = [g_[:3].contiguous() for g_ in geom]
+    f = lambda a, b, c, d: AG.signal(adj, *geom3, a, b, c, d)
+    assert torch.autograd.gradcheck(f, tuple(small), eps=1e-6, atol=1e-6, rtol=1e-5)
