@@ -248,6 +248,58 @@ def run_batch(args):
     return 0
 
 
+def run_adjoint(args):
+    """Differentiation workload (C5): one step = adjoint forward (signal + checkpoints) and backward
+    (gradients in M0, T1, T2 of every spin and in the 256 learnable RF flips), float64."""
+    import torch
+
+    from paper_1305_6861_gb300 import mrsim as M
+
+    torch.cuda.set_device(0)
+    w, tgt, rf0 = W.config5()
+    ev = w.sequence.events
+    params = np.full(len(ev), -1, dtype=np.int32)
+    idx = W.rf_event_index(w.sequence)
+    params[idx] = np.tile(np.arange(len(rf0), dtype=np.int32), idx.size // len(rf0))
+    ctx = M.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf0), ckpt_every=64)
+    P = M.Phantom(ctx, [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()], stream=stream)
+    rfd = torch.from_numpy(rf0.copy()).to(dev)
+    sig = torch.zeros(2 * adj.n_adc, dtype=torch.float64, device=dev)
+    target = torch.zeros_like(sig)
+    PT = M.Phantom(ctx, [torch.from_numpy(a).to(dev) for a in tgt.arrays()], stream=stream)
+    adj.forward(PT, rfd, target, stream)
+    grads = [torch.zeros(w.phantom.n, dtype=torch.float64, device=dev) for _ in range(3)]
+    drf = torch.zeros(len(rf0), dtype=torch.float64, device=dev)
+
+    def step():
+        adj.forward(P, rfd, sig, stream)
+        h = 2 * (sig - target)
+        adj.backward(P, h, rfd, *grads, drf, stream)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.stream_status(stream)
+    ev0 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev0[i][0].record(stream)
+        step()
+        ev0[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.stream_status(stream)
+    ms = sum(a.elapsed_time(b) for a, b in ev0) / args.steps
+    line = {"metric": "spin-steps/s of forward+backward (adjoint) at 1 GB300", "value": w.spin_steps / (ms * 1e-3),
+            "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": len(ev), "n_rf_params": len(rf0),
+                       "ckpt_every": 64, "step": "adjoint forward + backward"},
+            "gpu_launches": 4 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -255,6 +307,8 @@ def run_ours(args):
 
     if args.workload == "c4":
         return run_batch(args)
+    if args.workload == "c5":
+        return run_adjoint(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -424,7 +478,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c2")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c2")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--spins-per-thread", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
