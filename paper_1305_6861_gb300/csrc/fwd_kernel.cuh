@@ -77,37 +77,131 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s for one 4 KB chunk: on
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int RED_STRIDE = SAMPLE_WINDOW_F64 + 16;  // float64: per-warp, per-component window row
 constexpr int WIN_STRIDE = SAMPLE_WINDOW_F32 + 16;  // float32: block-wide window, per component
-constexpr int TILE_STRIDE = 36;                     // float32: row of a warp's 32x32 transpose tile
 
 __device__ __forceinline__ void red_shared_add(float *p, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(su32(p)), "f"(v) : "memory");
 }
 
-// Shared-memory transpose that leaves lane l with the warp-wide sum of v[l]: every lane writes
-// its 32 values down tile column `lane` (32 conflict-free stores that nothing waits on), reads
-// tile row l as 8 conflict-free 16-byte loads and adds the 32 values as a tree: 71 instructions
-// instead of the 124 of a shuffle butterfly.
-__device__ __forceinline__ float tile_reduce32(float (&v)[32], int lane, float *tile) {
+// ---- packed float32 pairs -------------------------------------------------------------------
+// sm_100-class SMs execute two float32 lanes per instruction (fma/mul/add/sub .rn.f32x2 on a
+// 64-bit register pair).  A thread with K >= 2 float32 spins keeps each quantity as K/2 pairs,
+// which halves the instructions issued for rotations, relaxations and spin sums; every lane is
+// rounded exactly like the scalar operation.
+struct f2 {
+    unsigned long long r;
+};
+__device__ __forceinline__ f2 pk2(float a, float b) {
+    f2 o;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(a), "f"(b));
+    return o;
+}
+__device__ __forceinline__ void unpk2(f2 a, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.r));
+}
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+__device__ __forceinline__ f2 vmul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ f2 vadd(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ f2 vsub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ f2 vneg(f2 a) { return vmul(a, pk2(-1.0f, -1.0f)); }
+__device__ __forceinline__ float hsum(f2 a) {
+    float x, y;
+    unpk2(a, x, y);
+    return x + y;
+}
+__device__ __forceinline__ float lane_of(f2 a, int h) {
+    float x, y;
+    unpk2(a, x, y);
+    return h ? y : x;
+}
+__device__ __forceinline__ void splat(f2 &o, float x) { o = pk2(x, x); }
+__device__ __forceinline__ void set_lanes(f2 &o, const float (&x)[2]) { o = pk2(x[0], x[1]); }
+
+// the same operations on one scalar lane (float64, and float32 with one spin per thread)
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+template <typename T>
+__device__ __forceinline__ T vmul(T a, T b) { return a * b; }
+template <typename T>
+__device__ __forceinline__ T vadd(T a, T b) { return a + b; }
+template <typename T>
+__device__ __forceinline__ T vsub(T a, T b) { return a - b; }
+template <typename T>
+__device__ __forceinline__ T vneg(T a) { return -a; }
+template <typename T>
+__device__ __forceinline__ T hsum(T a) { return a; }
+template <typename T>
+__device__ __forceinline__ T lane_of(T a, int) { return a; }
+template <typename T>
+__device__ __forceinline__ void splat(T &o, T x) { o = x; }
+template <typename T>
+__device__ __forceinline__ void set_lanes(T &o, const T (&x)[1]) { o = x[0]; }
+
+template <typename R, int K>
+struct Packing {  // float64: one spin per value
+    using P = R;
+    static constexpr int L = 1;
+};
+template <int K>
+struct Packing<float, K> {  // float32: pairs when the thread has two spins or more
+    using P = typename std::conditional<(K >= 2), f2, float>::type;
+    static constexpr int L = K >= 2 ? 2 : 1;
+};
+
+// per-spin phasor class entry (w = wr + j·wi) of one packed value
+template <typename P>
+struct alignas(2 * sizeof(P)) Cw {
+    P re, im;
+};
+
+// Shared-memory transpose that leaves lane l with the warp-wide sum of value l of a 16-sample
+// tile (sample l/2, component l%2).  Lane k stores its (x, y) pair of sample m with one 8-byte
+// store into row m, half k/16 of the tile (conflict-free: each half-warp fills 128 contiguous
+// bytes); lane l then reads row l/2, half l%2 (the pairs of 16 lanes, 8 conflict-free 16-byte
+// loads), adds the 16 pairs with packed adds and takes the other half-warp's share from its
+// neighbour lane: 16 stores, 8 loads, 16 adds and one shuffle per tile.
+constexpr int TILE_HALF = 36;  // floats per half row: 16 (x, y) pairs + 4 floats of padding
+constexpr int TILE_ROW = 2 * TILE_HALF;
+constexpr int TILE_FLOATS = 16 * TILE_ROW;  // one warp's tile
+__device__ __forceinline__ float tile_reduce_pairs(const f2 (&v)[16], int lane, float *tile) {
+    f2 *dst = reinterpret_cast<f2 *>(tile + (lane >> 4) * TILE_HALF) + (lane & 15);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) tile[i * TILE_STRIDE + lane] = v[i];
+    for (int m = 0; m < 16; ++m) dst[m * (TILE_ROW / 2)] = v[m];
     __syncwarp();
-    float a[32];
-    const float4 *row = reinterpret_cast<const float4 *>(tile + lane * TILE_STRIDE);
+    const float4 *row = reinterpret_cast<const float4 *>(tile + (lane >> 1) * TILE_ROW + (lane & 1) * TILE_HALF);
+    f2 a[16];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 t = row[q];
-        a[4 * q] = t.x;
-        a[4 * q + 1] = t.y;
-        a[4 * q + 2] = t.z;
-        a[4 * q + 3] = t.w;
+        a[2 * q] = pk2(t.x, t.y);
+        a[2 * q + 1] = pk2(t.z, t.w);
     }
     __syncwarp();
 #pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
+    for (int w = 8; w >= 1; w >>= 1) {
 #pragma unroll
-        for (int i = 0; i < w; ++i) a[i] += a[i + w];
+        for (int i = 0; i < w; ++i) a[i] = vadd(a[i], a[i + w]);
     }
-    return a[0];
+    float x, y;
+    unpk2(a[0], x, y);
+    const bool odd = (lane & 1) != 0;
+    const float mine = odd ? y : x, theirs = odd ? x : y;
+    return mine + __shfl_xor_sync(FULL, theirs, 1);
 }
 
 // Butterfly that leaves lane l with the warp-wide sum of v[l] (32 values per lane in, 1 out);
@@ -128,31 +222,20 @@ __device__ __forceinline__ R transpose_reduce32(R (&v)[32], int lane) {
     return v[0];
 }
 
-// Pairwise (tree) sum of K values: log2(K) dependent adds instead of K − 1.
-template <typename R, int K>
-__device__ __forceinline__ R tree_sum(const R (&a)[K]) {
-    if constexpr (K == 1) {
+// Pairwise (tree) sum of N values: log2(N) dependent adds instead of N − 1.
+template <typename P, int N>
+__device__ __forceinline__ P tree_sum(const P (&a)[N]) {
+    if constexpr (N == 1) {
         return a[0];
-    } else if constexpr (K == 2) {
-        return a[0] + a[1];
-    } else if constexpr (K == 4) {
-        return (a[0] + a[1]) + (a[2] + a[3]);
+    } else if constexpr (N == 2) {
+        return vadd(a[0], a[1]);
+    } else if constexpr (N == 4) {
+        return vadd(vadd(a[0], a[1]), vadd(a[2], a[3]));
     } else {
-        static_assert(K == 8, "K must be 1, 2, 4 or 8");
-        return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+        static_assert(N == 8, "N must be 1, 2, 4 or 8");
+        return vadd(vadd(vadd(a[0], a[1]), vadd(a[2], a[3])), vadd(vadd(a[4], a[5]), vadd(a[6], a[7])));
     }
 }
-
-template <typename R>
-struct V2;
-template <>
-struct V2<float> {
-    using T = float2;
-};
-template <>
-struct V2<double> {
-    using T = double2;
-};
 
 // Float-float product k·x reduced modulo 1 (cycles): returns frac(kh·xh) and accumulates the
 // small remainder kh·xh − fl(kh·xh) + kh·xl + kl·xh into `err`.
@@ -208,143 +291,188 @@ static __device__ __noinline__ void flush_window_f32(float *win, const float *de
 template <typename R, int K>
 struct Spins {
     using Op = typename std::conditional<std::is_same<R, float>::value, OpF32, OpF64>::type;
-    using V = typename V2<R>::T;
+    using P = typename Packing<R, K>::P;
+    using CwT = Cw<P>;
+    static constexpr int L = Packing<R, K>::L;  // spins per packed value
+    static constexpr int NP = K / L;            // packed values per quantity
     static constexpr bool F64 = std::is_same<R, double>::value;
     static constexpr int WIN = F64 ? SAMPLE_WINDOW_F64 : SAMPLE_WINDOW_F32;
 
-    R u[K], v[K], mz[K], rho[K];  // transverse part in the pulse frame, longitudinal, M0
-    R wr[K], wi[K];               // cached phasor class
-    R e1v[K];                     // cached T1 class ε1
+    // spin i = q + h·NP of the thread is lane h of packed value q
+    P u[NP], v[NP], mz[NP], rho[NP];  // transverse part in the pulse frame, longitudinal, M0
+    P wr[NP], wi[NP], nwi[NP];        // cached phasor class (nwi = −wi, kept for the pairs only)
+    P e1v[NP];                        // cached T1 class ε1
     int win_base, win_end;
 
     // shared-memory views and block geometry
-    const V *cw;
-    const V *train;  // sub-pulse table (cos α, sin α)
-    const R *ce1, *ce2, *prm;
+    const CwT *cw;
+    const void *train;  // sub-pulse table: float32 (cos, cos, sin, sin), float64 (cos, sin)
+    const P *ce1, *ce2;
+    const R *prm;
     R *red;       // float64: per-warp window rows
     float *tile;  // float32: this warp's transpose tile
     float *win;   // float32: block-wide window
-    int S, nthr, tid, lane, warp, nwarp;
+    int S, SP, nthr, tid, lane, warp, nwarp;
     int64_t base, np, n_spins;
     const double *params;
     const double *demod;
     const float *demod32;
     double *signal;
 
-    __device__ __forceinline__ int li(int i) const { return i * nthr + tid; }
+    __device__ __forceinline__ int li(int i) const { return i * nthr + tid; }  // spin i in the block
+    __device__ __forceinline__ int pi(int q) const { return q * nthr + tid; }  // packed value q
+    __device__ __forceinline__ P nwi_of(int q) const {
+        if constexpr (L == 2)
+            return nwi[q];
+        else
+            return vneg(wi[q]);
+    }
 
     __device__ __forceinline__ void load_w(int c) {
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const V w = cw[c * S + li(i)];
-            wr[i] = w.x;
-            wi[i] = w.y;
+        for (int q = 0; q < NP; ++q) {
+            const CwT w = cw[c * SP + pi(q)];
+            wr[q] = w.re;
+            wi[q] = w.im;
+            if constexpr (L == 2) nwi[q] = vneg(w.im);
         }
     }
     __device__ __forceinline__ void rot_w() {
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const R nu = u[i] * wr[i] - v[i] * wi[i];
-            const R nv = u[i] * wi[i] + v[i] * wr[i];
-            u[i] = nu;
-            v[i] = nv;
+        for (int q = 0; q < NP; ++q) {
+            const P nu = vfma(v[q], nwi_of(q), vmul(u[q], wr[q]));
+            const P nv = vfma(v[q], wr[q], vmul(u[q], wi[q]));
+            u[q] = nu;
+            v[q] = nv;
         }
     }
     __device__ __forceinline__ void t1_cached() {
 #pragma unroll
-        for (int i = 0; i < K; ++i) mz[i] = mz[i] - e1v[i] * (mz[i] - rho[i]);
+        for (int q = 0; q < NP; ++q) mz[q] = vfma(e1v[q], vsub(rho[q], mz[q]), mz[q]);
     }
     // lazy T1 recovery over the interval since the previous pulse
     __device__ __forceinline__ void t1_relax(const Op &op) {
         if (op.flags & F_E1CLS) {
             if (op.flags & F_E1LOAD) {
 #pragma unroll
-                for (int i = 0; i < K; ++i) e1v[i] = ce1[op.ecls * S + li(i)];
+                for (int q = 0; q < NP; ++q) e1v[q] = ce1[op.ecls * SP + pi(q)];
             }
             t1_cached();
         } else if (op.flags & F_E1INL) {
             const double tau = (double)op.f[10];
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const int64_t s = base + li(i);
-                const double r1 = s < n_spins ? params[P_R1 * np + s] : 0.0;
-                const R eps = (R)(-expm1(-tau * r1));
-                mz[i] = mz[i] - eps * (mz[i] - rho[i]);
+            for (int q = 0; q < NP; ++q) {
+                R eps[L];
+#pragma unroll
+                for (int h = 0; h < L; ++h) {
+                    const int64_t s = base + li(q + h * NP);
+                    const double r1 = s < n_spins ? params[P_R1 * np + s] : 0.0;
+                    eps[h] = (R)(-expm1(-tau * r1));
+                }
+                P e;
+                set_lanes(e, eps);
+                mz[q] = vfma(e, vsub(rho[q], mz[q]), mz[q]);
             }
         }
     }
-    // hard pulse about the frame's x axis (Eq. 3.19 in the pulse frame)
-    __device__ __forceinline__ void rf_turn(R ca, R sa) {
+    // hard pulse about the frame's x axis (Eq. 3.19 in the pulse frame); nsa = −sin α
+    __device__ __forceinline__ void rf_turn(P ca, P sa, P nsa) {
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const R nv = ca * v[i] + sa * mz[i];
-            const R nz = ca * mz[i] - sa * v[i];
-            v[i] = nv;
-            mz[i] = nz;
+        for (int q = 0; q < NP; ++q) {
+            const P nv = vfma(v[q], ca, vmul(mz[q], sa));
+            const P nz = vfma(v[q], nsa, vmul(mz[q], ca));
+            v[q] = nv;
+            mz[q] = nz;
         }
+    }
+    __device__ __forceinline__ void rf_turn_s(R ca, R sa) {
+        P c, s, ns;
+        splat(c, ca);
+        splat(s, sa);
+        splat(ns, -sa);
+        rf_turn(c, s, ns);
     }
     // turn the frame by exp(-jδ) (uniform over spins); float32 uses (hi, lo) constants
     __device__ __forceinline__ void frame_turn(const Op &op) {
         if constexpr (F64) {
-            const double c = op.f[2], s = op.f[3];
+            P c, s, ns;
+            splat(c, (R)op.f[2]);
+            splat(s, (R)op.f[3]);
+            splat(ns, (R)-op.f[3]);
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const double nu = u[i] * c + v[i] * s;
-                const double nv = v[i] * c - u[i] * s;
-                u[i] = nu;
-                v[i] = nv;
+            for (int q = 0; q < NP; ++q) {
+                const P nu = vfma(u[q], c, vmul(v[q], s));
+                const P nv = vfma(v[q], c, vmul(u[q], ns));
+                u[q] = nu;
+                v[q] = nv;
             }
         } else {
-            const float ch = op.f[2], cl = op.f[3], sh = op.f[4], sl = op.f[5];
+            P ch, cl, sh, sl, nsh, nsl;
+            splat(ch, op.f[2]);
+            splat(cl, op.f[3]);
+            splat(sh, op.f[4]);
+            splat(sl, op.f[5]);
+            splat(nsh, -op.f[4]);
+            splat(nsl, -op.f[5]);
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const float nu = fmaf(u[i], ch, fmaf(v[i], sh, fmaf(u[i], cl, v[i] * sl)));
-                const float nv = fmaf(v[i], ch, -fmaf(u[i], sh, fmaf(u[i], sl, -v[i] * cl)));
-                u[i] = nu;
-                v[i] = nv;
+            for (int q = 0; q < NP; ++q) {
+                const P nu = vfma(u[q], ch, vfma(v[q], sh, vfma(u[q], cl, vmul(v[q], sl))));
+                const P nv = vfma(v[q], ch, vfma(u[q], nsh, vfma(u[q], nsl, vmul(v[q], cl))));
+                u[q] = nu;
+                v[q] = nv;
             }
         }
     }
     // precession by the op's own moment and interval (not a cached class)
     __device__ __forceinline__ void prec_inline(const Op &op) {
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const int l = li(i);
-            R e2;
-            if (op.flags & F_E2CLS) {
-                e2 = ce2[op.ecls * S + l];
-            } else if (op.flags & F_DT) {
-                const int64_t s = base + l;
-                const double r2 = s < n_spins ? params[P_R2 * np + s] : 0.0;
-                e2 = (R)exp(-(double)op.f[F64 ? 3 : 8] * r2);
-            } else {
-                e2 = (R)1;
+        for (int q = 0; q < NP; ++q) {
+            R ar[L], ai[L], nai[L];
+#pragma unroll
+            for (int h = 0; h < L; ++h) {
+                const int l = li(q + h * NP);
+                R e2;
+                if (op.flags & F_E2CLS) {
+                    e2 = lane_of(ce2[op.ecls * SP + pi(q)], h);
+                } else if (op.flags & F_DT) {
+                    const int64_t s = base + l;
+                    const double r2 = s < n_spins ? params[P_R2 * np + s] : 0.0;
+                    e2 = (R)exp(-(double)op.f[F64 ? 3 : 8] * r2);
+                } else {
+                    e2 = (R)1;
+                }
+                R sn, cs;
+                if constexpr (F64) {
+                    double th = 0.0;
+                    if (op.flags & F_KX) th += op.f[0] * prm[0 * S + l];
+                    if (op.flags & F_KY) th += op.f[1] * prm[1 * S + l];
+                    if (op.flags & F_KZ) th += op.f[2] * prm[2 * S + l];
+                    if (op.flags & F_DT) th += op.f[3] * prm[3 * S + l];
+                    th -= rint(th);
+                    sincospi(2.0 * th, &sn, &cs);
+                } else {
+                    float err = 0.0f, t = 0.0f;
+                    if (op.flags & F_KX) t = wrap1(t + ff_term(op.f[0], op.f[1], prm[0 * S + l], prm[1 * S + l], err));
+                    if (op.flags & F_KY) t = wrap1(t + ff_term(op.f[2], op.f[3], prm[2 * S + l], prm[3 * S + l], err));
+                    if (op.flags & F_KZ) t = wrap1(t + ff_term(op.f[4], op.f[5], prm[4 * S + l], prm[5 * S + l], err));
+                    if (op.flags & F_DT) t = wrap1(t + ff_term(op.f[6], op.f[7], prm[6 * S + l], prm[7 * S + l], err));
+                    t = wrap1(t + err);
+                    // accurate sin/cos of the reduced angle (the hardware approximation's 2^-21 absolute
+                    // error would accumulate over many inline intervals)
+                    sincospif(2.0f * t, &sn, &cs);
+                }
+                ar[h] = e2 * cs;
+                ai[h] = -e2 * sn;
+                nai[h] = e2 * sn;
             }
-            R sn, cs;
-            if constexpr (F64) {
-                double th = 0.0;
-                if (op.flags & F_KX) th += op.f[0] * prm[0 * S + l];
-                if (op.flags & F_KY) th += op.f[1] * prm[1 * S + l];
-                if (op.flags & F_KZ) th += op.f[2] * prm[2 * S + l];
-                if (op.flags & F_DT) th += op.f[3] * prm[3 * S + l];
-                th -= rint(th);
-                sincospi(2.0 * th, &sn, &cs);
-            } else {
-                float err = 0.0f, t = 0.0f;
-                if (op.flags & F_KX) t = wrap1(t + ff_term(op.f[0], op.f[1], prm[0 * S + l], prm[1 * S + l], err));
-                if (op.flags & F_KY) t = wrap1(t + ff_term(op.f[2], op.f[3], prm[2 * S + l], prm[3 * S + l], err));
-                if (op.flags & F_KZ) t = wrap1(t + ff_term(op.f[4], op.f[5], prm[4 * S + l], prm[5 * S + l], err));
-                if (op.flags & F_DT) t = wrap1(t + ff_term(op.f[6], op.f[7], prm[6 * S + l], prm[7 * S + l], err));
-                t = wrap1(t + err);
-                // accurate sin/cos of the reduced angle (the hardware approximation's 2^-21 absolute
-                // error would accumulate over many inline intervals)
-                sincospif(2.0f * t, &sn, &cs);
-            }
-            const R ar = e2 * cs, ai = -e2 * sn;
-            const R nu = u[i] * ar - v[i] * ai;
-            const R nv = u[i] * ai + v[i] * ar;
-            u[i] = nu;
-            v[i] = nv;
+            P AR, AI, NAI;
+            set_lanes(AR, ar);
+            set_lanes(AI, ai);
+            set_lanes(NAI, nai);
+            const P nu = vfma(v[q], NAI, vmul(u[q], AR));
+            const P nv = vfma(v[q], AR, vmul(u[q], AI));
+            u[q] = nu;
+            v[q] = nv;
         }
     }
 
@@ -360,7 +488,7 @@ struct Spins {
 
     __device__ __forceinline__ void sample1(int j) {
         if (j + 1 - win_base > WIN) flush();
-        R sx = tree_sum<R, K>(u), sy = tree_sum<R, K>(v);
+        R sx = hsum(tree_sum<P, NP>(u)), sy = hsum(tree_sum<P, NP>(v));
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
             sx += __shfl_xor_sync(FULL, sx, off);
@@ -379,12 +507,6 @@ struct Spins {
     }
 
     // lane l holds the warp total of value l (sample l/2, component l%2) of a 16-sample tile
-    __device__ __forceinline__ R warp_tile_total(R (&vv)[32]) {
-        if constexpr (F64)
-            return transpose_reduce32(vv, lane);
-        else
-            return tile_reduce32(vv, lane, tile);
-    }
     __device__ __forceinline__ void store_tile(int slot, R tot) {
         if constexpr (F64)
             red_row(lane & 1)[slot + (lane >> 1)] = tot;
@@ -395,53 +517,85 @@ struct Spins {
     // one sample step of a run: rotate by the cached class, return the thread's sums
     __device__ __forceinline__ void run_step(R &sx, R &sy) {
         rot_w();
-        sx = tree_sum<R, K>(u);
-        sy = tree_sum<R, K>(v);
+        sx = hsum(tree_sum<P, NP>(u));
+        sy = hsum(tree_sum<P, NP>(v));
     }
 
-    __device__ __forceinline__ void run(const Op &op) {
-        const int n = op.n, j0 = op.adc0;
-        if (op.flags & F_PLOAD) load_w(op.pcls);
-        R au[K], av[K];
-        const bool anchor = (op.flags & F_ANCHOR) != 0;
-        if (anchor) {
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                au[i] = u[i];
-                av[i] = v[i];
-            }
-        }
-        if (j0 + n - win_base > WIN) flush();
-        const int slot0 = j0 - win_base;
-        int t0 = 0;
-        for (; t0 + 16 <= n; t0 += 16) {  // full tiles: no guards
-            R vv[32];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) run_step(vv[2 * t], vv[2 * t + 1]);
-            store_tile(slot0 + t0, warp_tile_total(vv));
-        }
-        if (t0 < n) {  // ragged tail
-            const int tt = n - t0;
+    // tt (<= 16) sample steps; the warp total of value l of the tile ends up in lane l
+    template <bool FULL_TILE>
+    __device__ __forceinline__ R tile_steps(int tt) {
+        if constexpr (F64) {
             R vv[32];
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
-                if (t < tt) {
+                if (FULL_TILE || t < tt) {
                     run_step(vv[2 * t], vv[2 * t + 1]);
                 } else {
                     vv[2 * t] = (R)0;
                     vv[2 * t + 1] = (R)0;
                 }
             }
-            const R tot = warp_tile_total(vv);
+            return transpose_reduce32(vv, lane);
+        } else {
+            f2 vt[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                R sx = 0.0f, sy = 0.0f;
+                if (FULL_TILE || t < tt) run_step(sx, sy);
+                vt[t] = pk2(sx, sy);
+            }
+            return tile_reduce_pairs(vt, lane, tile);
+        }
+    }
+
+    __device__ __forceinline__ void run(const Op &op) {
+        const int n = op.n, j0 = op.adc0;
+        if (op.flags & F_PLOAD) load_w(op.pcls);
+        P au[NP], av[NP];
+        const bool anchor = (op.flags & F_ANCHOR) != 0;
+        if (anchor) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                au[q] = u[q];
+                av[q] = v[q];
+            }
+        }
+        if (j0 + n - win_base > WIN) flush();
+        const int slot0 = j0 - win_base;
+        int t0 = 0;
+        for (; t0 + 16 <= n; t0 += 16) store_tile(slot0 + t0, tile_steps<true>(16));  // full tiles
+        if (t0 < n) {  // ragged tail
+            const int tt = n - t0;
+            const R tot = tile_steps<false>(tt);
             if (lane < 2 * tt) store_tile(slot0 + t0, tot);
         }
         win_end = j0 + n;
         if (anchor) {
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const V w = cw[op.acls * S + li(i)];
-                u[i] = au[i] * w.x - av[i] * w.y;
-                v[i] = au[i] * w.y + av[i] * w.x;
+            for (int q = 0; q < NP; ++q) {
+                const CwT w = cw[op.acls * SP + pi(q)];
+                u[q] = vfma(av[q], vneg(w.im), vmul(au[q], w.re));
+                v[q] = vfma(av[q], w.re, vmul(au[q], w.im));
+            }
+        }
+    }
+
+    __device__ __forceinline__ void load_train(int k, P &ca, P &sa, P &nsa) const {
+        if constexpr (F64) {
+            const double2 t = reinterpret_cast<const double2 *>(train)[k];
+            ca = t.x;
+            sa = t.y;
+            nsa = -t.y;
+        } else {
+            const float4 t = reinterpret_cast<const float4 *>(train)[k];
+            if constexpr (L == 2) {
+                ca = pk2(t.x, t.y);
+                sa = pk2(t.z, t.w);
+                nsa = vneg(sa);
+            } else {
+                ca = t.x;
+                sa = t.z;
+                nsa = -t.z;
             }
         }
     }
@@ -451,9 +605,10 @@ struct Spins {
     __device__ __forceinline__ void train_run(int off, int n) {
 #pragma unroll 2
         for (int i = 0; i < n; ++i) {
-            const V cs = train[off + i];
+            P ca, sa, nsa;
+            load_train(off + i, ca, sa, nsa);
             t1_cached();
-            rf_turn(cs.x, cs.y);
+            rf_turn(ca, sa, nsa);
             rot_w();
         }
     }
@@ -465,13 +620,13 @@ struct Spins {
             break;
         case OP_RF_FAST:  // sub-pulse of a shaped pulse: every cache already holds the right class
             t1_cached();
-            rf_turn((R)op.f[0], (R)op.f[1]);
+            rf_turn_s((R)op.f[0], (R)op.f[1]);
             rot_w();
             break;
         case OP_RF:
             if (op.flags & F_FRAME) frame_turn(op);
             t1_relax(op);
-            rf_turn((R)op.f[0], (R)op.f[1]);
+            rf_turn_s((R)op.f[0], (R)op.f[1]);
             if (op.flags & F_PCLS) {
                 if (op.flags & F_PLOAD) load_w(op.pcls);
                 rot_w();
@@ -524,12 +679,12 @@ __host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1
     L.prm = o;
     o = align_up(o + (size_t)nprm * S * rs, 16);
     L.train = o;
-    o = align_up(o + (size_t)n_train * 2 * rs, 16);
+    o = align_up(o + (size_t)n_train * 16, 16);  // float32 (c, c, s, s), float64 (c, s)
     L.red = o;
     if (f64)
         o = align_up(o + (size_t)nwarp * 2 * RED_STRIDE * rs, 16);
     else  // transpose tiles, then the block-wide window
-        o = align_up(o + (size_t)nwarp * 32 * TILE_STRIDE * 4 + (size_t)2 * WIN_STRIDE * 4, 16);
+        o = align_up(o + (size_t)nwarp * TILE_FLOATS * 4 + (size_t)2 * WIN_STRIDE * 4, 16);
     L.total = o;
     return L;
 }
@@ -551,9 +706,11 @@ template <typename R, int K>
 __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigned char *smem, uint32_t &seq) {
     using SP = Spins<R, K>;
     using Op = typename SP::Op;
-    using V = typename SP::V;
+    using PV = typename SP::P;
+    using CwT = typename SP::CwT;
     constexpr bool F64 = SP::F64;
     constexpr int CH = F64 ? CHUNK_F64 : CHUNK_F32;
+    constexpr int LN = SP::L, NP = SP::NP;
 
     SP sp;
     sp.nthr = blockDim.x;
@@ -562,29 +719,38 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     sp.warp = sp.tid >> 5;
     sp.nwarp = sp.nthr >> 5;
     sp.S = K * sp.nthr;
-    const int S = sp.S;
+    sp.SP = NP * sp.nthr;
+    const int S = sp.S, SPK = sp.SP;
     const Program &P = a.prog;
     const SmemLayout L = smem_layout(F64, P.n_pcls, P.n_e1, P.n_e2, P.n_train, S, sp.nwarp);
     Op *opbuf = reinterpret_cast<Op *>(smem + L.ops);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.bars);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.flag);
-    V *cw = reinterpret_cast<V *>(smem + L.cw);
-    R *ce1 = reinterpret_cast<R *>(smem + L.ce1);
-    R *ce2 = reinterpret_cast<R *>(smem + L.ce2);
+    CwT *cw = reinterpret_cast<CwT *>(smem + L.cw);
+    PV *ce1 = reinterpret_cast<PV *>(smem + L.ce1);
+    PV *ce2 = reinterpret_cast<PV *>(smem + L.ce2);
     R *prm = reinterpret_cast<R *>(smem + L.prm);
     sp.cw = cw;
-    {
-        V *tr = reinterpret_cast<V *>(smem + L.train);
-        const V *gtr = reinterpret_cast<const V *>(P.train);
+    if constexpr (F64) {
+        double2 *tr = reinterpret_cast<double2 *>(smem + L.train);
+        const double2 *gtr = reinterpret_cast<const double2 *>(P.train);
         for (int q = sp.tid; q < P.n_train; q += sp.nthr) tr[q] = gtr[q];
+        sp.train = tr;
+    } else {
+        float4 *tr = reinterpret_cast<float4 *>(smem + L.train);
+        const float2 *gtr = reinterpret_cast<const float2 *>(P.train);
+        for (int q = sp.tid; q < P.n_train; q += sp.nthr) {
+            const float2 t = gtr[q];
+            tr[q] = make_float4(t.x, t.x, t.y, t.y);
+        }
         sp.train = tr;
     }
     sp.ce1 = ce1;
     sp.ce2 = ce2;
     sp.prm = prm;
     sp.red = reinterpret_cast<R *>(smem + L.red);
-    sp.tile = reinterpret_cast<float *>(smem + L.red) + sp.warp * 32 * TILE_STRIDE;
-    sp.win = reinterpret_cast<float *>(smem + L.red) + sp.nwarp * 32 * TILE_STRIDE;
+    sp.tile = reinterpret_cast<float *>(smem + L.red) + sp.warp * TILE_FLOATS;
+    sp.win = reinterpret_cast<float *>(smem + L.red) + sp.nwarp * TILE_FLOATS;
     if constexpr (!F64)
         for (int q = sp.tid; q < 2 * WIN_STRIDE; q += sp.nthr) sp.win[q] = 0.0f;
     sp.demod = P.demod;
@@ -617,10 +783,14 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     }
 
     // ---- per-spin set-up: parameters, class tables (float64 math), initial state -------------
+    // Spin i of the thread is lane i / NP of packed value i % NP; a packed table entry holds its
+    // lanes' real parts first, then (phasor classes) their imaginary parts.
     const int64_t np = a.n_pad;
+    R su[K], sv[K], smz[K], srho[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const int l = sp.li(i);
+        const int qi = i % NP, hi = i / NP;
         const int64_t s = sp.base + l;
         const bool valid = s < a.n_spins;
         const double x = valid ? a.params[P_X * np + s] : 0.0;
@@ -630,7 +800,7 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
         const double m0 = valid ? a.params[P_RHO * np + s] : 0.0;
         const double r1 = valid ? a.params[P_R1 * np + s] : 0.0;
         const double r2 = valid ? a.params[P_R2 * np + s] : 0.0;
-        sp.rho[i] = (R)m0;
+        srho[i] = (R)m0;
         if constexpr (F64) {
             prm[0 * S + l] = x;
             prm[1 * S + l] = y;
@@ -653,25 +823,44 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
             double sn, cs;
             sincospi(2.0 * th, &sn, &cs);
             const double e2 = exp(-dt * r2);
-            V w;
-            w.x = (R)(e2 * cs);
-            w.y = (R)(-e2 * sn);
-            cw[c * S + l] = w;
+            R *w = reinterpret_cast<R *>(cw + c * SPK + sp.pi(qi));
+            w[hi] = (R)(e2 * cs);
+            w[LN + hi] = (R)(-e2 * sn);
         }
-        for (int c = 0; c < P.n_e1; ++c) ce1[c * S + l] = (R)(-expm1(-__ldg(P.e1 + c) * r1));
-        for (int c = 0; c < P.n_e2; ++c) ce2[c * S + l] = (R)exp(-__ldg(P.e2 + c) * r2);
+        for (int c = 0; c < P.n_e1; ++c)
+            reinterpret_cast<R *>(ce1 + c * SPK + sp.pi(qi))[hi] = (R)(-expm1(-__ldg(P.e1 + c) * r1));
+        for (int c = 0; c < P.n_e2; ++c)
+            reinterpret_cast<R *>(ce2 + c * SPK + sp.pi(qi))[hi] = (R)exp(-__ldg(P.e2 + c) * r2);
         if (a.state_in && valid) {  // laboratory frame = pulse frame ψ = 0 at the start
-            sp.u[i] = (R)a.state_in[3 * s];
-            sp.v[i] = (R)a.state_in[3 * s + 1];
-            sp.mz[i] = (R)a.state_in[3 * s + 2];
+            su[i] = (R)a.state_in[3 * s];
+            sv[i] = (R)a.state_in[3 * s + 1];
+            smz[i] = (R)a.state_in[3 * s + 2];
         } else {
-            sp.u[i] = (R)0;
-            sp.v[i] = (R)0;
-            sp.mz[i] = (R)m0;
+            su[i] = (R)0;
+            sv[i] = (R)0;
+            smz[i] = (R)m0;
         }
-        sp.wr[i] = (R)1;
-        sp.wi[i] = (R)0;
-        sp.e1v[i] = (R)0;
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        R lu[LN], lv[LN], lz[LN], lr[LN], one[LN], zero[LN];
+#pragma unroll
+        for (int h = 0; h < LN; ++h) {
+            lu[h] = su[q + h * NP];
+            lv[h] = sv[q + h * NP];
+            lz[h] = smz[q + h * NP];
+            lr[h] = srho[q + h * NP];
+            one[h] = (R)1;
+            zero[h] = (R)0;
+        }
+        set_lanes(sp.u[q], lu);
+        set_lanes(sp.v[q], lv);
+        set_lanes(sp.mz[q], lz);
+        set_lanes(sp.rho[q], lr);
+        set_lanes(sp.wr[q], one);
+        set_lanes(sp.wi[q], zero);
+        set_lanes(sp.nwi[q], zero);
+        set_lanes(sp.e1v[q], zero);
     }
     __syncthreads();
 
@@ -707,11 +896,12 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const int64_t s = sp.base + sp.li(i);
+            const int qi = i % NP, hi = i / NP;
             if (s < a.n_spins) {
-                const double uu = (double)sp.u[i], vv = (double)sp.v[i];
+                const double uu = (double)lane_of(sp.u[qi], hi), vv = (double)lane_of(sp.v[qi], hi);
                 a.state_out[3 * s] = uu * cps - vv * sps;
                 a.state_out[3 * s + 1] = uu * sps + vv * cps;
-                a.state_out[3 * s + 2] = (double)sp.mz[i];
+                a.state_out[3 * s + 2] = (double)lane_of(sp.mz[qi], hi);
             }
         }
     }
