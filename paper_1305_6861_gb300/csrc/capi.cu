@@ -273,6 +273,9 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     p.demod32 = s->d_demod32;
     p.n_train = (int32_t)(s->host.train.size() / 2);
     p.n_adc = s->host.n_adc;
+    for (const OpF32 &o : s->host.ops32)  // magnitude bound of the float32 inline phase terms
+        if (o.kind == OP_PREC && (o.flags & F_INLINE))
+            for (int a = 0; a < 4; ++a) p.kmax[a] = std::max(p.kmax[a], std::fabs(o.f[2 * a]));
     s->p32 = p;
     s->p32.ops = s->d_ops32;
     s->p32.train = s->d_train32;

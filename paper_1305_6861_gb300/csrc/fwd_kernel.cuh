@@ -118,7 +118,12 @@ __device__ __forceinline__ f2 vsub(f2 a, f2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
     return d;
 }
-__device__ __forceinline__ f2 vneg(f2 a) { return vmul(a, pk2(-1.0f, -1.0f)); }
+// sign flip of both lanes on the integer pipe (the FMA pipe is the bound)
+__device__ __forceinline__ f2 vneg(f2 a) {
+    f2 o;
+    asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(o.r) : "l"(a.r));
+    return o;
+}
 __device__ __forceinline__ float hsum(f2 a) {
     float x, y;
     unpk2(a, x, y);
@@ -152,6 +157,26 @@ __device__ __forceinline__ void splat(T &o, T x) { o = x; }
 template <typename T>
 __device__ __forceinline__ void set_lanes(T &o, const T (&x)[1]) { o = x[0]; }
 
+// Rounding constant 1.5·2^23: for |p| < 2^22, (p + c) − c is p rounded to the nearest integer
+// (round-to-nearest-even), so p − ((p + c) − c) is the exact fractional part in [−1/2, 1/2].
+constexpr float RINT_MAGIC = 12582912.0f;
+// The packed fractional-part step on spin pairs needs |k_hi·x_hi| < 2^22 cycles; blocks whose
+// coordinates and program could reach PHASE_SAFE take the one-spin-at-a-time path instead.
+constexpr float PHASE_SAFE = 2097152.0f;  // 2^21
+// Taylor coefficients of sin(πt) = Σ (−1)^k π^(2k+1) t^(2k+1)/(2k+1)! and
+// cos(πt) = Σ (−1)^k π^(2k) t^(2k)/(2k)!, truncated for |t| <= 1/2: the first omitted terms are
+// below 7e-10 (sine, t^15) and 7e-9 (cosine, t^14).
+constexpr double PI_D = 3.14159265358979323846;
+constexpr double taylor_pi(int n) {  // π^n / n!
+    double c = 1.0;
+    for (int i = 1; i <= n; ++i) c *= PI_D / i;
+    return c;
+}
+constexpr float SIN_C0 = (float)taylor_pi(1), SIN_C1 = (float)-taylor_pi(3), SIN_C2 = (float)taylor_pi(5),
+                SIN_C3 = (float)-taylor_pi(7), SIN_C4 = (float)taylor_pi(9), SIN_C5 = (float)-taylor_pi(11),
+                SIN_C6 = (float)taylor_pi(13);
+constexpr float COS_C1 = (float)-taylor_pi(2), COS_C2 = (float)taylor_pi(4), COS_C3 = (float)-taylor_pi(6),
+                COS_C4 = (float)taylor_pi(8), COS_C5 = (float)-taylor_pi(10), COS_C6 = (float)taylor_pi(12);
 template <typename R, int K>
 struct Packing {  // float64: one spin per value
     using P = R;
@@ -308,7 +333,9 @@ struct Spins {
     const CwT *cw;
     const void *train;  // sub-pulse table: float32 (cos, cos, sin, sin), float64 (cos, sin)
     const P *ce1, *ce2;
-    const R *prm;
+    const P *prm;      // spin coordinates for inline precessions (float32: hi/lo rows), pair-major
+    bool big_phase;    // some |k_hi·x_hi| of this block may reach PHASE_SAFE: scalar phase path
+    bool zero_df;      // every spin of this block has Δf = 0: no Δf·Δt phase term
     R *red;       // float64: per-warp window rows
     float *tile;  // float32: this warp's transpose tile
     float *win;   // float32: block-wide window
@@ -423,8 +450,85 @@ struct Spins {
             }
         }
     }
+    __device__ __forceinline__ R prm_at(int row, int q, int h) const { return lane_of(prm[row * SP + pi(q)], h); }
+
     // precession by the op's own moment and interval (not a cached class)
     __device__ __forceinline__ void prec_inline(const Op &op) {
+        if constexpr (L == 2) {
+            if (!big_phase) {
+                prec_inline_pairs(op);
+                return;
+            }
+        }
+        prec_inline_lanes(op);
+    }
+
+    // float32 pairs: phase φ = Σ k·x in cycles with k and x as float-float pairs: fractional part
+    // of each rounded product k_hi·x_hi (RINT_MAGIC), plus its exact residual and the cross terms,
+    // reduced to t ∈ [−1/2, 1/2]; sin and cos of πt
+    // from the Taylor polynomials, then of 2πt by the double-angle formulas; u + jv is multiplied
+    // by E2·exp(−j2πt) (Eqs. 3.5, 3.14 in the pulse frame)
+    __device__ __forceinline__ void prec_inline_pairs(const Op &op) {
+        const f2 mg = pk2(RINT_MAGIC, RINT_MAGIC);
+        const uint16_t fl = op.flags;
+        const bool tx = fl & F_KX, ty = fl & F_KY, tz = fl & F_KZ, tdf = (fl & F_DT) && !zero_df;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            f2 t = pk2(0.0f, 0.0f), er = pk2(0.0f, 0.0f);
+            auto term = [&](int a) {
+                f2 kh, kl;
+                splat(kh, op.f[2 * a]);
+                splat(kl, op.f[2 * a + 1]);
+                const f2 xh = prm[(2 * a) * SP + pi(q)], xl = prm[(2 * a + 1) * SP + pi(q)];
+                const f2 p = vmul(kh, xh);
+                t = vadd(t, vsub(p, vsub(vadd(p, mg), mg)));  // frac(p), exact
+                er = vadd(er, vfma(kh, xh, vneg(p)));          // kh·xh − p, exact
+                er = vfma(kl, xh, vfma(kh, xl, er));
+            };
+            if (tx) term(0);
+            if (ty) term(1);
+            if (tz) term(2);
+            if (tdf) term(3);
+            t = vadd(t, er);
+            t = vsub(t, vsub(vadd(t, mg), mg));
+            const f2 s2 = vmul(t, t);
+            auto horner = [&](f2 acc, float c) { return vfma(acc, s2, pk2(c, c)); };
+            f2 sp = pk2(SIN_C6, SIN_C6), cp = pk2(COS_C6, COS_C6);
+            sp = horner(horner(horner(horner(horner(horner(sp, SIN_C5), SIN_C4), SIN_C3), SIN_C2), SIN_C1), SIN_C0);
+            cp = horner(horner(horner(horner(horner(horner(cp, COS_C5), COS_C4), COS_C3), COS_C2), COS_C1), 1.0f);
+            const f2 sn = vmul(sp, t);  // sin πt
+            const f2 twos = vadd(sn, sn);
+            f2 one;
+            splat(one, 1.0f);
+            f2 ar = vfma(twos, vneg(sn), one);  // cos 2πt = 1 − 2 sin²πt
+            f2 as = vmul(twos, cp);             // sin 2πt
+            if (fl & (F_E2CLS | F_DT)) {
+                f2 e2;
+                if (fl & F_E2CLS) {
+                    e2 = ce2[op.ecls * SP + pi(q)];
+                } else {
+                    float ev[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int64_t s = base + li(q + h * NP);
+                        const double r2 = s < n_spins ? params[P_R2 * np + s] : 0.0;
+                        ev[h] = (float)exp(-(double)op.f[8] * r2);
+                    }
+                    set_lanes(e2, ev);
+                }
+                ar = vmul(e2, ar);
+                as = vmul(e2, as);
+            }
+            // (u + jv)·(ar − j·as)
+            const f2 nu = vfma(v[q], as, vmul(u[q], ar));
+            const f2 nv = vfma(u[q], vneg(as), vmul(v[q], ar));
+            u[q] = nu;
+            v[q] = nv;
+        }
+    }
+
+    // one spin at a time (float64; float32 with one spin per thread or large phases)
+    __device__ __forceinline__ void prec_inline_lanes(const Op &op) {
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             R ar[L], ai[L], nai[L];
@@ -444,18 +548,18 @@ struct Spins {
                 R sn, cs;
                 if constexpr (F64) {
                     double th = 0.0;
-                    if (op.flags & F_KX) th += op.f[0] * prm[0 * S + l];
-                    if (op.flags & F_KY) th += op.f[1] * prm[1 * S + l];
-                    if (op.flags & F_KZ) th += op.f[2] * prm[2 * S + l];
-                    if (op.flags & F_DT) th += op.f[3] * prm[3 * S + l];
+                    if (op.flags & F_KX) th += op.f[0] * prm_at(0, q, h);
+                    if (op.flags & F_KY) th += op.f[1] * prm_at(1, q, h);
+                    if (op.flags & F_KZ) th += op.f[2] * prm_at(2, q, h);
+                    if (op.flags & F_DT) th += op.f[3] * prm_at(3, q, h);
                     th -= rint(th);
                     sincospi(2.0 * th, &sn, &cs);
                 } else {
                     float err = 0.0f, t = 0.0f;
-                    if (op.flags & F_KX) t = wrap1(t + ff_term(op.f[0], op.f[1], prm[0 * S + l], prm[1 * S + l], err));
-                    if (op.flags & F_KY) t = wrap1(t + ff_term(op.f[2], op.f[3], prm[2 * S + l], prm[3 * S + l], err));
-                    if (op.flags & F_KZ) t = wrap1(t + ff_term(op.f[4], op.f[5], prm[4 * S + l], prm[5 * S + l], err));
-                    if (op.flags & F_DT) t = wrap1(t + ff_term(op.f[6], op.f[7], prm[6 * S + l], prm[7 * S + l], err));
+                    if (op.flags & F_KX) t = wrap1(t + ff_term(op.f[0], op.f[1], prm_at(0, q, h), prm_at(1, q, h), err));
+                    if (op.flags & F_KY) t = wrap1(t + ff_term(op.f[2], op.f[3], prm_at(2, q, h), prm_at(3, q, h), err));
+                    if (op.flags & F_KZ) t = wrap1(t + ff_term(op.f[4], op.f[5], prm_at(4, q, h), prm_at(5, q, h), err));
+                    if (op.flags & F_DT) t = wrap1(t + ff_term(op.f[6], op.f[7], prm_at(6, q, h), prm_at(7, q, h), err));
                     t = wrap1(t + err);
                     // accurate sin/cos of the reduced angle (the hardware approximation's 2^-21 absolute
                     // error would accumulate over many inline intervals)
@@ -668,8 +772,8 @@ __host__ __device__ inline SmemLayout smem_layout(bool f64, int n_pcls, int n_e1
     o += opb;
     L.bars = o;
     o += 16;
-    L.flag = o;
-    o += 16;
+    L.flag = o;  // abort flag, then 4 words of per-axis coordinate maxima (float bits)
+    o += 32;
     L.cw = o;
     o = align_up(o + (size_t)n_pcls * S * 2 * rs, 16);
     L.ce1 = o;
@@ -729,7 +833,8 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     CwT *cw = reinterpret_cast<CwT *>(smem + L.cw);
     PV *ce1 = reinterpret_cast<PV *>(smem + L.ce1);
     PV *ce2 = reinterpret_cast<PV *>(smem + L.ce2);
-    R *prm = reinterpret_cast<R *>(smem + L.prm);
+    PV *prm = reinterpret_cast<PV *>(smem + L.prm);
+    unsigned *bmax = reinterpret_cast<unsigned *>(smem + L.flag + 16);
     sp.cw = cw;
     if constexpr (F64) {
         double2 *tr = reinterpret_cast<double2 *>(smem + L.train);
@@ -778,6 +883,7 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     };
     if (sp.tid == 0) {
         *abort_flag = 0;
+        for (int q = 0; q < 4; ++q) bmax[q] = 0u;
         if (n_chunks > 0) issue(0);
         if (n_chunks > 1) issue(1);
     }
@@ -787,6 +893,7 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     // lanes' real parts first, then (phasor classes) their imaginary parts.
     const int64_t np = a.n_pad;
     R su[K], sv[K], smz[K], srho[K];
+    float amax[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // this thread's max |x_hi|, |y_hi|, |z_hi|, |Δf_hi|
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const int l = sp.li(i);
@@ -802,17 +909,17 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
         const double r2 = valid ? a.params[P_R2 * np + s] : 0.0;
         srho[i] = (R)m0;
         if constexpr (F64) {
-            prm[0 * S + l] = x;
-            prm[1 * S + l] = y;
-            prm[2 * S + l] = z;
-            prm[3 * S + l] = df;
+            const double vals[4] = {x, y, z, df};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) reinterpret_cast<R *>(prm + q * SPK + sp.pi(qi))[hi] = vals[q];
         } else {
             const double vals[4] = {x, y, z, df};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float h = (float)vals[q];
-                prm[(2 * q) * S + l] = h;
-                prm[(2 * q + 1) * S + l] = (float)(vals[q] - (double)h);
+                reinterpret_cast<R *>(prm + (2 * q) * SPK + sp.pi(qi))[hi] = h;
+                reinterpret_cast<R *>(prm + (2 * q + 1) * SPK + sp.pi(qi))[hi] = (float)(vals[q] - (double)h);
+                amax[q] = fmaxf(amax[q], fabsf(h));
             }
         }
         for (int c = 0; c < P.n_pcls; ++c) {
@@ -863,6 +970,24 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
         set_lanes(sp.e1v[q], zero);
     }
     __syncthreads();
+    if constexpr (!F64) {
+        // block-wide coordinate maxima decide whether the packed phase step is exact for every
+        // inline precession of the program (|k_hi|max · |x_hi|max < PHASE_SAFE per axis)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned m = __reduce_max_sync(FULL, __float_as_uint(amax[q]));
+            if (sp.lane == 0) atomicMax(bmax + q, m);
+        }
+        __syncthreads();
+        bool big = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) big |= !(P.kmax[q] * __uint_as_float(bmax[q]) < PHASE_SAFE);
+        sp.big_phase = big;
+        sp.zero_df = bmax[3] == 0u;
+    } else {
+        sp.big_phase = true;
+        sp.zero_df = false;
+    }
 
     // ---- the operation stream ------------------------------------------------------------------
     for (int c = 0; c < n_chunks; ++c) {

@@ -116,6 +116,7 @@ struct Program {
     const void *train;     // sub-pulse table: n_train (cos α, sin α) pairs, float2 or double2
     int32_t n_train;
     int64_t n_adc;
+    float kmax[4];  // float32 program: max |k_hi| of the inline precessions per term (kx, ky, kz, Δt)
 };
 
 struct FwdArgs {

@@ -83,6 +83,39 @@ def test_random_sequences_parity(M, ctx, oracle_mod, seed):
     assert np.max(np.abs(st32 - ref_state)) <= 1e-4
 
 
+def _inline_phase_sequence(rng, cycles, n_rep=40):
+    """Unique free-precession intervals (so they compile to inline precessions) whose largest
+    k·x term is about `cycles` cycles at the edge of a 0.5 m field of view, each followed by one
+    sample, with a hard pulse every 8 intervals."""
+    rows = [(0.0, 0.0, 0.0, 0.0, math.pi / 2, 0.3, 0, 0.0)]
+    kmax = cycles / 0.25  # cycles/m
+    for i in range(n_rep):
+        dt = rng.uniform(1e-4, 2e-3)
+        g = rng.uniform(-1, 1, 3) * kmax / (W.GAMMA_BAR * dt)
+        rows.append((dt, *g, 0.0, 0.0, 0, 0.0))
+        rows.append((1e-5, 0.0, 0.0, 0.0, 0.0, 0.0, 1, rng.uniform(0, 2 * math.pi)))
+        if i % 8 == 7:
+            rows.append((0.0, 0.0, 0.0, 0.0, rng.uniform(0.2, 1.0), rng.uniform(0, 2 * math.pi), 0, 0.0))
+    return W.Sequence(W.make_events(rows), W.GAMMA_BAR)
+
+
+@pytest.mark.parametrize("cycles", [300.0, 5.0e6])
+@pytest.mark.parametrize("off_resonance", [True, False])
+def test_fp32_inline_phase_paths(M, ctx, oracle_mod, cycles, off_resonance):
+    """float32 inline precessions: spin pairs with the packed phase (moderate moments), the
+    one-spin float-float path (moments whose products could reach 2^21 cycles) and one spin per
+    thread, with and without off-resonance (the Δf·Δt term is skipped when a block has none)."""
+    rng = np.random.default_rng(int(cycles) % 1000 + int(off_resonance))
+    ph = W.random_phantom(2500, rng)
+    if not off_resonance:
+        ph.dw[:] = 0.0
+    seq = _inline_phase_sequence(rng, cycles)
+    ref = oracle_mod.signal(ph, seq)
+    for k, t in ((4, 128), (2, 64), (8, 64), (1, 128)):
+        out = run(M, ctx, ph, seq, M.FP32, spins_per_thread=k, threads_per_block=t)
+        assert rel_l2(out, ref) <= TOL32, (k, t)
+
+
 @pytest.mark.parametrize("prec,shapes", [
     ("fp32", [(1, 32), (1, 64), (1, 512), (2, 128), (2, 512), (4, 96), (4, 512), (8, 64), (8, 256)]),
     ("fp64", [(1, 32), (1, 256), (2, 64), (2, 256)]),
