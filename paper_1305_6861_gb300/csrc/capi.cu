@@ -410,37 +410,55 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
-    TunedShape win;
-    win.ms = 1e30f;
+    // time one launch of the prefix in shape (k, t); < 0 if the shape cannot run
+    const int32_t short_ops = P.n_ops;
+    const int32_t long_ops = (int32_t)std::min<int64_t>((int64_t)short_ops * 3, (fp64 ? seq->p64 : seq->p32).n_ops);
+    auto trial = [&](int k, int t) -> float {
+        FwdArgs a{};
+        a.prog = P;
+        a.params = ph->params;
+        a.n_spins = ph->n;
+        a.n_pad = ph->n_pad;
+        a.signal = ctx->d_sig;
+        a.status = ctx->d_status;
+        cudaEventRecord(e0, st);
+        const int rc = fp64 ? launch_fwd_f64(a, k, t, stream) : launch_fwd_f32(a, k, t, stream);
+        cudaEventRecord(e1, st);
+        if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0f;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // pass 1: every shape that fits, once after a warm-up launch; pass 2: the three fastest on a
+    // three times longer prefix, twice each, so that timing noise does not pick the shape
+    std::vector<TunedShape> cand;
     for (int k : (fp64 ? std::vector<int>(f64k, f64k + 2) : std::vector<int>(f32k, f32k + 4))) {
         for (int t : thr) {
             if (t > (fp64 || k == 8 ? 256 : 512)) continue;
             const size_t smem = fwd_smem_bytes(fp64, P, k, t);
             if (smem > (size_t)ctx->max_smem_optin || fwd_blocks_per_sm(fp64, k, t, smem) == 0) continue;
-            FwdArgs a{};
-            a.prog = P;
-            a.params = ph->params;
-            a.n_spins = ph->n;
-            a.n_pad = ph->n_pad;
-            a.signal = ctx->d_sig;
-            a.status = ctx->d_status;
-            auto launch = [&]() { return fp64 ? launch_fwd_f64(a, k, t, stream) : launch_fwd_f32(a, k, t, stream); };
-            if (launch() != 0) {
-                cudaGetLastError();
-                continue;
-            }
-            cudaEventRecord(e0, st);
-            int rc = launch();
-            cudaEventRecord(e1, st);
-            if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < win.ms) win = TunedShape{k, t, ms};
+            if (trial(k, t) < 0.0f) continue;
+            const float ms = trial(k, t);
+            if (ms >= 0.0f) cand.push_back(TunedShape{k, t, ms});
         }
     }
+    std::sort(cand.begin(), cand.end(), [](const TunedShape &x, const TunedShape &y) { return x.ms < y.ms; });
+    if (cand.size() > 3) cand.resize(3);
+    P.n_ops = long_ops;
+    for (TunedShape &c : cand) {
+        c.ms = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            const float ms = trial(c.k, c.threads);
+            if (ms >= 0.0f) c.ms = std::min(c.ms, ms);
+        }
+    }
+    TunedShape win;
+    win.ms = 1e30f;
+    for (const TunedShape &c : cand)
+        if (c.ms < win.ms) win = c;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     mrsim_status ss = mrsim_stream_status(ctx, stream);
