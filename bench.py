@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1305_6861_gb300 import workloads as W  # noqa: E402
+from paper_1305_6861_gb300 import distributed as D  # noqa: E402
 
 METRIC = "spin-steps/s (isochromat×event updates) at 1 GB300, FP32 vs FP64, % FP32/SFU peak"
 # FP32 lane-operations the method needs per spin-step, by event type (pulse-frame formulation):
@@ -56,7 +57,7 @@ def fp32_alu_peak_ops(sm_mhz: float = SM_MAX_MHZ) -> float:
 
 
 def build_workload(name: str, rank: int = 0):
-    seed = None if rank == 0 else W.SEED_BASE + 100 * rank + {"c1": 1, "c2": 2, "c3": 3}[name]
+    seed = D.rank_seed(W.SEED_BASE, {"c1": 1, "c2": 2, "c3": 3}[name], rank)
     if name == "c1":
         return W.config1(seed)
     if name == "c2":
@@ -353,8 +354,7 @@ def run_ours(args):
 
     def step():
         M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
-        if dist:
-            dist.all_reduce(sig)
+        D.reduce_signal(sig)
 
     for _ in range(args.warmup):
         step()
@@ -372,8 +372,7 @@ def run_ours(args):
         kev[i][0].record(stream)
         M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
         kev[i][1].record(stream)
-        if dist:
-            dist.all_reduce(sig)
+        D.reduce_signal(sig)
         ev[i][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall
@@ -381,10 +380,7 @@ def run_ours(args):
     ctx.stream_status(stream)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
     kern_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
+    ms_per_step = D.max_over_ranks(step_ms, device=dev) / args.steps
     spin_steps = w.spin_steps
     value = world * spin_steps / (ms_per_step * 1e-3)
 

@@ -6,7 +6,7 @@ binding of the C-ABI (loaded on first use, never a CPU fallback).
 """
 import importlib
 
-__all__ = ["workloads", "mrsim"]
+__all__ = ["workloads", "mrsim", "autograd", "distributed"]
 
 
 def __getattr__(name):
