@@ -54,9 +54,10 @@ typedef enum {
 
 typedef enum {
     MRSIM_FP64 = 0, /* every step in float64 */
-    MRSIM_FP32 = 1  /* rotations/relaxation in float32 with float64 sequence precompute,
-                       float-float phase arguments, and the per-sample sum kept in float64
-                       across warps and thread blocks */
+    MRSIM_FP32 = 1  /* rotations/relaxation in float32 with float64 sequence precompute and
+                       float-float phase arguments; each sample's sum is a float32 pairwise tree
+                       within a warp, a float32 add across the warps of a thread block and a
+                       float64 sum across thread blocks */
 } mrsim_precision;
 
 /* One elementary sequence (§4.1; Eq. 4.1).  64 bytes, no padding. */
