@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,14 @@ Key key_of(const double k[3], double dt) {
     return key;
 }
 
+struct KeyHash {
+    size_t operator()(const Key &k) const {
+        uint64_t h = 0x9E3779B97F4A7C15ull;
+        for (uint64_t v : k) h = (h ^ v) * 0xBF58476D1CE4E5B9ull;
+        return (size_t)(h ^ (h >> 31));
+    }
+};
+
 bool is_zero(const double k[3], double dt) { return k[0] == 0.0 && k[1] == 0.0 && k[2] == 0.0 && dt == 0.0; }
 
 uint64_t bits(double x) {
@@ -51,8 +60,8 @@ uint64_t bits(double x) {
 }
 
 // Top-`limit` keys by use count (count >= 2), ties broken by first appearance.
-template <class K>
-std::map<K, int> pick_classes(const std::map<K, std::pair<int64_t, int64_t>> &uses, int limit) {
+template <class K, class UseMap>
+std::map<K, int> pick_classes(const UseMap &uses, int limit) {
     std::vector<std::pair<K, std::pair<int64_t, int64_t>>> v(uses.begin(), uses.end());
     std::sort(v.begin(), v.end(), [](const auto &a, const auto &b) {
         if (a.second.first != b.second.first) return a.second.first > b.second.first;
@@ -66,6 +75,29 @@ std::map<K, int> pick_classes(const std::map<K, std::pair<int64_t, int64_t>> &us
     }
     return out;
 }
+
+// cos and sin of x, remembered for repeated arguments: shaped pulses repeat their flip angles
+// every TR and the receiver phase is constant along a readout, so most calls are lookups.
+class TrigCache {
+    struct Entry {
+        uint64_t key;
+        double c, s;
+        bool ok;
+    };
+    static constexpr size_t N = 4096;
+    std::vector<Entry> t_;
+
+  public:
+    TrigCache() : t_(N, Entry{0, 0.0, 0.0, false}) {}
+    void get(double x, double &c, double &s) {
+        uint64_t b;
+        std::memcpy(&b, &x, 8);
+        Entry &e = t_[(b ^ (b >> 23) ^ (b >> 41)) & (N - 1)];
+        if (!(e.ok && e.key == b)) e = Entry{b, std::cos(x), std::sin(x), true};
+        c = e.c;
+        s = e.s;
+    }
+};
 
 void split(double v, float &hi, float &lo) {
     hi = (float)v;
@@ -175,8 +207,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             ++i;
         }
     }
-    std::map<Key, std::pair<int64_t, int64_t>> puses;  // key -> (count, first position)
-    std::map<uint64_t, std::pair<int64_t, int64_t>> e1uses, e2uses;
+    std::unordered_map<Key, std::pair<int64_t, int64_t>, KeyHash> puses;  // key -> (count, first position)
+    std::unordered_map<uint64_t, std::pair<int64_t, int64_t>> e1uses, e2uses;
     auto use = [](auto &m, const auto &key, int64_t cnt, int64_t pos) {
         auto it = m.find(key);
         if (it == m.end())
@@ -197,8 +229,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         }
         if ((it.kind == Item::RF || it.kind == Item::END) && it.tau > 0.0) use(e1uses, bits(it.tau), 1, pos);
     }
-    auto pmap = pick_classes(puses, MAX_PCLS);
-    auto e1map = pick_classes(e1uses, MAX_E1CLS);
+    auto pmap = pick_classes<Key>(puses, MAX_PCLS);
+    auto e1map = pick_classes<uint64_t>(e1uses, MAX_E1CLS);
     // E2 classes: intervals of the precessions that stay inline
     for (size_t g = 0; g < groups.size(); ++g) {
         const Item &it = items[groups[g].first];
@@ -206,7 +238,7 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             !pmap.count(key_of(it.k, it.dt)))
             use(e2uses, bits(it.dt), groups[g].n, (int64_t)groups[g].first);
     }
-    auto e2map = pick_classes(e2uses, MAX_E2CLS);
+    auto e2map = pick_classes<uint64_t>(e2uses, MAX_E2CLS);
 
     out.n_pcls = (int)pmap.size();
     out.n_e1 = (int)e1map.size();
@@ -225,6 +257,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     double psi = 0.0;
     int pcache = -1, e1cache = -1;
     out.demod.assign(2 * (size_t)out.n_adc, 0.0);
+    out.ops32.reserve(groups.size() + 1);
+    out.ops64.reserve(groups.size() + 1);
     auto new32 = [](uint8_t kind) {
         OpF32 o;
         std::memset(&o, 0, sizeof o);
@@ -247,10 +281,13 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         a.flags |= fl;
         b.flags |= fl;
     };
+    TrigCache trig;
     auto demod = [&](int64_t jj, double adc_phase) {
         // sample sum in the frame ψ: Σ(u + jv) = e^{-jψ} Σ(Mx + jMy), so the factor is e^{-j(φ_adc - ψ)}
-        out.demod[2 * (size_t)jj] = std::cos(adc_phase - psi);
-        out.demod[2 * (size_t)jj + 1] = -std::sin(adc_phase - psi);
+        double c, sn;
+        trig.get(adc_phase - psi, c, sn);
+        out.demod[2 * (size_t)jj] = c;
+        out.demod[2 * (size_t)jj + 1] = -sn;
     };
     auto set_e1 = [&](OpF32 &a, OpF64 &b, double t) {
         if (t > 0.0) {
@@ -295,7 +332,59 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             a.ecls = b.ecls = (int16_t)e2->second;
         }
     };
+    // Sub-pulse trains (Eq. 3.23): a run of 2..RUN_MAX consecutive fast sub-pulses becomes one
+    // OP_RF_TRAIN over a table of (cos α, sin α) pairs; identical runs (the same shaped pulse
+    // every TR) share table entries.  Fast sub-pulses wait in `pend` until their run ends.
+    std::vector<OpF32> pend32;
+    std::vector<OpF64> pend64;
+    std::map<std::vector<uint64_t>, int> seen;
+    std::vector<uint64_t> tkey;
+    auto flush_train = [&]() {
+        const size_t n = pend32.size();
+        if (n >= 2) {
+            tkey.clear();
+            for (size_t q = 0; q < n; ++q) {
+                tkey.push_back(bits(pend64[q].f[0]));
+                tkey.push_back(bits(pend64[q].f[1]));
+            }
+            auto it = seen.find(tkey);
+            int off = -1;
+            if (it != seen.end()) {
+                off = it->second;
+            } else if ((int64_t)(out.train.size() / 2 + n) <= TRAIN_TABLE_MAX) {
+                off = (int)(out.train.size() / 2);
+                for (size_t q = 0; q < n; ++q) {
+                    out.train.push_back(pend64[q].f[0]);
+                    out.train.push_back(pend64[q].f[1]);
+                }
+                seen.emplace(tkey, off);
+            }
+            if (off >= 0) {
+                OpF32 a = pend32[0];
+                OpF64 b = pend64[0];
+                a.kind = b.kind = OP_RF_TRAIN;
+                a.n = b.n = (int32_t)n;
+                a.adc0 = b.adc0 = off;
+                out.ops32.push_back(a);
+                out.ops64.push_back(b);
+                pend32.clear();
+                pend64.clear();
+                return;
+            }
+        }
+        out.ops32.insert(out.ops32.end(), pend32.begin(), pend32.end());
+        out.ops64.insert(out.ops64.end(), pend64.begin(), pend64.end());
+        pend32.clear();
+        pend64.clear();
+    };
     auto push = [&](const OpF32 &a, const OpF64 &b) {
+        if (a.kind == OP_RF_FAST) {
+            pend32.push_back(a);
+            pend64.push_back(b);
+            if ((int64_t)pend32.size() == RUN_MAX) flush_train();
+            return;
+        }
+        flush_train();
         out.ops32.push_back(a);
         out.ops64.push_back(b);
     };
@@ -309,19 +398,22 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             if (it.phi != psi) {
                 // turn the frame from ψ to φ: (u + jv) <- (u + jv)·exp(-jδ), δ = φ - ψ; the float32
                 // program gets (hi, lo) pairs so that the frame never drifts (it is uniform over spins)
-                const double d = it.phi - psi;
+                double cd, sd;
+                trig.get(it.phi - psi, cd, sd);
                 both(a, b, F_FRAME);
-                split(std::cos(d), a.f[2], a.f[3]);
-                split(std::sin(d), a.f[4], a.f[5]);
-                b.f[2] = std::cos(d);
-                b.f[3] = std::sin(d);
+                split(cd, a.f[2], a.f[3]);
+                split(sd, a.f[4], a.f[5]);
+                b.f[2] = cd;
+                b.f[3] = sd;
                 psi = it.phi;
             }
             set_e1(a, b, it.tau);
-            a.f[0] = (float)std::cos(it.alpha);
-            a.f[1] = (float)std::sin(it.alpha);
-            b.f[0] = std::cos(it.alpha);
-            b.f[1] = std::sin(it.alpha);
+            double ca, sa;
+            trig.get(it.alpha, ca, sa);
+            a.f[0] = (float)ca;
+            a.f[1] = (float)sa;
+            b.f[0] = ca;
+            b.f[1] = sa;
             // fuse a following class precession (the sub-pulse trains of shaped pulses, Eq. 3.23)
             if (g + 1 < groups.size()) {
                 const Item &nx = items[groups[g + 1].first];
@@ -399,67 +491,18 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             OpF64 b = new64(OP_END);
             set_e1(a, b, it.tau);
             // back to the laboratory frame for the final state: (Mx + jMy) = (u + jv)·exp(+jψ)
-            a.f[0] = (float)std::cos(psi);
-            a.f[1] = (float)std::sin(psi);
-            b.f[0] = std::cos(psi);
-            b.f[1] = std::sin(psi);
+            double cp, sp;
+            trig.get(psi, cp, sp);
+            a.f[0] = (float)cp;
+            a.f[1] = (float)sp;
+            b.f[0] = cp;
+            b.f[1] = sp;
             push(a, b);
             break;
         }
         }
     }
-    // ---- sub-pulse trains: runs of fast sub-pulses become one operation over a table of
-    // (cos α, sin α) pairs; identical trains (e.g. the same shaped pulse every TR) share entries.
-    {
-        std::vector<OpF32> o32;
-        std::vector<OpF64> o64;
-        o32.reserve(out.ops32.size());
-        o64.reserve(out.ops64.size());
-        std::map<std::vector<uint64_t>, int> seen;
-        for (size_t i = 0; i < out.ops32.size();) {
-            size_t e = i;
-            while (e < out.ops32.size() && out.ops32[e].kind == OP_RF_FAST && (int64_t)(e - i) < RUN_MAX) ++e;
-            const size_t n = e - i;
-            if (n >= 2) {
-                std::vector<uint64_t> key;
-                key.reserve(2 * n);
-                for (size_t q = i; q < e; ++q) {
-                    key.push_back(bits(out.ops64[q].f[0]));
-                    key.push_back(bits(out.ops64[q].f[1]));
-                }
-                auto it = seen.find(key);
-                int off = -1;
-                if (it != seen.end()) {
-                    off = it->second;
-                } else if ((int64_t)(out.train.size() / 2 + n) <= TRAIN_TABLE_MAX) {
-                    off = (int)(out.train.size() / 2);
-                    for (size_t q = i; q < e; ++q) {
-                        out.train.push_back(out.ops64[q].f[0]);
-                        out.train.push_back(out.ops64[q].f[1]);
-                    }
-                    seen[key] = off;
-                }
-                if (off >= 0) {
-                    OpF32 a = out.ops32[i];
-                    OpF64 b = out.ops64[i];
-                    a.kind = b.kind = OP_RF_TRAIN;
-                    a.n = b.n = (int32_t)n;
-                    a.adc0 = b.adc0 = off;
-                    o32.push_back(a);
-                    o64.push_back(b);
-                    i = e;
-                    continue;
-                }
-            }
-            for (size_t q = i; q < std::max(e, i + 1); ++q) {
-                o32.push_back(out.ops32[q]);
-                o64.push_back(out.ops64[q]);
-            }
-            i = std::max(e, i + 1);
-        }
-        out.ops32.swap(o32);
-        out.ops64.swap(o64);
-    }
+    flush_train();
     if (out.n_adc > (int64_t)INT32_MAX) {
         err = "too many ADC samples";
         return MRSIM_EINVAL;
