@@ -63,6 +63,9 @@ def _bind(path):
     lib.oracle_simulate_rf.restype = ctypes.c_int
     lib.oracle_simulate_rf.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                        i32p, d, d, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_simulate_coils.restype = ctypes.c_int
+    lib.oracle_simulate_coils.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_int32, d, d, ctypes.c_int64, ctypes.c_int]
     lib.oracle_gradient.restype = ctypes.c_int
     lib.oracle_gradient.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                     i32p, d, d, ctypes.c_int64, d, d, d, i32p, ctypes.c_int32, d, ctypes.c_int]
@@ -132,6 +135,26 @@ def simulate_rf(phantom, events, gamma_hz_per_t, rf_param, rf_values, n_threads=
     if rc != 0:
         raise RuntimeError(f"oracle_simulate_rf failed with code {rc}")
     return sig.view(np.complex128)
+
+
+def simulate_coils(phantom, events, gamma_hz_per_t, sens, n_threads=0, lib=None):
+    """Receive-coil signals (Eq. 3.25 with per-spin sensitivities): sens is complex
+    [n_coils, n_spins]; returns complex128 [n_coils, n_adc]."""
+    lib = _load() if lib is None else lib
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    arrs = [np.ascontiguousarray(getattr(phantom, k), dtype=np.float64) for k in ("x", "y", "z", "rho", "t1", "t2", "dw")]
+    n = arrs[0].shape[0]
+    c = np.ascontiguousarray(np.asarray(sens, dtype=np.complex128))
+    if c.ndim != 2 or c.shape[1] != n:
+        raise ValueError("sens must be [n_coils, n_spins]")
+    n_adc = int(np.count_nonzero(ev["adc"]))
+    sig = np.zeros(2 * n_adc * c.shape[0])
+    rc = lib.oracle_simulate_coils(n, *[_dp(a) for a in arrs], ev.shape[0], ev.ctypes.data_as(ctypes.c_void_p),
+                                   float(gamma_hz_per_t), int(c.shape[0]), _dp(c.view(np.float64).reshape(-1)),
+                                   _dp(sig), n_adc, int(n_threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_simulate_coils failed with code {rc}")
+    return sig.view(np.complex128).reshape(c.shape[0], n_adc)
 
 
 def gradient(phantom, events, gamma_hz_per_t, h, rf_param=None, rf_values=None, sel=(), n_threads=0, lib=None):

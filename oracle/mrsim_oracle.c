@@ -172,6 +172,74 @@ int oracle_simulate(int64_t n_spins, const double *x, const double *y, const dou
     return 0;
 }
 
+/*
+ * Forward simulation with receive-coil weighting (Eq. 3.25; §6.1 "Inhomogenitäten der
+ * Empfangssensitivität"): before the superposition of a sample, each spin's magnetisation is
+ * weighted with its coil's receive sensitivity, the scalar product of Eq. 3.25 taken as the
+ * complex product C·(Mx + jMy) of a transverse sensitivity C with the transverse magnetisation.
+ *   sens:   n_coils*n_spins complex values, interleaved (re, im), coil-major: C[c][s]
+ *   signal: n_coils*2*n_adc doubles, coil-major, overwritten:
+ *           signal_c[j] = exp(-j adc_phase_j) * sum_s C[c][s] * (Mx + jMy)_s
+ * Every spin starts in thermal equilibrium.  Returns as oracle_simulate.
+ */
+int oracle_simulate_coils(int64_t n_spins, const double *x, const double *y, const double *z,
+                          const double *rho, const double *t1, const double *t2, const double *dw,
+                          int64_t n_events, const void *events, double gamma_hz_per_t,
+                          int32_t n_coils, const double *sens, double *signal, int64_t n_adc,
+                          int n_threads)
+{
+    const oracle_event *ev = (const oracle_event *)events;
+    if (count_adc(ev, n_events) != n_adc || n_coils < 1) return -1;
+    const double gamma = ORACLE_TWO_PI * gamma_hz_per_t;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+#endif
+    const size_t per = (size_t)n_coils * (size_t)(2 * n_adc) + 1;
+    double *partial = (double *)calloc((size_t)nt * per, sizeof(double));
+    if (!partial) return -2;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = partial + (size_t)tid * per;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t s = 0; s < n_spins; ++s) {
+            double M[3] = {0.0, 0.0, rho[s]};
+            int64_t j = 0;
+            for (int64_t e = 0; e < n_events; ++e) {
+                if (apply_event(&ev[e], gamma, x[s], y[s], z[s], rho[s], t1[s], t2[s], dw[s], M)) {
+                    const double cph = cos(ev[e].adc_phase), sph = sin(ev[e].adc_phase);
+                    const double wr = M[0] * cph + M[1] * sph, wi = M[1] * cph - M[0] * sph;
+                    for (int32_t c = 0; c < n_coils; ++c) {
+                        const double cr = sens[2 * ((size_t)c * (size_t)n_spins + (size_t)s)];
+                        const double ci = sens[2 * ((size_t)c * (size_t)n_spins + (size_t)s) + 1];
+                        double *sig = mine + (size_t)c * (size_t)(2 * n_adc);
+                        sig[2 * j] += cr * wr - ci * wi;
+                        sig[2 * j + 1] += cr * wi + ci * wr;
+                    }
+                    ++j;
+                }
+            }
+        }
+    }
+    memset(signal, 0, sizeof(double) * (per - 1));
+    for (int t = 0; t < nt; ++t) {
+        const double *p = partial + (size_t)t * per;
+        for (size_t i = 0; i + 1 < per; ++i) signal[i] += p[i];
+    }
+    free(partial);
+    return 0;
+}
+
 /* Forward simulation with learnable flip angles: as oracle_simulate, but event e's flip angle is
  * rf_values[rf_param[e]] wherever rf_param[e] >= 0. */
 int oracle_simulate_rf(int64_t n_spins, const double *x, const double *y, const double *z,
