@@ -43,13 +43,25 @@ OPS_ADC, OPS_RF, OPS_OTHER = 6, 10, 4
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
-def algorithmic_ops_per_spin(events) -> int:
+def algorithmic_ops_per_spin(events, n_coils: int = 0) -> int:
+    """FP32 lane-ops per spin over the sequence; with receive coils a sample costs the precession
+    (4) plus one weighted complex accumulation per coil (4, the sum folded into the FMAs)."""
+    ops_adc = OPS_ADC if n_coils == 0 else 4 + 4 * n_coils
     adc = events["adc"] != 0
     rf = (events["rf_flip"] != 0) & ~adc
     other = ~adc & ~rf
     n_rf_adc = int(np.count_nonzero((events["rf_flip"] != 0) & adc))
-    return int(OPS_ADC * np.count_nonzero(adc) + OPS_RF * np.count_nonzero(rf) + OPS_OTHER * np.count_nonzero(other)
+    return int(ops_adc * np.count_nonzero(adc) + OPS_RF * np.count_nonzero(rf) + OPS_OTHER * np.count_nonzero(other)
                + (OPS_RF - OPS_OTHER + 2) * n_rf_adc)
+
+
+def ring_coils(phantom, n_coils: int, radius: float = 0.3, width: float = 0.25):
+    """Synthetic array-coil sensitivities: Gaussian magnitude around n coils on a ring, phase
+    growing along the ring; complex [n_coils, n_spins]."""
+    ang = 2 * math.pi * np.arange(n_coils) / n_coils
+    cx, cy = radius * np.cos(ang), radius * np.sin(ang)
+    d2 = (phantom.x[None, :] - cx[:, None]) ** 2 + (phantom.y[None, :] - cy[:, None]) ** 2
+    return np.exp(-d2 / width**2) * np.exp(1j * (ang[:, None] + 4.0 * phantom.x[None, :] * np.cos(ang)[:, None]))
 
 
 def fp32_alu_peak_ops(sm_mhz: float = SM_MAX_MHZ) -> float:
@@ -339,7 +351,11 @@ def run_ours(args):
     arrs = [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()]
     ph = M.Phantom(ctx, arrs, stream=stream)
     seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
-    sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64, device=dev)
+    n_coils = args.coils
+    sig = torch.zeros(2 * seq.n_adc * max(n_coils, 1), dtype=torch.float64, device=dev)
+    sens_dev = None
+    if n_coils:
+        sens_dev = torch.from_numpy(ring_coils(w.phantom, n_coils).view(np.float64).reshape(-1).copy()).to(dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     kw = {}
     if args.spins_per_thread:
@@ -347,13 +363,19 @@ def run_ours(args):
     if args.threads:
         kw["threads_per_block"] = args.threads
     tuned = None
-    if not kw and not args.no_tune:  # autotune the launch shape (part of warm-up, outside the timed region)
+    if not kw and not args.no_tune and not n_coils:  # autotune the launch shape (part of warm-up, outside the timed region)
         t0 = time.perf_counter()
         tuned = M.autotune(ctx, ph, seq, prec, stream=stream)
         tuned = {"spins_per_thread": tuned[0], "threads_per_block": tuned[1], "tune_s": time.perf_counter() - t0}
 
+    def simulate_once():
+        if n_coils:
+            M.simulate_coils(ctx, ph, seq, sens_dev, prec, stream=stream, out=sig)
+        else:
+            M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
+
     def step():
-        M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
+        simulate_once()
         D.reduce_signal(sig)
 
     for _ in range(args.warmup):
@@ -370,7 +392,7 @@ def run_ours(args):
         flush_buf.zero_()  # L2 flush between timed steps (outside the step's events)
         ev[i][0].record(stream)
         kev[i][0].record(stream)
-        M.simulate(ctx, ph, seq, prec, stream=stream, out=sig, **kw)
+        simulate_once()
         kev[i][1].record(stream)
         D.reduce_signal(sig)
         ev[i][1].record(stream)
@@ -385,17 +407,17 @@ def run_ours(args):
     value = world * spin_steps / (ms_per_step * 1e-3)
 
     # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
-    ops = algorithmic_ops_per_spin(w.sequence.events) * w.phantom.n
+    ops = algorithmic_ops_per_spin(w.sequence.events, n_coils) * w.phantom.n
     achieved = ops / (kern_ms * 1e-3) / 1e9
     peak = fp32_alu_peak_ops() / 1e9
     sha = kernel_source_sha()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
-            "traffic": traffic_for(sha, w.name), "kernel_ms": kern_ms,
+            "traffic": traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else "")), "kernel_ms": kern_ms,
             "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
             "ops_per_spin_step": ops / spin_steps}
 
     out = {}
-    if rank == 0 and not args.skip_extra:
+    if rank == 0 and not args.skip_extra and not n_coils:
         # float64 GPU path on the same workload, and its agreement with float32
         s32 = sig.clone()
         if dist:
@@ -453,7 +475,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
-            "config": {"workload": w.name, "n_spins_per_gpu": w.phantom.n, "n_events": w.sequence.n_events,
+            "config": {"workload": w.name + (f"_{n_coils}coils" if n_coils else ""), "n_spins_per_gpu": w.phantom.n,
+                       "n_events": w.sequence.n_events,
                        "n_adc": seq.n_adc, "n_ops": seq.n_ops, "spin_steps_per_gpu_step": spin_steps,
                        "precision": args.precision, "launch": kw or tuned or "library default",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
@@ -484,6 +507,7 @@ def main():
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--events", type=int, default=0, help="use only the first N events (profiling cases)")
+    ap.add_argument("--coils", type=int, default=0, help="receive coils (ring sensitivities), 0 = plain signal")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

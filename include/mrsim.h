@@ -146,6 +146,25 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
                                mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc,
                                const mrsim_options *opt);
 
+/* ---- receive coils ------------------------------------------------------------------------- */
+
+/* Signals of n_coils receive coils with inhomogeneous sensitivities.  Eq. 3.25 weights every
+ * spin's magnetisation with the coil's receive sensitivity before the superposition (§6.1,
+ * "Inhomogenitäten der Empfangssensitivität"; §9 names separate signals per array coil as the
+ * wanted extension); for a transverse sensitivity the scalar product is the complex product
+ *     signal_c[j] = exp(-j adc_phase_j) · Σ_s C[c][s] · (Mx + jMy)_s(t_j).
+ * A homogeneous C = 1 gives mrsim_simulate's signal (§3.5.2).
+ *   n_coils:    1..MRSIM_MAX_COILS
+ *   sens:       C, n_coils x n_spins complex float64 interleaved (re, im), coil-major; host or
+ *               device memory, read during the call (EINVAL if a value is not finite)
+ *   signal_out: n_coils x 2*n_adc doubles, coil-major (re, im); host or device
+ * Every spin starts in thermal equilibrium.  The rotations are computed once per spin and
+ * shared by the coils.  Host output synchronises `stream`; device output is asynchronous. */
+#define MRSIM_MAX_COILS 8
+mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                                  mrsim_precision prec, void *stream, int32_t n_coils, const double *sens,
+                                  double *signal_out, int64_t n_adc);
+
 /* ---- batches: many phantoms with their own sequences in one persistent launch ---------- */
 
 /* A batch borrows n phantom/sequence pairs (they must outlive it) and one device signal buffer

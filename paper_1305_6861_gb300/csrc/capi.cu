@@ -165,6 +165,7 @@ void mrsim_context_destroy(mrsim_ctx *ctx) {
     cudaFree(ctx->d_sig);
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_sens);
     delete ctx;
 }
 
@@ -377,6 +378,75 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     if (host_out) CK(cudaMemcpyAsync(o.state_out, dout, st_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy state out");
     if (host_sig) CK(cudaMemcpyAsync(signal_out, dsig, sig_bytes, cudaMemcpyDeviceToHost, st), "copy signal out");
     if (host_sig || host_out) return mrsim_stream_status(ctx, stream);
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                                  mrsim_precision prec, void *stream, int32_t n_coils, const double *sens,
+                                  double *signal_out, int64_t n_adc) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
+    if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
+    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (n_coils < 1 || n_coils > MAX_COILS)
+        return fail(ctx, MRSIM_EINVAL, "n_coils must be 1.." + std::to_string(MAX_COILS));
+    if (n_adc != seq->host.n_adc)
+        return fail(ctx, MRSIM_EINVAL, "n_adc = " + std::to_string(n_adc) + " but the sequence has " +
+                                           std::to_string(seq->host.n_adc) + " samples");
+    if (ph->n > 0 && !sens) return fail(ctx, MRSIM_EINVAL, "NULL sensitivities");
+    if (n_adc > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal buffer");
+    const bool fp64 = prec == MRSIM_FP64;
+    const int threads = 128, k = fp64 ? 1 : 2;
+    const Program &P = fp64 ? seq->p64 : seq->p32;
+    if (fwd_smem_bytes(fp64, P, k, threads) > (size_t)ctx->max_smem_optin)
+        return fail(ctx, MRSIM_EUNSUPPORTED, "shared memory of this program exceeds the device limit");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    mrsim_status rs;
+    // sensitivities into the kernel's layout (validated on the device)
+    const int64_t n = ph->n;
+    const double *dsrc = sens;
+    if (n > 0 && !is_device_ptr(sens)) {
+        if ((rs = grow(ctx, &ctx->d_stage, &ctx->stage_cap, (size_t)2 * n_coils * (size_t)n)) != MRSIM_OK) return rs;
+        CK(cudaMemcpyAsync(ctx->d_stage, sens, sizeof(double) * 2 * (size_t)n_coils * (size_t)n, cudaMemcpyHostToDevice, st),
+           "copy sensitivities");
+        dsrc = ctx->d_stage;
+    }
+    const size_t sens_doubles = (size_t)n_coils * (size_t)ph->n_pad * (fp64 ? 2 : 1);
+    if ((rs = grow(ctx, &ctx->d_sens, &ctx->sens_cap, std::max<size_t>(sens_doubles, 1))) != MRSIM_OK) return rs;
+    if (n > 0) {
+        const int big = 0x7fffffff;
+        int bad = big;
+        CK(cudaMemcpyAsync(ctx->d_bad, &big, sizeof(int), cudaMemcpyHostToDevice, st), "reset check");
+        const int rc = pack_sens(n_coils, n, ph->n_pad, dsrc, ctx->d_sens, !fp64, ctx->d_bad, st);
+        if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "pack sensitivities");
+        CK(cudaMemcpyAsync(&bad, ctx->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read check");
+        CK(cudaStreamSynchronize(st), "stream synchronize");
+        if (bad != big) return fail(ctx, MRSIM_EINVAL, "sensitivity " + std::to_string(bad) + " is not finite");
+    }
+    const size_t sig_doubles = (size_t)n_coils * 2 * (size_t)n_adc;
+    const bool host_sig = n_adc > 0 && !is_device_ptr(signal_out);
+    double *dsig = signal_out;
+    if (host_sig) {
+        if ((rs = grow(ctx, &ctx->d_sig, &ctx->sig_cap, sig_doubles)) != MRSIM_OK) return rs;
+        dsig = ctx->d_sig;
+    }
+    if (n_adc > 0) CK(cudaMemsetAsync(dsig, 0, sig_doubles * sizeof(double), st), "clear signal");
+    FwdArgs a{};
+    a.prog = P;
+    a.params = ph->params;
+    a.n_spins = ph->n;
+    a.n_pad = ph->n_pad;
+    a.signal = dsig;
+    a.status = ctx->d_status;
+    a.sens = ctx->d_sens;
+    a.n_coils = n_coils;
+    const int rc = fp64 ? launch_fwd_coils_f64(a, threads, stream) : launch_fwd_coils_f32(a, threads, stream);
+    if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel (coils)");
+    if (host_sig) {
+        CK(cudaMemcpyAsync(signal_out, dsig, sig_doubles * sizeof(double), cudaMemcpyDeviceToHost, st), "copy signal out");
+        return mrsim_stream_status(ctx, stream);
+    }
     return MRSIM_OK;
 }
 

@@ -75,6 +75,34 @@ __global__ void pack_kernel(int64_t n, int64_t np, const double *x, const double
     }
 }
 
+__global__ void pack_sens_kernel(int32_t n_coils, int64_t n, int64_t n_pad, const double *src, void *dst, bool f32,
+                                 int *bad) {
+    const int64_t total = (int64_t)n_coils * n_pad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / n_pad, s = i % n_pad;
+        double re = 0.0, im = 0.0;
+        if (s < n) {
+            re = src[2 * (c * n + s)];
+            im = src[2 * (c * n + s) + 1];
+            if (!isfinite(re) || !isfinite(im)) atomicMin(bad, (int)min(c * n + s, (int64_t)0x7ffffffe));
+        }
+        if (f32)
+            reinterpret_cast<float2 *>(dst)[i] = make_float2((float)re, (float)im);
+        else
+            reinterpret_cast<double2 *>(dst)[i] = make_double2(re, im);
+    }
+}
+
+int pack_sens(int32_t n_coils, int64_t n, int64_t n_pad, const double *src, void *dst, bool f32, int *bad,
+              void *stream) {
+    const int64_t total = (int64_t)n_coils * n_pad;
+    if (total <= 0) return 0;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    pack_sens_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n_coils, n, n_pad, src, dst, f32, bad);
+    return (int)cudaGetLastError();
+}
+
 // Zero the signal buffers of a batch (one launch instead of one memset per phantom).
 __global__ void zero_signals_kernel(const FwdArgs *descs, int n) {
     for (int d = 0; d < n; ++d) {
@@ -98,6 +126,14 @@ int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, cons
     if (blocks > 152 * 16) blocks = 152 * 16;
     pack_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, n_pad, x, y, z, rho, t1, t2, dw, params, bad);
     return (int)cudaGetLastError();
+}
+
+int launch_fwd_coils_f64(const FwdArgs &a, int threads, void *stream) {
+    if (a.n_coils <= 1) return dev::launch_one<double, 1, 256, 1>(a, threads, stream);
+    if (a.n_coils <= 2) return dev::launch_one<double, 1, 256, 2>(a, threads, stream);
+    if (a.n_coils <= 4) return dev::launch_one<double, 1, 256, 4>(a, threads, stream);
+    if (a.n_coils <= MAX_COILS) return dev::launch_one<double, 1, 256, 8>(a, threads, stream);
+    return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace mrsim

@@ -313,7 +313,59 @@ static __device__ __noinline__ void flush_window_f32(float *win, const float *de
     __syncthreads();
 }
 
-template <typename R, int K>
+// With receive coils the window holds NCR slots per sample (one per coil row): slot v
+// is sample win_base + v / NCR of coil v % NCR, whose signal starts at signal + coil * coil_stride.
+// Padding coils (coil >= n_coils) are not written.
+
+// Receive coils, float64: as flush_window with coil-major slots.
+template <typename R, int NCR>
+__device__ __noinline__ void flush_window_coils(const R *red, const double *demod, double *signal, int win_base,
+                                          int win_end, int tid, int nthr, int nwarp, int n_coils,
+                                          int64_t coil_stride) {
+    __syncthreads();
+    const int cnt = (win_end - win_base) * NCR;
+    for (int s = tid; s < cnt; s += nthr) {
+        const int coil = s % NCR;
+        if (coil >= n_coils) continue;
+        double re = 0.0, im = 0.0;
+        for (int w = 0; w < nwarp; ++w) {
+            re += (double)red[w * 2 * RED_STRIDE + s];
+            im += (double)red[w * 2 * RED_STRIDE + RED_STRIDE + s];
+        }
+        const int64_t j = (int64_t)win_base + s / NCR;
+        const double cr = demod[2 * j], ci = demod[2 * j + 1];
+        double *sig = signal + coil * coil_stride;
+        atomicAdd(sig + 2 * j, re * cr - im * ci);
+        atomicAdd(sig + 2 * j + 1, re * ci + im * cr);
+    }
+    __syncthreads();
+}
+
+// Receive coils, float32: as flush_window_f32 with coil-major slots.
+template <int NCR>
+static __device__ __noinline__ void flush_window_coils_f32(float *win, const float *demod32, double *signal, int win_base,
+                                                     int win_end, int tid, int nthr, int n_coils,
+                                                     int64_t coil_stride) {
+    __syncthreads();
+    const int cnt = (win_end - win_base) * NCR;
+    for (int s = tid; s < cnt; s += nthr) {
+        const float re = win[s], im = win[WIN_STRIDE + s];
+        win[s] = 0.0f;
+        win[WIN_STRIDE + s] = 0.0f;
+        const int coil = s % NCR;
+        if (coil >= n_coils) continue;
+        const int64_t j = (int64_t)win_base + s / NCR;
+        const float2 d = reinterpret_cast<const float2 *>(demod32)[j];
+        double *sig = signal + coil * coil_stride;
+        atomicAdd(sig + 2 * j, (double)(re * d.x - im * d.y));
+        atomicAdd(sig + 2 * j + 1, (double)(re * d.y + im * d.x));
+    }
+    __syncthreads();
+}
+
+// NC > 0: receive coils (Eq. 3.25 with per-spin sensitivities): each sample yields NC weighted
+// sums (NC = 1, 2, 4 or 8; the caller's coils beyond n_coils have zero weight and are not stored).
+template <typename R, int K, int NC = 0>
 struct Spins {
     using Op = typename std::conditional<std::is_same<R, float>::value, OpF32, OpF64>::type;
     using P = typename Packing<R, K>::P;
@@ -321,13 +373,19 @@ struct Spins {
     static constexpr int L = Packing<R, K>::L;  // spins per packed value
     static constexpr int NP = K / L;            // packed values per quantity
     static constexpr bool F64 = std::is_same<R, double>::value;
-    static constexpr int WIN = F64 ? SAMPLE_WINDOW_F64 : SAMPLE_WINDOW_F32;
+    static constexpr int WIN = F64 ? SAMPLE_WINDOW_F64 : SAMPLE_WINDOW_F32;  // window slots
+    static constexpr int NCR = NC > 0 ? NC : 1;                                // slots per sample
+    static constexpr int WINS = WIN / NCR;                                     // samples per window
+    static_assert(NCR == 1 || NCR == 2 || NCR == 4 || NCR == 8, "coil rows per sample: 1, 2, 4 or 8");
 
     // spin i = q + h·NP of the thread is lane h of packed value q
     P u[NP], v[NP], mz[NP], rho[NP];  // transverse part in the pulse frame, longitudinal, M0
     P wr[NP], wi[NP], nwi[NP];        // cached phasor class (nwi = −wi, kept for the pairs only)
     P e1v[NP];                        // cached T1 class ε1
+    P cre[NCR][NP], cim[NCR][NP], cnim[NCR][NP];  // coils: sensitivities C = cre + j·cim (cnim = −cim)
     int win_base, win_end;
+    int n_coils;          // receive coils stored (<= NCR)
+    int64_t coil_stride;  // doubles between two coils' signals (2·n_adc)
 
     // shared-memory views and block geometry
     const CwT *cw;
@@ -583,11 +641,137 @@ struct Spins {
     __device__ __forceinline__ R *red_row(int comp) { return red + warp * 2 * RED_STRIDE + comp * RED_STRIDE; }
 
     __device__ __forceinline__ void flush() {
-        if constexpr (F64)
+        if constexpr (NC > 0) {
+            if constexpr (F64)
+                flush_window_coils<R, NCR>(red, demod, signal, win_base, win_end, tid, nthr, nwarp, n_coils,
+                                           coil_stride);
+            else
+                flush_window_coils_f32<NCR>(win, demod32, signal, win_base, win_end, tid, nthr, n_coils, coil_stride);
+        } else if constexpr (F64) {
             flush_window(red, demod, signal, win_base, win_end, tid, nthr, nwarp);
-        else
+        } else {
             flush_window_f32(win, demod32, signal, win_base, win_end, tid, nthr);
+        }
         win_base = win_end;
+    }
+
+    // ---- receive coils ----------------------------------------------------------------------
+    // the thread's spins weighted with coil c's sensitivities: Σ_k C_ck·(u_k + j v_k)
+    __device__ __forceinline__ void coil_sum(int c, R &sx, R &sy) {
+        P re = vfma(v[0], cnim[c][0], vmul(u[0], cre[c][0]));
+        P im = vfma(u[0], cim[c][0], vmul(v[0], cre[c][0]));
+#pragma unroll
+        for (int q = 1; q < NP; ++q) {
+            re = vfma(v[q], cnim[c][q], vfma(u[q], cre[c][q], re));
+            im = vfma(u[q], cim[c][q], vfma(v[q], cre[c][q], im));
+        }
+        sx = hsum(re);
+        sy = hsum(im);
+    }
+    // tt (<= 16 / NCR) sample steps of a run; row s·NCR + c of the tile is sample s, coil c; the
+    // warp total of value l (row l/2, component l%2) ends up in lane l
+    template <bool FULL_TILE>
+    __device__ __forceinline__ R coil_tile(int tt) {
+        constexpr int TS = 16 / NCR;
+        if constexpr (F64) {
+            R vv[32];
+#pragma unroll
+            for (int t = 0; t < TS; ++t) {
+                if (FULL_TILE || t < tt) rot_w();
+#pragma unroll
+                for (int c = 0; c < NCR; ++c) {
+                    const int r = t * NCR + c;
+                    if (FULL_TILE || t < tt) {
+                        coil_sum(c, vv[2 * r], vv[2 * r + 1]);
+                    } else {
+                        vv[2 * r] = (R)0;
+                        vv[2 * r + 1] = (R)0;
+                    }
+                }
+            }
+            return transpose_reduce32(vv, lane);
+        } else {
+            f2 vt[16];
+#pragma unroll
+            for (int t = 0; t < TS; ++t) {
+                if (FULL_TILE || t < tt) rot_w();
+#pragma unroll
+                for (int c = 0; c < NCR; ++c) {
+                    R sx = 0.0f, sy = 0.0f;
+                    if (FULL_TILE || t < tt) coil_sum(c, sx, sy);
+                    vt[t * NCR + c] = pk2(sx, sy);
+                }
+            }
+            return tile_reduce_pairs(vt, lane, tile);
+        }
+    }
+    // a sample run with coils: the window holds WINS samples, so long runs go in window-sized
+    // chunks with a flush in between (every thread of the block takes the same path)
+    __device__ __forceinline__ void run_coils(const Op &op) {
+        constexpr int TS = 16 / NCR;
+        const int n = op.n, j0 = op.adc0;
+        if (op.flags & F_PLOAD) load_w(op.pcls);
+        P au[NP], av[NP];
+        const bool anchor = (op.flags & F_ANCHOR) != 0;
+        if (anchor) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                au[q] = u[q];
+                av[q] = v[q];
+            }
+        }
+        for (int t0 = 0; t0 < n;) {
+            if (j0 + t0 - win_base >= WINS) flush();
+            const int m = min(n - t0, WINS - (j0 + t0 - win_base));
+            const int slot0 = (j0 + t0 - win_base) * NCR;
+            int s0 = 0;
+            for (; s0 + TS <= m; s0 += TS) store_tile(slot0 + s0 * NCR, coil_tile<true>(TS));
+            if (s0 < m) {
+                const int tt = m - s0;
+                const R tot = coil_tile<false>(tt);
+                if (lane < 2 * tt * NCR) store_tile(slot0 + s0 * NCR, tot);
+            }
+            t0 += m;
+            win_end = j0 + t0;
+        }
+        if (anchor) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const CwT w = cw[op.acls * SP + pi(q)];
+                u[q] = vfma(av[q], vneg(w.im), vmul(au[q], w.re));
+                v[q] = vfma(av[q], w.re, vmul(au[q], w.im));
+            }
+        }
+    }
+    __device__ __forceinline__ void sample_coils(int j) {
+        if (j + 1 - win_base > WINS) flush();
+#pragma unroll
+        for (int c = 0; c < NCR; ++c) {
+            R sx, sy;
+            coil_sum(c, sx, sy);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                sx += __shfl_xor_sync(FULL, sx, off);
+                sy += __shfl_xor_sync(FULL, sy, off);
+            }
+            const int slot = (j - win_base) * NCR + c;
+            if (lane == 0) {
+                if constexpr (F64) {
+                    red_row(0)[slot] = sx;
+                    red_row(1)[slot] = sy;
+                } else {
+                    red_shared_add(win + slot, sx);
+                    red_shared_add(win + WIN_STRIDE + slot, sy);
+                }
+            }
+        }
+        win_end = j + 1;
+    }
+    __device__ __forceinline__ void sample_any(int j) {
+        if constexpr (NC > 0)
+            sample_coils(j);
+        else
+            sample1(j);
     }
 
     __device__ __forceinline__ void sample1(int j) {
@@ -735,7 +919,7 @@ struct Spins {
                 if (op.flags & F_PLOAD) load_w(op.pcls);
                 rot_w();
             }
-            if (op.flags & F_ADC) sample1(op.adc0);
+            if (op.flags & F_ADC) sample_any(op.adc0);
             break;
         case OP_PREC:
             if (op.flags & F_PCLS) {
@@ -744,10 +928,13 @@ struct Spins {
             } else if (op.flags & F_INLINE) {
                 prec_inline(op);
             }
-            if (op.flags & F_ADC) sample1(op.adc0);
+            if (op.flags & F_ADC) sample_any(op.adc0);
             break;
         case OP_RUN:
-            run(op);
+            if constexpr (NC > 0)
+                run_coils(op);
+            else
+                run(op);
             break;
         default:  // OP_END
             t1_relax(op);
@@ -806,9 +993,9 @@ __device__ __forceinline__ void init_op_barriers(unsigned char *smem, bool f64) 
 // the whole program.  `seq` counts the op chunks this block has staged so far (it selects the
 // buffer and the mbarrier phase, so consecutive tiles of a persistent block can reuse the
 // barriers).  Returns false if a bounded wait ran out (status recorded, block must stop).
-template <typename R, int K>
+template <typename R, int K, int NC = 0>
 __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigned char *smem, uint32_t &seq) {
-    using SP = Spins<R, K>;
+    using SP = Spins<R, K, NC>;
     using Op = typename SP::Op;
     using PV = typename SP::P;
     using CwT = typename SP::CwT;
@@ -864,6 +1051,10 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     sp.params = a.params;
     sp.win_base = 0;
     sp.win_end = 0;
+    if constexpr (NC > 0) {
+        sp.n_coils = a.n_coils;
+        sp.coil_stride = 2 * P.n_adc;
+    }
     sp.base = tile * S;
     sp.np = a.n_pad;
     sp.n_spins = a.n_spins;
@@ -969,6 +1160,31 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
         set_lanes(sp.nwi[q], zero);
         set_lanes(sp.e1v[q], zero);
     }
+    if constexpr (NC > 0) {  // sensitivities: [coil][n_pad] (re, im), zero for padding coils/spins
+        using V2T = typename std::conditional<F64, double2, float2>::type;
+        const V2T *sens = reinterpret_cast<const V2T *>(a.sens);
+#pragma unroll
+        for (int c = 0; c < SP::NCR; ++c) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                R re[LN], im[LN], nim[LN];
+#pragma unroll
+                for (int h = 0; h < LN; ++h) {
+                    const int64_t s = sp.base + sp.li(q + h * NP);
+                    V2T w;
+                    w.x = (R)0;
+                    w.y = (R)0;
+                    if (c < a.n_coils && s < a.n_spins) w = sens[(int64_t)c * np + s];
+                    re[h] = w.x;
+                    im[h] = w.y;
+                    nim[h] = -w.y;
+                }
+                set_lanes(sp.cre[c][q], re);
+                set_lanes(sp.cim[c][q], im);
+                set_lanes(sp.cnim[c][q], nim);
+            }
+        }
+    }
     __syncthreads();
     if constexpr (!F64) {
         // block-wide coordinate maxima decide whether the packed phase step is exact for every
@@ -1034,12 +1250,12 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     return true;
 }
 
-template <typename R, int K, int MAXT>
+template <typename R, int K, int MAXT, int NC = 0>
 __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (threadIdx.x == 0) init_op_barriers(smem, std::is_same<R, double>::value);
     uint32_t seq = 0;
-    run_tile<R, K>(a, (int64_t)blockIdx.x, smem, seq);
+    run_tile<R, K, NC>(a, (int64_t)blockIdx.x, smem, seq);
 }
 
 // Persistent batch kernel: each block pops (phantom, tile) work items from a global counter
@@ -1063,14 +1279,14 @@ __global__ void __launch_bounds__(MAXT, 1) batch_kernel(const BatchArgs b) {
     }
 }
 
-template <typename R, int K, int MAXT>
+template <typename R, int K, int MAXT, int NC = 0>
 int launch_one(const FwdArgs &a, int threads, void *stream) {
     if (threads <= 0 || threads > MAXT || threads % 32) return (int)cudaErrorInvalidValue;
     if (a.n_spins <= 0) return 0;
     const int S = K * threads;
     const SmemLayout L = smem_layout(std::is_same<R, double>::value, a.prog.n_pcls, a.prog.n_e1, a.prog.n_e2,
                                      a.prog.n_train, S, threads / 32);
-    auto kern = fwd_kernel<R, K, MAXT>;
+    auto kern = fwd_kernel<R, K, MAXT, NC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return (int)e;
     const int64_t grid = (a.n_spins + S - 1) / S;

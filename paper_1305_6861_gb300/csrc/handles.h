@@ -38,6 +38,8 @@ struct mrsim_ctx {
     size_t state_cap = 0;
     double *d_stage = nullptr;
     size_t stage_cap = 0;
+    double *d_sens = nullptr;  // receive-coil sensitivities in the kernel's layout
+    size_t sens_cap = 0;
     int *d_bad = nullptr;
 };
 

@@ -125,8 +125,10 @@ struct FwdArgs {
     int64_t n_spins, n_pad;
     const double *state_in;  // NULL or 3 per spin (device), laboratory frame
     double *state_out;       // NULL or 3 per spin (device), laboratory frame
-    double *signal;          // 2 * n_adc (device), accumulated with atomics
+    double *signal;          // 2 * n_adc (device), accumulated with atomics; with coils n_coils x 2 * n_adc
     int *status;             // device status word (0 = ok)
+    const void *sens;        // receive coils: n_coils x n_pad complex (float2 or double2), coil-major
+    int32_t n_coils;         // 0 = no coil weighting
 };
 
 // One work item of the persistent batch kernel: tile `tile` of the phantom of descriptor `desc`.
@@ -149,11 +151,21 @@ int batch_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t sme
 int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
+// Forward launch with receive coils (a.sens, a.n_coils in 1..MAX_COILS): float32 with 2 spins per
+// thread, float64 with 1; coil rows per sample are a.n_coils rounded up to 1, 2, 4 or 8.
+constexpr int MAX_COILS = MRSIM_MAX_COILS;
+int launch_fwd_coils_f32(const FwdArgs &a, int threads, void *stream);
+int launch_fwd_coils_f64(const FwdArgs &a, int threads, void *stream);
 // Registers per thread of a kernel instance (0 if the shape does not exist).
 int fwd_regs(bool fp64, int spins_per_thread);
 // Resident blocks per SM of a launch shape with `smem` dynamic shared memory (0 = cannot launch).
 int fwd_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
 int zero_signals(const FwdArgs *descs, int n, void *stream);
+// Validate receive sensitivities (complex float64, [n_coils][n], interleaved) and write them to
+// dst as [n_coils][n_pad] float2 (f32) or double2, zero-padded; bad = lowest index of a
+// non-finite value.
+int pack_sens(int32_t n_coils, int64_t n, int64_t n_pad, const double *src, void *dst, bool f32, int *bad,
+              void *stream);
 int pack_params(int64_t n, int64_t n_pad, const double *x, const double *y, const double *z,
                 const double *rho, const double *t1, const double *t2, const double *dw,
                 double *params, int *bad, void *stream);

@@ -33,6 +33,7 @@ EXPORTS = (
     "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
     "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
+    "mrsim_simulate_coils",
     "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
@@ -106,6 +107,7 @@ def lib():
             "mrsim_simulate": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
             "mrsim_simulate_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64, P(Options)]),
             "mrsim_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, P(Options)]),
+            "mrsim_simulate_coils": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, i32, vp, vp, i64]),
             "mrsim_batch_create": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, P(vp)]),
             "mrsim_batch_num_items": (i64, [vp]),
             "mrsim_batch_autotune": (ctypes.c_int, [vp, vp, P(Options)]),
@@ -254,6 +256,29 @@ def simulate(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP3
                   _ptr(state_in), _ptr(state_out))
     rc = lib().mrsim_simulate_ex(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), _ptr(out), seq.n_adc,
                                  ctypes.byref(opt))
+    ctx.check(rc)
+    return out
+
+
+MAX_COILS = 8
+
+
+def simulate_coils(ctx: Context, phantom: Phantom, seq: Sequence, sens, precision: int = FP32, stream=None,
+                   out=None):
+    """Receive-coil signals: `sens` complex [n_coils, n_spins] (numpy complex128, or a CUDA buffer of
+    n_coils*2*n_spins float64 with `n_coils` taken from its length).  `out`: numpy complex128
+    [n_coils, n_adc] (host, returned when None) or a CUDA buffer of n_coils*2*n_adc float64."""
+    if isinstance(sens, np.ndarray):
+        sens = np.ascontiguousarray(sens, dtype=np.complex128)
+        if sens.ndim != 2 or sens.shape[1] != phantom.n:
+            raise ValueError("sens must be [n_coils, n_spins]")
+        n_coils = sens.shape[0]
+    else:
+        n_coils = int(sens.numel()) // max(2 * phantom.n, 1)
+    if out is None:
+        out = np.zeros((n_coils, seq.n_adc), dtype=np.complex128)
+    rc = lib().mrsim_simulate_coils(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), int(n_coils),
+                                    _ptr(sens), _ptr(out), seq.n_adc)
     ctx.check(rc)
     return out
 
