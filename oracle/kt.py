@@ -54,7 +54,9 @@ def simulate_one(t1: float, t2: float, b1: float, df: float, steps: np.ndarray, 
         a, b = (T[0, 0] * a + T[0, 1] * ac + T[0, 2] * b,
                 T[2, 0] * a + T[2, 1] * ac + T[2, 2] * b)
         q = int(st["shift"])
-        if q > 0:
+        if abs(q) >= a.size:  # every population leaves the kept orders
+            a = np.zeros_like(a)
+        elif q > 0:
             a = np.concatenate([np.zeros(q, dtype=complex), a[:-q]])
         elif q < 0:
             a = np.concatenate([a[-q:], np.zeros(-q, dtype=complex)])
@@ -76,7 +78,9 @@ def simulate(t1, t2, b1, df, steps, max_order: int) -> np.ndarray:
     t2 = np.asarray(t2, dtype=float)
     b1 = np.ones(n) if b1 is None else np.asarray(b1, dtype=float)
     df = np.zeros(n) if df is None else np.asarray(df, dtype=float)
-    steps = np.ascontiguousarray(steps, dtype=STEP_DTYPE)
+    for f in ("alpha", "phi", "tau", "adc_phase", "shift", "sample"):
+        if f not in steps.dtype.names:
+            raise ValueError(f"steps need field {f}")
     return np.stack([simulate_one(t1[s], t2[s], b1[s], df[s], steps, max_order) for s in range(n)])
 
 

@@ -69,3 +69,12 @@ def test_kt_truncation_drops_high_orders():
     full = kt.simulate([1.0], [0.1], None, None, kt.make_steps(rows), max_order=4)[0]
     cut = kt.simulate([1.0], [0.1], None, None, kt.make_steps(rows), max_order=1)[0]
     assert abs(full[0]) > 0.1 and abs(full[0] - cut[0]) > 0.05
+
+
+def test_kt_shift_beyond_all_orders():
+    """A shift of more than 2K + 1 orders empties every transverse population (truncation)."""
+    rows = [(math.pi / 2, 0.0, 1e-3, 0, 1, 0.0), (0.0, 0.0, 1e-3, 3, 1, 0.0), (0.0, 0.0, 1e-3, -3, 1, 0.0)]
+    got = kt.simulate([1.0], [0.1], None, None, kt.make_steps(rows), max_order=0)[0]
+    assert abs(got[0]) > 0.9 and got[1] == 0 and got[2] == 0
+    full = kt.simulate([1.0], [0.1], None, None, kt.make_steps(rows), max_order=4)[0]
+    assert abs(full[2] - got[0] * math.exp(-2e-3 / 0.1)) < 1e-12  # with room the population comes back
