@@ -165,6 +165,38 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
                                   mrsim_precision prec, void *stream, int32_t n_coils, const double *sens,
                                   double *signal_out, int64_t n_adc);
 
+/* ---- K-t formalism: configuration populations of spin ensembles (§4.2) --------------------- */
+
+/* The paper's second simulation method (§4.2; "eigenständige Simulationsmethode"): instead of
+ * isochromats, an ensemble is described by the populations a_i of its transverse configurations
+ * (orders i = -K..K) and b_i of its longitudinal ones (§4.2.1), M0 = 1, thermal equilibrium at
+ * the start.  Each step is one elementary sequence: a hard pulse of flip B1·alpha and phase phi
+ * mixes (a_i, a*_-i, b_i) with T'_HF of Eq. 4.2 (Eq. 4.14); over tau the interval's gradient
+ * moves the transverse orders by `shift` (Eq. 4.17; populations beyond ±max_order are dropped),
+ * relaxation scales a_i by E2 and b_i by E1 and adds 1 - E1 to b_0 (Eqs. 4.15, 4.16), and the
+ * ensemble's off-resonance df turns the a_i by exp(-j 2π df tau).  A step with sample = 1
+ * records a_0·exp(-j adc_phase), the ensemble's transverse magnetisation.  Many ensembles (e.g.
+ * a dictionary over T1, T2, B1, Δf) run in parallel, one warp each. */
+typedef struct mrsim_kt_step {
+    double alpha;     /* flip angle [rad] before B1 scaling; 0 = no pulse */
+    double phi;       /* pulse phase [rad] (Eq. 4.2) */
+    double tau;       /* interval after the pulse [s], >= 0 */
+    double adc_phase; /* receiver phase [rad] of this step's sample */
+    int32_t shift;    /* order shift q of the interval's gradient moment q·Δk, |q| <= 64 */
+    int32_t sample;   /* 1 = record a_0 at the end of the step, 0 = no sample */
+} mrsim_kt_step;
+#define MRSIM_KT_MAX_ORDER 255
+/*   n_sets: ensembles; t1, t2 [s] (> 0, INFINITY allowed), b1 (flip scale; NULL = 1) and df
+ *           [Hz] (NULL = 0): n_sets float64 each, host or device memory
+ *   steps: host array of n_steps; max_order: K, 0..MRSIM_KT_MAX_ORDER
+ *   signal_out: n_sets x 2*n_samples doubles (ensemble-major, (re, im)), host or device;
+ *           n_samples must equal the number of steps with sample = 1
+ * EINVAL for invalid steps or parameters.  Host output synchronises `stream`. */
+mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1, const double *t2,
+                               const double *b1, const double *df, int64_t n_steps, const mrsim_kt_step *steps,
+                               int32_t max_order, mrsim_precision prec, void *stream, double *signal_out,
+                               int64_t n_samples);
+
 /* ---- batches: many phantoms with their own sequences in one persistent launch ---------- */
 
 /* A batch borrows n phantom/sequence pairs (they must outlive it) and one device signal buffer

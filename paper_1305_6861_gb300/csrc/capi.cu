@@ -166,6 +166,7 @@ void mrsim_context_destroy(mrsim_ctx *ctx) {
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_sens);
+    cudaFree(ctx->d_kt);
     delete ctx;
 }
 
@@ -443,6 +444,102 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
     a.n_coils = n_coils;
     const int rc = fp64 ? launch_fwd_coils_f64(a, threads, stream) : launch_fwd_coils_f32(a, threads, stream);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel (coils)");
+    if (host_sig) {
+        CK(cudaMemcpyAsync(signal_out, dsig, sig_doubles * sizeof(double), cudaMemcpyDeviceToHost, st), "copy signal out");
+        return mrsim_stream_status(ctx, stream);
+    }
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1, const double *t2,
+                               const double *b1, const double *df, int64_t n_steps, const mrsim_kt_step *steps,
+                               int32_t max_order, mrsim_precision prec, void *stream, double *signal_out,
+                               int64_t n_samples) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (n_sets < 0 || n_steps < 0) return fail(ctx, MRSIM_EINVAL, "negative count");
+    if (max_order < 0 || max_order > KT_MAX_ORDER)
+        return fail(ctx, MRSIM_EINVAL, "max_order must be 0.." + std::to_string(KT_MAX_ORDER));
+    if (n_sets > 0 && (!t1 || !t2)) return fail(ctx, MRSIM_EINVAL, "NULL T1/T2 array");
+    if (n_steps > 0 && (!steps || is_device_ptr(steps))) return fail(ctx, MRSIM_EINVAL, "steps must be in host memory");
+    // steps: validate and precompute the pulse's phase terms (float64, host)
+    std::vector<KtStepDev> hs((size_t)n_steps);
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const mrsim_kt_step &q = steps[k];
+        if (!std::isfinite(q.alpha) || !std::isfinite(q.phi) || !std::isfinite(q.tau) || !std::isfinite(q.adc_phase) ||
+            q.tau < 0.0 || (q.sample != 0 && q.sample != 1) || q.shift < -KT_MAX_SHIFT || q.shift > KT_MAX_SHIFT)
+            return fail(ctx, MRSIM_EINVAL, "step " + std::to_string(k) + ": non-finite field, tau < 0, sample not 0/1 or |shift| > " +
+                                               std::to_string(KT_MAX_SHIFT));
+        KtStepDev &d = hs[(size_t)k];
+        d.alpha = q.alpha;
+        d.cphi = std::cos(q.phi);
+        d.sphi = std::sin(q.phi);
+        d.c2phi = std::cos(2.0 * q.phi);
+        d.s2phi = std::sin(2.0 * q.phi);
+        d.tau = q.tau;
+        d.cadc = std::cos(q.adc_phase);
+        d.sadc = std::sin(q.adc_phase);
+        d.shift = q.shift;
+        d.sample = q.sample;
+        cnt += q.sample;
+    }
+    if (cnt != n_samples)
+        return fail(ctx, MRSIM_EINVAL, "n_samples = " + std::to_string(n_samples) + " but the steps take " +
+                                           std::to_string(cnt) + " samples");
+    if (n_sets > 0 && n_samples > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal buffer");
+    if (n_sets == 0) return MRSIM_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    mrsim_status rs;
+    // scratch: [steps | t1 | t2 | b1 | df] (parameters staged only when they are host arrays)
+    const size_t step_doubles = (size_t)n_steps * sizeof(KtStepDev) / sizeof(double);
+    const size_t need = step_doubles + 4 * (size_t)n_sets;
+    if ((rs = grow(ctx, &ctx->d_kt, &ctx->kt_cap, std::max<size_t>(need, 1))) != MRSIM_OK) return rs;
+    if (n_steps > 0)
+        CK(cudaMemcpyAsync(ctx->d_kt, hs.data(), hs.size() * sizeof(KtStepDev), cudaMemcpyHostToDevice, st), "copy steps");
+    const double *src[4] = {t1, t2, b1, df};
+    const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 4; ++i) {
+        if (!src[i]) continue;
+        if (is_device_ptr(src[i])) {
+            dev[i] = src[i];
+        } else {
+            double *d = ctx->d_kt + step_doubles + (size_t)i * (size_t)n_sets;
+            CK(cudaMemcpyAsync(d, src[i], sizeof(double) * (size_t)n_sets, cudaMemcpyHostToDevice, st), "copy parameters");
+            dev[i] = d;
+        }
+    }
+    {
+        const int big = 0x7fffffff;
+        int bad = big;
+        CK(cudaMemcpyAsync(ctx->d_bad, &big, sizeof(int), cudaMemcpyHostToDevice, st), "reset check");
+        const int rc = check_kt_params(n_sets, dev[0], dev[1], dev[2], dev[3], ctx->d_bad, st);
+        if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "check parameters");
+        CK(cudaMemcpyAsync(&bad, ctx->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read check");
+        CK(cudaStreamSynchronize(st), "stream synchronize");
+        if (bad != big) return fail(ctx, MRSIM_EINVAL, "ensemble " + std::to_string(bad) + ": T1/T2 <= 0 or NaN, or non-finite B1/df");
+    }
+    const size_t sig_doubles = (size_t)n_sets * 2 * (size_t)n_samples;
+    const bool host_sig = sig_doubles > 0 && !is_device_ptr(signal_out);
+    double *dsig = signal_out;
+    if (host_sig) {
+        if ((rs = grow(ctx, &ctx->d_sig, &ctx->sig_cap, sig_doubles)) != MRSIM_OK) return rs;
+        dsig = ctx->d_sig;
+    }
+    KtArgs a{};
+    a.steps = reinterpret_cast<const KtStepDev *>(ctx->d_kt);
+    a.n_steps = n_steps;
+    a.n_sets = n_sets;
+    a.n_samples = n_samples;
+    a.t1 = dev[0];
+    a.t2 = dev[1];
+    a.b1 = dev[2];
+    a.df = dev[3];
+    a.max_order = max_order;
+    a.signal = dsig;
+    const int rc = launch_kt(a, prec == MRSIM_FP64, stream);
+    if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch K-t kernel");
     if (host_sig) {
         CK(cudaMemcpyAsync(signal_out, dsig, sig_doubles * sizeof(double), cudaMemcpyDeviceToHost, st), "copy signal out");
         return mrsim_stream_status(ctx, stream);

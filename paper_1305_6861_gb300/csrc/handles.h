@@ -40,6 +40,8 @@ struct mrsim_ctx {
     size_t stage_cap = 0;
     double *d_sens = nullptr;  // receive-coil sensitivities in the kernel's layout
     size_t sens_cap = 0;
+    double *d_kt = nullptr;    // K-t steps and staged ensemble parameters
+    size_t kt_cap = 0;
     int *d_bad = nullptr;
 };
 

@@ -24,7 +24,10 @@
 //     sample of a constant-gradient readout.  The host tracks which class the
 //     kernel holds in registers and marks the operations that must reload it.
 #pragma once
+#include <cstddef>
 #include <cstdint>
+
+#include "../../include/mrsim.h"
 
 namespace mrsim {
 
@@ -151,6 +154,31 @@ int batch_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t sme
 int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
+// K-t formalism (kt_kernel.cu): one step per elementary sequence, with the pulse's phase terms
+// precomputed on the host.
+struct KtStepDev {
+    double alpha;              // flip [rad] before B1 scaling; 0 = no pulse
+    double cphi, sphi;         // cos φ, sin φ
+    double c2phi, s2phi;       // cos 2φ, sin 2φ
+    double tau;                // interval [s]
+    double cadc, sadc;         // cos, sin of the receiver phase
+    int32_t shift, sample;     // order shift q of the interval's gradient; 1 = record a_0
+};
+static_assert(sizeof(KtStepDev) == 72, "KtStepDev layout");
+constexpr int KT_MAX_ORDER = 255;  // 8 slots of 32 lanes
+constexpr int KT_MAX_SHIFT = 64;
+struct KtArgs {
+    const KtStepDev *steps;
+    int64_t n_steps, n_sets, n_samples;
+    const double *t1, *t2, *b1, *df;  // per ensemble; b1, df may be NULL (1, 0)
+    int32_t max_order;
+    double *signal;                   // n_sets x 2 * n_samples
+};
+int launch_kt(const KtArgs &a, bool fp64, void *stream);
+// lowest index of an ensemble with T1/T2 <= 0 or NaN, or non-finite B1/Δf, into *bad
+int check_kt_params(int64_t n, const double *t1, const double *t2, const double *b1, const double *df, int *bad,
+                    void *stream);
+
 // Forward launch with receive coils (a.sens, a.n_coils in 1..MAX_COILS): float32 with 2 spins per
 // thread, float64 with 1; coil rows per sample are a.n_coils rounded up to 1, 2, 4 or 8.
 constexpr int MAX_COILS = MRSIM_MAX_COILS;

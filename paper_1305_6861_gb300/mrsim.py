@@ -33,7 +33,7 @@ EXPORTS = (
     "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
     "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
-    "mrsim_simulate_coils",
+    "mrsim_simulate_coils", "mrsim_kt_simulate",
     "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
@@ -108,6 +108,7 @@ def lib():
             "mrsim_simulate_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64, P(Options)]),
             "mrsim_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, P(Options)]),
             "mrsim_simulate_coils": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, i32, vp, vp, i64]),
+            "mrsim_kt_simulate": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, i64, vp, i32, ctypes.c_int, vp, vp, i64]),
             "mrsim_batch_create": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, P(vp)]),
             "mrsim_batch_num_items": (i64, [vp]),
             "mrsim_batch_autotune": (ctypes.c_int, [vp, vp, P(Options)]),
@@ -279,6 +280,34 @@ def simulate_coils(ctx: Context, phantom: Phantom, seq: Sequence, sens, precisio
         out = np.zeros((n_coils, seq.n_adc), dtype=np.complex128)
     rc = lib().mrsim_simulate_coils(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), int(n_coils),
                                     _ptr(sens), _ptr(out), seq.n_adc)
+    ctx.check(rc)
+    return out
+
+
+KT_MAX_ORDER = 255
+
+
+def kt_simulate(ctx: Context, t1, t2, steps, max_order: int, b1=None, df=None, precision: int = FP32,
+                stream=None, out=None):
+    """K-t formalism (§4.2) for n ensembles: t1, t2 [s], b1 (flip scale), df [Hz] as float64 numpy
+    arrays or CUDA tensors; `steps`: workloads.KT_STEP_DTYPE array.  Returns (or fills) the
+    ensembles' samples: numpy complex128 [n, n_samples] or a CUDA buffer of n*2*n_samples float64."""
+    from . import workloads as W
+
+    st = np.ascontiguousarray(steps, dtype=W.KT_STEP_DTYPE)
+    n_samples = int(np.count_nonzero(st["sample"]))
+
+    def arr(a):
+        if a is None or hasattr(a, "data_ptr"):
+            return a
+        return np.ascontiguousarray(a, dtype=np.float64)
+
+    t1, t2, b1, df = arr(t1), arr(t2), arr(b1), arr(df)
+    n = int(t1.shape[0]) if hasattr(t1, "shape") else int(t1.numel())
+    if out is None:
+        out = np.zeros((n, n_samples), dtype=np.complex128)
+    rc = lib().mrsim_kt_simulate(ctx.h, n, _ptr(t1), _ptr(t2), _ptr(b1), _ptr(df), st.shape[0], _ptr(st),
+                                 int(max_order), int(precision), _stream(stream), _ptr(out), n_samples)
     ctx.check(rc)
     return out
 

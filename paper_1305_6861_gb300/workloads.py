@@ -635,3 +635,64 @@ def random_sequence(n_events: int, rng: np.random.Generator, fov: float = 0.5, r
             for _ in range(n):
                 ev.add(dt, *g)
     return Sequence(ev.array()[:n_events], GAMMA_BAR, (), "random")
+
+
+# ---------------------------------------------------------------------------
+# K-t formalism inputs (§4.2): ensembles (a dictionary over T1, T2, B1, Δf) and step lists
+# ---------------------------------------------------------------------------
+
+KT_STEP_DTYPE = np.dtype([("alpha", "<f8"), ("phi", "<f8"), ("tau", "<f8"), ("adc_phase", "<f8"),
+                          ("shift", "<i4"), ("sample", "<i4")])
+assert KT_STEP_DTYPE.itemsize == 40
+
+
+def kt_steps(rows) -> np.ndarray:
+    """Rows of (alpha, phi, tau, shift, sample, adc_phase) → KT_STEP_DTYPE array."""
+    out = np.zeros(len(rows), dtype=KT_STEP_DTYPE)
+    for k, (al, ph, tau, q, smp, adc) in enumerate(rows):
+        out[k] = (al, ph, tau, adc, q, smp)
+    return out
+
+
+@dataclasses.dataclass
+class KtDictionary:
+    t1: np.ndarray
+    t2: np.ndarray
+    b1: np.ndarray
+    df: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.t1.shape[0])
+
+
+def kt_dictionary(n: int, rng: np.random.Generator, off_resonance: bool = True) -> KtDictionary:
+    """Seeded ensemble parameters: T1 log-U[0.1, 4] s, T2 log-U[0.01, 1] s (<= T1), B1 U[0.7, 1.3],
+    Δf U[-50, 50] Hz (0 without off-resonance)."""
+    t1 = np.exp(rng.uniform(math.log(0.1), math.log(4.0), n))
+    t2 = np.minimum(np.exp(rng.uniform(math.log(0.01), math.log(1.0), n)), t1)
+    b1 = rng.uniform(0.7, 1.3, n)
+    df = rng.uniform(-50.0, 50.0, n) if off_resonance else np.zeros(n)
+    return KtDictionary(t1, t2, b1, df)
+
+
+def kt_fingerprint_sequence(n_tr: int, rng: np.random.Generator) -> np.ndarray:
+    """Fingerprinting-style train: an inversion, then n_tr pulses with a smoothly varying flip
+    (5°..70°), alternating phase, TR U[10, 15] ms, one order of unbalanced gradient per TR and a
+    sample every TR (receiver phase = pulse phase)."""
+    rows = [(math.pi, 0.0, 20e-3, 0, 0, 0.0)]
+    for k in range(n_tr):
+        al = math.radians(5.0 + 65.0 * abs(math.sin(math.pi * k / 250.0)))
+        ph = math.pi * (k % 2)
+        rows.append((al, ph, rng.uniform(10e-3, 15e-3), 1, 1, ph))
+    return kt_steps(rows)
+
+
+def kt_random_sequence(n_steps: int, rng: np.random.Generator, max_shift: int = 2) -> np.ndarray:
+    """Random flips and phases, intervals, order shifts in [-max_shift, max_shift], random samples."""
+    rows = []
+    for _ in range(n_steps):
+        al = rng.uniform(-math.pi, math.pi) if rng.uniform() < 0.8 else 0.0
+        rows.append((al, rng.uniform(0, 2 * math.pi), rng.uniform(0.0, 8e-3), int(rng.integers(-max_shift, max_shift + 1)),
+                     int(rng.uniform() < 0.6), rng.uniform(0, 2 * math.pi)))
+    return kt_steps(rows)
