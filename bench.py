@@ -313,6 +313,84 @@ def run_adjoint(args):
     return 0
 
 
+# K-t formalism: algorithmic FP32 lane-ops per (ensemble, step, order index i >= 0): the pulse's
+# three rows of Eq. 4.14 (10 each: one real-by-complex product and two complex products fused
+# into the sums) and the relaxation / precession of a_i, a_-i (4 each) and b_i (2)
+KT_OPS_PER_ORDER = 30 + 10
+
+
+def run_kt(args):
+    """K-t workload (§4.2): a fingerprinting-style dictionary, 65 536 ensembles over (T1, T2, B1,
+    Δf) through an inversion + 1000-pulse train with one order of unbalanced gradient per TR,
+    configuration orders up to K = 127, one sample per TR."""
+    import torch
+
+    from paper_1305_6861_gb300 import mrsim as M
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(W.SEED_BASE + 6)
+    n_sets, n_tr, K = args.kt_sets, 1000, 127
+    d = W.kt_dictionary(n_sets, rng)
+    steps = W.kt_fingerprint_sequence(n_tr, rng)
+    n_samples = int(np.count_nonzero(steps["sample"]))
+    prec = M.FP64 if args.precision == "fp64" else M.FP32
+    ctx = M.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    par = [torch.from_numpy(a.copy()).to(dev) for a in (d.t1, d.t2, d.b1, d.df)]
+    out = torch.zeros(n_sets * 2 * n_samples, dtype=torch.float64, device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        M.kt_simulate(ctx, par[0], par[1], steps, K, b1=par[2], df=par[3], precision=prec, stream=stream, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.stream_status(stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.15)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush_buf.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ctx.stream_status(stream)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ens_steps = n_sets * len(steps)
+    ops = ens_steps * (K + 1) * KT_OPS_PER_ORDER
+    achieved = ops / (ms * 1e-3) / 1e9
+    peak = fp32_alu_peak_ops() / 1e9
+    line = {"metric": "ensemble-steps/s of the K-t formalism (configuration populations) at 1 GB300",
+            "value": ens_steps / (ms * 1e-3), "unit": "ensemble-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}", "n_ensembles": n_sets,
+                       "n_steps": len(steps), "max_order": K, "n_samples": n_samples,
+                       "order_steps_per_step": ens_steps * (K + 1),
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel_ms": ms,
+                         "ops_per_order_step": KT_OPS_PER_ORDER},
+            "gpu_launches": 2 * args.steps, "clocks": ck}
+    if not args.no_cpu_baseline:
+        from oracle import kt as ORK
+
+        nb, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < args.cpu_seconds and nb < n_sets:
+            ORK.simulate(d.t1[nb:nb + 1], d.t2[nb:nb + 1], d.b1[nb:nb + 1], d.df[nb:nb + 1], steps, K)
+            nb += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nb * len(steps) / dt, "unit": "ensemble-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{nb} of {n_sets} ensembles, full train, {dt:.1f} s (numpy, one core)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -322,6 +400,8 @@ def run_ours(args):
         return run_batch(args)
     if args.workload == "c5":
         return run_adjoint(args)
+    if args.workload == "kt":
+        return run_kt(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -497,7 +577,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c2")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "kt"], default="c2")
+    ap.add_argument("--kt-sets", type=int, default=65536, help="ensembles of the K-t workload")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--spins-per-thread", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)

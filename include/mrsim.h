@@ -197,6 +197,17 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
                                int32_t max_order, mrsim_precision prec, void *stream, double *signal_out,
                                int64_t n_samples);
 
+/* Spatial sampling check for spin-based simulation (§5.2.3): the largest |k| that any
+ * configuration of the event list reaches, per axis (Eq. 5.1), in rad/m (k = γ·∫G dt).  A
+ * configuration exists from the first pulse on; a pulse can conjugate it (so the moments of
+ * consecutive inter-pulse segments add with one sign) or store it longitudinally, so
+ * K_max = max over t of Σ|moment of each completed segment| + |moment of the current segment up
+ * to t|.  Isochromats must be spaced below Δx_max = π / K_max (Eq. 5.2) along each axis for the
+ * discrete spin sum to be free of aliasing; off-resonance spread adds to k and is not included.
+ * Host only (no device needed).  EINVAL for invalid events. */
+mrsim_status mrsim_max_config_k(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
+                                double kmax_rad_per_m[3]);
+
 /* ---- batches: many phantoms with their own sequences in one persistent launch ---------- */
 
 /* A batch borrows n phantom/sequence pairs (they must outlive it) and one device signal buffer

@@ -547,6 +547,37 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
     return MRSIM_OK;
 }
 
+mrsim_status mrsim_max_config_k(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
+                                double kmax_rad_per_m[3]) {
+    if (!kmax_rad_per_m || n_events < 0 || (n_events > 0 && !events)) return MRSIM_EINVAL;
+    if (!(gamma_hz_per_t > 0.0) || !std::isfinite(gamma_hz_per_t)) return MRSIM_EINVAL;
+    const double two_pi_gamma = 2.0 * M_PI * gamma_hz_per_t;
+    double total[3] = {0, 0, 0}, seg[3] = {0, 0, 0}, best[3] = {0, 0, 0};
+    bool started = false;
+    for (int64_t i = 0; i < n_events; ++i) {
+        const mrsim_event &e = events[i];
+        const double g[3] = {e.gx, e.gy, e.gz};
+        if (!std::isfinite(e.dt) || e.dt < 0.0 || !std::isfinite(e.rf_flip) || !std::isfinite(g[0]) ||
+            !std::isfinite(g[1]) || !std::isfinite(g[2]))
+            return MRSIM_EINVAL;
+        if (e.rf_flip != 0.0) {  // the pulse at the event's start closes the current segment
+            if (started)
+                for (int a = 0; a < 3; ++a) {
+                    total[a] += std::fabs(seg[a]);
+                    seg[a] = 0.0;
+                }
+            started = true;
+        }
+        if (!started) continue;
+        for (int a = 0; a < 3; ++a) {
+            seg[a] += two_pi_gamma * g[a] * e.dt;  // |k| is linear within the event: check its end
+            best[a] = std::max(best[a], total[a] + std::fabs(seg[a]));
+        }
+    }
+    for (int a = 0; a < 3; ++a) kmax_rad_per_m[a] = best[a];
+    return MRSIM_OK;
+}
+
 mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq, mrsim_precision prec,
                             void *stream, mrsim_options *best) {
     if (!ctx) return MRSIM_EINVAL;

@@ -33,7 +33,7 @@ EXPORTS = (
     "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
     "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
-    "mrsim_simulate_coils", "mrsim_kt_simulate",
+    "mrsim_simulate_coils", "mrsim_kt_simulate", "mrsim_max_config_k",
     "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
@@ -109,6 +109,7 @@ def lib():
             "mrsim_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, P(Options)]),
             "mrsim_simulate_coils": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, i32, vp, vp, i64]),
             "mrsim_kt_simulate": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, i64, vp, i32, ctypes.c_int, vp, vp, i64]),
+            "mrsim_max_config_k": (ctypes.c_int, [i64, vp, ctypes.c_double, vp]),
             "mrsim_batch_create": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, P(vp)]),
             "mrsim_batch_num_items": (i64, [vp]),
             "mrsim_batch_autotune": (ctypes.c_int, [vp, vp, P(Options)]),
@@ -285,6 +286,24 @@ def simulate_coils(ctx: Context, phantom: Phantom, seq: Sequence, sens, precisio
 
 
 KT_MAX_ORDER = 255
+
+
+def max_config_k(events, gamma_hz_per_t: float) -> np.ndarray:
+    """Largest |k| [rad/m] per axis that any configuration of the event list reaches (Eq. 5.1)."""
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    out = np.zeros(3)
+    rc = lib().mrsim_max_config_k(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), _ptr(out))
+    if rc != 0:
+        raise MrsimError(rc, "mrsim_max_config_k failed")
+    return out
+
+
+def delta_x_max(events, gamma_hz_per_t: float) -> np.ndarray:
+    """Largest isochromat spacing per axis free of aliasing, Δx_max = π / K_max (Eq. 5.2); inf where
+    no configuration moves along the axis."""
+    k = max_config_k(events, gamma_hz_per_t)
+    with np.errstate(divide="ignore"):
+        return np.where(k > 0, np.pi / np.where(k > 0, k, 1.0), np.inf)
 
 
 def kt_simulate(ctx: Context, t1, t2, steps, max_order: int, b1=None, df=None, precision: int = FP32,
