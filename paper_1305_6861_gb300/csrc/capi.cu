@@ -496,8 +496,22 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
     const size_t step_doubles = (size_t)n_steps * sizeof(KtStepDev) / sizeof(double);
     const size_t need = step_doubles + 4 * (size_t)n_sets;
     if ((rs = grow(ctx, &ctx->d_kt, &ctx->kt_cap, std::max<size_t>(need, 1))) != MRSIM_OK) return rs;
-    if (n_steps > 0)
-        CK(cudaMemcpyAsync(ctx->d_kt, hs.data(), hs.size() * sizeof(KtStepDev), cudaMemcpyHostToDevice, st), "copy steps");
+    if (n_steps > 0) {
+        if (prec == MRSIM_FP64) {
+            CK(cudaMemcpyAsync(ctx->d_kt, hs.data(), hs.size() * sizeof(KtStepDev), cudaMemcpyHostToDevice, st),
+               "copy steps");
+        } else {
+            std::vector<KtStepF> hf(hs.size());
+            for (size_t k = 0; k < hs.size(); ++k) {
+                const KtStepDev &d = hs[k];
+                hf[k] = KtStepF{(float)d.alpha, (float)d.cphi, (float)d.sphi, (float)d.c2phi, (float)d.s2phi,
+                                (float)d.tau, (float)d.cadc, (float)d.sadc, d.shift, d.sample};
+            }
+            CK(cudaMemcpyAsync(ctx->d_kt, hf.data(), hf.size() * sizeof(KtStepF), cudaMemcpyHostToDevice, st),
+               "copy steps");
+            CK(cudaStreamSynchronize(st), "stream synchronize");  // hf is a local buffer
+        }
+    }
     const double *src[4] = {t1, t2, b1, df};
     const double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int i = 0; i < 4; ++i) {
@@ -528,7 +542,7 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
         dsig = ctx->d_sig;
     }
     KtArgs a{};
-    a.steps = reinterpret_cast<const KtStepDev *>(ctx->d_kt);
+    a.steps = ctx->d_kt;
     a.n_steps = n_steps;
     a.n_sets = n_sets;
     a.n_samples = n_samples;

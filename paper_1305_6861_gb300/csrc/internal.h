@@ -165,10 +165,15 @@ struct KtStepDev {
     int32_t shift, sample;     // order shift q of the interval's gradient; 1 = record a_0
 };
 static_assert(sizeof(KtStepDev) == 72, "KtStepDev layout");
+struct KtStepF {  // the same in float32, for the float32 kernel
+    float alpha, cphi, sphi, c2phi, s2phi, tau, cadc, sadc;
+    int32_t shift, sample;
+};
+static_assert(sizeof(KtStepF) == 40, "KtStepF layout");
 constexpr int KT_MAX_ORDER = 255;  // 8 slots of 32 lanes
 constexpr int KT_MAX_SHIFT = 64;
 struct KtArgs {
-    const KtStepDev *steps;
+    const void *steps;  // KtStepDev (float64) or KtStepF (float32) records
     int64_t n_steps, n_sets, n_samples;
     const double *t1, *t2, *b1, *df;  // per ensemble; b1, df may be NULL (1, 0)
     int32_t max_order;

@@ -13,7 +13,8 @@
 // a_-i and b_i: the pulse is lane-local (order i couples with -i only); a one-order shift moves
 // a_i one lane up (and a_-i one lane down), with the wrap between slots m and the exchange
 // a_0 <-> a_∓1 done by shuffles.  Every lane computes the step's scalars (sin/cos of the scaled
-// flip, E1, E2, off-resonance phasor) itself; no warp waits on another.
+// flip, E1, E2, off-resonance phasor) for one step of every 32 and the warp broadcasts them; no
+// warp waits on another.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -62,6 +63,8 @@ __device__ __forceinline__ void scpi(float x, float *s, float *c) { sincospif(x,
 __device__ __forceinline__ void scpi(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ float em1(float x) { return expm1f(x); }
 __device__ __forceinline__ double em1(double x) { return expm1(x); }
+__device__ __forceinline__ float ex(float x) { return expf(x); }
+__device__ __forceinline__ double ex(double x) { return exp(x); }
 
 template <typename R, int M>
 struct Ensemble {
@@ -70,18 +73,10 @@ struct Ensemble {
 
     __device__ __forceinline__ bool has(int m) const { return lane + 32 * m <= K; }
 
-    // Eq. 4.14 with T'_HF of Eq. 4.2 (flip alpha, phase cos/sin phi, cos/sin 2 phi)
-    __device__ __forceinline__ void pulse(R alpha, R cp, R sp, R c2p, R s2p) {
-        R sa, ca, sh, ch;
-        sc(alpha, &sa, &ca);
-        sc((R)0.5 * alpha, &sh, &ch);
-        const R c2 = ch * ch, s2 = sh * sh, hs = (R)0.5 * sa;
-        const Cx<R> t01{s2 * c2p, s2 * s2p};  // sin²(α/2) e^{2jφ}
-        const Cx<R> t10{s2 * c2p, -s2 * s2p};
-        const Cx<R> t02{-sa * sp, sa * cp};   // sin α e^{j(φ+π/2)} = j sin α e^{jφ}
-        const Cx<R> t12{-sa * sp, -sa * cp};  // sin α e^{-j(φ+π/2)}
-        const Cx<R> t20{hs * sp, hs * cp};    // (sin α / 2) e^{-j(φ-π/2)} = j (sin α / 2) e^{-jφ}
-        const Cx<R> t21{hs * sp, -hs * cp};   // (sin α / 2) e^{j(φ-π/2)}
+    // Eq. 4.14 with T'_HF of Eq. 4.2: c2 = cos²(α/2), ca = cos α, t01 = sin²(α/2) e^{2jφ},
+    // t02 = sin α e^{j(φ+π/2)}, t20 = (sin α / 2) e^{-j(φ-π/2)}; the other entries are conjugates
+    __device__ __forceinline__ void pulse(R c2, R ca, Cx<R> t01, Cx<R> t02, Cx<R> t20) {
+        const Cx<R> t10 = cconj(t01), t12 = cconj(t02), t21 = cconj(t20);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const Cx<R> x = ap[m], y = cconj(an[m]), z = bz[m];
@@ -154,11 +149,51 @@ struct Ensemble {
     }
 };
 
-template <typename R, int M>
+// The per-step scalars of one ensemble: pulse entries, relaxation, demodulation, flags.  Lane l
+// of a warp computes them for step base + l of a 32-step chunk; the warp then walks the chunk
+// and broadcasts each step's values with shuffles (the transcendentals are spread over the lanes).
+template <typename R>
+struct StepScalars {
+    R c2, ca, t01r, t01i, t02r, t02i, t20r, t20i;  // pulse (Eq. 4.2)
+    R e1m1, wr, wi;                                // E1 - 1; E2·exp(-j2πΔfτ)
+    R cadc, sadc;                                  // demodulation
+    int flags;                                     // shift + 128 (8 bits) | sample << 8 | pulse << 9
+};
+
+template <typename R, typename StepT>
+__device__ __forceinline__ StepScalars<R> step_scalars(const StepT &s, R b1, R r1, R r2, R df) {
+    StepScalars<R> o;
+    const R alpha = b1 * (R)s.alpha;
+    R sh, ch;
+    sc((R)0.5 * alpha, &sh, &ch);
+    const R cp = (R)s.cphi, sp = (R)s.sphi, s2 = sh * sh, sa = (R)2 * sh * ch, hs = sh * ch;
+    o.c2 = ch * ch;
+    o.ca = o.c2 - s2;
+    o.t01r = s2 * (R)s.c2phi;
+    o.t01i = s2 * (R)s.s2phi;
+    o.t02r = -sa * sp;  // j sin α e^{jφ}
+    o.t02i = sa * cp;
+    o.t20r = hs * sp;  // j (sin α / 2) e^{-jφ}
+    o.t20i = hs * cp;
+    const R tau = (R)s.tau;
+    o.e1m1 = em1(-tau * r1);
+    const R e2 = ex(-tau * r2);
+    R sn, cs;
+    scpi((R)2 * df * tau, &sn, &cs);
+    o.wr = e2 * cs;
+    o.wi = -e2 * sn;
+    o.cadc = (R)s.cadc;
+    o.sadc = (R)s.sadc;
+    o.flags = (s.shift + 128) | (s.sample << 8) | ((s.alpha != 0) << 9);
+    return o;
+}
+
+template <typename R, int M, typename StepT>
 __global__ void __launch_bounds__(128) kt_kernel(const KtArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t set = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (set >= a.n_sets) return;  // uniform over the warp
+    const StepT *steps = reinterpret_cast<const StepT *>(a.steps);
     const double t1 = a.t1[set], t2 = a.t2[set];
     const R r1 = isinf(t1) ? (R)0 : (R)(1.0 / t1), r2 = isinf(t2) ? (R)0 : (R)(1.0 / t2);
     const R b1 = a.b1 ? (R)a.b1[set] : (R)1;
@@ -174,30 +209,42 @@ __global__ void __launch_bounds__(128) kt_kernel(const KtArgs a) {
     }
     if (lane == 0) e.bz[0].re = (R)1;
     double *out = a.signal + 2 * set * a.n_samples;
-    int64_t j = 0;
-    for (int64_t k = 0; k < a.n_steps; ++k) {
-        const KtStepDev s = a.steps[k];
-        if (s.alpha != 0.0) e.pulse(b1 * (R)s.alpha, (R)s.cphi, (R)s.sphi, (R)s.c2phi, (R)s.s2phi);
-        for (int q = 0; q < s.shift; ++q) e.shift_up();
-        for (int q = 0; q > s.shift; --q) e.shift_down();
-        const R tau = (R)s.tau;
-        const R e1m1 = em1(-tau * r1);
-        const R e2 = exp(-tau * r2);
-        R sn, cs;
-        scpi((R)2 * df * tau, &sn, &cs);  // exp(-j 2π Δf τ)
-        e.relax(e1m1, Cx<R>{e2 * cs, -e2 * sn});
-        if (s.sample) {
-            if (lane == 0) {
-                const Cx<R> v = cmul(e.ap[0], Cx<R>{(R)s.cadc, -(R)s.sadc});
-                out[2 * j] = (double)v.re;
-                out[2 * j + 1] = (double)v.im;
+    int64_t j = 0;  // samples written before this chunk
+    for (int64_t base = 0; base < a.n_steps; base += 32) {
+        const int cnt = (int)min((int64_t)32, a.n_steps - base);
+        StepScalars<R> my{};
+        if (lane < cnt) my = step_scalars<R>(steps[base + lane], b1, r1, r2, df);
+        // lane k keeps the sample of step base + k and stores it after the chunk (one conversion
+        // to float64 per lane instead of one per sample for the whole warp)
+        const unsigned smask = __ballot_sync(FULLW, lane < cnt && (my.flags & 256));
+        Cx<R> mine{0, 0};
+        for (int k = 0; k < cnt; ++k) {
+            const int fl = __shfl_sync(FULLW, my.flags, k);
+            if (fl & 512)
+                e.pulse(__shfl_sync(FULLW, my.c2, k), __shfl_sync(FULLW, my.ca, k),
+                        Cx<R>{__shfl_sync(FULLW, my.t01r, k), __shfl_sync(FULLW, my.t01i, k)},
+                        Cx<R>{__shfl_sync(FULLW, my.t02r, k), __shfl_sync(FULLW, my.t02i, k)},
+                        Cx<R>{__shfl_sync(FULLW, my.t20r, k), __shfl_sync(FULLW, my.t20i, k)});
+            const int q = (fl & 255) - 128;
+            for (int i = 0; i < q; ++i) e.shift_up();
+            for (int i = 0; i > q; --i) e.shift_down();
+            e.relax(__shfl_sync(FULLW, my.e1m1, k), Cx<R>{__shfl_sync(FULLW, my.wr, k), __shfl_sync(FULLW, my.wi, k)});
+            if (fl & 256) {
+                const Cx<R> a0 = shfl(e.ap[0], 0);
+                if (lane == k) mine = a0;
             }
-            ++j;
         }
+        if (smask & (1u << lane)) {  // demodulated with this lane's own step
+            const Cx<R> v = cmul(mine, Cx<R>{my.cadc, -my.sadc});
+            const int64_t jj = j + __popc(smask & ((1u << lane) - 1u));
+            out[2 * jj] = (double)v.re;
+            out[2 * jj + 1] = (double)v.im;
+        }
+        j += __popc(smask);
     }
 }
 
-template <typename R>
+template <typename R, typename StepT>
 int launch_kt_t(const KtArgs &a, void *stream) {
     const int threads = 128;
     const int64_t blocks = (a.n_sets + 3) / 4;
@@ -206,13 +253,13 @@ int launch_kt_t(const KtArgs &a, void *stream) {
     const int M = (a.max_order + 32) / 32;  // slots per lane
     cudaStream_t st = (cudaStream_t)stream;
     if (M <= 1)
-        kt_kernel<R, 1><<<(unsigned)blocks, threads, 0, st>>>(a);
+        kt_kernel<R, 1, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
     else if (M <= 2)
-        kt_kernel<R, 2><<<(unsigned)blocks, threads, 0, st>>>(a);
+        kt_kernel<R, 2, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
     else if (M <= 4)
-        kt_kernel<R, 4><<<(unsigned)blocks, threads, 0, st>>>(a);
+        kt_kernel<R, 4, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
     else if (M <= 8)
-        kt_kernel<R, 8><<<(unsigned)blocks, threads, 0, st>>>(a);
+        kt_kernel<R, 8, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
     else
         return (int)cudaErrorInvalidValue;
     return (int)cudaGetLastError();
@@ -239,7 +286,7 @@ int check_kt_params(int64_t n, const double *t1, const double *t2, const double 
 }
 
 int launch_kt(const KtArgs &a, bool fp64, void *stream) {
-    return fp64 ? launch_kt_t<double>(a, stream) : launch_kt_t<float>(a, stream);
+    return fp64 ? launch_kt_t<double, KtStepDev>(a, stream) : launch_kt_t<float, KtStepF>(a, stream);
 }
 
 }  // namespace mrsim
