@@ -84,6 +84,8 @@ typedef struct mrsim_options {
     int32_t reserved;
     const double *state_in;    /* NULL = thermal equilibrium (0,0,M0); else 3*n_spins (Mx,My,Mz), host or device */
     double *state_out;         /* NULL, or 3*n_spins receiving (Mx,My,Mz) after the last event, host or device */
+    double *snapshots;         /* NULL, or n_snapshots x n_spins x 3 receiving (Mx,My,Mz) after each snapshot
+                                  event of a sequence loaded with mrsim_sequence_load_snapshots; host or device */
 } mrsim_options;
 
 #define MRSIM_ACCUMULATE 1u
@@ -127,6 +129,15 @@ void mrsim_phantom_destroy(mrsim_phantom *p);
  * reserved != 0 or gamma <= 0. */
 mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
                                  double gamma_hz_per_t, mrsim_sequence **out);
+/* As mrsim_sequence_load, and the program also records every spin's magnetisation after the
+ * events snap_after[0..n_snap-1] (strictly increasing indices < n_events): the "magnetisation
+ * data at arbitrary times" of §7.2.  The states are written to mrsim_options.snapshots in the
+ * rotating (laboratory) frame, with T1 recovery up to the end of the event applied.  The signal is
+ * the same as without snapshots. */
+mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                           double gamma_hz_per_t, int64_t n_snap, const int64_t *snap_after,
+                                           mrsim_sequence **out);
+int64_t mrsim_sequence_num_snapshots(const mrsim_sequence *s);
 int64_t mrsim_sequence_num_adc(const mrsim_sequence *s);
 int64_t mrsim_sequence_num_events(const mrsim_sequence *s);
 /* Number of compiled device operations (after merging runs of events); for diagnostics. */
@@ -315,6 +326,9 @@ typedef struct mrsim_program_dump {
 } mrsim_program_dump;
 mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
                                  mrsim_program_dump *dump);
+/* mrsim_debug_compile for a program with snapshots (as mrsim_sequence_load_snapshots). */
+mrsim_status mrsim_debug_compile_snapshots(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t,
+                                           int64_t n_snap, const int64_t *snap_after, mrsim_program_dump *dump);
 
 /* Autotuner: times every launch shape (spins per thread x threads per block) that fits the device
  * on a prefix of the compiled program (about 3e9 spin-steps, at least 256 operations) on `stream`,

@@ -167,6 +167,7 @@ void mrsim_context_destroy(mrsim_ctx *ctx) {
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_sens);
     cudaFree(ctx->d_kt);
+    cudaFree(ctx->d_snap);
     delete ctx;
 }
 
@@ -230,6 +231,14 @@ void mrsim_phantom_destroy(mrsim_phantom *p) {
 
 mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events, double gamma,
                                  mrsim_sequence **out) {
+    return mrsim_sequence_load_snapshots(ctx, n_events, events, gamma, 0, nullptr, out);
+}
+
+int64_t mrsim_sequence_num_snapshots(const mrsim_sequence *s) { return s ? s->host.n_snap : -1; }
+
+mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                           double gamma, int64_t n_snap, const int64_t *snap_after,
+                                           mrsim_sequence **out) {
     if (!ctx || !out) return MRSIM_EINVAL;
     *out = nullptr;
     if (n_events > 0 && is_device_ptr(events)) return fail(ctx, MRSIM_EINVAL, "events must be in host memory");
@@ -238,7 +247,7 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     s->ctx = ctx;
     s->n_events = n_events;
     std::string err;
-    int rc = compile_sequence(events, n_events, gamma, s->host, err);
+    int rc = compile_sequence(events, n_events, gamma, s->host, err, n_snap, snap_after);
     if (rc != MRSIM_OK) {
         delete s;
         return fail(ctx, (mrsim_status)rc, err);
@@ -365,6 +374,14 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
         }
         if (host_out) dout = ctx->d_state + st_n;
     }
+    // snapshots (host buffers go through their own scratch)
+    const size_t snap_n = (size_t)seq->host.n_snap * 3 * (size_t)ph->n;
+    double *dsnap = o.snapshots;
+    const bool host_snap = o.snapshots && snap_n > 0 && !is_device_ptr(o.snapshots);
+    if (host_snap) {
+        if ((rs = grow(ctx, &ctx->d_snap, &ctx->snap_cap, snap_n)) != MRSIM_OK) return rs;
+        dsnap = ctx->d_snap;
+    }
     FwdArgs a{};
     a.prog = P;
     a.params = ph->params;
@@ -372,13 +389,15 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     a.n_pad = ph->n_pad;
     a.state_in = din;
     a.state_out = dout;
+    a.snap = snap_n > 0 ? dsnap : nullptr;
     a.signal = dsig;
     a.status = ctx->d_status;
     int rc = fp64 ? launch_fwd_f64(a, L.k, L.threads, stream) : launch_fwd_f32(a, L.k, L.threads, stream);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel");
     if (host_out) CK(cudaMemcpyAsync(o.state_out, dout, st_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy state out");
+    if (host_snap) CK(cudaMemcpyAsync(o.snapshots, dsnap, snap_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy snapshots");
     if (host_sig) CK(cudaMemcpyAsync(signal_out, dsig, sig_bytes, cudaMemcpyDeviceToHost, st), "copy signal out");
-    if (host_sig || host_out) return mrsim_stream_status(ctx, stream);
+    if (host_sig || host_out || host_snap) return mrsim_stream_status(ctx, stream);
     return MRSIM_OK;
 }
 
@@ -688,10 +707,15 @@ mrsim_status mrsim_simulate(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
 }
 
 mrsim_status mrsim_debug_compile(int64_t n_events, const mrsim_event *events, double gamma, mrsim_program_dump *d) {
+    return mrsim_debug_compile_snapshots(n_events, events, gamma, 0, nullptr, d);
+}
+
+mrsim_status mrsim_debug_compile_snapshots(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
+                                           const int64_t *snap_after, mrsim_program_dump *d) {
     if (!d) return MRSIM_EINVAL;
     Compiled c;
     std::string err;
-    int rc = compile_sequence(events, n_events, gamma, c, err);
+    int rc = compile_sequence(events, n_events, gamma, c, err, n_snap, snap_after);
     if (rc != MRSIM_OK) return (mrsim_status)rc;
     const int64_t n_train = (int64_t)c.train.size() / 2;
     if ((d->ops && (int64_t)c.ops64.size() > d->n_ops) || (d->pcls && c.n_pcls > d->n_pcls) ||

@@ -21,12 +21,12 @@ namespace mrsim {
 namespace {
 
 struct Item {
-    enum Kind { RF, PREC, SAMPLE, END } kind;
+    enum Kind { RF, PREC, SAMPLE, END, SNAP } kind;
     double k[3];    // gradient moment γ/2π·G·Δt [cycles/m]
     double dt;      // interval [s]
     double alpha, phi;
     double tau;     // RF/END: time since the previous RF pulse [s]
-    int64_t j;      // SAMPLE: sample index
+    int64_t j;      // SAMPLE: sample index; SNAP: snapshot index
     double adc_phase;
 };
 
@@ -106,8 +106,18 @@ void split(double v, float &hi, float &lo) {
 
 }  // namespace
 
-int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err) {
+int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err,
+                     int64_t n_snap, const int64_t *snap_after) {
     out = Compiled();
+    if (n_snap < 0 || (n_snap > 0 && !snap_after)) {
+        err = "invalid snapshot list";
+        return MRSIM_EINVAL;
+    }
+    for (int64_t q = 0; q < n_snap; ++q)
+        if (snap_after[q] < 0 || snap_after[q] >= n || (q > 0 && snap_after[q] <= snap_after[q - 1])) {
+            err = "snapshot " + std::to_string(q) + ": event indices must be strictly increasing and < n_events";
+            return MRSIM_EINVAL;
+        }
     if (!(gamma_hz > 0.0) || !std::isfinite(gamma_hz)) {
         err = "gamma_hz_per_t must be finite and > 0";
         return MRSIM_EINVAL;
@@ -122,7 +132,7 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     double tau = 0.0;
     bool have = false;
     double pk[3] = {0, 0, 0}, pdt = 0.0;
-    int64_t j = 0;
+    int64_t j = 0, snap_next = 0;
     auto flush = [&]() {
         if (have && !is_zero(pk, pdt)) {
             Item it{};
@@ -177,6 +187,15 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             have = true;
         }
         tau += e.dt;
+        if (snap_next < n_snap && snap_after[snap_next] == i) {  // state after event i
+            flush();
+            Item it{};
+            it.kind = Item::SNAP;
+            it.j = snap_next++;
+            it.tau = tau;
+            items.push_back(it);
+            tau = 0.0;  // the snapshot applies the T1 recovery so far
+        }
     }
     flush();
     {
@@ -186,6 +205,7 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         items.push_back(it);
     }
     out.n_adc = j;
+    out.n_snap = n_snap;
 
     // ---- group sample runs and count class uses -------------------------------------------------
     struct Group {
@@ -227,7 +247,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             use(puses, key_of(it.k, it.dt), groups[g].n, pos);
             if (it.kind == Item::SAMPLE && groups[g].n >= 4) use(puses, anchor_key(it, groups[g].n), 1, pos);
         }
-        if ((it.kind == Item::RF || it.kind == Item::END) && it.tau > 0.0) use(e1uses, bits(it.tau), 1, pos);
+        if ((it.kind == Item::RF || it.kind == Item::END || it.kind == Item::SNAP) && it.tau > 0.0)
+            use(e1uses, bits(it.tau), 1, pos);
     }
     auto pmap = pick_classes<Key>(puses, MAX_PCLS);
     auto e1map = pick_classes<uint64_t>(e1uses, MAX_E1CLS);
@@ -484,6 +505,20 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
                     push(a, b);
                 }
             }
+            break;
+        }
+        case Item::SNAP: {
+            OpF32 a = new32(OP_SNAP);
+            OpF64 b = new64(OP_SNAP);
+            set_e1(a, b, it.tau);
+            double cp, sp;
+            trig.get(psi, cp, sp);
+            a.f[0] = (float)cp;
+            a.f[1] = (float)sp;
+            b.f[0] = cp;
+            b.f[1] = sp;
+            a.adc0 = b.adc0 = (int32_t)it.j;
+            push(a, b);
             break;
         }
         case Item::END: {

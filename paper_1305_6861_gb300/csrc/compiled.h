@@ -19,9 +19,13 @@ struct Compiled {
     std::vector<double> train;  // 2 per sub-pulse table entry: cos α, sin α
     int n_pcls = 0, n_e1 = 0, n_e2 = 0;
     int64_t n_adc = 0;
+    int64_t n_snap = 0;  // snapshots (OP_SNAP operations) in the program
 };
 
 // Returns an mrsim_status; on failure `err` says why.
-int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err);
+// snap_after: NULL or n_snap strictly increasing event indices after which every spin's state is
+// recorded (§7.2: magnetisation data at chosen times).
+int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err,
+                     int64_t n_snap = 0, const int64_t *snap_after = nullptr);
 
 }  // namespace mrsim

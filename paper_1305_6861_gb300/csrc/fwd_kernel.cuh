@@ -400,6 +400,7 @@ struct Spins {
     int S, SP, nthr, tid, lane, warp, nwarp;
     int64_t base, np, n_spins;
     const double *params;
+    double *snap;  // NULL or the snapshot buffer (n_snap x n_spins x 3)
     const double *demod;
     const float *demod32;
     double *signal;
@@ -901,6 +902,22 @@ struct Spins {
         }
     }
 
+    __device__ __forceinline__ void snapshot(const Op &op) {
+        const double cps = (double)op.f[0], sps = (double)op.f[1];
+        double *dst = snap + (int64_t)op.adc0 * n_spins * 3;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const int64_t s = base + li(i);
+            const int qi = i % NP, hi = i / NP;
+            if (s < n_spins) {
+                const double uu = (double)lane_of(u[qi], hi), vv = (double)lane_of(v[qi], hi);
+                dst[3 * s] = uu * cps - vv * sps;
+                dst[3 * s + 1] = uu * sps + vv * cps;
+                dst[3 * s + 2] = (double)lane_of(mz[qi], hi);
+            }
+        }
+    }
+
     __device__ __forceinline__ void exec(const Op &op) {
         switch (op.kind) {
         case OP_RF_TRAIN:
@@ -935,6 +952,10 @@ struct Spins {
                 run_coils(op);
             else
                 run(op);
+            break;
+        case OP_SNAP:  // bring Mz up to date, then record (Mx, My, Mz) in the laboratory frame
+            t1_relax(op);
+            if (snap) snapshot(op);
             break;
         default:  // OP_END
             t1_relax(op);
@@ -1049,6 +1070,7 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     sp.demod32 = P.demod32;
     sp.signal = a.signal;
     sp.params = a.params;
+    sp.snap = a.snap;
     sp.win_base = 0;
     sp.win_end = 0;
     if constexpr (NC > 0) {

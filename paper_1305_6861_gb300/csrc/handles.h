@@ -42,6 +42,8 @@ struct mrsim_ctx {
     size_t sens_cap = 0;
     double *d_kt = nullptr;    // K-t steps and staged ensemble parameters
     size_t kt_cap = 0;
+    double *d_snap = nullptr;  // snapshots for host output
+    size_t snap_cap = 0;
     int *d_bad = nullptr;
 };
 

@@ -39,6 +39,8 @@ enum OpKind : uint8_t {
     OP_PREC = 3,     // precession + T2 over one interval: cached class or inline; [single sample]
     OP_RUN = 4,      // n consecutive samples, each after one precession by the cached class
     OP_RF_TRAIN = 5, // n fast sub-pulses whose (cos α, sin α) are train-table entries adc0 .. adc0+n-1
+    OP_SNAP = 6,     // snapshot adc0 of every spin's state: lazy T1 over f[10] (the T1 clock restarts),
+                     // then (Mx + jMy, Mz) with f[0], f[1] = cos ψ, sin ψ of the current frame
 };
 
 enum OpFlags : uint16_t {
@@ -132,6 +134,7 @@ struct FwdArgs {
     int *status;             // device status word (0 = ok)
     const void *sens;        // receive coils: n_coils x n_pad complex (float2 or double2), coil-major
     int32_t n_coils;         // 0 = no coil weighting
+    double *snap;            // NULL or n_snap x n_spins x 3 (device), written by OP_SNAP (laboratory frame)
 };
 
 // One work item of the persistent batch kernel: tile `tile` of the phantom of descriptor `desc`.

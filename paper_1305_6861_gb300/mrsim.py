@@ -33,7 +33,8 @@ EXPORTS = (
     "mrsim_stream_status", "mrsim_phantom_create", "mrsim_phantom_create_device", "mrsim_phantom_num_spins",
     "mrsim_phantom_destroy", "mrsim_sequence_load", "mrsim_sequence_num_adc", "mrsim_sequence_num_events",
     "mrsim_sequence_num_ops", "mrsim_sequence_destroy", "mrsim_simulate", "mrsim_simulate_ex",
-    "mrsim_simulate_coils", "mrsim_kt_simulate", "mrsim_max_config_k",
+    "mrsim_simulate_coils", "mrsim_kt_simulate", "mrsim_max_config_k", "mrsim_sequence_load_snapshots",
+    "mrsim_sequence_num_snapshots", "mrsim_debug_compile_snapshots",
     "mrsim_debug_compile", "mrsim_autotune", "mrsim_batch_create", "mrsim_batch_num_items",
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
@@ -74,6 +75,7 @@ class Options(ctypes.Structure):
         ("reserved", ctypes.c_int32),
         ("state_in", ctypes.c_void_p),
         ("state_out", ctypes.c_void_p),
+        ("snapshots", ctypes.c_void_p),
     ]
 
 
@@ -110,6 +112,9 @@ def lib():
             "mrsim_simulate_coils": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, i32, vp, vp, i64]),
             "mrsim_kt_simulate": (ctypes.c_int, [vp, i64, vp, vp, vp, vp, i64, vp, i32, ctypes.c_int, vp, vp, i64]),
             "mrsim_max_config_k": (ctypes.c_int, [i64, vp, ctypes.c_double, vp]),
+            "mrsim_sequence_load_snapshots": (ctypes.c_int, [vp, i64, vp, ctypes.c_double, i64, vp, P(vp)]),
+            "mrsim_sequence_num_snapshots": (i64, [vp]),
+            "mrsim_debug_compile_snapshots": (ctypes.c_int, [i64, vp, ctypes.c_double, i64, vp, P(ProgramDump)]),
             "mrsim_batch_create": (ctypes.c_int, [vp, i32, vp, vp, ctypes.c_int, vp, P(vp)]),
             "mrsim_batch_num_items": (i64, [vp]),
             "mrsim_batch_autotune": (ctypes.c_int, [vp, vp, P(Options)]),
@@ -219,14 +224,21 @@ class Phantom:
 class Sequence:
     """Compiled event list (host numpy array of EVENT_DTYPE records)."""
 
-    def __init__(self, ctx: Context, events, gamma_hz_per_t: float):
+    def __init__(self, ctx: Context, events, gamma_hz_per_t: float, snapshots=None):
+        """`snapshots`: event indices after which every spin's state is recorded (§7.2)."""
         self.ctx = ctx
         ev = np.ascontiguousarray(events)
         if ev.dtype != EVENT_DTYPE:
             ev = ev.astype(EVENT_DTYPE)
         h = ctypes.c_void_p()
-        ctx.check(lib().mrsim_sequence_load(ctx.h, ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(h)))
+        if snapshots is None:
+            ctx.check(lib().mrsim_sequence_load(ctx.h, ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(h)))
+        else:
+            sn = np.ascontiguousarray(snapshots, dtype=np.int64)
+            ctx.check(lib().mrsim_sequence_load_snapshots(ctx.h, ev.shape[0], _ptr(ev), float(gamma_hz_per_t),
+                                                          sn.shape[0], _ptr(sn), ctypes.byref(h)))
         self.h = h
+        self.n_snapshots = int(lib().mrsim_sequence_num_snapshots(h))
         self.n_adc = int(lib().mrsim_sequence_num_adc(h))
         self.n_events = int(lib().mrsim_sequence_num_events(h))
         self.n_ops = int(lib().mrsim_sequence_num_ops(h))
@@ -249,13 +261,13 @@ class Sequence:
 
 def simulate(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None, out=None,
              spins_per_thread: int = 0, threads_per_block: int = 0, accumulate: bool = False,
-             state_in=None, state_out=None):
+             state_in=None, state_out=None, snapshots=None):
     """Run the forward simulation.  `out`: numpy complex128[n_adc] (host, returned when None) or a CUDA
     buffer of 2*n_adc float64 (asynchronous on `stream`)."""
     if out is None:
         out = np.zeros(seq.n_adc, dtype=np.complex128)
     opt = Options(int(spins_per_thread), int(threads_per_block), ACCUMULATE if accumulate else 0, 0,
-                  _ptr(state_in), _ptr(state_out))
+                  _ptr(state_in), _ptr(state_out), _ptr(snapshots))
     rc = lib().mrsim_simulate_ex(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), _ptr(out), seq.n_adc,
                                  ctypes.byref(opt))
     ctx.check(rc)
@@ -436,7 +448,7 @@ def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP3
     return int(opt.spins_per_thread), int(opt.threads_per_block)
 
 
-def debug_compile(events, gamma_hz_per_t: float):
+def debug_compile(events, gamma_hz_per_t: float, snapshots=None):
     """Host-only compile of an event list (no GPU needed).  Returns a dict with the float64 device
     program (op records), the class tables, the sub-pulse table and the per-sample demodulation
     factors (complex)."""
@@ -444,8 +456,14 @@ def debug_compile(events, gamma_hz_per_t: float):
     ev = np.ascontiguousarray(events)
     if ev.dtype != EVENT_DTYPE:
         ev = ev.astype(EVENT_DTYPE)
+    sn = np.ascontiguousarray([] if snapshots is None else snapshots, dtype=np.int64)
+
+    def call(d):
+        return L.mrsim_debug_compile_snapshots(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), sn.shape[0],
+                                               _ptr(sn) if sn.shape[0] else None, ctypes.byref(d))
+
     d = ProgramDump()
-    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(d))
+    rc = call(d)
     if rc != 0:
         raise MrsimError(rc, "mrsim_debug_compile failed")
     out = {
@@ -458,7 +476,7 @@ def debug_compile(events, gamma_hz_per_t: float):
     }
     for f in ("ops", "pcls", "e1", "e2", "train", "demod"):
         setattr(d, f, out[f].ctypes.data)
-    rc = L.mrsim_debug_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), ctypes.byref(d))
+    rc = call(d)
     if rc != 0:
         raise MrsimError(rc, "mrsim_debug_compile failed")
     return out
@@ -470,7 +488,7 @@ OP64_DTYPE = np.dtype(
      ("ecls", "<i2"), ("acls", "<i2"), ("rsv1", "<i2"), ("rsv2", "<i4"), ("f", "<f8", (13,))]
 )
 assert OP64_DTYPE.itemsize == 128
-OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN, OP_RF_TRAIN = 0, 1, 2, 3, 4, 5
+OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN, OP_RF_TRAIN, OP_SNAP = 0, 1, 2, 3, 4, 5, 6
 F_ADC, F_PCLS, F_PLOAD, F_INLINE, F_E1CLS, F_E1LOAD, F_E1INL, F_E2CLS, F_ANCHOR, F_FRAME = (
     1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
 F_KX, F_KY, F_KZ, F_DT = 1024, 2048, 4096, 8192

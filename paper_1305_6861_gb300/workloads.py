@@ -696,3 +696,32 @@ def kt_random_sequence(n_steps: int, rng: np.random.Generator, max_shift: int = 
         rows.append((al, rng.uniform(0, 2 * math.pi), rng.uniform(0.0, 8e-3), int(rng.integers(-max_shift, max_shift + 1)),
                      int(rng.uniform() < 0.6), rng.uniform(0, 2 * math.pi)))
     return kt_steps(rows)
+
+
+# ---------------------------------------------------------------------------
+# Static-field inhomogeneity of a whole-body magnet (Eq. 6.3)
+# ---------------------------------------------------------------------------
+
+
+def legendre(n: int, x):
+    """Legendre polynomial P_n(x) by the three-term (Bonnet) recursion."""
+    x = np.asarray(x, dtype=float)
+    p0, p1 = np.ones_like(x), x.copy()
+    if n == 0:
+        return p0
+    for k in range(1, n):
+        p0, p1 = p1, ((2 * k + 1) * x * p1 - k * p0) / (k + 1)
+    return p1
+
+
+def b0_legendre(x, y, z, c_tesla: float, radius: float) -> np.ndarray:
+    """ΔB0 [T] of Eq. 6.3: -C·(r/R)^12·P12(cos θ), r = |x|, θ the declination from the z axis."""
+    x, y, z = (np.asarray(a, dtype=float) for a in (x, y, z))
+    r = np.sqrt(x * x + y * y + z * z)
+    cos_t = np.divide(z, r, out=np.ones_like(r), where=r > 0)
+    return -c_tesla * (r / radius) ** 12 * legendre(12, cos_t)
+
+
+def dw_from_b0(delta_b0, gamma_hz_per_t: float = GAMMA_BAR) -> np.ndarray:
+    """Off-resonance [rad/s] of a field deviation: Δω0 = -γ·ΔB0 (Eqs. 6.1, 6.2, ω = -γB)."""
+    return -2 * math.pi * gamma_hz_per_t * np.asarray(delta_b0, dtype=float)

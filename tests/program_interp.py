@@ -14,8 +14,10 @@ import numpy as np
 from paper_1305_6861_gb300 import mrsim as M
 
 
-def interpret(events, gamma, ph, state_in=None):
-    prog = M.debug_compile(events, gamma)
+def interpret(events, gamma, ph, state_in=None, snapshots=None):
+    """Returns (signal, final state, ops[, snapshots]); snapshots: the states (laboratory frame)
+    after the given event indices, when asked for."""
+    prog = M.debug_compile(events, gamma, snapshots=snapshots)
     ops, pcls, e1tab, e2tab, demod, train = (prog[k] for k in ("ops", "pcls", "e1", "e2", "demod", "train"))
     n_adc = demod.shape[0]
     x, y, z, rho = ph.x, ph.y, ph.z, ph.rho
@@ -35,6 +37,7 @@ def interpret(events, gamma, ph, state_in=None):
         m = state_in[:, 0] + 1j * state_in[:, 1]
         mz = state_in[:, 2].copy()
     psi = 0.0  # frame angle, tracked here independently from the ops' frame turns
+    snaps = np.zeros((0 if snapshots is None else len(snapshots), ph.n, 3))
     wc = None  # register caches of the kernel
     e1c = None
 
@@ -107,9 +110,16 @@ def interpret(events, gamma, ph, state_in=None):
                 sample(op["adc0"] + t, m)
             if fl & M.F_ANCHOR:
                 m = start * W[op["acls"]]
+        elif k == M.OP_SNAP:
+            t1(op)
+            assert abs(math.atan2(f[1], f[0]) - math.atan2(math.sin(psi), math.cos(psi))) < 1e-9
+            lab = m * (f[0] + 1j * f[1])
+            snaps[op["adc0"]] = np.stack([lab.real, lab.imag, mz], 1)
         else:
             t1(op)
             assert abs(math.atan2(f[1], f[0]) - math.atan2(math.sin(psi), math.cos(psi))) < 1e-9
     lab = m * np.exp(1j * psi)
     state = np.stack([lab.real, lab.imag, mz], 1)
+    if snapshots is not None:
+        return sig, state, ops, snaps
     return sig, state, ops

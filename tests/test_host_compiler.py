@@ -136,3 +136,37 @@ def test_class_tables_bounded_and_used(mrsim_lib):
     # every readout is one run with an anchor
     runs = ops[ops["kind"] == M.OP_RUN]
     assert len(runs) == 32 and np.all(runs["flags"] & M.F_ANCHOR)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_snapshots_compiled_program(oracle_mod, mrsim_lib, seed):
+    """Snapshots (§7.2) after chosen events: the compiled program's states equal the oracle's final
+    state on the event prefix, and the signal is unchanged by them."""
+    rng = np.random.default_rng(4200 + seed)
+    ph = W.random_phantom(300, rng)
+    seq = W.random_sequence(700, rng, runs=True)
+    ev = seq.events
+    snaps = np.sort(rng.choice(len(ev), size=6, replace=False))
+    snaps[-1] = len(ev) - 1
+    M = mrsim_lib
+    sig, state, ops, got = interpret(ev, seq.gamma_hz_per_t, ph, snapshots=snaps)
+    assert np.count_nonzero(ops["kind"] == M.OP_SNAP) == len(snaps)
+    # float64 floor for phases of ~1e4 rad per event: each side rounds θ with relative error 2^-53
+    g = 2 * math.pi * seq.gamma_hz_per_t
+    th = (g * (np.abs(ev["gx"]) * np.abs(ph.x).max() + np.abs(ev["gy"]) * np.abs(ph.y).max()
+               + np.abs(ev["gz"]) * np.abs(ph.z).max()) + np.abs(ph.dw).max()) * ev["dt"]
+    tol = max(1e-12, 4 * 2.0**-53 * float(np.sqrt(np.sum(th**2))))
+    ref_sig, _ = oracle_mod.simulate(ph, ev, seq.gamma_hz_per_t)
+    assert np.linalg.norm(sig - ref_sig) <= tol * np.linalg.norm(ref_sig)
+    for q, e in enumerate(snaps):
+        _, st = oracle_mod.simulate(ph, ev[: e + 1], seq.gamma_hz_per_t, want_signal=False, want_state=True)
+        assert np.max(np.abs(got[q] - st)) <= tol * max(1.0, np.abs(st).max()), (q, e)
+    assert np.max(np.abs(got[-1] - state)) <= 1e-13
+
+
+def test_snapshot_lists_are_validated(mrsim_lib):
+    ev = W.random_sequence(50, np.random.default_rng(3)).events
+    for bad in ([5, 5], [7, 3], [-1], [50]):
+        with pytest.raises(mrsim_lib.MrsimError) as e:
+            mrsim_lib.debug_compile(ev, W.GAMMA_BAR, snapshots=bad)
+        assert e.value.status == mrsim_lib.Status.EINVAL
