@@ -257,8 +257,22 @@ def run_batch(args):
                      "ops_per_spin_step": ops / spin_steps},
         "gpu_launches": 2 * args.steps, "clocks": ck,
     }
+    if not args.no_cpu_baseline:  # the oracle on a bounded spin sample of the batch's longest program
+        wl = max(ws, key=lambda w: w.sequence.n_events)
+        cb, _ = cpu_baseline(wl, seconds=args.cpu_seconds)
+        cb["sample"] = "c4 phantom " + cb["sample"]
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     return 0
+
+
+# Adjoint (float64) work per spin-step, in float64 flops (an FMA is 2): forward step = pulse
+# (3x3 matrix-vector, 18 when the event has one) + precession/T2 (8) + T1 (3); the backward pass
+# recomputes the forward step and applies the transposed step (pulse 18, its flip derivative 18 +
+# 6 when the flip is learnable, precession 8, T1 3, parameter gradients 12).
+ADJ_FLOPS_FWD_RF, ADJ_FLOPS_FWD = 18, 11
+ADJ_FLOPS_BWD_RF, ADJ_FLOPS_BWD = 42, 23
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 float64 (profiling recipe; no measured figure)
 
 
 def run_adjoint(args):
@@ -296,6 +310,10 @@ def run_adjoint(args):
         step()
     ctx.stream_status(stream)
     ev0 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.15)
+    torch.cuda.synchronize()
     for i in range(args.steps):
         ev0[i][0].record(stream)
         step()
@@ -303,12 +321,44 @@ def run_adjoint(args):
     torch.cuda.synchronize()
     ctx.stream_status(stream)
     ms = sum(a.elapsed_time(b) for a, b in ev0) / args.steps
+    ck = clocks.stop()
+    n_rf = int(np.count_nonzero(ev["rf_flip"] != 0))
+    n_ev = len(ev)
+    flops_spin = (2 * ADJ_FLOPS_FWD * n_ev + 2 * ADJ_FLOPS_FWD_RF * n_rf  # forward + recompute
+                  + ADJ_FLOPS_BWD * n_ev + ADJ_FLOPS_BWD_RF * n_rf)
+    flops = flops_spin * w.phantom.n
+    achieved = flops / (ms * 1e-3) / 1e9
     line = {"metric": "spin-steps/s of forward+backward (adjoint) at 1 GB300", "value": w.spin_steps / (ms * 1e-3),
             "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": len(ev), "n_rf_params": len(rf0),
-                       "ckpt_every": 64, "step": "adjoint forward + backward"},
-            "gpu_launches": 4 * args.steps}
+                       "ckpt_every": 64, "step": "adjoint forward + backward",
+                       "note": "16 384 spins are 512 warps, fewer than the 608 schedulers: latency-bound by size"},
+            "roofline": {"bound": "fp64", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (float64)",
+                         "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None, "kernel_ms": ms,
+                         "peak_basis": "nominal float64 rate of the profiling recipe (no measured float64 figure)",
+                         "flops_per_spin_step": flops_spin / n_ev},
+            "gpu_launches": 4 * args.steps, "clocks": ck}
+    if not args.no_cpu_baseline:  # the oracle's forward-mode gradient (every flip) on a bounded spin sample
+        import oracle
+
+        cores = len(os.sched_getaffinity(0))
+        rng = np.random.default_rng(1)
+        h = np.ones(adj.n_adc, dtype=np.complex128)
+        sel = np.arange(len(rf0), dtype=np.int32)
+
+        def grad_time(n):
+            sub = w.phantom.subset(np.sort(rng.choice(w.phantom.n, n, replace=False)))
+            t0 = time.perf_counter()
+            oracle.gradient(sub, ev, W.GAMMA_BAR, h, params, rf0, sel, n_threads=cores)
+            return time.perf_counter() - t0
+
+        per_spin = grad_time(cores) / cores
+        n = int(max(cores, min(w.phantom.n, args.cpu_seconds / max(per_spin, 1e-9))))
+        el = grad_time(n)
+        line["cpu_baseline"] = {"value": n * n_ev / el, "unit": "spin-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"forward-mode gradient (M0, T1, T2 and all {len(rf0)} flips) of {n} of "
+                                          f"{w.phantom.n} spins over the full sequence, {el:.1f} s"}
     print(json.dumps(line), flush=True)
     return 0
 
