@@ -285,7 +285,7 @@ mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, con
     p.n_train = (int32_t)(s->host.train.size() / 2);
     p.n_adc = s->host.n_adc;
     for (const OpF32 &o : s->host.ops32)  // magnitude bound of the float32 inline phase terms
-        if (o.kind == OP_PREC && (o.flags & F_INLINE))
+        if ((o.kind == OP_PREC || o.kind == OP_RUN) && (o.flags & F_INLINE))
             for (int a = 0; a < 4; ++a) p.kmax[a] = std::max(p.kmax[a], std::fabs(o.f[2 * a]));
     s->p32 = p;
     s->p32.ops = s->d_ops32;

@@ -240,23 +240,72 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         double k[3] = {it.k[0] * (double)cnt, it.k[1] * (double)cnt, it.k[2] * (double)cnt};
         return key_of(k, it.dt * (double)cnt);
     };
+    auto is_run = [&](size_t g) {
+        const Item &it = items[groups[g].first];
+        return it.kind == Item::SAMPLE && !is_zero(it.k, it.dt) && groups[g].n >= 4;
+    };
     for (size_t g = 0; g < groups.size(); ++g) {
         const Item &it = items[groups[g].first];
         const int64_t pos = (int64_t)groups[g].first;
-        if (it.kind == Item::PREC || (it.kind == Item::SAMPLE && !is_zero(it.k, it.dt))) {
+        if (it.kind == Item::PREC || (it.kind == Item::SAMPLE && !is_zero(it.k, it.dt)))
             use(puses, key_of(it.k, it.dt), groups[g].n, pos);
-            if (it.kind == Item::SAMPLE && groups[g].n >= 4) use(puses, anchor_key(it, groups[g].n), 1, pos);
-        }
         if ((it.kind == Item::RF || it.kind == Item::END || it.kind == Item::SNAP) && it.tau > 0.0)
             use(e1uses, bits(it.tau), 1, pos);
     }
+    // Rewound readouts: a one-off precession A (phase encoding), a sample run R and a one-off
+    // precession B whose moments add up to one that recurs (B undoes A's encoding, as in every
+    // Cartesian gradient echo).  Precessions about z commute, so the state after B is the state
+    // before A times the phasor of the whole interval A+R+B (Eqs. 3.5, 3.14): the run starts with
+    // A inline, its anchor restores from the state before A with that class, and B disappears.
+    // Moment components that cancel to rounding level are snapped to zero so that the sum is
+    // the same in every repetition.
+    auto single = [&](size_t g) {
+        const Item &it = items[groups[g].first];
+        if (it.kind != Item::PREC) return false;
+        auto f = puses.find(key_of(it.k, it.dt));
+        return f != puses.end() && f->second.first < 2;  // stays inline
+    };
+    std::vector<Key> fkey(groups.size());
+    std::vector<char> cand(groups.size(), 0), claimed(groups.size(), 0);
+    std::unordered_map<Key, std::pair<int64_t, int64_t>, KeyHash> fuses;
+    for (size_t g = 1; g + 1 < groups.size(); ++g) {
+        if (claimed[g - 1] || !is_run(g) || !single(g - 1) || !single(g + 1)) continue;
+        const Item &A = items[groups[g - 1].first], &R = items[groups[g].first], &B = items[groups[g + 1].first];
+        const double n = (double)groups[g].n;
+        double k[3];
+        for (int c = 0; c < 3; ++c) {
+            const double s = A.k[c] + R.k[c] * n + B.k[c];
+            const double mag = std::fabs(A.k[c]) + std::fabs(R.k[c] * n) + std::fabs(B.k[c]);
+            k[c] = std::fabs(s) <= mag * 0x1p-46 ? 0.0 : s;
+        }
+        fkey[g] = key_of(k, A.dt + R.dt * n + B.dt);
+        cand[g] = claimed[g - 1] = claimed[g + 1] = 1;
+        use(fuses, fkey[g], 1, (int64_t)groups[g].first);
+    }
+    for (size_t g = 0; g < groups.size(); ++g) {
+        if (!is_run(g)) continue;
+        if (cand[g] && fuses[fkey[g]].first >= 2)
+            use(puses, fkey[g], 1, (int64_t)groups[g].first);
+        else
+            use(puses, anchor_key(items[groups[g].first], groups[g].n), 1, (int64_t)groups[g].first);
+    }
     auto pmap = pick_classes<Key>(puses, MAX_PCLS);
     auto e1map = pick_classes<uint64_t>(e1uses, MAX_E1CLS);
+    // fused triples: A goes into the run op (role 1), B is dropped (role 2)
+    std::vector<char> fused(groups.size(), 0), role(groups.size(), 0);
+    for (size_t g = 1; g + 1 < groups.size(); ++g) {
+        const Item &R = items[groups[g].first];
+        if (cand[g] && fuses[fkey[g]].first >= 2 && pmap.count(fkey[g]) && pmap.count(key_of(R.k, R.dt))) {
+            fused[g] = 1;
+            role[g - 1] = 1;
+            role[g + 1] = 2;
+        }
+    }
     // E2 classes: intervals of the precessions that stay inline
     for (size_t g = 0; g < groups.size(); ++g) {
         const Item &it = items[groups[g].first];
         if ((it.kind == Item::PREC || it.kind == Item::SAMPLE) && !is_zero(it.k, it.dt) && it.dt > 0.0 &&
-            !pmap.count(key_of(it.k, it.dt)))
+            !pmap.count(key_of(it.k, it.dt)) && role[g] != 2)
             use(e2uses, bits(it.dt), groups[g].n, (int64_t)groups[g].first);
     }
     auto e2map = pick_classes<uint64_t>(e2uses, MAX_E2CLS);
@@ -452,6 +501,7 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             break;
         }
         case Item::PREC: {
+            if (role[g]) break;  // inside a rewound readout: emitted with (A) or absorbed by (B) the run
             OpF32 a = new32(OP_PREC);
             OpF64 b = new64(OP_PREC);
             auto pc = pmap.find(key_of(it.k, it.dt));
@@ -483,7 +533,11 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
                 use_pcls(a, b, pc->second);
                 a.n = b.n = (int32_t)cnt;
                 a.adc0 = b.adc0 = (int32_t)it.j;
-                if (cnt >= 4) {
+                if (fused[g]) {  // A first, then the samples; the anchor covers A, the run and B
+                    set_inline_prec(a, b, items[groups[g - 1].first]);
+                    both(a, b, F_ANCHOR);
+                    a.acls = b.acls = (int16_t)pmap.at(fkey[g]);
+                } else if (cnt >= 4) {
                     auto an = pmap.find(anchor_key(it, cnt));
                     if (an != pmap.end()) {
                         both(a, b, F_ANCHOR);

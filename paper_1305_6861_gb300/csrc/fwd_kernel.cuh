@@ -721,6 +721,7 @@ struct Spins {
                 av[q] = v[q];
             }
         }
+        if (op.flags & F_INLINE) prec_inline(op);  // the run's leading precession (the anchor restores from before it)
         for (int t0 = 0; t0 < n;) {
             if (j0 + t0 - win_base >= WINS) flush();
             const int m = min(n - t0, WINS - (j0 + t0 - win_base));
@@ -849,6 +850,7 @@ struct Spins {
                 av[q] = v[q];
             }
         }
+        if (op.flags & F_INLINE) prec_inline(op);  // the run's leading precession (the anchor restores from before it)
         if (j0 + n - win_base > WIN) flush();
         const int slot0 = j0 - win_base;
         int t0 = 0;

@@ -37,7 +37,7 @@ enum OpKind : uint8_t {
                      // [fused class precession] [single sample]
     OP_RF_FAST = 2,  // sub-pulse of a train: lazy T1 with the cached class, rotation, cached precession
     OP_PREC = 3,     // precession + T2 over one interval: cached class or inline; [single sample]
-    OP_RUN = 4,      // n consecutive samples, each after one precession by the cached class
+    OP_RUN = 4,      // [inline precession] then n consecutive samples, each after one precession by the cached class
     OP_RF_TRAIN = 5, // n fast sub-pulses whose (cos α, sin α) are train-table entries adc0 .. adc0+n-1
     OP_SNAP = 6,     // snapshot adc0 of every spin's state: lazy T1 over f[10] (the T1 clock restarts),
                      // then (Mx + jMy, Mz) with f[0], f[1] = cos ψ, sin ψ of the current frame
@@ -47,12 +47,12 @@ enum OpFlags : uint16_t {
     F_ADC = 1,       // one sample (index adc0) after the operation
     F_PCLS = 2,      // precession by the cached phasor class
     F_PLOAD = 4,     // load phasor class pcls into the register cache first
-    F_INLINE = 8,    // PREC: phase from the op's own moment and Δt
+    F_INLINE = 8,    // PREC, RUN: phase from the op's own moment and Δt (a run applies it before its samples)
     F_E1CLS = 16,    // RF/END: lazy T1 factor from the cached T1 class
     F_E1LOAD = 32,   // load T1 class ecls into the register cache first
     F_E1INL = 64,    // RF/END: lazy T1 factor computed from f[10]
     F_E2CLS = 128,   // inline PREC: T2 factor from class ecls
-    F_ANCHOR = 256,  // RUN: state after the run = state before * phasor class acls (no drift)
+    F_ANCHOR = 256,  // RUN: state after the run = state before it (and its inline precession) * phasor class acls
     F_FRAME = 512,   // RF: turn the frame by exp(-jδ), f[2] = cos δ, f[3] = sin δ
     F_KX = 1024,     // inline PREC: which phase terms are non-zero
     F_KY = 2048,

@@ -2,7 +2,7 @@
 
 It executes the operation stream that ``mrsim_debug_compile`` returns with numpy, with the
 semantics the kernels implement (pulse frame, lazy T1 per pulse, cached precession and T1
-classes with explicit reloads, sample runs with anchors), so that the host compiler's
+classes with explicit reloads, sample runs with anchors and leading inline precessions), so that the host compiler's
 rewrites — merged intervals, fused sub-pulses, frame tracking, class selection, cache
 bookkeeping, run grouping — can be compared with the oracle on the CPU.  It is test
 infrastructure, not a fallback: the library never calls it.
@@ -63,6 +63,12 @@ def interpret(events, gamma, ph, state_in=None, snapshots=None):
             wc = W[op["pcls"]]
         return wc
 
+    def inline(op):
+        f = op["f"]
+        e2 = E2[op["ecls"]] if op["flags"] & M.F_E2CLS else np.exp(-f[3] * r2)
+        th = f[0] * x + f[1] * y + f[2] * z + f[3] * df
+        return e2 * np.exp(-2j * math.pi * th)
+
     for op in ops:
         k, fl, f = op["kind"], op["flags"], op["f"]
         if k == M.OP_RF_TRAIN:
@@ -97,13 +103,13 @@ def interpret(events, gamma, ph, state_in=None, snapshots=None):
                 for _ in range(op["n"]):
                     m = m * pcls_use(op)
             elif fl & M.F_INLINE:
-                e2 = E2[op["ecls"]] if fl & M.F_E2CLS else np.exp(-f[3] * r2)
-                th = f[0] * x + f[1] * y + f[2] * z + f[3] * df
-                m = m * e2 * np.exp(-2j * math.pi * th)
+                m = m * inline(op)
             if fl & M.F_ADC:
                 sample(op["adc0"], m)
         elif k == M.OP_RUN:
-            start = m
+            start = m  # the anchor restores from the state before the run's own precession
+            if fl & M.F_INLINE:
+                m = m * inline(op)
             w = pcls_use(op)
             for t in range(op["n"]):
                 m = m * w

@@ -170,3 +170,77 @@ def test_snapshot_lists_are_validated(mrsim_lib):
         with pytest.raises(mrsim_lib.MrsimError) as e:
             mrsim_lib.debug_compile(ev, W.GAMMA_BAR, snapshots=bad)
         assert e.value.status == mrsim_lib.Status.EINVAL
+
+
+# ---- rewound readouts: A (phase encoding), run, B (rewinder) folded into the run ----------------
+import rewound_cases as RC
+
+
+def _fold_check(M, oracle_mod, ev, ph, snapshots=None):
+    out = interpret(ev, RC.GAMMA, ph, snapshots=snapshots)
+    sig, state, ops = out[:3]
+    ref, ref_state = oracle_mod.simulate(ph, ev, RC.GAMMA, want_state=True)
+    _check_structure(ev, ops, int(np.count_nonzero(ev["adc"])))
+    tol = RC.phase_floor(ph, ev)
+    assert rel_l2(sig, ref) <= tol
+    assert np.max(np.abs(state - ref_state)) <= tol * max(1.0, np.max(np.abs(ref_state)))
+    return out
+
+
+@pytest.mark.parametrize("case", ["c1", "c3_small"])
+def test_gradient_echo_readouts_are_folded(case, mrsim_lib):
+    """Every readout of the gradient-echo configurations folds its phase encoding and rewinder:
+    no inline precession op is left and each TR is one pulse and one run."""
+    M = mrsim_lib
+    w = CASES[case]()
+    ops = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)["ops"]
+    runs = ops[ops["kind"] == M.OP_RUN]
+    assert len(runs) > 0 and np.all(runs["flags"] & M.F_INLINE) and np.all(runs["flags"] & M.F_ANCHOR)
+    assert not np.any((ops["kind"] == M.OP_PREC) & ((ops["flags"] & M.F_INLINE) != 0))
+
+
+def test_fold_program_matches_oracle(mrsim_lib, oracle_mod):
+    ev = RC.flash_like()
+    assert RC.fold_counts(mrsim_lib, ev) == (16, 16, 0)
+    _fold_check(mrsim_lib, oracle_mod, ev, RC.phantom(80, np.random.default_rng(7)))
+
+
+def test_no_fold_when_the_rewinder_misses(mrsim_lib, oracle_mod):
+    """A rewinder that leaves a different residual moment every TR gives no recurring total, so
+    nothing is folded (the readout keeps its own anchor) and the program is unchanged in meaning."""
+    ev = RC.flash_like(jitter=np.random.default_rng(3))
+    folded, runs, inline = RC.fold_counts(mrsim_lib, ev)
+    assert folded == 0 and runs == 16 and inline == 32
+    _fold_check(mrsim_lib, oracle_mod, ev, RC.phantom(60, np.random.default_rng(8)))
+
+
+def test_no_rewinder_no_fold(mrsim_lib, oracle_mod):
+    ev = RC.flash_like(rewind=False)
+    assert RC.fold_counts(mrsim_lib, ev)[0] == 0
+    _fold_check(mrsim_lib, oracle_mod, ev, RC.phantom(60, np.random.default_rng(9)))
+
+
+def test_overlapping_triples_fold_once(mrsim_lib, oracle_mod):
+    """Multi-echo readouts: A+R1+B and B+R2+C both recur; B can only belong to one fold, so the
+    first readout of each TR folds and the second keeps its plain anchor."""
+    ev = RC.multi_echo()
+    folded, runs, inline = RC.fold_counts(mrsim_lib, ev)
+    assert (folded, runs, inline) == (12, 24, 12)
+    _fold_check(mrsim_lib, oracle_mod, ev, RC.phantom(70, np.random.default_rng(10)))
+
+
+def test_snapshot_inside_a_rewound_readout(mrsim_lib, oracle_mod):
+    """A snapshot between the phase encoding and the readout (or inside the readout) needs the
+    state there: that TR is not folded, the others are."""
+    M = mrsim_lib
+    ev = RC.flash_like()
+    per_tr = len(ev) // 16
+    snaps = np.array([3 * per_tr + 1, 7 * per_tr + 5, len(ev) - 1])  # after A of TR 3; inside R of TR 7
+    folded, runs, _ = RC.fold_counts(M, ev, snapshots=snaps)
+    assert runs >= 16 and folded == 14
+    ph = RC.phantom(50, np.random.default_rng(11))
+    _, _, _, got = _fold_check(M, oracle_mod, ev, ph, snapshots=snaps)
+    tol = RC.phase_floor(ph, ev)
+    for q, e in enumerate(snaps):
+        _, st = oracle_mod.simulate(ph, ev[: e + 1], RC.GAMMA, want_signal=False, want_state=True)
+        assert np.max(np.abs(got[q] - st)) <= tol * max(1.0, np.abs(st).max()), q
