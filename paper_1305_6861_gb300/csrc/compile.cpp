@@ -86,18 +86,101 @@ class TrigCache {
     };
     static constexpr size_t N = 4096;
     std::vector<Entry> t_;
+    const Entry *last_ = nullptr;
 
   public:
     TrigCache() : t_(N, Entry{0, 0.0, 0.0, false}) {}
     void get(double x, double &c, double &s) {
         uint64_t b;
         std::memcpy(&b, &x, 8);
+        if (last_ && last_->key == b) {  // a readout repeats its receiver phase sample after sample
+            c = last_->c;
+            s = last_->s;
+            return;
+        }
         Entry &e = t_[(b ^ (b >> 23) ^ (b >> 41)) & (N - 1)];
+        last_ = &e;
         if (!(e.ok && e.key == b)) e = Entry{b, std::cos(x), std::sin(x), true};
         c = e.c;
         s = e.s;
     }
 };
+
+struct Group {
+    size_t first;
+    int64_t n;  // number of items (samples for runs)
+};
+
+// Per-thread scratch for the lowered items and their groups: kept between calls, so that
+// compiling sequences of similar size touches no fresh pages (above 64 MB it is released).
+struct Scratch {
+    std::vector<Item> items;
+    std::vector<Group> groups;
+};
+constexpr size_t SCRATCH_KEEP_BYTES = size_t(64) << 20;
+struct ScratchLease {
+    Scratch &s;
+    ScratchLease() : s(get()) {
+        s.items.clear();
+        s.groups.clear();
+    }
+    ~ScratchLease() {
+        if (s.items.capacity() * sizeof(Item) + s.groups.capacity() * sizeof(Group) > SCRATCH_KEEP_BYTES) {
+            std::vector<Item>().swap(s.items);
+            std::vector<Group>().swap(s.groups);
+        }
+    }
+    static Scratch &get() {
+        static thread_local Scratch t;
+        return t;
+    }
+};
+
+// Use counts of class keys: key -> (count, first position); consecutive uses of one key (the
+// sub-pulses of a shaped pulse, the samples of a readout) skip the hash lookup.
+template <class K, class H = std::hash<K>>
+struct Uses {
+    using Map = std::unordered_map<K, std::pair<int64_t, int64_t>, H>;
+    Map m;
+    typename Map::iterator last = m.end();
+    void add(const K &key, int64_t cnt, int64_t pos) {
+        if (last != m.end() && last->first == key) {
+            last->second.first += cnt;
+            return;
+        }
+        auto r = m.try_emplace(key, cnt, pos);
+        if (!r.second) r.first->second.first += cnt;
+        last = r.first;
+    }
+    int64_t count(const K &key) const {
+        auto f = m.find(key);
+        return f == m.end() ? 0 : f->second.first;
+    }
+};
+
+// Class index of a key (-1: none), remembering the previous query: consecutive items mostly ask
+// for the same key.
+template <class K>
+struct ClassOf {
+    const std::map<K, int> &map;
+    K last{};
+    int last_id = -1;
+    bool valid = false;
+    explicit ClassOf(const std::map<K, int> &m) : map(m) {}
+    int operator()(const K &key) {
+        if (!(valid && key == last)) {
+            auto f = map.find(key);
+            last = key;
+            last_id = f == map.end() ? -1 : f->second;
+            valid = true;
+        }
+        return last_id;
+    }
+};
+
+bool same_interval(const Item &a, const Item &b) {  // the key equality of key_of, without the keys
+    return a.k[0] == b.k[0] && a.k[1] == b.k[1] && a.k[2] == b.k[2] && a.dt == b.dt;
+}
 
 void split(double v, float &hi, float &lo) {
     hi = (float)v;
@@ -127,7 +210,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         return MRSIM_EINVAL;
     }
     // ---- validate and lower to items -------------------------------------------------------
-    std::vector<Item> items;
+    ScratchLease lease;
+    std::vector<Item> &items = lease.s.items;
     items.reserve((size_t)n + 2);
     double tau = 0.0;
     bool have = false;
@@ -208,17 +292,12 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     out.n_snap = n_snap;
 
     // ---- group sample runs and count class uses -------------------------------------------------
-    struct Group {
-        size_t first;
-        int64_t n;  // number of items (samples for runs)
-    };
-    std::vector<Group> groups;
+    std::vector<Group> &groups = lease.s.groups;
     for (size_t i = 0; i < items.size();) {
         if (items[i].kind == Item::SAMPLE && !is_zero(items[i].k, items[i].dt)) {
-            Key k0 = key_of(items[i].k, items[i].dt);
             size_t e = i + 1;
             while (e < items.size() && items[e].kind == Item::SAMPLE && (int64_t)(e - i) < RUN_MAX &&
-                   key_of(items[e].k, items[e].dt) == k0)
+                   same_interval(items[e], items[i]))
                 ++e;
             groups.push_back({i, (int64_t)(e - i)});
             i = e;
@@ -227,15 +306,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             ++i;
         }
     }
-    std::unordered_map<Key, std::pair<int64_t, int64_t>, KeyHash> puses;  // key -> (count, first position)
-    std::unordered_map<uint64_t, std::pair<int64_t, int64_t>> e1uses, e2uses;
-    auto use = [](auto &m, const auto &key, int64_t cnt, int64_t pos) {
-        auto it = m.find(key);
-        if (it == m.end())
-            m[key] = {cnt, pos};
-        else
-            it->second.first += cnt;
-    };
+    Uses<Key, KeyHash> puses;
+    Uses<uint64_t> e1uses, e2uses;
     auto anchor_key = [&](const Item &it, int64_t cnt) {
         double k[3] = {it.k[0] * (double)cnt, it.k[1] * (double)cnt, it.k[2] * (double)cnt};
         return key_of(k, it.dt * (double)cnt);
@@ -248,9 +320,9 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         const Item &it = items[groups[g].first];
         const int64_t pos = (int64_t)groups[g].first;
         if (it.kind == Item::PREC || (it.kind == Item::SAMPLE && !is_zero(it.k, it.dt)))
-            use(puses, key_of(it.k, it.dt), groups[g].n, pos);
+            puses.add(key_of(it.k, it.dt), groups[g].n, pos);
         if ((it.kind == Item::RF || it.kind == Item::END || it.kind == Item::SNAP) && it.tau > 0.0)
-            use(e1uses, bits(it.tau), 1, pos);
+            e1uses.add(bits(it.tau), 1, pos);
     }
     // Rewound readouts: a one-off precession A (phase encoding), a sample run R and a one-off
     // precession B whose moments add up to one that recurs (B undoes A's encoding, as in every
@@ -262,12 +334,11 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     auto single = [&](size_t g) {
         const Item &it = items[groups[g].first];
         if (it.kind != Item::PREC) return false;
-        auto f = puses.find(key_of(it.k, it.dt));
-        return f != puses.end() && f->second.first < 2;  // stays inline
+        return puses.count(key_of(it.k, it.dt)) < 2;  // stays inline
     };
-    std::vector<Key> fkey(groups.size());
-    std::vector<char> cand(groups.size(), 0), claimed(groups.size(), 0);
-    std::unordered_map<Key, std::pair<int64_t, int64_t>, KeyHash> fuses;
+    std::unordered_map<size_t, Key> fkey;  // candidate run group -> key of A+R+B
+    std::vector<char> claimed(groups.size(), 0);
+    Uses<Key, KeyHash> fuses;
     for (size_t g = 1; g + 1 < groups.size(); ++g) {
         if (claimed[g - 1] || !is_run(g) || !single(g - 1) || !single(g + 1)) continue;
         const Item &A = items[groups[g - 1].first], &R = items[groups[g].first], &B = items[groups[g + 1].first];
@@ -279,36 +350,42 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             k[c] = std::fabs(s) <= mag * 0x1p-46 ? 0.0 : s;
         }
         fkey[g] = key_of(k, A.dt + R.dt * n + B.dt);
-        cand[g] = claimed[g - 1] = claimed[g + 1] = 1;
-        use(fuses, fkey[g], 1, (int64_t)groups[g].first);
+        claimed[g - 1] = claimed[g + 1] = 1;
+        fuses.add(fkey[g], 1, (int64_t)groups[g].first);
     }
+    auto recurring = [&](size_t g) {
+        auto f = fkey.find(g);
+        return f != fkey.end() && fuses.count(f->second) >= 2;
+    };
     for (size_t g = 0; g < groups.size(); ++g) {
         if (!is_run(g)) continue;
-        if (cand[g] && fuses[fkey[g]].first >= 2)
-            use(puses, fkey[g], 1, (int64_t)groups[g].first);
+        if (recurring(g))
+            puses.add(fkey[g], 1, (int64_t)groups[g].first);
         else
-            use(puses, anchor_key(items[groups[g].first], groups[g].n), 1, (int64_t)groups[g].first);
+            puses.add(anchor_key(items[groups[g].first], groups[g].n), 1, (int64_t)groups[g].first);
     }
-    auto pmap = pick_classes<Key>(puses, MAX_PCLS);
-    auto e1map = pick_classes<uint64_t>(e1uses, MAX_E1CLS);
+    auto pmap = pick_classes<Key>(puses.m, MAX_PCLS);
+    auto e1map = pick_classes<uint64_t>(e1uses.m, MAX_E1CLS);
     // fused triples: A goes into the run op (role 1), B is dropped (role 2)
     std::vector<char> fused(groups.size(), 0), role(groups.size(), 0);
-    for (size_t g = 1; g + 1 < groups.size(); ++g) {
+    for (auto &fk : fkey) {
+        const size_t g = fk.first;
         const Item &R = items[groups[g].first];
-        if (cand[g] && fuses[fkey[g]].first >= 2 && pmap.count(fkey[g]) && pmap.count(key_of(R.k, R.dt))) {
+        if (recurring(g) && pmap.count(fk.second) && pmap.count(key_of(R.k, R.dt))) {
             fused[g] = 1;
             role[g - 1] = 1;
             role[g + 1] = 2;
         }
     }
     // E2 classes: intervals of the precessions that stay inline
+    ClassOf<Key> pclass(pmap);
     for (size_t g = 0; g < groups.size(); ++g) {
         const Item &it = items[groups[g].first];
         if ((it.kind == Item::PREC || it.kind == Item::SAMPLE) && !is_zero(it.k, it.dt) && it.dt > 0.0 &&
-            !pmap.count(key_of(it.k, it.dt)) && role[g] != 2)
-            use(e2uses, bits(it.dt), groups[g].n, (int64_t)groups[g].first);
+            pclass(key_of(it.k, it.dt)) < 0 && role[g] != 2)
+            e2uses.add(bits(it.dt), groups[g].n, (int64_t)groups[g].first);
     }
-    auto e2map = pick_classes<uint64_t>(e2uses, MAX_E2CLS);
+    auto e2map = pick_classes<uint64_t>(e2uses.m, MAX_E2CLS);
 
     out.n_pcls = (int)pmap.size();
     out.n_e1 = (int)e1map.size();
@@ -359,15 +436,16 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         out.demod[2 * (size_t)jj] = c;
         out.demod[2 * (size_t)jj + 1] = -sn;
     };
+    ClassOf<uint64_t> e1class(e1map);
     auto set_e1 = [&](OpF32 &a, OpF64 &b, double t) {
         if (t > 0.0) {
-            auto it = e1map.find(bits(t));
-            if (it != e1map.end()) {
+            const int c = e1class(bits(t));
+            if (c >= 0) {
                 both(a, b, F_E1CLS);
-                a.ecls = b.ecls = (int16_t)it->second;
-                if (e1cache != it->second) {
+                a.ecls = b.ecls = (int16_t)c;
+                if (e1cache != c) {
                     both(a, b, F_E1LOAD);
-                    e1cache = it->second;
+                    e1cache = c;
                 }
             } else {
                 both(a, b, F_E1INL);
@@ -488,9 +566,9 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             if (g + 1 < groups.size()) {
                 const Item &nx = items[groups[g + 1].first];
                 if (nx.kind == Item::PREC) {
-                    auto pc = pmap.find(key_of(nx.k, nx.dt));
-                    if (pc != pmap.end()) {
-                        use_pcls(a, b, pc->second);
+                    const int pc = pclass(key_of(nx.k, nx.dt));
+                    if (pc >= 0) {
+                        use_pcls(a, b, pc);
                         ++g;
                     }
                 }
@@ -504,9 +582,9 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             if (role[g]) break;  // inside a rewound readout: emitted with (A) or absorbed by (B) the run
             OpF32 a = new32(OP_PREC);
             OpF64 b = new64(OP_PREC);
-            auto pc = pmap.find(key_of(it.k, it.dt));
-            if (pc != pmap.end())
-                use_pcls(a, b, pc->second);
+            const int pc = pclass(key_of(it.k, it.dt));
+            if (pc >= 0)
+                use_pcls(a, b, pc);
             else
                 set_inline_prec(a, b, it);
             push(a, b);
@@ -526,17 +604,17 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
                 push(a, b);
                 break;
             }
-            auto pc = pmap.find(key_of(it.k, it.dt));
-            if (pc != pmap.end() && cnt > 1) {
+            const int pc = pclass(key_of(it.k, it.dt));
+            if (pc >= 0 && cnt > 1) {
                 OpF32 a = new32(OP_RUN);
                 OpF64 b = new64(OP_RUN);
-                use_pcls(a, b, pc->second);
+                use_pcls(a, b, pc);
                 a.n = b.n = (int32_t)cnt;
                 a.adc0 = b.adc0 = (int32_t)it.j;
                 if (fused[g]) {  // A first, then the samples; the anchor covers A, the run and B
                     set_inline_prec(a, b, items[groups[g - 1].first]);
                     both(a, b, F_ANCHOR);
-                    a.acls = b.acls = (int16_t)pmap.at(fkey[g]);
+                    a.acls = b.acls = (int16_t)pmap.at(fkey.at(g));
                 } else if (cnt >= 4) {
                     auto an = pmap.find(anchor_key(it, cnt));
                     if (an != pmap.end()) {
@@ -550,8 +628,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
                     const Item &s = items[groups[g].first + (size_t)q];
                     OpF32 a = new32(OP_PREC);
                     OpF64 b = new64(OP_PREC);
-                    if (pc != pmap.end())
-                        use_pcls(a, b, pc->second);
+                    if (pc >= 0)
+                        use_pcls(a, b, pc);
                     else
                         set_inline_prec(a, b, s);
                     both(a, b, F_ADC);
