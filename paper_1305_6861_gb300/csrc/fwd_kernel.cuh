@@ -25,6 +25,7 @@
 
 #include "../../include/mrsim.h"
 #include "internal.h"
+#include "packed.cuh"
 
 namespace mrsim {
 namespace dev {
@@ -81,81 +82,6 @@ constexpr int WIN_STRIDE = SAMPLE_WINDOW_F32 + 16;  // float32: block-wide windo
 __device__ __forceinline__ void red_shared_add(float *p, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(su32(p)), "f"(v) : "memory");
 }
-
-// ---- packed float32 pairs -------------------------------------------------------------------
-// sm_100-class SMs execute two float32 lanes per instruction (fma/mul/add/sub .rn.f32x2 on a
-// 64-bit register pair).  A thread with K >= 2 float32 spins keeps each quantity as K/2 pairs,
-// which halves the instructions issued for rotations, relaxations and spin sums; every lane is
-// rounded exactly like the scalar operation.
-struct f2 {
-    unsigned long long r;
-};
-__device__ __forceinline__ f2 pk2(float a, float b) {
-    f2 o;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(a), "f"(b));
-    return o;
-}
-__device__ __forceinline__ void unpk2(f2 a, float &x, float &y) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.r));
-}
-__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
-    return d;
-}
-__device__ __forceinline__ f2 vmul(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
-    return d;
-}
-__device__ __forceinline__ f2 vadd(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
-    return d;
-}
-__device__ __forceinline__ f2 vsub(f2 a, f2 b) {
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
-    return d;
-}
-// sign flip of both lanes on the integer pipe (the FMA pipe is the bound)
-__device__ __forceinline__ f2 vneg(f2 a) {
-    f2 o;
-    asm("xor.b64 %0, %1, 0x8000000080000000;" : "=l"(o.r) : "l"(a.r));
-    return o;
-}
-__device__ __forceinline__ float hsum(f2 a) {
-    float x, y;
-    unpk2(a, x, y);
-    return x + y;
-}
-__device__ __forceinline__ float lane_of(f2 a, int h) {
-    float x, y;
-    unpk2(a, x, y);
-    return h ? y : x;
-}
-__device__ __forceinline__ void splat(f2 &o, float x) { o = pk2(x, x); }
-__device__ __forceinline__ void set_lanes(f2 &o, const float (&x)[2]) { o = pk2(x[0], x[1]); }
-
-// the same operations on one scalar lane (float64, and float32 with one spin per thread)
-__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
-template <typename T>
-__device__ __forceinline__ T vmul(T a, T b) { return a * b; }
-template <typename T>
-__device__ __forceinline__ T vadd(T a, T b) { return a + b; }
-template <typename T>
-__device__ __forceinline__ T vsub(T a, T b) { return a - b; }
-template <typename T>
-__device__ __forceinline__ T vneg(T a) { return -a; }
-template <typename T>
-__device__ __forceinline__ T hsum(T a) { return a; }
-template <typename T>
-__device__ __forceinline__ T lane_of(T a, int) { return a; }
-template <typename T>
-__device__ __forceinline__ void splat(T &o, T x) { o = x; }
-template <typename T>
-__device__ __forceinline__ void set_lanes(T &o, const T (&x)[1]) { o = x[0]; }
 
 // Rounding constant 1.5·2^23: for |p| < 2^22, (p + c) − c is p rounded to the nearest integer
 // (round-to-nearest-even), so p − ((p + c) − c) is the exact fractional part in [−1/2, 1/2].

@@ -10,17 +10,19 @@
 // b_-i = conj(b_i), so M_z = Z_0 stays real.
 //
 // GPU layout: one warp per ensemble.  Lane l holds the orders i = l + 32·m (m < M) as a_i,
-// a_-i and b_i: the pulse is lane-local (order i couples with -i only); a one-order shift moves
-// a_i one lane up (and a_-i one lane down), with the wrap between slots m and the exchange
-// a_0 <-> a_∓1 done by shuffles.  Every lane computes the step's scalars (sin/cos of the scaled
-// flip, E1, E2, off-resonance phasor) for one step of every 32 and the warp broadcasts them; no
-// warp waits on another.
+// a_-i and b_i: the pulse is lane-local (order i couples with -i only) and runs on slot pairs
+// with f32x2 arithmetic in float32; a one-order shift rotates every slot by one lane (one
+// shuffle per slot and quantity) and lane 0 / lane 31 take their value from the neighbouring
+// slot.  Every lane computes the coefficients of one step of every 32 (sin/cos of the scaled
+// flip, E1, E2, off-resonance phasor) into shared memory, replicated for the packed arithmetic,
+// and the warp reads each step's set with broadcast loads; no warp waits on another.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <type_traits>
 
 #include "internal.h"
+#include "packed.cuh"
 
 namespace mrsim {
 namespace {
@@ -36,26 +38,6 @@ template <typename R>
 __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
     return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
-template <typename R>
-__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) {
-    return {a.re + b.re, a.im + b.im};
-}
-template <typename R>
-__device__ __forceinline__ Cx<R> cconj(Cx<R> a) {
-    return {a.re, -a.im};
-}
-template <typename R>
-__device__ __forceinline__ Cx<R> shfl(Cx<R> v, int src) {
-    return {__shfl_sync(FULLW, v.re, src), __shfl_sync(FULLW, v.im, src)};
-}
-template <typename R>
-__device__ __forceinline__ Cx<R> shfl_up1(Cx<R> v) {
-    return {__shfl_up_sync(FULLW, v.re, 1), __shfl_up_sync(FULLW, v.im, 1)};
-}
-template <typename R>
-__device__ __forceinline__ Cx<R> shfl_down1(Cx<R> v) {
-    return {__shfl_down_sync(FULLW, v.re, 1), __shfl_down_sync(FULLW, v.im, 1)};
-}
 
 __device__ __forceinline__ void sc(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sc(double x, double *s, double *c) { sincos(x, s, c); }
@@ -66,176 +48,266 @@ __device__ __forceinline__ double em1(double x) { return expm1(x); }
 __device__ __forceinline__ float ex(float x) { return expf(x); }
 __device__ __forceinline__ double ex(double x) { return exp(x); }
 
+// Coefficient values: float32 with M >= 2 order slots per lane works on slot pairs (2p, 2p + 1)
+// with f32x2 arithmetic, so each coefficient is replicated into a pair; otherwise one slot per
+// operation.
+template <typename R, int M>
+struct KtPack {
+    using P = R;
+    static constexpr int L = 1, NP = M;
+};
+template <int M>
+struct KtPack<float, M> {
+    using P = typename std::conditional<(M >= 2), dev::f2, float>::type;
+    static constexpr int L = M >= 2 ? 2 : 1, NP = M >= 2 ? M / 2 : 1;
+};
+
+__device__ __forceinline__ float lo(float v) { return v; }
+__device__ __forceinline__ double lo(double v) { return v; }
+__device__ __forceinline__ float lo(dev::f2 v) { return dev::lane_of(v, 0); }
+
+// The per-step coefficients of Eqs. 4.2 (T'_HF entries and their negatives), 4.15/4.16 and the
+// ensemble's precession, each replicated to a register value P.  Lane k of a warp computes the
+// set of step base + k of a 32-step chunk into shared memory; every lane then reads each step's
+// set with broadcast loads.
+template <typename P>
+struct alignas(16) Coef {
+    P c2, ca, t01r, t01i, nt01r, t02r, t02i, nt02r, nt02i, t20r, t20i, nt20r, nt20i;  // pulse
+    P e1m1, wr, wi, nwi;  // E1 - 1; E2·exp(-j2πΔfτ) and its negated imaginary part
+    int flags;            // shift + 128 (8 bits) | sample << 8 | pulse << 9
+};
+
+// The populations of one ensemble in a warp: one register per order slot and quantity (the
+// shifts move single slots between lanes); the pulse and the relaxation pack slot pairs.
 template <typename R, int M>
 struct Ensemble {
-    Cx<R> ap[M], an[M], bz[M];  // a_i, a_-i, b_i for i = lane + 32 m
+    using KP = KtPack<R, M>;
+    using P = typename KP::P;
+    static constexpr int L = KP::L, NP = KP::NP;
+    R apr[M], api[M], anr[M], ani[M], bzr[M], bzi[M];  // a_i, a_-i, b_i for i = lane + 32·slot
     int lane, K;
+    bool full;  // K = 32·M - 1: every stored order exists
 
-    __device__ __forceinline__ bool has(int m) const { return lane + 32 * m <= K; }
-
-    // Eq. 4.14 with T'_HF of Eq. 4.2: c2 = cos²(α/2), ca = cos α, t01 = sin²(α/2) e^{2jφ},
-    // t02 = sin α e^{j(φ+π/2)}, t20 = (sin α / 2) e^{-j(φ-π/2)}; the other entries are conjugates
-    __device__ __forceinline__ void pulse(R c2, R ca, Cx<R> t01, Cx<R> t02, Cx<R> t20) {
-        const Cx<R> t10 = cconj(t01), t12 = cconj(t02), t21 = cconj(t20);
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const Cx<R> x = ap[m], y = cconj(an[m]), z = bz[m];
-            const Cx<R> nx = cadd(cadd(Cx<R>{c2 * x.re, c2 * x.im}, cmul(t01, y)), cmul(t02, z));
-            const Cx<R> ny = cadd(cadd(cmul(t10, x), Cx<R>{c2 * y.re, c2 * y.im}), cmul(t12, z));
-            const Cx<R> nz = cadd(cadd(cmul(t20, x), cmul(t21, y)), Cx<R>{ca * z.re, ca * z.im});
-            ap[m] = nx;
-            an[m] = cconj(ny);
-            bz[m] = nz;
-        }
-        if (lane == 0) an[0] = ap[0];  // order 0: a_-0 is a_0
+    __device__ __forceinline__ P ld(const R (&v)[M], int p) const {
+        if constexpr (L == 2)
+            return dev::pk2(v[2 * p], v[2 * p + 1]);
+        else
+            return v[p];
+    }
+    __device__ __forceinline__ void st(R (&v)[M], int p, P x) {
+        if constexpr (L == 2)
+            dev::unpk2(x, v[2 * p], v[2 * p + 1]);
+        else
+            v[p] = x;
     }
 
-    // Eq. 4.17 with q = +1: a_i <- a_{i-1} (i >= 1), a_0 <- a_-1, a_-i <- a_-(i+1)
+    // order 0: a_-0 is a_0 (kept bit-identical)
+    __device__ __forceinline__ void tie_zero() {
+        if (lane == 0) {
+            anr[0] = apr[0];
+            ani[0] = api[0];
+        }
+    }
+
+    // Eq. 4.14 with T'_HF of Eq. 4.2 acting on (a_i, conj(a_-i), b_i), written out in real
+    // arithmetic for (a_i, a_-i, b_i)
+    __device__ __forceinline__ void pulse(const Coef<P> &c) {
+        using namespace dev;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const P xr = ld(apr, p), xi = ld(api, p), ar = ld(anr, p), ai = ld(ani, p), zr = ld(bzr, p),
+                    zi = ld(bzi, p);
+            st(apr, p, vfma(c.nt02i, zi, vfma(c.t02r, zr, vfma(c.t01i, ai, vfma(c.t01r, ar, vmul(c.c2, xr))))));
+            st(api, p, vfma(c.t02i, zr, vfma(c.t02r, zi, vfma(c.t01i, ar, vfma(c.nt01r, ai, vmul(c.c2, xi))))));
+            st(anr, p, vfma(c.t02i, zi, vfma(c.t02r, zr, vfma(c.c2, ar, vfma(c.t01i, xi, vmul(c.t01r, xr))))));
+            st(ani, p, vfma(c.t02i, zr, vfma(c.nt02r, zi, vfma(c.c2, ai, vfma(c.t01i, xr, vmul(c.nt01r, xi))))));
+            st(bzr, p, vfma(c.ca, zr, vfma(c.nt20i, ai, vfma(c.t20r, ar, vfma(c.nt20i, xi, vmul(c.t20r, xr))))));
+            st(bzi, p, vfma(c.ca, zi, vfma(c.nt20i, ar, vfma(c.nt20r, ai, vfma(c.t20i, xr, vmul(c.t20r, xi))))));
+        }
+        tie_zero();
+    }
+
+    // Eq. 4.17 with q = +1: a_i <- a_{i-1} (i >= 1), a_0 <- a_-1, a_-i <- a_-(i+1).  Each slot is
+    // rotated by one lane; lane 0 (lane 31) takes the value the neighbouring slot's rotation
+    // brought it, i.e. the other end of that slot.
     __device__ __forceinline__ void shift_up() {
-        const Cx<R> a_m1 = shfl(an[0], 1);  // a_-1 from lane 1
-        Cx<R> nap[M], nan[M];
+        const R a_m1r = __shfl_sync(FULLW, anr[0], 1), a_m1i = __shfl_sync(FULLW, ani[0], 1);
+        const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
+        R rr[M], ri[M], sr[M], si[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            Cx<R> up = shfl_up1(ap[m]);                               // a_{i-1} within the slot
-            const Cx<R> wrap = shfl(m > 0 ? ap[m - 1] : ap[0], 31);   // a_{32m-1} from lane 31
-            if (lane == 0) up = m > 0 ? wrap : a_m1;
-            nap[m] = has(m) ? up : Cx<R>{0, 0};                       // orders beyond K are dropped
-            Cx<R> dn = shfl_down1(an[m]);                             // a_-(i+1) within the slot
-            const Cx<R> wrap2 = shfl(m + 1 < M ? an[m + 1] : an[0], 0);
-            if (lane == 31) dn = m + 1 < M ? wrap2 : Cx<R>{0, 0};
-            nan[m] = has(m) ? dn : Cx<R>{0, 0};
+        for (int s = 0; s < M; ++s) {
+            rr[s] = __shfl_sync(FULLW, apr[s], up);
+            ri[s] = __shfl_sync(FULLW, api[s], up);
+            sr[s] = __shfl_sync(FULLW, anr[s], dn);
+            si[s] = __shfl_sync(FULLW, ani[s], dn);
         }
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            ap[m] = nap[m];
-            an[m] = nan[m];
+        for (int s = 0; s < M; ++s) {  // order 32s <- 32s - 1; order -(32s + 31) <- -(32s + 32)
+            apr[s] = lane == 0 ? (s > 0 ? rr[s - 1] : a_m1r) : rr[s];
+            api[s] = lane == 0 ? (s > 0 ? ri[s - 1] : a_m1i) : ri[s];
+            anr[s] = lane == 31 ? (s + 1 < M ? sr[s + 1] : (R)0) : sr[s];
+            ani[s] = lane == 31 ? (s + 1 < M ? si[s + 1] : (R)0) : si[s];
         }
-        if (lane == 0) an[0] = ap[0];
+        if (!full) drop(apr, api);
+        tie_zero();
     }
 
     // Eq. 4.17 with q = -1: a_i <- a_{i+1} (i >= 0), a_-1 <- a_0, a_-i <- a_-(i-1)
     __device__ __forceinline__ void shift_down() {
-        const Cx<R> a_0 = shfl(ap[0], 0);
-        Cx<R> nap[M], nan[M];
+        const R a0r = __shfl_sync(FULLW, apr[0], 0), a0i = __shfl_sync(FULLW, api[0], 0);
+        const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
+        R rr[M], ri[M], sr[M], si[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            Cx<R> dn = shfl_down1(ap[m]);
-            const Cx<R> wrap = shfl(m + 1 < M ? ap[m + 1] : ap[0], 0);
-            if (lane == 31) dn = m + 1 < M ? wrap : Cx<R>{0, 0};
-            nap[m] = has(m) ? dn : Cx<R>{0, 0};
-            Cx<R> up = shfl_up1(an[m]);
-            const Cx<R> wrap2 = shfl(m > 0 ? an[m - 1] : an[0], 31);
-            if (lane == 0) up = m > 0 ? wrap2 : an[0];
-            if (lane == 1 && m == 0) up = a_0;
-            nan[m] = has(m) ? up : Cx<R>{0, 0};
+        for (int s = 0; s < M; ++s) {
+            rr[s] = __shfl_sync(FULLW, apr[s], dn);
+            ri[s] = __shfl_sync(FULLW, api[s], dn);
+            sr[s] = __shfl_sync(FULLW, anr[s], up);
+            si[s] = __shfl_sync(FULLW, ani[s], up);
         }
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            ap[m] = nap[m];
-            an[m] = nan[m];
+        for (int s = 0; s < M; ++s) {  // order 32s + 31 <- 32s + 32; order -32s <- -(32s - 1)
+            apr[s] = lane == 31 ? (s + 1 < M ? rr[s + 1] : (R)0) : rr[s];
+            api[s] = lane == 31 ? (s + 1 < M ? ri[s + 1] : (R)0) : ri[s];
+            R nr = (lane == 0 && s > 0) ? sr[s - 1] : sr[s];
+            R ni = (lane == 0 && s > 0) ? si[s - 1] : si[s];
+            if (s == 0) {  // a_-1 <- a_0
+                nr = lane == 1 ? a0r : nr;
+                ni = lane == 1 ? a0i : ni;
+            }
+            anr[s] = nr;
+            ani[s] = ni;
         }
-        if (lane == 0) an[0] = ap[0];
+        if (!full) drop(anr, ani);
+        tie_zero();  // a_0 <- a_1, and a_-0 with it
+    }
+
+    // populations pushed past order K are dropped (only needed when the top slot is partial)
+    __device__ __forceinline__ void drop(R (&re)[M], R (&im)[M]) {
+#pragma unroll
+        for (int s = 0; s < M; ++s)
+            if (lane + 32 * s > K) {
+                re[s] = (R)0;
+                im[s] = (R)0;
+            }
     }
 
     // Eqs. 4.15, 4.16 and the ensemble's precession: a *= E2·exp(-jθ), b *= E1, b_0 += 1 - E1
-    __device__ __forceinline__ void relax(R e1m1, Cx<R> w) {
+    __device__ __forceinline__ void relax(const Coef<P> &c) {
+        using namespace dev;
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            ap[m] = cmul(ap[m], w);
-            an[m] = cmul(an[m], w);
-            bz[m] = {bz[m].re + e1m1 * bz[m].re, bz[m].im + e1m1 * bz[m].im};
+        for (int p = 0; p < NP; ++p) {
+            const P xr = ld(apr, p), xi = ld(api, p), yr = ld(anr, p), yi = ld(ani, p), br = ld(bzr, p),
+                    bi = ld(bzi, p);
+            st(apr, p, vfma(xi, c.nwi, vmul(xr, c.wr)));
+            st(api, p, vfma(xi, c.wr, vmul(xr, c.wi)));
+            st(anr, p, vfma(yi, c.nwi, vmul(yr, c.wr)));
+            st(ani, p, vfma(yi, c.wr, vmul(yr, c.wi)));
+            st(bzr, p, vfma(br, c.e1m1, br));
+            st(bzi, p, vfma(bi, c.e1m1, bi));
         }
-        if (lane == 0) bz[0].re -= e1m1;  // b_0 + (E1 - 1)(b_0 - 1)
+        if (lane == 0) bzr[0] -= lo(c.e1m1);  // b_0 + (E1 - 1)(b_0 - 1)
     }
 };
 
-// The per-step scalars of one ensemble: pulse entries, relaxation, demodulation, flags.  Lane l
-// of a warp computes them for step base + l of a 32-step chunk; the warp then walks the chunk
-// and broadcasts each step's values with shuffles (the transcendentals are spread over the lanes).
-template <typename R>
-struct StepScalars {
-    R c2, ca, t01r, t01i, t02r, t02i, t20r, t20i;  // pulse (Eq. 4.2)
-    R e1m1, wr, wi;                                // E1 - 1; E2·exp(-j2πΔfτ)
-    R cadc, sadc;                                  // demodulation
-    int flags;                                     // shift + 128 (8 bits) | sample << 8 | pulse << 9
-};
+template <typename P, typename R>
+__device__ __forceinline__ P rep(R x) {
+    P o;
+    dev::splat(o, x);
+    return o;
+}
 
-template <typename R, typename StepT>
-__device__ __forceinline__ StepScalars<R> step_scalars(const StepT &s, R b1, R r1, R r2, R df) {
-    StepScalars<R> o;
+// The coefficient set of one step for one ensemble (Eq. 4.2 entries from the B1-scaled flip)
+template <typename P, typename R, typename StepT>
+__device__ __forceinline__ void step_coef(Coef<P> &o, const StepT &s, R b1, R r1, R r2, R df) {
     const R alpha = b1 * (R)s.alpha;
     R sh, ch;
     sc((R)0.5 * alpha, &sh, &ch);
     const R cp = (R)s.cphi, sp = (R)s.sphi, s2 = sh * sh, sa = (R)2 * sh * ch, hs = sh * ch;
-    o.c2 = ch * ch;
-    o.ca = o.c2 - s2;
-    o.t01r = s2 * (R)s.c2phi;
-    o.t01i = s2 * (R)s.s2phi;
-    o.t02r = -sa * sp;  // j sin α e^{jφ}
-    o.t02i = sa * cp;
-    o.t20r = hs * sp;  // j (sin α / 2) e^{-jφ}
-    o.t20i = hs * cp;
+    const R c2 = ch * ch;
+    const R t01r = s2 * (R)s.c2phi, t01i = s2 * (R)s.s2phi;
+    const R t02r = -sa * sp, t02i = sa * cp;  // j sin α e^{jφ}
+    const R t20r = hs * sp, t20i = hs * cp;   // j (sin α / 2) e^{-jφ}
+    o.c2 = rep<P>(c2);
+    o.ca = rep<P>(c2 - s2);
+    o.t01r = rep<P>(t01r);
+    o.t01i = rep<P>(t01i);
+    o.nt01r = rep<P>(-t01r);
+    o.t02r = rep<P>(t02r);
+    o.t02i = rep<P>(t02i);
+    o.nt02r = rep<P>(-t02r);
+    o.nt02i = rep<P>(-t02i);
+    o.t20r = rep<P>(t20r);
+    o.t20i = rep<P>(t20i);
+    o.nt20r = rep<P>(-t20r);
+    o.nt20i = rep<P>(-t20i);
     const R tau = (R)s.tau;
-    o.e1m1 = em1(-tau * r1);
+    o.e1m1 = rep<P>(em1(-tau * r1));
     const R e2 = ex(-tau * r2);
     R sn, cs;
     scpi((R)2 * df * tau, &sn, &cs);
-    o.wr = e2 * cs;
-    o.wi = -e2 * sn;
-    o.cadc = (R)s.cadc;
-    o.sadc = (R)s.sadc;
+    o.wr = rep<P>(e2 * cs);
+    o.wi = rep<P>(-e2 * sn);
+    o.nwi = rep<P>(e2 * sn);
     o.flags = (s.shift + 128) | (s.sample << 8) | ((s.alpha != 0) << 9);
-    return o;
 }
 
+constexpr int KT_WARPS = 4;  // warps (ensembles) per block
+
 template <typename R, int M, typename StepT>
-__global__ void __launch_bounds__(128) kt_kernel(const KtArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t set = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (set >= a.n_sets) return;  // uniform over the warp
+__global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
+    using E = Ensemble<R, M>;
+    using P = typename E::P;
+    __shared__ Coef<P> coef[KT_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t set = (int64_t)blockIdx.x * KT_WARPS + w;
+    if (set >= a.n_sets) return;  // uniform over the warp; no block-wide barrier follows
     const StepT *steps = reinterpret_cast<const StepT *>(a.steps);
     const double t1 = a.t1[set], t2 = a.t2[set];
     const R r1 = isinf(t1) ? (R)0 : (R)(1.0 / t1), r2 = isinf(t2) ? (R)0 : (R)(1.0 / t2);
     const R b1 = a.b1 ? (R)a.b1[set] : (R)1;
     const R df = a.df ? (R)a.df[set] : (R)0;
-    Ensemble<R, M> e;
+    E e;
     e.lane = lane;
     e.K = a.max_order;
+    e.full = a.max_order == 32 * M - 1;
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-        e.ap[m] = {0, 0};
-        e.an[m] = {0, 0};
-        e.bz[m] = {0, 0};
-    }
-    if (lane == 0) e.bz[0].re = (R)1;
+    for (int s = 0; s < M; ++s) e.apr[s] = e.api[s] = e.anr[s] = e.ani[s] = e.bzr[s] = e.bzi[s] = (R)0;
+    if (lane == 0) e.bzr[0] = (R)1;
     double *out = a.signal + 2 * set * a.n_samples;
+    Coef<P> *cw = coef[w];
     int64_t j = 0;  // samples written before this chunk
     for (int64_t base = 0; base < a.n_steps; base += 32) {
         const int cnt = (int)min((int64_t)32, a.n_steps - base);
-        StepScalars<R> my{};
-        if (lane < cnt) my = step_scalars<R>(steps[base + lane], b1, r1, r2, df);
+        __syncwarp();  // the previous chunk's reads are done
+        R cadc = 0, sadc = 0;
+        int myflags = 0;
+        if (lane < cnt) {
+            const StepT st = steps[base + lane];
+            step_coef<P, R>(cw[lane], st, b1, r1, r2, df);
+            cadc = (R)st.cadc;
+            sadc = (R)st.sadc;
+            myflags = cw[lane].flags;
+        }
+        __syncwarp();
         // lane k keeps the sample of step base + k and stores it after the chunk (one conversion
         // to float64 per lane instead of one per sample for the whole warp)
-        const unsigned smask = __ballot_sync(FULLW, lane < cnt && (my.flags & 256));
+        const unsigned smask = __ballot_sync(FULLW, lane < cnt && (myflags & 256));
         Cx<R> mine{0, 0};
         for (int k = 0; k < cnt; ++k) {
-            const int fl = __shfl_sync(FULLW, my.flags, k);
-            if (fl & 512)
-                e.pulse(__shfl_sync(FULLW, my.c2, k), __shfl_sync(FULLW, my.ca, k),
-                        Cx<R>{__shfl_sync(FULLW, my.t01r, k), __shfl_sync(FULLW, my.t01i, k)},
-                        Cx<R>{__shfl_sync(FULLW, my.t02r, k), __shfl_sync(FULLW, my.t02i, k)},
-                        Cx<R>{__shfl_sync(FULLW, my.t20r, k), __shfl_sync(FULLW, my.t20i, k)});
+            const Coef<P> &c = cw[k];
+            const int fl = c.flags;
+            if (fl & 512) e.pulse(c);
             const int q = (fl & 255) - 128;
             for (int i = 0; i < q; ++i) e.shift_up();
             for (int i = 0; i > q; --i) e.shift_down();
-            e.relax(__shfl_sync(FULLW, my.e1m1, k), Cx<R>{__shfl_sync(FULLW, my.wr, k), __shfl_sync(FULLW, my.wi, k)});
+            e.relax(c);
             if (fl & 256) {
-                const Cx<R> a0 = shfl(e.ap[0], 0);
-                if (lane == k) mine = a0;
+                const R sr = __shfl_sync(FULLW, e.apr[0], 0), si = __shfl_sync(FULLW, e.api[0], 0);
+                if (lane == k) mine = Cx<R>{sr, si};
             }
         }
         if (smask & (1u << lane)) {  // demodulated with this lane's own step
-            const Cx<R> v = cmul(mine, Cx<R>{my.cadc, -my.sadc});
+            const Cx<R> v = cmul(mine, Cx<R>{cadc, -sadc});
             const int64_t jj = j + __popc(smask & ((1u << lane) - 1u));
             out[2 * jj] = (double)v.re;
             out[2 * jj + 1] = (double)v.im;
@@ -246,8 +318,8 @@ __global__ void __launch_bounds__(128) kt_kernel(const KtArgs a) {
 
 template <typename R, typename StepT>
 int launch_kt_t(const KtArgs &a, void *stream) {
-    const int threads = 128;
-    const int64_t blocks = (a.n_sets + 3) / 4;
+    const int threads = 32 * KT_WARPS;
+    const int64_t blocks = (a.n_sets + KT_WARPS - 1) / KT_WARPS;
     if (blocks <= 0) return 0;
     if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
     const int M = (a.max_order + 32) / 32;  // slots per lane
