@@ -29,7 +29,8 @@
  * Ownership: create functions copy their inputs; the caller keeps ownership of
  * every buffer it passes.  Handles are owned by the caller and released with
  * the matching destroy function (NULL is accepted).  A context must outlive the
- * handles created on it.  Calls on one context are not thread-safe.
+ * handles created on it.  Calls on one context are not thread-safe; mrsim_compile
+ * uses no context and may run on any thread at any time.
  *
  * Pointers marked "host or device" may be either: the library asks the CUDA
  * runtime what a pointer is and copies host data itself.
@@ -121,6 +122,27 @@ int64_t mrsim_phantom_num_spins(const mrsim_phantom *p);
 void mrsim_phantom_destroy(mrsim_phantom *p);
 
 /* ---- sequence: elementary sequences (§4.1) compiled once in float64 ------------------- */
+
+/* A compiled program on the host: the compilation step of mrsim_sequence_load on its own.  It
+ * needs no context and no GPU, so a caller can compile the next request on another thread while
+ * a context simulates the current one.  Different threads may compile at the same time. */
+typedef struct mrsim_compiled mrsim_compiled;
+/* Validates and compiles n_events events (host memory) with optional snapshots (see
+ * mrsim_sequence_load_snapshots); same validation and error codes as mrsim_sequence_load.  On
+ * failure *out = NULL and mrsim_compile_last_error() says why. */
+mrsim_status mrsim_compile(int64_t n_events, const mrsim_event *events, double gamma_hz_per_t, int64_t n_snap,
+                           const int64_t *snap_after, mrsim_compiled **out);
+/* Message of the calling thread's last failed mrsim_compile ("" if none); valid until its next
+ * mrsim_compile call. */
+const char *mrsim_compile_last_error(void);
+int64_t mrsim_compiled_num_adc(const mrsim_compiled *c);
+/* Bytes mrsim_sequence_create copies to the device for this program (operations, class tables,
+ * demodulation factors, sub-pulse tables, in both precisions). */
+int64_t mrsim_compiled_upload_bytes(const mrsim_compiled *c);
+void mrsim_compiled_destroy(mrsim_compiled *c);
+/* Uploads a compiled program to ctx's device.  The sequence shares the program's host tables, so
+ * c may be destroyed (or uploaded again, to any context) right after the call. */
+mrsim_status mrsim_sequence_create(mrsim_ctx *ctx, const mrsim_compiled *c, mrsim_sequence **out);
 
 /* Validates and compiles n_events events (host memory) with γ/2π = gamma_hz_per_t [Hz/T]:
  * gradient moments γ·G·Δt, RF rotation matrices (Eq. 3.19), relaxation intervals and the

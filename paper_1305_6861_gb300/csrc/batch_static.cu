@@ -75,7 +75,7 @@ extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, c
         if (!p || !q || p->ctx != ctx || q->ctx != ctx)
             return bad(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": NULL handle or another context");
         cudaPointerAttributes at;
-        if (q->host.n_adc > 0 && (!signals_out[i] || cudaPointerGetAttributes(&at, signals_out[i]) != cudaSuccess ||
+        if (q->prog->host.n_adc > 0 && (!signals_out[i] || cudaPointerGetAttributes(&at, signals_out[i]) != cudaSuccess ||
                                   (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged))) {
             cudaGetLastError();
             return bad(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": signal buffer must be device memory");

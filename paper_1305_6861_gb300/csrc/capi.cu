@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -105,7 +107,7 @@ mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStr
 }
 
 TuneKey tune_key(mrsim_precision prec, const mrsim_phantom *ph, const mrsim_sequence *seq) {
-    const Compiled &c = seq->host;
+    const Compiled &c = seq->prog->host;
     return TuneKey{(int64_t)prec, ph->n, (int64_t)c.ops32.size(), c.n_pcls, c.n_e1, c.n_e2,
                    c.n_adc * 4096 + (int64_t)c.train.size()};
 }
@@ -234,59 +236,121 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     return mrsim_sequence_load_snapshots(ctx, n_events, events, gamma, 0, nullptr, out);
 }
 
-int64_t mrsim_sequence_num_snapshots(const mrsim_sequence *s) { return s ? s->host.n_snap : -1; }
+int64_t mrsim_sequence_num_snapshots(const mrsim_sequence *s) { return s ? s->prog->host.n_snap : -1; }
 
-mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
-                                           double gamma, int64_t n_snap, const int64_t *snap_after,
-                                           mrsim_sequence **out) {
+namespace {
+
+thread_local std::string t_compile_err;  // mrsim_compile's message, per calling thread
+
+// Compilation plus the host-side conversions of the upload; no CUDA call.
+mrsim_status compile_host(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
+                          const int64_t *snap_after, std::shared_ptr<HostProgram> &out, std::string &err) {
+    std::shared_ptr<HostProgram> c;
+    try {
+        c = std::make_shared<HostProgram>();
+        int rc = compile_sequence(events, n_events, gamma, c->host, err, n_snap, snap_after);
+        if (rc != MRSIM_OK) return (mrsim_status)rc;
+        c->n_events = n_events;
+        c->demod32.assign(c->host.demod.begin(), c->host.demod.end());
+        c->train32.assign(c->host.train.begin(), c->host.train.end());
+        for (const OpF32 &o : c->host.ops32)  // magnitude bound of the float32 inline phase terms
+            if ((o.kind == OP_PREC || o.kind == OP_RUN) && (o.flags & F_INLINE))
+                for (int a = 0; a < 4; ++a) c->kmax[a] = std::max(c->kmax[a], std::fabs(o.f[2 * a]));
+    } catch (const std::bad_alloc &) {
+        err = "host allocation failed";
+        return MRSIM_ENOMEM;
+    }
+    out = std::move(c);
+    return MRSIM_OK;
+}
+
+}  // namespace
+
+mrsim_status mrsim_compile(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
+                           const int64_t *snap_after, mrsim_compiled **out) {
+    t_compile_err.clear();
+    if (!out) {
+        t_compile_err = "NULL output handle";
+        return MRSIM_EINVAL;
+    }
+    *out = nullptr;
+    if (n_events > 0 && is_device_ptr(events)) {
+        t_compile_err = "events must be in host memory";
+        return MRSIM_EINVAL;
+    }
+    std::shared_ptr<HostProgram> prog;
+    std::string err;
+    mrsim_status rc = compile_host(n_events, events, gamma, n_snap, snap_after, prog, err);
+    if (rc != MRSIM_OK) {
+        t_compile_err = err;
+        return rc;
+    }
+    mrsim_compiled *c = new (std::nothrow) mrsim_compiled();
+    if (!c) {
+        t_compile_err = "host allocation failed";
+        return MRSIM_ENOMEM;
+    }
+    c->prog = std::move(prog);
+    *out = c;
+    return MRSIM_OK;
+}
+
+const char *mrsim_compile_last_error(void) { return t_compile_err.c_str(); }
+
+int64_t mrsim_compiled_num_adc(const mrsim_compiled *c) { return c ? c->prog->host.n_adc : -1; }
+
+int64_t mrsim_compiled_upload_bytes(const mrsim_compiled *c) {
+    if (!c) return -1;
+    const HostProgram &p = *c->prog;
+    return (int64_t)(p.host.ops32.size() * sizeof(OpF32) + p.host.ops64.size() * sizeof(OpF64) +
+                     (p.host.pcls.size() + p.host.e1.size() + p.host.e2.size() + p.host.demod.size() +
+                      p.host.train.size()) * sizeof(double) +
+                     (p.demod32.size() + p.train32.size()) * sizeof(float));
+}
+
+void mrsim_compiled_destroy(mrsim_compiled *c) { delete c; }
+
+mrsim_status mrsim_sequence_create(mrsim_ctx *ctx, const mrsim_compiled *c, mrsim_sequence **out) {
     if (!ctx || !out) return MRSIM_EINVAL;
     *out = nullptr;
-    if (n_events > 0 && is_device_ptr(events)) return fail(ctx, MRSIM_EINVAL, "events must be in host memory");
+    if (!c) return fail(ctx, MRSIM_EINVAL, "NULL compiled program");
     mrsim_sequence *s = new (std::nothrow) mrsim_sequence();
     if (!s) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");
     s->ctx = ctx;
-    s->n_events = n_events;
-    std::string err;
-    int rc = compile_sequence(events, n_events, gamma, s->host, err, n_snap, snap_after);
-    if (rc != MRSIM_OK) {
-        delete s;
-        return fail(ctx, (mrsim_status)rc, err);
-    }
+    s->prog = c->prog;
+    s->n_events = c->prog->n_events;
+    const HostProgram &h = *s->prog;
     cudaSetDevice(ctx->device);
     mrsim_status st = MRSIM_OK;
     auto up = [&](auto **d, const auto &v) {
         if (st == MRSIM_OK) st = upload(ctx, d, v);
     };
-    up((OpF32 **)&s->d_ops32, s->host.ops32);
-    up((OpF64 **)&s->d_ops64, s->host.ops64);
-    up(&s->d_pcls, s->host.pcls);
-    up(&s->d_e1, s->host.e1);
-    up(&s->d_e2, s->host.e2);
-    up(&s->d_demod, s->host.demod);
-    std::vector<float> d32(s->host.demod.begin(), s->host.demod.end());
-    up(&s->d_demod32, d32);
-    std::vector<float> t32(s->host.train.begin(), s->host.train.end());
-    up(&s->d_train32, t32);
-    up(&s->d_train64, s->host.train);
+    up((OpF32 **)&s->d_ops32, h.host.ops32);
+    up((OpF64 **)&s->d_ops64, h.host.ops64);
+    up(&s->d_pcls, h.host.pcls);
+    up(&s->d_e1, h.host.e1);
+    up(&s->d_e2, h.host.e2);
+    up(&s->d_demod, h.host.demod);
+    up(&s->d_demod32, h.demod32);
+    up(&s->d_train32, h.train32);
+    up(&s->d_train64, h.host.train);
     if (st != MRSIM_OK) {
         mrsim_sequence_destroy(s);
         return st;
     }
     Program p{};
-    p.n_ops = (int32_t)s->host.ops32.size();
-    p.n_pcls = s->host.n_pcls;
-    p.n_e1 = s->host.n_e1;
-    p.n_e2 = s->host.n_e2;
+    p.n_ops = (int32_t)h.host.ops32.size();
+    p.n_pcls = h.host.n_pcls;
+    p.n_e1 = h.host.n_e1;
+    p.n_e2 = h.host.n_e2;
     p.pcls = s->d_pcls;
     p.e1 = s->d_e1;
     p.e2 = s->d_e2;
     p.demod = s->d_demod;
     p.demod32 = s->d_demod32;
-    p.n_train = (int32_t)(s->host.train.size() / 2);
-    p.n_adc = s->host.n_adc;
-    for (const OpF32 &o : s->host.ops32)  // magnitude bound of the float32 inline phase terms
-        if ((o.kind == OP_PREC || o.kind == OP_RUN) && (o.flags & F_INLINE))
-            for (int a = 0; a < 4; ++a) p.kmax[a] = std::max(p.kmax[a], std::fabs(o.f[2 * a]));
+    p.n_train = (int32_t)(h.host.train.size() / 2);
+    p.n_adc = h.host.n_adc;
+    for (int a = 0; a < 4; ++a) p.kmax[a] = h.kmax[a];
     s->p32 = p;
     s->p32.ops = s->d_ops32;
     s->p32.train = s->d_train32;
@@ -297,9 +361,24 @@ mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, con
     return MRSIM_OK;
 }
 
-int64_t mrsim_sequence_num_adc(const mrsim_sequence *s) { return s ? s->host.n_adc : -1; }
+mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                           double gamma, int64_t n_snap, const int64_t *snap_after,
+                                           mrsim_sequence **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
+    if (n_events > 0 && is_device_ptr(events)) return fail(ctx, MRSIM_EINVAL, "events must be in host memory");
+    mrsim_compiled c;
+    std::shared_ptr<HostProgram> prog;
+    std::string err;
+    mrsim_status rc = compile_host(n_events, events, gamma, n_snap, snap_after, prog, err);
+    if (rc != MRSIM_OK) return fail(ctx, rc, err);
+    c.prog = std::move(prog);
+    return mrsim_sequence_create(ctx, &c, out);
+}
+
+int64_t mrsim_sequence_num_adc(const mrsim_sequence *s) { return s ? s->prog->host.n_adc : -1; }
 int64_t mrsim_sequence_num_events(const mrsim_sequence *s) { return s ? s->n_events : -1; }
-int64_t mrsim_sequence_num_ops(const mrsim_sequence *s) { return s ? (int64_t)s->host.ops32.size() : -1; }
+int64_t mrsim_sequence_num_ops(const mrsim_sequence *s) { return s ? (int64_t)s->prog->host.ops32.size() : -1; }
 
 void mrsim_sequence_destroy(mrsim_sequence *s) {
     if (!s) return;
@@ -323,9 +402,9 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
     if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
-    if (n_adc != seq->host.n_adc)
+    if (n_adc != seq->prog->host.n_adc)
         return fail(ctx, MRSIM_EINVAL, "n_adc = " + std::to_string(n_adc) + " but the sequence has " +
-                                           std::to_string(seq->host.n_adc) + " samples");
+                                           std::to_string(seq->prog->host.n_adc) + " samples");
     if (n_adc > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal_out");
     const bool fp64 = prec == MRSIM_FP64;
     mrsim_options o{};
@@ -375,7 +454,7 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
         if (host_out) dout = ctx->d_state + st_n;
     }
     // snapshots (host buffers go through their own scratch)
-    const size_t snap_n = (size_t)seq->host.n_snap * 3 * (size_t)ph->n;
+    const size_t snap_n = (size_t)seq->prog->host.n_snap * 3 * (size_t)ph->n;
     double *dsnap = o.snapshots;
     const bool host_snap = o.snapshots && snap_n > 0 && !is_device_ptr(o.snapshots);
     if (host_snap) {
@@ -410,9 +489,9 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
     if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_coils < 1 || n_coils > MAX_COILS)
         return fail(ctx, MRSIM_EINVAL, "n_coils must be 1.." + std::to_string(MAX_COILS));
-    if (n_adc != seq->host.n_adc)
+    if (n_adc != seq->prog->host.n_adc)
         return fail(ctx, MRSIM_EINVAL, "n_adc = " + std::to_string(n_adc) + " but the sequence has " +
-                                           std::to_string(seq->host.n_adc) + " samples");
+                                           std::to_string(seq->prog->host.n_adc) + " samples");
     if (ph->n > 0 && !sens) return fail(ctx, MRSIM_EINVAL, "NULL sensitivities");
     if (n_adc > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal buffer");
     const bool fp64 = prec == MRSIM_FP64;
@@ -818,7 +897,7 @@ mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *
             delete b;
             return fail(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": NULL handle or another context");
         }
-        if (q->host.n_adc > 0 && !is_device_ptr(signals_out[i])) {
+        if (q->prog->host.n_adc > 0 && !is_device_ptr(signals_out[i])) {
             delete b;
             return fail(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": signal buffer must be device memory");
         }

@@ -4,6 +4,7 @@
 
 #include <array>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -53,10 +54,25 @@ struct mrsim_phantom {
     double *params = nullptr;
 };
 
+namespace mrsim {
+// A compiled program with the host-side conversions the upload needs (float32 copies of the
+// demodulation and sub-pulse tables, the moment bound of the float32 inline phase terms).
+struct HostProgram {
+    Compiled host;
+    std::vector<float> demod32, train32;
+    float kmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int64_t n_events = 0;
+};
+}  // namespace mrsim
+
+struct mrsim_compiled {
+    std::shared_ptr<const mrsim::HostProgram> prog;
+};
+
 struct mrsim_sequence {
     mrsim_ctx *ctx = nullptr;
     int64_t n_events = 0;
-    Compiled host;
+    std::shared_ptr<const mrsim::HostProgram> prog;  // shared with the mrsim_compiled it came from
     void *d_ops32 = nullptr, *d_ops64 = nullptr;
     double *d_pcls = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_demod = nullptr;
     float *d_demod32 = nullptr;

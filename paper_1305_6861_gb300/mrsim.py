@@ -39,7 +39,8 @@ EXPORTS = (
     "mrsim_batch_autotune", "mrsim_batch_set_shape", "mrsim_batch_launch", "mrsim_batch_launch_graph",
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
     "mrsim_adjoint_create", "mrsim_adjoint_num_adc", "mrsim_adjoint_forward", "mrsim_adjoint_backward",
-    "mrsim_adjoint_destroy",
+    "mrsim_adjoint_destroy", "mrsim_compile", "mrsim_compile_last_error", "mrsim_compiled_num_adc",
+    "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create",
 )
 
 
@@ -130,6 +131,12 @@ def lib():
             "mrsim_adjoint_backward": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "mrsim_adjoint_destroy": (None, [vp]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
+            "mrsim_compile": (ctypes.c_int, [i64, vp, dbl, i64, vp, P(vp)]),
+            "mrsim_compile_last_error": (ctypes.c_char_p, []),
+            "mrsim_compiled_num_adc": (i64, [vp]),
+            "mrsim_compiled_upload_bytes": (i64, [vp]),
+            "mrsim_compiled_destroy": (None, [vp]),
+            "mrsim_sequence_create": (ctypes.c_int, [vp, vp, P(vp)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -221,6 +228,36 @@ class Phantom:
             pass
 
 
+class Compiled:
+    """Host-compiled program (mrsim_compile): no context and no GPU involved, so it can be built on
+    a worker thread while a context simulates (ctypes releases the GIL during the call)."""
+
+    def __init__(self, events, gamma_hz_per_t: float, snapshots=None):
+        ev = np.ascontiguousarray(events)
+        if ev.dtype != EVENT_DTYPE:
+            ev = ev.astype(EVENT_DTYPE)
+        sn = np.ascontiguousarray([] if snapshots is None else snapshots, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = lib().mrsim_compile(ev.shape[0], _ptr(ev), float(gamma_hz_per_t), sn.shape[0],
+                                 _ptr(sn) if sn.shape[0] else None, ctypes.byref(h))
+        if rc != 0:
+            raise MrsimError(rc, lib().mrsim_compile_last_error().decode())
+        self.h = h
+        self.n_adc = int(lib().mrsim_compiled_num_adc(h))
+        self.upload_bytes = int(lib().mrsim_compiled_upload_bytes(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_compiled_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Sequence:
     """Compiled event list (host numpy array of EVENT_DTYPE records)."""
 
@@ -246,6 +283,20 @@ class Sequence:
     @classmethod
     def from_workload_sequence(cls, ctx, seq):
         return cls(ctx, seq.events, seq.gamma_hz_per_t)
+
+    @classmethod
+    def from_compiled(cls, ctx: Context, compiled: "Compiled"):
+        """Upload a host-compiled program (mrsim_sequence_create)."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx.check(lib().mrsim_sequence_create(ctx.h, compiled.h, ctypes.byref(h)))
+        self.h = h
+        self.n_snapshots = int(lib().mrsim_sequence_num_snapshots(h))
+        self.n_adc = int(lib().mrsim_sequence_num_adc(h))
+        self.n_events = int(lib().mrsim_sequence_num_events(h))
+        self.n_ops = int(lib().mrsim_sequence_num_ops(h))
+        return self
 
     def close(self):
         if getattr(self, "h", None):

@@ -266,3 +266,26 @@ def test_config3_subset_parity(M, ctx, oracle_mod):
     ref = oracle_mod.signal(sub, w.sequence)
     assert rel_l2(run(M, ctx, sub, w.sequence, M.FP64), ref) <= TOL64
     assert rel_l2(run(M, ctx, sub, w.sequence, M.FP32), ref) <= TOL32
+
+
+def test_sequence_from_host_compiled_program(M, ctx, oracle_mod):
+    """mrsim_compile on a worker thread + mrsim_sequence_create equals mrsim_sequence_load; the
+    sequence keeps the program's tables after the compiled handle is destroyed."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    w = W.config1()
+    with ThreadPoolExecutor(1) as pool:
+        comp = pool.submit(M.Compiled, w.sequence.events, w.sequence.gamma_hz_per_t).result()
+    s = M.Sequence.from_compiled(ctx, comp)
+    comp.close()
+    assert s.n_adc == w.sequence.n_adc and s.n_events == w.sequence.n_events
+    p = M.Phantom.from_workload_phantom(ctx, w.phantom)
+    ref = oracle_mod.signal(w)
+    plain = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    for prec, tol in ((M.FP64, TOL64), (M.FP32, TOL32)):
+        got = M.simulate(ctx, p, s, prec)
+        assert rel_l2(got, ref) <= tol
+        assert rel_l2(got, M.simulate(ctx, p, plain, prec)) <= tol
+    s.close()
+    plain.close()
+    p.close()

@@ -244,3 +244,60 @@ def test_snapshot_inside_a_rewound_readout(mrsim_lib, oracle_mod):
     for q, e in enumerate(snaps):
         _, st = oracle_mod.simulate(ph, ev[: e + 1], RC.GAMMA, want_signal=False, want_state=True)
         assert np.max(np.abs(got[q] - st)) <= tol * max(1.0, np.abs(st).max()), q
+
+
+# ---- context-free compilation (mrsim_compile) -------------------------------------------------
+def test_compile_without_context(mrsim_lib):
+    """mrsim_compile needs no GPU; its upload size is the program the debug dump describes."""
+    M = mrsim_lib
+    w = CASES["c2_small"]()
+    c = M.Compiled(w.sequence.events, w.sequence.gamma_hz_per_t)
+    d = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
+    n_adc, n_tr = len(d["demod"]), len(d["train"])
+    assert c.n_adc == n_adc == w.sequence.n_adc
+    doubles = d["pcls"].size + d["e1"].size + d["e2"].size + 2 * n_adc + 2 * n_tr
+    assert c.upload_bytes == len(d["ops"]) * (64 + 128) + 8 * doubles + 4 * (2 * n_adc + 2 * n_tr)
+    c.close()
+    c.close()  # idempotent
+
+
+def test_compile_errors_are_per_thread(mrsim_lib):
+    import threading
+
+    M = mrsim_lib
+    good = W.config1().sequence.events
+    bad = W.make_events([(1e-3, 0, 0, 0, 0.5, 0, 1, 0.0)] * 3)
+    bad["dt"][1] = -1.0
+    msgs = {}
+
+    def run(name, ev):
+        try:
+            M.Compiled(ev, W.GAMMA_BAR).close()
+            msgs[name] = M.lib().mrsim_compile_last_error().decode()
+        except M.MrsimError as e:
+            msgs[name] = str(e)
+
+    ts = [threading.Thread(target=run, args=("bad", bad)), threading.Thread(target=run, args=("good", good))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert "negative duration" in msgs["bad"] and msgs["good"] == ""
+
+
+def test_concurrent_compiles_are_identical(mrsim_lib):
+    """Compilation keeps no shared state: programs compiled on several threads at once match the
+    serial one field by field."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    M = mrsim_lib
+    seqs = [CASES["c2_small"]().sequence.events, W.config1().sequence.events,
+            W.random_sequence(3000, np.random.default_rng(77)).events, RC.flash_like()]
+    gammas = [W.GAMMA_BAR, W.GAMMA_BAR, W.GAMMA_BAR, RC.GAMMA]
+    ref = [M.debug_compile(e, g) for e, g in zip(seqs, gammas)]
+    with ThreadPoolExecutor(8) as pool:
+        got = list(pool.map(lambda i: M.debug_compile(seqs[i % 4], gammas[i % 4]), range(32)))
+    for i, d in enumerate(got):
+        r = ref[i % 4]
+        for k in r:
+            assert np.array_equal(r[k].view(np.uint8), d[k].view(np.uint8)), (i, k)
