@@ -144,9 +144,13 @@ def traffic_for(kernel_src_sha: str, workload: str):
     return None
 
 
-def kernel_source_sha() -> str:
+FWD_SOURCES = ("fwd_kernel.cuh", "packed.cuh", "internal.h", "compile.cpp")
+KT_SOURCES = ("kt_kernel.cu", "packed.cuh", "internal.h")
+
+
+def kernel_source_sha(files=FWD_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in ("fwd_kernel.cuh", "packed.cuh", "internal.h", "compile.cpp"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1305_6861_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -424,7 +428,9 @@ def run_kt(args):
                        "order_steps_per_step": ens_steps * (K + 1),
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s",
-                         "frac": achieved / peak, "traffic": None, "kernel_ms": ms,
+                         "frac": achieved / peak,
+                         "traffic": traffic_for(kernel_source_sha(KT_SOURCES), f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}")
+                         if prec == M.FP32 else None, "kernel_ms": ms,
                          "ops_per_order_step": KT_OPS_PER_ORDER},
             "gpu_launches": 2 * args.steps, "clocks": ck}
     if not args.no_cpu_baseline:
