@@ -12,7 +12,9 @@
 //          (ε1 = 1 − exp(−τ/T1) evaluated accurately, never 1 − E1 in float32), then the
 //          Eq. 3.19 rotation, which in the pulse frame is a turn about the frame's x axis;
 //   PREC : u + jv <- (u + jv)·E2·exp(-j2πφ) with φ = k·x + Δf·Δt in cycles (Eqs. 3.5/3.11/3.14);
-//   RUN  : n samples of one constant-gradient readout, each (u + jv) <- (u + jv)·w;
+//   RUN  : n samples of one constant-gradient readout, each (u + jv) <- (u + jv)·w, optionally
+//          preceded by an inline precession (a folded phase encoding) and ended by an anchor
+//          that sets the state from the one before the run times an exact class phasor;
 //   samples: Σ_spins (u + jv) (§5.1.1, Eq. 3.32) reduced in-thread over the K spins (tree),
 //            across the warp by a transposed butterfly (16 samples per pass: lane l ends up
 //            with the warp total of value l), across warps in shared memory and across blocks
