@@ -100,3 +100,27 @@ def test_snapshots_device_buffer_and_batch(M, ctx, oracle_mod):
     ref = oracle_mod.signal(w)
     assert rel_l2(sig.cpu().numpy().view(np.complex128), ref) <= 1e-12
     b.close()
+
+
+def test_snapshots_through_host_compile(M, ctx, oracle_mod):
+    """Snapshots compiled by mrsim_compile (no context) and uploaded with mrsim_sequence_create
+    give the states of mrsim_sequence_load_snapshots."""
+    rng = np.random.default_rng(4400)
+    ph = W.random_phantom(700, rng)
+    seq = W.random_sequence(600, rng, runs=True)
+    snaps = np.sort(rng.choice(len(seq.events), size=5, replace=False))
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    comp = M.Compiled(seq.events, W.GAMMA_BAR, snapshots=snaps)
+    s1 = M.Sequence.from_compiled(ctx, comp)
+    comp.close()
+    s2 = M.Sequence(ctx, seq.events, W.GAMMA_BAR, snapshots=snaps)
+    assert s1.n_snapshots == s2.n_snapshots == len(snaps)
+    tol64 = phase_floor(ph, seq.events, W.GAMMA_BAR)
+    a, b = np.zeros((len(snaps), ph.n, 3)), np.zeros((len(snaps), ph.n, 3))
+    sa = M.simulate(ctx, p, s1, M.FP64, snapshots=a)
+    sb = M.simulate(ctx, p, s2, M.FP64, snapshots=b)
+    ctx.stream_status()
+    assert np.max(np.abs(a - b)) <= tol64 * max(1.0, np.abs(b).max())
+    assert rel_l2(sa, sb) <= tol64
+    ref, _ = oracle_mod.simulate(ph, seq.events, W.GAMMA_BAR)
+    assert rel_l2(sa, ref) <= tol64
