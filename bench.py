@@ -584,7 +584,7 @@ def run_ours(args):
         host_arrays = [p.numpy() for p in pinned]
         ev_pinned = torch.from_numpy(w.sequence.events.view(np.uint8)).pin_memory().numpy().view(W.EVENT_DTYPE)
         host_sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64).pin_memory().numpy().view(np.complex128)
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = max(3, min(args.steps, 20))
         gamma = w.sequence.gamma_hz_per_t
 
         def e2e_serial_step():

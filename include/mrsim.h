@@ -136,8 +136,9 @@ mrsim_status mrsim_compile(int64_t n_events, const mrsim_event *events, double g
  * mrsim_compile call. */
 const char *mrsim_compile_last_error(void);
 int64_t mrsim_compiled_num_adc(const mrsim_compiled *c);
-/* Bytes mrsim_sequence_create copies to the device for this program (operations, class tables,
- * demodulation factors, sub-pulse tables, in both precisions). */
+/* Bytes mrsim_sequence_create copies to the device for this program: operations, class tables,
+ * demodulation factors and sub-pulse tables in both precisions, in one image whose tables start
+ * on 256-byte boundaries (one allocation, one copy). */
 int64_t mrsim_compiled_upload_bytes(const mrsim_compiled *c);
 void mrsim_compiled_destroy(mrsim_compiled *c);
 /* Uploads a compiled program to ctx's device.  The sequence shares the program's host tables, so

@@ -61,15 +61,6 @@ mrsim_status grow(mrsim_ctx *ctx, double **buf, size_t *cap, size_t need_doubles
     return MRSIM_OK;
 }
 
-template <class T>
-mrsim_status upload(mrsim_ctx *ctx, T **dst, const std::vector<T> &v) {
-    *dst = nullptr;
-    if (v.empty()) return MRSIM_OK;
-    CK(cudaMalloc(dst, v.size() * sizeof(T)), "cudaMalloc sequence");
-    CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload sequence");
-    return MRSIM_OK;
-}
-
 mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStream_t st, mrsim_phantom **out) {
     mrsim_phantom *p = new (std::nothrow) mrsim_phantom();
     if (!p) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");
@@ -256,6 +247,23 @@ mrsim_status compile_host(int64_t n_events, const mrsim_event *events, double ga
         for (const OpF32 &o : c->host.ops32)  // magnitude bound of the float32 inline phase terms
             if ((o.kind == OP_PREC || o.kind == OP_RUN) && (o.flags & F_INLINE))
                 for (int a = 0; a < 4; ++a) c->kmax[a] = std::max(c->kmax[a], std::fabs(o.f[2 * a]));
+        const Compiled &h = c->host;
+        const void *src[HostProgram::N_TABLES] = {h.ops32.data(), h.ops64.data(), h.pcls.data(), h.e1.data(),
+                                                  h.e2.data(), h.demod.data(), c->demod32.data(),
+                                                  c->train32.data(), h.train.data()};
+        const size_t bytes[HostProgram::N_TABLES] = {
+            h.ops32.size() * sizeof(OpF32), h.ops64.size() * sizeof(OpF64), h.pcls.size() * sizeof(double),
+            h.e1.size() * sizeof(double),   h.e2.size() * sizeof(double),    h.demod.size() * sizeof(double),
+            c->demod32.size() * sizeof(float), c->train32.size() * sizeof(float), h.train.size() * sizeof(double)};
+        size_t o = 0;
+        for (int t = 0; t < HostProgram::N_TABLES; ++t) {
+            c->off[t] = o;
+            c->len[t] = bytes[t];
+            o = (o + bytes[t] + 255) / 256 * 256;
+        }
+        c->image.assign(o, 0);
+        for (int t = 0; t < HostProgram::N_TABLES; ++t)
+            if (bytes[t]) std::memcpy(c->image.data() + c->off[t], src[t], bytes[t]);
     } catch (const std::bad_alloc &) {
         err = "host allocation failed";
         return MRSIM_ENOMEM;
@@ -299,14 +307,7 @@ const char *mrsim_compile_last_error(void) { return t_compile_err.c_str(); }
 
 int64_t mrsim_compiled_num_adc(const mrsim_compiled *c) { return c ? c->prog->host.n_adc : -1; }
 
-int64_t mrsim_compiled_upload_bytes(const mrsim_compiled *c) {
-    if (!c) return -1;
-    const HostProgram &p = *c->prog;
-    return (int64_t)(p.host.ops32.size() * sizeof(OpF32) + p.host.ops64.size() * sizeof(OpF64) +
-                     (p.host.pcls.size() + p.host.e1.size() + p.host.e2.size() + p.host.demod.size() +
-                      p.host.train.size()) * sizeof(double) +
-                     (p.demod32.size() + p.train32.size()) * sizeof(float));
-}
+int64_t mrsim_compiled_upload_bytes(const mrsim_compiled *c) { return c ? (int64_t)c->prog->image.size() : -1; }
 
 void mrsim_compiled_destroy(mrsim_compiled *c) { delete c; }
 
@@ -321,23 +322,24 @@ mrsim_status mrsim_sequence_create(mrsim_ctx *ctx, const mrsim_compiled *c, mrsi
     s->n_events = c->prog->n_events;
     const HostProgram &h = *s->prog;
     cudaSetDevice(ctx->device);
-    mrsim_status st = MRSIM_OK;
-    auto up = [&](auto **d, const auto &v) {
-        if (st == MRSIM_OK) st = upload(ctx, d, v);
-    };
-    up((OpF32 **)&s->d_ops32, h.host.ops32);
-    up((OpF64 **)&s->d_ops64, h.host.ops64);
-    up(&s->d_pcls, h.host.pcls);
-    up(&s->d_e1, h.host.e1);
-    up(&s->d_e2, h.host.e2);
-    up(&s->d_demod, h.host.demod);
-    up(&s->d_demod32, h.demod32);
-    up(&s->d_train32, h.train32);
-    up(&s->d_train64, h.host.train);
-    if (st != MRSIM_OK) {
-        mrsim_sequence_destroy(s);
-        return st;
+    if (!h.image.empty()) {  // one allocation and one copy for every table
+        cudaError_t e = cudaMalloc(&s->d_image, h.image.size());
+        if (e == cudaSuccess) e = cudaMemcpy(s->d_image, h.image.data(), h.image.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            mrsim_sequence_destroy(s);
+            return cuda_fail(ctx, e, "upload sequence");
+        }
     }
+    auto at = [&](HostProgram::Table t) -> void * { return h.len[t] ? (void *)(s->d_image + h.off[t]) : nullptr; };
+    s->d_ops32 = at(HostProgram::OPS32);
+    s->d_ops64 = at(HostProgram::OPS64);
+    s->d_pcls = (double *)at(HostProgram::PCLS);
+    s->d_e1 = (double *)at(HostProgram::E1);
+    s->d_e2 = (double *)at(HostProgram::E2);
+    s->d_demod = (double *)at(HostProgram::DEMOD);
+    s->d_demod32 = (float *)at(HostProgram::DEMOD32);
+    s->d_train32 = (float *)at(HostProgram::TRAIN32);
+    s->d_train64 = (double *)at(HostProgram::TRAIN64);
     Program p{};
     p.n_ops = (int32_t)h.host.ops32.size();
     p.n_pcls = h.host.n_pcls;
@@ -383,15 +385,7 @@ int64_t mrsim_sequence_num_ops(const mrsim_sequence *s) { return s ? (int64_t)s-
 void mrsim_sequence_destroy(mrsim_sequence *s) {
     if (!s) return;
     cudaSetDevice(s->ctx->device);
-    cudaFree(s->d_ops32);
-    cudaFree(s->d_ops64);
-    cudaFree(s->d_pcls);
-    cudaFree(s->d_e1);
-    cudaFree(s->d_e2);
-    cudaFree(s->d_demod);
-    cudaFree(s->d_demod32);
-    cudaFree(s->d_train32);
-    cudaFree(s->d_train64);
+    cudaFree(s->d_image);
     delete s;
 }
 

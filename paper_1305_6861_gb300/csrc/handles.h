@@ -62,6 +62,12 @@ struct HostProgram {
     std::vector<float> demod32, train32;
     float kmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     int64_t n_events = 0;
+    // every device table in one 256-byte-aligned image, uploaded with a single copy: operations
+    // (float32, float64), phasor classes, T1 and T2 classes, demodulation (float64, float32),
+    // sub-pulse tables (float32, float64)
+    enum Table { OPS32, OPS64, PCLS, E1, E2, DEMOD, DEMOD32, TRAIN32, TRAIN64, N_TABLES };
+    std::vector<unsigned char> image;
+    size_t off[N_TABLES] = {}, len[N_TABLES] = {};
 };
 }  // namespace mrsim
 
@@ -73,6 +79,7 @@ struct mrsim_sequence {
     mrsim_ctx *ctx = nullptr;
     int64_t n_events = 0;
     std::shared_ptr<const mrsim::HostProgram> prog;  // shared with the mrsim_compiled it came from
+    unsigned char *d_image = nullptr;                 // the program's tables; the pointers below view it
     void *d_ops32 = nullptr, *d_ops64 = nullptr;
     double *d_pcls = nullptr, *d_e1 = nullptr, *d_e2 = nullptr, *d_demod = nullptr;
     float *d_demod32 = nullptr;
