@@ -149,10 +149,17 @@ KT_SOURCES = ("kt_kernel.cu", "packed.cuh", "internal.h")
 
 
 def kernel_source_sha(files=FWD_SOURCES) -> str:
+    """Hash of the kernel sources' code (comments and whitespace removed), so that a counter
+    capture stays valid across documentation edits and is dropped when the code changes."""
+    import re
+
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_1305_6861_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1305_6861_gb300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
