@@ -230,7 +230,11 @@ def run_batch(args):
     outs = [torch.zeros(max(2 * q.n_adc, 2), dtype=torch.float64, device=dev) for q in sqs]
     b = M.Batch(ctx, phs, sqs, prec, outs)
     t0 = time.perf_counter()
-    shape = b.autotune(stream=stream)
+    if args.spins_per_thread and args.threads:  # a fixed shape (profiling runs: no tuning launches)
+        shape = (args.spins_per_thread, args.threads)
+        b.set_shape(*shape)
+    else:
+        shape = b.autotune(stream=stream)
     tune_s = time.perf_counter() - t0
     spin_steps = sum(w.spin_steps for w in ws)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -264,8 +268,9 @@ def run_batch(args):
                               "mode": "persistent kernel + work queue, CUDA graph replay"},
                    "l2": "flushed between timed steps (256 MB write, outside the step events)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s",
-                     "frac": achieved / peak, "traffic": None, "kernel_ms": ms,
-                     "ops_per_spin_step": ops / spin_steps},
+                     "frac": achieved / peak,
+                     "traffic": traffic_for(kernel_source_sha(), "c4_batch64") if prec == M.FP32 else None,
+                     "kernel_ms": ms, "ops_per_spin_step": ops / spin_steps},
         "gpu_launches": 2 * args.steps, "clocks": ck,
     }
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample of the batch's longest program
@@ -344,7 +349,7 @@ def run_adjoint(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": len(ev), "n_rf_params": len(rf0),
                        "ckpt_every": 64, "step": "adjoint forward + backward",
-                       "note": "16 384 spins are 512 warps, fewer than the 608 schedulers: latency-bound by size"},
+                       "note": "float64-pipe bound (ncu: the backward kernel keeps it 71 % busy with 4 warps per SM); the flop model counts the formulation's arithmetic, about half the executed float64 instructions"},
             "roofline": {"bound": "fp64", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (float64)",
                          "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None, "kernel_ms": ms,
                          "peak_basis": "nominal float64 rate of the profiling recipe (no measured float64 figure)",
