@@ -31,6 +31,7 @@ namespace {
 constexpr int ADJ_MAX_CLASSES = 16;
 constexpr int ADJ_MAX_SEG = 128;  // events per checkpoint segment (per-thread state buffer size)
 constexpr int ADJ_THREADS = 128;
+constexpr int ADJ_LOCAL_PARAMS = 256;  // RF parameters summed per thread in local memory
 
 enum AdjFlags : int32_t { A_RF = 1, A_ADC = 2, A_CLS = 4, A_INL = 8 };
 
@@ -54,7 +55,7 @@ struct RfSpec {
 };
 struct RfEntry {
     double R[9];
-    double D[9];
+    double G[9];         // (dR/dα)·Rᵀ: the derivative applied to the state after the pulse
     int32_t param, pad;  // learnable parameter index or -1
 };
 
@@ -98,16 +99,21 @@ __global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values,
         e.R[6] = sa * n1;
         e.R[7] = -sa * n0;
         e.R[8] = ca;
-        // dR/dα = −sin α·I + sin α·n nᵀ − cos α·[n]x
-        e.D[0] = -sa + sa * n0 * n0;
-        e.D[1] = sa * n0 * n1;
-        e.D[2] = -ca * n1;
-        e.D[3] = sa * n0 * n1;
-        e.D[4] = -sa + sa * n1 * n1;
-        e.D[5] = ca * n0;
-        e.D[6] = ca * n1;
-        e.D[7] = -ca * n0;
-        e.D[8] = -sa;
+        // dR/dα = −sin α·I + sin α·n nᵀ − cos α·[n]x, then G = (dR/dα)·Rᵀ (R is orthogonal, so the
+        // state before the pulse is Rᵀ times the state after it)
+        double D[9];
+        D[0] = -sa + sa * n0 * n0;
+        D[1] = sa * n0 * n1;
+        D[2] = -ca * n1;
+        D[3] = sa * n0 * n1;
+        D[4] = -sa + sa * n1 * n1;
+        D[5] = ca * n0;
+        D[6] = ca * n1;
+        D[7] = -ca * n0;
+        D[8] = -sa;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                e.G[3 * r + c] = D[3 * r] * e.R[3 * c] + D[3 * r + 1] * e.R[3 * c + 1] + D[3 * r + 2] * e.R[3 * c + 2];
         e.param = s.param;
         e.pad = 0;
         out[i] = e;
@@ -199,10 +205,8 @@ __device__ __forceinline__ void apply_rf(const double *R, double M[3]) {
     M[2] = z;
 }
 
-// forward step of one event (Eq. 4.1)
-__device__ __forceinline__ void step(const AdjArgs &a, const AdjEvent &e, const SpinP &p, const double *tab,
-                                     double M[3]) {
-    if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, M);
+// the part of an event after its pulse: precession, T2 and T1 over the interval
+__device__ __forceinline__ void after_pulse(const AdjEvent &e, const SpinP &p, const double *tab, double M[3]) {
     double wr, wi, e1;
     factors(e, p, tab, wr, wi, e1);
     const double x = M[0] * wr - M[1] * wi;
@@ -210,6 +214,13 @@ __device__ __forceinline__ void step(const AdjArgs &a, const AdjEvent &e, const 
     M[0] = x;
     M[1] = y;
     M[2] = e1 * M[2] + p.rho * (1.0 - e1);
+}
+
+// forward step of one event (Eq. 4.1)
+__device__ __forceinline__ void step(const AdjArgs &a, const AdjEvent &e, const SpinP &p, const double *tab,
+                                     double M[3]) {
+    if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, M);
+    after_pulse(e, p, tab, M);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -260,6 +271,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_forward_kernel(const AdjArgs 
     }
 }
 
+// LOCAL: each thread sums its RF-parameter gradients in a local array (n_params <= ADJ_LOCAL_PARAMS)
+// and the block reduces them once at the end; otherwise every pulse reduces over the warp.
+template <bool LOCAL>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     AdjEvent *sev = reinterpret_cast<AdjEvent *>(smem);
@@ -271,7 +285,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
     for (int q = threadIdx.x; q < a.n_params; q += blockDim.x) grf[q] = 0.0;
     const int lane = threadIdx.x & 31;
     const bool valid = s < a.n_spins;
-    double buf[ADJ_MAX_SEG][3];  // states at the start of each event of the segment
+    double buf[ADJ_MAX_SEG][3];  // states after each event's pulse, for the segment
+    double gl[LOCAL ? ADJ_LOCAL_PARAMS : 1];
+    if constexpr (LOCAL)
+        for (int q = 0; q < a.n_params; ++q) gl[q] = 0.0;
     double L[3] = {0.0, 0.0, 0.0};
     double g_rho = 0.0, g_r1 = 0.0, g_r2 = 0.0;
     const int64_t n_seg = (a.n_events + a.seg - 1) / a.seg;
@@ -289,10 +306,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
             M[0] = M[1] = M[2] = 0.0;
         }
         for (int i = 0; i < m; ++i) {
+            const AdjEvent &e = sev[i];
+            if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, M);
             buf[i][0] = M[0];
             buf[i][1] = M[1];
             buf[i][2] = M[2];
-            step(a, sev[i], p, tab, M);
+            after_pulse(e, p, tab, M);
         }
         for (int i = m - 1; i >= 0; --i) {
             const AdjEvent &e = sev[i];
@@ -302,10 +321,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
                 L[0] += cr * hr - ci * hi;
                 L[1] += cr * hi + ci * hr;
             }
-            // state before the event, and after its pulse
-            double Mn[3] = {buf[i][0], buf[i][1], buf[i][2]};
-            double Ma[3] = {Mn[0], Mn[1], Mn[2]};
-            if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, Ma);
+            const double Ma[3] = {buf[i][0], buf[i][1], buf[i][2]};  // state after the event's pulse
             double wr, wi, e1;
             factors(e, p, tab, wr, wi, e1);
             // parameter gradients through P (λ is the adjoint after the event)
@@ -318,13 +334,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
             if (e.flags & A_RF) {
                 const RfEntry &rf = a.rf[e.rf];
                 if (rf.param >= 0) {
-                    // dL/dα = λ_aᵀ·(dR/dα)·M_n, reduced over the warp, then the block (shared atomics)
-                    const double *D = rf.D;
-                    const double dx = D[0] * Mn[0] + D[1] * Mn[1] + D[2] * Mn[2];
-                    const double dy = D[3] * Mn[0] + D[4] * Mn[1] + D[5] * Mn[2];
-                    const double dz = D[6] * Mn[0] + D[7] * Mn[1] + D[8] * Mn[2];
-                    const double g = warp_sum(lax * dx + lay * dy + laz * dz);
-                    if (lane == 0) atomicAdd(&grf[rf.param], g);
+                    // dL/dα = λ_aᵀ·(dR/dα)·M_n = λ_aᵀ·G·M_a
+                    const double *G = rf.G;
+                    const double dx = G[0] * Ma[0] + G[1] * Ma[1] + G[2] * Ma[2];
+                    const double dy = G[3] * Ma[0] + G[4] * Ma[1] + G[5] * Ma[2];
+                    const double dz = G[6] * Ma[0] + G[7] * Ma[1] + G[8] * Ma[2];
+                    const double g = lax * dx + lay * dy + laz * dz;
+                    if constexpr (LOCAL) {
+                        gl[rf.param] += g;
+                    } else {  // reduced over the warp, then the block (shared atomics)
+                        const double gw = warp_sum(g);
+                        if (lane == 0) atomicAdd(&grf[rf.param], gw);
+                    }
                 }
                 // λ_n = Rᵀ λ_a
                 L[0] = rf.R[0] * lax + rf.R[3] * lay + rf.R[6] * laz;
@@ -338,6 +359,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
         }
     }
     g_rho += L[2];  // initial state (0, 0, M0)
+    if constexpr (LOCAL) {
+        for (int q = 0; q < a.n_params; ++q) {
+            const double gw = warp_sum(gl[q]);
+            if (lane == 0 && gw != 0.0) atomicAdd(&grf[q], gw);
+        }
+    }
     __syncthreads();
     if (a.d_rf)
         for (int q = threadIdx.x; q < a.n_params; q += blockDim.x)
@@ -586,9 +613,14 @@ mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph,
     a.d_t2 = d_t2;
     a.d_rf = d_rf;
     const size_t smem = adj_smem(adj, true);
-    cudaFuncSetAttribute(adj_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = (ph->n + ADJ_THREADS - 1) / ADJ_THREADS;
-    adj_backward_kernel<<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    if (adj->n_params <= ADJ_LOCAL_PARAMS) {
+        cudaFuncSetAttribute(adj_backward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        adj_backward_kernel<true><<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(adj_backward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        adj_backward_kernel<false><<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("adjoint backward: ") + cudaGetErrorString(e));
     return MRSIM_OK;
