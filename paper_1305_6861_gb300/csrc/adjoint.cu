@@ -10,6 +10,10 @@
 // in reverse order: the forward pass stores every spin's state at the start of each segment of C
 // events (checkpoints); the backward pass restores a checkpoint, recomputes the segment's states
 // into a per-thread buffer and sweeps the segment backward.  Everything here is float64.
+// The forward pass is the library's float64 forward kernel on a program compiled once with the
+// learnable flips as parametric pulses (their rotations read from a table written before each
+// launch) and snapshots at the segment starts, which are the checkpoints; with more learnable
+// flips than that table holds, a one-thread-per-spin forward kernel of its own does the same.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -70,7 +75,8 @@ struct mrsim_adjoint {
     RfEntry *d_rf = nullptr;
     double *d_cls = nullptr;    // 4 per class: kx, ky, kz, dt
     double *d_demod = nullptr;  // 2 per sample: cos(adc_phase), -sin(adc_phase)
-    double *d_ckpt = nullptr;   // n_seg x 3 x n_spins
+    double *d_ckpt = nullptr;   // checkpoints: (n_seg - 1) x n_spins x 3 (forward kernel), else n_seg x 3 x n_spins
+    mrsim_sequence *fwd = nullptr;  // the forward program (parametric pulses, snapshots at segment starts)
     size_t ckpt_cap = 0;
     const mrsim_phantom *last_ph = nullptr;
     int64_t last_n = -1;
@@ -120,6 +126,18 @@ __global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values,
     }
 }
 
+// the learnable flips into the forward program's sub-pulse table, in both precisions
+__global__ void rf_param_table_kernel(const double *values, int n, double *t64, float *t32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double sa, ca;
+        sincos(values[i], &sa, &ca);
+        t64[2 * i] = ca;
+        t64[2 * i + 1] = sa;
+        t32[2 * i] = (float)ca;
+        t32[2 * i + 1] = (float)sa;
+    }
+}
+
 struct AdjArgs {
     const AdjEvent *ev;
     int64_t n_events;
@@ -130,7 +148,8 @@ struct AdjArgs {
     const double *demod;
     const double *params;
     int64_t n_spins, n_pad;
-    double *ckpt;     // n_seg x 3 x n_spins
+    double *ckpt;     // see mrsim_adjoint::d_ckpt
+    int32_t ckpt_snap;  // checkpoints written as snapshots by the forward kernel
     double *signal;   // forward
     const double *h;  // backward: dL/ds, 2 per sample
     double *d_rho, *d_t1, *d_t2, *d_rf;
@@ -296,14 +315,21 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
         const int64_t e0 = sg * a.seg;
         const int m = (int)min((int64_t)a.seg, a.n_events - e0);
         stage(a, e0, m, sev);
-        double M[3];
-        if (valid) {
+        double M[3] = {0.0, 0.0, 0.0};
+        if (valid && a.ckpt_snap) {  // state after event sg·C − 1; the first segment starts at rest
+            if (sg == 0) {
+                M[2] = p.rho;
+            } else {
+                const double *ck = a.ckpt + ((sg - 1) * a.n_spins + s) * 3;
+                M[0] = ck[0];
+                M[1] = ck[1];
+                M[2] = ck[2];
+            }
+        } else if (valid) {
             const double *ck = a.ckpt + sg * 3 * a.n_spins;
             M[0] = ck[s];
             M[1] = ck[a.n_spins + s];
             M[2] = ck[2 * a.n_spins + s];
-        } else {
-            M[0] = M[1] = M[2] = 0.0;
         }
         for (int i = 0; i < m; ++i) {
             const AdjEvent &e = sev[i];
@@ -414,6 +440,7 @@ AdjArgs adj_args(const mrsim_adjoint *adj, const mrsim_phantom *ph) {
     a.n_spins = ph->n;
     a.n_pad = ph->n_pad;
     a.ckpt = adj->d_ckpt;
+    a.ckpt_snap = adj->fwd != nullptr;
     a.n_params = adj->n_params;
     return a;
 }
@@ -540,6 +567,27 @@ mrsim_status mrsim_adjoint_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_
         mrsim_adjoint_destroy(adj);
         return afail(ctx, MRSIM_EUNSUPPORTED, "adjoint program needs more shared memory than the device has");
     }
+    if (n_params <= TRAIN_TABLE_MAX / 2) {  // the forward program: parametric pulses, a snapshot per segment start
+        std::vector<int64_t> snaps;
+        for (int64_t e0 = ckpt_every; e0 < n_events; e0 += ckpt_every) snaps.push_back(e0 - 1);
+        mrsim_compiled c;
+        std::shared_ptr<HostProgram> prog;
+        std::string err;
+        mrsim_status rc = compile_host(n_events, events, gamma, (int64_t)snaps.size(), snaps.data(), prog, err,
+                                       n_params > 0 ? rf_param : nullptr, n_params);
+        c.prog = std::move(prog);
+        if (rc == MRSIM_OK) {
+            rc = mrsim_sequence_create(ctx, &c, &adj->fwd);
+            if (rc == MRSIM_OK && fwd_smem_bytes(true, adj->fwd->p64, 1, ADJ_THREADS) > (size_t)ctx->max_smem_optin) {
+                mrsim_sequence_destroy(adj->fwd);
+                adj->fwd = nullptr;
+            }
+        }
+        if (rc != MRSIM_OK) {
+            mrsim_adjoint_destroy(adj);
+            return afail(ctx, rc, "adjoint forward program: " + (err.empty() ? std::string(mrsim_last_error(ctx)) : err));
+        }
+    }
     *out = adj;
     return MRSIM_OK;
 }
@@ -576,6 +624,25 @@ mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, 
     adj->last_ph = ph;
     adj->last_n = ph->n;
     if (ph->n == 0) return MRSIM_OK;
+    if (adj->fwd) {  // the float64 forward kernel on the parametric program; snapshots = checkpoints
+        if (adj->n_params > 0) {
+            rf_param_table_kernel<<<(adj->n_params + 127) / 128, 128, 0, st>>>(rf_values, adj->n_params,
+                                                                              adj->fwd->d_train64, adj->fwd->d_train32);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("flip table: ") + cudaGetErrorString(e));
+        }
+        FwdArgs f{};
+        f.prog = adj->fwd->p64;
+        f.params = ph->params;
+        f.n_spins = ph->n;
+        f.n_pad = ph->n_pad;
+        f.signal = signal_out;
+        f.status = ctx->d_status;
+        f.snap = adj->d_ckpt;
+        const int rc = launch_fwd_f64(f, 1, ADJ_THREADS, st);
+        if (rc != 0) return afail(ctx, MRSIM_ECUDA, std::string("adjoint forward: ") + cudaGetErrorString((cudaError_t)rc));
+        return MRSIM_OK;
+    }
     AdjArgs a = adj_args(adj, ph);
     a.signal = signal_out;
     const size_t smem = adj_smem(adj, false);
@@ -635,6 +702,7 @@ void mrsim_adjoint_destroy(mrsim_adjoint *adj) {
     cudaFree(adj->d_cls);
     cudaFree(adj->d_demod);
     cudaFree(adj->d_ckpt);
+    mrsim_sequence_destroy(adj->fwd);
     delete adj;
 }
 

@@ -229,17 +229,20 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
 
 int64_t mrsim_sequence_num_snapshots(const mrsim_sequence *s) { return s ? s->prog->host.n_snap : -1; }
 
-namespace {
+}  // extern "C"
 
+namespace {
 thread_local std::string t_compile_err;  // mrsim_compile's message, per calling thread
+}  // namespace
 
 // Compilation plus the host-side conversions of the upload; no CUDA call.
-mrsim_status compile_host(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
-                          const int64_t *snap_after, std::shared_ptr<HostProgram> &out, std::string &err) {
+mrsim_status mrsim::compile_host(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
+                                 const int64_t *snap_after, std::shared_ptr<HostProgram> &out, std::string &err,
+                                 const int32_t *rf_param, int32_t n_params) {
     std::shared_ptr<HostProgram> c;
     try {
         c = std::make_shared<HostProgram>();
-        int rc = compile_sequence(events, n_events, gamma, c->host, err, n_snap, snap_after);
+        int rc = compile_sequence(events, n_events, gamma, c->host, err, n_snap, snap_after, rf_param, n_params);
         if (rc != MRSIM_OK) return (mrsim_status)rc;
         c->n_events = n_events;
         c->demod32.assign(c->host.demod.begin(), c->host.demod.end());
@@ -272,7 +275,7 @@ mrsim_status compile_host(int64_t n_events, const mrsim_event *events, double ga
     return MRSIM_OK;
 }
 
-}  // namespace
+extern "C" {
 
 mrsim_status mrsim_compile(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
                            const int64_t *snap_after, mrsim_compiled **out) {

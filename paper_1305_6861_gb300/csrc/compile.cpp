@@ -28,6 +28,7 @@ struct Item {
     double tau;     // RF/END: time since the previous RF pulse [s]
     int64_t j;      // SAMPLE: sample index; SNAP: snapshot index
     double adc_phase;
+    int32_t param;  // RF: learnable-flip index of a parametric pulse, or -1
 };
 
 using Key = std::array<uint64_t, 4>;
@@ -190,8 +191,12 @@ void split(double v, float &hi, float &lo) {
 }  // namespace
 
 int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err,
-                     int64_t n_snap, const int64_t *snap_after) {
+                     int64_t n_snap, const int64_t *snap_after, const int32_t *rf_param, int32_t n_params) {
     out = Compiled();
+    if (rf_param && (n_params < 0 || n_params > TRAIN_TABLE_MAX / 2)) {
+        err = "parametric pulses: n_params must be in [0, " + std::to_string(TRAIN_TABLE_MAX / 2) + "]";
+        return MRSIM_EINVAL;
+    }
     if (n_snap < 0 || (n_snap > 0 && !snap_after)) {
         err = "invalid snapshot list";
         return MRSIM_EINVAL;
@@ -245,13 +250,19 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             err = "event " + std::to_string(i) + ": adc must be 0/1 and reserved 0";
             return MRSIM_EINVAL;
         }
-        if (e.rf_flip != 0.0) {
+        const int32_t prm = rf_param ? rf_param[i] : -1;
+        if (prm < -1 || prm >= (rf_param ? n_params : 0)) {
+            err = "event " + std::to_string(i) + ": learnable-flip index out of range";
+            return MRSIM_EINVAL;
+        }
+        if (e.rf_flip != 0.0 || prm >= 0) {
             flush();
             Item it{};
             it.kind = Item::RF;
             it.alpha = e.rf_flip;
             it.phi = e.rf_phase;
             it.tau = tau;
+            it.param = prm;
             items.push_back(it);
             tau = 0.0;
         }
@@ -487,9 +498,40 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     std::vector<OpF64> pend64;
     std::map<std::vector<uint64_t>, int> seen;
     std::vector<uint64_t> tkey;
+    if (rf_param) {  // entries 0 .. n_params-1: the learnable flips, written before each launch
+        out.train.reserve(2 * (size_t)n_params);
+        for (int32_t q = 0; q < n_params; ++q) {
+            out.train.push_back(1.0);
+            out.train.push_back(0.0);
+        }
+    }
+    // a run of parametric sub-pulses with consecutive indices reads its table entries in place
+    auto param_run = [&]() {
+        if (!(pend32[0].flags & F_RFTAB)) return -1;
+        for (size_t q = 0; q < pend32.size(); ++q)
+            if (!(pend32[q].flags & F_RFTAB) || pend32[q].tab != pend32[0].tab + (int)q) return -1;
+        return (int)pend32[0].tab;
+    };
     auto flush_train = [&]() {
         const size_t n = pend32.size();
-        if (n >= 2) {
+        bool mixed = false;
+        for (size_t q = 1; q < n; ++q) mixed |= ((pend32[q].flags ^ pend32[0].flags) & F_RFTAB) != 0;
+        if (n >= 2 && (pend32[0].flags & F_RFTAB) && !mixed) {
+            const int off = param_run();
+            if (off >= 0) {
+                OpF32 a = pend32[0];
+                OpF64 b = pend64[0];
+                a.kind = b.kind = OP_RF_TRAIN;
+                a.flags = b.flags = (uint16_t)(a.flags & ~F_RFTAB);
+                a.n = b.n = (int32_t)n;
+                a.adc0 = b.adc0 = off;
+                out.ops32.push_back(a);
+                out.ops64.push_back(b);
+                pend32.clear();
+                pend64.clear();
+                return;
+            }
+        } else if (n >= 2 && !mixed) {
             tkey.clear();
             for (size_t q = 0; q < n; ++q) {
                 tkey.push_back(bits(pend64[q].f[0]));
@@ -562,6 +604,10 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             a.f[1] = (float)sa;
             b.f[0] = ca;
             b.f[1] = sa;
+            if (it.param >= 0) {  // the rotation comes from table entry `param` at run time
+                both(a, b, F_RFTAB);
+                a.tab = b.tab = (int16_t)it.param;
+            }
             // fuse a following class precession (the sub-pulse trains of shaped pulses, Eq. 3.23)
             if (g + 1 < groups.size()) {
                 const Item &nx = items[groups[g + 1].first];

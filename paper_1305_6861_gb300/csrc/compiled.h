@@ -25,7 +25,11 @@ struct Compiled {
 // Returns an mrsim_status; on failure `err` says why.
 // snap_after: NULL or n_snap strictly increasing event indices after which every spin's state is
 // recorded (§7.2: magnetisation data at chosen times).
+// rf_param: NULL, or per event a learnable-flip index in [0, n_params) or -1.  Events with an index
+// become parametric pulses: their (cos α, sin α) are read at run time from sub-pulse table entry
+// index (the table's first n_params entries, which the caller fills before each launch).
 int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err,
-                     int64_t n_snap = 0, const int64_t *snap_after = nullptr);
+                     int64_t n_snap = 0, const int64_t *snap_after = nullptr, const int32_t *rf_param = nullptr,
+                     int32_t n_params = 0);
 
 }  // namespace mrsim

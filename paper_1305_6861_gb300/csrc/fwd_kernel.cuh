@@ -399,6 +399,16 @@ struct Spins {
             mz[q] = nz;
         }
     }
+    // the op's own rotation, or for a parametric pulse the one in sub-pulse table entry op.tab
+    __device__ __forceinline__ void rf_turn_op(const Op &op) {
+        if (op.flags & F_RFTAB) {
+            P ca, sa, nsa;
+            load_train(op.tab, ca, sa, nsa);
+            rf_turn(ca, sa, nsa);
+        } else {
+            rf_turn_s((R)op.f[0], (R)op.f[1]);
+        }
+    }
     __device__ __forceinline__ void rf_turn_s(R ca, R sa) {
         P c, s, ns;
         splat(c, ca);
@@ -855,13 +865,13 @@ struct Spins {
             break;
         case OP_RF_FAST:  // sub-pulse of a shaped pulse: every cache already holds the right class
             t1_cached();
-            rf_turn_s((R)op.f[0], (R)op.f[1]);
+            rf_turn_op(op);
             rot_w();
             break;
         case OP_RF:
             if (op.flags & F_FRAME) frame_turn(op);
             t1_relax(op);
-            rf_turn_s((R)op.f[0], (R)op.f[1]);
+            rf_turn_op(op);
             if (op.flags & F_PCLS) {
                 if (op.flags & F_PLOAD) load_w(op.pcls);
                 rot_w();

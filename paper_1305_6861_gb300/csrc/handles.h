@@ -71,6 +71,14 @@ struct HostProgram {
 };
 }  // namespace mrsim
 
+namespace mrsim {
+// mrsim_compile without the handle: compilation plus the host-side conversions of the upload (no
+// CUDA call); rf_param / n_params as for compile_sequence.
+mrsim_status compile_host(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
+                          const int64_t *snap_after, std::shared_ptr<HostProgram> &out, std::string &err,
+                          const int32_t *rf_param = nullptr, int32_t n_params = 0);
+}  // namespace mrsim
+
 struct mrsim_compiled {
     std::shared_ptr<const mrsim::HostProgram> prog;
 };

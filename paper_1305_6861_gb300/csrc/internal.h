@@ -58,6 +58,7 @@ enum OpFlags : uint16_t {
     F_KY = 2048,
     F_KZ = 4096,
     F_DT = 8192,
+    F_RFTAB = 16384,  // RF, RF_FAST: (cos α, sin α) from sub-pulse table entry `tab` (a parametric pulse)
 };
 
 // float32 program: 64 bytes.  Inline PREC payload: kx, ky, kz, Δt as (hi, lo) float pairs
@@ -69,7 +70,7 @@ struct alignas(16) OpF32 {
     int32_t n;
     int32_t adc0;
     int16_t pcls, ecls;
-    int16_t acls, rsv1;
+    int16_t acls, tab;  // tab: sub-pulse table entry of a parametric pulse (F_RFTAB)
     float f[11];
 };
 static_assert(sizeof(OpF32) == 64, "OpF32 must be 64 bytes");
@@ -82,7 +83,7 @@ struct alignas(16) OpF64 {
     int32_t n;
     int32_t adc0;
     int16_t pcls, ecls;
-    int16_t acls, rsv1;
+    int16_t acls, tab;  // as in OpF32
     int32_t rsv2;
     double f[13];
 };

@@ -536,7 +536,7 @@ def debug_compile(events, gamma_hz_per_t: float, snapshots=None):
 # Layout of one float64 device operation (128 bytes), for diagnostics.
 OP64_DTYPE = np.dtype(
     [("kind", "u1"), ("rsv0", "u1"), ("flags", "<u2"), ("n", "<i4"), ("adc0", "<i4"), ("pcls", "<i2"),
-     ("ecls", "<i2"), ("acls", "<i2"), ("rsv1", "<i2"), ("rsv2", "<i4"), ("f", "<f8", (13,))]
+     ("ecls", "<i2"), ("acls", "<i2"), ("tab", "<i2"), ("rsv2", "<i4"), ("f", "<f8", (13,))]
 )
 assert OP64_DTYPE.itemsize == 128
 OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN, OP_RF_TRAIN, OP_SNAP = 0, 1, 2, 3, 4, 5, 6
