@@ -71,11 +71,15 @@ def gpu_grads(M, ctx, torch, ph, ev, params, rf, h, ckpt=64):
 
 # up to 256 RF parameters each thread sums its RF gradients in local memory, beyond that every
 # pulse reduces over the warp; up to 1024 the forward pass is the library's forward kernel on a
-# parametric program, beyond that the adjoint's own forward kernel: every path is covered
-@pytest.mark.parametrize("seed,n_sp,ckpt,n_rf", [(0, 40, 64, 16), (1, 300, 7, 16), (2, 1, 1, 16), (3, 129, 128, 16),
-                                                (4, 70, 64, 300), (5, 33, 32, 256), (6, 20, 64, 1100)])
-def test_adjoint_matches_oracle_gradient(M, ctx, torch, oracle_mod, seed, n_sp, ckpt, n_rf):
+# parametric program, beyond that the adjoint's own forward kernel.  `n_par` declares that many
+# learnable flips (the pulse uses the first n_rf; the others get zero gradient), so every path
+# runs on the same well-conditioned sequences.
+@pytest.mark.parametrize("seed,n_sp,ckpt,n_rf,n_par", [(0, 40, 64, 16, 16), (1, 300, 7, 16, 16), (2, 1, 1, 16, 16),
+                                                      (3, 129, 128, 16, 16), (4, 70, 64, 300, 300),
+                                                      (5, 33, 32, 16, 256), (6, 20, 64, 16, 1100)])
+def test_adjoint_matches_oracle_gradient(M, ctx, torch, oracle_mod, seed, n_sp, ckpt, n_rf, n_par):
     ph, ev, params, rf, rng = shaped_case(seed, n_sp, n_rf=n_rf, n_tr=3 if n_rf <= 16 else 2)
+    rf = np.concatenate([rf, rng.uniform(-1.0, 1.0, n_par - n_rf)])
     sig_ref = oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf)
     target = oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf * 1.1) * 0.9
     h = 2 * (sig_ref - target)
