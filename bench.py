@@ -178,10 +178,28 @@ def cpu_baseline(w, seconds: float = 10.0, seed: int = 1):
     n = int(max(cores, min(w.phantom.n, seconds / max(per_spin, 1e-9))))
     sub = w.phantom.subset(np.sort(rng.choice(w.phantom.n, n, replace=False)))
     t0 = time.perf_counter()
-    oracle.signal(sub, w.sequence, n_threads=cores)
+    ref = oracle.signal(sub, w.sequence, n_threads=cores)
     el = time.perf_counter() - t0
     return {"value": n * w.sequence.n_events / el, "unit": "spin-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{w.name}: full sequence ({w.sequence.n_events} events) on {n} of {w.phantom.n} spins, {el:.1f} s"}, sub
+            "sample": f"{w.name}: full sequence ({w.sequence.n_events} events) on {n} of {w.phantom.n} spins, {el:.1f} s"}, \
+        (sub, ref)
+
+
+def oracle_parity(ctx, M, w, sub, ref, n_coils: int = 0):
+    """The GPU signal of the CPU baseline's spin sample in both precisions against the float64
+    oracle's signal of the same spins: relative L2 and dB (the error report per configuration)."""
+    p = M.Phantom.from_workload_phantom(ctx, sub)
+    s = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    out = {"sample_spins": int(sub.n)}
+    nr = float(np.linalg.norm(ref))
+    for name, prec in (("fp32", M.FP32), ("fp64", M.FP64)):
+        got = M.simulate(ctx, p, s, prec)
+        rel = float(np.linalg.norm(got - ref) / nr) if nr > 0 else 0.0
+        out[f"{name}_rel_l2"] = rel
+        out[f"{name}_db"] = 20 * math.log10(rel) if rel > 0 else None
+    p.close()
+    s.close()
+    return out
 
 
 def run_reference(args):
@@ -275,9 +293,10 @@ def run_batch(args):
     }
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample of the batch's longest program
         wl = max(ws, key=lambda w: w.sequence.n_events)
-        cb, _ = cpu_baseline(wl, seconds=args.cpu_seconds)
+        cb, (sub, ref) = cpu_baseline(wl, seconds=args.cpu_seconds)
         cb["sample"] = "c4 phantom " + cb["sample"]
         line["cpu_baseline"] = cb
+        line["oracle_parity"] = dict(oracle_parity(ctx, M, wl, sub, ref), phantom=wl.name)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -448,13 +467,19 @@ def run_kt(args):
     if not args.no_cpu_baseline:
         from oracle import kt as ORK
 
-        nb, t0 = 0, time.perf_counter()
+        nb, t0, refs = 0, time.perf_counter(), []
         while time.perf_counter() - t0 < args.cpu_seconds and nb < n_sets:
-            ORK.simulate(d.t1[nb:nb + 1], d.t2[nb:nb + 1], d.b1[nb:nb + 1], d.df[nb:nb + 1], steps, K)
+            refs.append(ORK.simulate(d.t1[nb:nb + 1], d.t2[nb:nb + 1], d.b1[nb:nb + 1], d.df[nb:nb + 1], steps, K)[0])
             nb += 1
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": nb * len(steps) / dt, "unit": "ensemble-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{nb} of {n_sets} ensembles, full train, {dt:.1f} s (numpy, one core)"}
+        # the GPU's samples of those ensembles (last timed step) against the oracle's
+        got = out.view(torch.complex128).view(n_sets, n_samples)[:nb].cpu().numpy()
+        ref = np.stack(refs)
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        line["oracle_parity"] = {"sample_ensembles": nb, f"{'fp64' if prec == M.FP64 else 'fp32'}_rel_l2": rel,
+                                 f"{'fp64' if prec == M.FP64 else 'fp32'}_db": 20 * math.log10(rel) if rel > 0 else None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -652,8 +677,9 @@ def run_ours(args):
                                   "uploads, kernel and read-back (first compile not overlapped)",
                       "serial_ms_per_step": serial_s * 1e3}
         if not args.no_cpu_baseline:
-            cb, _ = cpu_baseline(w, seconds=args.cpu_seconds)
+            cb, (sub, ref) = cpu_baseline(w, seconds=args.cpu_seconds)
             out["cpu_baseline"] = cb
+            out["oracle_parity"] = oracle_parity(ctx, M, w, sub, ref)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
