@@ -27,7 +27,8 @@ struct Compiled {
 // recorded (§7.2: magnetisation data at chosen times).
 // rf_param: NULL, or per event a learnable-flip index in [0, n_params) or -1.  Events with an index
 // become parametric pulses: their (cos α, sin α) are read at run time from sub-pulse table entry
-// index (the table's first n_params entries, which the caller fills before each launch).
+// index (the table's first n_params entries, which the caller fills before each launch).  Only the
+// float64 kernel reads such tables; the float32 program of a parametric compile is not runnable.
 int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled &out, std::string &err,
                      int64_t n_snap = 0, const int64_t *snap_after = nullptr, const int32_t *rf_param = nullptr,
                      int32_t n_params = 0);

@@ -400,14 +400,17 @@ struct Spins {
         }
     }
     // the op's own rotation, or for a parametric pulse the one in sub-pulse table entry op.tab
+    // (parametric programs drive the float64 adjoint forward only; the float32 kernels skip the test)
     __device__ __forceinline__ void rf_turn_op(const Op &op) {
-        if (op.flags & F_RFTAB) {
-            P ca, sa, nsa;
-            load_train(op.tab, ca, sa, nsa);
-            rf_turn(ca, sa, nsa);
-        } else {
-            rf_turn_s((R)op.f[0], (R)op.f[1]);
+        if constexpr (F64) {
+            if (op.flags & F_RFTAB) {
+                P ca, sa, nsa;
+                load_train(op.tab, ca, sa, nsa);
+                rf_turn(ca, sa, nsa);
+                return;
+            }
         }
+        rf_turn_s((R)op.f[0], (R)op.f[1]);
     }
     __device__ __forceinline__ void rf_turn_s(R ca, R sa) {
         P c, s, ns;
