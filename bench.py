@@ -41,6 +41,7 @@ METRIC = "spin-steps/s (isochromat×event updates) at 1 GB300, FP32 vs FP64, % F
 #   other    : precession (4); T1 recovery is folded into the next pulse
 OPS_ADC, OPS_RF, OPS_OTHER = 6, 10, 4
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 float64 (profiling recipe; no measured figure)
 
 
 def algorithmic_ops_per_spin(events, n_coils: int = 0) -> int:
@@ -66,6 +67,15 @@ def ring_coils(phantom, n_coils: int, radius: float = 0.3, width: float = 0.25):
 
 def fp32_alu_peak_ops(sm_mhz: float = SM_MAX_MHZ) -> float:
     return SMS * FP32_LANES * sm_mhz * 1e6
+
+
+def fp64_roofline(achieved_g: float) -> dict:
+    """Algorithmic lane-ops of a float64 run against the float64 FMA rate (G lane-ops/s)."""
+    peak = FP64_NOMINAL_GFLOPS / 2
+    return {"bound": "fp64", "achieved": achieved_g, "peak": peak, "unit": "G float64 lane-ops/s",
+            "frac": achieved_g / peak, "traffic": None,
+            "peak_basis": "nominal float64 rate of the profiling recipe, 1.25 TFLOP/s = 0.625 T FMA lane-ops/s "
+                          "(no measured float64 figure)"}
 
 
 def build_workload(name: str, rank: int = 0):
@@ -307,7 +317,6 @@ def run_batch(args):
 # 6 when the flip is learnable, precession 8, T1 3, parameter gradients 12).
 ADJ_FLOPS_FWD_RF, ADJ_FLOPS_FWD = 18, 11
 ADJ_FLOPS_BWD_RF, ADJ_FLOPS_BWD = 42, 23
-FP64_NOMINAL_GFLOPS = 1250.0  # GB300 float64 (profiling recipe; no measured figure)
 
 
 def run_adjoint(args):
@@ -458,11 +467,11 @@ def run_kt(args):
                        "n_steps": len(steps), "max_order": K, "n_samples": n_samples,
                        "order_steps_per_step": ens_steps * (K + 1),
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s",
-                         "frac": achieved / peak,
-                         "traffic": traffic_for(kernel_source_sha(KT_SOURCES), f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}")
-                         if prec == M.FP32 else None, "kernel_ms": ms,
-                         "ops_per_order_step": KT_OPS_PER_ORDER},
+            "roofline": dict(fp64_roofline(achieved), kernel_ms=ms, ops_per_order_step=KT_OPS_PER_ORDER)
+            if prec == M.FP64 else
+            {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
+             "traffic": traffic_for(kernel_source_sha(KT_SOURCES), f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}"),
+             "kernel_ms": ms, "ops_per_order_step": KT_OPS_PER_ORDER},
             "gpu_launches": 2 * args.steps, "clocks": ck}
     if not args.no_cpu_baseline:
         from oracle import kt as ORK
@@ -582,12 +591,15 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
     ops = algorithmic_ops_per_spin(w.sequence.events, n_coils) * w.phantom.n
     achieved = ops / (kern_ms * 1e-3) / 1e9
-    peak = fp32_alu_peak_ops() / 1e9
     sha = kernel_source_sha()
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
-            "traffic": traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else "")), "kernel_ms": kern_ms,
-            "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
-            "ops_per_spin_step": ops / spin_steps}
+    if prec == M.FP64:  # the same algorithmic lane-ops against the float64 FMA rate
+        roof = dict(fp64_roofline(achieved), kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps)
+    else:
+        peak = fp32_alu_peak_ops() / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
+                "traffic": traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else "")), "kernel_ms": kern_ms,
+                "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
+                "ops_per_spin_step": ops / spin_steps}
 
     out = {}
     if rank == 0 and not args.skip_extra and not n_coils:
@@ -614,12 +626,7 @@ def run_ours(args):
         key = "fp64_gpu" if prec == M.FP32 else "fp32_gpu"
         out[key] = {"value": spin_steps / (o_ms * 1e-3), "unit": "spin-steps/s", "ms_per_step": o_ms}
         if key == "fp64_gpu":  # the same algorithmic lane-ops against the float64 FMA rate
-            f64_peak = FP64_NOMINAL_GFLOPS / 2
-            f64_ach = ops / (o_ms * 1e-3) / 1e9
-            out[key]["roofline"] = {"bound": "fp64", "achieved": f64_ach, "peak": f64_peak,
-                                    "unit": "G float64 lane-ops/s", "frac": f64_ach / f64_peak,
-                                    "peak_basis": "nominal float64 rate of the profiling recipe, 1.25 TFLOP/s "
-                                                  "= 0.625 T FMA lane-ops/s (no measured float64 figure)"}
+            out[key]["roofline"] = fp64_roofline(ops / (o_ms * 1e-3) / 1e9)
         out["fp32_vs_fp64_gpu_rel_l2"] = rel
         out["fp32_vs_fp64_gpu_db"] = 20 * math.log10(rel) if rel > 0 else None
 
