@@ -253,7 +253,8 @@ __device__ __forceinline__ void step_coef(Coef<P> &o, const StepT &s, R b1, R r1
 
 constexpr int KT_WARPS = 4;  // warps (ensembles) per block
 
-template <typename R, int M, typename StepT>
+// FULL: every stored order exists (K = 32·M − 1), so shifts never drop a population
+template <typename R, int M, typename StepT, bool FULL>
 __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
     using E = Ensemble<R, M>;
     using P = typename E::P;
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
     E e;
     e.lane = lane;
     e.K = a.max_order;
-    e.full = a.max_order == 32 * M - 1;
+    e.full = FULL;
 #pragma unroll
     for (int s = 0; s < M; ++s) e.apr[s] = e.api[s] = e.anr[s] = e.ani[s] = e.bzr[s] = e.bzi[s] = (R)0;
     if (lane == 0) e.bzr[0] = (R)1;
@@ -296,6 +297,14 @@ __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
         for (int k = 0; k < cnt; ++k) {
             const Coef<P> &c = cw[k];
             const int fl = c.flags;
+            if (FULL && fl == (512 | 256 | 129)) {  // the common step: pulse, one order up, sample
+                e.pulse(c);
+                e.shift_up();
+                e.relax(c);
+                const R sr = __shfl_sync(FULLW, e.apr[0], 0), si = __shfl_sync(FULLW, e.api[0], 0);
+                if (lane == k) mine = Cx<R>{sr, si};
+                continue;
+            }
             if (fl & 512) e.pulse(c);
             const int q = (fl & 255) - 128;
             for (int i = 0; i < q; ++i) e.shift_up();
@@ -324,16 +333,20 @@ int launch_kt_t(const KtArgs &a, void *stream) {
     if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
     const int M = (a.max_order + 32) / 32;  // slots per lane
     cudaStream_t st = (cudaStream_t)stream;
+    // FULL: K = 32·M − 1 for the slot count the kernel is built for, so no order is ever dropped
+    const bool full = a.max_order + 1 == 32 * (M <= 1 ? 1 : M <= 2 ? 2 : M <= 4 ? 4 : 8);
+#define KTL(MM) (full ? kt_kernel<R, MM, StepT, true><<<(unsigned)blocks, threads, 0, st>>>(a)                       : kt_kernel<R, MM, StepT, false><<<(unsigned)blocks, threads, 0, st>>>(a))
     if (M <= 1)
-        kt_kernel<R, 1, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
+        KTL(1);
     else if (M <= 2)
-        kt_kernel<R, 2, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
+        KTL(2);
     else if (M <= 4)
-        kt_kernel<R, 4, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
+        KTL(4);
     else if (M <= 8)
-        kt_kernel<R, 8, StepT><<<(unsigned)blocks, threads, 0, st>>>(a);
+        KTL(8);
     else
         return (int)cudaErrorInvalidValue;
+#undef KTL
     return (int)cudaGetLastError();
 }
 

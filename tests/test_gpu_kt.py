@@ -42,11 +42,12 @@ def both(M, ctx, d, steps, K):
     return ref, g64, g32
 
 
-def test_fingerprint_dictionary(M, ctx):
+@pytest.mark.parametrize("K", [100, 127])  # 127 fills 4 slots per lane: the kernel's fast step
+def test_fingerprint_dictionary(M, ctx, K):
     rng = np.random.default_rng(1300)
     d = W.kt_dictionary(67, rng)  # 17 blocks of 4 ensembles, ragged
     steps = W.kt_fingerprint_sequence(300, rng)
-    ref, g64, g32 = both(M, ctx, d, steps, 100)
+    ref, g64, g32 = both(M, ctx, d, steps, K)
     assert rel_l2(g64, ref) <= TOL64
     assert rel_l2(g32, ref) <= TOL32
 
