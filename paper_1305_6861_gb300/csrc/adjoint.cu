@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
     for (int q = threadIdx.x; q < a.n_params; q += blockDim.x) grf[q] = 0.0;
     const int lane = threadIdx.x & 31;
     const bool valid = s < a.n_spins;
-    double buf[ADJ_MAX_SEG][3];  // states after each event's pulse, for the segment
+    double buf[ADJ_MAX_SEG][5];  // per event of the segment: state after its pulse, then the transverse state after it
     double gl[LOCAL ? ADJ_LOCAL_PARAMS : 1];
     if constexpr (LOCAL)
         for (int q = 0; q < a.n_params; ++q) gl[q] = 0.0;
@@ -338,6 +338,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
             buf[i][1] = M[1];
             buf[i][2] = M[2];
             after_pulse(e, p, tab, M);
+            buf[i][3] = M[0];
+            buf[i][4] = M[1];
         }
         for (int i = m - 1; i >= 0; --i) {
             const AdjEvent &e = sev[i];
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
             double wr, wi, e1;
             factors(e, p, tab, wr, wi, e1);
             // parameter gradients through P (λ is the adjoint after the event)
-            const double mx = Ma[0] * wr - Ma[1] * wi, my = Ma[0] * wi + Ma[1] * wr;
+            const double mx = buf[i][3], my = buf[i][4];  // P·M_a, transverse part
             g_r2 += -e.dt * (L[0] * mx + L[1] * my);
             g_r1 += -e.dt * e1 * (Ma[2] - p.rho) * L[2];
             g_rho += (1.0 - e1) * L[2];
