@@ -302,3 +302,21 @@ def test_concurrent_compiles_are_identical(mrsim_lib):
         r = ref[i % 4]
         for k in r:
             assert np.array_equal(r[k].view(np.uint8), d[k].view(np.uint8)), (i, k)
+
+
+def test_compile_argument_checks(mrsim_lib):
+    import ctypes
+
+    L = mrsim_lib.lib()
+    ev = np.ascontiguousarray(W.config1().sequence.events)
+    assert L.mrsim_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), W.GAMMA_BAR, 0, None, None) == 1
+    assert "NULL" in L.mrsim_compile_last_error().decode()
+    h = ctypes.c_void_p()
+    assert L.mrsim_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), W.GAMMA_BAR, 0, None, ctypes.byref(h)) == 0
+    assert L.mrsim_compile_last_error().decode() == "" and L.mrsim_compiled_num_adc(h) == 4096
+    L.mrsim_compiled_destroy(h)
+    assert L.mrsim_compiled_num_adc(None) == -1 and L.mrsim_compiled_upload_bytes(None) == -1
+    L.mrsim_compiled_destroy(None)
+    snaps = np.array([5, 3], dtype=np.int64)  # not increasing
+    assert L.mrsim_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), W.GAMMA_BAR, 2,
+                           ctypes.c_void_p(snaps.ctypes.data), ctypes.byref(h)) == 1
