@@ -103,6 +103,11 @@ const char *mrsim_last_error(const mrsim_ctx *ctx);
 /* Synchronise `stream` (cudaStream_t, NULL = legacy default stream) and report any device-side
  * status recorded by kernels of this context (e.g. MRSIM_ETIMEOUT); clears the status word. */
 mrsim_status mrsim_stream_status(mrsim_ctx *ctx, void *stream);
+/* Diagnostic: launches on `stream` one block that runs the kernels' bounded mbarrier wait on a
+ * barrier nothing completes, with limit_ns (1e3 .. 1e9) instead of the 2 s of the op pipeline; the
+ * wait runs out, the block records MRSIM_ETIMEOUT in the status word and ends.  This is how the
+ * timeout path is tested without any fault; the context stays usable. */
+mrsim_status mrsim_debug_wait_timeout(mrsim_ctx *ctx, int64_t limit_ns, void *stream);
 
 /* ---- phantom: the object as a list of isochromats (§6.1.1, Eq. 6.2) ------------------- */
 

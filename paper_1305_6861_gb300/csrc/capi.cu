@@ -120,6 +120,15 @@ const char *mrsim_status_string(mrsim_status s) {
     return "unknown status";
 }
 
+mrsim_status mrsim_debug_wait_timeout(mrsim_ctx *ctx, int64_t limit_ns, void *stream) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (limit_ns < 1000 || limit_ns > 1000000000) return fail(ctx, MRSIM_EINVAL, "limit_ns must be in [1e3, 1e9]");
+    cudaSetDevice(ctx->device);
+    const int rc = launch_wait_probe(ctx->d_status, (uint64_t)limit_ns, stream);
+    if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "wait probe");
+    return MRSIM_OK;
+}
+
 const char *mrsim_last_error(const mrsim_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 mrsim_status mrsim_context_create(int device, mrsim_ctx **out) {

@@ -2,6 +2,25 @@
 #include "fwd_kernel.cuh"
 
 namespace mrsim {
+namespace dev {
+// Diagnostic: the op-stream pipeline's bounded wait on an mbarrier that nothing completes (no copy
+// is issued and nobody arrives), so that the timeout path (status word, no fault, the context
+// stays usable) can be exercised on purpose.
+__global__ void wait_probe_kernel(int *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_ns)) atomicCAS(status, 0, (int)MRSIM_ETIMEOUT);
+}
+}  // namespace dev
+
+int launch_wait_probe(int *status, uint64_t limit_ns, void *stream) {
+    dev::wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(status, limit_ns);
+    return (int)cudaGetLastError();
+}
 
 int launch_fwd_f64(const FwdArgs &a, int k, int threads, void *stream) {
     switch (k) {

@@ -77,6 +77,7 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t pari
 }
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s for one 4 KB chunk: only a fault takes that long
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int RED_STRIDE = SAMPLE_WINDOW_F64 + 16;  // float64: per-warp, per-component window row
 constexpr int WIN_STRIDE = SAMPLE_WINDOW_F32 + 16;  // float32: block-wide window, per component

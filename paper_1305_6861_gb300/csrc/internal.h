@@ -157,6 +157,8 @@ int launch_batch(bool fp64, const BatchArgs &b, int spins_per_thread, int thread
 int batch_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
 int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
+// one block whose bounded mbarrier wait runs out after limit_ns and records MRSIM_ETIMEOUT in *status
+int launch_wait_probe(int *status, uint64_t limit_ns, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
 // K-t formalism (kt_kernel.cu): one step per elementary sequence, with the pulse's phase terms
 // precomputed on the host.

@@ -40,7 +40,7 @@ EXPORTS = (
     "mrsim_batch_destroy", "mrsim_simulate_batch", "mrsim_simulate_batch_static",
     "mrsim_adjoint_create", "mrsim_adjoint_num_adc", "mrsim_adjoint_forward", "mrsim_adjoint_backward",
     "mrsim_adjoint_destroy", "mrsim_compile", "mrsim_compile_last_error", "mrsim_compiled_num_adc",
-    "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create",
+    "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
 )
 
 
@@ -137,6 +137,7 @@ def lib():
             "mrsim_compiled_upload_bytes": (i64, [vp]),
             "mrsim_compiled_destroy": (None, [vp]),
             "mrsim_sequence_create": (ctypes.c_int, [vp, vp, P(vp)]),
+            "mrsim_debug_wait_timeout": (ctypes.c_int, [vp, i64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -289,3 +289,17 @@ def test_sequence_from_host_compiled_program(M, ctx, oracle_mod):
     s.close()
     plain.close()
     p.close()
+
+
+def test_bounded_wait_timeout_is_reported(M, ctx, oracle_mod):
+    """Failure detection without a fault: the kernels' bounded mbarrier wait, run on a barrier that
+    nothing completes with a 20 ms limit, gives up, records MRSIM_ETIMEOUT in the status word,
+    which the next status read reports and clears; the context keeps working."""
+    L = M.lib()
+    assert L.mrsim_debug_wait_timeout(ctx.h, 20_000_000, None) == 0
+    assert L.mrsim_stream_status(ctx.h, None) == 4  # MRSIM_ETIMEOUT
+    assert L.mrsim_stream_status(ctx.h, None) == 0  # cleared
+    assert L.mrsim_debug_wait_timeout(ctx.h, 10, None) == 1  # limit outside [1e3, 1e9] ns
+    w = W.config1()
+    ref = oracle_mod.signal(w)
+    assert rel_l2(run(M, ctx, w.phantom, w.sequence, M.FP64), ref) <= TOL64
