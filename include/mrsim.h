@@ -100,6 +100,15 @@ void mrsim_context_destroy(mrsim_ctx *ctx);
 const char *mrsim_status_string(mrsim_status s);
 /* Message of the last failed call on ctx ("" if none).  Owned by ctx, valid until the next call. */
 const char *mrsim_last_error(const mrsim_ctx *ctx);
+/* Failure log: fn(status, message, user) is called, on the calling thread, for every failed call
+ * of any context and for every failed mrsim_compile; NULL removes it.  With the environment
+ * variable MRSIM_LOG set (to anything but "0") the same messages also go to stderr. */
+typedef void (*mrsim_log_fn)(mrsim_status status, const char *message, void *user);
+void mrsim_set_log_callback(mrsim_log_fn fn, void *user);
+/* Test hook: the device allocation that follows `after` further successful ones on this context
+ * fails once with MRSIM_ENOMEM, as a full device would (after < 0 switches the hook off), so that
+ * the out-of-memory paths can be tested without exhausting the device. */
+mrsim_status mrsim_debug_fail_alloc(mrsim_ctx *ctx, int32_t after);
 /* Synchronise `stream` (cudaStream_t, NULL = legacy default stream) and report any device-side
  * status recorded by kernels of this context (e.g. MRSIM_ETIMEOUT); clears the status word. */
 mrsim_status mrsim_stream_status(mrsim_ctx *ctx, void *stream);
@@ -363,8 +372,11 @@ mrsim_status mrsim_debug_compile_snapshots(int64_t n_events, const mrsim_event *
  * and keeps the fastest in the context, keyed by precision, spin count and the compiled program's
  * size and class tables; later mrsim_simulate / mrsim_simulate_ex calls without an explicit shape
  * on any phantom/sequence with the same key use it.  Returns the shape in
- * best->spins_per_thread / best->threads_per_block (other fields zeroed).  Synchronises `stream`;
- * tuning again replaces the entry. */
+ * best->spins_per_thread / best->threads_per_block (other fields zeroed).  Synchronises `stream`.
+ * A key the context already holds is answered without timing.  With the environment variable
+ * MRSIM_AUTOTUNE_CACHE naming a file, contexts load the shapes tuned on a device with the same SM
+ * count from it when they are created and append every new one, so other processes skip the
+ * timing. */
 mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
                             mrsim_precision prec, void *stream, mrsim_options *best);
 

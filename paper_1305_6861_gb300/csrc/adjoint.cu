@@ -411,6 +411,7 @@ namespace {
 
 mrsim_status afail(mrsim_ctx *ctx, mrsim_status st, const std::string &m) {
     if (ctx) ctx->err = m;
+    log_failure(st, m);
     return st;
 }
 
@@ -610,7 +611,7 @@ mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, 
         cudaFree(adj->d_ckpt);
         adj->d_ckpt = nullptr;
         adj->ckpt_cap = 0;
-        cudaError_t e = cudaMalloc(&adj->d_ckpt, need * sizeof(double));
+        cudaError_t e = ctx_malloc(ctx, &adj->d_ckpt, need * sizeof(double));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return afail(ctx, MRSIM_ENOMEM, "checkpoint storage: " + std::to_string(need * 8) + " bytes");

@@ -1,10 +1,17 @@
 // capi.cu -- the C-ABI of libmrsim (see include/mrsim.h): handles, validation, memory, launches.
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <memory>
 #include <new>
@@ -19,10 +26,29 @@
 
 using namespace mrsim;
 
+
 namespace {
+
+std::atomic<mrsim_log_fn> g_log_fn{nullptr};
+std::atomic<void *> g_log_user{nullptr};
+
+bool env_log() {
+    static const bool on = [] {
+        const char *v = std::getenv("MRSIM_LOG");
+        return v && *v && std::strcmp(v, "0") != 0;
+    }();
+    return on;
+}
+
+// One NVTX range per public call, visible in nsys / ncu --nvtx timelines (free without a tool).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 mrsim_status fail(mrsim_ctx *ctx, mrsim_status st, const std::string &msg) {
     if (ctx) ctx->err = msg;
+    log_failure(st, msg);
     return st;
 }
 
@@ -56,7 +82,7 @@ mrsim_status grow(mrsim_ctx *ctx, double **buf, size_t *cap, size_t need_doubles
     *buf = nullptr;
     *cap = 0;
     size_t n = std::max<size_t>(need_doubles, 1024);
-    CK(cudaMalloc(buf, n * sizeof(double)), "cudaMalloc scratch");
+    CK(ctx_malloc(ctx, buf, n * sizeof(double)), "cudaMalloc scratch");
     *cap = n;
     return MRSIM_OK;
 }
@@ -68,7 +94,7 @@ mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStr
     p->n = n;
     p->n_pad = (n + 31) / 32 * 32;
     if (n > 0) {
-        cudaError_t e = cudaMalloc(&p->params, (size_t)NPARAM * p->n_pad * sizeof(double));
+        cudaError_t e = ctx_malloc(ctx, &p->params, (size_t)NPARAM * p->n_pad * sizeof(double));
         if (e != cudaSuccess) {
             delete p;
             return cuda_fail(ctx, e, "cudaMalloc phantom");
@@ -97,6 +123,34 @@ mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStr
     return MRSIM_OK;
 }
 
+// MRSIM_AUTOTUNE_CACHE: one line per tuned shape, "mrsim-tune-1 <SMs> <key x 7> <K> <threads> <ms>";
+// lines of another SM count or malformed ones are ignored.
+void load_tune_cache(mrsim_ctx *ctx) {
+    std::ifstream in(ctx->tune_cache);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream is(line);
+        std::string tag;
+        int sms = 0;
+        TuneKey key{};
+        TunedShape sh;
+        if (!(is >> tag >> sms) || tag != "mrsim-tune-1" || sms != ctx->num_sms) continue;
+        bool ok = true;
+        for (auto &v : key) ok = ok && static_cast<bool>(is >> v);
+        if (ok && (is >> sh.k >> sh.threads >> sh.ms) && sh.k > 0 && sh.threads > 0) ctx->tuned[key] = sh;
+    }
+}
+
+void save_tune_entry(const mrsim_ctx *ctx, const TuneKey &key, const TunedShape &sh) {
+    if (ctx->tune_cache.empty()) return;
+    std::ostringstream os;
+    os << "mrsim-tune-1 " << ctx->num_sms;
+    for (int64_t v : key) os << ' ' << v;
+    os << ' ' << sh.k << ' ' << sh.threads << ' ' << sh.ms << '\n';
+    std::ofstream out(ctx->tune_cache, std::ios::app);  // one short append per entry
+    out << os.str();
+}
+
 TuneKey tune_key(mrsim_precision prec, const mrsim_phantom *ph, const mrsim_sequence *seq) {
     const Compiled &c = seq->prog->host;
     return TuneKey{(int64_t)prec, ph->n, (int64_t)c.ops32.size(), c.n_pcls, c.n_e1, c.n_e2,
@@ -105,6 +159,11 @@ TuneKey tune_key(mrsim_precision prec, const mrsim_phantom *ph, const mrsim_sequ
 
 
 }  // namespace
+
+void mrsim::log_failure(mrsim_status st, const std::string &msg) {
+    if (mrsim_log_fn f = g_log_fn.load()) f(st, msg.c_str(), g_log_user.load());
+    if (env_log()) std::fprintf(stderr, "mrsim: %s: %s\n", mrsim_status_string(st), msg.c_str());
+}
 
 extern "C" {
 
@@ -118,6 +177,17 @@ const char *mrsim_status_string(mrsim_status s) {
     case MRSIM_EUNSUPPORTED: return "unsupported";
     }
     return "unknown status";
+}
+
+void mrsim_set_log_callback(mrsim_log_fn fn, void *user) {
+    g_log_user.store(user);
+    g_log_fn.store(fn);
+}
+
+mrsim_status mrsim_debug_fail_alloc(mrsim_ctx *ctx, int32_t after) {
+    if (!ctx) return MRSIM_EINVAL;
+    ctx->fail_alloc = after < 0 ? -1 : after;
+    return MRSIM_OK;
 }
 
 mrsim_status mrsim_debug_wait_timeout(mrsim_ctx *ctx, int64_t limit_ns, void *stream) {
@@ -147,6 +217,10 @@ mrsim_status mrsim_context_create(int device, mrsim_ctx **out) {
     if (!ctx) return MRSIM_ENOMEM;
     ctx->device = device;
     ctx->num_sms = prop.multiProcessorCount;
+    if (const char *cache = std::getenv("MRSIM_AUTOTUNE_CACHE")) {
+        ctx->tune_cache = cache;
+        load_tune_cache(ctx);
+    }
     cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&ctx->d_bad, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
@@ -189,6 +263,7 @@ mrsim_status mrsim_stream_status(mrsim_ctx *ctx, void *stream) {
 mrsim_status mrsim_phantom_create(mrsim_ctx *ctx, int64_t n, const double *x, const double *y, const double *z,
                                   const double *rho, const double *t1, const double *t2, const double *dw,
                                   mrsim_phantom **out) {
+    Range nvtx_range("mrsim_phantom_create");
     if (!ctx || !out) return MRSIM_EINVAL;
     *out = nullptr;
     if (n < 0) return fail(ctx, MRSIM_EINVAL, "n_spins < 0");
@@ -211,6 +286,7 @@ mrsim_status mrsim_phantom_create(mrsim_ctx *ctx, int64_t n, const double *x, co
 mrsim_status mrsim_phantom_create_device(mrsim_ctx *ctx, int64_t n, const double *x, const double *y,
                                          const double *z, const double *rho, const double *t1, const double *t2,
                                          const double *dw, void *stream, mrsim_phantom **out) {
+    Range nvtx_range("mrsim_phantom_create_device");
     if (!ctx || !out) return MRSIM_EINVAL;
     *out = nullptr;
     if (n < 0) return fail(ctx, MRSIM_EINVAL, "n_spins < 0");
@@ -288,6 +364,7 @@ extern "C" {
 
 mrsim_status mrsim_compile(int64_t n_events, const mrsim_event *events, double gamma, int64_t n_snap,
                            const int64_t *snap_after, mrsim_compiled **out) {
+    Range nvtx_range("mrsim_compile");
     t_compile_err.clear();
     if (!out) {
         t_compile_err = "NULL output handle";
@@ -303,6 +380,7 @@ mrsim_status mrsim_compile(int64_t n_events, const mrsim_event *events, double g
     mrsim_status rc = compile_host(n_events, events, gamma, n_snap, snap_after, prog, err);
     if (rc != MRSIM_OK) {
         t_compile_err = err;
+        log_failure(rc, err);
         return rc;
     }
     mrsim_compiled *c = new (std::nothrow) mrsim_compiled();
@@ -324,6 +402,7 @@ int64_t mrsim_compiled_upload_bytes(const mrsim_compiled *c) { return c ? (int64
 void mrsim_compiled_destroy(mrsim_compiled *c) { delete c; }
 
 mrsim_status mrsim_sequence_create(mrsim_ctx *ctx, const mrsim_compiled *c, mrsim_sequence **out) {
+    Range nvtx_range("mrsim_sequence_create");
     if (!ctx || !out) return MRSIM_EINVAL;
     *out = nullptr;
     if (!c) return fail(ctx, MRSIM_EINVAL, "NULL compiled program");
@@ -335,7 +414,7 @@ mrsim_status mrsim_sequence_create(mrsim_ctx *ctx, const mrsim_compiled *c, mrsi
     const HostProgram &h = *s->prog;
     cudaSetDevice(ctx->device);
     if (!h.image.empty()) {  // one allocation and one copy for every table
-        cudaError_t e = cudaMalloc(&s->d_image, h.image.size());
+        cudaError_t e = ctx_malloc(ctx, &s->d_image, h.image.size());
         if (e == cudaSuccess) e = cudaMemcpy(s->d_image, h.image.data(), h.image.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             mrsim_sequence_destroy(s);
@@ -404,6 +483,7 @@ void mrsim_sequence_destroy(mrsim_sequence *s) {
 mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
                                mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc,
                                const mrsim_options *opt) {
+    Range nvtx_range("mrsim_simulate");
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
@@ -489,6 +569,7 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
 mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
                                   mrsim_precision prec, void *stream, int32_t n_coils, const double *sens,
                                   double *signal_out, int64_t n_adc) {
+    Range nvtx_range("mrsim_simulate_coils");
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
@@ -559,6 +640,7 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
                                const double *b1, const double *df, int64_t n_steps, const mrsim_kt_step *steps,
                                int32_t max_order, mrsim_precision prec, void *stream, double *signal_out,
                                int64_t n_samples) {
+    Range nvtx_range("mrsim_kt_simulate");
     if (!ctx) return MRSIM_EINVAL;
     if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_sets < 0 || n_steps < 0) return fail(ctx, MRSIM_EINVAL, "negative count");
@@ -698,6 +780,7 @@ mrsim_status mrsim_max_config_k(int64_t n_events, const mrsim_event *events, dou
 
 mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq, mrsim_precision prec,
                             void *stream, mrsim_options *best) {
+    Range nvtx_range("mrsim_autotune");
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq || !best) return fail(ctx, MRSIM_EINVAL, "NULL argument");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
@@ -708,6 +791,12 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     if (ph->n == 0) {
         best->spins_per_thread = def.k;
         best->threads_per_block = def.threads;
+        return MRSIM_OK;
+    }
+    const auto known = ctx->tuned.find(tune_key(prec, ph, seq));  // tuned before, or in the cache file
+    if (known != ctx->tuned.end()) {
+        best->spins_per_thread = known->second.k;
+        best->threads_per_block = known->second.threads;
         return MRSIM_OK;
     }
     cudaSetDevice(ctx->device);
@@ -781,6 +870,7 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     if (ss != MRSIM_OK) return ss;
     if (win.k == 0) return fail(ctx, MRSIM_EUNSUPPORTED, "no launch shape fits this program on the device");
     ctx->tuned[tune_key(prec, ph, seq)] = win;
+    save_tune_entry(ctx, tune_key(prec, ph, seq), win);
     best->spins_per_thread = win.k;
     best->threads_per_block = win.threads;
     return MRSIM_OK;
@@ -848,7 +938,7 @@ mrsim_status batch_layout(mrsim_batch *b, int k, int threads) {
     cudaFree(b->d_items);
     b->d_items = nullptr;
     if (!items.empty()) {
-        CK(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)), "cudaMalloc batch items");
+        CK(ctx_malloc(ctx, &b->d_items, items.size() * sizeof(BatchItem)), "cudaMalloc batch items");
         CK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice), "upload items");
     }
     b->items.swap(items);
@@ -925,10 +1015,10 @@ mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *
         return st;
     };
     if (n > 0) {
-        cudaError_t e = cudaMalloc(&b->d_descs, b->descs.size() * sizeof(FwdArgs));
+        cudaError_t e = ctx_malloc(ctx, &b->d_descs, b->descs.size() * sizeof(FwdArgs));
         if (e == cudaSuccess)
             e = cudaMemcpy(b->d_descs, b->descs.data(), b->descs.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_head, sizeof(int));
+        if (e == cudaSuccess) e = ctx_malloc(ctx, &b->d_head, sizeof(int));
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "batch descriptors"));
     }
     // default shape: the single-phantom heuristic for the largest phantom, shrunk until it fits
@@ -973,7 +1063,7 @@ mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *b
     for (auto &a : trunc) a.signal = ctx->d_sig;  // all phantoms add into one scratch buffer
     for (auto &a : warm) a.signal = ctx->d_sig;
     FwdArgs *d_trunc = nullptr;
-    CK(cudaMalloc(&d_trunc, 2 * trunc.size() * sizeof(FwdArgs)), "cudaMalloc tuning descriptors");
+    CK(ctx_malloc(ctx, &d_trunc, 2 * trunc.size() * sizeof(FwdArgs)), "cudaMalloc tuning descriptors");
     FwdArgs *d_warm = d_trunc + trunc.size();
     CK(cudaMemcpy(d_trunc, trunc.data(), trunc.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice), "upload tuning descriptors");
     CK(cudaMemcpy(d_warm, warm.data(), warm.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice), "upload tuning descriptors");
@@ -1037,12 +1127,14 @@ mrsim_status mrsim_batch_set_shape(mrsim_batch *b, int32_t spins_per_thread, int
 }
 
 mrsim_status mrsim_batch_launch(mrsim_batch *b, void *stream) {
+    Range nvtx_range("mrsim_batch_launch");
     if (!b) return MRSIM_EINVAL;
     cudaSetDevice(b->ctx->device);
     return batch_enqueue(b, b->d_descs, (cudaStream_t)stream);
 }
 
 mrsim_status mrsim_batch_launch_graph(mrsim_batch *b, void *stream) {
+    Range nvtx_range("mrsim_batch_launch_graph");
     if (!b) return MRSIM_EINVAL;
     mrsim_ctx *ctx = b->ctx;
     cudaSetDevice(ctx->device);

@@ -27,6 +27,8 @@ using TuneKey = std::array<int64_t, 7>;
 
 struct mrsim_ctx {
     std::map<TuneKey, TunedShape> tuned;
+    std::string tune_cache;  // MRSIM_AUTOTUNE_CACHE: file that keeps tuned shapes across processes
+    int fail_alloc = -1;     // test hook: device allocations left before one fails (-1: off)
     int device = 0;
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -55,6 +57,23 @@ struct mrsim_phantom {
 };
 
 namespace mrsim {
+// Device allocation for the library's handles; honours the context's failure-injection hook
+// (mrsim_debug_fail_alloc), which makes one chosen allocation report out-of-memory.
+inline cudaError_t ctx_malloc(mrsim_ctx *ctx, void **p, size_t bytes) {
+    if (ctx && ctx->fail_alloc >= 0 && ctx->fail_alloc-- == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+template <class T>
+cudaError_t ctx_malloc(mrsim_ctx *ctx, T **p, size_t bytes) {
+    return ctx_malloc(ctx, reinterpret_cast<void **>(p), bytes);
+}
+// Reports a failed call to the log callback (mrsim_set_log_callback) and, with MRSIM_LOG set, to
+// stderr.
+void log_failure(mrsim_status st, const std::string &msg);
+
 // A compiled program with the host-side conversions the upload needs (float32 copies of the
 // demodulation and sub-pulse tables, the moment bound of the float32 inline phase terms).
 struct HostProgram {

@@ -41,6 +41,7 @@ EXPORTS = (
     "mrsim_adjoint_create", "mrsim_adjoint_num_adc", "mrsim_adjoint_forward", "mrsim_adjoint_backward",
     "mrsim_adjoint_destroy", "mrsim_compile", "mrsim_compile_last_error", "mrsim_compiled_num_adc",
     "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
+    "mrsim_set_log_callback", "mrsim_debug_fail_alloc",
 )
 
 
@@ -138,6 +139,8 @@ def lib():
             "mrsim_compiled_destroy": (None, [vp]),
             "mrsim_sequence_create": (ctypes.c_int, [vp, vp, P(vp)]),
             "mrsim_debug_wait_timeout": (ctypes.c_int, [vp, i64, vp]),
+            "mrsim_set_log_callback": (None, [vp, vp]),
+            "mrsim_debug_fail_alloc": (ctypes.c_int, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

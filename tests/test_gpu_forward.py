@@ -6,6 +6,7 @@ workloads are checked on spin subsets (the signal is additive over spins, §5.3.
 launch shape the benchmark uses, plus properties that hold at any size.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -303,3 +304,61 @@ def test_bounded_wait_timeout_is_reported(M, ctx, oracle_mod):
     w = W.config1()
     ref = oracle_mod.signal(w)
     assert rel_l2(run(M, ctx, w.phantom, w.sequence, M.FP64), ref) <= TOL64
+
+
+@pytest.mark.parametrize("what", ["phantom", "sequence", "host_output"])
+def test_allocation_failure_is_reported(M, oracle_mod, what):
+    """Out-of-memory without exhausting the device: the failure hook makes the next device
+    allocation of the call fail; the call returns MRSIM_ENOMEM, leaves nothing half-built and the
+    same call succeeds afterwards (the hook fires once)."""
+    w = W.config1()
+    L = M.lib()
+    c = M.Context(0)  # fresh: its host-output scratch is not allocated yet
+    try:
+        p = M.Phantom.from_workload_phantom(c, w.phantom) if what != "phantom" else None
+        s = M.Sequence.from_workload_sequence(c, w.sequence) if what == "host_output" else None
+        assert L.mrsim_debug_fail_alloc(c.h, 0) == 0
+        with pytest.raises(M.MrsimError) as e:
+            if what == "phantom":
+                M.Phantom.from_workload_phantom(c, w.phantom)
+            elif what == "sequence":
+                M.Sequence.from_workload_sequence(c, w.sequence)
+            else:
+                M.simulate(c, p, s, M.FP64)
+        assert e.value.status == M.Status.ENOMEM
+        if p is None:
+            p = M.Phantom.from_workload_phantom(c, w.phantom)
+        if s is None:
+            s = M.Sequence.from_workload_sequence(c, w.sequence)
+        assert rel_l2(M.simulate(c, p, s, M.FP64), oracle_mod.signal(w)) <= TOL64
+        c.stream_status()
+        p.close()
+        s.close()
+    finally:
+        c.close()
+
+
+def test_autotune_cache_file(M, tmp_path):
+    """MRSIM_AUTOTUNE_CACHE: the first process tunes and appends its shape; a second process
+    loads it and answers mrsim_autotune without timing (same shape, no new line)."""
+    import subprocess
+    import sys
+
+    cache = tmp_path / "tune.txt"
+    code = ("import time, numpy as np\n"
+            "from paper_1305_6861_gb300 import mrsim as M, workloads as W\n"
+            "w = W.config2(n=64, iso=1)\nctx = M.Context(0)\n"
+            "p = M.Phantom.from_workload_phantom(ctx, w.phantom)\ns = M.Sequence.from_workload_sequence(ctx, w.sequence)\n"
+            "t0 = time.perf_counter(); k, t = M.autotune(ctx, p, s, M.FP32); dt = time.perf_counter() - t0\n"
+            "print(k, t, dt)\n")
+    env = dict(os.environ, MRSIM_AUTOTUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(r.stdout.split())
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("mrsim-tune-1 ")
+    assert outs[0][:2] == outs[1][:2]
+    assert float(outs[1][2]) < float(outs[0][2])

@@ -320,3 +320,32 @@ def test_compile_argument_checks(mrsim_lib):
     snaps = np.array([5, 3], dtype=np.int64)  # not increasing
     assert L.mrsim_compile(ev.shape[0], ctypes.c_void_p(ev.ctypes.data), W.GAMMA_BAR, 2,
                            ctypes.c_void_p(snaps.ctypes.data), ctypes.byref(h)) == 1
+
+
+def test_log_callback_and_env(mrsim_lib):
+    """Failed calls reach the log callback (here: mrsim_compile, which needs no GPU) and, with
+    MRSIM_LOG set, stderr."""
+    import ctypes
+    import subprocess
+    import sys
+
+    L = mrsim_lib.lib()
+    got = []
+    FN = ctypes.CFUNCTYPE(None, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p)
+    cb = FN(lambda st, msg, user: got.append((st, msg.decode())))
+    L.mrsim_set_log_callback(ctypes.cast(cb, ctypes.c_void_p), None)
+    try:
+        bad = W.make_events([(1e-3, 0, 0, 0, 0.5, 0, 1, 0.0)] * 2)
+        bad["dt"][0] = -1.0
+        with pytest.raises(mrsim_lib.MrsimError):
+            mrsim_lib.Compiled(bad, W.GAMMA_BAR)
+    finally:
+        L.mrsim_set_log_callback(None, None)
+    assert got and got[-1][0] == 1 and "negative duration" in got[-1][1]
+    code = ("import numpy as np\n"
+            "from paper_1305_6861_gb300 import mrsim as M, workloads as W\n"
+            "ev = W.make_events([(1e-3, 0, 0, 0, 0.5, 0, 1, 0.0)]); ev['adc'][0] = 3\n"
+            "try:\n    M.Compiled(ev, W.GAMMA_BAR)\nexcept M.MrsimError:\n    pass\n")
+    env = dict(os.environ, MRSIM_LOG="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "mrsim: invalid argument: event 0: adc must be 0/1" in r.stderr
