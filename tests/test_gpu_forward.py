@@ -347,7 +347,7 @@ def test_autotune_cache_file(M, tmp_path):
     cache = tmp_path / "tune.txt"
     code = ("import time, numpy as np\n"
             "from paper_1305_6861_gb300 import mrsim as M, workloads as W\n"
-            "w = W.config2(n=64, iso=1)\nctx = M.Context(0)\n"
+            "w = W.config2(n=64, iso=2)\nctx = M.Context(0)\n"
             "p = M.Phantom.from_workload_phantom(ctx, w.phantom)\ns = M.Sequence.from_workload_sequence(ctx, w.sequence)\n"
             "t0 = time.perf_counter(); k, t = M.autotune(ctx, p, s, M.FP32); dt = time.perf_counter() - t0\n"
             "print(k, t, dt)\n")
