@@ -50,7 +50,7 @@ typedef enum {
     MRSIM_ENOMEM = 2,      /* host or device allocation failed */
     MRSIM_ECUDA = 3,       /* a CUDA runtime call failed */
     MRSIM_ETIMEOUT = 4,    /* a bounded device wait ran out */
-    MRSIM_EUNSUPPORTED = 5 /* valid request this build cannot serve (e.g. no sm_103 device) */
+    MRSIM_EUNSUPPORTED = 5 /* valid request this library binary cannot serve (e.g. no sm_103 device) */
 } mrsim_status;
 
 typedef enum {
