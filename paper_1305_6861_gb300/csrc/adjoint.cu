@@ -459,10 +459,10 @@ mrsim_status prepare_rf(mrsim_adjoint *adj, const double *rf_values, cudaStream_
 }
 
 template <class T>
-cudaError_t put(T **d, const std::vector<T> &v) {
+cudaError_t put(mrsim_ctx *ctx, T **d, const std::vector<T> &v) {
     *d = nullptr;
     if (v.empty()) return cudaSuccess;
-    cudaError_t e = cudaMalloc(d, v.size() * sizeof(T));
+    cudaError_t e = ctx_malloc(ctx, d, v.size() * sizeof(T));
     if (e == cudaSuccess) e = cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
 }
@@ -557,14 +557,16 @@ mrsim_status mrsim_adjoint_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_
     adj->seg = ckpt_every;
     adj->n_rf = (int32_t)spec.size();
     adj->n_cls = (int32_t)cls.size();
-    cudaError_t e = put(&adj->d_ev, ev);
-    if (e == cudaSuccess) e = put(&adj->d_spec, spec);
-    if (e == cudaSuccess && !spec.empty()) e = cudaMalloc(&adj->d_rf, spec.size() * sizeof(RfEntry));
-    if (e == cudaSuccess) e = put(&adj->d_cls, ctab);
-    if (e == cudaSuccess) e = put(&adj->d_demod, demod);
+    cudaError_t e = put(ctx, &adj->d_ev, ev);
+    if (e == cudaSuccess) e = put(ctx, &adj->d_spec, spec);
+    if (e == cudaSuccess && !spec.empty()) e = ctx_malloc(ctx, &adj->d_rf, spec.size() * sizeof(RfEntry));
+    if (e == cudaSuccess) e = put(ctx, &adj->d_cls, ctab);
+    if (e == cudaSuccess) e = put(ctx, &adj->d_demod, demod);
     if (e != cudaSuccess) {
         mrsim_adjoint_destroy(adj);
-        return afail(ctx, MRSIM_ENOMEM, std::string("adjoint program: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return afail(ctx, e == cudaErrorMemoryAllocation ? MRSIM_ENOMEM : MRSIM_ECUDA,
+                     std::string("adjoint program: ") + cudaGetErrorString(e));
     }
     if (adj_smem(adj, true) > (size_t)ctx->max_smem_optin) {
         mrsim_adjoint_destroy(adj);

@@ -812,9 +812,13 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     if (rs != MRSIM_OK) return rs;
     static const int f32k[] = {1, 2, 4, 8}, f64k[] = {1, 2};
     static const int thr[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0), "event");
-    CK(cudaEventCreate(&e1), "event");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ee = cudaEventCreate(&e0);
+    if (ee == cudaSuccess) ee = cudaEventCreate(&e1);
+    if (ee != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ctx, ee, "event");
+    }
     // time one launch of the prefix in shape (k, t); < 0 if the shape cannot run
     const int32_t short_ops = P.n_ops;
     const int32_t long_ops = (int32_t)std::min<int64_t>((int64_t)short_ops * 3, (fp64 ? seq->p64 : seq->p32).n_ops);
@@ -1065,11 +1069,20 @@ mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *b
     FwdArgs *d_trunc = nullptr;
     CK(ctx_malloc(ctx, &d_trunc, 2 * trunc.size() * sizeof(FwdArgs)), "cudaMalloc tuning descriptors");
     FwdArgs *d_warm = d_trunc + trunc.size();
-    CK(cudaMemcpy(d_trunc, trunc.data(), trunc.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice), "upload tuning descriptors");
-    CK(cudaMemcpy(d_warm, warm.data(), warm.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice), "upload tuning descriptors");
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaError_t ue = cudaMemcpy(d_trunc, trunc.data(), trunc.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice);
+    if (ue == cudaSuccess) ue = cudaMemcpy(d_warm, warm.data(), warm.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice);
+    if (ue != cudaSuccess) {
+        cudaFree(d_trunc);
+        return cuda_fail(ctx, ue, "upload tuning descriptors");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ee = cudaEventCreate(&e0);
+    if (ee == cudaSuccess) ee = cudaEventCreate(&e1);
+    if (ee != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaFree(d_trunc);
+        return cuda_fail(ctx, ee, "event");
+    }
     static const int f32k[] = {1, 2, 4, 8}, f64k[] = {1, 2};
     static const int thr[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
     int bk = 0, bt = 0;

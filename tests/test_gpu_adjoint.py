@@ -170,3 +170,44 @@ def test_autograd_function(M, ctx, torch, oracle_mod):
     geom3 = [g_[:3].contiguous() for g_ in geom]
     f = lambda a, b, c, d: AG.signal(adj, *geom3, a, b, c, d)
     assert torch.autograd.gradcheck(f, tuple(small), eps=1e-6, atol=1e-6, rtol=1e-5)
+
+
+def test_allocation_failures_in_adjoint(M, torch, oracle_mod):
+    """Each device allocation of adjoint creation and of the first forward pass (the checkpoint
+    store) fails in turn through the allocation-failure hook: the call returns MRSIM_ENOMEM and
+    the context stays usable; once the hook stops firing, the same calls give the oracle's
+    signal."""
+    ph, ev, params, rf, _ = shaped_case(31, 300)
+    L = M.lib()
+    c = M.Context(0)
+    try:
+        P = M.Phantom.from_workload_phantom(c, ph)
+        dev = torch.device("cuda:0")
+        rfd = torch.from_numpy(np.asarray(rf, dtype=np.float64)).to(dev)
+        failed = 0
+        for after in range(16):
+            assert L.mrsim_debug_fail_alloc(c.h, after) == 0
+            adj = None
+            try:
+                adj = M.Adjoint(c, ev, W.GAMMA_BAR, params, len(rf), ckpt_every=16)
+                sig = torch.zeros(2 * adj.n_adc, dtype=torch.float64, device=dev)
+                adj.forward(P, rfd, sig)
+                torch.cuda.synchronize()
+                c.stream_status()
+            except M.MrsimError as e:
+                assert e.status == M.Status.ENOMEM, e
+                failed += 1
+                continue
+            finally:
+                if adj is not None:
+                    adj.close()
+            break
+        else:
+            pytest.fail("the hook never stopped firing")
+        L.mrsim_debug_fail_alloc(c.h, -1)
+        # events, pulse specs, rotation tables, classes, demodulation, the forward program, checkpoints
+        assert failed >= 6
+        assert rel(sig.cpu().numpy().view(np.complex128), oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf)) <= 1e-12
+        P.close()
+    finally:
+        c.close()
