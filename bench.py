@@ -13,6 +13,10 @@ sum-reduce of the complex signal over ranks (NCCL all-reduce).
 
 The reference arm (`--impl reference`) times the FP64 CPU oracle on the host cores, on a
 bounded spin sample of the same workload.
+
+`--raster 1e-5` is a stress mode for c1-c3: every event is cut into pieces of at most 10 µs (the
+"piecewise-constant 10 µs events" reading of the event lists), the signal is the same, and the
+spin-step count is that of the pieces; the line is labelled `stress_mode` in its config.
 """
 from __future__ import annotations
 
@@ -215,11 +219,24 @@ def oracle_parity(ctx, M, w, sub, ref, n_coils: int = 0):
     return out
 
 
+def rasterized(w, raster: float):
+    """The stress variant of a workload: every event cut into pieces of at most `raster` seconds
+    (same signal, many more events; the spin-step count is that of the pieces)."""
+    return W.Workload(w.name + f"_rasterized{raster * 1e6:g}us", w.phantom, W.rasterize(w.sequence, raster), w.note)
+
+
+RASTER_NOTE = ("stress mode: every event cut into pieces of at most {r:g} us, counted as events; the host "
+               "compiler merges the pieces back into the canonical program, so the roofline counts the "
+               "canonical list's work ({n} events)")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w = build_workload(args.workload)
+    if args.raster:
+        w = rasterized(w, args.raster)
     times = []
     cb = None
     for i in range(args.warmup + args.steps):
@@ -526,6 +543,11 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     w = build_workload(args.workload, rank)
+    canonical = w.sequence
+    if args.raster:
+        if args.events:
+            raise SystemExit("--raster and --events do not combine")
+        w = rasterized(w, args.raster)
     if args.events:  # profiling aid: a prefix of the sequence (whole repetitions), named in config
         w = W.Workload(w.name + f"_first{args.events}ev", w.phantom,
                        W.Sequence(w.sequence.events[: args.events], w.sequence.gamma_hz_per_t), w.note)
@@ -592,7 +614,7 @@ def run_ours(args):
     value = world * spin_steps / (ms_per_step * 1e-3)
 
     # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
-    ops = algorithmic_ops_per_spin(w.sequence.events, n_coils) * w.phantom.n
+    ops = algorithmic_ops_per_spin((canonical if args.raster else w.sequence).events, n_coils) * w.phantom.n
     achieved = ops / (kern_ms * 1e-3) / 1e9
     sha = kernel_source_sha()
     if prec == M.FP64:  # the same algorithmic lane-ops against the float64 FMA rate
@@ -700,7 +722,9 @@ def run_ours(args):
                        "n_adc": seq.n_adc, "n_ops": seq.n_ops, "spin_steps_per_gpu_step": spin_steps,
                        "precision": args.precision, "launch": kw or tuned or "library default",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
-                       "parallelism": f"spin-sharded x{world}" if world > 1 else "1 GPU"},
+                       "parallelism": f"spin-sharded x{world}" if world > 1 else "1 GPU",
+                       **({"stress_mode": RASTER_NOTE.format(r=args.raster * 1e6, n=canonical.n_events)}
+                          if args.raster else {})},
             "roofline": roof, "gpu_launches": args.steps, "clocks": ck, "wall_s_timed": t_wall,
             "peaks_file": {k: read_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
         }
@@ -729,6 +753,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--events", type=int, default=0, help="use only the first N events (profiling cases)")
     ap.add_argument("--coils", type=int, default=0, help="receive coils (ring sensitivities), 0 = plain signal")
+    ap.add_argument("--raster", type=float, default=0.0,
+                    help="stress mode (c1-c3): cut every event into pieces of at most this many seconds (1e-5)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -219,21 +219,33 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     std::vector<Item> &items = lease.s.items;
     items.reserve((size_t)n + 2);
     double tau = 0.0;
-    bool have = false;
-    double pk[3] = {0, 0, 0}, pdt = 0.0;
+    // The pending free interval (pk, pdt) since the last item.  Its trailing events that share one
+    // gradient tg are also summed on their own (tk, tdt), with (hk, hdt) the pending interval
+    // before them: a sample whose event has that gradient absorbs the trailing part (one interval
+    // of constant gradient, precession and relaxation compose), so a readout whose dwell is split
+    // into several events still compiles to uniform samples.
+    bool have = false, hhave = false, thave = false;
+    double pk[3] = {0, 0, 0}, pdt = 0.0, hk[3] = {0, 0, 0}, hdt = 0.0, tk[3] = {0, 0, 0}, tdt = 0.0;
+    double tg[3] = {0, 0, 0};
     int64_t j = 0, snap_next = 0;
-    auto flush = [&]() {
-        if (have && !is_zero(pk, pdt)) {
-            Item it{};
-            it.kind = Item::PREC;
-            std::memcpy(it.k, pk, sizeof pk);
-            it.dt = pdt;
-            items.push_back(it);
-        }
-        have = false;
-        pk[0] = pk[1] = pk[2] = 0.0;
-        pdt = 0.0;
+    auto push_prec = [&](const double *k, double dt) {
+        if (is_zero(k, dt)) return;
+        Item it{};
+        it.kind = Item::PREC;
+        std::memcpy(it.k, k, 3 * sizeof(double));
+        it.dt = dt;
+        items.push_back(it);
     };
+    auto reset = [&]() {
+        have = hhave = thave = false;
+        for (int c = 0; c < 3; ++c) pk[c] = hk[c] = tk[c] = 0.0;
+        pdt = hdt = tdt = 0.0;
+    };
+    auto flush = [&]() {
+        if (have) push_prec(pk, pdt);
+        reset();
+    };
+    auto same_g = [&](const mrsim_event &e) { return thave && e.gx == tg[0] && e.gy == tg[1] && e.gz == tg[2]; };
     for (int64_t i = 0; i < n; ++i) {
         const mrsim_event &e = ev[i];
         const double f[7] = {e.dt, e.gx, e.gy, e.gz, e.rf_flip, e.rf_phase, e.adc_phase};
@@ -268,16 +280,37 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         }
         const double k[3] = {gamma_hz * e.gx * e.dt, gamma_hz * e.gy * e.dt, gamma_hz * e.gz * e.dt};
         if (e.adc) {
-            flush();
             Item it{};
             it.kind = Item::SAMPLE;
-            std::memcpy(it.k, k, sizeof k);
-            it.dt = e.dt;
+            if (same_g(e)) {  // the trailing constant-gradient part joins the sample's interval
+                if (hhave) push_prec(hk, hdt);
+                for (int c = 0; c < 3; ++c) it.k[c] = tk[c] + k[c];
+                it.dt = tdt + e.dt;
+                reset();
+            } else {
+                flush();
+                std::memcpy(it.k, k, sizeof k);
+                it.dt = e.dt;
+            }
             it.j = j++;
             it.adc_phase = e.adc_phase;
             items.push_back(it);
         } else {
-            for (int c = 0; c < 3; ++c) pk[c] += k[c];
+            if (!same_g(e)) {  // a new trailing run starts here
+                std::memcpy(hk, pk, sizeof pk);
+                hdt = pdt;
+                hhave = have;
+                tg[0] = e.gx;
+                tg[1] = e.gy;
+                tg[2] = e.gz;
+                tk[0] = tk[1] = tk[2] = tdt = 0.0;
+                thave = true;
+            }
+            for (int c = 0; c < 3; ++c) {
+                tk[c] += k[c];
+                pk[c] += k[c];
+            }
+            tdt += e.dt;
             pdt += e.dt;
             have = true;
         }

@@ -579,6 +579,29 @@ def with_rf_waveform(seq: Sequence, waveform: np.ndarray) -> Sequence:
     return Sequence(ev, seq.gamma_hz_per_t, seq.kshape, seq.name)
 
 
+def rasterize(seq: Sequence, raster: float = 10e-6) -> Sequence:
+    """Stress variant of a sequence: every event longer than `raster` becomes ceil(Δt/raster)
+    consecutive events of equal length with the same gradient; the RF pulse stays on the first
+    piece (it acts at the start of the event) and the ADC sample on the last (it is taken at the
+    end).  Precession angles and relaxation over the pieces compose to those of the whole event
+    (Eq. 4.1 applied piecewise), so the signal is unchanged; only the number of events grows
+    (the 10 µs piecewise-constant reading of the event lists)."""
+    ev = seq.events
+    n = np.maximum(1, np.ceil(ev["dt"] / raster * (1.0 - 1e-9))).astype(np.int64)
+    out = np.repeat(ev, n)
+    out["dt"] = np.repeat(ev["dt"] / n, n)
+    start = np.concatenate([[0], np.cumsum(n)[:-1]])
+    not_first = np.ones(out.shape[0], dtype=bool)
+    not_first[start] = False
+    not_last = np.ones(out.shape[0], dtype=bool)
+    not_last[start + n - 1] = False
+    out["rf_flip"][not_first] = 0.0
+    out["rf_phase"][not_first] = 0.0
+    out["adc"][not_last] = 0
+    out["adc_phase"][not_last] = 0.0
+    return Sequence(out, seq.gamma_hz_per_t, seq.kshape, (seq.name or "seq") + f"_rasterized{raster * 1e6:g}us")
+
+
 # ---------------------------------------------------------------------------
 # Small random cases (parity tests, edge cases)
 # ---------------------------------------------------------------------------

@@ -243,6 +243,23 @@ def test_config2_subset_parity(M, ctx, oracle_mod):
     assert rel_l2(run(M, ctx, sub, w.sequence, M.FP32), ref) <= TOL32
 
 
+def test_rasterized_sequences_parity(M, ctx, oracle_mod):
+    """The 10 µs rasterized stress lists: C1 against the oracle on the rasterized list itself, and
+    a C2 spin subset against the oracle on the canonical list (the two lists give the same signal:
+    Eq. 4.1 composes over the pieces, pinned on the CPU)."""
+    w = W.config1()
+    r = W.rasterize(w.sequence)
+    ref = oracle_mod.signal(w.phantom, r)
+    assert rel_l2(run(M, ctx, w.phantom, r, M.FP64), ref) <= TOL64
+    assert rel_l2(run(M, ctx, w.phantom, r, M.FP32), ref) <= TOL32
+    w = W.config2()
+    sub = w.phantom.subset(np.sort(np.random.default_rng(22).choice(w.phantom.n, 1200, replace=False)))
+    ref = oracle_mod.signal(sub, w.sequence)
+    r = W.rasterize(w.sequence)
+    assert rel_l2(run(M, ctx, sub, r, M.FP64), ref) <= TOL64
+    assert rel_l2(run(M, ctx, sub, r, M.FP32), ref) <= TOL32
+
+
 def test_config2_full_size_fp32_vs_fp64(M, ctx):
     """Full-size C2 in the benchmark's launch shape: float32 against the float64 GPU path, and
     additivity of the float64 path over two disjoint halves of the spins."""
