@@ -179,6 +179,20 @@ struct ClassOf {
     }
 };
 
+// Compensated running sum (Neumaier's variant of Kahan summation): the rounding error of each
+// addition is carried in `c`, so an interval made of many short events (a list on a fine time
+// raster) sums to its moment within about one rounding instead of one per event.  For one or two
+// terms the value equals the plain sum.
+struct CSum {
+    double s = 0.0, c = 0.0;
+    void add(double x) {
+        const double t = s + x;
+        c += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    double value() const { return s + c; }
+};
+
 bool same_interval(const Item &a, const Item &b) {  // the key equality of key_of, without the keys
     return a.k[0] == b.k[0] && a.k[1] == b.k[1] && a.k[2] == b.k[2] && a.dt == b.dt;
 }
@@ -219,30 +233,31 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     std::vector<Item> &items = lease.s.items;
     items.reserve((size_t)n + 2);
     double tau = 0.0;
-    // The pending free interval (pk, pdt) since the last item.  Its trailing events that share one
-    // gradient tg are also summed on their own (tk, tdt), with (hk, hdt) the pending interval
-    // before them: a sample whose event has that gradient absorbs the trailing part (one interval
-    // of constant gradient, precession and relaxation compose), so a readout whose dwell is split
-    // into several events still compiles to uniform samples.
+    // The pending free interval pk since the last item.  Its trailing events that share one
+    // gradient tg are also summed on their own (tk), with hk the pending interval before them: a
+    // sample whose event has that gradient absorbs the trailing part (one interval of constant
+    // gradient; precession and relaxation compose), so a readout whose dwell is split into several
+    // events still compiles to uniform samples.
+    // (moments and durations as compensated sums: components 0-2 the moment, 3 the duration)
     bool have = false, hhave = false, thave = false;
-    double pk[3] = {0, 0, 0}, pdt = 0.0, hk[3] = {0, 0, 0}, hdt = 0.0, tk[3] = {0, 0, 0}, tdt = 0.0;
+    CSum pk[4], hk[4], tk[4];
     double tg[3] = {0, 0, 0};
     int64_t j = 0, snap_next = 0;
-    auto push_prec = [&](const double *k, double dt) {
+    auto push_prec = [&](const CSum *sum) {
+        const double k[3] = {sum[0].value(), sum[1].value(), sum[2].value()}, dt = sum[3].value();
         if (is_zero(k, dt)) return;
         Item it{};
         it.kind = Item::PREC;
-        std::memcpy(it.k, k, 3 * sizeof(double));
+        std::memcpy(it.k, k, sizeof k);
         it.dt = dt;
         items.push_back(it);
     };
     auto reset = [&]() {
         have = hhave = thave = false;
-        for (int c = 0; c < 3; ++c) pk[c] = hk[c] = tk[c] = 0.0;
-        pdt = hdt = tdt = 0.0;
+        for (int c = 0; c < 4; ++c) pk[c] = hk[c] = tk[c] = CSum{};
     };
     auto flush = [&]() {
-        if (have) push_prec(pk, pdt);
+        if (have) push_prec(pk);
         reset();
     };
     auto same_g = [&](const mrsim_event &e) { return thave && e.gx == tg[0] && e.gy == tg[1] && e.gz == tg[2]; };
@@ -283,9 +298,10 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             Item it{};
             it.kind = Item::SAMPLE;
             if (same_g(e)) {  // the trailing constant-gradient part joins the sample's interval
-                if (hhave) push_prec(hk, hdt);
-                for (int c = 0; c < 3; ++c) it.k[c] = tk[c] + k[c];
-                it.dt = tdt + e.dt;
+                if (hhave) push_prec(hk);
+                for (int c = 0; c < 4; ++c) tk[c].add(c < 3 ? k[c] : e.dt);
+                for (int c = 0; c < 3; ++c) it.k[c] = tk[c].value();
+                it.dt = tk[3].value();
                 reset();
             } else {
                 flush();
@@ -297,21 +313,21 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             items.push_back(it);
         } else {
             if (!same_g(e)) {  // a new trailing run starts here
-                std::memcpy(hk, pk, sizeof pk);
-                hdt = pdt;
+                for (int c = 0; c < 4; ++c) {
+                    hk[c] = pk[c];
+                    tk[c] = CSum{};
+                }
                 hhave = have;
                 tg[0] = e.gx;
                 tg[1] = e.gy;
                 tg[2] = e.gz;
-                tk[0] = tk[1] = tk[2] = tdt = 0.0;
                 thave = true;
             }
-            for (int c = 0; c < 3; ++c) {
-                tk[c] += k[c];
-                pk[c] += k[c];
+            for (int c = 0; c < 4; ++c) {
+                const double v = c < 3 ? k[c] : e.dt;
+                tk[c].add(v);
+                pk[c].add(v);
             }
-            tdt += e.dt;
-            pdt += e.dt;
             have = true;
         }
         tau += e.dt;

@@ -250,7 +250,11 @@ def test_rasterized_sequences_parity(M, ctx, oracle_mod):
     w = W.config1()
     r = W.rasterize(w.sequence)
     ref = oracle_mod.signal(w.phantom, r)
-    assert rel_l2(run(M, ctx, w.phantom, r, M.FP64), ref) <= TOL64
+    # the oracle turns every spin once per event: each turn's cos/sin rounding changes |M| by up to
+    # about 2^-52, so on 64 000 events its own float64 floor is 2·2^-53·n_events ≈ 1.4e-11
+    # (the library merges the pieces and turns once per canonical interval)
+    tol64 = max(TOL64, 2 * 2.0**-53 * r.n_events)
+    assert rel_l2(run(M, ctx, w.phantom, r, M.FP64), ref) <= tol64
     assert rel_l2(run(M, ctx, w.phantom, r, M.FP32), ref) <= TOL32
     w = W.config2()
     sub = w.phantom.subset(np.sort(np.random.default_rng(22).choice(w.phantom.n, 1200, replace=False)))

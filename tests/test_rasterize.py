@@ -55,7 +55,9 @@ def test_oracle_invariant_under_rasterization(oracle_mod):
     ph = W.Phantom(*(a[sub] for a in ph.arrays()))
     ref = oracle_mod.simulate(ph, w.sequence.events, w.sequence.gamma_hz_per_t)[0]
     r = W.rasterize(w.sequence)
-    assert rel_l2(oracle_mod.simulate(ph, r.events, r.gamma_hz_per_t)[0], ref) <= 1e-12
+    # float64 floor of an oracle that turns every spin once per event: the cos/sin rounding of
+    # each turn changes |M| by up to about 2^-52, i.e. 2·2^-53 per event over 64 000 events
+    assert rel_l2(oracle_mod.simulate(ph, r.events, r.gamma_hz_per_t)[0], ref) <= max(1e-12, 2 * 2.0**-53 * r.n_events)
 
 
 @pytest.mark.parametrize("seed", range(3))
