@@ -94,6 +94,17 @@ def build_workload(name: str, rank: int = 0):
     raise ValueError(name)
 
 
+def source_id() -> dict:
+    """Which code produced the line: the kernel-source hash and, where the tree is a git checkout,
+    the commit."""
+    try:
+        rev = subprocess.run(["git", "-C", ROOT, "rev-parse", "--short=12", "HEAD"], capture_output=True, text=True,
+                             timeout=10).stdout.strip() or None
+    except Exception:
+        rev = None
+    return {"fwd_kernel_source_sha": kernel_source_sha(), "kt_kernel_source_sha": kernel_source_sha(KT_SOURCES), "git": rev}
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -319,7 +330,7 @@ def run_batch(args):
                      "frac": achieved / peak,
                      "traffic": traffic_for(kernel_source_sha(), "c4_batch64") if prec == M.FP32 else None,
                      "kernel_ms": ms, "ops_per_spin_step": ops / spin_steps},
-        "gpu_launches": 2 * args.steps, "clocks": ck,
+        "gpu_launches": 2 * args.steps, "clocks": ck, "source": source_id(),
     }
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample of the batch's longest program
         wl = max(ws, key=lambda w: w.sequence.n_events)
@@ -402,7 +413,7 @@ def run_adjoint(args):
                          "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None, "kernel_ms": ms,
                          "peak_basis": "nominal float64 rate of the profiling recipe (no measured float64 figure)",
                          "flops_per_spin_step": flops_spin / n_ev},
-            "gpu_launches": 4 * args.steps, "clocks": ck}
+            "gpu_launches": 4 * args.steps, "clocks": ck, "source": source_id()}
     if not args.no_cpu_baseline:  # the oracle's forward-mode gradient (every flip) on a bounded spin sample
         import oracle
 
@@ -492,7 +503,7 @@ def run_kt(args):
             {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
              "traffic": traffic_for(kernel_source_sha(KT_SOURCES), f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}"),
              "kernel_ms": ms, "ops_per_order_step": KT_OPS_PER_ORDER},
-            "gpu_launches": 2 * args.steps, "clocks": ck}
+            "gpu_launches": 2 * args.steps, "clocks": ck, "source": source_id()}
     if not args.no_cpu_baseline:
         from oracle import kt as ORK
 
@@ -727,6 +738,7 @@ def run_ours(args):
                           if args.raster else {})},
             "roofline": roof, "gpu_launches": args.steps, "clocks": ck, "wall_s_timed": t_wall,
             "peaks_file": {k: read_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
+            "source": source_id(),
         }
         line.update(out)
         print(json.dumps(line), flush=True)

@@ -107,7 +107,9 @@ typedef void (*mrsim_log_fn)(mrsim_status status, const char *message, void *use
 void mrsim_set_log_callback(mrsim_log_fn fn, void *user);
 /* Test hook: the device allocation that follows `after` further successful ones on this context
  * fails once with MRSIM_ENOMEM, as a full device would (after < 0 switches the hook off), so that
- * the out-of-memory paths can be tested without exhausting the device. */
+ * the out-of-memory paths can be tested without exhausting the device.  The environment variable
+ * MRSIM_FAIL_ALLOC=<after> arms it in every context when the context is created (for programs
+ * that cannot call this function).  The context's own status buffers are not counted. */
 mrsim_status mrsim_debug_fail_alloc(mrsim_ctx *ctx, int32_t after);
 /* Synchronise `stream` (cudaStream_t, NULL = legacy default stream) and report any device-side
  * status recorded by kernels of this context (e.g. MRSIM_ETIMEOUT); clears the status word. */

@@ -221,6 +221,11 @@ mrsim_status mrsim_context_create(int device, mrsim_ctx **out) {
         ctx->tune_cache = cache;
         load_tune_cache(ctx);
     }
+    if (const char *f = std::getenv("MRSIM_FAIL_ALLOC")) {  // the allocation-failure hook, armed for every context
+        char *end = nullptr;
+        const long v = std::strtol(f, &end, 10);
+        if (end != f && v >= 0 && v <= INT32_MAX) ctx->fail_alloc = (int32_t)v;
+    }
     cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&ctx->d_bad, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {

@@ -383,3 +383,21 @@ def test_autotune_cache_file(M, tmp_path):
     assert len(lines) == 1 and lines[0].startswith("mrsim-tune-1 ")
     assert outs[0][:2] == outs[1][:2]
     assert float(outs[1][2]) < float(outs[0][2])
+
+
+def test_allocation_failure_from_environment(M):
+    """MRSIM_FAIL_ALLOC arms the allocation-failure hook in a process that does not call the
+    library's hook itself: its first phantom upload fails with ENOMEM, the second succeeds."""
+    import subprocess
+    import sys
+
+    code = ("from paper_1305_6861_gb300 import mrsim as M, workloads as W\n"
+            "w = W.config1()\nctx = M.Context(0)\n"
+            "try:\n    M.Phantom.from_workload_phantom(ctx, w.phantom)\n    print('no failure')\n"
+            "except M.MrsimError as e:\n    print(e.status.name)\n"
+            "p = M.Phantom.from_workload_phantom(ctx, w.phantom)\nprint('ok', p.n)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=dict(os.environ, MRSIM_FAIL_ALLOC="0"),
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.split() == ["ENOMEM", "ok", "4096"], r.stdout
