@@ -1053,76 +1053,92 @@ mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *b
     cudaStream_t st = (cudaStream_t)stream;
     const bool fp64 = b->prec == MRSIM_FP64;
     if (b->descs.empty()) return MRSIM_OK;
-    // time a prefix of every program: the same fraction of each, about 5e9 spin-steps in all
-    // (warm-up launches run an 8-operation prefix so that each kernel is loaded before timing)
-    std::vector<FwdArgs> trunc = b->descs, warm = b->descs;
-    const double frac = std::min(1.0, 5e9 / (double)std::max<int64_t>(b->spin_steps, 1));
-    for (size_t i = 0; i < trunc.size(); ++i) {
-        FwdArgs &a = trunc[i];
-        int64_t nt = (int64_t)std::ceil(a.prog.n_ops * frac);
-        nt = std::max<int64_t>(nt, std::min<int64_t>(a.prog.n_ops, 64));
-        a.prog.n_ops = (int32_t)std::min<int64_t>(nt, a.prog.n_ops);
-        warm[i].prog.n_ops = std::min<int32_t>(a.prog.n_ops, 8);
-        a.signal = nullptr;  // filled below: the tuning runs write to scratch
+    // Time prefixes of every program, the same fraction of each so that the mix of programs is
+    // that of the whole batch: pass 1 every shape on about 2e10 spin-steps in all, pass 2 the
+    // three fastest on about 3e11 (a short prefix over-weights the per-spin set-up and the first
+    // TRs).  Warm-up launches run an 8-operation prefix so that each kernel is loaded first.
+    const size_t nd = b->descs.size();
+    std::vector<FwdArgs> sets[3] = {b->descs, b->descs, b->descs};  // pass 1, pass 2, warm-up
+    const double fracs[2] = {std::min(1.0, 2e10 / (double)std::max<int64_t>(b->spin_steps, 1)),
+                             std::min(1.0, 3e11 / (double)std::max<int64_t>(b->spin_steps, 1))};
+    for (size_t i = 0; i < nd; ++i) {
+        for (int q = 0; q < 2; ++q) {
+            FwdArgs &a = sets[q][i];
+            const int64_t nt = std::max<int64_t>((int64_t)std::ceil(a.prog.n_ops * fracs[q]), 8);
+            a.prog.n_ops = (int32_t)std::min<int64_t>(nt, a.prog.n_ops);
+        }
+        sets[2][i].prog.n_ops = std::min<int32_t>(sets[2][i].prog.n_ops, 8);
     }
     size_t max_adc = 0;
-    for (auto &a : trunc) max_adc = std::max<size_t>(max_adc, (size_t)a.prog.n_adc);
+    for (auto &a : b->descs) max_adc = std::max<size_t>(max_adc, (size_t)a.prog.n_adc);
     mrsim_status rs = grow(ctx, &ctx->d_sig, &ctx->sig_cap, 2 * std::max<size_t>(max_adc, 1));
     if (rs != MRSIM_OK) return rs;
-    for (auto &a : trunc) a.signal = ctx->d_sig;  // all phantoms add into one scratch buffer
-    for (auto &a : warm) a.signal = ctx->d_sig;
-    FwdArgs *d_trunc = nullptr;
-    CK(ctx_malloc(ctx, &d_trunc, 2 * trunc.size() * sizeof(FwdArgs)), "cudaMalloc tuning descriptors");
-    FwdArgs *d_warm = d_trunc + trunc.size();
-    cudaError_t ue = cudaMemcpy(d_trunc, trunc.data(), trunc.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice);
-    if (ue == cudaSuccess) ue = cudaMemcpy(d_warm, warm.data(), warm.size() * sizeof(FwdArgs), cudaMemcpyHostToDevice);
+    for (auto &v : sets)
+        for (auto &a : v) a.signal = ctx->d_sig;  // the tuning runs all add into one scratch buffer
+    FwdArgs *d_sets = nullptr;
+    CK(ctx_malloc(ctx, &d_sets, 3 * nd * sizeof(FwdArgs)), "cudaMalloc tuning descriptors");
+    cudaError_t ue = cudaSuccess;
+    for (int q = 0; q < 3 && ue == cudaSuccess; ++q)
+        ue = cudaMemcpy(d_sets + q * nd, sets[q].data(), nd * sizeof(FwdArgs), cudaMemcpyHostToDevice);
     if (ue != cudaSuccess) {
-        cudaFree(d_trunc);
+        cudaFree(d_sets);
         return cuda_fail(ctx, ue, "upload tuning descriptors");
     }
+    const FwdArgs *d_pass[2] = {d_sets, d_sets + nd}, *d_warm = d_sets + 2 * nd;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ee = cudaEventCreate(&e0);
     if (ee == cudaSuccess) ee = cudaEventCreate(&e1);
     if (ee != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
-        cudaFree(d_trunc);
+        cudaFree(d_sets);
         return cuda_fail(ctx, ee, "event");
     }
+    // one warm-up launch and one timed launch of shape (k, t); < 0 if the shape cannot run
+    auto trial = [&](int k, int t, const FwdArgs *d_descs) -> float {
+        std::string keep = ctx->err;
+        if (batch_layout(b, k, t) != MRSIM_OK) {
+            ctx->err = keep;
+            return -1.0f;
+        }
+        if (batch_enqueue(b, d_warm, st) != MRSIM_OK) {
+            cudaGetLastError();
+            return -1.0f;
+        }
+        cudaEventRecord(e0, st);
+        mrsim_status q = batch_enqueue(b, d_descs, st);
+        cudaEventRecord(e1, st);
+        if (q != MRSIM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0f;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
     static const int f32k[] = {1, 2, 4, 8}, f64k[] = {1, 2};
     static const int thr[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
-    int bk = 0, bt = 0;
-    float bms = 1e30f;
-    for (int k : (fp64 ? std::vector<int>(f64k, f64k + 2) : std::vector<int>(f32k, f32k + 4))) {
+    std::vector<TunedShape> cand;
+    for (int k : (fp64 ? std::vector<int>(f64k, f64k + 2) : std::vector<int>(f32k, f32k + 4)))
         for (int t : thr) {
             if (t > (fp64 || k == 8 ? 256 : 512)) continue;
-            std::string keep = ctx->err;
-            if (batch_layout(b, k, t) != MRSIM_OK) {
-                ctx->err = keep;
-                continue;
-            }
-            if (batch_enqueue(b, d_warm, st) != MRSIM_OK) {
-                cudaGetLastError();
-                continue;
-            }
-            cudaEventRecord(e0, st);
-            mrsim_status q = batch_enqueue(b, d_trunc, st);
-            cudaEventRecord(e1, st);
-            if (q != MRSIM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < bms) {
-                bms = ms;
-                bk = k;
-                bt = t;
-            }
+            const float ms = trial(k, t, d_pass[0]);
+            if (ms >= 0.0f) cand.push_back(TunedShape{k, t, ms});
+        }
+    std::sort(cand.begin(), cand.end(), [](const TunedShape &x, const TunedShape &y) { return x.ms < y.ms; });
+    if (cand.size() > 3) cand.resize(3);
+    int bk = 0, bt = 0;
+    float bms = 1e30f;
+    for (const TunedShape &c : cand) {
+        const float ms = trial(c.k, c.threads, d_pass[1]);
+        if (ms >= 0.0f && ms < bms) {
+            bms = ms;
+            bk = c.k;
+            bt = c.threads;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_trunc);
+    cudaFree(d_sets);
     mrsim_status ss = mrsim_stream_status(ctx, stream);
     if (ss != MRSIM_OK) return ss;
     if (!bk) return fail(ctx, MRSIM_EUNSUPPORTED, "no launch shape fits this batch");
