@@ -1,0 +1,93 @@
+"""The benchmark's host side without a GPU: the reference arm's JSON line (the oracle on the host
+cores), the algorithmic work model behind the roofline, the traffic-record lookup, and that the
+GPU arm refuses to run without a GPU instead of falling back to the CPU."""
+import importlib.util
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1305_6861_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+def _run(args, env=None, timeout=600):
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
+                          text=True, timeout=timeout, env=dict(os.environ, **(env or {})))
+
+
+def test_reference_arm_line(oracle_mod):
+    r = _run(["--impl", "reference", "--workload", "c1", "--steps", "1", "--warmup", "3", "--ref-seconds", "0.3"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "gpu_launches"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["warmup"] >= 3 and d["steps"] == 1 and d["vs_baseline"] is None
+    assert d["config"]["workload"] == "c1_flash2d_64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    r = _run(["--impl", "reference", "--workload", "c1", "--steps", "1"], env={"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_gpu_arm_has_no_cpu_fallback():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = _run(["--workload", "c1", "--steps", "1", "--warmup", "3", "--no-cpu-baseline"], timeout=300)
+    assert r.returncode != 0
+    assert not any(ln.startswith("{") for ln in r.stdout.splitlines())
+
+
+def test_algorithmic_work_model(bench):
+    rows = [(1e-5, 0, 0, 0, 0.3, 0, 0, 0.0),   # RF: 10
+            (1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0),  # sample: 6
+            (1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0),  # sample: 6
+            (1e-3, 0, 0, 0, 0, 0, 0, 0.0),     # free: 4
+            (1e-5, 0, 0, 0, 0.2, 0, 1, 0.0)]   # RF and sample in one event: 6 + 10 - 4 + 2
+    ev = W.make_events(rows)
+    assert bench.algorithmic_ops_per_spin(ev) == 10 + 6 + 6 + 4 + 14
+    # with receive coils a sample costs the precession plus one weighted sum per coil
+    assert bench.algorithmic_ops_per_spin(ev, n_coils=3) == 10 + 2 * 16 + 4 + (16 + 10 - 4 + 2)
+    # a rasterized list has more events but the same canonical work (the roofline uses the latter)
+    w = W.config1()
+    r = bench.rasterized(w, 1e-5)
+    assert r.name == "c1_flash2d_64_rasterized10us" and r.sequence.n_events == 64000
+    assert r.phantom is w.phantom
+
+
+def test_traffic_records_follow_the_kernel_source(bench):
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    for name, e in rec.items():
+        assert bench.traffic_for(e["kernel_source_sha"], name) == e["dram_bytes_per_launch"]
+        assert bench.traffic_for("0" * 16, name) is None
+        assert e["dram_bytes_per_launch"] == e["dram_read_bytes"] + e["dram_write_bytes"]
+        assert "--clock-control none" in e["source"]
+    # the hash ignores comments and whitespace only
+    assert len(bench.kernel_source_sha()) == 16 and bench.kernel_source_sha() != bench.kernel_source_sha(bench.KT_SOURCES)
