@@ -149,7 +149,8 @@ struct Ensemble {
             ani[s] = lane == 31 ? (s + 1 < M ? si[s + 1] : (R)0) : si[s];
         }
         if (!full) drop(apr, api);
-        tie_zero();
+        // a_-0 needs no tie here: lane 0's a_0 and a_-0 both came from lane 1's a_-1 (and the
+        // drop never reaches order 0)
     }
 
     // Eq. 4.17 with q = -1: a_i <- a_{i+1} (i >= 0), a_-1 <- a_0, a_-i <- a_-(i-1)
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
     using E = Ensemble<R, M>;
     using P = typename E::P;
     __shared__ Coef<P> coef[KT_WARPS][32];
+    __shared__ Cx<R> smp[KT_WARPS][32];  // a_0 after the chunk's sampled steps (written by lane 0)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t set = (int64_t)blockIdx.x * KT_WARPS + w;
     if (set >= a.n_sets) return;  // uniform over the warp; no block-wide barrier follows
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
         // lane k keeps the sample of step base + k and stores it after the chunk (one conversion
         // to float64 per lane instead of one per sample for the whole warp)
         const unsigned smask = __ballot_sync(FULLW, lane < cnt && (myflags & 256));
-        Cx<R> mine{0, 0};
+        Cx<R> *sw = smp[w];
         for (int k = 0; k < cnt; ++k) {
             const Coef<P> &c = cw[k];
             const int fl = c.flags;
@@ -301,8 +303,7 @@ __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
                 e.pulse(c);
                 e.shift_up();
                 e.relax(c);
-                const R sr = __shfl_sync(FULLW, e.apr[0], 0), si = __shfl_sync(FULLW, e.api[0], 0);
-                if (lane == k) mine = Cx<R>{sr, si};
+                if (lane == 0) sw[k] = Cx<R>{e.apr[0], e.api[0]};
                 continue;
             }
             if (fl & 512) e.pulse(c);
@@ -310,12 +311,11 @@ __global__ void __launch_bounds__(32 * KT_WARPS) kt_kernel(const KtArgs a) {
             for (int i = 0; i < q; ++i) e.shift_up();
             for (int i = 0; i > q; --i) e.shift_down();
             e.relax(c);
-            if (fl & 256) {
-                const R sr = __shfl_sync(FULLW, e.apr[0], 0), si = __shfl_sync(FULLW, e.api[0], 0);
-                if (lane == k) mine = Cx<R>{sr, si};
-            }
+            if ((fl & 256) && lane == 0) sw[k] = Cx<R>{e.apr[0], e.api[0]};
         }
+        __syncwarp();  // lane 0's samples are visible to the warp
         if (smask & (1u << lane)) {  // demodulated with this lane's own step
+            const Cx<R> mine = sw[lane];
             const Cx<R> v = cmul(mine, Cx<R>{cadc, -sadc});
             const int64_t jj = j + __popc(smask & ((1u << lane) - 1u));
             out[2 * jj] = (double)v.re;
