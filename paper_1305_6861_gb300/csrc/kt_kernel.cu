@@ -9,11 +9,10 @@
 // off-resonance turns the transverse populations; a sampled step records a_0·exp(-j adc_phase).
 // b_-i = conj(b_i), so M_z = Z_0 stays real.
 //
-// GPU layout: one warp per ensemble.  Lane l holds the orders i = l + 32·m (m < M) as a_i,
-// a_-i and b_i: the pulse is lane-local (order i couples with -i only) and runs on slot pairs
-// with f32x2 arithmetic in float32; a one-order shift rotates every slot by one lane (one
-// shuffle per slot and quantity) and lane 0 / lane 31 take their value from the neighbouring
-// slot.  Every lane computes the coefficients of one step of every 32 (sin/cos of the scaled
+// GPU layout: one warp per ensemble.  Lane l holds the M consecutive orders i = M·l + m (m < M)
+// as a_i, a_-i and b_i: the pulse is lane-local (order i couples with -i only) and runs on slot
+// pairs with f32x2 arithmetic in float32; a one-order shift moves the slots within each lane and
+// takes one value per quantity from the neighbouring lane (one shuffle).  Every lane computes the coefficients of one step of every 32 (sin/cos of the scaled
 // flip, E1, E2, off-resonance phasor) into shared memory, replicated for the packed arithmetic,
 // and the warp reads each step's set with broadcast loads; no warp waits on another.
 #include <cuda_runtime.h>
@@ -84,7 +83,7 @@ struct Ensemble {
     using KP = KtPack<R, M>;
     using P = typename KP::P;
     static constexpr int L = KP::L, NP = KP::NP;
-    R apr[M], api[M], anr[M], ani[M], bzr[M], bzi[M];  // a_i, a_-i, b_i for i = lane + 32·slot
+    R apr[M], api[M], anr[M], ani[M], bzr[M], bzi[M];  // a_i, a_-i, b_i for i = M·lane + slot
     int lane, K;
     bool full;  // K = 32·M - 1: every stored order exists
 
@@ -127,57 +126,56 @@ struct Ensemble {
         tie_zero();
     }
 
-    // Eq. 4.17 with q = +1: a_i <- a_{i-1} (i >= 1), a_0 <- a_-1, a_-i <- a_-(i+1).  Each slot is
-    // rotated by one lane; lane 0 (lane 31) takes the value the neighbouring slot's rotation
-    // brought it, i.e. the other end of that slot.
+    // Eq. 4.17 with q = +1: a_i <- a_{i-1} (i >= 1), a_0 <- a_-1, a_-i <- a_-(i+1).  Within a lane
+    // the slots move by one; the slot that crosses a lane boundary comes from the neighbour (one
+    // shuffle per quantity).  At lane 0, a_-1 is its own slot 1 (with one slot per lane, lane 1's
+    // slot 0).  The new a_-0 is the old a_-1 as well, so the order-0 pair stays tied.
     __device__ __forceinline__ void shift_up() {
-        const R a_m1r = __shfl_sync(FULLW, anr[0], 1), a_m1i = __shfl_sync(FULLW, ani[0], 1);
         const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
-        R rr[M], ri[M], sr[M], si[M];
-#pragma unroll
-        for (int s = 0; s < M; ++s) {
-            rr[s] = __shfl_sync(FULLW, apr[s], up);
-            ri[s] = __shfl_sync(FULLW, api[s], up);
-            sr[s] = __shfl_sync(FULLW, anr[s], dn);
-            si[s] = __shfl_sync(FULLW, ani[s], dn);
+        const R rr = __shfl_sync(FULLW, apr[M - 1], up), ri = __shfl_sync(FULLW, api[M - 1], up);
+        const R sr = __shfl_sync(FULLW, anr[0], dn), si = __shfl_sync(FULLW, ani[0], dn);
+        R m1r = sr, m1i = si;
+        if constexpr (M > 1) {
+            m1r = anr[1];
+            m1i = ani[1];
         }
 #pragma unroll
-        for (int s = 0; s < M; ++s) {  // order 32s <- 32s - 1; order -(32s + 31) <- -(32s + 32)
-            apr[s] = lane == 0 ? (s > 0 ? rr[s - 1] : a_m1r) : rr[s];
-            api[s] = lane == 0 ? (s > 0 ? ri[s - 1] : a_m1i) : ri[s];
-            anr[s] = lane == 31 ? (s + 1 < M ? sr[s + 1] : (R)0) : sr[s];
-            ani[s] = lane == 31 ? (s + 1 < M ? si[s + 1] : (R)0) : si[s];
+        for (int s = M - 1; s > 0; --s) {
+            apr[s] = apr[s - 1];
+            api[s] = api[s - 1];
         }
+        apr[0] = lane == 0 ? m1r : rr;
+        api[0] = lane == 0 ? m1i : ri;
+#pragma unroll
+        for (int s = 0; s + 1 < M; ++s) {
+            anr[s] = anr[s + 1];
+            ani[s] = ani[s + 1];
+        }
+        anr[M - 1] = lane == 31 ? (R)0 : sr;  // order -(32M) does not exist
+        ani[M - 1] = lane == 31 ? (R)0 : si;
         if (!full) drop(apr, api);
-        // a_-0 needs no tie here: lane 0's a_0 and a_-0 both came from lane 1's a_-1 (and the
-        // drop never reaches order 0)
     }
 
-    // Eq. 4.17 with q = -1: a_i <- a_{i+1} (i >= 0), a_-1 <- a_0, a_-i <- a_-(i-1)
+    // Eq. 4.17 with q = -1: a_i <- a_{i+1} (i >= 0), a_-1 <- a_0, a_-i <- a_-(i-1).  a_-1 <- a_0
+    // comes from the old a_-0 (tied to a_0); the new a_-0 is tied to the new a_0 at the end.
     __device__ __forceinline__ void shift_down() {
-        const R a0r = __shfl_sync(FULLW, apr[0], 0), a0i = __shfl_sync(FULLW, api[0], 0);
         const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
-        R rr[M], ri[M], sr[M], si[M];
+        const R rr = __shfl_sync(FULLW, apr[0], dn), ri = __shfl_sync(FULLW, api[0], dn);
+        const R sr = __shfl_sync(FULLW, anr[M - 1], up), si = __shfl_sync(FULLW, ani[M - 1], up);
 #pragma unroll
-        for (int s = 0; s < M; ++s) {
-            rr[s] = __shfl_sync(FULLW, apr[s], dn);
-            ri[s] = __shfl_sync(FULLW, api[s], dn);
-            sr[s] = __shfl_sync(FULLW, anr[s], up);
-            si[s] = __shfl_sync(FULLW, ani[s], up);
+        for (int s = 0; s + 1 < M; ++s) {
+            apr[s] = apr[s + 1];
+            api[s] = api[s + 1];
         }
+        apr[M - 1] = lane == 31 ? (R)0 : rr;  // order 32M does not exist
+        api[M - 1] = lane == 31 ? (R)0 : ri;
 #pragma unroll
-        for (int s = 0; s < M; ++s) {  // order 32s + 31 <- 32s + 32; order -32s <- -(32s - 1)
-            apr[s] = lane == 31 ? (s + 1 < M ? rr[s + 1] : (R)0) : rr[s];
-            api[s] = lane == 31 ? (s + 1 < M ? ri[s + 1] : (R)0) : ri[s];
-            R nr = (lane == 0 && s > 0) ? sr[s - 1] : sr[s];
-            R ni = (lane == 0 && s > 0) ? si[s - 1] : si[s];
-            if (s == 0) {  // a_-1 <- a_0
-                nr = lane == 1 ? a0r : nr;
-                ni = lane == 1 ? a0i : ni;
-            }
-            anr[s] = nr;
-            ani[s] = ni;
+        for (int s = M - 1; s > 0; --s) {
+            anr[s] = anr[s - 1];
+            ani[s] = ani[s - 1];
         }
+        anr[0] = sr;  // at lane 0 replaced by the tie below
+        ani[0] = si;
         if (!full) drop(anr, ani);
         tie_zero();  // a_0 <- a_1, and a_-0 with it
     }
@@ -186,7 +184,7 @@ struct Ensemble {
     __device__ __forceinline__ void drop(R (&re)[M], R (&im)[M]) {
 #pragma unroll
         for (int s = 0; s < M; ++s)
-            if (lane + 32 * s > K) {
+            if (M * lane + s > K) {
                 re[s] = (R)0;
                 im[s] = (R)0;
             }
