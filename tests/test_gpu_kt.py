@@ -119,3 +119,21 @@ def test_invalid_kt_inputs(M, ctx):
     rc = M.lib().mrsim_kt_simulate(ctx.h, d.n, M._ptr(d.t1), M._ptr(d.t2), None, None, steps.shape[0], M._ptr(steps),
                                    10, M.FP32, None, M._ptr(np.zeros(2 * d.n * 20)), 11)
     assert rc == M.Status.EINVAL
+
+
+def test_full_size_fingerprint_dictionary_sampled(M, ctx):
+    """The benchmark's workload at full size, in its launch configuration (65 536 ensembles ×
+    1001 steps, K = 127, the seeded dictionary of the benchmark): both precisions on the GPU,
+    sampled ensembles against the oracle one by one (every ensemble is independent)."""
+    rng = np.random.default_rng(W.SEED_BASE + 6)
+    d = W.kt_dictionary(65536, rng)
+    steps = W.kt_fingerprint_sequence(1000, rng)
+    K = 127
+    g64 = M.kt_simulate(ctx, d.t1, d.t2, steps, K, b1=d.b1, df=d.df, precision=M.FP64)
+    g32 = M.kt_simulate(ctx, d.t1, d.t2, steps, K, b1=d.b1, df=d.df, precision=M.FP32)
+    pick = np.sort(np.random.default_rng(7).choice(d.n, 12, replace=False))
+    pick = np.concatenate([[0], pick, [d.n - 1]])
+    for i in pick:
+        ref = ORK.simulate_one(d.t1[i], d.t2[i], d.b1[i], d.df[i], steps, K)
+        assert rel_l2(g64[i], ref) <= TOL64, i
+        assert rel_l2(g32[i], ref) <= TOL32, i
