@@ -119,3 +119,24 @@ def test_rasterized_random_programs_match_oracle(seed, mrsim_lib, oracle_mod):
     # as above: the oracle rounds the phase of every piece, the program that of merged intervals
     assert rel_l2(sig, ref) < 1e-9
     assert np.max(np.abs(state - ref_state)) < 1e-9
+
+
+def test_snapshots_inside_split_intervals(mrsim_lib, oracle_mod):
+    """A snapshot after a piece in the middle of a split readout dwell or rest interval ends the
+    merge there: the state at the snapshot is the oracle's state on that prefix, and the samples
+    are unchanged."""
+    rng = np.random.default_rng(77)
+    ph = W.random_phantom(40, rng)
+    w = W.config1()
+    seq = W.rasterize(W.Sequence(w.sequence.events[: 67 * 3], w.sequence.gamma_hz_per_t), 2.5e-6)
+    ev = seq.events
+    # pieces that are neither the first nor the last of their event: mid-dwell and mid-rest
+    mid = np.nonzero((ev["adc"] == 0) & (ev["rf_flip"] == 0))[0]
+    snaps = np.sort(rng.choice(mid, size=5, replace=False))
+    sig, _, ops, got = interpret(ev, seq.gamma_hz_per_t, ph, snapshots=snaps)
+    ref_sig, _ = oracle_mod.simulate(ph, ev, seq.gamma_hz_per_t)
+    tol = max(1e-12, 2 * 2.0**-53 * len(ev))
+    assert rel_l2(sig, ref_sig) <= tol
+    for q, e in enumerate(snaps):
+        _, st = oracle_mod.simulate(ph, ev[: e + 1], seq.gamma_hz_per_t, want_signal=False, want_state=True)
+        assert np.max(np.abs(got[q] - st)) <= tol, (q, e)
