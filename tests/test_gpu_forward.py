@@ -401,3 +401,28 @@ def test_allocation_failure_from_environment(M):
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.split() == ["ENOMEM", "ok", "4096"], r.stdout
+
+
+def test_rasterized_snapshots_parity(M, ctx, oracle_mod):
+    """Snapshots in the middle of split intervals of a rasterized list (the compiler ends the
+    merge there) in both precisions against the oracle's prefix states."""
+    rng = np.random.default_rng(78)
+    ph = W.random_phantom(1500 + 37, rng)
+    w = W.config1()
+    seq = W.rasterize(W.Sequence(w.sequence.events[: 67 * 4], w.sequence.gamma_hz_per_t), 2.5e-6)
+    ev = seq.events
+    mid = np.nonzero((ev["adc"] == 0) & (ev["rf_flip"] == 0))[0]
+    snaps = np.sort(rng.choice(mid, size=4, replace=False))
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    s = M.Sequence(ctx, ev, seq.gamma_hz_per_t, snapshots=snaps)
+    ref_sig, _ = oracle_mod.simulate(ph, ev, seq.gamma_hz_per_t)
+    refs = [oracle_mod.simulate(ph, ev[: e + 1], seq.gamma_hz_per_t, want_signal=False, want_state=True)[1]
+            for e in snaps]
+    tol64 = max(TOL64, 2 * 2.0**-53 * len(ev))
+    for prec, tol_s, tol_m in ((M.FP64, tol64, tol64), (M.FP32, TOL32, 1e-4)):
+        out = np.zeros((len(snaps), ph.n, 3))
+        sig = M.simulate(ctx, p, s, prec, snapshots=out)
+        ctx.stream_status()
+        assert rel_l2(sig, ref_sig) <= tol_s
+        for q in range(len(snaps)):
+            assert np.max(np.abs(out[q] - refs[q])) <= tol_m, (prec, q)
