@@ -134,7 +134,10 @@ mrsim_status mrsim_phantom_create_device(mrsim_ctx *ctx, int64_t n_spins, const 
                                          const double *z, const double *rho, const double *t1,
                                          const double *t2, const double *dw, void *stream,
                                          mrsim_phantom **out);
+/* Spin count of the phantom (-1 for NULL). */
 int64_t mrsim_phantom_num_spins(const mrsim_phantom *p);
+/* Frees the phantom's device memory (NULL is ignored) with cudaFree, which waits for the device's
+ * outstanding work first. */
 void mrsim_phantom_destroy(mrsim_phantom *p);
 
 /* ---- sequence: elementary sequences (§4.1) compiled once in float64 ------------------- */
@@ -176,6 +179,7 @@ mrsim_status mrsim_sequence_load(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
 mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
                                            double gamma_hz_per_t, int64_t n_snap, const int64_t *snap_after,
                                            mrsim_sequence **out);
+/* Snapshots, samples (the length of the signal) and events of the compiled sequence (-1 for NULL). */
 int64_t mrsim_sequence_num_snapshots(const mrsim_sequence *s);
 int64_t mrsim_sequence_num_adc(const mrsim_sequence *s);
 int64_t mrsim_sequence_num_events(const mrsim_sequence *s);
@@ -269,9 +273,11 @@ typedef struct mrsim_batch mrsim_batch;
 mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
                                 const mrsim_sequence *const *seqs, mrsim_precision prec,
                                 double *const *signals_out, mrsim_batch **out);
+/* Work items (phantom, spin tile) of the batch in its current launch shape (-1 for NULL). */
 int64_t mrsim_batch_num_items(const mrsim_batch *b);
-/* Times every launch shape on a prefix of all programs (about 1e10 spin-steps in total) and keeps
- * the fastest for this batch; returns it in best (other fields zeroed).  Synchronises `stream`. */
+/* Times every launch shape on the same fraction of every program (about 2e10 spin-steps in all),
+ * then the three fastest on about 3e11, and keeps the fastest for this batch; returns it in best
+ * (other fields zeroed).  Synchronises `stream`. */
 mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *best);
 /* Sets the launch shape explicitly (EINVAL / EUNSUPPORTED as for mrsim_simulate_ex). */
 mrsim_status mrsim_batch_set_shape(mrsim_batch *b, int32_t spins_per_thread, int32_t threads_per_block);
@@ -302,6 +308,7 @@ typedef struct mrsim_adjoint mrsim_adjoint;
 mrsim_status mrsim_adjoint_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
                                   double gamma_hz_per_t, const int32_t *rf_param, int32_t n_params,
                                   int32_t ckpt_every, mrsim_adjoint **out);
+/* Samples of the adjoint's event list (the length of its signal; -1 for NULL). */
 int64_t mrsim_adjoint_num_adc(const mrsim_adjoint *adj);
 /* Forward simulation that also stores the checkpoints.  rf_values: device array of n_params flip
  * angles [rad] (may be NULL when n_params = 0); signal_out: device, 2*num_adc doubles.
@@ -314,6 +321,7 @@ mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, 
 mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph, const double *rf_values,
                                     const double *dl_dsignal, void *stream, double *d_rho, double *d_t1,
                                     double *d_t2, double *d_rf);
+/* Frees the adjoint's device tables and checkpoint storage (NULL is ignored). */
 void mrsim_adjoint_destroy(mrsim_adjoint *adj);
 
 /* ---- batches without allocation ---------------------------------------------------------- */
