@@ -3,13 +3,27 @@
 A step is one forward simulation (all operations of the hot path: RF rotations, precession and
 relaxation of every spin through every event, and the per-sample signal sum) of the workload's
 phantom through its sequence, with inputs resident in device memory.  Default workload: the
-2D 256² spin echo (4 isochromats/voxel, sinc 90/180 pulses, B0 + fat; `--workload c2`).
+3D 128³ RF-spoiled gradient echo (2 isochromats/voxel, 4 194 304 spins, 2 146 304 events;
+`--workload c3`); `--workload c1|c2|c4|c5|kt` gives the others.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1|c4|c5|kt] [--impl ours|reference]
 
 N > 1 (torchrun): weak scaling — every rank simulates its own phantom of the workload's size
 (a different seed), the ranks' phantoms form one object, and the per-step exchange is the
 sum-reduce of the complex signal over ranks (NCCL all-reduce).
+
+Roofline: FP32 lane-operations of the per-event model (an ADC event that repeats the previous
+event's gradient and duration 7, an RF event 9, any other event 12, plus 3/k per sample for the
+shared-memory transpose of k spins per thread) per launch, over the kernel's CUDA-event time,
+against SMs (read from the device) x 128 FP32 lanes x the SM clock sampled during the timed
+region.  Beside it: the stricter formulation model (the arithmetic the pulse-frame formulation
+needs) and the multiply-add rates a probe kernel measures on the same device in the same run
+(float32, float32 pairs, float64; the float64 figure is the float64 path's peak).
+
+Oracle parity: the float64 CPU oracle on a seeded spin sample (1 % of C3's spins by default)
+against the GPU signal of the same spins taken from a launch of the whole phantom in the timed
+launch shape, with every other spin's M0 set to zero (their contribution is exactly zero), so
+the sample runs through the benchmark's own blocks and cross-block sums.
 
 The reference arm (`--impl reference`) times the FP64 CPU oracle on the host cores, on a
 bounded spin sample of the same workload.
@@ -45,8 +59,13 @@ METRIC = "spin-steps/s (isochromat×event updates) at 1 GB300, FP32 vs FP64, % F
 #   RF event : hard pulse in its own frame (4) + T1 recovery of Mz (2) + precession (4)
 #   other    : precession (4); T1 recovery is folded into the next pulse
 OPS_ADC, OPS_RF, OPS_OTHER = 6, 10, 4
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP64_NOMINAL_GFLOPS = 1250.0  # GB300 float64 (profiling recipe; no measured figure)
+# Per-event model of the FP32 work per spin-step (FMA = 1): an ADC event that repeats the previous
+# event's (G, Δt) reuses the spin's rotation factor (7), an RF event is the 3x3 rotation (9), any
+# other event is a precession-relaxation with a fresh phase (12); each sample also costs 3/k for
+# the shared-memory transpose of its partial sums with k spins per thread.
+EV_ADC_REPEAT, EV_RF, EV_OTHER, EV_SAMPLE_TRANSPOSE = 7, 9, 12, 3
+FP32_LANES = 128      # FP32 lanes per SM (unit count)
+SM_MAX_MHZ = 2070.0   # used only when no clock sample exists
 
 
 def algorithmic_ops_per_spin(events, n_coils: int = 0) -> int:
@@ -70,17 +89,85 @@ def ring_coils(phantom, n_coils: int, radius: float = 0.3, width: float = 0.25):
     return np.exp(-d2 / width**2) * np.exp(1j * (ang[:, None] + 4.0 * phantom.x[None, :] * np.cos(ang)[:, None]))
 
 
-def fp32_alu_peak_ops(sm_mhz: float = SM_MAX_MHZ) -> float:
-    return SMS * FP32_LANES * sm_mhz * 1e6
+def per_event_ops_per_spin(events, spins_per_thread: int) -> float:
+    """FP32 lane-ops per spin over the sequence by the per-event model (EV_*)."""
+    ev = events
+    adc = ev["adc"] != 0
+    rf = ev["rf_flip"] != 0
+    same = np.zeros(len(ev), dtype=bool)
+    if len(ev) > 1:
+        same[1:] = ((ev["dt"][1:] == ev["dt"][:-1]) & (ev["gx"][1:] == ev["gx"][:-1])
+                    & (ev["gy"][1:] == ev["gy"][:-1]) & (ev["gz"][1:] == ev["gz"][:-1]))
+    n_rf = int(np.count_nonzero(rf))
+    n_adc_rep = int(np.count_nonzero(adc & ~rf & same))
+    n_other = len(ev) - n_rf - n_adc_rep
+    return (EV_RF * n_rf + EV_ADC_REPEAT * n_adc_rep + EV_OTHER * n_other
+            + EV_SAMPLE_TRANSPOSE / max(int(spins_per_thread), 1) * int(np.count_nonzero(adc)))
+
+
+# Device facts and measured rates, filled by measure_device() before any timed region.
+DEVICE = {"sms": None, "fp32_lane_ops_per_s": None, "fp32x2_lane_ops_per_s": None, "fp64_lane_ops_per_s": None,
+          "probe_sm_mhz": None}
+
+
+def measure_device(ctx, M, device: int, stream=None) -> dict:
+    """SM count from the device, and the multiply-add rates the library's probe kernel reaches on
+    it (float32, float32 pairs, float64; about 0.3 s each), with the SM clock sampled meanwhile."""
+    import torch
+
+    DEVICE["sms"] = torch.cuda.get_device_properties(device).multi_processor_count
+    ck = ClockSampler(device, tag="probe")
+    ck.start()
+    time.sleep(0.1)
+    for key, kind in (("fp32_lane_ops_per_s", M.FMA_F32), ("fp32x2_lane_ops_per_s", M.FMA_F32X2),
+                      ("fp64_lane_ops_per_s", M.FMA_F64)):
+        DEVICE[key] = M.measure_fma_rate(ctx, kind, 300.0, stream=stream)[0]
+    DEVICE["probe_sm_mhz"] = ck.stop().get("sm_mhz")
+    return dict(DEVICE)
+
+
+def sm_clock(ck: dict) -> float:
+    """The SM clock of a peak: the median sampled under load in the timed region, else the maximum."""
+    return float(ck.get("sm_mhz") or ck.get("sm_max_mhz") or SM_MAX_MHZ)
+
+
+def fp32_alu_peak_ops(sm_mhz: float) -> float:
+    """Unit-count FP32 rate: SMs (from the device) x 128 lanes x the SM clock."""
+    return DEVICE["sms"] * FP32_LANES * sm_mhz * 1e6
+
+
+def fp32_roofline(achieved_g: float, ck: dict, **extra) -> dict:
+    """FP32 lane-ops against the unit-count peak at the sampled clock, and against the measured
+    float32 multiply-add rate of the same device."""
+    mhz = sm_clock(ck)
+    peak = fp32_alu_peak_ops(mhz) / 1e9
+    r = {"bound": "alu", "achieved": achieved_g, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved_g / peak,
+         "peak_basis": f"{DEVICE['sms']} SMs (device) x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (median SM clock "
+                       "sampled in the timed region)"}
+    r.update(extra)
+    meas = max(DEVICE["fp32_lane_ops_per_s"] or 0.0, DEVICE["fp32x2_lane_ops_per_s"] or 0.0) / 1e9
+    if meas:
+        r["measured_fma"] = {"peak": meas, "frac": achieved_g / meas, "sm_mhz": DEVICE["probe_sm_mhz"],
+                             "basis": "float32 multiply-add chains (scalar or pairs, the faster) on every SM, "
+                                      "CUDA-event timed in this run"}
+    return r
 
 
 def fp64_roofline(achieved_g: float) -> dict:
-    """Algorithmic lane-ops of a float64 run against the float64 FMA rate (G lane-ops/s)."""
-    peak = FP64_NOMINAL_GFLOPS / 2
+    """Algorithmic lane-ops of a float64 run against the float64 multiply-add rate measured on the
+    same device in the same run (G lane-ops/s)."""
+    peak = DEVICE["fp64_lane_ops_per_s"] / 1e9
     return {"bound": "fp64", "achieved": achieved_g, "peak": peak, "unit": "G float64 lane-ops/s",
             "frac": achieved_g / peak, "traffic": None,
-            "peak_basis": "nominal float64 rate of the profiling recipe, 1.25 TFLOP/s = 0.625 T FMA lane-ops/s "
-                          "(no measured float64 figure)"}
+            "peak_basis": "float64 multiply-add chains on every SM, CUDA-event timed in this run "
+                          f"(SM clock {DEVICE['probe_sm_mhz']} MHz)"}
+
+
+def measured_rates() -> dict:
+    return {"sms": DEVICE["sms"], "sm_mhz": DEVICE["probe_sm_mhz"],
+            "fp32_G_lane_ops_per_s": (DEVICE["fp32_lane_ops_per_s"] or 0) / 1e9,
+            "fp32x2_G_lane_ops_per_s": (DEVICE["fp32x2_lane_ops_per_s"] or 0) / 1e9,
+            "fp64_G_lane_ops_per_s": (DEVICE["fp64_lane_ops_per_s"] or 0) / 1e9}
 
 
 def build_workload(name: str, rank: int = 0):
@@ -119,12 +206,12 @@ class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, tag: str = "timed"):
         self.device = device
         self.proc = None
         # the raw samples go to $MRSIM_CLOCKS_DIR when set (kept beside the run's other logs)
         d = os.environ.get("MRSIM_CLOCKS_DIR") or tempfile.gettempdir()
-        self.path = os.path.join(d, f"clocks_rank{device}_{os.getpid()}.csv")
+        self.path = os.path.join(d, f"clocks_{tag}_rank{device}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -230,6 +317,85 @@ def oracle_parity(ctx, M, w, sub, ref, n_coils: int = 0):
     return out
 
 
+def sample_index(ph, fraction: float, seed: int = 7) -> np.ndarray:
+    """Seeded sample of `fraction` of the phantom's spin count (all spins for fraction >= 1), drawn
+    from the spins with M0 > 0 (air spins contribute nothing to the signal), sorted."""
+    n = ph.n
+    if fraction >= 1.0:
+        return np.arange(n)
+    m = max(1, int(round(fraction * n)))
+    pool = np.nonzero(ph.rho > 0)[0]
+    if pool.size < m:
+        pool = np.arange(n)
+    return np.sort(np.random.default_rng(seed).choice(pool, min(m, pool.size), replace=False))
+
+
+def masked_phantom(ph, idx):
+    """The phantom with M0 = 0 for every spin outside idx: such a spin stays at (0, 0, 0) through
+    every event, so the signal is that of the sample alone while the launch covers every spin."""
+    rho = np.zeros_like(ph.rho)
+    rho[idx] = ph.rho[idx]
+    return W.Phantom(ph.x, ph.y, ph.z, rho, ph.t1, ph.t2, ph.dw)
+
+
+class OracleRun:
+    """A host thread running `signal_fn(sub, sequence, n_threads=cores)` on a spin sample of a
+    workload (the C oracle releases the interpreter while it runs on all host cores)."""
+
+    def __init__(self, w, idx, signal_fn):
+        import threading
+
+        self.w, self.idx, self.fn, self.ref, self.err, self.seconds = w, idx, signal_fn, None, None, None
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _run(self):
+        try:
+            sub = self.w.phantom.subset(self.idx)
+            t0 = time.perf_counter()
+            self.ref = self.fn(sub, self.w.sequence, n_threads=len(os.sched_getaffinity(0)))
+            self.seconds = time.perf_counter() - t0
+        except Exception as e:  # reported in the line
+            self.err = repr(e)
+
+    def join(self):
+        self.thread.join()
+        return self.ref
+
+
+def cpu_baseline_parity_run(w, idx) -> OracleRun:
+    """CPU-baseline leg: the float64 oracle, as it stands, on the parity sample, started on a host
+    thread while the GPU legs run."""
+    import oracle
+
+    return OracleRun(w, idx, oracle.signal)
+
+
+def oracle_parity_sample(ctx, M, w, run: OracleRun, seq, shape, stream=None):
+    """The oracle's signal of a spin sample against the GPU's: float32 from a launch of the whole
+    phantom with M0 = 0 outside the sample, in the timed launch shape (the sample's spins sit in
+    the benchmark's own blocks and go through its cross-block sums); float64 from the sample
+    alone."""
+    ref = run.join()
+    if ref is None:
+        return {"error": run.err}
+    out = {"sample_spins": int(run.idx.size), "of_spins": int(w.phantom.n),
+           "sample_fraction": run.idx.size / max(w.phantom.n, 1), "oracle_s": run.seconds,
+           "fp32_launch": f"whole phantom, M0 = 0 outside the sample, {shape[0]} spins/thread x {shape[1]} threads"}
+    nr = float(np.linalg.norm(ref))
+    pm = M.Phantom.from_workload_phantom(ctx, masked_phantom(w.phantom, run.idx), stream=stream)
+    got32 = M.simulate(ctx, pm, seq, M.FP32, spins_per_thread=shape[0], threads_per_block=shape[1])
+    pm.close()
+    ps = M.Phantom.from_workload_phantom(ctx, w.phantom.subset(run.idx), stream=stream)
+    got64 = M.simulate(ctx, ps, seq, M.FP64)
+    ps.close()
+    for name, got in (("fp32", got32), ("fp64", got64)):
+        rel = float(np.linalg.norm(got - ref) / nr) if nr > 0 else 0.0
+        out[f"{name}_rel_l2"] = rel
+        out[f"{name}_db"] = 20 * math.log10(rel) if rel > 0 else None
+    return out
+
+
 def rasterized(w, raster: float):
     """The stress variant of a workload: every event cut into pieces of at most `raster` seconds
     (same signal, many more events; the spin-step count is that of the pieces)."""
@@ -284,6 +450,7 @@ def run_batch(args):
     ctx = M.Context(0)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", 0)
+    measure_device(ctx, M, 0, stream)
     phs = [M.Phantom(ctx, [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()], stream=stream) for w in ws]
     sqs = [M.Sequence.from_workload_sequence(ctx, w.sequence) for w in ws]
     outs = [torch.zeros(max(2 * q.n_adc, 2), dtype=torch.float64, device=dev) for q in sqs]
@@ -314,9 +481,10 @@ def run_batch(args):
     ck = clocks.stop()
     ctx.stream_status(stream)
     ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
-    ops = sum(algorithmic_ops_per_spin(w.sequence.events) * w.phantom.n for w in ws)
+    form_ops = sum(algorithmic_ops_per_spin(w.sequence.events) * w.phantom.n for w in ws)
+    ops = sum(per_event_ops_per_spin(w.sequence.events, shape[0]) * w.phantom.n for w in ws)
     achieved = ops / (ms * 1e-3) / 1e9
-    peak = fp32_alu_peak_ops() / 1e9
+    form_g = form_ops / (ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": spin_steps / (ms * 1e-3), "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -326,11 +494,14 @@ def run_batch(args):
                    "launch": {"spins_per_thread": shape[0], "threads_per_block": shape[1], "tune_s": tune_s,
                               "mode": "persistent kernel + work queue, CUDA graph replay"},
                    "l2": "flushed between timed steps (256 MB write, outside the step events)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s",
-                     "frac": achieved / peak,
-                     "traffic": traffic_for(kernel_source_sha(), "c4_batch64") if prec == M.FP32 else None,
-                     "kernel_ms": ms, "ops_per_spin_step": ops / spin_steps},
-        "gpu_launches": 2 * args.steps, "clocks": ck, "source": source_id(),
+        "roofline": fp64_roofline(achieved) if prec == M.FP64 else fp32_roofline(
+            achieved, ck, traffic=traffic_for(kernel_source_sha(), "c4_batch64"), kernel_ms=ms,
+            ops_per_spin_step=ops / spin_steps,
+            op_model=f"per event: ADC repeating the previous (G, dt) {EV_ADC_REPEAT}, RF {EV_RF}, other {EV_OTHER}, "
+                     f"+ {EV_SAMPLE_TRANSPOSE}/k per sample with k = {shape[0]} spins per thread",
+            formulation_model={"ops_per_spin_step": form_ops / spin_steps, "achieved": form_g,
+                               "frac": form_g / (fp32_alu_peak_ops(sm_clock(ck)) / 1e9)}),
+        "gpu_launches": 2 * args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id(),
     }
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample of the batch's longest program
         wl = max(ws, key=lambda w: w.sequence.n_events)
@@ -366,6 +537,7 @@ def run_adjoint(args):
     ctx = M.Context(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
+    measure_device(ctx, M, 0, stream)
     adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf0), ckpt_every=64)
     P = M.Phantom(ctx, [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()], stream=stream)
     rfd = torch.from_numpy(rf0.copy()).to(dev)
@@ -403,17 +575,19 @@ def run_adjoint(args):
                   + ADJ_FLOPS_BWD * n_ev + ADJ_FLOPS_BWD_RF * n_rf)
     flops = flops_spin * w.phantom.n
     achieved = flops / (ms * 1e-3) / 1e9
+    fp64_peak = 2 * DEVICE["fp64_lane_ops_per_s"] / 1e9
     line = {"metric": "spin-steps/s of forward+backward (adjoint) at 1 GB300", "value": w.spin_steps / (ms * 1e-3),
             "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": len(ev), "n_rf_params": len(rf0),
                        "ckpt_every": 64, "step": "adjoint forward + backward",
                        "note": "float64-pipe bound (ncu: the backward kernel keeps it 71 % busy with 4 warps per SM); the flop model counts the formulation's arithmetic, about half the executed float64 instructions"},
-            "roofline": {"bound": "fp64", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (float64)",
-                         "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None, "kernel_ms": ms,
-                         "peak_basis": "nominal float64 rate of the profiling recipe (no measured float64 figure)",
+            "roofline": {"bound": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s (float64)",
+                         "frac": achieved / fp64_peak, "traffic": None, "kernel_ms": ms,
+                         "peak_basis": "2 x the float64 multiply-add rate measured on every SM in this run "
+                                       f"(SM clock {DEVICE['probe_sm_mhz']} MHz)",
                          "flops_per_spin_step": flops_spin / n_ev},
-            "gpu_launches": 4 * args.steps, "clocks": ck, "source": source_id()}
+            "gpu_launches": 4 * args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id()}
     if not args.no_cpu_baseline:  # the oracle's forward-mode gradient (every flip) on a bounded spin sample
         import oracle
 
@@ -462,6 +636,7 @@ def run_kt(args):
     ctx = M.Context(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
+    measure_device(ctx, M, 0, stream)
     par = [torch.from_numpy(a.copy()).to(dev) for a in (d.t1, d.t2, d.b1, d.df)]
     out = torch.zeros(n_sets * 2 * n_samples, dtype=torch.float64, device=dev)
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -489,7 +664,6 @@ def run_kt(args):
     ens_steps = n_sets * len(steps)
     ops = ens_steps * (K + 1) * KT_OPS_PER_ORDER
     achieved = ops / (ms * 1e-3) / 1e9
-    peak = fp32_alu_peak_ops() / 1e9
     line = {"metric": "ensemble-steps/s of the K-t formalism (configuration populations) at 1 GB300",
             "value": ens_steps / (ms * 1e-3), "unit": "ensemble-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -500,10 +674,10 @@ def run_kt(args):
                        "l2": "flushed between timed steps (256 MB write, outside the step events)"},
             "roofline": dict(fp64_roofline(achieved), kernel_ms=ms, ops_per_order_step=KT_OPS_PER_ORDER)
             if prec == M.FP64 else
-            {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
-             "traffic": traffic_for(kernel_source_sha(KT_SOURCES), f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}"),
-             "kernel_ms": ms, "ops_per_order_step": KT_OPS_PER_ORDER},
-            "gpu_launches": 2 * args.steps, "clocks": ck, "source": source_id()}
+            fp32_roofline(achieved, ck,
+                          traffic=traffic_for(kernel_source_sha(KT_SOURCES), f"kt_fingerprint_{n_sets}x{len(steps)}_K{K}"),
+                          kernel_ms=ms, ops_per_order_step=KT_OPS_PER_ORDER),
+            "gpu_launches": 2 * args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id()}
     if not args.no_cpu_baseline:
         from oracle import kt as ORK
 
@@ -566,6 +740,7 @@ def run_ours(args):
     ctx = M.Context(local)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
+    measure_device(ctx, M, local, stream)
     arrs = [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()]
     ph = M.Phantom(ctx, arrs, stream=stream)
     seq = M.Sequence.from_workload_sequence(ctx, w.sequence)
@@ -585,6 +760,13 @@ def run_ours(args):
         t0 = time.perf_counter()
         tuned = M.autotune(ctx, ph, seq, prec, stream=stream)
         tuned = {"spins_per_thread": tuned[0], "threads_per_block": tuned[1], "tune_s": time.perf_counter() - t0}
+    if n_coils:
+        k_spins = 2 if prec == M.FP32 else 1  # the coil kernels' fixed spins per thread
+    else:
+        k_spins = kw.get("spins_per_thread") or (tuned or {}).get("spins_per_thread") or 8
+    # the launch shape of the timed runs (0, 0: the library's choice)
+    shape = (kw.get("spins_per_thread") or (tuned or {}).get("spins_per_thread") or 0,
+             kw.get("threads_per_block") or (tuned or {}).get("threads_per_block") or 0)
 
     def simulate_once():
         if n_coils:
@@ -599,6 +781,14 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     ctx.stream_status(stream)
+
+    # the float64 oracle on a spin sample runs on the host cores meanwhile (rank 0, plain lists)
+    extras = rank == 0 and not args.skip_extra and not n_coils
+    frac = args.oracle_fraction if args.oracle_fraction >= 0 else {"c1": 1.0, "c2": 1.0, "c3": 0.01}[args.workload]
+    orun = None
+    if extras and not args.no_cpu_baseline and not args.raster and not args.events and frac > 0:
+        orun = cpu_baseline_parity_run(w, sample_index(w.phantom, frac))
+
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -625,46 +815,61 @@ def run_ours(args):
     value = world * spin_steps / (ms_per_step * 1e-3)
 
     # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
-    ops = algorithmic_ops_per_spin((canonical if args.raster else w.sequence).events, n_coils) * w.phantom.n
-    achieved = ops / (kern_ms * 1e-3) / 1e9
+    base_ev = (canonical if args.raster else w.sequence).events
+    form_ops = algorithmic_ops_per_spin(base_ev, n_coils) * w.phantom.n
+    form_g = form_ops / (kern_ms * 1e-3) / 1e9
     sha = kernel_source_sha()
-    if prec == M.FP64:  # the same algorithmic lane-ops against the float64 FMA rate
-        roof = dict(fp64_roofline(achieved), kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps)
+    if n_coils:  # the per-event model has no coil term: the formulation model is the algorithmic work
+        ops, model = form_ops, "formulation model with receive coils (a sample costs 4 + 4 per coil)"
     else:
-        peak = fp32_alu_peak_ops() / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP32 lane-ops/s", "frac": achieved / peak,
-                "traffic": traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else "")), "kernel_ms": kern_ms,
-                "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {SM_MAX_MHZ:.0f} MHz (max SM clock)",
-                "ops_per_spin_step": ops / spin_steps}
+        ops = per_event_ops_per_spin(base_ev, k_spins) * w.phantom.n
+        model = (f"per event: ADC repeating the previous (G, dt) {EV_ADC_REPEAT}, RF {EV_RF}, other {EV_OTHER}, "
+                 f"+ {EV_SAMPLE_TRANSPOSE}/k per sample with k = {k_spins} spins per thread")
+    achieved = ops / (kern_ms * 1e-3) / 1e9
+    if prec == M.FP64:  # the same algorithmic lane-ops against the measured float64 rate
+        roof = dict(fp64_roofline(achieved), kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps, op_model=model)
+    else:
+        roof = fp32_roofline(
+            achieved, ck, traffic=traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else "")),
+            kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps, op_model=model,
+            formulation_model={"ops_per_spin_step": form_ops / spin_steps, "achieved": form_g,
+                               "frac": form_g / (fp32_alu_peak_ops(sm_clock(ck)) / 1e9),
+                               "basis": f"ADC {OPS_ADC}, RF {OPS_RF}, other {OPS_OTHER} (pulse-frame formulation)"})
 
     out = {}
-    if rank == 0 and not args.skip_extra and not n_coils:
+    if extras:
         # float64 GPU path on the same workload, and its agreement with float32
         s32 = sig.clone()
         if dist:
             M.simulate(ctx, ph, seq, M.FP32, stream=stream, out=s32, **kw)
         other = M.FP32 if prec == M.FP64 else M.FP64
         so = torch.zeros_like(sig)
-        M.simulate(ctx, ph, seq, other, stream=stream, out=so)
-        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        reps = 2
+        if kern_ms < 200.0:  # short kernels: one untimed run, then two timed ones
+            M.simulate(ctx, ph, seq, other, stream=stream, out=so)
+            reps = 2
+        else:  # a long kernel is timed on its one run (launch overheads are negligible)
+            reps = 1
+        torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(reps):
             M.simulate(ctx, ph, seq, other, stream=stream, out=so)
         e1.record(stream)
         torch.cuda.synchronize()
+        ctx.stream_status(stream)
         o_ms = e0.elapsed_time(e1) / reps
         a32 = (s32 if prec == M.FP32 else so).cpu().numpy().view(np.complex128)
         a64 = (so if prec == M.FP32 else s32).cpu().numpy().view(np.complex128)
         rel = float(np.linalg.norm(a32 - a64) / np.linalg.norm(a64))
         key = "fp64_gpu" if prec == M.FP32 else "fp32_gpu"
-        out[key] = {"value": spin_steps / (o_ms * 1e-3), "unit": "spin-steps/s", "ms_per_step": o_ms}
-        if key == "fp64_gpu":  # the same algorithmic lane-ops against the float64 FMA rate
+        out[key] = {"value": spin_steps / (o_ms * 1e-3), "unit": "spin-steps/s", "ms_per_step": o_ms, "runs": reps}
+        if key == "fp64_gpu":  # the same algorithmic lane-ops against the measured float64 rate
             out[key]["roofline"] = fp64_roofline(ops / (o_ms * 1e-3) / 1e9)
         out["fp32_vs_fp64_gpu_rel_l2"] = rel
         out["fp32_vs_fp64_gpu_db"] = 20 * math.log10(rel) if rel > 0 else None
+        if orun is not None:
+            out["oracle_parity"] = oracle_parity_sample(ctx, M, w, orun, seq, shape, stream)
 
         # end to end through the public API with host buffers (pinned), copies inside the region
         pinned = [torch.from_numpy(a).pin_memory() for a in w.phantom.arrays()]
@@ -672,6 +877,7 @@ def run_ours(args):
         ev_pinned = torch.from_numpy(w.sequence.events.view(np.uint8)).pin_memory().numpy().view(W.EVENT_DTYPE)
         host_sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64).pin_memory().numpy().view(np.complex128)
         e2e_steps = max(3, min(args.steps, 20))
+        serial_steps = e2e_steps if kern_ms < 200.0 else 3
         gamma = w.sequence.gamma_hz_per_t
 
         def e2e_serial_step():
@@ -703,10 +909,10 @@ def run_ours(args):
         e2e_pipelined(2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+        for _ in range(serial_steps):
             e2e_serial_step()
         torch.cuda.synchronize()
-        serial_s = (time.perf_counter() - t0) / e2e_steps
+        serial_s = (time.perf_counter() - t0) / serial_steps
         t0 = time.perf_counter()
         e2e_pipelined(e2e_steps)
         torch.cuda.synchronize()
@@ -718,11 +924,12 @@ def run_ours(args):
                       "d2h_bytes_per_step": int(16 * seq.n_adc), "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
                       "pipeline": "the next step's host compile runs on a worker thread during this step's "
                                   "uploads, kernel and read-back (first compile not overlapped)",
-                      "serial_ms_per_step": serial_s * 1e3}
-        if not args.no_cpu_baseline:
+                      "serial_ms_per_step": serial_s * 1e3, "serial_steps": serial_steps}
+        if not args.no_cpu_baseline:  # the oracle alone on the host cores, on a bounded sample
             cb, (sub, ref) = cpu_baseline(w, seconds=args.cpu_seconds)
             out["cpu_baseline"] = cb
-            out["oracle_parity"] = oracle_parity(ctx, M, w, sub, ref)
+            if orun is None:
+                out["oracle_parity"] = oracle_parity(ctx, M, w, sub, ref)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
@@ -737,6 +944,7 @@ def run_ours(args):
                        **({"stress_mode": RASTER_NOTE.format(r=args.raster * 1e6, n=canonical.n_events)}
                           if args.raster else {})},
             "roofline": roof, "gpu_launches": args.steps, "clocks": ck, "wall_s_timed": t_wall,
+            "measured_rates": measured_rates(),
             "peaks_file": {k: read_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
             "source": source_id(),
         }
@@ -753,12 +961,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "kt"], default="c2")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "kt"], default="c3")
     ap.add_argument("--kt-sets", type=int, default=65536, help="ensembles of the K-t workload")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--spins-per-thread", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--oracle-fraction", type=float, default=-1.0,
+                    help="oracle-parity sample as a fraction of the spin count, drawn from spins with M0 > 0 "
+                         "(default: c1, c2 all spins; c3 1 %%)")
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")

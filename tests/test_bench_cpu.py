@@ -75,6 +75,18 @@ def test_algorithmic_work_model(bench):
     assert bench.algorithmic_ops_per_spin(ev) == 10 + 6 + 6 + 4 + 14
     # with receive coils a sample costs the precession plus one weighted sum per coil
     assert bench.algorithmic_ops_per_spin(ev, n_coils=3) == 10 + 2 * 16 + 4 + (16 + 10 - 4 + 2)
+    # the per-event model: RF 9; a sample that repeats the previous event's (G, dt) 7, one that does
+    # not 12; any other event 12; plus 3/k per sample for k spins per thread
+    assert bench.per_event_ops_per_spin(ev, 4) == 9 + 12 + 7 + 12 + 9 + 3 * 3 / 4
+    assert bench.per_event_ops_per_spin(ev, 1) == 9 + 12 + 7 + 12 + 9 + 3 * 3
+    # C2's mix: 65 280 repeating and 256 other samples, 65 536 sub-pulses, 1 536 other events
+    w2 = W.config2()
+    ev2 = w2.sequence.events
+    per = bench.per_event_ops_per_spin(ev2, 8) / len(ev2)
+    n_adc = int(np.count_nonzero(ev2["adc"]))
+    n_rf = int(np.count_nonzero(ev2["rf_flip"] != 0))
+    assert n_adc == 65536 and n_rf == 65536
+    assert abs(per - (7 * (n_adc - 256) + 12 * (256 + len(ev2) - n_adc - n_rf) + 9 * n_rf + 3 / 8 * n_adc) / len(ev2)) < 1e-12
     # a rasterized list has more events but the same canonical work (the roofline uses the latter)
     w = W.config1()
     r = bench.rasterized(w, 1e-5)
