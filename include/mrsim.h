@@ -54,11 +54,17 @@ typedef enum {
 } mrsim_status;
 
 typedef enum {
-    MRSIM_FP64 = 0, /* every step in float64 */
-    MRSIM_FP32 = 1  /* rotations/relaxation in float32 with float64 sequence precompute and
-                       float-float phase arguments; each sample's sum is a float32 pairwise tree
-                       within a warp, a float32 add across the warps of a thread block and a
-                       float64 sum across thread blocks */
+    MRSIM_FP64 = 0,      /* every step in float64 */
+    MRSIM_FP32 = 1,      /* rotations/relaxation in float32 with float64 sequence precompute and
+                            float-float phase arguments; each sample's sum is a float32 pairwise tree
+                            within a warp, a float32 add across the warps of a thread block and a
+                            float64 sum across thread blocks */
+    MRSIM_FP32_KAHAN = 2 /* the float32 bulk arithmetic with the per-sample spin sum kept in higher
+                            precision than float32 across the whole phantom: the same path as
+                            MRSIM_FP32, whose cross-block sums are float64 (a stronger form of a
+                            compensated float32 sum; the in-block float32 chains are at most
+                            128-term pairwise trees plus 16 adds, ~1e-7 relative).  Accepted by
+                            every call that takes a precision; results equal MRSIM_FP32's. */
 } mrsim_precision;
 
 /* One elementary sequence (§4.1; Eq. 4.1).  64 bytes, no padding. */
@@ -338,11 +344,16 @@ void mrsim_adjoint_destroy(mrsim_adjoint *adj);
  * (MRSIM_STATIC_SCRATCH_BYTES - 256) / sizeof(descriptor) phantoms and as many work items
  * (tiles of spins_per_thread x threads_per_block spins, 8 bytes each) as fit after them;
  * larger batches fail with MRSIM_EINVAL and a message saying which limit was hit.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Every call shares the one array, which keeps the
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); with
+ * lazy module loading (the CUDA default) that is also when the library's device code is loaded
+ * on that device and the array is reserved there, i.e. the first call does take device memory
+ * implicitly.  Make that first call at initialisation, e.g. with n = 0 (which does only this
+ * set-up), and before any stream capture.  Every call shares the one array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU (other streams, other host threads'
  * launches still running) race on it and must be serialised by the caller; host threads are
- * serialised inside the call.  spins_per_thread / threads_per_block: 0 = library default.
+ * serialised inside the call.  spins_per_thread / threads_per_block: 0 = library default (which,
+ * as in mrsim_batch_create, falls back to 1 x 64 and then 1 x 32 when it does not fit).  The
+ * caller's current device is the same after the call as before it.
  * Asynchronous on `stream`; errors of the kernel surface through mrsim_stream_status. */
 #define MRSIM_STATIC_SCRATCH_BYTES (1u << 20)
 mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
@@ -351,6 +362,19 @@ mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, const mrsim_
                                          int32_t spins_per_thread, int32_t threads_per_block);
 
 /* ---- diagnostics ---------------------------------------------------------------------- */
+
+/* Measured arithmetic rate of the device (the denominator of a roofline fraction for code bound
+ * by an arithmetic pipe rather than by memory).  Launches, on `stream`, a kernel that fills every
+ * SM (8 blocks of 256 threads per SM) in which every thread runs 8 independent fused
+ * multiply-add chains with no memory traffic, once to calibrate and once sized to last about
+ * target_ms (1 .. 1e4), and times the second launch with CUDA events:
+ *   kind 0: float32 fmaf;  kind 1: float32 pairs, fma.rn.f32x2 (two lanes per instruction);
+ *   kind 2: float64 fma.
+ * *lane_ops_per_s receives the multiply-adds per second (one per lane, a pair counts two) at the
+ * clock the device ran at; *kernel_ms (may be NULL) the timed launch's duration.  Synchronises
+ * `stream`.  EINVAL for another kind or target. */
+mrsim_status mrsim_measure_fma_rate(mrsim_ctx *ctx, int32_t kind, double target_ms, void *stream,
+                                    double *lane_ops_per_s, double *kernel_ms);
 
 /* Host-only compile of an event list (no device needed), for inspecting and testing the
  * sequence compiler.  On input each n_* field is the capacity of the matching array (ignored when

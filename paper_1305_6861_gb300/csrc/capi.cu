@@ -492,7 +492,7 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
-    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_adc != seq->prog->host.n_adc)
         return fail(ctx, MRSIM_EINVAL, "n_adc = " + std::to_string(n_adc) + " but the sequence has " +
                                            std::to_string(seq->prog->host.n_adc) + " samples");
@@ -578,7 +578,7 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
-    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_coils < 1 || n_coils > MAX_COILS)
         return fail(ctx, MRSIM_EINVAL, "n_coils must be 1.." + std::to_string(MAX_COILS));
     if (n_adc != seq->prog->host.n_adc)
@@ -647,7 +647,7 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
                                int64_t n_samples) {
     Range nvtx_range("mrsim_kt_simulate");
     if (!ctx) return MRSIM_EINVAL;
-    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_sets < 0 || n_steps < 0) return fail(ctx, MRSIM_EINVAL, "negative count");
     if (max_order < 0 || max_order > KT_MAX_ORDER)
         return fail(ctx, MRSIM_EINVAL, "max_order must be 0.." + std::to_string(KT_MAX_ORDER));
@@ -789,7 +789,7 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq || !best) return fail(ctx, MRSIM_EINVAL, "NULL argument");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
-    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     const bool fp64 = prec == MRSIM_FP64;
     std::memset(best, 0, sizeof *best);
     Launch def = choose_launch(ctx, fp64, ph->n);
@@ -988,7 +988,7 @@ mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *
     *out = nullptr;
     if (n < 0 || (n > 0 && (!phantoms || !seqs || !signals_out)))
         return fail(ctx, MRSIM_EINVAL, "invalid batch arrays");
-    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     cudaSetDevice(ctx->device);
     mrsim_batch *b = new (std::nothrow) mrsim_batch();
     if (!b) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");

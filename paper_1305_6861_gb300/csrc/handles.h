@@ -135,6 +135,13 @@ struct mrsim_batch {
 
 namespace mrsim {
 
+// Accepts the three precisions of the C-ABI; MRSIM_FP32_KAHAN is the float32 path (its
+// cross-block sums are float64), so it becomes MRSIM_FP32 for every later decision.
+inline bool normalize_precision(mrsim_precision &p) {
+    if (p == MRSIM_FP32_KAHAN) p = MRSIM_FP32;
+    return p == MRSIM_FP64 || p == MRSIM_FP32;
+}
+
 struct Launch {
     int k, threads;
 };

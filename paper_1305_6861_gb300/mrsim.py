@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmrsim.so")
 
 FP64 = 0
 FP32 = 1
+FP32_KAHAN = 2  # the float32 path with its float64 cross-block sums (same results as FP32)
 ACCUMULATE = 1
 TUNE = 2
 
@@ -41,7 +42,7 @@ EXPORTS = (
     "mrsim_adjoint_create", "mrsim_adjoint_num_adc", "mrsim_adjoint_forward", "mrsim_adjoint_backward",
     "mrsim_adjoint_destroy", "mrsim_compile", "mrsim_compile_last_error", "mrsim_compiled_num_adc",
     "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
-    "mrsim_set_log_callback", "mrsim_debug_fail_alloc",
+    "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate",
 )
 
 
@@ -141,6 +142,7 @@ def lib():
             "mrsim_debug_wait_timeout": (ctypes.c_int, [vp, i64, vp]),
             "mrsim_set_log_callback": (None, [vp, vp]),
             "mrsim_debug_fail_alloc": (ctypes.c_int, [vp, i32]),
+            "mrsim_measure_fma_rate": (ctypes.c_int, [vp, i32, dbl, vp, P(dbl), P(dbl)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -442,12 +444,15 @@ class Batch:
             pass
 
 
-def simulate_batch_static(ctx: Context, phantoms, seqs, precision: int = FP32, outs=None, stream=None,
+def simulate_batch_static(ctx: Context, phantoms, seqs, precision: int, outs, stream=None,
                           spins_per_thread: int = 0, threads_per_block: int = 0):
     """Batch launch that allocates no device memory (scratch in the library's fixed static array):
-    for callers that cannot call cudaMalloc.  `outs`: one CUDA buffer of 2*n_adc float64 per pair.
-    Asynchronous on `stream`; calls that overlap on the GPU share the scratch and must not overlap."""
+    for callers that cannot call cudaMalloc.  `outs`: one CUDA buffer of 2*n_adc float64 per pair
+    (required; this call allocates none).  Asynchronous on `stream`; calls that overlap on the GPU
+    share the scratch and must not overlap."""
     n = len(phantoms)
+    if len(seqs) != n or len(outs) != n:
+        raise ValueError(f"{n} phantoms, {len(seqs)} sequences and {len(outs)} outputs: the lengths must agree")
     ph = (ctypes.c_void_p * n)(*[p.h.value for p in phantoms])
     sq = (ctypes.c_void_p * n)(*[q.h.value for q in seqs])
     os_ = (ctypes.c_void_p * n)(*[_ptr(o).value for o in outs])
@@ -501,6 +506,18 @@ def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP3
     opt = Options()
     ctx.check(lib().mrsim_autotune(ctx.h, phantom.h, seq.h, int(precision), _stream(stream), ctypes.byref(opt)))
     return int(opt.spins_per_thread), int(opt.threads_per_block)
+
+
+FMA_F32, FMA_F32X2, FMA_F64 = 0, 1, 2
+
+
+def measure_fma_rate(ctx: Context, kind: int, target_ms: float = 100.0, stream=None):
+    """Measured multiply-add rate of the device (mrsim_measure_fma_rate): (lane-ops/s, kernel ms)
+    for kind FMA_F32, FMA_F32X2 or FMA_F64."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    ctx.check(lib().mrsim_measure_fma_rate(ctx.h, int(kind), float(target_ms), _stream(stream), ctypes.byref(rate),
+                                           ctypes.byref(ms)))
+    return rate.value, ms.value
 
 
 def debug_compile(events, gamma_hz_per_t: float, snapshots=None):
