@@ -39,6 +39,68 @@ mrsim_status bad(mrsim_ctx *ctx, mrsim_status st, const std::string &m) {
     return st;
 }
 
+// Makes the context's device current for the call and gives the caller's current device back on
+// every way out of it.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// The work list of one launch shape in the host staging area, after the descriptors: every
+// phantom's tiles, longest sequences first.  Returns MRSIM_OK and the sizes, or the status and a
+// message saying which limit was hit.
+struct Layout {
+    size_t items_off = 0, n_items = 0, smem = 0;
+    int per_sm = 0;
+};
+
+mrsim_status lay_out(mrsim_ctx *ctx, int n, const mrsim_sequence *const *seqs, const FwdArgs *hd, bool fp64,
+                     const Launch &L, Layout *out, std::string *msg) {
+    Layout y;
+    y.items_off = (HEAD_BYTES + (size_t)n * sizeof(FwdArgs) + 255) / 256 * 256;
+    BatchItem *hi = reinterpret_cast<BatchItem *>(h_stage + y.items_off);
+    const size_t max_items = (SCRATCH_BYTES - y.items_off) / sizeof(BatchItem);
+    const int64_t S = (int64_t)L.k * L.threads;
+    // order phantoms by sequence length without allocating: repeated selection of the next longest
+    int64_t prev = INT64_MAX;
+    int prev_idx = -1;
+    for (int done = 0; done < n; ++done) {
+        int pick = -1;
+        for (int i = 0; i < n; ++i) {
+            const int64_t e = seqs[i]->n_events;
+            const bool after_prev = e < prev || (e == prev && i > prev_idx);
+            if (after_prev && (pick < 0 || e > seqs[pick]->n_events)) pick = i;
+        }
+        prev = seqs[pick]->n_events;
+        prev_idx = pick;
+        const int64_t tiles = (hd[pick].n_spins + S - 1) / S;
+        if ((int64_t)y.n_items + tiles > (int64_t)max_items) {
+            *msg = "batch needs more work items than the static scratch holds (" + std::to_string(max_items) +
+                   " with this launch shape)";
+            return MRSIM_EINVAL;
+        }
+        for (int64_t t = 0; t < tiles; ++t) hi[y.n_items++] = BatchItem{pick, (int32_t)t};
+        y.smem = std::max(y.smem, fwd_smem_bytes(fp64, hd[pick].prog, L.k, L.threads));
+    }
+    if (y.smem > (size_t)ctx->max_smem_optin) {
+        *msg = "launch shape exceeds shared memory";
+        return MRSIM_EUNSUPPORTED;
+    }
+    y.per_sm = batch_blocks_per_sm(fp64, L.k, L.threads, y.smem);
+    if (y.per_sm <= 0) {
+        *msg = "launch shape cannot be resident";
+        return MRSIM_EUNSUPPORTED;
+    }
+    *out = y;
+    return MRSIM_OK;
+}
+
 }  // namespace
 
 extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
@@ -47,11 +109,11 @@ extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, c
                                                     int32_t threads_per_block) {
     if (!ctx) return MRSIM_EINVAL;
     if (n < 0 || (n > 0 && (!phantoms || !seqs || !signals_out))) return bad(ctx, MRSIM_EINVAL, "invalid batch arrays");
-    if (prec != MRSIM_FP64 && prec != MRSIM_FP32) return bad(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec)) return bad(ctx, MRSIM_EINVAL, "unknown precision");
     if (ctx->device < 0 || ctx->device >= MAX_DEVICES) return bad(ctx, MRSIM_EUNSUPPORTED, "device ordinal too large");
     const bool fp64 = prec == MRSIM_FP64;
     std::lock_guard<std::mutex> lock(g_mu);
-    cudaSetDevice(ctx->device);
+    DeviceScope scope(ctx->device);
     // set-up, once per device, with that device current: the device address of g_scratch
     if (!g_scratch_dev[ctx->device]) {
         void *p = nullptr;
@@ -91,40 +153,29 @@ extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, c
         max_n = std::max(max_n, p->n);
     }
     Launch L = choose_launch(ctx, fp64, max_n);
+    const bool library_shape = !spins_per_thread && !threads_per_block;
     if (spins_per_thread) L.k = spins_per_thread;
     if (threads_per_block) L.threads = threads_per_block;
     const bool k_ok = fp64 ? (L.k == 1 || L.k == 2) : (L.k == 1 || L.k == 2 || L.k == 4 || L.k == 8);
     if (!k_ok || L.threads < 32 || L.threads % 32 || L.threads > (fp64 || L.k == 8 ? 256 : 512))
         return bad(ctx, MRSIM_EINVAL, "unsupported spins_per_thread / threads_per_block");
 
-    // work items, longest sequences first, after the descriptors (8-byte aligned)
-    const size_t items_off = (HEAD_BYTES + desc_bytes + 255) / 256 * 256;
-    BatchItem *hi = reinterpret_cast<BatchItem *>(h_stage + items_off);
-    const size_t max_items = (SCRATCH_BYTES - items_off) / sizeof(BatchItem);
-    const int64_t S = (int64_t)L.k * L.threads;
-    size_t n_items = 0, smem = 0;
-    // order phantoms by sequence length without allocating: repeated selection of the next longest
-    int64_t prev = INT64_MAX;
-    int prev_idx = -1;
-    for (int done = 0; done < n; ++done) {
-        int pick = -1;
-        for (int i = 0; i < n; ++i) {
-            const int64_t e = seqs[i]->n_events;
-            const bool after_prev = e < prev || (e == prev && i > prev_idx);
-            if (after_prev && (pick < 0 || e > seqs[pick]->n_events)) pick = i;
+    // work items after the descriptors; the library's own shape falls back to smaller blocks
+    // (1 x 64, then 1 x 32) when it does not fit, as mrsim_batch_create does
+    Layout y;
+    std::string msg;
+    mrsim_status ls = lay_out(ctx, n, seqs, hd, fp64, L, &y, &msg);
+    if (ls == MRSIM_EUNSUPPORTED && library_shape) {
+        for (const Launch f : {Launch{1, 64}, Launch{1, 32}}) {
+            if ((ls = lay_out(ctx, n, seqs, hd, fp64, f, &y, &msg)) != MRSIM_EUNSUPPORTED) {
+                L = f;
+                break;
+            }
         }
-        prev = seqs[pick]->n_events;
-        prev_idx = pick;
-        const int64_t tiles = (hd[pick].n_spins + S - 1) / S;
-        if ((int64_t)n_items + tiles > (int64_t)max_items)
-            return bad(ctx, MRSIM_EINVAL, "batch needs more work items than the static scratch holds (" +
-                                              std::to_string(max_items) + " with this launch shape)");
-        for (int64_t t = 0; t < tiles; ++t) hi[n_items++] = BatchItem{pick, (int32_t)t};
-        smem = std::max(smem, fwd_smem_bytes(fp64, hd[pick].prog, L.k, L.threads));
     }
-    if (smem > (size_t)ctx->max_smem_optin) return bad(ctx, MRSIM_EUNSUPPORTED, "launch shape exceeds shared memory");
-    const int per_sm = batch_blocks_per_sm(fp64, L.k, L.threads, smem);
-    if (per_sm <= 0) return bad(ctx, MRSIM_EUNSUPPORTED, "launch shape cannot be resident");
+    if (ls != MRSIM_OK) return bad(ctx, ls, msg);
+    const size_t items_off = y.items_off, n_items = y.n_items, smem = y.smem;
+    const int per_sm = y.per_sm;
 
     cudaStream_t st = (cudaStream_t)stream;
     const size_t used = items_off + n_items * sizeof(BatchItem);

@@ -1,6 +1,8 @@
 """The batch entry point that allocates nothing (mrsim_simulate_batch_static), for callers that
-cannot call cudaMalloc when they simulate: its output must equal the regular batch API's, call
-after call, and batches beyond its fixed scratch must be refused with EINVAL.
+cannot call cudaMalloc when they simulate (a plug-in whose host application owns every device
+allocation, a real-time loop under a fixed memory budget): its output must equal the regular batch
+API's and the float64 CPU oracle's, call after call, a call after the first must leave the
+device's free memory unchanged, and batches beyond its fixed scratch must be refused with EINVAL.
 
 Kept in a file of its own, collected last, so that a run stopping at the first failure has
 already run every other test."""
@@ -34,13 +36,14 @@ def _pairs():
     return out
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-6), ("fp64", 1e-12)])
-def test_static_scratch_batch_matches_batch_api(mrsim_lib, prec, tol):
+@pytest.mark.parametrize("prec,tol,tol_oracle", [("fp32", 1e-6, 2e-5), ("fp64", 1e-12, 1e-12)])
+def test_static_scratch_batch_matches_batch_api(mrsim_lib, oracle_mod, prec, tol, tol_oracle):
     torch = pytest.importorskip("torch")
     M = mrsim_lib
     p = M.FP32 if prec == "fp32" else M.FP64
     ctx = M.Context(0)
     pairs = _pairs()
+    oracle_refs = [oracle_mod.signal(ph, seq) for ph, seq in pairs]
     phs = [M.Phantom.from_workload_phantom(ctx, a) for a, _ in pairs]
     sqs = [M.Sequence.from_workload_sequence(ctx, s) for _, s in pairs]
     ref_out = [torch.zeros(max(2 * q.n_adc, 2), dtype=torch.float64, device="cuda") for q in sqs]
@@ -52,12 +55,17 @@ def test_static_scratch_batch_matches_batch_api(mrsim_lib, prec, tol):
     ref = [o.cpu().numpy()[: 2 * q.n_adc].view(np.complex128) for o, q in zip(ref_out, sqs)]
     out = [torch.full((max(2 * q.n_adc, 2),), 7.0, dtype=torch.float64, device="cuda") for q in sqs]
     for call in range(2):  # two calls in a row share the static scratch
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         M.simulate_batch_static(ctx, phs, sqs, p, out, spins_per_thread=2, threads_per_block=64)
         torch.cuda.synchronize()
+        if call:  # the first call may load the module; later ones take no device memory at all
+            assert torch.cuda.mem_get_info()[0] == free_before
         ctx.stream_status()
         got = [o.cpu().numpy()[: 2 * q.n_adc].view(np.complex128) for o, q in zip(out, sqs)]
-        for i, (g, r) in enumerate(zip(got, ref)):
+        for i, (g, r, o) in enumerate(zip(got, ref, oracle_refs)):
             assert rel_l2(g, r) <= tol, (call, i)
+            assert rel_l2(g, o) <= tol_oracle, (call, i)
     b.close()
     ctx.close()
 
@@ -76,4 +84,27 @@ def test_static_scratch_limits(mrsim_lib):
     rc = M.lib().mrsim_simulate_batch_static(ctx.h, n, arr_p, arr_s, M.FP32, None, arr_o, 1, 32)
     assert rc == M.Status.EINVAL
     assert b"static scratch" in M.lib().mrsim_last_error(ctx.h)
+    ctx.close()
+
+
+def test_static_scratch_library_shape_and_current_device(mrsim_lib, oracle_mod):
+    """With the library's default shape (0, 0) the call serves the same batch as the batch API
+    and gives the caller's current device back unchanged."""
+    torch = pytest.importorskip("torch")
+    M = mrsim_lib
+    ctx = M.Context(0)
+    pairs = _pairs()
+    phs = [M.Phantom.from_workload_phantom(ctx, a) for a, _ in pairs]
+    sqs = [M.Sequence.from_workload_sequence(ctx, s) for _, s in pairs]
+    out = [torch.zeros(max(2 * q.n_adc, 2), dtype=torch.float64, device="cuda") for q in sqs]
+    dev_before = torch.cuda.current_device()
+    M.simulate_batch_static(ctx, phs, sqs, M.FP32, out)
+    assert torch.cuda.current_device() == dev_before
+    torch.cuda.synchronize()
+    ctx.stream_status()
+    for (ph, seq), o, q in zip(pairs, out, sqs):
+        g = o.cpu().numpy()[: 2 * q.n_adc].view(np.complex128)
+        assert rel_l2(g, oracle_mod.signal(ph, seq)) <= 2e-5
+    with pytest.raises(ValueError):
+        M.simulate_batch_static(ctx, phs, sqs[:-1], M.FP32, out)
     ctx.close()
