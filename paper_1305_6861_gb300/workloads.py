@@ -504,6 +504,19 @@ def config2(seed=None, n: int = 256, iso: int = 4) -> Workload:
     return Workload(f"c2_se2d_{n}", ph, seq, "jittered isochromats, fat fraction, B0 polynomial ±200 Hz")
 
 
+def config2_legendre(seed=None, n: int = 256, iso: int = 4, c_tesla: float = 20e-6, radius: float = 0.25) -> Workload:
+    """C2 with the static-field inhomogeneity of a whole-body magnet (Eq. 6.3) in place of the
+    random polynomial: C = 20 µT and a homogeneity sphere of diameter 0.5 m (the values of §7.1.2
+    and Fig. 6.2); fat isochromats keep their chemical shift."""
+    w = config2(seed, n, iso)
+    ph = w.phantom
+    fat = np.zeros(ph.n, dtype=bool)
+    fat[np.tile(np.arange(iso) >= iso // 2, ph.n // iso)] = True
+    dw = dw_from_b0(b0_legendre(ph.x, ph.y, ph.z, c_tesla, radius)) + np.where(fat, 2 * math.pi * FAT_SHIFT_HZ, 0.0)
+    return Workload(f"c2_se2d_{n}_legendre", Phantom(ph.x, ph.y, ph.z, ph.rho, ph.t1, ph.t2, dw), w.sequence,
+                    f"Eq. 6.3 inhomogeneity C = {c_tesla * 1e6:g} uT, R = {radius:g} m, plus fat shift")
+
+
 def config3(seed=None, n: int = 128, iso: int = 2) -> Workload:
     """3D n³ RF-spoiled GRE, 2 iso/voxel, 10°, TR 8 ms, TE 4 ms, dwell 10 µs."""
     rng = rng_for(3, seed)
@@ -746,5 +759,12 @@ def b0_legendre(x, y, z, c_tesla: float, radius: float) -> np.ndarray:
 
 
 def dw_from_b0(delta_b0, gamma_hz_per_t: float = GAMMA_BAR) -> np.ndarray:
-    """Off-resonance [rad/s] of a field deviation: Δω0 = -γ·ΔB0 (Eqs. 6.1, 6.2, ω = -γB)."""
-    return -2 * math.pi * gamma_hz_per_t * np.asarray(delta_b0, dtype=float)
+    """Off-resonance [rad/s] of a field deviation along z: Δω0 = +γ·ΔB0.
+
+    The simulation turns a spin by θ = (γ G·x + Δω)·Δt, Mxy <- Mxy·exp(-jθ): Δω enters exactly as
+    a gradient's field G·x does, i.e. Δω/γ is a field along z in the same sense as G·x (the Bloch
+    equation in the rotating frame, Eqs. 3.11, 3.13).  So a deviation ΔB0 of the static field
+    enters as +γ·ΔB0, and a spin at the centre in a deviation equal to G·x0 precesses like a spin
+    at x0 in the gradient G.  (Eq. 6.1 writes ω = -γB with the opposite orientation of the
+    angle; the library's Δω is the clockwise-positive frequency of its precession matrices.)"""
+    return 2 * math.pi * gamma_hz_per_t * np.asarray(delta_b0, dtype=float)

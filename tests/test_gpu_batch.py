@@ -116,10 +116,15 @@ def test_empty_batch(M, ctx):
     ctx.stream_status()
 
 
-def test_config4_batch_equals_single_launches(M, ctx, torch, oracle_mod):
+@pytest.fixture(scope="module")
+def c4():
+    return W.config4()
+
+
+def test_config4_batch_equals_single_launches(M, ctx, torch, oracle_mod, c4):
     """The 64-phantom batched workload (uneven 1e4..2e6 spins, FLASH/SE mix): one graph-replayed
     persistent launch equals 64 single-phantom launches, and the oracle on spin subsets."""
-    ws = W.config4()
+    ws = c4
     pairs = [(w.phantom, w.sequence) for w in ws]
     b, phs, sqs, outs = make_batch(M, ctx, torch, pairs, M.FP32)
     k, t = b.autotune()
@@ -142,3 +147,47 @@ def test_config4_batch_equals_single_launches(M, ctx, torch, oracle_mod):
         ref = oracle_mod.signal(sub, w.sequence)
         ps = M.Phantom.from_workload_phantom(ctx, sub)
         assert rel_l2(M.simulate(ctx, ps, sqs[i], M.FP32), ref) <= TOL32
+
+
+@pytest.fixture(scope="module")
+def c4_samples(c4, oracle_mod):
+    """The 4 smallest phantoms whole, every other phantom on a seeded 1 % sample of its tissue
+    spins: (phantoms with M0 = 0 outside the samples, oracle signals of the samples)."""
+    n = np.array([w.phantom.n for w in c4])
+    whole = set(np.argsort(n)[:4].tolist())
+    rng = np.random.default_rng(44)
+    phs, refs = [], []
+    for i, w in enumerate(c4):
+        if i in whole:
+            idx = np.arange(w.phantom.n)
+        else:
+            pool = np.nonzero(w.phantom.rho > 0)[0]
+            idx = np.sort(rng.choice(pool, max(1, int(round(0.01 * w.phantom.n))), replace=False))
+        ph = w.phantom
+        rho = np.zeros_like(ph.rho)
+        rho[idx] = ph.rho[idx]
+        phs.append(W.Phantom(ph.x, ph.y, ph.z, rho, ph.t1, ph.t2, ph.dw))
+        refs.append(oracle_mod.signal(ph.subset(idx), w.sequence))
+    return phs, refs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_config4_batch_graph_against_oracle(M, ctx, torch, c4, c4_samples, prec):
+    """The 64-phantom batch through the graph-replayed persistent launch itself, against the
+    oracle: the 4 smallest phantoms whole, every other phantom on a seeded 1 % sample of its
+    tissue spins.  The batch holds all 64 phantoms at full size, with M0 = 0 outside each sample
+    (such spins stay at (0, 0, 0) and add exact zeros), so the samples run in the batch's own work
+    items and launch shape."""
+    phs_m, refs = c4_samples
+    p = M.FP64 if prec == "fp64" else M.FP32
+    tol = TOL64 if prec == "fp64" else TOL32
+    b, phs, sqs, outs = make_batch(M, ctx, torch, list(zip(phs_m, [w.sequence for w in c4])), p)
+    if p == M.FP32:
+        b.autotune()  # the benchmark's batch tuning
+    b.launch(graph=True)  # capture
+    b.launch(graph=True)  # replay
+    torch.cuda.synchronize()
+    ctx.stream_status()
+    for i, (g, r) in enumerate(zip(signals(outs, sqs), refs)):
+        assert np.linalg.norm(r) > 0, i
+        assert rel_l2(g, r) <= tol, (i, c4[i].name, rel_l2(g, r))

@@ -426,3 +426,44 @@ def test_rasterized_snapshots_parity(M, ctx, oracle_mod):
         assert rel_l2(sig, ref_sig) <= tol_s
         for q in range(len(snaps)):
             assert np.max(np.abs(out[q] - refs[q])) <= tol_m, (prec, q)
+
+
+def test_fp32_kahan_precision_is_the_float32_path(M, ctx, oracle_mod):
+    """MRSIM_FP32_KAHAN (float32 bulk arithmetic, per-sample sums above float32 precision across
+    the phantom) is accepted by the forward, coil and batch calls and gives the float32 path's
+    results bit for bit (same launch shape); an unknown precision is refused."""
+    import ctypes
+
+    w = W.config1()
+    p = M.Phantom.from_workload_phantom(ctx, w.phantom)
+    s = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    a = M.simulate(ctx, p, s, M.FP32, spins_per_thread=2, threads_per_block=128)
+    b = M.simulate(ctx, p, s, M.FP32_KAHAN, spins_per_thread=2, threads_per_block=128)
+    assert np.array_equal(a, b)
+    assert rel_l2(b, oracle_mod.signal(w)) <= TOL32
+    sens = np.ones((2, w.phantom.n), dtype=complex)
+    ca = M.simulate_coils(ctx, p, s, sens, M.FP32)
+    cb = M.simulate_coils(ctx, p, s, sens, M.FP32_KAHAN)
+    assert np.array_equal(ca, cb)
+    out = np.zeros(s.n_adc, dtype=complex)
+    rc = M.lib().mrsim_simulate(ctx.h, p.h, s.h, 3, None, ctypes.c_void_p(out.ctypes.data), s.n_adc)
+    assert rc == M.Status.EINVAL
+
+
+def test_config2_legendre_field_parity(M, ctx, oracle_mod):
+    """C2 with the Eq. 6.3 inhomogeneity (C = 20 µT, homogeneity sphere of diameter 0.5 m) on spin
+    subsets, both precisions: spins inside 0.9 R (offsets up to a few hundred Hz) at the 1e-12 /
+    2e-5 bars; spins anywhere in the 0.5 m field of view (up to 12.7 kHz at the corners, phases of
+    ~4e4 rad per rest interval) at the float64 floor those phases set and the float32 bar."""
+    w = W.config2_legendre()
+    ph = w.phantom
+    r = np.sqrt(ph.x**2 + ph.y**2 + ph.z**2)
+    rng = np.random.default_rng(23)
+    inner = np.sort(rng.choice(np.nonzero((r < 0.9 * 0.25) & (ph.rho > 0))[0], 1200, replace=False))
+    anywhere = np.sort(rng.choice(ph.n, 1200, replace=False))
+    for idx, tol64 in ((inner, TOL64), (anywhere, None)):
+        sub = ph.subset(idx)
+        ref = oracle_mod.signal(sub, w.sequence)
+        t64 = tol64 if tol64 is not None else fp64_phase_tolerance(sub, w.sequence)
+        assert rel_l2(run(M, ctx, sub, w.sequence, M.FP64), ref) <= t64
+        assert rel_l2(run(M, ctx, sub, w.sequence, M.FP32), ref) <= TOL32

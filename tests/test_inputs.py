@@ -38,6 +38,37 @@ def test_b0_legendre_field():
     assert W.b0_legendre(*rot, c, R) == pytest.approx(W.b0_legendre(*v, c, R), rel=1e-12)
 
 
-def test_off_resonance_sign():
-    """ω = -γB (Eq. 6.1): a positive field deviation lowers the precession frequency."""
-    assert W.dw_from_b0(1e-6) == pytest.approx(-2 * math.pi * W.GAMMA_BAR * 1e-6, rel=1e-15)
+def test_off_resonance_enters_like_a_gradient_field(oracle_mod):
+    """A field deviation ΔB0 along z must turn a spin exactly as a gradient field of the same size
+    does: a spin at the centre with Δω = dw_from_b0(G·x0) and no gradient gives the signal of a
+    spin at x0 in the gradient G (Eqs. 3.11, 3.13: both are fields along z in the rotating frame).
+    The opposite sign would give the complex conjugate phase history and fails."""
+    g, x0 = 3e-3, 0.07  # 3 mT/m, 7 cm
+    rows = [(0.0, 0.0, 0.0, 0.0, math.pi / 2, 0.3, 0, 0.0)]
+    for k in range(40):
+        rows.append((25e-6, g, 0.0, 0.0, 0.0, 0.0, 1, 0.0))
+        if k == 19:
+            rows.append((0.0, 0.0, 0.0, 0.0, 2.0, 1.1, 0, 0.0))
+    grad = W.Sequence(W.make_events(rows), W.GAMMA_BAR)
+    ev = grad.events.copy()
+    ev["gx"] = 0.0
+    nograd = W.Sequence(ev, W.GAMMA_BAR)
+    one = lambda x, dw: W.Phantom(*(np.array([v], dtype=float) for v in (x, 0.0, 0.0, 1.0, 0.8, 0.05, dw)))
+    s_grad = oracle_mod.signal(one(x0, 0.0), grad)
+    s_b0 = oracle_mod.signal(one(0.0, float(W.dw_from_b0(g * x0))), nograd)
+    assert np.max(np.abs(s_grad - s_b0)) < 1e-12
+    assert np.max(np.abs(s_grad - s_grad.conj())) > 0.1  # the phases are not trivially symmetric
+    assert W.dw_from_b0(1e-6) == pytest.approx(2 * math.pi * W.GAMMA_BAR * 1e-6, rel=1e-15)
+
+
+def test_legendre_workload(oracle_mod):
+    """The C2 variant with the Eq. 6.3 field: Δω of every water spin is +γΔB0 of its position, fat
+    spins add the chemical shift; spins at the centre of the homogeneity sphere see no field."""
+    w = W.config2_legendre(n=32, iso=2)
+    ph = w.phantom
+    b0 = W.b0_legendre(ph.x, ph.y, ph.z, 20e-6, 0.25)
+    water = np.tile([True, False], ph.n // 2)
+    assert np.allclose(ph.dw[water], 2 * math.pi * W.GAMMA_BAR * b0[water], rtol=1e-14, atol=0)
+    assert np.allclose(ph.dw[~water] - 2 * math.pi * W.GAMMA_BAR * b0[~water], 2 * math.pi * W.FAT_SHIFT_HZ,
+                       rtol=1e-12, atol=1e-9)
+    assert np.max(np.abs(b0)) > 1e-6  # the corners of the 0.5 m field of view leave the sphere
