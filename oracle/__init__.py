@@ -66,6 +66,9 @@ def _bind(path):
     lib.oracle_simulate_coils.restype = ctypes.c_int
     lib.oracle_simulate_coils.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_double, ctypes.c_int32, d, d, ctypes.c_int64, ctypes.c_int]
+    lib.oracle_simulate_fields.restype = ctypes.c_int
+    lib.oracle_simulate_fields.argtypes = [ctypes.c_int64] + [d] * 7 + [d, ctypes.c_int64, ctypes.c_void_p, d,
+                                           ctypes.c_double, ctypes.c_double, d, ctypes.c_int64, d, ctypes.c_int]
     lib.oracle_gradient.restype = ctypes.c_int
     lib.oracle_gradient.argtypes = [ctypes.c_int64] + [d] * 7 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                     i32p, d, d, ctypes.c_int64, d, d, d, i32p, ctypes.c_int32, d, ctypes.c_int]
@@ -155,6 +158,33 @@ def simulate_coils(phantom, events, gamma_hz_per_t, sens, n_threads=0, lib=None)
     if rc != 0:
         raise RuntimeError(f"oracle_simulate_coils failed with code {rc}")
     return sig.view(np.complex128).reshape(c.shape[0], n_adc)
+
+
+def simulate_fields(phantom, events, gamma_hz_per_t, ndir, gt=None, b0=1.5, want_state=False, n_threads=0,
+                    lib=None):
+    """Forward signal with non-parallel fields (§3.2, §3.4.3.2): ndir [n_spins, 3] unit static-field
+    directions, gt None or [n_events, 6] transverse gradient components (gtx, gty) [T/m], b0 [T].
+    Returns (signal complex128[n_adc], state [n, 3] or None)."""
+    lib = _load() if lib is None else lib
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    arrs = [np.ascontiguousarray(getattr(phantom, k), dtype=np.float64) for k in ("x", "y", "z", "rho", "t1", "t2", "dw")]
+    n = arrs[0].shape[0]
+    nd = np.ascontiguousarray(np.asarray(ndir, dtype=np.float64).reshape(-1))
+    if nd.shape[0] != 3 * n:
+        raise ValueError("ndir must have 3 values per spin")
+    g = None
+    if gt is not None:
+        g = np.ascontiguousarray(np.asarray(gt, dtype=np.float64).reshape(-1))
+        if g.shape[0] != 6 * ev.shape[0]:
+            raise ValueError("gt must have 6 values per event")
+    n_adc = int(np.count_nonzero(ev["adc"]))
+    sig = np.zeros(2 * n_adc)
+    st = np.zeros(3 * n) if want_state else None
+    rc = lib.oracle_simulate_fields(n, *[_dp(a) for a in arrs], _dp(nd), ev.shape[0], ev.ctypes.data_as(ctypes.c_void_p),
+                                    _dp(g), float(gamma_hz_per_t), float(b0), _dp(sig), n_adc, _dp(st), int(n_threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_simulate_fields failed with code {rc}")
+    return sig.view(np.complex128), (st.reshape(n, 3) if st is not None else None)
 
 
 def gradient(phantom, events, gamma_hz_per_t, h, rf_param=None, rf_values=None, sel=(), n_threads=0, lib=None):

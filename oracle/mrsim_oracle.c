@@ -409,3 +409,127 @@ int oracle_gradient(int64_t n_spins, const double *x, const double *y, const dou
     free(part);
     return 0;
 }
+
+/*
+ * Non-parallel fields (§3.2, §3.4.3.2): forward simulation where the static field at each spin
+ * points along its own unit vector n_s, and an elementary sequence's gradient field may have
+ * components transverse to z.
+ *
+ * §3.2: where the static field is not along z, the frame is turned locally so that one axis lies
+ * along the field, the Bloch equation (3.4) is applied in that frame, and the result is turned
+ * back.  §3.4.3.2: a constant gradient field with transverse components changes the direction of
+ * the total field; T1 relaxation follows the resulting direction and Eqs. 3.14/3.15 hold in the
+ * frame turned to it.  Written out for one spin and one event:
+ *   b = (gtx.x, gty.x, G.x)              gradient field at the spin [T]
+ *   u = B0*n + b,  u_hat = u/|u|         total field and its direction
+ *   theta = (gamma*(|u| - B0) + dw)*dt   precession angle in the frame rotating at gamma*B0
+ * and, with M_par = M.u_hat and M_perp = M - M_par*u_hat,
+ *   M <- E2*(cos(theta)*M_perp - sin(theta)*(u_hat x M_perp)) + (E1*M_par + M0*(1 - E1))*u_hat,
+ * the clockwise turn of Eq. 3.5 about u_hat (for u_hat = z it is Eq. 3.5 itself) with T2 decay of
+ * the part across the field and T1 recovery along it.  |u| - B0 is evaluated as
+ * (2*B0*(n.b) + |b|^2)/(|u| + B0), the same number without the cancellation of two nearly equal
+ * terms.  The RF pulse acts first, as Eq. 3.19 in the rotating frame; the sample is
+ * (Mx + jMy)*exp(-j*adc_phase) after the step.  Every spin starts in equilibrium along its static
+ * field, M = M0*n.
+ *   ndir: 3*n_spins doubles (nx, ny, nz) per spin, unit vectors
+ *   gt:   NULL or 6*n_events doubles per event: gtx (3), gty (3) [T/m]
+ *   b0:   |B0| [T] > 0
+ * Returns as oracle_simulate.
+ */
+static int apply_event_fields(const oracle_event *e, const double *gt, double gamma, double b0,
+                              double x, double y, double z, const double n[3], double rho, double t1,
+                              double t2, double dw, double M[3])
+{
+    if (e->rf_flip != 0.0) {
+        double R[3][3];
+        rf_rotation(e->rf_flip, e->rf_phase, R);
+        const double mx = R[0][0] * M[0] + R[0][1] * M[1] + R[0][2] * M[2];
+        const double my = R[1][0] * M[0] + R[1][1] * M[1] + R[1][2] * M[2];
+        const double mz = R[2][0] * M[0] + R[2][1] * M[1] + R[2][2] * M[2];
+        M[0] = mx; M[1] = my; M[2] = mz;
+    }
+    double b[3] = {0.0, 0.0, e->gx * x + e->gy * y + e->gz * z};
+    if (gt) {
+        b[0] = gt[0] * x + gt[1] * y + gt[2] * z;
+        b[1] = gt[3] * x + gt[4] * y + gt[5] * z;
+    }
+    const double u[3] = {b0 * n[0] + b[0], b0 * n[1] + b[1], b0 * n[2] + b[2]};
+    const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double h[3] = {u[0] / un, u[1] / un, u[2] / un};
+    const double nb = n[0] * b[0] + n[1] * b[1] + n[2] * b[2];
+    const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const double excess = (2.0 * b0 * nb + bb) / (un + b0); /* |u| - B0 */
+    const double theta = (gamma * excess + dw) * e->dt;
+    const double c = cos(theta), s = sin(theta);
+    const double e2 = exp(-e->dt / t2);
+    const double e1 = exp(-e->dt / t1);
+    const double par = M[0] * h[0] + M[1] * h[1] + M[2] * h[2];
+    const double p[3] = {M[0] - par * h[0], M[1] - par * h[1], M[2] - par * h[2]};
+    const double hxp[3] = {h[1] * p[2] - h[2] * p[1], h[2] * p[0] - h[0] * p[2], h[0] * p[1] - h[1] * p[0]};
+    const double along = par * e1 + rho * (1.0 - e1);
+    for (int i = 0; i < 3; ++i) M[i] = e2 * (c * p[i] - s * hxp[i]) + along * h[i];
+    return e->adc != 0;
+}
+
+int oracle_simulate_fields(int64_t n_spins, const double *x, const double *y, const double *z,
+                           const double *rho, const double *t1, const double *t2, const double *dw,
+                           const double *ndir, int64_t n_events, const void *events, const double *gt,
+                           double gamma_hz_per_t, double b0, double *signal, int64_t n_adc, double *m_final,
+                           int n_threads)
+{
+    const oracle_event *ev = (const oracle_event *)events;
+    if (count_adc(ev, n_events) != n_adc || !(b0 > 0.0)) return -1;
+    const double gamma = ORACLE_TWO_PI * gamma_hz_per_t;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+#endif
+    double *partial = NULL;
+    if (signal) {
+        partial = (double *)calloc((size_t)nt * (size_t)(2 * n_adc + 1), sizeof(double));
+        if (!partial) return -2;
+    }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *mine = partial ? partial + (size_t)tid * (size_t)(2 * n_adc + 1) : NULL;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t s = 0; s < n_spins; ++s) {
+            const double *n = ndir + 3 * s;
+            double M[3] = {rho[s] * n[0], rho[s] * n[1], rho[s] * n[2]};
+            int64_t j = 0;
+            for (int64_t e = 0; e < n_events; ++e) {
+                if (apply_event_fields(&ev[e], gt ? gt + 6 * e : NULL, gamma, b0, x[s], y[s], z[s], n, rho[s],
+                                       t1[s], t2[s], dw[s], M)) {
+                    if (mine) {
+                        const double cph = cos(ev[e].adc_phase), sph = sin(ev[e].adc_phase);
+                        mine[2 * j] += M[0] * cph + M[1] * sph;
+                        mine[2 * j + 1] += M[1] * cph - M[0] * sph;
+                    }
+                    ++j;
+                }
+            }
+            if (m_final) {
+                m_final[3 * s] = M[0]; m_final[3 * s + 1] = M[1]; m_final[3 * s + 2] = M[2];
+            }
+        }
+    }
+    if (signal) {
+        memset(signal, 0, sizeof(double) * (size_t)(2 * n_adc));
+        for (int t = 0; t < nt; ++t) {
+            const double *p = partial + (size_t)t * (size_t)(2 * n_adc + 1);
+            for (int64_t i = 0; i < 2 * n_adc; ++i) signal[i] += p[i];
+        }
+        free(partial);
+    }
+    return 0;
+}
