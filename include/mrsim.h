@@ -329,6 +329,57 @@ mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph,
                                     double *d_t2, double *d_rf);
 /* Frees the adjoint's device tables and checkpoint storage (NULL is ignored). */
 void mrsim_adjoint_destroy(mrsim_adjoint *adj);
+/* One-shot gradient of a real loss L of the simulated signal (the same adjoint recursion as
+ * mrsim_adjoint_create/forward/backward, Eq. 4.1 run backward through its transposed steps) for a
+ * phantom and an already loaded sequence; the paper has no gradients, this differentiates its
+ * forward method.  The call creates the adjoint program from the sequence's own event list,
+ * runs the checkpointed forward pass with the pulses' own flips and the backward pass, copies
+ * the results out and frees everything again, so it synchronises `stream`.
+ *   prec:       MRSIM_FP64 (the gradients are float64; MRSIM_FP32 and MRSIM_FP32_KAHAN give
+ *               MRSIM_EUNSUPPORTED)
+ *   ckpt_every: events per checkpoint segment, 1..128 (0 = 64)
+ *   dL_dsignal: 2*n_adc doubles (dL/dRe s_j, dL/dIm s_j), host or device
+ *   d_rho, d_t1, d_t2: NULL or n_spins doubles each, host or device: dL/dM0, dL/dT1, dL/dT2 of
+ *               every spin (dL/dT = 0 where T = INFINITY)
+ *   d_rf_flip:  NULL or one double per pulse (event with rf_flip != 0) in event order, host or
+ *               device: dL/dα of that pulse's flip angle
+ * Needs device memory for the checkpoints (ceil(n_events/ckpt_every) x 3 doubles per spin) and
+ * the signal; ENOMEM when it is not available. */
+mrsim_status mrsim_simulate_adjoint(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                                    mrsim_precision prec, int32_t ckpt_every, const double *dL_dsignal, void *stream,
+                                    double *d_rho, double *d_t1, double *d_t2, double *d_rf_flip);
+/* Pulses of a loaded sequence (events with rf_flip != 0): the length of mrsim_simulate_adjoint's
+ * d_rf_flip (-1 for NULL). */
+int64_t mrsim_sequence_num_pulses(const mrsim_sequence *s);
+
+/* ---- non-parallel fields: local static-field direction, transverse gradient components ---- */
+
+/* Forward simulation where the static field at each spin points along its own unit vector n_s
+ * and an elementary sequence's gradient field may have components transverse to z (§3.2: the
+ * frame is turned locally so that one axis lies along the static field, the Bloch equation is
+ * applied there and the result turned back; §3.4.3.2: a constant gradient field with transverse
+ * components changes the direction of the total field, and T1 relaxation follows that direction,
+ * Eqs. 3.14/3.15 holding in the turned frame).  Per spin and event, after the RF pulse of Eq.
+ * 3.19 (rotating frame, as in mrsim_simulate):
+ *     b = (gtx.x, gty.x, G.x),   u = B0*n_s + b,   h = u/|u|
+ *     θ = (γ (|u| - B0) + Δω) Δt
+ *     M <- E2 (cos θ M⊥ - sin θ h × M⊥) + (E1 (M.h) + M0 (1 - E1)) h,   M⊥ = M - (M.h) h
+ * (for n_s = z and no transverse components this is mrsim_simulate's step), and every spin
+ * starts in equilibrium along its static field, M = M0 n_s.  Samples as in mrsim_simulate.
+ *   b0_dir:       3*n_spins doubles (nx, ny, nz) per spin, unit vectors (|n|^2 within 2e-9 of 1,
+ *                 else EINVAL naming the spin); host or device
+ *   events:       n_events elementary sequences, host memory
+ *   g_transverse: NULL, or 6*n_events doubles, host memory: per event gtx (3) and gty (3) [T/m],
+ *                 the transverse field components Bx = gtx.x, By = gty.x during the event
+ *   b0_tesla:     |B0| [T] > 0; must exceed the gradient field at every spin (u != 0)
+ *   signal_out:   2*n_adc doubles, host or device; n_adc = number of sample events
+ * One thread per spin runs every event (the elementary sequences are not compiled or merged as
+ * in mrsim_simulate).  The call synchronises `stream`.  float32 keeps the phase's large part in
+ * float-float products; its error grows with the square root of the event count. */
+mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, const double *b0_dir, int64_t n_events,
+                                   const mrsim_event *events, const double *g_transverse, double gamma_hz_per_t,
+                                   double b0_tesla, mrsim_precision prec, void *stream, double *signal_out,
+                                   int64_t n_adc);
 
 /* ---- batches without allocation ---------------------------------------------------------- */
 

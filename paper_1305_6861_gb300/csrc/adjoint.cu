@@ -698,6 +698,94 @@ mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph,
     return MRSIM_OK;
 }
 
+mrsim_status mrsim_simulate_adjoint(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_sequence *seq,
+                                    mrsim_precision prec, int32_t ckpt_every, const double *dl_dsignal, void *stream,
+                                    double *d_rho, double *d_t1, double *d_t2, double *d_rf_flip) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (!ph || !seq || ph->ctx != ctx || seq->ctx != ctx)
+        return afail(ctx, MRSIM_EINVAL, "NULL phantom / sequence or another context");
+    if (!normalize_precision(prec)) return afail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (prec != MRSIM_FP64) return afail(ctx, MRSIM_EUNSUPPORTED, "the adjoint runs in float64 only (MRSIM_FP64)");
+    const HostProgram &hp = *seq->prog;
+    const int64_t n_ev = hp.n_events, n_adc = hp.host.n_adc, n = ph->n;
+    if (n_adc > 0 && !dl_dsignal) return afail(ctx, MRSIM_EINVAL, "dl_dsignal is NULL");
+    // with d_rf_flip every pulse (event with rf_flip != 0) is a learnable flip, in event order
+    std::vector<int32_t> rp;
+    std::vector<double> flips;
+    if (d_rf_flip) {
+        rp.assign((size_t)n_ev, -1);
+        for (int64_t e = 0; e < n_ev; ++e)
+            if (hp.events[(size_t)e].rf_flip != 0.0) {
+                rp[(size_t)e] = (int32_t)flips.size();
+                flips.push_back(hp.events[(size_t)e].rf_flip);
+            }
+    }
+    const int32_t n_params = (int32_t)flips.size();
+    mrsim_adjoint *adj = nullptr;
+    mrsim_status rs = mrsim_adjoint_create(ctx, n_ev, hp.events.data(), hp.gamma, d_rf_flip ? rp.data() : nullptr,
+                                           n_params, ckpt_every, &adj);
+    if (rs != MRSIM_OK) return rs;
+    // one device block for the flips, the signal and every host-side input or output:
+    // [flips | signal | dL/ds | d_rho | d_t1 | d_t2 | d_rf]
+    const bool h_dl = n_adc > 0 && !dev_ptr(dl_dsignal);
+    double *outs[4] = {d_rho, d_t1, d_t2, d_rf_flip};
+    const int64_t out_n[4] = {n, n, n, n_params};
+    bool h_out[4];
+    size_t need = (size_t)n_params + 2 * (size_t)n_adc + (h_dl ? 2 * (size_t)n_adc : 0);
+    for (int i = 0; i < 4; ++i) {
+        h_out[i] = outs[i] && out_n[i] > 0 && !dev_ptr(outs[i]);
+        if (h_out[i]) need += (size_t)out_n[i];
+    }
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *blk = nullptr;
+    if (need > 0) {
+        cudaError_t e = ctx_malloc(ctx, &blk, need * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            mrsim_adjoint_destroy(adj);
+            return afail(ctx, MRSIM_ENOMEM, "adjoint buffers: " + std::to_string(need * 8) + " bytes");
+        }
+    }
+    double *q = blk;
+    double *rfv = n_params ? q : nullptr;
+    q += n_params;
+    double *sig = q;
+    q += 2 * n_adc;
+    const double *dl = dl_dsignal;
+    if (h_dl) {
+        dl = q;
+        q += 2 * n_adc;
+    }
+    double *dout[4];
+    for (int i = 0; i < 4; ++i) {
+        dout[i] = outs[i];
+        if (h_out[i]) {
+            dout[i] = q;
+            q += out_n[i];
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (n_params) e = cudaMemcpyAsync(rfv, flips.data(), flips.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && h_dl)
+        e = cudaMemcpyAsync((double *)dl, dl_dsignal, 16 * (size_t)n_adc, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rs = afail(ctx, MRSIM_ECUDA, std::string("adjoint inputs: ") + cudaGetErrorString(e));
+    if (rs == MRSIM_OK) rs = mrsim_adjoint_forward(adj, ph, rfv, stream, sig);
+    if (rs == MRSIM_OK) rs = mrsim_adjoint_backward(adj, ph, rfv, dl, stream, dout[0], dout[1], dout[2], dout[3]);
+    for (int i = 0; i < 4 && rs == MRSIM_OK; ++i)
+        if (h_out[i]) {
+            e = cudaMemcpyAsync(outs[i], dout[i], sizeof(double) * (size_t)out_n[i], cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) rs = afail(ctx, MRSIM_ECUDA, std::string("adjoint outputs: ") + cudaGetErrorString(e));
+        }
+    // the adjoint's tables and checkpoints are freed below: wait for the work that reads them
+    e = cudaStreamSynchronize(st);
+    if (rs == MRSIM_OK && e != cudaSuccess) rs = afail(ctx, MRSIM_ECUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    cudaFree(blk);
+    mrsim_adjoint_destroy(adj);
+    if (rs == MRSIM_OK) rs = mrsim_stream_status(ctx, stream);
+    return rs;
+}
+
 void mrsim_adjoint_destroy(mrsim_adjoint *adj) {
     if (!adj) return;
     cudaSetDevice(adj->ctx->device);

@@ -335,6 +335,8 @@ mrsim_status mrsim::compile_host(int64_t n_events, const mrsim_event *events, do
         int rc = compile_sequence(events, n_events, gamma, c->host, err, n_snap, snap_after, rf_param, n_params);
         if (rc != MRSIM_OK) return (mrsim_status)rc;
         c->n_events = n_events;
+        if (n_events > 0) c->events.assign(events, events + n_events);
+        c->gamma = gamma;
         c->demod32.assign(c->host.demod.begin(), c->host.demod.end());
         c->train32.assign(c->host.train.begin(), c->host.train.end());
         for (const OpF32 &o : c->host.ops32)  // magnitude bound of the float32 inline phase terms
@@ -477,6 +479,13 @@ mrsim_status mrsim_sequence_load_snapshots(mrsim_ctx *ctx, int64_t n_events, con
 int64_t mrsim_sequence_num_adc(const mrsim_sequence *s) { return s ? s->prog->host.n_adc : -1; }
 int64_t mrsim_sequence_num_events(const mrsim_sequence *s) { return s ? s->n_events : -1; }
 int64_t mrsim_sequence_num_ops(const mrsim_sequence *s) { return s ? (int64_t)s->prog->host.ops32.size() : -1; }
+
+int64_t mrsim_sequence_num_pulses(const mrsim_sequence *s) {
+    if (!s) return -1;
+    int64_t n = 0;
+    for (const mrsim_event &e : s->prog->events) n += e.rf_flip != 0.0;
+    return n;
+}
 
 void mrsim_sequence_destroy(mrsim_sequence *s) {
     if (!s) return;

@@ -1,0 +1,496 @@
+// fields_kernel.cu -- simulation with non-parallel fields (§3.2, §3.4.3.2): a static field whose
+// direction n differs from z at each spin, and gradient fields with components transverse to z.
+//
+// §3.2 turns the frame locally so that one axis lies along the static field, applies the Bloch
+// equation there and turns the result back; §3.4.3.2 lets a constant gradient field with
+// transverse components change the direction of the total field, with T1 relaxation following
+// that direction.  Per spin and elementary sequence, after the RF pulse (Eq. 3.19, rotating
+// frame):
+//   b = (gtx.x, gty.x, G.x),  u = B0 n + b,  h = u/|u|
+//   θ = γ (|u| - B0) Δt + Δω Δt,      |u| - B0 = p + r²/(|u| + B0 + p),  p = n.b,  r = |b - p n|
+//   M <- E2 (cos θ M⊥ - sin θ h × M⊥) + (E1 (M.h) + M0 (1 - E1)) h,      M⊥ = M - (M.h) h
+// i.e. Eqs. 3.5/3.14 in the frame turned to h.  Every spin starts at M0 n.
+//
+// Layout: one thread per spin (its state, direction and position in registers), 128 threads per
+// block; the event records are staged through shared memory in chunks of FIELD_CHUNK by the
+// whole block; each sample's spin sum is a warp butterfly, a shared-memory window per chunk and
+// float64 atomics across blocks.
+//
+// float32 path: the large part of the phase, γ/2π Δt p = Σ_j n_j (k_j . x) with the moments
+// k_j = γ/2π g_j Δt in cycles/m, is summed from float-float products (hi, lo pairs of the
+// float64 values) whose integer parts drop out exactly; the small remainder γ/2π Δt r²/(...) and
+// everything else are float32.  Its error grows like the square root of the number of events
+// (about 1e-7 rad per event).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/mrsim.h"
+#include "handles.h"
+#include "internal.h"
+
+using namespace mrsim;
+
+namespace {
+
+constexpr int FIELD_THREADS = 128;
+constexpr int FIELD_CHUNK = 32;
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+enum FieldFlags : int32_t { FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8 };
+
+// float64 record: 22 doubles + 4 ints = 192 bytes
+struct alignas(16) FieldEv64 {
+    double R[9];        // Eq. 3.19 rotation (row-major) when FF_RF
+    double g[3];        // G [T/m]: field along z, G.x
+    double gt[6];       // transverse components [T/m]: Bx = gt[0..2].x, By = gt[3..5].x
+    double gdt;         // γ Δt [rad/(T)]
+    double dt;          // Δt [s]
+    double dem[2];      // cos, sin of the receiver phase
+    int32_t flags, adc, slot, pad;
+};
+static_assert(sizeof(FieldEv64) == 192, "FieldEv64 layout");
+
+// float32 record: 48 floats/ints = 192 bytes
+struct alignas(16) FieldEv32 {
+    float R[9];
+    float g[3];
+    float gt[6];
+    float kh[9], kl[9];  // k_j[d] = γ/2π g_j[d] Δt [cycles/m] as (hi, lo): j = z (G), x, y (transverse)
+    float dth, dtl;      // Δt as (hi, lo)
+    float gdt2pi;        // γ/2π Δt [cycles/T] (for the small remainder)
+    float dt;
+    float dem[2];
+    int32_t flags, adc, slot, pad;
+};
+static_assert(sizeof(FieldEv32) == 192, "FieldEv32 layout");
+
+struct FieldArgs {
+    const void *ev;
+    int64_t n_events;
+    const double *params;  // NPARAM x n_pad
+    int64_t n_spins, n_pad;
+    const double *ndir;    // 3 per spin
+    double b0;
+    double *signal;        // 2 per sample
+};
+
+// Phase accumulator in cycles for products of (hi, lo) pairs: per product the integer part of
+// the leading product is removed exactly (|ah bh| < 2^22) and the fractional parts are summed
+// without rounding error (two-sum, the error goes to the small part); the leading product's own
+// rounding error (an FMA) and the cross terms go to the small part.  value() rounds once.
+struct PhaseAcc {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add_exact(float f) {  // s + f with its rounding error kept in c
+        const float t = s + f;
+        const float bb = t - s;
+        c += (s - (t - bb)) + (f - bb);
+        s = t - rintf(t);
+    }
+    __device__ __forceinline__ void add_product(float ah, float al, float bh, float bl) {
+        const float p = ah * bh;
+        c += fmaf(ah, bh, -p) + fmaf(ah, bl, al * bh);
+        add_exact(p - rintf(p));
+    }
+    __device__ __forceinline__ float value() const {
+        const float t = s + c;
+        return t - rintf(t);
+    }
+};
+
+__host__ __device__ __forceinline__ void split(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Shared staging of one chunk of records and the chunk's sample window; flush adds the window's
+// samples to the signal.
+template <typename Ev, typename W>
+__device__ __forceinline__ int stage_chunk(const Ev *src, int64_t c0, int64_t n_events, Ev *evs, W *win) {
+    const int nc = (int)min((int64_t)FIELD_CHUNK, n_events - c0);
+    const int4 *s4 = reinterpret_cast<const int4 *>(src + c0);
+    int4 *d4 = reinterpret_cast<int4 *>(evs);
+    const int words = nc * (int)(sizeof(Ev) / sizeof(int4));
+    for (int i = threadIdx.x; i < words; i += blockDim.x) d4[i] = s4[i];
+    for (int i = threadIdx.x; i < 2 * FIELD_CHUNK; i += blockDim.x) win[i] = W(0);
+    return nc;
+}
+
+template <typename Ev, typename W>
+__device__ __forceinline__ void flush_chunk(const Ev *evs, int nc, const W *win, double *signal) {
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        if (evs[i].flags & FF_ADC) {
+            atomicAdd(&signal[2 * (int64_t)evs[i].adc], (double)win[2 * evs[i].slot]);
+            atomicAdd(&signal[2 * (int64_t)evs[i].adc + 1], (double)win[2 * evs[i].slot + 1]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) {
+    __shared__ FieldEv64 evs[FIELD_CHUNK];
+    __shared__ double win[2 * FIELD_CHUNK];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s < a.n_spins;
+    const int64_t si = live ? s : 0;
+    const int64_t np = a.n_pad;
+    const double x = a.params[P_X * np + si], y = a.params[P_Y * np + si], z = a.params[P_Z * np + si];
+    const double dw = TWO_PI * a.params[P_DF * np + si];
+    const double m0 = live ? a.params[P_RHO * np + si] : 0.0;
+    const double r1 = a.params[P_R1 * np + si], r2 = a.params[P_R2 * np + si];
+    const double n0 = a.ndir[3 * si], n1 = a.ndir[3 * si + 1], n2 = a.ndir[3 * si + 2];
+    const double b0 = a.b0;
+    double M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
+    const FieldEv64 *src = static_cast<const FieldEv64 *>(a.ev);
+    for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
+        __syncthreads();
+        const int nc = stage_chunk(src, c0, a.n_events, evs, win);
+        __syncthreads();
+        for (int i = 0; i < nc; ++i) {
+            const FieldEv64 &e = evs[i];
+            if (e.flags & FF_RF) {
+                const double t0 = e.R[0] * M0 + e.R[1] * M1 + e.R[2] * M2;
+                const double t1 = e.R[3] * M0 + e.R[4] * M1 + e.R[5] * M2;
+                const double t2 = e.R[6] * M0 + e.R[7] * M1 + e.R[8] * M2;
+                M0 = t0;
+                M1 = t1;
+                M2 = t2;
+            }
+            if (e.flags & FF_FREE) {
+                double bx = 0.0, by = 0.0;
+                const double bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
+                if (e.flags & FF_TRANSVERSE) {
+                    bx = e.gt[0] * x + e.gt[1] * y + e.gt[2] * z;
+                    by = e.gt[3] * x + e.gt[4] * y + e.gt[5] * z;
+                }
+                const double p = n0 * bx + n1 * by + n2 * bz;
+                const double qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
+                const double ux = b0 * n0 + bx, uy = b0 * n1 + by, uz = b0 * n2 + bz;
+                const double un = sqrt(ux * ux + uy * uy + uz * uz);
+                const double excess = p + (qx * qx + qy * qy + qz * qz) / (un + b0 + p);
+                const double inv = 1.0 / un;
+                const double hx = ux * inv, hy = uy * inv, hz = uz * inv;
+                double sn, cs;
+                sincos(e.gdt * excess + dw * e.dt, &sn, &cs);
+                const double e1m = expm1(-e.dt * r1), e2 = exp(-e.dt * r2);
+                const double par = M0 * hx + M1 * hy + M2 * hz;
+                const double px = M0 - par * hx, py = M1 - par * hy, pz = M2 - par * hz;
+                const double cx = hy * pz - hz * py, cy = hz * px - hx * pz, cz = hx * py - hy * px;
+                const double along = par + e1m * (par - m0);  // E1 M.h + M0 (1 - E1)
+                M0 = e2 * (cs * px - sn * cx) + along * hx;
+                M1 = e2 * (cs * py - sn * cy) + along * hy;
+                M2 = e2 * (cs * pz - sn * cz) + along * hz;
+            }
+            if (e.flags & FF_ADC) {
+                double sr = M0 * e.dem[0] + M1 * e.dem[1];
+                double sim = M1 * e.dem[0] - M0 * e.dem[1];
+                sr = warp_sum(live ? sr : 0.0);
+                sim = warp_sum(live ? sim : 0.0);
+                if ((threadIdx.x & 31) == 0) {
+                    atomicAdd(&win[2 * e.slot], sr);
+                    atomicAdd(&win[2 * e.slot + 1], sim);
+                }
+            }
+        }
+        __syncthreads();
+        flush_chunk(evs, nc, win, a.signal);
+    }
+}
+
+__global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) {
+    __shared__ FieldEv32 evs[FIELD_CHUNK];
+    __shared__ float win[2 * FIELD_CHUNK];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = s < a.n_spins;
+    const int64_t si = live ? s : 0;
+    const int64_t np = a.n_pad;
+    // set-up in float64: positions, direction and the products n_j x_d as (hi, lo) pairs
+    const double xd[3] = {a.params[P_X * np + si], a.params[P_Y * np + si], a.params[P_Z * np + si]};
+    const double nd[3] = {a.ndir[3 * si], a.ndir[3 * si + 1], a.ndir[3 * si + 2]};
+    float wh[9], wl[9];  // j = z, x, y (the order of the moments k_j), d = x, y, z
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        split(nd[2] * xd[d], wh[d], wl[d]);
+        split(nd[0] * xd[d], wh[3 + d], wl[3 + d]);
+        split(nd[1] * xd[d], wh[6 + d], wl[6 + d]);
+    }
+    float dfh, dfl;
+    split(a.params[P_DF * np + si], dfh, dfl);
+    const float x = (float)xd[0], y = (float)xd[1], z = (float)xd[2];
+    const float n0 = (float)nd[0], n1 = (float)nd[1], n2 = (float)nd[2];
+    const float m0 = live ? (float)a.params[P_RHO * np + si] : 0.0f;
+    const float r1 = (float)a.params[P_R1 * np + si], r2 = (float)a.params[P_R2 * np + si];
+    const float b0 = (float)a.b0;
+    float M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
+    const FieldEv32 *src = static_cast<const FieldEv32 *>(a.ev);
+    for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
+        __syncthreads();
+        const int nc = stage_chunk(src, c0, a.n_events, evs, win);
+        __syncthreads();
+        for (int i = 0; i < nc; ++i) {
+            const FieldEv32 &e = evs[i];
+            if (e.flags & FF_RF) {
+                const float t0 = e.R[0] * M0 + e.R[1] * M1 + e.R[2] * M2;
+                const float t1 = e.R[3] * M0 + e.R[4] * M1 + e.R[5] * M2;
+                const float t2 = e.R[6] * M0 + e.R[7] * M1 + e.R[8] * M2;
+                M0 = t0;
+                M1 = t1;
+                M2 = t2;
+            }
+            if (e.flags & FF_FREE) {
+                float bx = 0.0f, by = 0.0f;
+                const float bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
+                // phase in cycles: n_z (k_z . x) [+ n_x (k_x . x) + n_y (k_y . x)] + Δf Δt + remainder
+                PhaseAcc acc;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
+                acc.add_product(dfh, dfl, e.dth, e.dtl);
+                if (e.flags & FF_TRANSVERSE) {
+                    bx = e.gt[0] * x + e.gt[1] * y + e.gt[2] * z;
+                    by = e.gt[3] * x + e.gt[4] * y + e.gt[5] * z;
+#pragma unroll
+                    for (int q = 3; q < 9; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
+                }
+                const float p = n0 * bx + n1 * by + n2 * bz;
+                const float qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
+                const float ux = b0 * n0 + bx, uy = b0 * n1 + by, uz = b0 * n2 + bz;
+                const float un = sqrtf(ux * ux + uy * uy + uz * uz);
+                acc.c += e.gdt2pi * ((qx * qx + qy * qy + qz * qz) / (un + b0 + p));
+                const float t = acc.value();
+                const float inv = 1.0f / un;
+                const float hx = ux * inv, hy = uy * inv, hz = uz * inv;
+                float sn, cs;
+                sincospif(2.0f * t, &sn, &cs);
+                const float e1m = expm1f(-e.dt * r1), e2 = expf(-e.dt * r2);
+                const float par = M0 * hx + M1 * hy + M2 * hz;
+                const float px = M0 - par * hx, py = M1 - par * hy, pz = M2 - par * hz;
+                const float cx = hy * pz - hz * py, cy = hz * px - hx * pz, cz = hx * py - hy * px;
+                const float along = par + e1m * (par - m0);
+                M0 = e2 * (cs * px - sn * cx) + along * hx;
+                M1 = e2 * (cs * py - sn * cy) + along * hy;
+                M2 = e2 * (cs * pz - sn * cz) + along * hz;
+            }
+            if (e.flags & FF_ADC) {
+                float sr = M0 * e.dem[0] + M1 * e.dem[1];
+                float sim = M1 * e.dem[0] - M0 * e.dem[1];
+                sr = warp_sum(live ? sr : 0.0f);
+                sim = warp_sum(live ? sim : 0.0f);
+                if ((threadIdx.x & 31) == 0) {
+                    atomicAdd(&win[2 * e.slot], sr);
+                    atomicAdd(&win[2 * e.slot + 1], sim);
+                }
+            }
+        }
+        __syncthreads();
+        flush_chunk(evs, nc, win, a.signal);
+    }
+}
+
+// lowest index of a direction that is not a finite unit vector (|n| - 1 beyond 1e-9)
+__global__ void check_dirs_kernel(int64_t n, const double *nd, int *bad) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const double a = nd[3 * s], b = nd[3 * s + 1], c = nd[3 * s + 2];
+        const double l = a * a + b * b + c * c;
+        if (!(isfinite(a) && isfinite(b) && isfinite(c)) || !(fabs(l - 1.0) <= 2e-9))
+            atomicMin(bad, (int)min(s, (int64_t)0x7ffffffe));
+    }
+}
+
+// Eq. 3.19: the hard pulse as the rotation by -α about (cos φ, sin φ, 0), written as
+// R = cos α I + (1 - cos α) a aᵀ - sin α [a]x.
+void rf_matrix(double alpha, double phi, double R[9]) {
+    const double ca = std::cos(alpha), sa = std::sin(alpha), ax = std::cos(phi), ay = std::sin(phi);
+    const double o = 1.0 - ca;
+    R[0] = ca + o * ax * ax;
+    R[1] = o * ax * ay;
+    R[2] = -sa * ay;
+    R[3] = o * ax * ay;
+    R[4] = ca + o * ay * ay;
+    R[5] = sa * ax;
+    R[6] = sa * ay;
+    R[7] = -sa * ax;
+    R[8] = ca;
+}
+
+bool finite_event(const mrsim_event &e) {
+    for (double v : {e.dt, e.gx, e.gy, e.gz, e.rf_flip, e.rf_phase, e.adc_phase})
+        if (!std::isfinite(v)) return false;
+    return e.dt >= 0.0 && (e.adc == 0 || e.adc == 1) && e.reserved == 0;
+}
+
+mrsim_status ffail(mrsim_ctx *ctx, mrsim_status st, const std::string &m) {
+    if (ctx) ctx->err = m;
+    log_failure(st, m);
+    return st;
+}
+
+bool on_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, const double *b0_dir,
+                                              int64_t n_events, const mrsim_event *events, const double *g_transverse,
+                                              double gamma_hz_per_t, double b0_tesla, mrsim_precision prec,
+                                              void *stream, double *signal_out, int64_t n_adc) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (!ph || ph->ctx != ctx) return ffail(ctx, MRSIM_EINVAL, "NULL phantom or another context");
+    if (!normalize_precision(prec)) return ffail(ctx, MRSIM_EINVAL, "unknown precision");
+    const bool f64 = prec == MRSIM_FP64;
+    if (n_events < 0 || (n_events > 0 && !events)) return ffail(ctx, MRSIM_EINVAL, "invalid event list");
+    if (n_events > 0 && on_device(events)) return ffail(ctx, MRSIM_EINVAL, "events must be in host memory");
+    if (g_transverse && on_device(g_transverse))
+        return ffail(ctx, MRSIM_EINVAL, "g_transverse must be in host memory");
+    if (!(gamma_hz_per_t > 0.0) || !std::isfinite(gamma_hz_per_t)) return ffail(ctx, MRSIM_EINVAL, "gamma must be > 0");
+    if (!(b0_tesla > 0.0) || !std::isfinite(b0_tesla)) return ffail(ctx, MRSIM_EINVAL, "b0_tesla must be > 0");
+    if (ph->n > 0 && !b0_dir) return ffail(ctx, MRSIM_EINVAL, "b0_dir is NULL");
+    // host records
+    int64_t samples = 0;
+    for (int64_t i = 0; i < n_events; ++i) {
+        if (!finite_event(events[i])) return ffail(ctx, MRSIM_EINVAL, "invalid event " + std::to_string(i));
+        if (g_transverse)
+            for (int q = 0; q < 6; ++q)
+                if (!std::isfinite(g_transverse[6 * i + q]))
+                    return ffail(ctx, MRSIM_EINVAL, "non-finite transverse gradient at event " + std::to_string(i));
+        samples += events[i].adc;
+    }
+    if (samples != n_adc) return ffail(ctx, MRSIM_EINVAL, "n_adc does not match the sample events");
+    const double gamma = TWO_PI * gamma_hz_per_t;
+    std::vector<FieldEv64> e64;
+    std::vector<FieldEv32> e32;
+    try {
+        if (f64) e64.resize((size_t)n_events);
+        else e32.resize((size_t)n_events);
+    } catch (const std::bad_alloc &) {
+        return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    }
+    int64_t j = 0;
+    int slot = 0;
+    for (int64_t i = 0; i < n_events; ++i) {
+        if (i % FIELD_CHUNK == 0) slot = 0;
+        const mrsim_event &v = events[i];
+        const double *gt = g_transverse ? g_transverse + 6 * i : nullptr;
+        const bool tr = gt && (gt[0] != 0.0 || gt[1] != 0.0 || gt[2] != 0.0 || gt[3] != 0.0 || gt[4] != 0.0 || gt[5] != 0.0);
+        int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
+                        (v.dt > 0.0 ? FF_FREE : 0);
+        double R[9];
+        rf_matrix(v.rf_flip, v.rf_phase, R);
+        const double g[3] = {v.gx, v.gy, v.gz};
+        const double dem[2] = {std::cos(v.adc_phase), std::sin(v.adc_phase)};
+        const int32_t adc = v.adc ? (int32_t)j : -1, sl = v.adc ? slot : 0;
+        if (f64) {
+            FieldEv64 &r = e64[(size_t)i];
+            for (int q = 0; q < 9; ++q) r.R[q] = R[q];
+            for (int q = 0; q < 3; ++q) r.g[q] = g[q];
+            for (int q = 0; q < 6; ++q) r.gt[q] = tr ? gt[q] : 0.0;
+            r.gdt = gamma * v.dt;
+            r.dt = v.dt;
+            r.dem[0] = dem[0];
+            r.dem[1] = dem[1];
+            r.flags = flags;
+            r.adc = adc;
+            r.slot = sl;
+            r.pad = 0;
+        } else {
+            FieldEv32 &r = e32[(size_t)i];
+            for (int q = 0; q < 9; ++q) r.R[q] = (float)R[q];
+            for (int q = 0; q < 3; ++q) r.g[q] = (float)g[q];
+            for (int q = 0; q < 6; ++q) r.gt[q] = tr ? (float)gt[q] : 0.0f;
+            for (int d = 0; d < 3; ++d) {
+                split(gamma_hz_per_t * g[d] * v.dt, r.kh[d], r.kl[d]);
+                split(tr ? gamma_hz_per_t * gt[d] * v.dt : 0.0, r.kh[3 + d], r.kl[3 + d]);
+                split(tr ? gamma_hz_per_t * gt[3 + d] * v.dt : 0.0, r.kh[6 + d], r.kl[6 + d]);
+            }
+            split(v.dt, r.dth, r.dtl);
+            r.gdt2pi = (float)(gamma_hz_per_t * v.dt);
+            r.dt = (float)v.dt;
+            r.dem[0] = (float)dem[0];
+            r.dem[1] = (float)dem[1];
+            r.flags = flags;
+            r.adc = adc;
+            r.slot = sl;
+            r.pad = 0;
+        }
+        if (v.adc) {
+            ++j;
+            ++slot;
+        }
+    }
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // device block: [records | directions (host input only) | signal (host output only)]
+    const size_t rec_bytes = (size_t)n_events * (f64 ? sizeof(FieldEv64) : sizeof(FieldEv32));
+    const bool host_dir = ph->n > 0 && !on_device(b0_dir);
+    const bool host_sig = n_adc > 0 && !on_device(signal_out);
+    if (n_adc > 0 && !signal_out) return ffail(ctx, MRSIM_EINVAL, "signal_out is NULL");
+    const size_t dir_bytes = host_dir ? 24 * (size_t)ph->n : 0, sig_bytes = 16 * (size_t)n_adc;
+    const size_t dir_off = (rec_bytes + 255) / 256 * 256, sig_off = (dir_off + dir_bytes + 255) / 256 * 256;
+    const size_t need = sig_off + (host_sig ? sig_bytes : 0);
+    unsigned char *blk = nullptr;
+    if (need > 0) {
+        cudaError_t e = ctx_malloc(ctx, &blk, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ffail(ctx, MRSIM_ENOMEM, "field records: " + std::to_string(need) + " bytes");
+        }
+    }
+    mrsim_status rs = MRSIM_OK;
+    cudaError_t e = cudaSuccess;
+    const double *dir = host_dir ? reinterpret_cast<const double *>(blk + dir_off) : b0_dir;
+    double *sig = host_sig ? reinterpret_cast<double *>(blk + sig_off) : signal_out;
+    if (rec_bytes) e = cudaMemcpyAsync(blk, f64 ? (const void *)e64.data() : (const void *)e32.data(), rec_bytes,
+                                       cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && host_dir) e = cudaMemcpyAsync((void *)dir, b0_dir, dir_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_adc > 0) e = cudaMemsetAsync(sig, 0, sig_bytes, st);
+    if (e == cudaSuccess && ph->n > 0) {  // directions: finite unit vectors
+        e = cudaMemsetAsync(ctx->d_bad, 0x7f, sizeof(int), st);
+        if (e == cudaSuccess) {
+            check_dirs_kernel<<<(int)std::min<int64_t>((ph->n + 255) / 256, 4096), 256, 0, st>>>(ph->n, dir, ctx->d_bad);
+            e = cudaGetLastError();
+        }
+        int bad = 0x7f7f7f7f;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && bad != 0x7f7f7f7f)
+            rs = ffail(ctx, MRSIM_EINVAL, "b0_dir of spin " + std::to_string(bad) + " is not a finite unit vector");
+    }
+    if (e == cudaSuccess && rs == MRSIM_OK && ph->n > 0 && n_events > 0) {
+        FieldArgs a{};
+        a.ev = blk;
+        a.n_events = n_events;
+        a.params = ph->params;
+        a.n_spins = ph->n;
+        a.n_pad = ph->n_pad;
+        a.ndir = dir;
+        a.b0 = b0_tesla;
+        a.signal = sig;
+        const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
+        if (f64) fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
+        else fields_kernel_f32<<<grid, FIELD_THREADS, 0, st>>>(a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && rs == MRSIM_OK && host_sig) e = cudaMemcpyAsync(signal_out, sig, sig_bytes, cudaMemcpyDeviceToHost, st);
+    // the records are freed below: the launch must be done with them
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    cudaFree(blk);
+    if (rs != MRSIM_OK) return rs;
+    if (e != cudaSuccess) return ffail(ctx, MRSIM_ECUDA, std::string("fields simulation: ") + cudaGetErrorString(e));
+    return MRSIM_OK;
+}

@@ -81,6 +81,10 @@ struct HostProgram {
     std::vector<float> demod32, train32;
     float kmax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     int64_t n_events = 0;
+    // the event list and γ/2π it was compiled from (the one-shot adjoint recompiles them with
+    // learnable pulses)
+    std::vector<mrsim_event> events;
+    double gamma = 0.0;
     // every device table in one 256-byte-aligned image, uploaded with a single copy: operations
     // (float32, float64), phasor classes, T1 and T2 classes, demodulation (float64, float32),
     // sub-pulse tables (float32, float64)

@@ -42,7 +42,8 @@ EXPORTS = (
     "mrsim_adjoint_create", "mrsim_adjoint_num_adc", "mrsim_adjoint_forward", "mrsim_adjoint_backward",
     "mrsim_adjoint_destroy", "mrsim_compile", "mrsim_compile_last_error", "mrsim_compiled_num_adc",
     "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
-    "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate",
+    "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate", "mrsim_simulate_adjoint",
+    "mrsim_sequence_num_pulses", "mrsim_simulate_fields",
 )
 
 
@@ -132,6 +133,9 @@ def lib():
             "mrsim_adjoint_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "mrsim_adjoint_backward": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "mrsim_adjoint_destroy": (None, [vp]),
+            "mrsim_simulate_adjoint": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, i32, vp, vp, vp, vp, vp, vp]),
+            "mrsim_sequence_num_pulses": (i64, [vp]),
+            "mrsim_simulate_fields": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, dbl, dbl, ctypes.c_int, vp, vp, i64]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
             "mrsim_compile": (ctypes.c_int, [i64, vp, dbl, i64, vp, P(vp)]),
             "mrsim_compile_last_error": (ctypes.c_char_p, []),
@@ -498,6 +502,42 @@ class Adjoint:
             self.close()
         except Exception:
             pass
+
+
+def simulate_adjoint(ctx: Context, phantom: Phantom, seq: Sequence, dl_dsignal, precision: int = FP64,
+                     ckpt_every: int = 64, stream=None, outs=None, rf: bool = True):
+    """One-shot gradients (mrsim_simulate_adjoint) of a loss with dL/ds = `dl_dsignal` (numpy
+    complex128[n_adc] or a CUDA buffer of 2*n_adc float64).  Returns (dL/dM0, dL/dT1, dL/dT2,
+    dL/dα per pulse in event order, or None without `rf`) as numpy arrays, or fills `outs`
+    (four buffers, host or CUDA, any of them None)."""
+    if isinstance(dl_dsignal, np.ndarray):
+        dl_dsignal = np.ascontiguousarray(dl_dsignal, dtype=np.complex128)
+    if outs is None:
+        n_p = int(lib().mrsim_sequence_num_pulses(seq.h))
+        outs = [np.zeros(phantom.n), np.zeros(phantom.n), np.zeros(phantom.n), np.zeros(n_p) if rf else None]
+    ctx.check(lib().mrsim_simulate_adjoint(ctx.h, phantom.h, seq.h, int(precision), int(ckpt_every), _ptr(dl_dsignal),
+                                           _stream(stream), *[_ptr(o) for o in outs]))
+    return tuple(outs)
+
+
+def simulate_fields(ctx: Context, phantom: Phantom, events, gamma_hz_per_t: float, b0_dir, g_transverse=None,
+                    b0_tesla: float = 1.5, precision: int = FP32, stream=None, out=None):
+    """Non-parallel fields (mrsim_simulate_fields): b0_dir [n_spins, 3] unit vectors (numpy, or a
+    CUDA buffer of 3*n_spins float64), g_transverse None or [n_events, 6] (gtx, gty) [T/m].
+    Returns (or fills) the signal: numpy complex128[n_adc] or a CUDA buffer of 2*n_adc float64."""
+    ev = np.ascontiguousarray(events)
+    if ev.dtype != EVENT_DTYPE:
+        ev = ev.astype(EVENT_DTYPE)
+    if isinstance(b0_dir, np.ndarray):
+        b0_dir = np.ascontiguousarray(b0_dir, dtype=np.float64).reshape(-1)
+    gt = None if g_transverse is None else np.ascontiguousarray(g_transverse, dtype=np.float64).reshape(-1)
+    n_adc = int(np.count_nonzero(ev["adc"]))
+    if out is None:
+        out = np.zeros(n_adc, dtype=np.complex128)
+    ctx.check(lib().mrsim_simulate_fields(ctx.h, phantom.h, _ptr(b0_dir), ev.shape[0], _ptr(ev), _ptr(gt),
+                                          float(gamma_hz_per_t), float(b0_tesla), int(precision), _stream(stream),
+                                          _ptr(out), n_adc))
+    return out
 
 
 def autotune(ctx: Context, phantom: Phantom, seq: Sequence, precision: int = FP32, stream=None):

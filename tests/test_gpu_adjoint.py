@@ -211,3 +211,40 @@ def test_allocation_failures_in_adjoint(M, torch, oracle_mod):
         P.close()
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("seed,n_sp,ckpt,host", [(10, 150, 64, True), (11, 37, 5, False), (12, 1, 0, True)])
+def test_simulate_adjoint_one_shot(M, ctx, torch, oracle_mod, seed, n_sp, ckpt, host):
+    """mrsim_simulate_adjoint on a loaded sequence: every pulse's flip is a learnable parameter (in
+    event order); host or device buffers; against the oracle's forward-mode gradient at the
+    adjoint's bar; a float32 precision is refused (the gradients are float64)."""
+    ph, ev, _, _, rng = shaped_case(seed, n_sp)
+    flips = ev["rf_flip"]
+    params = np.full(len(ev), -1, dtype=np.int32)
+    pulses = np.nonzero(flips != 0)[0]
+    params[pulses] = np.arange(pulses.size, dtype=np.int32)
+    rf = flips[pulses].copy()
+    sig = oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf)
+    h = 2 * (sig - 0.8 * sig[::-1])
+    g = oracle_mod.gradient(ph, ev, W.GAMMA_BAR, h, params, rf, list(range(rf.size)))
+    P = M.Phantom.from_workload_phantom(ctx, ph)
+    seq = M.Sequence(ctx, ev, W.GAMMA_BAR)
+    assert M.lib().mrsim_sequence_num_pulses(seq.h) == pulses.size
+    if host:
+        got = M.simulate_adjoint(ctx, P, seq, h, ckpt_every=ckpt)
+    else:
+        dev = torch.device("cuda:0")
+        hd = torch.from_numpy(np.ascontiguousarray(h).view(np.float64).copy()).to(dev)
+        outs = [torch.zeros(ph.n, dtype=torch.float64, device=dev) for _ in range(3)]
+        outs.append(torch.zeros(pulses.size, dtype=torch.float64, device=dev))
+        M.simulate_adjoint(ctx, P, seq, hd, ckpt_every=ckpt, outs=outs)
+        got = [o.cpu().numpy() for o in outs]
+    for a, b in zip(got, g):
+        assert rel(a, b) <= 1e-10
+    # without RF gradients, only the spin parameters
+    d_rho, d_t1, d_t2, d_rf = M.simulate_adjoint(ctx, P, seq, h, rf=False)
+    assert d_rf is None and rel(d_rho, g[0]) <= 1e-10 and rel(d_t2, g[2]) <= 1e-10
+    for prec in (M.FP32, M.FP32_KAHAN):
+        with pytest.raises(M.MrsimError) as e:
+            M.simulate_adjoint(ctx, P, seq, h, precision=prec)
+        assert e.value.status == M.Status.EUNSUPPORTED

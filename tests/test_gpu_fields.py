@@ -1,0 +1,147 @@
+"""Non-parallel fields on the GPU (mrsim_simulate_fields, §3.2 and §3.4.3.2) against the oracle:
+per-spin static-field directions (small tilts and arbitrary directions), gradient fields with
+transverse components, low and high main field, several thread blocks with a ragged tail, both
+precisions (relative L2 of the signal: float64 at the phase-rounding floor of the sequence, at
+least 1e-12; float32 2e-5); the parallel case equals the standard path; invalid inputs."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1305_6861_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def M(mrsim_lib):
+    return mrsim_lib
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def directions(rng, n, max_tilt):
+    ct = rng.uniform(math.cos(max_tilt), 1.0, n)
+    st = np.sqrt(1 - ct**2)
+    ph = rng.uniform(0, 2 * math.pi, n)
+    return np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=1)
+
+
+def case(rng, n_spins, n_events, transverse=True):
+    ph = W.random_phantom(n_spins, rng)
+    ph.dw[:] = 2 * math.pi * rng.uniform(-100, 100, n_spins)
+    rows = []
+    for _ in range(n_events):
+        flip = rng.uniform(-math.pi, math.pi) if rng.uniform() < 0.1 else 0.0
+        g = rng.uniform(-5e-3, 5e-3, 3) if rng.uniform() < 0.8 else np.zeros(3)
+        dt = rng.uniform(0.0, 3e-4) if rng.uniform() < 0.95 else 0.0
+        rows.append((dt, *g, flip, rng.uniform(0, 2 * math.pi), int(rng.uniform() < 0.4), rng.uniform(0, 2 * math.pi)))
+    ev = W.make_events(rows)
+    gt = None
+    if transverse:
+        gt = rng.uniform(-4e-3, 4e-3, (n_events, 6))
+        gt[rng.uniform(size=n_events) < 0.4] = 0.0
+    return ph, ev, gt
+
+
+def phase_floor(ph, ev, gt, b0):
+    """float64 floor of a sequence: each side rounds every event's angle with relative error
+    2^-53, so 4 * 2^-53 * sqrt(sum of squared angles) bounds the relative signal difference."""
+    x = np.stack([ph.x, ph.y, ph.z], axis=1)
+    g = np.stack([ev["gx"], ev["gy"], ev["gz"]], axis=1)
+    b = np.abs(g) @ np.abs(x).max(axis=0)
+    if gt is not None:
+        b = b + np.abs(gt[:, :3]) @ np.abs(x).max(axis=0) + np.abs(gt[:, 3:]) @ np.abs(x).max(axis=0)
+    th = (2 * math.pi * W.GAMMA_BAR * b + np.abs(ph.dw).max()) * ev["dt"]
+    return max(TOL64, 4 * 2.0**-53 * float(np.sqrt(np.sum(th**2))))
+
+
+@pytest.mark.parametrize("seed,n_spins,n_events,max_tilt,b0,transverse", [
+    (0, 3001, 700, 0.2, 1.5, True),       # small tilts, transverse gradients, 1.5 T
+    (1, 1000, 500, math.pi, 0.05, True),  # arbitrary directions at a low main field
+    (2, 257, 900, 1.0, 0.3, False),       # tilted fields, parallel gradients only
+    (3, 1, 300, math.pi, 1.0, True),      # one spin
+])
+def test_fields_match_oracle(M, ctx, oracle_mod, seed, n_spins, n_events, max_tilt, b0, transverse):
+    rng = np.random.default_rng(900 + seed)
+    ph, ev, gt = case(rng, n_spins, n_events, transverse)
+    nd = directions(rng, n_spins, max_tilt)
+    ref, _ = oracle_mod.simulate_fields(ph, ev, W.GAMMA_BAR, nd, gt, b0)
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    got64 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, b0, M.FP64)
+    got32 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, b0, M.FP32)
+    ctx.stream_status()
+    assert rel_l2(got64, ref) <= phase_floor(ph, ev, gt, b0)
+    assert rel_l2(got32, ref) <= TOL32
+
+
+def test_fields_parallel_case_is_the_standard_path(M, ctx, oracle_mod):
+    """n = z everywhere and no transverse components: the C1 FLASH through the field path equals the
+    oracle (1e-12 / 2e-5) and the standard path."""
+    w = W.config1()
+    ev = w.sequence.events
+    nd = np.tile([0.0, 0.0, 1.0], (w.phantom.n, 1))
+    ref = oracle_mod.signal(w)
+    p = M.Phantom.from_workload_phantom(ctx, w.phantom)
+    s = M.Sequence.from_workload_sequence(ctx, w.sequence)
+    std = M.simulate(ctx, p, s, M.FP64)
+    got64 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, None, 1.5, M.FP64)
+    got32 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, np.zeros((len(ev), 6)), 1.5, M.FP32)
+    assert rel_l2(got64, ref) <= TOL64 and rel_l2(got64, std) <= TOL64
+    assert rel_l2(got32, ref) <= TOL32
+
+
+def test_fields_device_buffers(M, ctx, oracle_mod):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(905)
+    ph, ev, gt = case(rng, 700, 400)
+    nd = directions(rng, ph.n, 0.5)
+    ref, _ = oracle_mod.simulate_fields(ph, ev, W.GAMMA_BAR, nd, gt, 0.5)
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    dev = torch.device("cuda:0")
+    ndd = torch.from_numpy(nd.reshape(-1).copy()).to(dev)
+    out = torch.zeros(2 * int(np.count_nonzero(ev["adc"])), dtype=torch.float64, device=dev)
+    M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, ndd, gt, 0.5, M.FP64, out=out)
+    assert rel_l2(out.cpu().numpy().view(np.complex128), ref) <= phase_floor(ph, ev, gt, 0.5)
+
+
+def test_fields_edge_cases_and_invalid_inputs(M, ctx, oracle_mod):
+    rng = np.random.default_rng(906)
+    ph, ev, gt = case(rng, 50, 100)
+    nd = directions(rng, ph.n, 1.0)
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    # no spins: zero signal; no events: empty signal
+    p0 = M.Phantom.from_workload_phantom(ctx, W.random_phantom(0, rng))
+    for prec in (M.FP64, M.FP32):
+        z = M.simulate_fields(ctx, p0, ev, W.GAMMA_BAR, np.zeros((0, 3)), gt, 1.5, prec)
+        assert z.shape == (int(np.count_nonzero(ev["adc"])),) and not np.any(z)
+        assert M.simulate_fields(ctx, p, ev[:0], W.GAMMA_BAR, nd, None, 1.5, prec).shape == (0,)
+    bad = nd.copy()
+    bad[7] *= 1.01  # not a unit vector
+    with pytest.raises(M.MrsimError) as e:
+        M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, bad, gt, 1.5, M.FP32)
+    assert e.value.status == M.Status.EINVAL and "spin 7" in str(e.value)
+    for b0 in (0.0, -1.0, float("nan")):
+        with pytest.raises(M.MrsimError) as e:
+            M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, b0, M.FP64)
+        assert e.value.status == M.Status.EINVAL
+    g_bad = gt.copy()
+    g_bad[3, 2] = np.inf
+    with pytest.raises(M.MrsimError):
+        M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, g_bad, 1.5, M.FP64)
+    # the context stays usable
+    ref, _ = oracle_mod.simulate_fields(ph, ev, W.GAMMA_BAR, nd, gt, 1.5)
+    assert rel_l2(M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, 1.5, M.FP64), ref) <= phase_floor(ph, ev, gt, 1.5)
