@@ -354,32 +354,44 @@ int64_t mrsim_sequence_num_pulses(const mrsim_sequence *s);
 
 /* ---- non-parallel fields: local static-field direction, transverse gradient components ---- */
 
-/* Forward simulation where the static field at each spin points along its own unit vector n_s
- * and an elementary sequence's gradient field may have components transverse to z (§3.2: the
- * frame is turned locally so that one axis lies along the static field, the Bloch equation is
- * applied there and the result turned back; §3.4.3.2: a constant gradient field with transverse
- * components changes the direction of the total field, and T1 relaxation follows that direction,
- * Eqs. 3.14/3.15 holding in the turned frame).  Per spin and event, after the RF pulse of Eq.
- * 3.19 (rotating frame, as in mrsim_simulate):
+/* The static field at each spin may point along its own unit vector n_s (§3.2: the frame is
+ * turned locally so that one axis lies along the static field, the Bloch equation is applied
+ * there and the result turned back), and an elementary sequence's gradient field may have
+ * components transverse to z (§3.4.3.2: a constant gradient field with transverse components
+ * changes the direction of the total field, T1 relaxation follows that direction, and Eqs.
+ * 3.14/3.15 hold in the turned frame).  Per spin and event, after the RF pulse of Eq. 3.19
+ * (rotating frame, as in mrsim_simulate):
  *     b = (gtx.x, gty.x, G.x),   u = B0*n_s + b,   h = u/|u|
  *     θ = (γ (|u| - B0) + Δω) Δt
  *     M <- E2 (cos θ M⊥ - sin θ h × M⊥) + (E1 (M.h) + M0 (1 - E1)) h,   M⊥ = M - (M.h) h
  * (for n_s = z and no transverse components this is mrsim_simulate's step), and every spin
- * starts in equilibrium along its static field, M = M0 n_s.  Samples as in mrsim_simulate.
- *   b0_dir:       3*n_spins doubles (nx, ny, nz) per spin, unit vectors (|n|^2 within 2e-9 of 1,
- *                 else EINVAL naming the spin); host or device
- *   events:       n_events elementary sequences, host memory
+ * starts in equilibrium along its static field, M = M0 n_s.  Samples as in mrsim_simulate. */
+
+/* Sets the phantom's static-field directions: b0_dir = 3*n_spins doubles (nx, ny, nz) per spin,
+ * unit vectors (|n|^2 within 2e-9 of 1, else EINVAL naming the first bad spin), host or device;
+ * the phantom keeps a device copy (3 doubles per spin).  A phantom without directions has its
+ * field along z.  Synchronises `stream`. */
+mrsim_status mrsim_phantom_set_b0_direction(mrsim_phantom *ph, const double *b0_dir, void *stream);
+/* An event list prepared for mrsim_simulate_fields (the events are not compiled or merged as for
+ * mrsim_simulate: one thread per spin runs every event):
+ *   events:       n_events elementary sequences, host memory (validated as for mrsim_sequence_load)
  *   g_transverse: NULL, or 6*n_events doubles, host memory: per event gtx (3) and gty (3) [T/m],
  *                 the transverse field components Bx = gtx.x, By = gty.x during the event
- *   b0_tesla:     |B0| [T] > 0; must exceed the gradient field at every spin (u != 0)
- *   signal_out:   2*n_adc doubles, host or device; n_adc = number of sample events
- * One thread per spin runs every event (the elementary sequences are not compiled or merged as
- * in mrsim_simulate).  The call synchronises `stream`.  float32 keeps the phase's large part in
- * float-float products; its error grows with the square root of the event count. */
-mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, const double *b0_dir, int64_t n_events,
-                                   const mrsim_event *events, const double *g_transverse, double gamma_hz_per_t,
-                                   double b0_tesla, mrsim_precision prec, void *stream, double *signal_out,
-                                   int64_t n_adc);
+ *   b0_tesla:     |B0| [T] > 0; it must exceed the gradient field at every spin (u != 0)
+ * The records (float64 and float32, 192 bytes each per event) are uploaded once. */
+typedef struct mrsim_fields mrsim_fields;
+mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                 const double *g_transverse, double gamma_hz_per_t, double b0_tesla,
+                                 mrsim_fields **out);
+/* Samples of the prepared list (the signal's length; -1 for NULL). */
+int64_t mrsim_fields_num_adc(const mrsim_fields *f);
+void mrsim_fields_destroy(mrsim_fields *f);
+/* Forward simulation with non-parallel fields: signal_out = 2*n_adc doubles, host or device
+ * (device output: asynchronous on `stream`; host output synchronises).  float32 keeps the
+ * phase's large part in float-float products; its error grows with the square root of the
+ * number of events a spin's state carries (about 1e-7 rad per event). */
+mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_fields *f,
+                                   mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc);
 
 /* ---- batches without allocation ---------------------------------------------------------- */
 

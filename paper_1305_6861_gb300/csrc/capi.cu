@@ -309,6 +309,7 @@ void mrsim_phantom_destroy(mrsim_phantom *p) {
     if (!p) return;
     cudaSetDevice(p->ctx->device);
     cudaFree(p->params);
+    cudaFree(p->d_dir);
     delete p;
 }
 

@@ -73,7 +73,7 @@ struct FieldArgs {
     int64_t n_events;
     const double *params;  // NPARAM x n_pad
     int64_t n_spins, n_pad;
-    const double *ndir;    // 3 per spin
+    const double *ndir;    // 3 per spin, or NULL: every spin's field along z
     double b0;
     double *signal;        // 2 per sample
 };
@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
     const double dw = TWO_PI * a.params[P_DF * np + si];
     const double m0 = live ? a.params[P_RHO * np + si] : 0.0;
     const double r1 = a.params[P_R1 * np + si], r2 = a.params[P_R2 * np + si];
-    const double n0 = a.ndir[3 * si], n1 = a.ndir[3 * si + 1], n2 = a.ndir[3 * si + 2];
+    const double n0 = a.ndir ? a.ndir[3 * si] : 0.0, n1 = a.ndir ? a.ndir[3 * si + 1] : 0.0;
+    const double n2 = a.ndir ? a.ndir[3 * si + 2] : 1.0;
     const double b0 = a.b0;
     double M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
     const FieldEv64 *src = static_cast<const FieldEv64 *>(a.ev);
@@ -215,7 +216,8 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) 
     const int64_t np = a.n_pad;
     // set-up in float64: positions, direction and the products n_j x_d as (hi, lo) pairs
     const double xd[3] = {a.params[P_X * np + si], a.params[P_Y * np + si], a.params[P_Z * np + si]};
-    const double nd[3] = {a.ndir[3 * si], a.ndir[3 * si + 1], a.ndir[3 * si + 2]};
+    const double nd[3] = {a.ndir ? a.ndir[3 * si] : 0.0, a.ndir ? a.ndir[3 * si + 1] : 0.0,
+                          a.ndir ? a.ndir[3 * si + 2] : 1.0};
     float wh[9], wl[9];  // j = z, x, y (the order of the moments k_j), d = x, y, z
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -345,38 +347,73 @@ bool on_device(const void *p) {
 
 }  // namespace
 
-extern "C" mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, const double *b0_dir,
-                                              int64_t n_events, const mrsim_event *events, const double *g_transverse,
-                                              double gamma_hz_per_t, double b0_tesla, mrsim_precision prec,
-                                              void *stream, double *signal_out, int64_t n_adc) {
-    if (!ctx) return MRSIM_EINVAL;
-    if (!ph || ph->ctx != ctx) return ffail(ctx, MRSIM_EINVAL, "NULL phantom or another context");
-    if (!normalize_precision(prec)) return ffail(ctx, MRSIM_EINVAL, "unknown precision");
-    const bool f64 = prec == MRSIM_FP64;
+struct mrsim_fields {
+    mrsim_ctx *ctx = nullptr;
+    int64_t n_events = 0, n_adc = 0;
+    double b0 = 0.0;
+    unsigned char *d_rec = nullptr;  // [float64 records | float32 records]
+    size_t off32 = 0;
+};
+
+extern "C" {
+
+mrsim_status mrsim_phantom_set_b0_direction(mrsim_phantom *ph, const double *b0_dir, void *stream) {
+    if (!ph) return MRSIM_EINVAL;
+    mrsim_ctx *ctx = ph->ctx;
+    if (ph->n > 0 && !b0_dir) return ffail(ctx, MRSIM_EINVAL, "b0_dir is NULL");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 24 * (size_t)ph->n;
+    double *d = nullptr;
+    if (bytes) {
+        cudaError_t e = ctx_malloc(ctx, &d, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ffail(ctx, MRSIM_ENOMEM, "field directions: " + std::to_string(bytes) + " bytes");
+        }
+        e = cudaMemcpyAsync(d, b0_dir, bytes, on_device(b0_dir) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bad, 0x7f, sizeof(int), st);
+        if (e == cudaSuccess) {
+            check_dirs_kernel<<<(int)std::min<int64_t>((ph->n + 255) / 256, 4096), 256, 0, st>>>(ph->n, d, ctx->d_bad);
+            e = cudaGetLastError();
+        }
+        int bad = 0x7f7f7f7f;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || bad != 0x7f7f7f7f) {
+            cudaFree(d);
+            if (e != cudaSuccess) return ffail(ctx, MRSIM_ECUDA, std::string("field directions: ") + cudaGetErrorString(e));
+            return ffail(ctx, MRSIM_EINVAL, "b0_dir of spin " + std::to_string(bad) + " is not a finite unit vector");
+        }
+    }
+    cudaFree(ph->d_dir);
+    ph->d_dir = d;
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
+                                 const double *g_transverse, double gamma_hz_per_t, double b0_tesla,
+                                 mrsim_fields **out) {
+    if (!ctx || !out) return MRSIM_EINVAL;
+    *out = nullptr;
     if (n_events < 0 || (n_events > 0 && !events)) return ffail(ctx, MRSIM_EINVAL, "invalid event list");
     if (n_events > 0 && on_device(events)) return ffail(ctx, MRSIM_EINVAL, "events must be in host memory");
-    if (g_transverse && on_device(g_transverse))
-        return ffail(ctx, MRSIM_EINVAL, "g_transverse must be in host memory");
+    if (g_transverse && on_device(g_transverse)) return ffail(ctx, MRSIM_EINVAL, "g_transverse must be in host memory");
     if (!(gamma_hz_per_t > 0.0) || !std::isfinite(gamma_hz_per_t)) return ffail(ctx, MRSIM_EINVAL, "gamma must be > 0");
     if (!(b0_tesla > 0.0) || !std::isfinite(b0_tesla)) return ffail(ctx, MRSIM_EINVAL, "b0_tesla must be > 0");
-    if (ph->n > 0 && !b0_dir) return ffail(ctx, MRSIM_EINVAL, "b0_dir is NULL");
-    // host records
-    int64_t samples = 0;
     for (int64_t i = 0; i < n_events; ++i) {
         if (!finite_event(events[i])) return ffail(ctx, MRSIM_EINVAL, "invalid event " + std::to_string(i));
         if (g_transverse)
             for (int q = 0; q < 6; ++q)
                 if (!std::isfinite(g_transverse[6 * i + q]))
                     return ffail(ctx, MRSIM_EINVAL, "non-finite transverse gradient at event " + std::to_string(i));
-        samples += events[i].adc;
     }
-    if (samples != n_adc) return ffail(ctx, MRSIM_EINVAL, "n_adc does not match the sample events");
     const double gamma = TWO_PI * gamma_hz_per_t;
     std::vector<FieldEv64> e64;
     std::vector<FieldEv32> e32;
     try {
-        if (f64) e64.resize((size_t)n_events);
-        else e32.resize((size_t)n_events);
+        e64.resize((size_t)n_events);
+        e32.resize((size_t)n_events);
     } catch (const std::bad_alloc &) {
         return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
     }
@@ -387,110 +424,134 @@ extern "C" mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phanto
         const mrsim_event &v = events[i];
         const double *gt = g_transverse ? g_transverse + 6 * i : nullptr;
         const bool tr = gt && (gt[0] != 0.0 || gt[1] != 0.0 || gt[2] != 0.0 || gt[3] != 0.0 || gt[4] != 0.0 || gt[5] != 0.0);
-        int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
-                        (v.dt > 0.0 ? FF_FREE : 0);
+        const int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
+                              (v.dt > 0.0 ? FF_FREE : 0);
         double R[9];
         rf_matrix(v.rf_flip, v.rf_phase, R);
         const double g[3] = {v.gx, v.gy, v.gz};
         const double dem[2] = {std::cos(v.adc_phase), std::sin(v.adc_phase)};
         const int32_t adc = v.adc ? (int32_t)j : -1, sl = v.adc ? slot : 0;
-        if (f64) {
-            FieldEv64 &r = e64[(size_t)i];
-            for (int q = 0; q < 9; ++q) r.R[q] = R[q];
-            for (int q = 0; q < 3; ++q) r.g[q] = g[q];
-            for (int q = 0; q < 6; ++q) r.gt[q] = tr ? gt[q] : 0.0;
-            r.gdt = gamma * v.dt;
-            r.dt = v.dt;
-            r.dem[0] = dem[0];
-            r.dem[1] = dem[1];
-            r.flags = flags;
-            r.adc = adc;
-            r.slot = sl;
-            r.pad = 0;
-        } else {
-            FieldEv32 &r = e32[(size_t)i];
-            for (int q = 0; q < 9; ++q) r.R[q] = (float)R[q];
-            for (int q = 0; q < 3; ++q) r.g[q] = (float)g[q];
-            for (int q = 0; q < 6; ++q) r.gt[q] = tr ? (float)gt[q] : 0.0f;
-            for (int d = 0; d < 3; ++d) {
-                split(gamma_hz_per_t * g[d] * v.dt, r.kh[d], r.kl[d]);
-                split(tr ? gamma_hz_per_t * gt[d] * v.dt : 0.0, r.kh[3 + d], r.kl[3 + d]);
-                split(tr ? gamma_hz_per_t * gt[3 + d] * v.dt : 0.0, r.kh[6 + d], r.kl[6 + d]);
-            }
-            split(v.dt, r.dth, r.dtl);
-            r.gdt2pi = (float)(gamma_hz_per_t * v.dt);
-            r.dt = (float)v.dt;
-            r.dem[0] = (float)dem[0];
-            r.dem[1] = (float)dem[1];
-            r.flags = flags;
-            r.adc = adc;
-            r.slot = sl;
-            r.pad = 0;
+        FieldEv64 &r = e64[(size_t)i];
+        FieldEv32 &f = e32[(size_t)i];
+        for (int q = 0; q < 9; ++q) {
+            r.R[q] = R[q];
+            f.R[q] = (float)R[q];
         }
+        for (int q = 0; q < 3; ++q) {
+            r.g[q] = g[q];
+            f.g[q] = (float)g[q];
+        }
+        for (int q = 0; q < 6; ++q) {
+            r.gt[q] = tr ? gt[q] : 0.0;
+            f.gt[q] = (float)r.gt[q];
+        }
+        for (int d = 0; d < 3; ++d) {
+            split(gamma_hz_per_t * g[d] * v.dt, f.kh[d], f.kl[d]);
+            split(gamma_hz_per_t * r.gt[d] * v.dt, f.kh[3 + d], f.kl[3 + d]);
+            split(gamma_hz_per_t * r.gt[3 + d] * v.dt, f.kh[6 + d], f.kl[6 + d]);
+        }
+        r.gdt = gamma * v.dt;
+        r.dt = v.dt;
+        split(v.dt, f.dth, f.dtl);
+        f.gdt2pi = (float)(gamma_hz_per_t * v.dt);
+        f.dt = (float)v.dt;
+        r.dem[0] = dem[0];
+        r.dem[1] = dem[1];
+        f.dem[0] = (float)dem[0];
+        f.dem[1] = (float)dem[1];
+        r.flags = f.flags = flags;
+        r.adc = f.adc = adc;
+        r.slot = f.slot = sl;
+        r.pad = f.pad = 0;
         if (v.adc) {
             ++j;
             ++slot;
         }
     }
     cudaSetDevice(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    // device block: [records | directions (host input only) | signal (host output only)]
-    const size_t rec_bytes = (size_t)n_events * (f64 ? sizeof(FieldEv64) : sizeof(FieldEv32));
-    const bool host_dir = ph->n > 0 && !on_device(b0_dir);
-    const bool host_sig = n_adc > 0 && !on_device(signal_out);
-    if (n_adc > 0 && !signal_out) return ffail(ctx, MRSIM_EINVAL, "signal_out is NULL");
-    const size_t dir_bytes = host_dir ? 24 * (size_t)ph->n : 0, sig_bytes = 16 * (size_t)n_adc;
-    const size_t dir_off = (rec_bytes + 255) / 256 * 256, sig_off = (dir_off + dir_bytes + 255) / 256 * 256;
-    const size_t need = sig_off + (host_sig ? sig_bytes : 0);
-    unsigned char *blk = nullptr;
-    if (need > 0) {
-        cudaError_t e = ctx_malloc(ctx, &blk, need);
+    mrsim_fields *fh = new (std::nothrow) mrsim_fields();
+    if (!fh) return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    fh->ctx = ctx;
+    fh->n_events = n_events;
+    fh->n_adc = j;
+    fh->b0 = b0_tesla;
+    const size_t b64 = (size_t)n_events * sizeof(FieldEv64), b32 = (size_t)n_events * sizeof(FieldEv32);
+    fh->off32 = (b64 + 255) / 256 * 256;
+    if (n_events > 0) {
+        cudaError_t e = ctx_malloc(ctx, &fh->d_rec, fh->off32 + b32);
+        if (e == cudaSuccess) e = cudaMemcpy(fh->d_rec, e64.data(), b64, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(fh->d_rec + fh->off32, e32.data(), b32, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return ffail(ctx, MRSIM_ENOMEM, "field records: " + std::to_string(need) + " bytes");
+            cudaFree(fh->d_rec);
+            delete fh;
+            return ffail(ctx, e == cudaErrorMemoryAllocation ? MRSIM_ENOMEM : MRSIM_ECUDA,
+                         std::string("field records: ") + cudaGetErrorString(e));
         }
     }
-    mrsim_status rs = MRSIM_OK;
+    *out = fh;
+    return MRSIM_OK;
+}
+
+int64_t mrsim_fields_num_adc(const mrsim_fields *f) { return f ? f->n_adc : -1; }
+
+void mrsim_fields_destroy(mrsim_fields *f) {
+    if (!f) return;
+    cudaSetDevice(f->ctx->device);
+    cudaFree(f->d_rec);
+    delete f;
+}
+
+mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim_fields *f,
+                                   mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc) {
+    if (!ctx) return MRSIM_EINVAL;
+    if (!ph || !f || ph->ctx != ctx || f->ctx != ctx) return ffail(ctx, MRSIM_EINVAL, "NULL handle or another context");
+    if (!normalize_precision(prec)) return ffail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (n_adc != f->n_adc) return ffail(ctx, MRSIM_EINVAL, "n_adc does not match the sample events");
+    if (n_adc > 0 && !signal_out) return ffail(ctx, MRSIM_EINVAL, "signal_out is NULL");
+    const bool f64 = prec == MRSIM_FP64;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t sig_bytes = 16 * (size_t)n_adc;
+    const bool host_sig = n_adc > 0 && !on_device(signal_out);
+    double *sig = signal_out;
+    if (host_sig) {  // the context's signal scratch
+        if (sig_bytes > ctx->sig_cap * sizeof(double)) {
+            cudaFree(ctx->d_sig);
+            ctx->d_sig = nullptr;
+            ctx->sig_cap = 0;
+            cudaError_t e = ctx_malloc(ctx, &ctx->d_sig, sig_bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return ffail(ctx, MRSIM_ENOMEM, "signal scratch");
+            }
+            ctx->sig_cap = 2 * (size_t)n_adc;
+        }
+        sig = ctx->d_sig;
+    }
     cudaError_t e = cudaSuccess;
-    const double *dir = host_dir ? reinterpret_cast<const double *>(blk + dir_off) : b0_dir;
-    double *sig = host_sig ? reinterpret_cast<double *>(blk + sig_off) : signal_out;
-    if (rec_bytes) e = cudaMemcpyAsync(blk, f64 ? (const void *)e64.data() : (const void *)e32.data(), rec_bytes,
-                                       cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && host_dir) e = cudaMemcpyAsync((void *)dir, b0_dir, dir_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && n_adc > 0) e = cudaMemsetAsync(sig, 0, sig_bytes, st);
-    if (e == cudaSuccess && ph->n > 0) {  // directions: finite unit vectors
-        e = cudaMemsetAsync(ctx->d_bad, 0x7f, sizeof(int), st);
-        if (e == cudaSuccess) {
-            check_dirs_kernel<<<(int)std::min<int64_t>((ph->n + 255) / 256, 4096), 256, 0, st>>>(ph->n, dir, ctx->d_bad);
-            e = cudaGetLastError();
-        }
-        int bad = 0x7f7f7f7f;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess && bad != 0x7f7f7f7f)
-            rs = ffail(ctx, MRSIM_EINVAL, "b0_dir of spin " + std::to_string(bad) + " is not a finite unit vector");
-    }
-    if (e == cudaSuccess && rs == MRSIM_OK && ph->n > 0 && n_events > 0) {
+    if (n_adc > 0) e = cudaMemsetAsync(sig, 0, sig_bytes, st);
+    if (e == cudaSuccess && ph->n > 0 && f->n_events > 0) {
         FieldArgs a{};
-        a.ev = blk;
-        a.n_events = n_events;
+        a.ev = f64 ? (const void *)f->d_rec : (const void *)(f->d_rec + f->off32);
+        a.n_events = f->n_events;
         a.params = ph->params;
         a.n_spins = ph->n;
         a.n_pad = ph->n_pad;
-        a.ndir = dir;
-        a.b0 = b0_tesla;
+        a.ndir = ph->d_dir;
+        a.b0 = f->b0;
         a.signal = sig;
         const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
         if (f64) fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
         else fields_kernel_f32<<<grid, FIELD_THREADS, 0, st>>>(a);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && rs == MRSIM_OK && host_sig) e = cudaMemcpyAsync(signal_out, sig, sig_bytes, cudaMemcpyDeviceToHost, st);
-    // the records are freed below: the launch must be done with them
-    const cudaError_t es = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = es;
-    cudaFree(blk);
-    if (rs != MRSIM_OK) return rs;
+    if (e == cudaSuccess && host_sig) {
+        e = cudaMemcpyAsync(signal_out, sig, sig_bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) return ffail(ctx, MRSIM_ECUDA, std::string("fields simulation: ") + cudaGetErrorString(e));
     return MRSIM_OK;
 }
+
+}  // extern "C"

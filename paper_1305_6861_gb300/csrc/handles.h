@@ -54,6 +54,7 @@ struct mrsim_phantom {
     mrsim_ctx *ctx = nullptr;
     int64_t n = 0, n_pad = 0;
     double *params = nullptr;
+    double *d_dir = nullptr;  // static-field direction per spin (3 each), NULL = along z
 };
 
 namespace mrsim {

@@ -43,7 +43,8 @@ EXPORTS = (
     "mrsim_adjoint_destroy", "mrsim_compile", "mrsim_compile_last_error", "mrsim_compiled_num_adc",
     "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
     "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate", "mrsim_simulate_adjoint",
-    "mrsim_sequence_num_pulses", "mrsim_simulate_fields",
+    "mrsim_sequence_num_pulses", "mrsim_simulate_fields", "mrsim_phantom_set_b0_direction", "mrsim_fields_create",
+    "mrsim_fields_num_adc", "mrsim_fields_destroy",
 )
 
 
@@ -135,7 +136,11 @@ def lib():
             "mrsim_adjoint_destroy": (None, [vp]),
             "mrsim_simulate_adjoint": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, i32, vp, vp, vp, vp, vp, vp]),
             "mrsim_sequence_num_pulses": (i64, [vp]),
-            "mrsim_simulate_fields": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, dbl, dbl, ctypes.c_int, vp, vp, i64]),
+            "mrsim_simulate_fields": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
+            "mrsim_phantom_set_b0_direction": (ctypes.c_int, [vp, vp, vp]),
+            "mrsim_fields_create": (ctypes.c_int, [vp, i64, vp, vp, dbl, dbl, P(vp)]),
+            "mrsim_fields_num_adc": (i64, [vp]),
+            "mrsim_fields_destroy": (None, [vp]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
             "mrsim_compile": (ctypes.c_int, [i64, vp, dbl, i64, vp, P(vp)]),
             "mrsim_compile_last_error": (ctypes.c_char_p, []),
@@ -520,23 +525,50 @@ def simulate_adjoint(ctx: Context, phantom: Phantom, seq: Sequence, dl_dsignal, 
     return tuple(outs)
 
 
-def simulate_fields(ctx: Context, phantom: Phantom, events, gamma_hz_per_t: float, b0_dir, g_transverse=None,
-                    b0_tesla: float = 1.5, precision: int = FP32, stream=None, out=None):
-    """Non-parallel fields (mrsim_simulate_fields): b0_dir [n_spins, 3] unit vectors (numpy, or a
-    CUDA buffer of 3*n_spins float64), g_transverse None or [n_events, 6] (gtx, gty) [T/m].
-    Returns (or fills) the signal: numpy complex128[n_adc] or a CUDA buffer of 2*n_adc float64."""
-    ev = np.ascontiguousarray(events)
-    if ev.dtype != EVENT_DTYPE:
-        ev = ev.astype(EVENT_DTYPE)
+def set_b0_direction(ctx: Context, phantom: Phantom, b0_dir, stream=None):
+    """Static-field direction per spin (mrsim_phantom_set_b0_direction): [n_spins, 3] unit vectors,
+    numpy or a CUDA buffer of 3*n_spins float64."""
     if isinstance(b0_dir, np.ndarray):
         b0_dir = np.ascontiguousarray(b0_dir, dtype=np.float64).reshape(-1)
-    gt = None if g_transverse is None else np.ascontiguousarray(g_transverse, dtype=np.float64).reshape(-1)
-    n_adc = int(np.count_nonzero(ev["adc"]))
+    ctx.check(lib().mrsim_phantom_set_b0_direction(phantom.h, _ptr(b0_dir), _stream(stream)))
+
+
+class Fields:
+    """An event list prepared for non-parallel fields (mrsim_fields_create): g_transverse None or
+    [n_events, 6] (gtx, gty) [T/m], b0_tesla the main field."""
+
+    def __init__(self, ctx: Context, events, gamma_hz_per_t: float, g_transverse=None, b0_tesla: float = 1.5):
+        self.ctx = ctx
+        ev = np.ascontiguousarray(events)
+        if ev.dtype != EVENT_DTYPE:
+            ev = ev.astype(EVENT_DTYPE)
+        gt = None if g_transverse is None else np.ascontiguousarray(g_transverse, dtype=np.float64).reshape(-1)
+        h = ctypes.c_void_p()
+        ctx.check(lib().mrsim_fields_create(ctx.h, ev.shape[0], _ptr(ev), _ptr(gt), float(gamma_hz_per_t),
+                                            float(b0_tesla), ctypes.byref(h)))
+        self.h = h
+        self.n_adc = int(lib().mrsim_fields_num_adc(h))
+        self.n_events = int(ev.shape[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrsim_fields_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate_fields(ctx: Context, phantom: Phantom, fields: Fields, precision: int = FP32, stream=None, out=None):
+    """Forward simulation with non-parallel fields (mrsim_simulate_fields).  Returns (or fills) the
+    signal: numpy complex128[n_adc] or a CUDA buffer of 2*n_adc float64 (asynchronous)."""
     if out is None:
-        out = np.zeros(n_adc, dtype=np.complex128)
-    ctx.check(lib().mrsim_simulate_fields(ctx.h, phantom.h, _ptr(b0_dir), ev.shape[0], _ptr(ev), _ptr(gt),
-                                          float(gamma_hz_per_t), float(b0_tesla), int(precision), _stream(stream),
-                                          _ptr(out), n_adc))
+        out = np.zeros(fields.n_adc, dtype=np.complex128)
+    ctx.check(lib().mrsim_simulate_fields(ctx.h, phantom.h, fields.h, int(precision), _stream(stream), _ptr(out),
+                                          fields.n_adc))
     return out
 
 

@@ -517,6 +517,60 @@ def config2_legendre(seed=None, n: int = 256, iso: int = 4, c_tesla: float = 20e
                     f"Eq. 6.3 inhomogeneity C = {c_tesla * 1e6:g} uT, R = {radius:g} m, plus fat shift")
 
 
+def concomitant_transverse(events) -> np.ndarray:
+    """Transverse components of the gradient field that Maxwell's equations require beside an
+    ideal z-field (G.x) e_z (§3.4.3.2 names them concomitant gradients): the curl- and
+    divergence-free completion B = (-Gz x/2 + Gx z, -Gz y/2 + Gy z, G.x), i.e. per event
+    gtx = (-Gz/2, 0, Gx) and gty = (0, -Gz/2, Gy) [T/m], as [n_events, 6]."""
+    ev = events
+    gt = np.zeros((len(ev), 6))
+    gt[:, 0] = -0.5 * ev["gz"]
+    gt[:, 2] = ev["gx"]
+    gt[:, 4] = -0.5 * ev["gz"]
+    gt[:, 5] = ev["gy"]
+    return gt
+
+
+def tilted_field_directions(ph: Phantom, max_tilt: float, rng: np.random.Generator) -> np.ndarray:
+    """Unit static-field directions per spin (§3.2): a seeded smooth tilt, polar angle linear in
+    position up to max_tilt at the edge of a 0.5 m field of view, azimuth a seeded linear field;
+    [n_spins, 3]."""
+    c = rng.uniform(-1, 1, 6)
+    tilt = max_tilt * np.clip(np.abs(c[0] * ph.x + c[1] * ph.y + c[2] * ph.z) / (0.25 * np.abs(c[:3]).sum()), 0, 1)
+    az = math.pi * (c[3] * ph.x + c[4] * ph.y + c[5] * ph.z) / 0.25
+    return np.stack([np.sin(tilt) * np.cos(az), np.sin(tilt) * np.sin(az), np.cos(tilt)], axis=1)
+
+
+@dataclasses.dataclass
+class FieldWorkload:
+    name: str
+    phantom: Phantom
+    sequence: Sequence
+    b0_dir: np.ndarray       # [n_spins, 3]
+    g_transverse: np.ndarray  # [n_events, 6]
+    b0_tesla: float
+
+    @property
+    def spin_steps(self) -> int:
+        return self.phantom.n * self.sequence.n_events
+
+
+def config_fields(seed=None, base: str = "c1", b0_tesla: float | None = None,
+                  max_tilt: float = math.radians(10.0)) -> FieldWorkload:
+    """Non-parallel fields: a static field whose direction tilts smoothly by up to 10° across the
+    object, and the Maxwell concomitant components of every gradient, on
+      base "c1": the 64² FLASH at a low main field (0.05 T, where concomitant fields matter), or
+      base "c2": the 256² spin echo with B0 polynomial and fat at 1.5 T (the field its fat shift
+                 belongs to)."""
+    w = {"c1": config1, "c2": config2}[base](seed)
+    b0 = b0_tesla if b0_tesla is not None else {"c1": 0.05, "c2": 1.5}[base]
+    rng = rng_for(7, seed)
+    nd = tilted_field_directions(w.phantom, max_tilt, rng)
+    stem = {"c1": "flash2d_64", "c2": "se2d_256"}[base]
+    return FieldWorkload(f"fields_{stem}_b0_{b0:g}T", w.phantom, w.sequence, nd,
+                         concomitant_transverse(w.sequence.events), b0)
+
+
 def config3(seed=None, n: int = 128, iso: int = 2) -> Workload:
     """3D n³ RF-spoiled GRE, 2 iso/voxel, 10°, TR 8 ms, TE 4 ms, dwell 10 µs."""
     rng = rng_for(3, seed)

@@ -81,8 +81,10 @@ def test_fields_match_oracle(M, ctx, oracle_mod, seed, n_spins, n_events, max_ti
     nd = directions(rng, n_spins, max_tilt)
     ref, _ = oracle_mod.simulate_fields(ph, ev, W.GAMMA_BAR, nd, gt, b0)
     p = M.Phantom.from_workload_phantom(ctx, ph)
-    got64 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, b0, M.FP64)
-    got32 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, b0, M.FP32)
+    M.set_b0_direction(ctx, p, nd)
+    f = M.Fields(ctx, ev, W.GAMMA_BAR, gt, b0)
+    got64 = M.simulate_fields(ctx, p, f, M.FP64)
+    got32 = M.simulate_fields(ctx, p, f, M.FP32)
     ctx.stream_status()
     assert rel_l2(got64, ref) <= phase_floor(ph, ev, gt, b0)
     assert rel_l2(got32, ref) <= TOL32
@@ -98,8 +100,9 @@ def test_fields_parallel_case_is_the_standard_path(M, ctx, oracle_mod):
     p = M.Phantom.from_workload_phantom(ctx, w.phantom)
     s = M.Sequence.from_workload_sequence(ctx, w.sequence)
     std = M.simulate(ctx, p, s, M.FP64)
-    got64 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, None, 1.5, M.FP64)
-    got32 = M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, np.zeros((len(ev), 6)), 1.5, M.FP32)
+    got64 = M.simulate_fields(ctx, p, M.Fields(ctx, ev, W.GAMMA_BAR, None, 1.5), M.FP64)  # no directions: z
+    M.set_b0_direction(ctx, p, nd)
+    got32 = M.simulate_fields(ctx, p, M.Fields(ctx, ev, W.GAMMA_BAR, np.zeros((len(ev), 6)), 1.5), M.FP32)
     assert rel_l2(got64, ref) <= TOL64 and rel_l2(got64, std) <= TOL64
     assert rel_l2(got32, ref) <= TOL32
 
@@ -113,8 +116,13 @@ def test_fields_device_buffers(M, ctx, oracle_mod):
     p = M.Phantom.from_workload_phantom(ctx, ph)
     dev = torch.device("cuda:0")
     ndd = torch.from_numpy(nd.reshape(-1).copy()).to(dev)
-    out = torch.zeros(2 * int(np.count_nonzero(ev["adc"])), dtype=torch.float64, device=dev)
-    M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, ndd, gt, 0.5, M.FP64, out=out)
+    M.set_b0_direction(ctx, p, ndd)
+    f = M.Fields(ctx, ev, W.GAMMA_BAR, gt, 0.5)
+    out = torch.zeros(2 * f.n_adc, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream()
+    M.simulate_fields(ctx, p, f, M.FP64, stream=s, out=out)  # asynchronous on s
+    s.synchronize()
+    ctx.stream_status(s)
     assert rel_l2(out.cpu().numpy().view(np.complex128), ref) <= phase_floor(ph, ev, gt, 0.5)
 
 
@@ -123,25 +131,47 @@ def test_fields_edge_cases_and_invalid_inputs(M, ctx, oracle_mod):
     ph, ev, gt = case(rng, 50, 100)
     nd = directions(rng, ph.n, 1.0)
     p = M.Phantom.from_workload_phantom(ctx, ph)
+    M.set_b0_direction(ctx, p, nd)
+    f = M.Fields(ctx, ev, W.GAMMA_BAR, gt, 1.5)
     # no spins: zero signal; no events: empty signal
     p0 = M.Phantom.from_workload_phantom(ctx, W.random_phantom(0, rng))
+    M.set_b0_direction(ctx, p0, np.zeros((0, 3)))
+    f0 = M.Fields(ctx, ev[:0], W.GAMMA_BAR, None, 1.5)
     for prec in (M.FP64, M.FP32):
-        z = M.simulate_fields(ctx, p0, ev, W.GAMMA_BAR, np.zeros((0, 3)), gt, 1.5, prec)
-        assert z.shape == (int(np.count_nonzero(ev["adc"])),) and not np.any(z)
-        assert M.simulate_fields(ctx, p, ev[:0], W.GAMMA_BAR, nd, None, 1.5, prec).shape == (0,)
+        z = M.simulate_fields(ctx, p0, f, prec)
+        assert z.shape == (f.n_adc,) and not np.any(z)
+        assert M.simulate_fields(ctx, p, f0, prec).shape == (0,)
     bad = nd.copy()
     bad[7] *= 1.01  # not a unit vector
     with pytest.raises(M.MrsimError) as e:
-        M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, bad, gt, 1.5, M.FP32)
+        M.set_b0_direction(ctx, p, bad)
     assert e.value.status == M.Status.EINVAL and "spin 7" in str(e.value)
     for b0 in (0.0, -1.0, float("nan")):
         with pytest.raises(M.MrsimError) as e:
-            M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, b0, M.FP64)
+            M.Fields(ctx, ev, W.GAMMA_BAR, gt, b0)
         assert e.value.status == M.Status.EINVAL
     g_bad = gt.copy()
     g_bad[3, 2] = np.inf
     with pytest.raises(M.MrsimError):
-        M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, g_bad, 1.5, M.FP64)
-    # the context stays usable
+        M.Fields(ctx, ev, W.GAMMA_BAR, g_bad, 1.5)
+    out = np.zeros(f.n_adc + 1, dtype=complex)
+    import ctypes
+
+    rc = M.lib().mrsim_simulate_fields(ctx.h, p.h, f.h, M.FP64, None, ctypes.c_void_p(out.ctypes.data), f.n_adc + 1)
+    assert rc == M.Status.EINVAL
+    # the failed direction update kept the earlier directions; the context stays usable
     ref, _ = oracle_mod.simulate_fields(ph, ev, W.GAMMA_BAR, nd, gt, 1.5)
-    assert rel_l2(M.simulate_fields(ctx, p, ev, W.GAMMA_BAR, nd, gt, 1.5, M.FP64), ref) <= phase_floor(ph, ev, gt, 1.5)
+    assert rel_l2(M.simulate_fields(ctx, p, f, M.FP64), ref) <= phase_floor(ph, ev, gt, 1.5)
+
+
+def test_fields_workload_c1_low_field(M, ctx, oracle_mod):
+    """The 64² FLASH at 0.05 T with a 10° smooth tilt and Maxwell concomitant fields, every spin,
+    both precisions."""
+    w = W.config_fields()
+    ref, _ = oracle_mod.simulate_fields(w.phantom, w.sequence.events, W.GAMMA_BAR, w.b0_dir, w.g_transverse,
+                                        w.b0_tesla)
+    p = M.Phantom.from_workload_phantom(ctx, w.phantom)
+    M.set_b0_direction(ctx, p, w.b0_dir)
+    f = M.Fields(ctx, w.sequence.events, W.GAMMA_BAR, w.g_transverse, w.b0_tesla)
+    assert rel_l2(M.simulate_fields(ctx, p, f, M.FP64), ref) <= TOL64
+    assert rel_l2(M.simulate_fields(ctx, p, f, M.FP32), ref) <= TOL32

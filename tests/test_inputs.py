@@ -72,3 +72,24 @@ def test_legendre_workload(oracle_mod):
     assert np.allclose(ph.dw[~water] - 2 * math.pi * W.GAMMA_BAR * b0[~water], 2 * math.pi * W.FAT_SHIFT_HZ,
                        rtol=1e-12, atol=1e-9)
     assert np.max(np.abs(b0)) > 1e-6  # the corners of the 0.5 m field of view leave the sphere
+
+
+def test_concomitant_components_satisfy_maxwell():
+    """The transverse completion of an ideal z-gradient field is divergence- and curl-free: the
+    field's Jacobian (rows gtx, gty, G) is traceless and symmetric."""
+    rng = np.random.default_rng(5)
+    ev = W.make_events([(1e-3, *rng.normal(size=3), 0.0, 0.0, 0, 0.0) for _ in range(20)])
+    gt = W.concomitant_transverse(ev)
+    for e, g in zip(ev, gt):
+        J = np.array([g[:3], g[3:], [e["gx"], e["gy"], e["gz"]]])
+        assert abs(np.trace(J)) < 1e-15
+        assert np.allclose(J, J.T, atol=0)
+
+
+def test_field_workload_directions():
+    w = W.config_fields()
+    assert w.b0_dir.shape == (w.phantom.n, 3)
+    assert np.allclose(np.linalg.norm(w.b0_dir, axis=1), 1.0, atol=1e-15)
+    tilt = np.arccos(np.clip(w.b0_dir[:, 2], -1, 1))
+    assert tilt.max() <= math.radians(10.0) + 1e-12 and tilt.max() > math.radians(5.0)
+    assert w.g_transverse.shape == (w.sequence.n_events, 6)
