@@ -698,6 +698,118 @@ def run_kt(args):
     return 0
 
 
+# Non-parallel fields: FP32 lane-operations of the formulation per spin and event.  An event with
+# a duration: the gradient field G.x (3), n.b (3), b - (n.b) n (3) and its square (3), u = B0 n + b
+# (3), |u|^2 (3), the remainder r^2/(|u| + B0 + n.b) (2), h = u/|u| (3), the phase from four
+# float-float products (6 each) and its reduction (3), the turn about h with T2 and T1 (the part
+# along h 3, across it 3, h x M (6), the new state 9, the T1 term 2); with transverse components 6
+# more for (gtx.x, gty.x) and six more products (36).  A pulse is the 3x3 rotation (9), a sample
+# the demodulated value (4).  Transcendentals (sin/cos, exp, sqrt, division) are not counted.
+FIELD_OPS_FREE, FIELD_OPS_TRANSVERSE, FIELD_OPS_RF, FIELD_OPS_ADC = 73, 42, 9, 4
+
+
+def field_ops_per_spin(events, g_transverse) -> int:
+    free = events["dt"] > 0
+    tr = np.any(g_transverse != 0, axis=1) if g_transverse is not None else np.zeros(len(events), dtype=bool)
+    return int(FIELD_OPS_FREE * np.count_nonzero(free) + FIELD_OPS_TRANSVERSE * np.count_nonzero(free & tr)
+               + FIELD_OPS_RF * np.count_nonzero(events["rf_flip"] != 0) + FIELD_OPS_ADC * np.count_nonzero(events["adc"]))
+
+
+def run_fields(args):
+    """Non-parallel fields (static-field direction per spin, Maxwell concomitant gradient
+    components): the 256² spin echo with a 10° smooth tilt at 1.5 T.  One step = one forward
+    simulation of the whole phantom through mrsim_simulate_fields."""
+    import torch
+
+    from paper_1305_6861_gb300 import mrsim as M
+
+    torch.cuda.set_device(0)
+    w = W.config_fields(base="c2")
+    prec = M.FP64 if args.precision == "fp64" else M.FP32
+    ctx = M.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    measure_device(ctx, M, 0, stream)
+    P = M.Phantom(ctx, [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()], stream=stream)
+    M.set_b0_direction(ctx, P, torch.from_numpy(w.b0_dir.reshape(-1).copy()).to(dev), stream=stream)
+    F = M.Fields(ctx, w.sequence.events, W.GAMMA_BAR, w.g_transverse, w.b0_tesla)
+    sig = torch.zeros(2 * F.n_adc, dtype=torch.float64, device=dev)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        M.simulate_fields(ctx, P, F, prec, stream=stream, out=sig)
+    ctx.stream_status(stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.15)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush_buf.zero_()
+        evs[i][0].record(stream)
+        M.simulate_fields(ctx, P, F, prec, stream=stream, out=sig)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ctx.stream_status(stream)
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ops = field_ops_per_spin(w.sequence.events, w.g_transverse) * w.phantom.n
+    achieved = ops / (ms * 1e-3) / 1e9
+    line = {"metric": "spin-steps/s of the non-parallel-field simulation at 1 GB300", "value": w.spin_steps / (ms * 1e-3),
+            "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": w.sequence.n_events, "n_adc": F.n_adc,
+                       "b0_tesla": w.b0_tesla, "max_tilt_deg": 10.0, "transverse": "Maxwell concomitant components",
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)"},
+            "roofline": dict(fp64_roofline(achieved), kernel_ms=ms, ops_per_spin_step=ops / w.spin_steps)
+            if prec == M.FP64 else fp32_roofline(achieved, ck, traffic=None, kernel_ms=ms,
+                                                  ops_per_spin_step=ops / w.spin_steps,
+                                                  op_model="formulation arithmetic per event, transcendentals not counted"),
+            "gpu_launches": args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id()}
+    if not args.no_cpu_baseline:  # the oracle on a bounded spin sample, and the GPU on the same spins
+        cb = cpu_baseline_fields(w, args.cpu_seconds)
+        line["cpu_baseline"] = cb["baseline"]
+        sub = cb["sample"]
+        ps = M.Phantom.from_workload_phantom(ctx, w.phantom.subset(sub))
+        M.set_b0_direction(ctx, ps, w.b0_dir[sub])
+        par = {"sample_spins": int(sub.size)}
+        nr = float(np.linalg.norm(cb["ref"]))
+        for name, pr in (("fp32", M.FP32), ("fp64", M.FP64)):
+            got = M.simulate_fields(ctx, ps, F, pr)
+            rel = float(np.linalg.norm(got - cb["ref"]) / nr)
+            par[f"{name}_rel_l2"] = rel
+            par[f"{name}_db"] = 20 * math.log10(rel) if rel > 0 else None
+        line["oracle_parity"] = par
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_fields(w, seconds: float = 10.0, seed: int = 3):
+    """CPU-baseline leg of the field workload: the oracle, as it stands, on a bounded spin sample
+    (full sequence)."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(seed)
+    pool = np.nonzero(w.phantom.rho > 0)[0]
+
+    def timed(idx):
+        t0 = time.perf_counter()
+        ref, _ = oracle.simulate_fields(w.phantom.subset(idx), w.sequence.events, W.GAMMA_BAR, w.b0_dir[idx],
+                                        w.g_transverse, w.b0_tesla, n_threads=cores)
+        return ref, time.perf_counter() - t0
+
+    cal = np.sort(rng.choice(pool, min(cores * 4, pool.size), replace=False))
+    _, dt = timed(cal)
+    n = int(max(cores, min(pool.size, seconds / max(dt / cal.size, 1e-9))))
+    idx = np.sort(rng.choice(pool, n, replace=False))
+    ref, el = timed(idx)
+    return {"baseline": {"value": n * w.sequence.n_events / el, "unit": "spin-steps/s", "cores": cores,
+                         "kind": "oracle", "sample": f"{w.name}: full sequence ({w.sequence.n_events} events) on "
+                                                     f"{n} of {w.phantom.n} spins, {el:.1f} s"},
+            "sample": idx, "ref": ref}
+
+
 def run_ours(args):
     import torch
 
@@ -709,6 +821,8 @@ def run_ours(args):
         return run_adjoint(args)
     if args.workload == "kt":
         return run_kt(args)
+    if args.workload == "fields":
+        return run_fields(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -961,7 +1075,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "kt"], default="c3")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "kt", "fields"], default="c3")
     ap.add_argument("--kt-sets", type=int, default=65536, help="ensembles of the K-t workload")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--spins-per-thread", type=int, default=0)

@@ -40,15 +40,21 @@ constexpr int FIELD_THREADS = 128;
 constexpr int FIELD_CHUNK = 32;
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
-enum FieldFlags : int32_t { FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8 };
+// FF_RUN_START: the first event of a run of identical free intervals (same Δt, G, transverse
+// components, no pulse): its state before the step is kept; FF_RUN: a later event of the run,
+// whose record holds the run's interval so far (j·Δt and its moments), applied to the kept state.
+// The turn and the relaxation of j equal intervals are one turn by jθ with E^j (the axis h is the
+// same for all of them), so a run is computed from its start instead of step by step and the
+// rounding of one interval's rotation does not repeat j times.
+enum FieldFlags : int32_t { FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8, FF_RUN_START = 16, FF_RUN = 32 };
 
 // float64 record: 22 doubles + 4 ints = 192 bytes
 struct alignas(16) FieldEv64 {
     double R[9];        // Eq. 3.19 rotation (row-major) when FF_RF
     double g[3];        // G [T/m]: field along z, G.x
     double gt[6];       // transverse components [T/m]: Bx = gt[0..2].x, By = gt[3..5].x
-    double gdt;         // γ Δt [rad/(T)]
-    double dt;          // Δt [s]
+    double gdt;         // γ Δt [rad/(T)]  (in a run: of the run's interval so far)
+    double dt;          // Δt [s]          (likewise)
     double dem[2];      // cos, sin of the receiver phase
     int32_t flags, adc, slot, pad;
 };
@@ -151,6 +157,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
     const double n2 = a.ndir ? a.ndir[3 * si + 2] : 1.0;
     const double b0 = a.b0;
     double M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
+    double S0 = M0, S1 = M1, S2 = M2;  // state at the start of the current run
     const FieldEv64 *src = static_cast<const FieldEv64 *>(a.ev);
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
@@ -165,6 +172,15 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
                 M0 = t0;
                 M1 = t1;
                 M2 = t2;
+            }
+            if (e.flags & FF_RUN_START) {
+                S0 = M0;
+                S1 = M1;
+                S2 = M2;
+            } else if (e.flags & FF_RUN) {
+                M0 = S0;
+                M1 = S1;
+                M2 = S2;
             }
             if (e.flags & FF_FREE) {
                 double bx = 0.0, by = 0.0;
@@ -233,6 +249,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) 
     const float r1 = (float)a.params[P_R1 * np + si], r2 = (float)a.params[P_R2 * np + si];
     const float b0 = (float)a.b0;
     float M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
+    float S0 = M0, S1 = M1, S2 = M2;  // state at the start of the current run
     const FieldEv32 *src = static_cast<const FieldEv32 *>(a.ev);
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
@@ -247,6 +264,15 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) 
                 M0 = t0;
                 M1 = t1;
                 M2 = t2;
+            }
+            if (e.flags & FF_RUN_START) {
+                S0 = M0;
+                S1 = M1;
+                S2 = M2;
+            } else if (e.flags & FF_RUN) {
+                M0 = S0;
+                M1 = S1;
+                M2 = S2;
             }
             if (e.flags & FF_FREE) {
                 float bx = 0.0f, by = 0.0f;
@@ -417,15 +443,28 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     } catch (const std::bad_alloc &) {
         return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
     }
-    int64_t j = 0;
+    int64_t j = 0, run = 0;  // run: index of the event within its run of identical free intervals (0: none)
     int slot = 0;
+    static const double zero6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int64_t i = 0; i < n_events; ++i) {
         if (i % FIELD_CHUNK == 0) slot = 0;
         const mrsim_event &v = events[i];
         const double *gt = g_transverse ? g_transverse + 6 * i : nullptr;
         const bool tr = gt && (gt[0] != 0.0 || gt[1] != 0.0 || gt[2] != 0.0 || gt[3] != 0.0 || gt[4] != 0.0 || gt[5] != 0.0);
+        if (v.rf_flip != 0.0 || !(v.dt > 0.0)) {
+            run = 0;
+        } else if (run > 0) {
+            const mrsim_event &u = events[i - 1];
+            const double *gp = g_transverse ? g_transverse + 6 * (i - 1) : zero6, *gc = gt ? gt : zero6;
+            bool same = u.dt == v.dt && u.gx == v.gx && u.gy == v.gy && u.gz == v.gz;
+            for (int q = 0; q < 6 && same; ++q) same = gp[q] == gc[q];
+            run = same ? run + 1 : 1;
+        } else {
+            run = 1;
+        }
+        const double span = v.dt * (double)std::max<int64_t>(run, 1);  // the run's interval so far
         const int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
-                              (v.dt > 0.0 ? FF_FREE : 0);
+                              (v.dt > 0.0 ? FF_FREE : 0) | (run == 1 ? FF_RUN_START : 0) | (run > 1 ? FF_RUN : 0);
         double R[9];
         rf_matrix(v.rf_flip, v.rf_phase, R);
         const double g[3] = {v.gx, v.gy, v.gz};
@@ -446,15 +485,15 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
             f.gt[q] = (float)r.gt[q];
         }
         for (int d = 0; d < 3; ++d) {
-            split(gamma_hz_per_t * g[d] * v.dt, f.kh[d], f.kl[d]);
-            split(gamma_hz_per_t * r.gt[d] * v.dt, f.kh[3 + d], f.kl[3 + d]);
-            split(gamma_hz_per_t * r.gt[3 + d] * v.dt, f.kh[6 + d], f.kl[6 + d]);
+            split(gamma_hz_per_t * g[d] * span, f.kh[d], f.kl[d]);
+            split(gamma_hz_per_t * r.gt[d] * span, f.kh[3 + d], f.kl[3 + d]);
+            split(gamma_hz_per_t * r.gt[3 + d] * span, f.kh[6 + d], f.kl[6 + d]);
         }
-        r.gdt = gamma * v.dt;
-        r.dt = v.dt;
-        split(v.dt, f.dth, f.dtl);
-        f.gdt2pi = (float)(gamma_hz_per_t * v.dt);
-        f.dt = (float)v.dt;
+        r.gdt = gamma * span;
+        r.dt = span;
+        split(span, f.dth, f.dtl);
+        f.gdt2pi = (float)(gamma_hz_per_t * span);
+        f.dt = (float)span;
         r.dem[0] = dem[0];
         r.dem[1] = dem[1];
         f.dem[0] = (float)dem[0];

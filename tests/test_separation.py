@@ -59,7 +59,7 @@ def test_oracle_users_outside_tests():
     """__graft_entry__ loads it in build() (to compile it) and smoke(); bench.py only inside its
     CPU-baseline legs (the timed sample, the oracle-parity sample) and reference-arm code."""
     allowed = {"__graft_entry__.py": {"build", "smoke"},
-               "bench.py": {"cpu_baseline", "cpu_baseline_parity_run", "run_adjoint", "run_kt"}}
+               "bench.py": {"cpu_baseline", "cpu_baseline_parity_run", "cpu_baseline_fields", "run_adjoint", "run_kt"}}
     for name, funcs in allowed.items():
         tree = ast.parse(open(os.path.join(ROOT, name), encoding="utf-8").read())
         users = set()
