@@ -503,6 +503,48 @@ def run_batch(args):
                                "frac": form_g / (fp32_alu_peak_ops(sm_clock(ck)) / 1e9)}),
         "gpu_launches": 2 * args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id(),
     }
+    if prec == M.FP32 and not args.skip_extra:
+        # the float64 and the compensated (double-float) batch on the same phantoms: their times,
+        # and every phantom's float32 and compensated signal against the float64 one
+        s32 = [o.clone() for o in outs]
+
+        def other(pr, tune):
+            o2 = [torch.zeros_like(o) for o in outs]
+            b2 = M.Batch(ctx, phs, sqs, pr, o2)
+            sh = b2.autotune(stream=stream) if tune else None
+            b2.launch(stream=stream, graph=True)  # capture + first run
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b2.launch(stream=stream, graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.stream_status(stream)
+            t = e0.elapsed_time(e1)
+            b2.close()
+            return o2, t, sh
+
+        s64, ms64, _ = other(M.FP64, False)
+        sk, msk, shk = other(M.FP32_KAHAN, True)
+
+        def per_phantom(got):
+            errs = []
+            for w, g, r in zip(ws, got, s64):
+                a, b_ = g.cpu().numpy(), r.cpu().numpy()
+                nb = float(np.linalg.norm(b_))
+                errs.append((float(np.linalg.norm(a - b_) / nb) if nb > 0 else 0.0, w.name, w.sequence.name))
+            errs.sort(reverse=True)
+            return {"max": errs[0][0], "n_above_2e-5": sum(e > 2e-5 for e, _, _ in errs),
+                    "max_flash": max((e for e, _, q in errs if q.startswith("flash")), default=0.0),
+                    "max_spin_echo": max((e for e, _, q in errs if q.startswith("se")), default=0.0),
+                    "worst": [[n, q, e] for e, n, q in errs[:6]]}
+
+        line["fp64_gpu"] = {"value": spin_steps / (ms64 * 1e-3), "unit": "spin-steps/s", "ms_per_step": ms64,
+                            "roofline": fp64_roofline(ops / (ms64 * 1e-3) / 1e9)}
+        line["fp32_kahan_gpu"] = {"value": spin_steps / (msk * 1e-3), "unit": "spin-steps/s", "ms_per_step": msk,
+                                  "launch": {"spins_per_thread": shk[0], "threads_per_block": shk[1]},
+                                  "arithmetic": "double-float (float32 pairs with their rounding error) on the FP32 pipe"}
+        line["per_phantom_vs_fp64_gpu"] = {"fp32": per_phantom(s32), "fp32_kahan": per_phantom(sk)}
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample of the batch's longest program
         wl = max(ws, key=lambda w: w.sequence.n_events)
         cb, (sub, ref) = cpu_baseline(wl, seconds=args.cpu_seconds)
@@ -982,6 +1024,25 @@ def run_ours(args):
             out[key]["roofline"] = fp64_roofline(ops / (o_ms * 1e-3) / 1e9)
         out["fp32_vs_fp64_gpu_rel_l2"] = rel
         out["fp32_vs_fp64_gpu_db"] = 20 * math.log10(rel) if rel > 0 else None
+        if not args.no_kahan and prec == M.FP32:
+            # the compensated precision (double-float on the FP32 pipe): one timed run and its
+            # agreement with the float64 path
+            sk = torch.zeros_like(sig)
+            kk = M.autotune(ctx, ph, seq, M.FP32_KAHAN, stream=stream)
+            M.simulate(ctx, ph, seq, M.FP32_KAHAN, stream=stream, out=sk)  # warm-up
+            torch.cuda.synchronize()
+            e0.record(stream)
+            M.simulate(ctx, ph, seq, M.FP32_KAHAN, stream=stream, out=sk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.stream_status(stream)
+            k_ms = e0.elapsed_time(e1)
+            ak = sk.cpu().numpy().view(np.complex128)
+            rk = float(np.linalg.norm(ak - a64) / np.linalg.norm(a64))
+            out["fp32_kahan_gpu"] = {"value": spin_steps / (k_ms * 1e-3), "unit": "spin-steps/s", "ms_per_step": k_ms,
+                                     "launch": {"spins_per_thread": kk[0], "threads_per_block": kk[1]},
+                                     "rel_l2_vs_fp64_gpu": rk,
+                                     "arithmetic": "double-float (float32 pairs with their rounding error) on the FP32 pipe"}
         if orun is not None:
             out["oracle_parity"] = oracle_parity_sample(ctx, M, w, orun, seq, shape, stream)
 
@@ -1087,6 +1148,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--no-kahan", action="store_true", help="skip the compensated-precision leg")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--events", type=int, default=0, help="use only the first N events (profiling cases)")
     ap.add_argument("--coils", type=int, default=0, help="receive coils (ring sensitivities), 0 = plain signal")

@@ -60,8 +60,9 @@ struct Layout {
     int per_sm = 0;
 };
 
-mrsim_status lay_out(mrsim_ctx *ctx, int n, const mrsim_sequence *const *seqs, const FwdArgs *hd, bool fp64,
+mrsim_status lay_out(mrsim_ctx *ctx, int n, const mrsim_sequence *const *seqs, const FwdArgs *hd, int mode,
                      const Launch &L, Layout *out, std::string *msg) {
+    const bool fp64 = mode != MODE_F32;
     Layout y;
     y.items_off = (HEAD_BYTES + (size_t)n * sizeof(FwdArgs) + 255) / 256 * 256;
     BatchItem *hi = reinterpret_cast<BatchItem *>(h_stage + y.items_off);
@@ -92,7 +93,7 @@ mrsim_status lay_out(mrsim_ctx *ctx, int n, const mrsim_sequence *const *seqs, c
         *msg = "launch shape exceeds shared memory";
         return MRSIM_EUNSUPPORTED;
     }
-    y.per_sm = batch_blocks_per_sm(fp64, L.k, L.threads, y.smem);
+    y.per_sm = batch_blocks_per_sm(mode, L.k, L.threads, y.smem);
     if (y.per_sm <= 0) {
         *msg = "launch shape cannot be resident";
         return MRSIM_EUNSUPPORTED;
@@ -111,7 +112,8 @@ extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, c
     if (n < 0 || (n > 0 && (!phantoms || !seqs || !signals_out))) return bad(ctx, MRSIM_EINVAL, "invalid batch arrays");
     if (!normalize_precision(prec)) return bad(ctx, MRSIM_EINVAL, "unknown precision");
     if (ctx->device < 0 || ctx->device >= MAX_DEVICES) return bad(ctx, MRSIM_EUNSUPPORTED, "device ordinal too large");
-    const bool fp64 = prec == MRSIM_FP64;
+    const int mode = launch_mode(prec);
+    const bool fp64 = mode != MODE_F32;  // float64 program and layouts (float64, double-float)
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceScope scope(ctx->device);
     // set-up, once per device, with that device current: the device address of g_scratch
@@ -164,10 +166,10 @@ extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, c
     // (1 x 64, then 1 x 32) when it does not fit, as mrsim_batch_create does
     Layout y;
     std::string msg;
-    mrsim_status ls = lay_out(ctx, n, seqs, hd, fp64, L, &y, &msg);
+    mrsim_status ls = lay_out(ctx, n, seqs, hd, mode, L, &y, &msg);
     if (ls == MRSIM_EUNSUPPORTED && library_shape) {
         for (const Launch f : {Launch{1, 64}, Launch{1, 32}}) {
-            if ((ls = lay_out(ctx, n, seqs, hd, fp64, f, &y, &msg)) != MRSIM_EUNSUPPORTED) {
+            if ((ls = lay_out(ctx, n, seqs, hd, mode, f, &y, &msg)) != MRSIM_EUNSUPPORTED) {
                 L = f;
                 break;
             }
@@ -191,7 +193,7 @@ extern "C" mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, c
     a.n_items = (int32_t)n_items;
     a.head = reinterpret_cast<int *>(dev);
     const int grid = (int)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, (int64_t)n_items);
-    rc = launch_batch(fp64, a, L.k, L.threads, smem, grid, stream);
+    rc = launch_batch(mode, a, L.k, L.threads, smem, grid, stream);
     if (rc != 0) return bad(ctx, MRSIM_ECUDA, std::string("launch batch kernel: ") + cudaGetErrorString((cudaError_t)rc));
     return MRSIM_OK;
 }

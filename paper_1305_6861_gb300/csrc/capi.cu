@@ -507,7 +507,8 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
         return fail(ctx, MRSIM_EINVAL, "n_adc = " + std::to_string(n_adc) + " but the sequence has " +
                                            std::to_string(seq->prog->host.n_adc) + " samples");
     if (n_adc > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal_out");
-    const bool fp64 = prec == MRSIM_FP64;
+    const int mode = launch_mode(prec);
+    const bool fp64 = mode != MODE_F32;  // float64 program and layouts (float64, double-float)
     mrsim_options o{};
     if (opt) o = *opt;
     if ((o.flags & MRSIM_TUNE) && !o.spins_per_thread && !o.threads_per_block &&
@@ -572,7 +573,9 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     a.snap = snap_n > 0 ? dsnap : nullptr;
     a.signal = dsig;
     a.status = ctx->d_status;
-    int rc = fp64 ? launch_fwd_f64(a, L.k, L.threads, stream) : launch_fwd_f32(a, L.k, L.threads, stream);
+    int rc = mode == MODE_F64 ? launch_fwd_f64(a, L.k, L.threads, stream)
+             : mode == MODE_DF ? launch_fwd_df(a, L.k, L.threads, stream)
+                               : launch_fwd_f32(a, L.k, L.threads, stream);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel");
     if (host_out) CK(cudaMemcpyAsync(o.state_out, dout, st_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy state out");
     if (host_snap) CK(cudaMemcpyAsync(o.snapshots, dsnap, snap_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy snapshots");
@@ -588,7 +591,7 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !seq) return fail(ctx, MRSIM_EINVAL, "NULL phantom or sequence");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
-    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec, true)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_coils < 1 || n_coils > MAX_COILS)
         return fail(ctx, MRSIM_EINVAL, "n_coils must be 1.." + std::to_string(MAX_COILS));
     if (n_adc != seq->prog->host.n_adc)
@@ -657,7 +660,7 @@ mrsim_status mrsim_kt_simulate(mrsim_ctx *ctx, int64_t n_sets, const double *t1,
                                int64_t n_samples) {
     Range nvtx_range("mrsim_kt_simulate");
     if (!ctx) return MRSIM_EINVAL;
-    if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec, true)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_sets < 0 || n_steps < 0) return fail(ctx, MRSIM_EINVAL, "negative count");
     if (max_order < 0 || max_order > KT_MAX_ORDER)
         return fail(ctx, MRSIM_EINVAL, "max_order must be 0.." + std::to_string(KT_MAX_ORDER));
@@ -800,7 +803,8 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
     if (!ph || !seq || !best) return fail(ctx, MRSIM_EINVAL, "NULL argument");
     if (ph->ctx != ctx || seq->ctx != ctx) return fail(ctx, MRSIM_EINVAL, "handle belongs to another context");
     if (!normalize_precision(prec)) return fail(ctx, MRSIM_EINVAL, "unknown precision");
-    const bool fp64 = prec == MRSIM_FP64;
+    const int mode = launch_mode(prec);
+    const bool fp64 = mode != MODE_F32;
     std::memset(best, 0, sizeof *best);
     Launch def = choose_launch(ctx, fp64, ph->n);
     if (ph->n == 0) {
@@ -846,7 +850,9 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
         a.signal = ctx->d_sig;
         a.status = ctx->d_status;
         cudaEventRecord(e0, st);
-        const int rc = fp64 ? launch_fwd_f64(a, k, t, stream) : launch_fwd_f32(a, k, t, stream);
+        const int rc = mode == MODE_F64 ? launch_fwd_f64(a, k, t, stream)
+                       : mode == MODE_DF ? launch_fwd_df(a, k, t, stream)
+                                         : launch_fwd_f32(a, k, t, stream);
         cudaEventRecord(e1, st);
         if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
             cudaGetLastError();
@@ -863,7 +869,7 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
         for (int t : thr) {
             if (t > (fp64 || k == 8 ? 256 : 512)) continue;
             const size_t smem = fwd_smem_bytes(fp64, P, k, t);
-            if (smem > (size_t)ctx->max_smem_optin || fwd_blocks_per_sm(fp64, k, t, smem) == 0) continue;
+            if (smem > (size_t)ctx->max_smem_optin || fwd_blocks_per_sm(mode, k, t, smem) == 0) continue;
             if (trial(k, t) < 0.0f) continue;
             const float ms = trial(k, t);
             if (ms >= 0.0f) cand.push_back(TunedShape{k, t, ms});
@@ -937,7 +943,8 @@ namespace {
 // the launch geometry of the persistent kernel.
 mrsim_status batch_layout(mrsim_batch *b, int k, int threads) {
     mrsim_ctx *ctx = b->ctx;
-    const bool fp64 = b->prec == MRSIM_FP64;
+    const int mode = launch_mode(b->prec);
+    const bool fp64 = mode != MODE_F32;
     const int64_t S = (int64_t)k * threads;
     std::vector<int> order(b->descs.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
@@ -951,7 +958,7 @@ mrsim_status batch_layout(mrsim_batch *b, int k, int threads) {
         smem = std::max(smem, fwd_smem_bytes(fp64, b->descs[d].prog, k, threads));
     }
     if (smem > (size_t)ctx->max_smem_optin) return fail(ctx, MRSIM_EUNSUPPORTED, "launch shape exceeds shared memory");
-    const int per_sm = batch_blocks_per_sm(fp64, k, threads, smem);
+    const int per_sm = batch_blocks_per_sm(mode, k, threads, smem);
     if (per_sm <= 0) return fail(ctx, MRSIM_EUNSUPPORTED, "launch shape cannot be resident");
     if (items.size() > (size_t)INT32_MAX) return fail(ctx, MRSIM_EINVAL, "too many work items");
     cudaFree(b->d_items);
@@ -984,7 +991,7 @@ mrsim_status batch_enqueue(mrsim_batch *b, const FwdArgs *d_descs, cudaStream_t 
     a.items = b->d_items;
     a.n_items = (int32_t)b->items.size();
     a.head = b->d_head;
-    rc = launch_batch(b->prec == MRSIM_FP64, a, b->k, b->threads, b->smem, b->grid, st);
+    rc = launch_batch(launch_mode(b->prec), a, b->k, b->threads, b->smem, b->grid, st);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch batch kernel");
     return MRSIM_OK;
 }
@@ -1017,7 +1024,7 @@ mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *
             return fail(ctx, MRSIM_EINVAL, "batch entry " + std::to_string(i) + ": signal buffer must be device memory");
         }
         FwdArgs a{};
-        a.prog = prec == MRSIM_FP64 ? q->p64 : q->p32;
+        a.prog = prec != MRSIM_FP32 ? q->p64 : q->p32;  // float64 program for float64 and double-float
         a.params = p->params;
         a.n_spins = p->n;
         a.n_pad = p->n_pad;
@@ -1041,7 +1048,7 @@ mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "batch descriptors"));
     }
     // default shape: the single-phantom heuristic for the largest phantom, shrunk until it fits
-    Launch L = choose_launch(ctx, prec == MRSIM_FP64, max_n);
+    Launch L = choose_launch(ctx, prec != MRSIM_FP32, max_n);
     mrsim_status st = batch_layout(b, L.k, L.threads);
     for (int t : {64, 32}) {
         if (st != MRSIM_EUNSUPPORTED) break;
@@ -1061,7 +1068,7 @@ mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *b
     std::memset(best, 0, sizeof *best);
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const bool fp64 = b->prec == MRSIM_FP64;
+    const bool fp64 = b->prec != MRSIM_FP32;
     if (b->descs.empty()) return MRSIM_OK;
     // Time prefixes of every program, the same fraction of each so that the mix of programs is
     // that of the whole batch: pass 1 every shape on about 2e10 spin-steps in all, pass 2 the
@@ -1161,7 +1168,7 @@ mrsim_status mrsim_batch_autotune(mrsim_batch *b, void *stream, mrsim_options *b
 
 mrsim_status mrsim_batch_set_shape(mrsim_batch *b, int32_t spins_per_thread, int32_t threads_per_block) {
     if (!b) return MRSIM_EINVAL;
-    const bool fp64 = b->prec == MRSIM_FP64;
+    const bool fp64 = b->prec != MRSIM_FP32;
     const int k = spins_per_thread, t = threads_per_block;
     const bool ok = fp64 ? (k == 1 || k == 2) : (k == 1 || k == 2 || k == 4 || k == 8);
     if (!ok || t < 32 || t % 32 || t > (fp64 || k == 8 ? 256 : 512))

@@ -545,7 +545,7 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
                                    mrsim_precision prec, void *stream, double *signal_out, int64_t n_adc) {
     if (!ctx) return MRSIM_EINVAL;
     if (!ph || !f || ph->ctx != ctx || f->ctx != ctx) return ffail(ctx, MRSIM_EINVAL, "NULL handle or another context");
-    if (!normalize_precision(prec)) return ffail(ctx, MRSIM_EINVAL, "unknown precision");
+    if (!normalize_precision(prec, true)) return ffail(ctx, MRSIM_EINVAL, "unknown precision");
     if (n_adc != f->n_adc) return ffail(ctx, MRSIM_EINVAL, "n_adc does not match the sample events");
     if (n_adc > 0 && !signal_out) return ffail(ctx, MRSIM_EINVAL, "signal_out is NULL");
     const bool f64 = prec == MRSIM_FP64;

@@ -33,9 +33,14 @@ int launch_fwd_f64(const FwdArgs &a, int k, int threads, void *stream) {
 int fwd_regs_f32(int k);
 int launch_batch_f32(const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream);
 int batch_blocks_per_sm_f32(int k, int threads, size_t smem);
+int launch_batch_df(const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream);
+int batch_blocks_per_sm_df(int k, int threads, size_t smem);
+int fwd_blocks_per_sm_df(int k, int threads, size_t smem);
+int fwd_regs_df(int k);
 
-int launch_batch(bool fp64, const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream) {
-    if (!fp64) return launch_batch_f32(b, k, threads, smem, grid, stream);
+int launch_batch(int mode, const BatchArgs &b, int k, int threads, size_t smem, int grid, void *stream) {
+    if (mode == MODE_F32) return launch_batch_f32(b, k, threads, smem, grid, stream);
+    if (mode == MODE_DF) return launch_batch_df(b, k, threads, smem, grid, stream);
     switch (k) {
     case 1: return dev::launch_batch_one<double, 1, 256>(b, threads, smem, grid, stream);
     case 2: return dev::launch_batch_one<double, 2, 256>(b, threads, smem, grid, stream);
@@ -43,8 +48,9 @@ int launch_batch(bool fp64, const BatchArgs &b, int k, int threads, size_t smem,
     }
 }
 
-int batch_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
-    if (!fp64) return batch_blocks_per_sm_f32(k, threads, smem);
+int batch_blocks_per_sm(int mode, int k, int threads, size_t smem) {
+    if (mode == MODE_F32) return batch_blocks_per_sm_f32(k, threads, smem);
+    if (mode == MODE_DF) return batch_blocks_per_sm_df(k, threads, smem);
     switch (k) {
     case 1: return dev::batch_blocks_per_sm<double, 1, 256>(threads, smem);
     case 2: return dev::batch_blocks_per_sm<double, 2, 256>(threads, smem);
@@ -52,8 +58,9 @@ int batch_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
     }
 }
 int fwd_blocks_per_sm_f32(int k, int threads, size_t smem);
-int fwd_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
-    if (!fp64) return fwd_blocks_per_sm_f32(k, threads, smem);
+int fwd_blocks_per_sm(int mode, int k, int threads, size_t smem) {
+    if (mode == MODE_F32) return fwd_blocks_per_sm_f32(k, threads, smem);
+    if (mode == MODE_DF) return fwd_blocks_per_sm_df(k, threads, smem);
     switch (k) {
     case 1: return dev::blocks_per_sm<double, 1, 256>(threads, smem);
     case 2: return dev::blocks_per_sm<double, 2, 256>(threads, smem);
@@ -61,8 +68,9 @@ int fwd_blocks_per_sm(bool fp64, int k, int threads, size_t smem) {
     }
 }
 
-int fwd_regs(bool fp64, int k) {
-    if (!fp64) return fwd_regs_f32(k);
+int fwd_regs(int mode, int k) {
+    if (mode == MODE_F32) return fwd_regs_f32(k);
+    if (mode == MODE_DF) return fwd_regs_df(k);
     switch (k) {
     case 1: return dev::regs_of<double, 1, 256>();
     case 2: return dev::regs_of<double, 2, 256>();

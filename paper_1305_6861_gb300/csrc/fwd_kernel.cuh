@@ -27,6 +27,7 @@
 
 #include "../../include/mrsim.h"
 #include "internal.h"
+#include "dfloat.cuh"
 #include "packed.cuh"
 
 namespace mrsim {
@@ -170,7 +171,7 @@ __device__ __forceinline__ R transpose_reduce32(R (&v)[32], int lane) {
             const R a = v[i], b = v[i + off];
             const R send = up ? a : b;
             const R keep = up ? b : a;
-            v[i] = keep + __shfl_xor_sync(FULL, send, off);
+            v[i] = keep + shfl_x(send, off);
         }
     }
     return v[0];
@@ -301,7 +302,9 @@ struct Spins {
     using CwT = Cw<P>;
     static constexpr int L = Packing<R, K>::L;  // spins per packed value
     static constexpr int NP = K / L;            // packed values per quantity
-    static constexpr bool F64 = std::is_same<R, double>::value;
+    // float64 and double-float (the compensated precision) share the float64 program, layouts and
+    // code paths; float32 has its own
+    static constexpr bool F64 = is_wide<R>::value;
     static constexpr int WIN = F64 ? SAMPLE_WINDOW_F64 : SAMPLE_WINDOW_F32;  // window slots
     static constexpr int NCR = NC > 0 ? NC : 1;                                // slots per sample
     static constexpr int WINS = WIN / NCR;                                     // samples per window
@@ -549,12 +552,15 @@ struct Spins {
                 R sn, cs;
                 if constexpr (F64) {
                     double th = 0.0;
-                    if (op.flags & F_KX) th += op.f[0] * prm_at(0, q, h);
-                    if (op.flags & F_KY) th += op.f[1] * prm_at(1, q, h);
-                    if (op.flags & F_KZ) th += op.f[2] * prm_at(2, q, h);
-                    if (op.flags & F_DT) th += op.f[3] * prm_at(3, q, h);
+                    if (op.flags & F_KX) th += op.f[0] * (double)prm_at(0, q, h);
+                    if (op.flags & F_KY) th += op.f[1] * (double)prm_at(1, q, h);
+                    if (op.flags & F_KZ) th += op.f[2] * (double)prm_at(2, q, h);
+                    if (op.flags & F_DT) th += op.f[3] * (double)prm_at(3, q, h);
                     th -= rint(th);
-                    sincospi(2.0 * th, &sn, &cs);
+                    double snd, csd;
+                    sincospi(2.0 * th, &snd, &csd);
+                    sn = (R)snd;
+                    cs = (R)csd;
                 } else {
                     float err = 0.0f, t = 0.0f;
                     if (op.flags & F_KX) t = wrap1(t + ff_term(op.f[0], op.f[1], prm_at(0, q, h), prm_at(1, q, h), err));
@@ -695,8 +701,8 @@ struct Spins {
             coil_sum(c, sx, sy);
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) {
-                sx += __shfl_xor_sync(FULL, sx, off);
-                sy += __shfl_xor_sync(FULL, sy, off);
+                sx += shfl_x(sx, off);
+                sy += shfl_x(sy, off);
             }
             const int slot = (j - win_base) * NCR + c;
             if (lane == 0) {
@@ -723,8 +729,8 @@ struct Spins {
         R sx = hsum(tree_sum<P, NP>(u)), sy = hsum(tree_sum<P, NP>(v));
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
-            sx += __shfl_xor_sync(FULL, sx, off);
-            sy += __shfl_xor_sync(FULL, sy, off);
+            sx += shfl_x(sx, off);
+            sy += shfl_x(sy, off);
         }
         if (lane == 0) {
             if constexpr (F64) {
@@ -1219,7 +1225,7 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
 template <typename R, int K, int MAXT, int NC = 0>
 __global__ void __launch_bounds__(MAXT, 1) fwd_kernel(const FwdArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (threadIdx.x == 0) init_op_barriers(smem, std::is_same<R, double>::value);
+    if (threadIdx.x == 0) init_op_barriers(smem, is_wide<R>::value);
     uint32_t seq = 0;
     run_tile<R, K, NC>(a, (int64_t)blockIdx.x, smem, seq);
 }
@@ -1231,7 +1237,7 @@ template <typename R, int K, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) batch_kernel(const BatchArgs b) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_item;
-    if (threadIdx.x == 0) init_op_barriers(smem, std::is_same<R, double>::value);
+    if (threadIdx.x == 0) init_op_barriers(smem, is_wide<R>::value);
     uint32_t seq = 0;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(b.head, 1);
@@ -1250,7 +1256,7 @@ int launch_one(const FwdArgs &a, int threads, void *stream) {
     if (threads <= 0 || threads > MAXT || threads % 32) return (int)cudaErrorInvalidValue;
     if (a.n_spins <= 0) return 0;
     const int S = K * threads;
-    const SmemLayout L = smem_layout(std::is_same<R, double>::value, a.prog.n_pcls, a.prog.n_e1, a.prog.n_e2,
+    const SmemLayout L = smem_layout(is_wide<R>::value, a.prog.n_pcls, a.prog.n_e1, a.prog.n_e2,
                                      a.prog.n_train, S, threads / 32);
     auto kern = fwd_kernel<R, K, MAXT, NC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);

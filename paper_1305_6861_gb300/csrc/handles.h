@@ -140,11 +140,12 @@ struct mrsim_batch {
 
 namespace mrsim {
 
-// Accepts the three precisions of the C-ABI; MRSIM_FP32_KAHAN is the float32 path (its
-// cross-block sums are float64), so it becomes MRSIM_FP32 for every later decision.
-inline bool normalize_precision(mrsim_precision &p) {
-    if (p == MRSIM_FP32_KAHAN) p = MRSIM_FP32;
-    return p == MRSIM_FP64 || p == MRSIM_FP32;
+// Accepts the three precisions of the C-ABI.  Calls without a compensated kernel (receive
+// coils, K-t, non-parallel fields) serve MRSIM_FP32_KAHAN with their float32 kernels: they pass
+// fold_kahan = true and get MRSIM_FP32.
+inline bool normalize_precision(mrsim_precision &p, bool fold_kahan = false) {
+    if (fold_kahan && p == MRSIM_FP32_KAHAN) p = MRSIM_FP32;
+    return p == MRSIM_FP64 || p == MRSIM_FP32 || p == MRSIM_FP32_KAHAN;
 }
 
 struct Launch {

@@ -151,12 +151,21 @@ struct BatchArgs {
     int *head;               // work-queue counter, zero before the launch (device)
 };
 
-// Kernel launchers (fwd_f32.cu / fwd_f64.cu).  Return a cudaError_t value.
-int launch_batch(bool fp64, const BatchArgs &b, int spins_per_thread, int threads, size_t smem, int grid,
+// Arithmetic of a launch: float32, float64, or double-float (float32 pairs carrying their
+// rounding error: the compensated precision).  Double-float uses the float64 program and
+// layouts (fp64 = mode != MODE_F32 wherever a layout or program is chosen).
+enum LaunchMode : int { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2 };
+inline int launch_mode(mrsim_precision p) {
+    return p == MRSIM_FP64 ? MODE_F64 : p == MRSIM_FP32_KAHAN ? MODE_DF : MODE_F32;
+}
+
+// Kernel launchers (fwd_f32.cu / fwd_f64.cu / fwd_df.cu).  Return a cudaError_t value.
+int launch_batch(int mode, const BatchArgs &b, int spins_per_thread, int threads, size_t smem, int grid,
                  void *stream);
-int batch_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
+int batch_blocks_per_sm(int mode, int spins_per_thread, int threads, size_t smem);
 int launch_fwd_f32(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 int launch_fwd_f64(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
+int launch_fwd_df(const FwdArgs &a, int spins_per_thread, int threads, void *stream);
 // one block whose bounded mbarrier wait runs out after limit_ns and records MRSIM_ETIMEOUT in *status
 int launch_wait_probe(int *status, uint64_t limit_ns, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
@@ -196,9 +205,9 @@ constexpr int MAX_COILS = MRSIM_MAX_COILS;
 int launch_fwd_coils_f32(const FwdArgs &a, int threads, void *stream);
 int launch_fwd_coils_f64(const FwdArgs &a, int threads, void *stream);
 // Registers per thread of a kernel instance (0 if the shape does not exist).
-int fwd_regs(bool fp64, int spins_per_thread);
+int fwd_regs(int mode, int spins_per_thread);
 // Resident blocks per SM of a launch shape with `smem` dynamic shared memory (0 = cannot launch).
-int fwd_blocks_per_sm(bool fp64, int spins_per_thread, int threads, size_t smem);
+int fwd_blocks_per_sm(int mode, int spins_per_thread, int threads, size_t smem);
 int zero_signals(const FwdArgs *descs, int n, void *stream);
 // Validate receive sensitivities (complex float64, [n_coils][n], interleaved) and write them to
 // dst as [n_coils][n_pad] float2 (f32) or double2, zero-padded; bad = lowest index of a
