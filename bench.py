@@ -892,7 +892,7 @@ def run_ours(args):
     if args.events:  # profiling aid: a prefix of the sequence (whole repetitions), named in config
         w = W.Workload(w.name + f"_first{args.events}ev", w.phantom,
                        W.Sequence(w.sequence.events[: args.events], w.sequence.gamma_hz_per_t), w.note)
-    prec = M.FP64 if args.precision == "fp64" else M.FP32
+    prec = {"fp64": M.FP64, "kahan": M.FP32_KAHAN}.get(args.precision, M.FP32)
     ctx = M.Context(local)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
@@ -939,7 +939,7 @@ def run_ours(args):
     ctx.stream_status(stream)
 
     # the float64 oracle on a spin sample runs on the host cores meanwhile (rank 0, plain lists)
-    extras = rank == 0 and not args.skip_extra and not n_coils
+    extras = rank == 0 and not args.skip_extra and not n_coils and prec != M.FP32_KAHAN
     frac = args.oracle_fraction if args.oracle_fraction >= 0 else {"c1": 1.0, "c2": 1.0, "c3": 0.01}[args.workload]
     orun = None
     if extras and not args.no_cpu_baseline and not args.raster and not args.events and frac > 0:
@@ -1109,7 +1109,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {M.FP64: "f64", M.FP32_KAHAN: "df32"}.get(prec, "f32"), "data": "synthetic",
             "config": {"workload": w.name + (f"_{n_coils}coils" if n_coils else ""), "n_spins_per_gpu": w.phantom.n,
                        "n_events": w.sequence.n_events,
                        "n_adc": seq.n_adc, "n_ops": seq.n_ops, "spin_steps_per_gpu_step": spin_steps,
@@ -1138,7 +1138,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "kt", "fields"], default="c3")
     ap.add_argument("--kt-sets", type=int, default=65536, help="ensembles of the K-t workload")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "kahan"], default="fp32",
+                    help="kahan: the compensated precision (double-float on the FP32 pipe)")
     ap.add_argument("--spins-per-thread", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
