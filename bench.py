@@ -581,6 +581,9 @@ def run_adjoint(args):
     stream = torch.cuda.current_stream()
     measure_device(ctx, M, 0, stream)
     adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf0), ckpt_every=64)
+    kahan = args.precision == "kahan"
+    if kahan:  # the recursion in double-float pairs on the FP32 pipe
+        adj.set_precision(M.FP32_KAHAN)
     P = M.Phantom(ctx, [torch.from_numpy(a).to(dev) for a in w.phantom.arrays()], stream=stream)
     rfd = torch.from_numpy(rf0.copy()).to(dev)
     sig = torch.zeros(2 * adj.n_adc, dtype=torch.float64, device=dev)
@@ -618,17 +621,23 @@ def run_adjoint(args):
     flops = flops_spin * w.phantom.n
     achieved = flops / (ms * 1e-3) / 1e9
     fp64_peak = 2 * DEVICE["fp64_lane_ops_per_s"] / 1e9
+    roof = {"bound": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s (float64)",
+            "frac": achieved / fp64_peak, "traffic": None, "kernel_ms": ms,
+            "peak_basis": "2 x the float64 multiply-add rate measured on every SM in this run "
+                          f"(SM clock {DEVICE['probe_sm_mhz']} MHz)",
+            "flops_per_spin_step": flops_spin / n_ev}
+    if kahan:  # the same arithmetic in double-float pairs, against the FP32 pipe
+        roof = fp32_roofline(achieved / 2, ck, traffic=None, kernel_ms=ms, flops_per_spin_step=flops_spin / n_ev,
+                             op_model="the float64 flop model's multiply-adds, executed as double-float pairs "
+                                      "(each about 10-20 float32 operations)")
     line = {"metric": "spin-steps/s of forward+backward (adjoint) at 1 GB300", "value": w.spin_steps / (ms * 1e-3),
             "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32" if kahan else "f64",
+            "data": "synthetic",
             "config": {"workload": w.name, "n_spins": w.phantom.n, "n_events": len(ev), "n_rf_params": len(rf0),
                        "ckpt_every": 64, "step": "adjoint forward + backward",
                        "note": "float64-pipe bound (ncu: the backward kernel keeps it 71 % busy with 4 warps per SM); the flop model counts the formulation's arithmetic, about half the executed float64 instructions"},
-            "roofline": {"bound": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s (float64)",
-                         "frac": achieved / fp64_peak, "traffic": None, "kernel_ms": ms,
-                         "peak_basis": "2 x the float64 multiply-add rate measured on every SM in this run "
-                                       f"(SM clock {DEVICE['probe_sm_mhz']} MHz)",
-                         "flops_per_spin_step": flops_spin / n_ev},
+            "roofline": roof,
             "gpu_launches": 4 * args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id()}
     if not args.no_cpu_baseline:  # the oracle's forward-mode gradient (every flip) on a bounded spin sample
         import oracle

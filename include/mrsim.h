@@ -327,6 +327,11 @@ mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, 
 mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph, const double *rf_values,
                                     const double *dl_dsignal, void *stream, double *d_rho, double *d_t1,
                                     double *d_t2, double *d_rf);
+/* Arithmetic of the adjoint's forward and backward recursion: MRSIM_FP64 (the default) or
+ * MRSIM_FP32_KAHAN, double-float pairs on the FP32 pipe (about 48 significant bits; GB300 runs
+ * float64 at 1/64 of its float32 rate); MRSIM_FP32 gives MRSIM_EUNSUPPORTED.  The next forward
+ * call recomputes the checkpoints. */
+mrsim_status mrsim_adjoint_set_precision(mrsim_adjoint *adj, mrsim_precision prec);
 /* Frees the adjoint's device tables and checkpoint storage (NULL is ignored). */
 void mrsim_adjoint_destroy(mrsim_adjoint *adj);
 /* One-shot gradient of a real loss L of the simulated signal (the same adjoint recursion as
@@ -335,8 +340,8 @@ void mrsim_adjoint_destroy(mrsim_adjoint *adj);
  * forward method.  The call creates the adjoint program from the sequence's own event list,
  * runs the checkpointed forward pass with the pulses' own flips and the backward pass, copies
  * the results out and frees everything again, so it synchronises `stream`.
- *   prec:       MRSIM_FP64 (the gradients are float64; MRSIM_FP32 and MRSIM_FP32_KAHAN give
- *               MRSIM_EUNSUPPORTED)
+ *   prec:       MRSIM_FP64, or MRSIM_FP32_KAHAN (the recursion in double-float pairs, see
+ *               mrsim_adjoint_set_precision); MRSIM_FP32 gives MRSIM_EUNSUPPORTED
  *   ckpt_every: events per checkpoint segment, 1..128 (0 = 64)
  *   dL_dsignal: 2*n_adc doubles (dL/dRe s_j, dL/dIm s_j), host or device
  *   d_rho, d_t1, d_t2: NULL or n_spins doubles each, host or device: dL/dM0, dL/dT1, dL/dT2 of

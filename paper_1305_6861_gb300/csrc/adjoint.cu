@@ -28,6 +28,7 @@
 #include "../../include/mrsim.h"
 #include "handles.h"
 #include "internal.h"
+#include "dfloat.cuh"
 
 using namespace mrsim;
 
@@ -48,7 +49,8 @@ struct AdjEvent {
     int32_t adc;    // sample index (A_ADC)
     double k[3];    // inline moment [cycles/m] (A_INL)
     double dt;      // interval [s]
-    double pad[2];
+    float dth, dtl; // the interval as a float pair (hi, lo), for the compensated precision
+    double pad;
 };
 static_assert(sizeof(AdjEvent) == 64, "AdjEvent must be 64 bytes");
 
@@ -58,11 +60,14 @@ struct RfSpec {
     double alpha, phi;
     int32_t param, pad;
 };
-struct RfEntry {
-    double R[9];
-    double G[9];         // (dR/dα)·Rᵀ: the derivative applied to the state after the pulse
+template <typename T>
+struct RfE {
+    T R[9];
+    T G[9];              // (dR/dα)·Rᵀ: the derivative applied to the state after the pulse
     int32_t param, pad;  // learnable parameter index or -1
 };
+using RfEntry = RfE<double>;  // the compensated precision's table has the same size (8-byte values)
+static_assert(sizeof(RfE<double>) == sizeof(RfE<dev::dfl>), "RF table entries of both precisions");
 
 }  // namespace
 
@@ -77,6 +82,8 @@ struct mrsim_adjoint {
     double *d_demod = nullptr;  // 2 per sample: cos(adc_phase), -sin(adc_phase)
     double *d_ckpt = nullptr;   // checkpoints: (n_seg - 1) x n_spins x 3 (forward kernel), else n_seg x 3 x n_spins
     mrsim_sequence *fwd = nullptr;  // the forward program (parametric pulses, snapshots at segment starts)
+    mrsim_precision prec = MRSIM_FP64;  // MRSIM_FP64, or MRSIM_FP32_KAHAN (double-float recursion)
+    void *d_lam = nullptr;              // 2 values per sample: conj(demod)·dL/ds (float64 or double-float)
     size_t ckpt_cap = 0;
     const mrsim_phantom *last_ph = nullptr;
     int64_t last_n = -1;
@@ -85,7 +92,8 @@ struct mrsim_adjoint {
 namespace {
 
 // Eq. 3.19 as the rotation by −α about n = (cos φ, sin φ, 0), and its derivative in α.
-__global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values, RfEntry *out) {
+template <typename T>
+__global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values, RfE<T> *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const RfSpec s = spec[i];
         const double a = s.param >= 0 ? values[s.param] : s.alpha;
@@ -94,7 +102,7 @@ __global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values,
         sincos(s.phi, &sp, &cp);
         const double n0 = cp, n1 = sp;
         const double omc = 1.0 - ca;
-        RfEntry e;
+        RfEntry e;  // built in float64, stored in T
         // R = cos α·I + (1 − cos α)·n nᵀ − sin α·[n]x
         e.R[0] = ca + omc * n0 * n0;
         e.R[1] = omc * n0 * n1;
@@ -120,9 +128,14 @@ __global__ void rf_table_kernel(const RfSpec *spec, int n, const double *values,
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c)
                 e.G[3 * r + c] = D[3 * r] * e.R[3 * c] + D[3 * r + 1] * e.R[3 * c + 1] + D[3 * r + 2] * e.R[3 * c + 2];
-        e.param = s.param;
-        e.pad = 0;
-        out[i] = e;
+        RfE<T> o;
+        for (int q = 0; q < 9; ++q) {
+            o.R[q] = T(e.R[q]);
+            o.G[q] = T(e.G[q]);
+        }
+        o.param = s.param;
+        o.pad = 0;
+        out[i] = o;
     }
 }
 
@@ -138,45 +151,73 @@ __global__ void rf_param_table_kernel(const double *values, int n, double *t64, 
     }
 }
 
+// the backward's sample source: conj(demod_j)·h_j per sample, formed in float64 and stored in T
+template <typename T>
+__global__ void lam_kernel(const double *demod, const double *h, int64_t n, T *out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double cr = demod[2 * j], ci = -demod[2 * j + 1];
+        const double hr = h[2 * j], hi = h[2 * j + 1];
+        out[2 * j] = T(cr * hr - ci * hi);
+        out[2 * j + 1] = T(cr * hi + ci * hr);
+    }
+}
+
 struct AdjArgs {
     const AdjEvent *ev;
     int64_t n_events;
-    const RfEntry *rf;
+    const void *rf;          // RfE<T> entries
     const double *cls;
     int32_t n_cls;
     int32_t seg;
-    const double *demod;
+    const double *demod;     // forward: 2 per sample
     const double *params;
     int64_t n_spins, n_pad;
     double *ckpt;     // see mrsim_adjoint::d_ckpt
     int32_t ckpt_snap;  // checkpoints written as snapshots by the forward kernel
     double *signal;   // forward
-    const double *h;  // backward: dL/ds, 2 per sample
+    const void *lam;  // backward: conj(demod)·dL/ds per sample, 2 T values each (the adjoint's sample source)
     double *d_rho, *d_t1, *d_t2, *d_rf;
     int32_t n_params;
 };
 
+// Spin parameters: coordinates, Δf and rates in float64 (the phases are formed in float64), and
+// M0 and the rates again in the arithmetic type T of the recursion.
+template <typename T>
 struct SpinP {
-    double x, y, z, df, rho, r1, r2;
+    double x, y, z, df, r1d, r2d;
+    T rho, r1, r2;
 };
 
-__device__ __forceinline__ SpinP load_spin(const AdjArgs &a, int64_t s) {
-    SpinP p{};
+template <typename T>
+__device__ __forceinline__ SpinP<T> load_spin(const AdjArgs &a, int64_t s) {
+    SpinP<T> p{};
+    double rho = 0.0, r1 = 0.0, r2 = 0.0;
+    p.x = p.y = p.z = p.df = 0.0;
     if (s < a.n_spins) {
         const int64_t np = a.n_pad;
         p.x = a.params[P_X * np + s];
         p.y = a.params[P_Y * np + s];
         p.z = a.params[P_Z * np + s];
         p.df = a.params[P_DF * np + s];
-        p.rho = a.params[P_RHO * np + s];
-        p.r1 = a.params[P_R1 * np + s];
-        p.r2 = a.params[P_R2 * np + s];
+        rho = a.params[P_RHO * np + s];
+        r1 = a.params[P_R1 * np + s];
+        r2 = a.params[P_R2 * np + s];
     }
+    p.r1d = r1;
+    p.r2d = r2;
+    p.rho = T(rho);
+    p.r1 = T(r1);
+    p.r2 = T(r2);
     return p;
 }
 
-// per-spin class table in shared memory: w (complex, with E2) and E1, per class
-__device__ __forceinline__ void fill_classes(const AdjArgs &a, const SpinP &p, double *tab) {
+// the event's interval in T
+__device__ __forceinline__ double dt_of(const AdjEvent &e, double) { return e.dt; }
+__device__ __forceinline__ dev::dfl dt_of(const AdjEvent &e, dev::dfl) { return dev::dfl(e.dth, e.dtl); }
+
+// per-spin class table in shared memory: w (complex, with E2) and E1, per class (float64 math)
+template <typename T>
+__device__ __forceinline__ void fill_classes(const AdjArgs &a, const SpinP<T> &p, T *tab) {
     const int t = threadIdx.x, nt = blockDim.x;
     for (int c = 0; c < a.n_cls; ++c) {
         const double kx = a.cls[4 * c], ky = a.cls[4 * c + 1], kz = a.cls[4 * c + 2], dt = a.cls[4 * c + 3];
@@ -184,16 +225,16 @@ __device__ __forceinline__ void fill_classes(const AdjArgs &a, const SpinP &p, d
         th -= rint(th);
         double sn, cs;
         sincospi(2.0 * th, &sn, &cs);
-        const double e2 = exp(-dt * p.r2);
-        tab[(3 * c + 0) * nt + t] = e2 * cs;
-        tab[(3 * c + 1) * nt + t] = -e2 * sn;
-        tab[(3 * c + 2) * nt + t] = exp(-dt * p.r1);
+        const double e2 = exp(-dt * p.r2d);
+        tab[(3 * c + 0) * nt + t] = T(e2 * cs);
+        tab[(3 * c + 1) * nt + t] = T(-e2 * sn);
+        tab[(3 * c + 2) * nt + t] = T(exp(-dt * p.r1d));
     }
 }
 
 // precession + relaxation factors of one event for this spin: w = E2·exp(−j2πφ), E1
-__device__ __forceinline__ void factors(const AdjEvent &e, const SpinP &p, const double *tab, double &wr, double &wi,
-                                       double &e1) {
+template <typename T>
+__device__ __forceinline__ void factors(const AdjEvent &e, const SpinP<T> &p, const T *tab, T &wr, T &wi, T &e1) {
     const int t = threadIdx.x, nt = blockDim.x;
     if (e.flags & A_CLS) {
         wr = tab[(3 * e.cls + 0) * nt + t];
@@ -204,47 +245,55 @@ __device__ __forceinline__ void factors(const AdjEvent &e, const SpinP &p, const
         th -= rint(th);
         double sn, cs;
         sincospi(2.0 * th, &sn, &cs);
-        const double e2 = exp(-e.dt * p.r2);
-        wr = e2 * cs;
-        wi = -e2 * sn;
-        e1 = exp(-e.dt * p.r1);
+        const double e2 = exp(-e.dt * p.r2d);
+        wr = T(e2 * cs);
+        wi = T(-e2 * sn);
+        e1 = T(exp(-e.dt * p.r1d));
     } else {
-        wr = 1.0;
-        wi = 0.0;
-        e1 = 1.0;
+        wr = T(1);
+        wi = T(0);
+        e1 = T(1);
     }
 }
 
-__device__ __forceinline__ void apply_rf(const double *R, double M[3]) {
-    const double x = R[0] * M[0] + R[1] * M[1] + R[2] * M[2];
-    const double y = R[3] * M[0] + R[4] * M[1] + R[5] * M[2];
-    const double z = R[6] * M[0] + R[7] * M[1] + R[8] * M[2];
+template <typename T>
+__device__ __forceinline__ void apply_rf(const T *R, T M[3]) {
+    const T x = R[0] * M[0] + R[1] * M[1] + R[2] * M[2];
+    const T y = R[3] * M[0] + R[4] * M[1] + R[5] * M[2];
+    const T z = R[6] * M[0] + R[7] * M[1] + R[8] * M[2];
     M[0] = x;
     M[1] = y;
     M[2] = z;
 }
 
 // the part of an event after its pulse: precession, T2 and T1 over the interval
-__device__ __forceinline__ void after_pulse(const AdjEvent &e, const SpinP &p, const double *tab, double M[3]) {
-    double wr, wi, e1;
+template <typename T>
+__device__ __forceinline__ void after_pulse(const AdjEvent &e, const SpinP<T> &p, const T *tab, T M[3]) {
+    T wr, wi, e1;
     factors(e, p, tab, wr, wi, e1);
-    const double x = M[0] * wr - M[1] * wi;
-    const double y = M[0] * wi + M[1] * wr;
+    const T x = M[0] * wr - M[1] * wi;
+    const T y = M[0] * wi + M[1] * wr;
     M[0] = x;
     M[1] = y;
-    M[2] = e1 * M[2] + p.rho * (1.0 - e1);
+    M[2] = e1 * M[2] + p.rho * (T(1) - e1);
+}
+
+template <typename T>
+__device__ __forceinline__ const RfE<T> &rf_at(const AdjArgs &a, int i) {
+    return static_cast<const RfE<T> *>(a.rf)[i];
 }
 
 // forward step of one event (Eq. 4.1)
-__device__ __forceinline__ void step(const AdjArgs &a, const AdjEvent &e, const SpinP &p, const double *tab,
-                                     double M[3]) {
-    if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, M);
+template <typename T>
+__device__ __forceinline__ void step(const AdjArgs &a, const AdjEvent &e, const SpinP<T> &p, const T *tab, T M[3]) {
+    if (e.flags & A_RF) apply_rf(rf_at<T>(a, e.rf).R, M);
     after_pulse(e, p, tab, M);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    for (int off = 16; off >= 1; off >>= 1) v = v + dev::shfl_x(v, off);
     return v;
 }
 
@@ -257,29 +306,30 @@ __device__ __forceinline__ void stage(const AdjArgs &a, int64_t e0, int m, AdjEv
     __syncthreads();
 }
 
+template <typename T>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_forward_kernel(const AdjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     AdjEvent *sev = reinterpret_cast<AdjEvent *>(smem);
-    double *tab = reinterpret_cast<double *>(smem + sizeof(AdjEvent) * a.seg);
+    T *tab = reinterpret_cast<T *>(smem + sizeof(AdjEvent) * a.seg);
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const SpinP p = load_spin(a, s);
+    const SpinP<T> p = load_spin<T>(a, s);
     fill_classes(a, p, tab);
-    double M[3] = {0.0, 0.0, p.rho};
+    T M[3] = {T(0), T(0), p.rho};
     const int lane = threadIdx.x & 31;
     for (int64_t e0 = 0, sg = 0; e0 < a.n_events; e0 += a.seg, ++sg) {
         const int m = (int)min((int64_t)a.seg, a.n_events - e0);
         stage(a, e0, m, sev);
         if (s < a.n_spins) {
             double *ck = a.ckpt + sg * 3 * a.n_spins;
-            ck[s] = M[0];
-            ck[a.n_spins + s] = M[1];
-            ck[2 * a.n_spins + s] = M[2];
+            ck[s] = (double)M[0];
+            ck[a.n_spins + s] = (double)M[1];
+            ck[2 * a.n_spins + s] = (double)M[2];
         }
         for (int i = 0; i < m; ++i) {
             const AdjEvent &e = sev[i];
             step(a, e, p, tab, M);
             if (e.flags & A_ADC) {
-                const double sx = warp_sum(M[0]), sy = warp_sum(M[1]);
+                const double sx = (double)warp_sum(M[0]), sy = (double)warp_sum(M[1]);
                 if (lane == 0) {
                     const double cr = a.demod[2 * e.adc], ci = a.demod[2 * e.adc + 1];
                     atomicAdd(a.signal + 2 * e.adc, sx * cr - sy * ci);
@@ -292,48 +342,49 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_forward_kernel(const AdjArgs 
 
 // LOCAL: each thread sums its RF-parameter gradients in a local array (n_params <= ADJ_LOCAL_PARAMS)
 // and the block reduces them once at the end; otherwise every pulse reduces over the warp.
-template <bool LOCAL>
+template <typename T, bool LOCAL>
 __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     AdjEvent *sev = reinterpret_cast<AdjEvent *>(smem);
-    double *tab = reinterpret_cast<double *>(smem + sizeof(AdjEvent) * a.seg);
-    double *grf = tab + 3 * a.n_cls * blockDim.x;  // block's RF-parameter gradient
+    T *tab = reinterpret_cast<T *>(smem + sizeof(AdjEvent) * a.seg);
+    double *grf = reinterpret_cast<double *>(tab + 3 * a.n_cls * blockDim.x);  // block's RF-parameter gradient
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const SpinP p = load_spin(a, s);
+    const SpinP<T> p = load_spin<T>(a, s);
     fill_classes(a, p, tab);
     for (int q = threadIdx.x; q < a.n_params; q += blockDim.x) grf[q] = 0.0;
     const int lane = threadIdx.x & 31;
     const bool valid = s < a.n_spins;
-    double buf[ADJ_MAX_SEG][5];  // per event of the segment: state after its pulse, then the transverse state after it
-    double gl[LOCAL ? ADJ_LOCAL_PARAMS : 1];
+    const T *lam = static_cast<const T *>(a.lam);
+    T buf[ADJ_MAX_SEG][5];  // per event of the segment: state after its pulse, then the transverse state after it
+    T gl[LOCAL ? ADJ_LOCAL_PARAMS : 1];
     if constexpr (LOCAL)
-        for (int q = 0; q < a.n_params; ++q) gl[q] = 0.0;
-    double L[3] = {0.0, 0.0, 0.0};
-    double g_rho = 0.0, g_r1 = 0.0, g_r2 = 0.0;
+        for (int q = 0; q < a.n_params; ++q) gl[q] = T(0);
+    T L[3] = {T(0), T(0), T(0)};
+    T g_rho = T(0), g_r1 = T(0), g_r2 = T(0);
     const int64_t n_seg = (a.n_events + a.seg - 1) / a.seg;
     for (int64_t sg = n_seg - 1; sg >= 0; --sg) {
         const int64_t e0 = sg * a.seg;
         const int m = (int)min((int64_t)a.seg, a.n_events - e0);
         stage(a, e0, m, sev);
-        double M[3] = {0.0, 0.0, 0.0};
+        T M[3] = {T(0), T(0), T(0)};
         if (valid && a.ckpt_snap) {  // state after event sg·C − 1; the first segment starts at rest
             if (sg == 0) {
                 M[2] = p.rho;
             } else {
                 const double *ck = a.ckpt + ((sg - 1) * a.n_spins + s) * 3;
-                M[0] = ck[0];
-                M[1] = ck[1];
-                M[2] = ck[2];
+                M[0] = T(ck[0]);
+                M[1] = T(ck[1]);
+                M[2] = T(ck[2]);
             }
         } else if (valid) {
             const double *ck = a.ckpt + sg * 3 * a.n_spins;
-            M[0] = ck[s];
-            M[1] = ck[a.n_spins + s];
-            M[2] = ck[2 * a.n_spins + s];
+            M[0] = T(ck[s]);
+            M[1] = T(ck[a.n_spins + s]);
+            M[2] = T(ck[2 * a.n_spins + s]);
         }
         for (int i = 0; i < m; ++i) {
             const AdjEvent &e = sev[i];
-            if (e.flags & A_RF) apply_rf(a.rf[e.rf].R, M);
+            if (e.flags & A_RF) apply_rf(rf_at<T>(a, e.rf).R, M);
             buf[i][0] = M[0];
             buf[i][1] = M[1];
             buf[i][2] = M[2];
@@ -344,34 +395,33 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
         for (int i = m - 1; i >= 0; --i) {
             const AdjEvent &e = sev[i];
             if (e.flags & A_ADC) {  // λ += conj(d_j)·h_j
-                const double cr = a.demod[2 * e.adc], ci = -a.demod[2 * e.adc + 1];
-                const double hr = a.h[2 * e.adc], hi = a.h[2 * e.adc + 1];
-                L[0] += cr * hr - ci * hi;
-                L[1] += cr * hi + ci * hr;
+                L[0] += lam[2 * e.adc];
+                L[1] += lam[2 * e.adc + 1];
             }
-            const double Ma[3] = {buf[i][0], buf[i][1], buf[i][2]};  // state after the event's pulse
-            double wr, wi, e1;
+            const T Ma[3] = {buf[i][0], buf[i][1], buf[i][2]};  // state after the event's pulse
+            T wr, wi, e1;
             factors(e, p, tab, wr, wi, e1);
             // parameter gradients through P (λ is the adjoint after the event)
-            const double mx = buf[i][3], my = buf[i][4];  // P·M_a, transverse part
-            g_r2 += -e.dt * (L[0] * mx + L[1] * my);
-            g_r1 += -e.dt * e1 * (Ma[2] - p.rho) * L[2];
-            g_rho += (1.0 - e1) * L[2];
+            const T mx = buf[i][3], my = buf[i][4];  // P·M_a, transverse part
+            const T ndt = -dt_of(e, T(0));
+            g_r2 += ndt * (L[0] * mx + L[1] * my);
+            g_r1 += ndt * e1 * (Ma[2] - p.rho) * L[2];
+            g_rho += (T(1) - e1) * L[2];
             // λ_a = Pᵀ λ: conj(w)·λ on the transverse part, E1 on z
-            const double lax = L[0] * wr + L[1] * wi, lay = -L[0] * wi + L[1] * wr, laz = e1 * L[2];
+            const T lax = L[0] * wr + L[1] * wi, lay = L[1] * wr - L[0] * wi, laz = e1 * L[2];
             if (e.flags & A_RF) {
-                const RfEntry &rf = a.rf[e.rf];
+                const RfE<T> &rf = rf_at<T>(a, e.rf);
                 if (rf.param >= 0) {
                     // dL/dα = λ_aᵀ·(dR/dα)·M_n = λ_aᵀ·G·M_a
-                    const double *G = rf.G;
-                    const double dx = G[0] * Ma[0] + G[1] * Ma[1] + G[2] * Ma[2];
-                    const double dy = G[3] * Ma[0] + G[4] * Ma[1] + G[5] * Ma[2];
-                    const double dz = G[6] * Ma[0] + G[7] * Ma[1] + G[8] * Ma[2];
-                    const double g = lax * dx + lay * dy + laz * dz;
+                    const T *G = rf.G;
+                    const T dx = G[0] * Ma[0] + G[1] * Ma[1] + G[2] * Ma[2];
+                    const T dy = G[3] * Ma[0] + G[4] * Ma[1] + G[5] * Ma[2];
+                    const T dz = G[6] * Ma[0] + G[7] * Ma[1] + G[8] * Ma[2];
+                    const T g = lax * dx + lay * dy + laz * dz;
                     if constexpr (LOCAL) {
                         gl[rf.param] += g;
                     } else {  // reduced over the warp, then the block (shared atomics)
-                        const double gw = warp_sum(g);
+                        const double gw = (double)warp_sum(g);
                         if (lane == 0) atomicAdd(&grf[rf.param], gw);
                     }
                 }
@@ -389,7 +439,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
     g_rho += L[2];  // initial state (0, 0, M0)
     if constexpr (LOCAL) {
         for (int q = 0; q < a.n_params; ++q) {
-            const double gw = warp_sum(gl[q]);
+            const double gw = (double)warp_sum(gl[q]);
             if (lane == 0 && gw != 0.0) atomicAdd(&grf[q], gw);
         }
     }
@@ -399,9 +449,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
             if (grf[q] != 0.0) atomicAdd(a.d_rf + q, grf[q]);
     if (valid) {
         // dL/dT = dL/dR · dR/dT = −dL/dR / T², i.e. −dL/dR · R²; T = ∞ (R = 0) gives 0
-        if (a.d_rho) a.d_rho[s] = g_rho;
-        if (a.d_t1) a.d_t1[s] = -g_r1 * p.r1 * p.r1;
-        if (a.d_t2) a.d_t2[s] = -g_r2 * p.r2 * p.r2;
+        if (a.d_rho) a.d_rho[s] = (double)g_rho;
+        if (a.d_t1) a.d_t1[s] = -(double)g_r1 * p.r1d * p.r1d;
+        if (a.d_t2) a.d_t2[s] = -(double)g_r2 * p.r2d * p.r2d;
     }
 }
 
@@ -452,7 +502,11 @@ mrsim_status prepare_rf(mrsim_adjoint *adj, const double *rf_values, cudaStream_
     mrsim_ctx *ctx = adj->ctx;
     if (adj->n_params > 0 && !dev_ptr(rf_values)) return afail(ctx, MRSIM_EINVAL, "rf_values must be device memory");
     if (adj->n_rf == 0) return MRSIM_OK;
-    rf_table_kernel<<<(adj->n_rf + 127) / 128, 128, 0, st>>>(adj->d_spec, adj->n_rf, rf_values, adj->d_rf);
+    if (adj->prec == MRSIM_FP32_KAHAN)
+        rf_table_kernel<dev::dfl><<<(adj->n_rf + 127) / 128, 128, 0, st>>>(
+            adj->d_spec, adj->n_rf, rf_values, reinterpret_cast<RfE<dev::dfl> *>(adj->d_rf));
+    else
+        rf_table_kernel<double><<<(adj->n_rf + 127) / 128, 128, 0, st>>>(adj->d_spec, adj->n_rf, rf_values, adj->d_rf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("rf table: ") + cudaGetErrorString(e));
     return MRSIM_OK;
@@ -527,6 +581,8 @@ mrsim_status mrsim_adjoint_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_
         }
         const std::array<double, 4> key = {gamma * e.gx * e.dt, gamma * e.gy * e.dt, gamma * e.gz * e.dt, e.dt};
         a.dt = e.dt;
+        a.dth = (float)e.dt;
+        a.dtl = (float)(e.dt - (double)a.dth);
         if (e.dt > 0.0) {
             auto c = cls.find(key);
             if (c != cls.end()) {
@@ -644,16 +700,22 @@ mrsim_status mrsim_adjoint_forward(mrsim_adjoint *adj, const mrsim_phantom *ph, 
         f.signal = signal_out;
         f.status = ctx->d_status;
         f.snap = adj->d_ckpt;
-        const int rc = launch_fwd_f64(f, 1, ADJ_THREADS, st);
+        const int rc = adj->prec == MRSIM_FP32_KAHAN ? launch_fwd_df(f, 1, ADJ_THREADS, st)
+                                                      : launch_fwd_f64(f, 1, ADJ_THREADS, st);
         if (rc != 0) return afail(ctx, MRSIM_ECUDA, std::string("adjoint forward: ") + cudaGetErrorString((cudaError_t)rc));
         return MRSIM_OK;
     }
     AdjArgs a = adj_args(adj, ph);
     a.signal = signal_out;
     const size_t smem = adj_smem(adj, false);
-    cudaFuncSetAttribute(adj_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t grid = (ph->n + ADJ_THREADS - 1) / ADJ_THREADS;
-    adj_forward_kernel<<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    if (adj->prec == MRSIM_FP32_KAHAN) {
+        cudaFuncSetAttribute(adj_forward_kernel<dev::dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        adj_forward_kernel<dev::dfl><<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(adj_forward_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        adj_forward_kernel<double><<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
     return MRSIM_OK;
@@ -679,22 +741,55 @@ mrsim_status mrsim_adjoint_backward(mrsim_adjoint *adj, const mrsim_phantom *ph,
     }
     if (ph->n == 0) return MRSIM_OK;
     AdjArgs a = adj_args(adj, ph);
-    a.h = dl_dsignal;
+    if (adj->n_adc > 0) {  // the sample source conj(demod)·dL/ds in the recursion's arithmetic
+        if (!adj->d_lam) {
+            cudaError_t e = ctx_malloc(ctx, &adj->d_lam, 16 * (size_t)adj->n_adc);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return afail(ctx, MRSIM_ENOMEM, "adjoint sample sources");
+            }
+        }
+        const int blocks = (int)std::min<int64_t>((adj->n_adc + 255) / 256, 1024);
+        if (adj->prec == MRSIM_FP32_KAHAN)
+            lam_kernel<dev::dfl><<<blocks, 256, 0, st>>>(adj->d_demod, dl_dsignal, adj->n_adc,
+                                                        static_cast<dev::dfl *>(adj->d_lam));
+        else
+            lam_kernel<double><<<blocks, 256, 0, st>>>(adj->d_demod, dl_dsignal, adj->n_adc,
+                                                      static_cast<double *>(adj->d_lam));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("adjoint sample sources: ") + cudaGetErrorString(e));
+    }
+    a.lam = adj->d_lam;
     a.d_rho = d_rho;
     a.d_t1 = d_t1;
     a.d_t2 = d_t2;
     a.d_rf = d_rf;
     const size_t smem = adj_smem(adj, true);
     const int64_t grid = (ph->n + ADJ_THREADS - 1) / ADJ_THREADS;
-    if (adj->n_params <= ADJ_LOCAL_PARAMS) {
-        cudaFuncSetAttribute(adj_backward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        adj_backward_kernel<true><<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    auto run = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+    };
+    const bool local = adj->n_params <= ADJ_LOCAL_PARAMS;
+    if (adj->prec == MRSIM_FP32_KAHAN) {
+        if (local) run(adj_backward_kernel<dev::dfl, true>);
+        else run(adj_backward_kernel<dev::dfl, false>);
     } else {
-        cudaFuncSetAttribute(adj_backward_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        adj_backward_kernel<false><<<(unsigned)grid, ADJ_THREADS, smem, st>>>(a);
+        if (local) run(adj_backward_kernel<double, true>);
+        else run(adj_backward_kernel<double, false>);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(ctx, MRSIM_ECUDA, std::string("adjoint backward: ") + cudaGetErrorString(e));
+    return MRSIM_OK;
+}
+
+mrsim_status mrsim_adjoint_set_precision(mrsim_adjoint *adj, mrsim_precision prec) {
+    if (!adj) return MRSIM_EINVAL;
+    if (prec == MRSIM_FP32) return afail(adj->ctx, MRSIM_EUNSUPPORTED, "the adjoint has no plain float32 recursion");
+    if (prec != MRSIM_FP64 && prec != MRSIM_FP32_KAHAN) return afail(adj->ctx, MRSIM_EINVAL, "unknown precision");
+    adj->prec = prec;
+    adj->last_ph = nullptr;  // checkpoints of the other arithmetic are not reused
+    adj->last_n = -1;
     return MRSIM_OK;
 }
 
@@ -705,7 +800,8 @@ mrsim_status mrsim_simulate_adjoint(mrsim_ctx *ctx, const mrsim_phantom *ph, con
     if (!ph || !seq || ph->ctx != ctx || seq->ctx != ctx)
         return afail(ctx, MRSIM_EINVAL, "NULL phantom / sequence or another context");
     if (!normalize_precision(prec)) return afail(ctx, MRSIM_EINVAL, "unknown precision");
-    if (prec != MRSIM_FP64) return afail(ctx, MRSIM_EUNSUPPORTED, "the adjoint runs in float64 only (MRSIM_FP64)");
+    if (prec == MRSIM_FP32)
+        return afail(ctx, MRSIM_EUNSUPPORTED, "the adjoint runs in float64 or the compensated precision, not float32");
     const HostProgram &hp = *seq->prog;
     const int64_t n_ev = hp.n_events, n_adc = hp.host.n_adc, n = ph->n;
     if (n_adc > 0 && !dl_dsignal) return afail(ctx, MRSIM_EINVAL, "dl_dsignal is NULL");
@@ -725,6 +821,7 @@ mrsim_status mrsim_simulate_adjoint(mrsim_ctx *ctx, const mrsim_phantom *ph, con
     mrsim_status rs = mrsim_adjoint_create(ctx, n_ev, hp.events.data(), hp.gamma, d_rf_flip ? rp.data() : nullptr,
                                            n_params, ckpt_every, &adj);
     if (rs != MRSIM_OK) return rs;
+    if (prec == MRSIM_FP32_KAHAN) mrsim_adjoint_set_precision(adj, prec);
     // one device block for the flips, the signal and every host-side input or output:
     // [flips | signal | dL/ds | d_rho | d_t1 | d_t2 | d_rf]
     const bool h_dl = n_adc > 0 && !dev_ptr(dl_dsignal);
@@ -795,6 +892,7 @@ void mrsim_adjoint_destroy(mrsim_adjoint *adj) {
     cudaFree(adj->d_cls);
     cudaFree(adj->d_demod);
     cudaFree(adj->d_ckpt);
+    cudaFree(adj->d_lam);
     mrsim_sequence_destroy(adj->fwd);
     delete adj;
 }

@@ -44,7 +44,7 @@ EXPORTS = (
     "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
     "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate", "mrsim_simulate_adjoint",
     "mrsim_sequence_num_pulses", "mrsim_simulate_fields", "mrsim_phantom_set_b0_direction", "mrsim_fields_create",
-    "mrsim_fields_num_adc", "mrsim_fields_destroy",
+    "mrsim_fields_num_adc", "mrsim_fields_destroy", "mrsim_adjoint_set_precision",
 )
 
 
@@ -134,6 +134,7 @@ def lib():
             "mrsim_adjoint_forward": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "mrsim_adjoint_backward": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "mrsim_adjoint_destroy": (None, [vp]),
+            "mrsim_adjoint_set_precision": (ctypes.c_int, [vp, ctypes.c_int]),
             "mrsim_simulate_adjoint": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, i32, vp, vp, vp, vp, vp, vp]),
             "mrsim_sequence_num_pulses": (i64, [vp]),
             "mrsim_simulate_fields": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp, i64]),
@@ -487,6 +488,10 @@ class Adjoint:
         self.h = h
         self.n_params = int(n_params)
         self.n_adc = int(lib().mrsim_adjoint_num_adc(h))
+
+    def set_precision(self, precision: int):
+        """FP64 (default) or FP32_KAHAN (the recursion in double-float pairs on the FP32 pipe)."""
+        self.ctx.check(lib().mrsim_adjoint_set_precision(self.h, int(precision)))
 
     def forward(self, phantom: Phantom, rf_values=None, out=None, stream=None):
         self.ctx.check(lib().mrsim_adjoint_forward(self.h, phantom.h, _ptr(rf_values), _stream(stream), _ptr(out)))

@@ -53,8 +53,10 @@ def shaped_case(seed, n_sp, n_rf=16, n_tr=3, n_read=8):
     return ph, ev, np.array(params, dtype=np.int32), rf, rng
 
 
-def gpu_grads(M, ctx, torch, ph, ev, params, rf, h, ckpt=64):
+def gpu_grads(M, ctx, torch, ph, ev, params, rf, h, ckpt=64, precision=None):
     adj = M.Adjoint(ctx, ev, W.GAMMA_BAR, params, len(rf), ckpt_every=ckpt)
+    if precision is not None:
+        adj.set_precision(precision)
     P = M.Phantom.from_workload_phantom(ctx, ph)
     dev = torch.device("cuda:0")
     rfd = torch.from_numpy(np.asarray(rf, dtype=np.float64)).to(dev)
@@ -244,7 +246,53 @@ def test_simulate_adjoint_one_shot(M, ctx, torch, oracle_mod, seed, n_sp, ckpt, 
     # without RF gradients, only the spin parameters
     d_rho, d_t1, d_t2, d_rf = M.simulate_adjoint(ctx, P, seq, h, rf=False)
     assert d_rf is None and rel(d_rho, g[0]) <= 1e-10 and rel(d_t2, g[2]) <= 1e-10
-    for prec in (M.FP32, M.FP32_KAHAN):
-        with pytest.raises(M.MrsimError) as e:
-            M.simulate_adjoint(ctx, P, seq, h, precision=prec)
-        assert e.value.status == M.Status.EUNSUPPORTED
+    with pytest.raises(M.MrsimError) as e:
+        M.simulate_adjoint(ctx, P, seq, h, precision=M.FP32)
+    assert e.value.status == M.Status.EUNSUPPORTED
+    # the compensated precision of the same call
+    gk = M.simulate_adjoint(ctx, P, seq, h, precision=M.FP32_KAHAN, ckpt_every=ckpt)
+    for a, b in zip(gk, g):
+        assert rel(a, b) <= 1e-10
+
+
+
+@pytest.mark.parametrize("seed,n_sp,ckpt,n_rf,n_par", [(20, 300, 64, 16, 16), (21, 129, 7, 16, 256),
+                                                      (22, 40, 64, 16, 1100)])
+def test_compensated_adjoint_matches_oracle_gradient(M, ctx, torch, oracle_mod, seed, n_sp, ckpt, n_rf, n_par):
+    """The adjoint recursion in the compensated precision (double-float pairs on the FP32 pipe):
+    forward signal and gradients in M0, T1, T2 and the learnable flips against the oracle at the
+    float64 adjoint's bars, on every path (local / warp-reduced RF gradients, library forward /
+    the adjoint's own forward)."""
+    ph, ev, params, rf, rng = shaped_case(seed, n_sp, n_rf=n_rf)
+    rf = np.concatenate([rf, rng.uniform(-1.0, 1.0, n_par - n_rf)])
+    sig_ref = oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf)
+    h = 2 * (sig_ref - 0.9 * oracle_mod.simulate_rf(ph, ev, W.GAMMA_BAR, params, rf * 1.1))
+    g = oracle_mod.gradient(ph, ev, W.GAMMA_BAR, h, params, rf, list(range(len(rf))))
+    sig, (a_rho, a_t1, a_t2), a_rf = gpu_grads(M, ctx, torch, ph, ev, params, rf, h, ckpt, M.FP32_KAHAN)
+    assert rel(sig, sig_ref) <= 1e-11
+    for a, b in zip((a_rho, a_t1, a_t2, a_rf), g):
+        assert rel(a, b) <= 1e-10
+
+
+def test_compensated_adjoint_config5(M, ctx, torch, oracle_mod):
+    """C5 in the compensated precision: signal and spin gradients against the float64 adjoint on
+    the full phantom, and a sampled spin set against the oracle's gradient."""
+    w, tgt, rf0 = W.config5()
+    ev = w.sequence.events
+    params = np.full(len(ev), -1, dtype=np.int32)
+    idx = W.rf_event_index(w.sequence)
+    params[idx] = np.tile(np.arange(len(rf0), dtype=np.int32), idx.size // len(rf0))
+    h = np.random.default_rng(5).normal(size=w.sequence.n_adc) * (1 + 1j)
+    res = {}
+    for prec in (M.FP64, M.FP32_KAHAN):
+        res[prec] = gpu_grads(M, ctx, torch, w.phantom, ev, params, rf0, h, 64, prec)
+    s64, g64, r64 = res[M.FP64]
+    sk, gk, rk = res[M.FP32_KAHAN]
+    assert rel(sk, s64) <= 1e-11
+    for a, b in zip(gk, g64):
+        assert rel(a, b) <= 1e-10
+    assert rel(rk, r64) <= 1e-10
+    sel = np.sort(np.random.default_rng(6).choice(w.phantom.n, 300, replace=False))
+    go = oracle_mod.gradient(w.phantom.subset(sel), ev, W.GAMMA_BAR, h, params, rf0, [])
+    for a, b in zip(gk, go[:3]):
+        assert rel(a[sel], b) <= 1e-10
