@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) 
     const float m0 = live ? (float)a.params[P_RHO * np + si] : 0.0f;
     const float r1 = (float)a.params[P_R1 * np + si], r2 = (float)a.params[P_R2 * np + si];
     const float b0 = (float)a.b0;
+    const float bn0 = (float)(a.b0 * nd[0]), bn1 = (float)(a.b0 * nd[1]), bn2 = (float)(a.b0 * nd[2]);  // B0 n
     float M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
     float S0 = M0, S1 = M1, S2 = M2;  // state at the start of the current run
     const FieldEv32 *src = static_cast<const FieldEv32 *>(a.ev);
@@ -290,11 +291,13 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) 
                 }
                 const float p = n0 * bx + n1 * by + n2 * bz;
                 const float qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
-                const float ux = b0 * n0 + bx, uy = b0 * n1 + by, uz = b0 * n2 + bz;
-                const float un = sqrtf(ux * ux + uy * uy + uz * uz);
-                acc.c += e.gdt2pi * ((qx * qx + qy * qy + qz * qz) / (un + b0 + p));
+                const float ux = bn0 + bx, uy = bn1 + by, uz = bn2 + bz;
+                const float uu = ux * ux + uy * uy + uz * uz;
+                const float inv = rsqrtf(uu);  // 1/|u|
+                const float un = uu * inv;
+                // the remainder r²/(|u| + B0 + n.b) is a second-order correction: a fast quotient suffices
+                acc.c += e.gdt2pi * __fdividef(qx * qx + qy * qy + qz * qz, un + b0 + p);
                 const float t = acc.value();
-                const float inv = 1.0f / un;
                 const float hx = ux * inv, hy = uy * inv, hz = uz * inv;
                 float sn, cs;
                 sincospif(2.0f * t, &sn, &cs);

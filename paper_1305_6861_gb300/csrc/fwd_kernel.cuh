@@ -820,7 +820,12 @@ struct Spins {
     }
 
     __device__ __forceinline__ void load_train(int k, P &ca, P &sa, P &nsa) const {
-        if constexpr (F64) {
+        if constexpr (std::is_same<R, dfl>::value) {  // converted once at set-up: (cos, sin) as pairs
+            const dfl *t = reinterpret_cast<const dfl *>(train) + 2 * k;
+            ca = t[0];
+            sa = t[1];
+            nsa = -t[1];
+        } else if constexpr (F64) {
             const double2 t = reinterpret_cast<const double2 *>(train)[k];
             ca = t.x;
             sa = t.y;
@@ -994,7 +999,16 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
     PV *prm = reinterpret_cast<PV *>(smem + L.prm);
     unsigned *bmax = reinterpret_cast<unsigned *>(smem + L.flag + 16);
     sp.cw = cw;
-    if constexpr (F64) {
+    if constexpr (std::is_same<R, dfl>::value) {  // double-float: the table as pairs, converted once here
+        dfl *tr = reinterpret_cast<dfl *>(smem + L.train);
+        const double2 *gtr = reinterpret_cast<const double2 *>(P.train);
+        for (int q = sp.tid; q < P.n_train; q += sp.nthr) {
+            const double2 t = gtr[q];
+            tr[2 * q] = dfl(t.x);
+            tr[2 * q + 1] = dfl(t.y);
+        }
+        sp.train = tr;
+    } else if constexpr (F64) {
         double2 *tr = reinterpret_cast<double2 *>(smem + L.train);
         const double2 *gtr = reinterpret_cast<const double2 *>(P.train);
         for (int q = sp.tid; q < P.n_train; q += sp.nthr) tr[q] = gtr[q];
