@@ -600,7 +600,7 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
     if (ph->n > 0 && !sens) return fail(ctx, MRSIM_EINVAL, "NULL sensitivities");
     if (n_adc > 0 && !signal_out) return fail(ctx, MRSIM_EINVAL, "NULL signal buffer");
     const bool fp64 = prec == MRSIM_FP64;
-    const int threads = 128, k = fp64 ? 1 : 2;
+    const int threads = 128, k = fp64 ? 1 : coil_spins_per_thread_f32(n_coils);
     const Program &P = fp64 ? seq->p64 : seq->p32;
     if (fwd_smem_bytes(fp64, P, k, threads) > (size_t)ctx->max_smem_optin)
         return fail(ctx, MRSIM_EUNSUPPORTED, "shared memory of this program exceeds the device limit");

@@ -53,11 +53,13 @@ int fwd_regs_f32(int k) {
     }
 }
 
+int coil_spins_per_thread_f32(int n_coils) { return n_coils > 2 ? 4 : 2; }
+
 int launch_fwd_coils_f32(const FwdArgs &a, int threads, void *stream) {
     if (a.n_coils <= 1) return dev::launch_one<float, 2, 512, 1>(a, threads, stream);
     if (a.n_coils <= 2) return dev::launch_one<float, 2, 512, 2>(a, threads, stream);
-    if (a.n_coils <= 4) return dev::launch_one<float, 2, 512, 4>(a, threads, stream);
-    if (a.n_coils <= MAX_COILS) return dev::launch_one<float, 2, 512, 8>(a, threads, stream);
+    if (a.n_coils <= 4) return dev::launch_one<float, 4, 256, 4>(a, threads, stream);
+    if (a.n_coils <= MAX_COILS) return dev::launch_one<float, 4, 256, 8>(a, threads, stream);
     return (int)cudaErrorInvalidValue;
 }
 

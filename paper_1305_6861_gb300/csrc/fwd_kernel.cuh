@@ -314,7 +314,7 @@ struct Spins {
     P u[NP], v[NP], mz[NP], rho[NP];  // transverse part in the pulse frame, longitudinal, M0
     P wr[NP], wi[NP], nwi[NP];        // cached phasor class (nwi = −wi, kept for the pairs only)
     P e1v[NP];                        // cached T1 class ε1
-    P cre[NCR][NP], cim[NCR][NP], cnim[NCR][NP];  // coils: sensitivities C = cre + j·cim (cnim = −cim)
+    P cre[NCR][NP], cim[NCR][NP];  // coils: sensitivities C = cre + j·cim (−cim formed on the integer pipe)
     int win_base, win_end;
     int n_coils;          // receive coils stored (<= NCR)
     int64_t coil_stride;  // doubles between two coils' signals (2·n_adc)
@@ -607,11 +607,11 @@ struct Spins {
     // ---- receive coils ----------------------------------------------------------------------
     // the thread's spins weighted with coil c's sensitivities: Σ_k C_ck·(u_k + j v_k)
     __device__ __forceinline__ void coil_sum(int c, R &sx, R &sy) {
-        P re = vfma(v[0], cnim[c][0], vmul(u[0], cre[c][0]));
+        P re = vfma(v[0], vneg(cim[c][0]), vmul(u[0], cre[c][0]));
         P im = vfma(u[0], cim[c][0], vmul(v[0], cre[c][0]));
 #pragma unroll
         for (int q = 1; q < NP; ++q) {
-            re = vfma(v[q], cnim[c][q], vfma(u[q], cre[c][q], re));
+            re = vfma(v[q], vneg(cim[c][q]), vfma(u[q], cre[c][q], re));
             im = vfma(u[q], cim[c][q], vfma(v[q], cre[c][q], im));
         }
         sx = hsum(re);
@@ -1153,7 +1153,7 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
         for (int c = 0; c < SP::NCR; ++c) {
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                R re[LN], im[LN], nim[LN];
+                R re[LN], im[LN];
 #pragma unroll
                 for (int h = 0; h < LN; ++h) {
                     const int64_t s = sp.base + sp.li(q + h * NP);
@@ -1163,11 +1163,10 @@ __device__ __forceinline__ bool run_tile(const FwdArgs &a, int64_t tile, unsigne
                     if (c < a.n_coils && s < a.n_spins) w = sens[(int64_t)c * np + s];
                     re[h] = w.x;
                     im[h] = w.y;
-                    nim[h] = -w.y;
                 }
                 set_lanes(sp.cre[c][q], re);
                 set_lanes(sp.cim[c][q], im);
-                set_lanes(sp.cnim[c][q], nim);
+
             }
         }
     }

@@ -203,6 +203,8 @@ int check_kt_params(int64_t n, const double *t1, const double *t2, const double 
 // thread, float64 with 1; coil rows per sample are a.n_coils rounded up to 1, 2, 4 or 8.
 constexpr int MAX_COILS = MRSIM_MAX_COILS;
 int launch_fwd_coils_f32(const FwdArgs &a, int threads, void *stream);
+// spins per thread of the float32 coil kernel for n_coils receive coils
+int coil_spins_per_thread_f32(int n_coils);
 int launch_fwd_coils_f64(const FwdArgs &a, int threads, void *stream);
 // Registers per thread of a kernel instance (0 if the shape does not exist).
 int fwd_regs(int mode, int spins_per_thread);
