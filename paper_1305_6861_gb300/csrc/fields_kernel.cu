@@ -38,6 +38,7 @@ namespace {
 
 constexpr int FIELD_THREADS = 128;
 constexpr int FIELD_CHUNK = 32;
+constexpr int FIELD_K32 = 2;  // spins per thread of the float32 kernel
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
 // FF_RUN_START: the first event of a run of identical free intervals (same Δt, G, transverse
@@ -85,24 +86,19 @@ struct FieldArgs {
 };
 
 // Phase accumulator in cycles for products of (hi, lo) pairs: per product the integer part of
-// the leading product is removed exactly (|ah bh| < 2^22) and the fractional parts are summed
-// without rounding error (two-sum, the error goes to the small part); the leading product's own
-// rounding error (an FMA) and the cross terms go to the small part.  value() rounds once.
+// the leading product is removed exactly (|ah bh| < 2^22, the fractional part is exact), its
+// rounding error (an FMA) and the cross terms go to a small part; value() adds the fractional
+// parts and the small part and reduces the sum to [-1/2, 1/2].  The sum of a few fractional
+// parts rounds at ulp(2) = 2^-22 cycles at most, below the float32 rounding of the turn itself.
 struct PhaseAcc {
     float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add_exact(float f) {  // s + f with its rounding error kept in c
-        const float t = s + f;
-        const float bb = t - s;
-        c += (s - (t - bb)) + (f - bb);
-        s = t - rintf(t);
-    }
     __device__ __forceinline__ void add_product(float ah, float al, float bh, float bl) {
         const float p = ah * bh;
         c += fmaf(ah, bh, -p) + fmaf(ah, bl, al * bh);
-        add_exact(p - rintf(p));
+        s += p - rintf(p);
     }
     __device__ __forceinline__ float value() const {
-        const float t = s + c;
+        const float t = (s - rintf(s)) + c;
         return t - rintf(t);
     }
 };
@@ -223,34 +219,109 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
     }
 }
 
+// One spin of the float32 kernel: its constants (set up in float64) and its state.
+struct FSpin32 {
+    float wh[9], wl[9];  // n_j x_d as (hi, lo): j = z, x, y (the order of the moments k_j), d = x, y, z
+    float dfh, dfl;      // Δf as (hi, lo)
+    float x, y, z, n0, n1, n2, bn0, bn1, bn2, m0, r1, r2;
+    float M0, M1, M2, S0, S1, S2;  // state, and the state at the start of the current run
+    bool live;
+
+    __device__ __forceinline__ void setup(const FieldArgs &a, int64_t s) {
+        live = s < a.n_spins;
+        const int64_t si = live ? s : 0;
+        const int64_t np = a.n_pad;
+        const double xd[3] = {a.params[P_X * np + si], a.params[P_Y * np + si], a.params[P_Z * np + si]};
+        const double nd[3] = {a.ndir ? a.ndir[3 * si] : 0.0, a.ndir ? a.ndir[3 * si + 1] : 0.0,
+                              a.ndir ? a.ndir[3 * si + 2] : 1.0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            split(nd[2] * xd[d], wh[d], wl[d]);
+            split(nd[0] * xd[d], wh[3 + d], wl[3 + d]);
+            split(nd[1] * xd[d], wh[6 + d], wl[6 + d]);
+        }
+        split(a.params[P_DF * np + si], dfh, dfl);
+        x = (float)xd[0];
+        y = (float)xd[1];
+        z = (float)xd[2];
+        n0 = (float)nd[0];
+        n1 = (float)nd[1];
+        n2 = (float)nd[2];
+        bn0 = (float)(a.b0 * nd[0]);  // B0 n
+        bn1 = (float)(a.b0 * nd[1]);
+        bn2 = (float)(a.b0 * nd[2]);
+        m0 = live ? (float)a.params[P_RHO * np + si] : 0.0f;
+        r1 = (float)a.params[P_R1 * np + si];
+        r2 = (float)a.params[P_R2 * np + si];
+        M0 = S0 = m0 * n0;
+        M1 = S1 = m0 * n1;
+        M2 = S2 = m0 * n2;
+    }
+
+    __device__ __forceinline__ void event(const FieldEv32 &e, float b0) {
+        if (e.flags & FF_RF) {
+            const float t0 = e.R[0] * M0 + e.R[1] * M1 + e.R[2] * M2;
+            const float t1 = e.R[3] * M0 + e.R[4] * M1 + e.R[5] * M2;
+            const float t2 = e.R[6] * M0 + e.R[7] * M1 + e.R[8] * M2;
+            M0 = t0;
+            M1 = t1;
+            M2 = t2;
+        }
+        if (e.flags & FF_RUN_START) {
+            S0 = M0;
+            S1 = M1;
+            S2 = M2;
+        } else if (e.flags & FF_RUN) {
+            M0 = S0;
+            M1 = S1;
+            M2 = S2;
+        }
+        if (!(e.flags & FF_FREE)) return;
+        float bx = 0.0f, by = 0.0f;
+        const float bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
+        // phase in cycles: n_z (k_z . x) [+ n_x (k_x . x) + n_y (k_y . x)] + Δf Δt + remainder
+        PhaseAcc acc;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
+        acc.add_product(dfh, dfl, e.dth, e.dtl);
+        if (e.flags & FF_TRANSVERSE) {
+            bx = e.gt[0] * x + e.gt[1] * y + e.gt[2] * z;
+            by = e.gt[3] * x + e.gt[4] * y + e.gt[5] * z;
+#pragma unroll
+            for (int q = 3; q < 9; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
+        }
+        const float p = n0 * bx + n1 * by + n2 * bz;
+        const float qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
+        const float ux = bn0 + bx, uy = bn1 + by, uz = bn2 + bz;
+        const float uu = ux * ux + uy * uy + uz * uz;
+        const float inv = rsqrtf(uu);  // 1/|u|
+        const float un = uu * inv;
+        // the remainder r²/(|u| + B0 + n.b) is a second-order correction: a fast quotient suffices
+        acc.c += e.gdt2pi * __fdividef(qx * qx + qy * qy + qz * qz, un + b0 + p);
+        const float t = acc.value();
+        const float hx = ux * inv, hy = uy * inv, hz = uz * inv;
+        float sn, cs;
+        sincospif(2.0f * t, &sn, &cs);
+        const float e1m = expm1f(-e.dt * r1), e2 = expf(-e.dt * r2);
+        const float par = M0 * hx + M1 * hy + M2 * hz;
+        const float px = M0 - par * hx, py = M1 - par * hy, pz = M2 - par * hz;
+        const float cx = hy * pz - hz * py, cy = hz * px - hx * pz, cz = hx * py - hy * px;
+        const float along = par + e1m * (par - m0);
+        M0 = e2 * (cs * px - sn * cx) + along * hx;
+        M1 = e2 * (cs * py - sn * cy) + along * hy;
+        M2 = e2 * (cs * pz - sn * cz) + along * hz;
+    }
+};
+
+// K spins per thread: spin k of thread t in block b is (b·K + k)·blockDim + t (coalesced per k).
+template <int K>
 __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) {
     __shared__ FieldEv32 evs[FIELD_CHUNK];
     __shared__ float win[2 * FIELD_CHUNK];
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = s < a.n_spins;
-    const int64_t si = live ? s : 0;
-    const int64_t np = a.n_pad;
-    // set-up in float64: positions, direction and the products n_j x_d as (hi, lo) pairs
-    const double xd[3] = {a.params[P_X * np + si], a.params[P_Y * np + si], a.params[P_Z * np + si]};
-    const double nd[3] = {a.ndir ? a.ndir[3 * si] : 0.0, a.ndir ? a.ndir[3 * si + 1] : 0.0,
-                          a.ndir ? a.ndir[3 * si + 2] : 1.0};
-    float wh[9], wl[9];  // j = z, x, y (the order of the moments k_j), d = x, y, z
+    FSpin32 sp[K];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        split(nd[2] * xd[d], wh[d], wl[d]);
-        split(nd[0] * xd[d], wh[3 + d], wl[3 + d]);
-        split(nd[1] * xd[d], wh[6 + d], wl[6 + d]);
-    }
-    float dfh, dfl;
-    split(a.params[P_DF * np + si], dfh, dfl);
-    const float x = (float)xd[0], y = (float)xd[1], z = (float)xd[2];
-    const float n0 = (float)nd[0], n1 = (float)nd[1], n2 = (float)nd[2];
-    const float m0 = live ? (float)a.params[P_RHO * np + si] : 0.0f;
-    const float r1 = (float)a.params[P_R1 * np + si], r2 = (float)a.params[P_R2 * np + si];
+    for (int k = 0; k < K; ++k) sp[k].setup(a, ((int64_t)blockIdx.x * K + k) * blockDim.x + threadIdx.x);
     const float b0 = (float)a.b0;
-    const float bn0 = (float)(a.b0 * nd[0]), bn1 = (float)(a.b0 * nd[1]), bn2 = (float)(a.b0 * nd[2]);  // B0 n
-    float M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
-    float S0 = M0, S1 = M1, S2 = M2;  // state at the start of the current run
     const FieldEv32 *src = static_cast<const FieldEv32 *>(a.ev);
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
@@ -258,63 +329,19 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) 
         __syncthreads();
         for (int i = 0; i < nc; ++i) {
             const FieldEv32 &e = evs[i];
-            if (e.flags & FF_RF) {
-                const float t0 = e.R[0] * M0 + e.R[1] * M1 + e.R[2] * M2;
-                const float t1 = e.R[3] * M0 + e.R[4] * M1 + e.R[5] * M2;
-                const float t2 = e.R[6] * M0 + e.R[7] * M1 + e.R[8] * M2;
-                M0 = t0;
-                M1 = t1;
-                M2 = t2;
-            }
-            if (e.flags & FF_RUN_START) {
-                S0 = M0;
-                S1 = M1;
-                S2 = M2;
-            } else if (e.flags & FF_RUN) {
-                M0 = S0;
-                M1 = S1;
-                M2 = S2;
-            }
-            if (e.flags & FF_FREE) {
-                float bx = 0.0f, by = 0.0f;
-                const float bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
-                // phase in cycles: n_z (k_z . x) [+ n_x (k_x . x) + n_y (k_y . x)] + Δf Δt + remainder
-                PhaseAcc acc;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
-                acc.add_product(dfh, dfl, e.dth, e.dtl);
-                if (e.flags & FF_TRANSVERSE) {
-                    bx = e.gt[0] * x + e.gt[1] * y + e.gt[2] * z;
-                    by = e.gt[3] * x + e.gt[4] * y + e.gt[5] * z;
-#pragma unroll
-                    for (int q = 3; q < 9; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
-                }
-                const float p = n0 * bx + n1 * by + n2 * bz;
-                const float qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
-                const float ux = bn0 + bx, uy = bn1 + by, uz = bn2 + bz;
-                const float uu = ux * ux + uy * uy + uz * uz;
-                const float inv = rsqrtf(uu);  // 1/|u|
-                const float un = uu * inv;
-                // the remainder r²/(|u| + B0 + n.b) is a second-order correction: a fast quotient suffices
-                acc.c += e.gdt2pi * __fdividef(qx * qx + qy * qy + qz * qz, un + b0 + p);
-                const float t = acc.value();
-                const float hx = ux * inv, hy = uy * inv, hz = uz * inv;
-                float sn, cs;
-                sincospif(2.0f * t, &sn, &cs);
-                const float e1m = expm1f(-e.dt * r1), e2 = expf(-e.dt * r2);
-                const float par = M0 * hx + M1 * hy + M2 * hz;
-                const float px = M0 - par * hx, py = M1 - par * hy, pz = M2 - par * hz;
-                const float cx = hy * pz - hz * py, cy = hz * px - hx * pz, cz = hx * py - hy * px;
-                const float along = par + e1m * (par - m0);
-                M0 = e2 * (cs * px - sn * cx) + along * hx;
-                M1 = e2 * (cs * py - sn * cy) + along * hy;
-                M2 = e2 * (cs * pz - sn * cz) + along * hz;
-            }
+            for (int k = 0; k < K; ++k) sp[k].event(e, b0);
             if (e.flags & FF_ADC) {
-                float sr = M0 * e.dem[0] + M1 * e.dem[1];
-                float sim = M1 * e.dem[0] - M0 * e.dem[1];
-                sr = warp_sum(live ? sr : 0.0f);
-                sim = warp_sum(live ? sim : 0.0f);
+                float sr = 0.0f, sim = 0.0f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (sp[k].live) {
+                        sr += sp[k].M0 * e.dem[0] + sp[k].M1 * e.dem[1];
+                        sim += sp[k].M1 * e.dem[0] - sp[k].M0 * e.dem[1];
+                    }
+                }
+                sr = warp_sum(sr);
+                sim = warp_sum(sim);
                 if ((threadIdx.x & 31) == 0) {
                     atomicAdd(&win[2 * e.slot], sr);
                     atomicAdd(&win[2 * e.slot + 1], sim);
@@ -583,9 +610,13 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
         a.ndir = ph->d_dir;
         a.b0 = f->b0;
         a.signal = sig;
-        const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
-        if (f64) fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
-        else fields_kernel_f32<<<grid, FIELD_THREADS, 0, st>>>(a);
+        if (f64) {
+            const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
+            fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
+        } else {
+            const unsigned grid = (unsigned)((ph->n + FIELD_K32 * FIELD_THREADS - 1) / (FIELD_K32 * FIELD_THREADS));
+            fields_kernel_f32<FIELD_K32><<<grid, FIELD_THREADS, 0, st>>>(a);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && host_sig) {

@@ -103,3 +103,16 @@ def test_traffic_records_follow_the_kernel_source(bench):
         assert "--clock-control none" in e["source"]
     # the hash ignores comments and whitespace only
     assert len(bench.kernel_source_sha()) == 16 and bench.kernel_source_sha() != bench.kernel_source_sha(bench.KT_SOURCES)
+
+
+def test_field_work_model(bench):
+    """Formulation model of the non-parallel-field step: a free interval 73 (+42 with transverse
+    components), a pulse 9, a sample 4; events of zero length cost no free step."""
+    rows = [(1e-5, 0, 0, 0, 0.3, 0, 0, 0.0),    # pulse + free: 9 + 73
+            (1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0),   # free (transverse) + sample: 73 + 42 + 4
+            (0.0, 0, 0, 0, 0.2, 0, 1, 0.0)]     # pulse + sample, no interval: 9 + 4
+    ev = W.make_events(rows)
+    gt = np.zeros((3, 6))
+    gt[1, 0] = 1e-3
+    assert bench.field_ops_per_spin(ev, gt) == (9 + 73) + (73 + 42 + 4) + (9 + 4)
+    assert bench.field_ops_per_spin(ev, None) == (9 + 73) + (73 + 4) + (9 + 4)
