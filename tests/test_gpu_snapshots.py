@@ -60,7 +60,7 @@ def test_snapshots_match_prefix_states(M, ctx, oracle_mod, case):
     ref_sig, _ = oracle_mod.simulate(ph, ev, W.GAMMA_BAR)
     refs = [oracle_mod.simulate(ph, ev[: e + 1], W.GAMMA_BAR, want_signal=False, want_state=True)[1] for e in snaps]
     tol64 = phase_floor(ph, ev, W.GAMMA_BAR)
-    for prec in (M.FP64, M.FP32):
+    for prec in (M.FP64, M.FP32, M.FP32_KAHAN):
         out = np.zeros((len(snaps), ph.n, 3))
         sig = M.simulate(ctx, p, s_snap, prec, snapshots=out)
         plain = M.simulate(ctx, p, s_plain, prec)
@@ -72,6 +72,11 @@ def test_snapshots_match_prefix_states(M, ctx, oracle_mod, case):
             assert rel_l2(sig, ref_sig) <= tol64
             for q in range(len(snaps)):
                 assert np.max(np.abs(out[q] - refs[q])) <= tol64 * max(1.0, np.abs(refs[q]).max()), q
+        elif prec == M.FP32_KAHAN:  # compensated: the float64 bars, at least 1e-10
+            tolk = max(1e-10, tol64)
+            assert rel_l2(sig, ref_sig) <= tolk
+            for q in range(len(snaps)):
+                assert np.max(np.abs(out[q] - refs[q])) <= tolk * max(1.0, np.abs(refs[q]).max()), q
         else:
             assert rel_l2(sig, ref_sig) <= 2e-5
             for q in range(len(snaps)):

@@ -36,11 +36,12 @@ def _pairs():
     return out
 
 
-@pytest.mark.parametrize("prec,tol,tol_oracle", [("fp32", 1e-6, 2e-5), ("fp64", 1e-12, 1e-12)])
+@pytest.mark.parametrize("prec,tol,tol_oracle", [("fp32", 1e-6, 2e-5), ("fp64", 1e-12, 1e-12),
+                                                 ("fp32_kahan", 1e-12, 1e-10)])
 def test_static_scratch_batch_matches_batch_api(mrsim_lib, oracle_mod, prec, tol, tol_oracle):
     torch = pytest.importorskip("torch")
     M = mrsim_lib
-    p = M.FP32 if prec == "fp32" else M.FP64
+    p = {"fp32": M.FP32, "fp64": M.FP64, "fp32_kahan": M.FP32_KAHAN}[prec]
     ctx = M.Context(0)
     pairs = _pairs()
     oracle_refs = [oracle_mod.signal(ph, seq) for ph, seq in pairs]
