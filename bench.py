@@ -749,21 +749,61 @@ def run_kt(args):
     return 0
 
 
-# Non-parallel fields: FP32 lane-operations of the formulation per spin and event.  An event with
-# a duration: the gradient field G.x (3), n.b (3), b - (n.b) n (3) and its square (3), u = B0 n + b
-# (3), |u|^2 (3), the remainder r^2/(|u| + B0 + n.b) (2), h = u/|u| (3), the phase from four
-# float-float products (6 each) and its reduction (3), the turn about h with T2 and T1 (the part
-# along h 3, across it 3, h x M (6), the new state 9, the T1 term 2); with transverse components 6
-# more for (gtx.x, gty.x) and six more products (36).  A pulse is the 3x3 rotation (9), a sample
-# the demodulated value (4).  Transcendentals (sin/cos, exp, sqrt, division) are not counted.
-FIELD_OPS_FREE, FIELD_OPS_TRANSVERSE, FIELD_OPS_RF, FIELD_OPS_ADC = 73, 42, 9, 4
+# Non-parallel fields: FP32 lane-operations per spin and event of the cached-map formulation.  An
+# interval computed from its record (a new interval, or an anchored step of a run): the gradient
+# field G.x (3), n.b (3), b - (n.b) n (3) and its square (3), u = B0 n + b (3), |u|^2 (3), the
+# remainder r^2/(|u| + B0 + n.b) (2), h = u/|u| (3), the phase from four float-float products (6
+# each) and its reduction (3), the map A = E2 cos(th) (I - h h^T) - E2 sin(th) [h]x + E1 h h^T and
+# c = M0 (1 - E1) h (22) and its application (9): 81; with transverse components 6 more for
+# (gtx.x, gty.x) and six more products (36).  An interval equal to the one whose map the spin
+# holds: the map (9).  A pulse is the 3x3 rotation (9), a sample the demodulated value (4).
+# Transcendentals (sin/cos, exp, square root, division) are not counted.
+FIELD_OPS_COMPUTED, FIELD_OPS_TRANSVERSE, FIELD_OPS_MAP, FIELD_OPS_RF, FIELD_OPS_ADC = 81, 42, 9, 9, 4
+FIELD_ANCHOR = 16  # every 16th step of a run of equal intervals, and its last, is computed from the run's start
+
+
+def field_event_classes(events, g_transverse):
+    """Which events compute their interval from the record (`computed`) and which apply the map the
+    spin holds (`repeat`), as the field records mark them: a run is a sequence of equal free
+    intervals (equal dt, G and transverse components) without pulses; its FIELD_ANCHOR-th steps
+    and its last are computed from the run's start; any other interval equal to the last computed
+    one (not counting anchored steps) repeats it."""
+    n = len(events)
+    gt = np.zeros((n, 6)) if g_transverse is None else np.asarray(g_transverse, dtype=float)
+    key = np.concatenate([np.stack([events["dt"], events["gx"], events["gy"], events["gz"]], axis=1), gt], axis=1)
+    free = events["dt"] > 0
+    runnable = free & (events["rf_flip"] == 0)
+    run = np.zeros(n, dtype=np.int64)
+    for i in range(n):
+        if runnable[i]:
+            run[i] = run[i - 1] + 1 if i > 0 and run[i - 1] > 0 and np.array_equal(key[i], key[i - 1]) else 1
+    length = np.zeros(n, dtype=np.int64)
+    for i in range(n - 1, -1, -1):
+        if run[i] > 0:
+            length[i] = length[i + 1] if i + 1 < n and run[i + 1] == run[i] + 1 else run[i]
+    anchor = (run > 1) & ((run % FIELD_ANCHOR == 0) | (run == length))
+    computed = np.zeros(n, dtype=bool)
+    repeat = np.zeros(n, dtype=bool)
+    cached = None
+    for i in range(n):
+        if not free[i]:
+            continue
+        if anchor[i]:
+            computed[i] = True
+        elif cached is not None and np.array_equal(key[i], cached):
+            repeat[i] = True
+        else:
+            computed[i] = True
+            cached = key[i]
+    return computed, repeat
 
 
 def field_ops_per_spin(events, g_transverse) -> int:
-    free = events["dt"] > 0
+    computed, repeat = field_event_classes(events, g_transverse)
     tr = np.any(g_transverse != 0, axis=1) if g_transverse is not None else np.zeros(len(events), dtype=bool)
-    return int(FIELD_OPS_FREE * np.count_nonzero(free) + FIELD_OPS_TRANSVERSE * np.count_nonzero(free & tr)
-               + FIELD_OPS_RF * np.count_nonzero(events["rf_flip"] != 0) + FIELD_OPS_ADC * np.count_nonzero(events["adc"]))
+    return int(FIELD_OPS_COMPUTED * np.count_nonzero(computed) + FIELD_OPS_TRANSVERSE * np.count_nonzero(computed & tr)
+               + FIELD_OPS_MAP * np.count_nonzero(repeat) + FIELD_OPS_RF * np.count_nonzero(events["rf_flip"] != 0)
+               + FIELD_OPS_ADC * np.count_nonzero(events["adc"]))
 
 
 def run_fields(args):
@@ -815,7 +855,9 @@ def run_fields(args):
             "roofline": dict(fp64_roofline(achieved), kernel_ms=ms, ops_per_spin_step=ops / w.spin_steps)
             if prec == M.FP64 else fp32_roofline(achieved, ck, traffic=None, kernel_ms=ms,
                                                   ops_per_spin_step=ops / w.spin_steps,
-                                                  op_model="formulation arithmetic per event, transcendentals not counted"),
+                                                  op_model="cached-map formulation per event (a computed interval 81 (+42 "
+                                                           "transverse), a repeated one 9, pulse 9, sample 4), "
+                                                           "transcendentals not counted"),
             "gpu_launches": args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id()}
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample, and the GPU on the same spins
         cb = cpu_baseline_fields(w, args.cpu_seconds)

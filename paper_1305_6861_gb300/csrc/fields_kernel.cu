@@ -11,6 +11,13 @@
 //   M <- E2 (cos θ M⊥ - sin θ h × M⊥) + (E1 (M.h) + M0 (1 - E1)) h,      M⊥ = M - (M.h) h
 // i.e. Eqs. 3.5/3.14 in the frame turned to h.  Every spin starts at M0 n.
 //
+// The turn of one interval is an affine map M <- A M + c with
+//   A = E2 cos θ (I - h hᵀ) - E2 sin θ [h]x + E1 h hᵀ,   c = M0 (1 - E1) h,
+// which depends on the event only through its free interval (Δt, G, transverse components).  Each
+// spin keeps the map of the last interval it computed, and an event whose interval equals that one
+// (every sub-pulse of a shaped pulse after the first, every step of a readout) applies it with nine
+// FMAs instead of recomputing the field, its direction, the phase and the exponentials.
+//
 // Layout: one thread per spin (its state, direction and position in registers), 128 threads per
 // block; the event records are staged through shared memory in chunks of FIELD_CHUNK by the
 // whole block; each sample's spin sum is a warp butterfly, a shared-memory window per chunk and
@@ -42,12 +49,18 @@ constexpr int FIELD_K32 = 2;  // spins per thread of the float32 kernel
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
 // FF_RUN_START: the first event of a run of identical free intervals (same Δt, G, transverse
-// components, no pulse): its state before the step is kept; FF_RUN: a later event of the run,
-// whose record holds the run's interval so far (j·Δt and its moments), applied to the kept state.
-// The turn and the relaxation of j equal intervals are one turn by jθ with E^j (the axis h is the
-// same for all of them), so a run is computed from its start instead of step by step and the
-// rounding of one interval's rotation does not repeat j times.
-enum FieldFlags : int32_t { FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8, FF_RUN_START = 16, FF_RUN = 32 };
+// components, no pulse): its state before the step is kept.  FF_RUN: an anchored later event of
+// the run, whose record holds the run's interval so far (j·Δt and its moments), applied to the kept
+// state.  The turn and the relaxation of j equal intervals are one turn by jθ with E^j (the axis h
+// is the same for all of them), so an anchored step is computed from the run's start and the
+// rounding of one interval's turn does not repeat j times.  Every FIELD_ANCHOR-th step of a run and
+// its last step are anchored; the steps between apply the cached one-interval map (FF_SAME), so
+// the repeated rounding reaches at most FIELD_ANCHOR - 1 steps and never the state a run hands on.
+// FF_SAME: the free interval equals the one whose map the spin holds; apply it.
+enum FieldFlags : int32_t {
+    FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8, FF_RUN_START = 16, FF_RUN = 32, FF_SAME = 64
+};
+constexpr int64_t FIELD_ANCHOR = 16;
 
 // float64 record: 22 doubles + 4 ints = 192 bytes
 struct alignas(16) FieldEv64 {
@@ -57,7 +70,10 @@ struct alignas(16) FieldEv64 {
     double gdt;         // γ Δt [rad/(T)]  (in a run: of the run's interval so far)
     double dt;          // Δt [s]          (likewise)
     double dem[2];      // cos, sin of the receiver phase
-    int32_t flags, adc, slot, pad;
+    int32_t flags;
+    int32_t adc;        // index of the event's sample, or of the next sample if it takes none
+    int32_t slot;       // position of the sample within the chunk of FIELD_CHUNK events
+    int32_t nslot;      // samples in the event's chunk
 };
 static_assert(sizeof(FieldEv64) == 192, "FieldEv64 layout");
 
@@ -71,7 +87,7 @@ struct alignas(16) FieldEv32 {
     float gdt2pi;        // γ/2π Δt [cycles/T] (for the small remainder)
     float dt;
     float dem[2];
-    int32_t flags, adc, slot, pad;
+    int32_t flags, adc, slot, nslot;  // as in FieldEv64
 };
 static_assert(sizeof(FieldEv32) == 192, "FieldEv32 layout");
 
@@ -106,6 +122,38 @@ struct PhaseAcc {
 __host__ __device__ __forceinline__ void split(double v, float &hi, float &lo) {
     hi = (float)v;
     lo = (float)(v - (double)hi);
+}
+
+// The map of one turn about h by θ with E2 = e2 across and E1 = 1 + e1m along h, in A and c.
+template <typename T>
+__device__ __forceinline__ void turn_map(T hx, T hy, T hz, T cs, T sn, T e1m, T e2, T m0, T (&A)[9], T (&c)[3]) {
+    const T a = e2 * cs, d = e2 * sn;
+    const T b = (T(1) + e1m) - a;  // E1 - E2 cos θ: the coefficient of h hᵀ
+    const T bx = b * hx, by = b * hy, bz = b * hz;
+    const T xy = bx * hy, xz = bx * hz, yz = by * hz;
+    A[0] = bx * hx + a;
+    A[1] = xy + d * hz;
+    A[2] = xz - d * hy;
+    A[3] = xy - d * hz;
+    A[4] = by * hy + a;
+    A[5] = yz + d * hx;
+    A[6] = xz + d * hy;
+    A[7] = yz - d * hx;
+    A[8] = bz * hz + a;
+    const T w = -e1m * m0;  // M0 (1 - E1)
+    c[0] = w * hx;
+    c[1] = w * hy;
+    c[2] = w * hz;
+}
+
+template <typename T>
+__device__ __forceinline__ void apply_map(const T (&A)[9], const T (&c)[3], T &M0, T &M1, T &M2) {
+    const T t0 = A[0] * M0 + A[1] * M1 + A[2] * M2 + c[0];
+    const T t1 = A[3] * M0 + A[4] * M1 + A[5] * M2 + c[1];
+    const T t2 = A[6] * M0 + A[7] * M1 + A[8] * M2 + c[2];
+    M0 = t0;
+    M1 = t1;
+    M2 = t2;
 }
 
 template <typename T>
@@ -154,6 +202,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
     const double b0 = a.b0;
     double M0 = m0 * n0, M1 = m0 * n1, M2 = m0 * n2;
     double S0 = M0, S1 = M1, S2 = M2;  // state at the start of the current run
+    double A[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0}, cv[3] = {0.0, 0.0, 0.0};  // cached map
     const FieldEv64 *src = static_cast<const FieldEv64 *>(a.ev);
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
@@ -178,7 +227,9 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
                 M1 = S1;
                 M2 = S2;
             }
-            if (e.flags & FF_FREE) {
+            if ((e.flags & FF_FREE) && (e.flags & FF_SAME)) {
+                apply_map(A, cv, M0, M1, M2);
+            } else if (e.flags & FF_FREE) {
                 double bx = 0.0, by = 0.0;
                 const double bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
                 if (e.flags & FF_TRANSVERSE) {
@@ -195,13 +246,15 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
                 double sn, cs;
                 sincos(e.gdt * excess + dw * e.dt, &sn, &cs);
                 const double e1m = expm1(-e.dt * r1), e2 = exp(-e.dt * r2);
-                const double par = M0 * hx + M1 * hy + M2 * hz;
-                const double px = M0 - par * hx, py = M1 - par * hy, pz = M2 - par * hz;
-                const double cx = hy * pz - hz * py, cy = hz * px - hx * pz, cz = hx * py - hy * px;
-                const double along = par + e1m * (par - m0);  // E1 M.h + M0 (1 - E1)
-                M0 = e2 * (cs * px - sn * cx) + along * hx;
-                M1 = e2 * (cs * py - sn * cy) + along * hy;
-                M2 = e2 * (cs * pz - sn * cz) + along * hz;
+                double B[9], cb[3];
+                turn_map(hx, hy, hz, cs, sn, e1m, e2, m0, B, cb);
+                apply_map(B, cb, M0, M1, M2);
+                if (!(e.flags & FF_RUN)) {  // an anchored step's map spans j intervals: not cached
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) A[q] = B[q];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) cv[q] = cb[q];
+                }
             }
             if (e.flags & FF_ADC) {
                 double sr = M0 * e.dem[0] + M1 * e.dem[1];
@@ -219,16 +272,18 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
     }
 }
 
-// One spin of the float32 kernel: its constants (set up in float64) and its state.
+// One spin of the float32 kernel: its constants (set up in float64), its state and the map of the
+// last interval it computed.  A spin past the end of the phantom has M0 = 0: its state stays zero
+// (every map is linear with c = M0 (1 - E1) h = 0), so it needs no test.
 struct FSpin32 {
     float wh[9], wl[9];  // n_j x_d as (hi, lo): j = z, x, y (the order of the moments k_j), d = x, y, z
     float dfh, dfl;      // Δf as (hi, lo)
-    float x, y, z, n0, n1, n2, bn0, bn1, bn2, m0, r1, r2;
+    float x, y, z, n0, n1, n2, m0, r1, r2;
     float M0, M1, M2, S0, S1, S2;  // state, and the state at the start of the current run
-    bool live;
+    float A[9], cv[3];             // the map of the last computed interval
 
     __device__ __forceinline__ void setup(const FieldArgs &a, int64_t s) {
-        live = s < a.n_spins;
+        const bool live = s < a.n_spins;
         const int64_t si = live ? s : 0;
         const int64_t np = a.n_pad;
         const double xd[3] = {a.params[P_X * np + si], a.params[P_Y * np + si], a.params[P_Z * np + si]};
@@ -247,36 +302,30 @@ struct FSpin32 {
         n0 = (float)nd[0];
         n1 = (float)nd[1];
         n2 = (float)nd[2];
-        bn0 = (float)(a.b0 * nd[0]);  // B0 n
-        bn1 = (float)(a.b0 * nd[1]);
-        bn2 = (float)(a.b0 * nd[2]);
         m0 = live ? (float)a.params[P_RHO * np + si] : 0.0f;
         r1 = (float)a.params[P_R1 * np + si];
         r2 = (float)a.params[P_R2 * np + si];
         M0 = S0 = m0 * n0;
         M1 = S1 = m0 * n1;
         M2 = S2 = m0 * n2;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) A[q] = (q % 4 == 0) ? 1.0f : 0.0f;
+        cv[0] = cv[1] = cv[2] = 0.0f;
     }
 
-    __device__ __forceinline__ void event(const FieldEv32 &e, float b0) {
-        if (e.flags & FF_RF) {
-            const float t0 = e.R[0] * M0 + e.R[1] * M1 + e.R[2] * M2;
-            const float t1 = e.R[3] * M0 + e.R[4] * M1 + e.R[5] * M2;
-            const float t2 = e.R[6] * M0 + e.R[7] * M1 + e.R[8] * M2;
-            M0 = t0;
-            M1 = t1;
-            M2 = t2;
-        }
-        if (e.flags & FF_RUN_START) {
-            S0 = M0;
-            S1 = M1;
-            S2 = M2;
-        } else if (e.flags & FF_RUN) {
-            M0 = S0;
-            M1 = S1;
-            M2 = S2;
-        }
-        if (!(e.flags & FF_FREE)) return;
+    __device__ __forceinline__ void rf(const float (&R)[9]) {
+        const float t0 = R[0] * M0 + R[1] * M1 + R[2] * M2;
+        const float t1 = R[3] * M0 + R[4] * M1 + R[5] * M2;
+        const float t2 = R[6] * M0 + R[7] * M1 + R[8] * M2;
+        M0 = t0;
+        M1 = t1;
+        M2 = t2;
+    }
+
+    // An interval computed from its record: the field, its direction, the phase and the
+    // exponentials; the map is applied and, unless the step is anchored (its record spans j
+    // intervals of a run), kept for the events that repeat the interval.
+    __device__ __forceinline__ void full(const FieldEv32 &e, float b0, int flags) {
         float bx = 0.0f, by = 0.0f;
         const float bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
         // phase in cycles: n_z (k_z . x) [+ n_x (k_x . x) + n_y (k_y . x)] + Δf Δt + remainder
@@ -284,7 +333,7 @@ struct FSpin32 {
 #pragma unroll
         for (int q = 0; q < 3; ++q) acc.add_product(e.kh[q], e.kl[q], wh[q], wl[q]);
         acc.add_product(dfh, dfl, e.dth, e.dtl);
-        if (e.flags & FF_TRANSVERSE) {
+        if (flags & FF_TRANSVERSE) {
             bx = e.gt[0] * x + e.gt[1] * y + e.gt[2] * z;
             by = e.gt[3] * x + e.gt[4] * y + e.gt[5] * z;
 #pragma unroll
@@ -292,64 +341,115 @@ struct FSpin32 {
         }
         const float p = n0 * bx + n1 * by + n2 * bz;
         const float qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
-        const float ux = bn0 + bx, uy = bn1 + by, uz = bn2 + bz;
+        const float ux = b0 * n0 + bx, uy = b0 * n1 + by, uz = b0 * n2 + bz;
         const float uu = ux * ux + uy * uy + uz * uz;
         const float inv = rsqrtf(uu);  // 1/|u|
         const float un = uu * inv;
         // the remainder r²/(|u| + B0 + n.b) is a second-order correction: a fast quotient suffices
         acc.c += e.gdt2pi * __fdividef(qx * qx + qy * qy + qz * qz, un + b0 + p);
         const float t = acc.value();
-        const float hx = ux * inv, hy = uy * inv, hz = uz * inv;
         float sn, cs;
         sincospif(2.0f * t, &sn, &cs);
         const float e1m = expm1f(-e.dt * r1), e2 = expf(-e.dt * r2);
-        const float par = M0 * hx + M1 * hy + M2 * hz;
-        const float px = M0 - par * hx, py = M1 - par * hy, pz = M2 - par * hz;
-        const float cx = hy * pz - hz * py, cy = hz * px - hx * pz, cz = hx * py - hy * px;
-        const float along = par + e1m * (par - m0);
-        M0 = e2 * (cs * px - sn * cx) + along * hx;
-        M1 = e2 * (cs * py - sn * cy) + along * hy;
-        M2 = e2 * (cs * pz - sn * cz) + along * hz;
+        float B[9], cb[3];
+        turn_map(ux * inv, uy * inv, uz * inv, cs, sn, e1m, e2, m0, B, cb);
+        apply_map(B, cb, M0, M1, M2);
+        if (!(flags & FF_RUN)) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) A[q] = B[q];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cv[q] = cb[q];
+        }
     }
 };
 
-// K spins per thread: spin k of thread t in block b is (b·K + k)·blockDim + t (coalesced per k).
-template <int K>
-__global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f32(FieldArgs a) {
+// K spins per thread, T threads per block: spin k of thread t in block b is (b·K + k)·T + t
+// (coalesced per k).  Each event's flags are tested once for all K spins.  Samples: each thread
+// writes the sum over its spins of each sample of the chunk to its own column of a shared window
+// (no exchange between threads while the events run); after the chunk, each of the 2·nslot rows (a
+// sample's real or imaginary part) is summed over the T columns (64 entries per thread, in four
+// partial sums) and added to the signal in float64.  The rows are padded to T + T/64 floats so
+// that the threads summing different rows at the same time read different banks.
+template <int K, int T>
+__global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
+    static_assert(T == 64 || T == 128, "one or two threads per window row");
+    constexpr int PER_ROW = T / 64, STRIDE = T + PER_ROW;
     __shared__ FieldEv32 evs[FIELD_CHUNK];
-    __shared__ float win[2 * FIELD_CHUNK];
+    __shared__ float win[2 * FIELD_CHUNK * STRIDE];
+    const int t = threadIdx.x;
     FSpin32 sp[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) sp[k].setup(a, ((int64_t)blockIdx.x * K + k) * blockDim.x + threadIdx.x);
+    for (int k = 0; k < K; ++k) sp[k].setup(a, ((int64_t)blockIdx.x * K + k) * T + t);
     const float b0 = (float)a.b0;
     const FieldEv32 *src = static_cast<const FieldEv32 *>(a.ev);
+    const int row = t / PER_ROW, part = t % PER_ROW;
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
-        const int nc = stage_chunk(src, c0, a.n_events, evs, win);
+        const int nc = (int)min((int64_t)FIELD_CHUNK, a.n_events - c0);
+        {
+            const int4 *s4 = reinterpret_cast<const int4 *>(src + c0);
+            int4 *d4 = reinterpret_cast<int4 *>(evs);
+            const int words = nc * (int)(sizeof(FieldEv32) / sizeof(int4));
+            for (int i = t; i < words; i += T) d4[i] = s4[i];
+        }
         __syncthreads();
         for (int i = 0; i < nc; ++i) {
             const FieldEv32 &e = evs[i];
+            const int flags = e.flags;
+            if (flags & FF_RF) {
+                float R[9];
 #pragma unroll
-            for (int k = 0; k < K; ++k) sp[k].event(e, b0);
-            if (e.flags & FF_ADC) {
+                for (int q = 0; q < 9; ++q) R[q] = e.R[q];
+#pragma unroll
+                for (int k = 0; k < K; ++k) sp[k].rf(R);
+            }
+            if (flags & FF_RUN_START) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    sp[k].S0 = sp[k].M0;
+                    sp[k].S1 = sp[k].M1;
+                    sp[k].S2 = sp[k].M2;
+                }
+            } else if (flags & FF_RUN) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    sp[k].M0 = sp[k].S0;
+                    sp[k].M1 = sp[k].S1;
+                    sp[k].M2 = sp[k].S2;
+                }
+            }
+            if (flags & FF_SAME) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) apply_map(sp[k].A, sp[k].cv, sp[k].M0, sp[k].M1, sp[k].M2);
+            } else if (flags & FF_FREE) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) sp[k].full(e, b0, flags);
+            }
+            if (flags & FF_ADC) {
+                const float d0 = e.dem[0], d1 = e.dem[1];
                 float sr = 0.0f, sim = 0.0f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    if (sp[k].live) {
-                        sr += sp[k].M0 * e.dem[0] + sp[k].M1 * e.dem[1];
-                        sim += sp[k].M1 * e.dem[0] - sp[k].M0 * e.dem[1];
-                    }
+                    sr += sp[k].M0 * d0 + sp[k].M1 * d1;
+                    sim += sp[k].M1 * d0 - sp[k].M0 * d1;
                 }
-                sr = warp_sum(sr);
-                sim = warp_sum(sim);
-                if ((threadIdx.x & 31) == 0) {
-                    atomicAdd(&win[2 * e.slot], sr);
-                    atomicAdd(&win[2 * e.slot + 1], sim);
-                }
+                float *w = win + (2 * e.slot) * STRIDE + t;
+                w[0] = sr;
+                w[STRIDE] = sim;
             }
         }
         __syncthreads();
-        flush_chunk(evs, nc, win, a.signal);
+        const int nslot = evs[0].nslot, adc0 = evs[0].adc;
+        float v = 0.0f;
+        if (row < 2 * nslot) {
+            const float *w = win + row * STRIDE + part;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int q = 0; q < 64; ++q) acc[q & 3] += w[PER_ROW * q];
+            v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        }
+        if (PER_ROW == 2) v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if (part == 0 && row < 2 * nslot) atomicAdd(&a.signal[2 * (int64_t)adc0 + row], (double)v);
     }
 }
 
@@ -473,33 +573,50 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     } catch (const std::bad_alloc &) {
         return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
     }
-    int64_t j = 0, run = 0;  // run: index of the event within its run of identical free intervals (0: none)
-    int slot = 0;
     static const double zero6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    auto same_interval = [&](int64_t i, int64_t k) {  // equal Δt, G and transverse components
+        const mrsim_event &u = events[i], &v = events[k];
+        const double *gi = g_transverse ? g_transverse + 6 * i : zero6, *gk = g_transverse ? g_transverse + 6 * k : zero6;
+        bool same = u.dt == v.dt && u.gx == v.gx && u.gy == v.gy && u.gz == v.gz;
+        for (int q = 0; q < 6 && same; ++q) same = gi[q] == gk[q];
+        return same;
+    };
+    // run[i]: position of event i in its run of identical free intervals without pulses (1 = the
+    // first, 0 = none); len[i]: the length of that run
+    std::vector<int64_t> run, len;
+    try {
+        run.assign((size_t)n_events, 0);
+        len.assign((size_t)n_events, 0);
+    } catch (const std::bad_alloc &) {
+        return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    }
+    for (int64_t i = 0; i < n_events; ++i) {
+        const mrsim_event &v = events[i];
+        if (v.rf_flip == 0.0 && v.dt > 0.0) run[i] = (i > 0 && run[i - 1] > 0 && same_interval(i - 1, i)) ? run[i - 1] + 1 : 1;
+    }
+    for (int64_t i = n_events - 1; i >= 0; --i)
+        if (run[i] > 0) len[i] = (i + 1 < n_events && run[i + 1] == run[i] + 1) ? len[i + 1] : run[i];
+    int64_t j = 0, cached = -1;  // cached: the event whose one-interval map the spins hold
+    int slot = 0;
     for (int64_t i = 0; i < n_events; ++i) {
         if (i % FIELD_CHUNK == 0) slot = 0;
         const mrsim_event &v = events[i];
         const double *gt = g_transverse ? g_transverse + 6 * i : nullptr;
         const bool tr = gt && (gt[0] != 0.0 || gt[1] != 0.0 || gt[2] != 0.0 || gt[3] != 0.0 || gt[4] != 0.0 || gt[5] != 0.0);
-        if (v.rf_flip != 0.0 || !(v.dt > 0.0)) {
-            run = 0;
-        } else if (run > 0) {
-            const mrsim_event &u = events[i - 1];
-            const double *gp = g_transverse ? g_transverse + 6 * (i - 1) : zero6, *gc = gt ? gt : zero6;
-            bool same = u.dt == v.dt && u.gx == v.gx && u.gy == v.gy && u.gz == v.gz;
-            for (int q = 0; q < 6 && same; ++q) same = gp[q] == gc[q];
-            run = same ? run + 1 : 1;
-        } else {
-            run = 1;
-        }
-        const double span = v.dt * (double)std::max<int64_t>(run, 1);  // the run's interval so far
+        const bool free = v.dt > 0.0;
+        const int64_t pos = run[(size_t)i];
+        const bool anchor = pos > 1 && (pos % FIELD_ANCHOR == 0 || pos == len[(size_t)i]);
+        const bool same = free && !anchor && cached >= 0 && same_interval(cached, i);
+        if (free && !anchor && !same) cached = i;
+        const double span = anchor ? v.dt * (double)pos : v.dt;  // an anchored step: the run's interval so far
         const int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
-                              (v.dt > 0.0 ? FF_FREE : 0) | (run == 1 ? FF_RUN_START : 0) | (run > 1 ? FF_RUN : 0);
+                              (free ? FF_FREE : 0) | (pos == 1 ? FF_RUN_START : 0) | (anchor ? FF_RUN : 0) |
+                              (same ? FF_SAME : 0);
         double R[9];
         rf_matrix(v.rf_flip, v.rf_phase, R);
         const double g[3] = {v.gx, v.gy, v.gz};
         const double dem[2] = {std::cos(v.adc_phase), std::sin(v.adc_phase)};
-        const int32_t adc = v.adc ? (int32_t)j : -1, sl = v.adc ? slot : 0;
+        const int32_t adc = (int32_t)j, sl = v.adc ? slot : 0;
         FieldEv64 &r = e64[(size_t)i];
         FieldEv32 &f = e32[(size_t)i];
         for (int q = 0; q < 9; ++q) {
@@ -531,11 +648,12 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
         r.flags = f.flags = flags;
         r.adc = f.adc = adc;
         r.slot = f.slot = sl;
-        r.pad = f.pad = 0;
         if (v.adc) {
             ++j;
             ++slot;
         }
+        if ((i + 1) % FIELD_CHUNK == 0 || i + 1 == n_events)  // the chunk is complete: its sample count
+            for (int64_t k = i / FIELD_CHUNK * FIELD_CHUNK; k <= i; ++k) e64[(size_t)k].nslot = e32[(size_t)k].nslot = slot;
     }
     cudaSetDevice(ctx->device);
     mrsim_fields *fh = new (std::nothrow) mrsim_fields();
@@ -614,8 +732,22 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
             const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
             fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
         } else {
-            const unsigned grid = (unsigned)((ph->n + FIELD_K32 * FIELD_THREADS - 1) / (FIELD_K32 * FIELD_THREADS));
-            fields_kernel_f32<FIELD_K32><<<grid, FIELD_THREADS, 0, st>>>(a);
+            // 64 or 128 threads per block, whichever fills the last wave of resident blocks better
+            const int64_t blocks128 = (ph->n + FIELD_K32 * 128 - 1) / (FIELD_K32 * 128);
+            const int64_t blocks64 = (ph->n + FIELD_K32 * 64 - 1) / (FIELD_K32 * 64);
+            int r128 = 0, r64 = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r128, fields_kernel_f32<FIELD_K32, 128>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r64, fields_kernel_f32<FIELD_K32, 64>, 64, 0);
+            auto waves = [&](int64_t blocks, int per_sm) {  // time in units of one full wave of 64-thread work
+                const int64_t cap = std::max<int64_t>(1, (int64_t)per_sm * ctx->num_sms);
+                return (double)((blocks + cap - 1) / cap);
+            };
+            // a wave of 128-thread blocks holds r128 blocks per SM, each twice the spins of a 64-thread block
+            const double w128 = waves(blocks128, r128) * 2.0 * r128, w64 = waves(blocks64, r64) * r64;
+            if (r64 > 0 && (r128 <= 0 || w64 < w128))
+                fields_kernel_f32<FIELD_K32, 64><<<(unsigned)blocks64, 64, 0, st>>>(a);
+            else
+                fields_kernel_f32<FIELD_K32, 128><<<(unsigned)blocks128, 128, 0, st>>>(a);
         }
         e = cudaGetLastError();
     }

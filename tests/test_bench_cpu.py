@@ -106,13 +106,22 @@ def test_traffic_records_follow_the_kernel_source(bench):
 
 
 def test_field_work_model(bench):
-    """Formulation model of the non-parallel-field step: a free interval 73 (+42 with transverse
-    components), a pulse 9, a sample 4; events of zero length cost no free step."""
-    rows = [(1e-5, 0, 0, 0, 0.3, 0, 0, 0.0),    # pulse + free: 9 + 73
-            (1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0),   # free (transverse) + sample: 73 + 42 + 4
+    """Cached-map model of the non-parallel-field step: an interval computed from its record 81
+    (+42 with transverse components), an interval equal to the held one 9, a pulse 9, a sample 4;
+    events of zero length cost no free step; the anchored steps of a run are computed."""
+    rows = [(1e-5, 0, 0, 0, 0.3, 0, 0, 0.0),    # pulse + new interval: 9 + 81
+            (1e-5, 0, 0, 0, 0.3, 0, 0, 0.0),    # pulse + the same interval: 9 + 9
+            (1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0),   # new interval (transverse) + sample: 81 + 42 + 4
             (0.0, 0, 0, 0, 0.2, 0, 1, 0.0)]     # pulse + sample, no interval: 9 + 4
     ev = W.make_events(rows)
-    gt = np.zeros((3, 6))
-    gt[1, 0] = 1e-3
-    assert bench.field_ops_per_spin(ev, gt) == (9 + 73) + (73 + 42 + 4) + (9 + 4)
-    assert bench.field_ops_per_spin(ev, None) == (9 + 73) + (73 + 4) + (9 + 4)
+    gt = np.zeros((4, 6))
+    gt[2, 0] = 1e-3
+    assert bench.field_ops_per_spin(ev, gt) == (9 + 81) + (9 + 9) + (81 + 42 + 4) + (9 + 4)
+    # without transverse components the third interval is still new (its G differs)
+    assert bench.field_ops_per_spin(ev, None) == (9 + 81) + (9 + 9) + (81 + 4) + (9 + 4)
+    # a readout run of 40 equal intervals: the first computed, steps 16 and 32 and the last (40)
+    # anchored, the other 36 repeat the first
+    ro = W.make_events([(1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0)] * 40)
+    computed, repeat = bench.field_event_classes(ro, None)
+    assert np.flatnonzero(computed).tolist() == [0, 15, 31, 39] and np.count_nonzero(repeat) == 36
+    assert bench.field_ops_per_spin(ro, None) == 4 * 81 + 36 * 9 + 40 * 4
