@@ -62,6 +62,13 @@ enum FieldFlags : int32_t {
 };
 constexpr int64_t FIELD_ANCHOR = 16;
 
+// The two kinds of event that make up most sequences, which the float32 kernel runs in loops of
+// their own: a sample step of a readout (the held map, then the sample) and a sub-pulse of a
+// shaped pulse (the pulse, then the held map).  Any other event takes the general path.
+constexpr int32_t KIND_MASK = FF_RF | FF_ADC | FF_FREE | FF_RUN_START | FF_RUN | FF_SAME;
+constexpr int32_t KIND_READ = FF_ADC | FF_FREE | FF_SAME;
+constexpr int32_t KIND_TRAIN = FF_RF | FF_FREE | FF_SAME;
+
 // float64 record: 22 doubles + 4 ints = 192 bytes
 struct alignas(16) FieldEv64 {
     double R[9];        // Eq. 3.19 rotation (row-major) when FF_RF
@@ -88,6 +95,8 @@ struct alignas(16) FieldEv32 {
     float dt;
     float dem[2];
     int32_t flags, adc, slot, nslot;  // as in FieldEv64
+    int32_t seg;                      // events from this one on, within the chunk, of the same kind
+    int32_t pad;
 };
 static_assert(sizeof(FieldEv32) == 192, "FieldEv32 layout");
 
@@ -148,9 +157,9 @@ __device__ __forceinline__ void turn_map(T hx, T hy, T hz, T cs, T sn, T e1m, T 
 
 template <typename T>
 __device__ __forceinline__ void apply_map(const T (&A)[9], const T (&c)[3], T &M0, T &M1, T &M2) {
-    const T t0 = A[0] * M0 + A[1] * M1 + A[2] * M2 + c[0];
-    const T t1 = A[3] * M0 + A[4] * M1 + A[5] * M2 + c[1];
-    const T t2 = A[6] * M0 + A[7] * M1 + A[8] * M2 + c[2];
+    const T t0 = A[2] * M2 + (A[1] * M1 + (A[0] * M0 + c[0]));  // three multiply-adds per row
+    const T t1 = A[5] * M2 + (A[4] * M1 + (A[3] * M0 + c[1]));
+    const T t2 = A[8] * M2 + (A[7] * M1 + (A[6] * M0 + c[2]));
     M0 = t0;
     M1 = t1;
     M2 = t2;
@@ -314,12 +323,19 @@ struct FSpin32 {
     }
 
     __device__ __forceinline__ void rf(const float (&R)[9]) {
-        const float t0 = R[0] * M0 + R[1] * M1 + R[2] * M2;
-        const float t1 = R[3] * M0 + R[4] * M1 + R[5] * M2;
-        const float t2 = R[6] * M0 + R[7] * M1 + R[8] * M2;
+        const float t0 = R[2] * M2 + (R[1] * M1 + R[0] * M0);
+        const float t1 = R[5] * M2 + (R[4] * M1 + R[3] * M0);
+        const float t2 = R[8] * M2 + (R[7] * M1 + R[6] * M0);
         M0 = t0;
         M1 = t1;
         M2 = t2;
+    }
+
+    // the held map applied to (u0, u1, u2), written to (o0, o1, o2)
+    __device__ __forceinline__ void map(float u0, float u1, float u2, float &o0, float &o1, float &o2) const {
+        o0 = A[2] * u2 + (A[1] * u1 + (A[0] * u0 + cv[0]));
+        o1 = A[5] * u2 + (A[4] * u1 + (A[3] * u0 + cv[1]));
+        o2 = A[8] * u2 + (A[7] * u1 + (A[6] * u0 + cv[2]));
     }
 
     // An interval computed from its record: the field, its direction, the phase and the
@@ -363,13 +379,30 @@ struct FSpin32 {
     }
 };
 
+template <int K>
+__device__ __forceinline__ void write_sample(float *win, int stride, int slot, float d0, float d1, const float (&u0)[K],
+                                             const float (&u1)[K]) {
+    float sr = u0[0] * d0 + u1[0] * d1, sim = u1[0] * d0 - u0[0] * d1;
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        sr = u1[k] * d1 + (u0[k] * d0 + sr);
+        sim = u1[k] * d0 + (sim - u0[k] * d1);
+    }
+    float *w = win + (2 * slot) * stride;
+    w[0] = sr;
+    w[stride] = sim;
+}
+
 // K spins per thread, T threads per block: spin k of thread t in block b is (b·K + k)·T + t
-// (coalesced per k).  Each event's flags are tested once for all K spins.  Samples: each thread
-// writes the sum over its spins of each sample of the chunk to its own column of a shared window
-// (no exchange between threads while the events run); after the chunk, each of the 2·nslot rows (a
-// sample's real or imaginary part) is summed over the T columns (64 entries per thread, in four
-// partial sums) and added to the signal in float64.  The rows are padded to T + T/64 floats so
-// that the threads summing different rows at the same time read different banks.
+// (coalesced per k).  The events of a chunk run as segments: a run of readout samples (the host
+// marks its length) applies the held map in a loop unrolled by two, whose halves alternate between
+// the state and a second set of registers; a run of sub-pulses turns and maps each spin with no
+// copy; any other event takes the general path, its flags tested once for all K spins.  Samples:
+// each thread writes the sum over its spins of each sample of the chunk to its own column of a
+// shared window (no exchange between threads while the events run); after the chunk, each of the
+// 2·nslot rows (a sample's real or imaginary part) is summed over the T columns (64 entries per
+// thread, in four partial sums) and added to the signal in float64.  The rows are padded to
+// T + T/64 floats so that the threads summing different rows at the same time read different banks.
 template <int K, int T>
 __global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
     static_assert(T == 64 || T == 128, "one or two threads per window row");
@@ -383,6 +416,7 @@ __global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
     const float b0 = (float)a.b0;
     const FieldEv32 *src = static_cast<const FieldEv32 *>(a.ev);
     const int row = t / PER_ROW, part = t % PER_ROW;
+    float *wcol = win + t;
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
         const int nc = (int)min((int64_t)FIELD_CHUNK, a.n_events - c0);
@@ -393,49 +427,104 @@ __global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
             for (int i = t; i < words; i += T) d4[i] = s4[i];
         }
         __syncthreads();
-        for (int i = 0; i < nc; ++i) {
+        int i = 0;
+        while (i < nc) {
             const FieldEv32 &e = evs[i];
             const int flags = e.flags;
-            if (flags & FF_RF) {
-                float R[9];
+            const int kind = flags & KIND_MASK;
+            if (kind == KIND_READ) {
+                const int n = e.seg;
+                int slot = e.slot;
+                int j = 0;
+                for (; j + 1 < n; j += 2, slot += 2) {
+                    float u0[K], u1[K], u2[K];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) R[q] = e.R[q];
+                    for (int k = 0; k < K; ++k) sp[k].map(sp[k].M0, sp[k].M1, sp[k].M2, u0[k], u1[k], u2[k]);
+                    write_sample<K>(wcol, STRIDE, slot, evs[i + j].dem[0], evs[i + j].dem[1], u0, u1);
+                    float m0[K], m1[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) sp[k].rf(R);
-            }
-            if (flags & FF_RUN_START) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    sp[k].S0 = sp[k].M0;
-                    sp[k].S1 = sp[k].M1;
-                    sp[k].S2 = sp[k].M2;
+                    for (int k = 0; k < K; ++k) {
+                        sp[k].map(u0[k], u1[k], u2[k], sp[k].M0, sp[k].M1, sp[k].M2);
+                        m0[k] = sp[k].M0;
+                        m1[k] = sp[k].M1;
+                    }
+                    write_sample<K>(wcol, STRIDE, slot + 1, evs[i + j + 1].dem[0], evs[i + j + 1].dem[1], m0, m1);
                 }
-            } else if (flags & FF_RUN) {
+                if (j < n) {
+                    float m0[K], m1[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    sp[k].M0 = sp[k].S0;
-                    sp[k].M1 = sp[k].S1;
-                    sp[k].M2 = sp[k].S2;
+                    for (int k = 0; k < K; ++k) {
+                        float u0, u1, u2;
+                        sp[k].map(sp[k].M0, sp[k].M1, sp[k].M2, u0, u1, u2);
+                        sp[k].M0 = m0[k] = u0;
+                        sp[k].M1 = m1[k] = u1;
+                        sp[k].M2 = u2;
+                    }
+                    write_sample<K>(wcol, STRIDE, slot, evs[i + j].dem[0], evs[i + j].dem[1], m0, m1);
                 }
-            }
-            if (flags & FF_SAME) {
+                i += n;
+            } else if (kind == KIND_TRAIN) {
+                const int n = e.seg;
+                for (int j = 0; j < n; ++j) {
+                    const float4 ra = *reinterpret_cast<const float4 *>(&evs[i + j].R[0]);
+                    const float4 rb = *reinterpret_cast<const float4 *>(&evs[i + j].R[4]);
+                    const float r8 = evs[i + j].R[8];
 #pragma unroll
-                for (int k = 0; k < K; ++k) apply_map(sp[k].A, sp[k].cv, sp[k].M0, sp[k].M1, sp[k].M2);
-            } else if (flags & FF_FREE) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) sp[k].full(e, b0, flags);
-            }
-            if (flags & FF_ADC) {
-                const float d0 = e.dem[0], d1 = e.dem[1];
-                float sr = 0.0f, sim = 0.0f;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    sr += sp[k].M0 * d0 + sp[k].M1 * d1;
-                    sim += sp[k].M1 * d0 - sp[k].M0 * d1;
+                    for (int k = 0; k < K; ++k) {
+                        const float M0 = sp[k].M0, M1 = sp[k].M1, M2 = sp[k].M2;
+                        const float u0 = ra.z * M2 + (ra.y * M1 + ra.x * M0);
+                        const float u1 = rb.y * M2 + (rb.x * M1 + ra.w * M0);
+                        const float u2 = r8 * M2 + (rb.w * M1 + rb.z * M0);
+                        sp[k].map(u0, u1, u2, sp[k].M0, sp[k].M1, sp[k].M2);
+                    }
                 }
-                float *w = win + (2 * e.slot) * STRIDE + t;
-                w[0] = sr;
-                w[STRIDE] = sim;
+                i += n;
+            } else {
+                if (flags & FF_RF) {
+                    float R[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) R[q] = e.R[q];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) sp[k].rf(R);
+                }
+                if (flags & FF_RUN_START) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        sp[k].S0 = sp[k].M0;
+                        sp[k].S1 = sp[k].M1;
+                        sp[k].S2 = sp[k].M2;
+                    }
+                } else if (flags & FF_RUN) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        sp[k].M0 = sp[k].S0;
+                        sp[k].M1 = sp[k].S1;
+                        sp[k].M2 = sp[k].S2;
+                    }
+                }
+                if (flags & FF_SAME) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        float u0, u1, u2;
+                        sp[k].map(sp[k].M0, sp[k].M1, sp[k].M2, u0, u1, u2);
+                        sp[k].M0 = u0;
+                        sp[k].M1 = u1;
+                        sp[k].M2 = u2;
+                    }
+                } else if (flags & FF_FREE) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) sp[k].full(e, b0, flags);
+                }
+                if (flags & FF_ADC) {
+                    float m0[K], m1[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        m0[k] = sp[k].M0;
+                        m1[k] = sp[k].M1;
+                    }
+                    write_sample<K>(wcol, STRIDE, e.slot, e.dem[0], e.dem[1], m0, m1);
+                }
+                i += 1;
             }
         }
         __syncthreads();
@@ -646,6 +735,8 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
         f.dem[0] = (float)dem[0];
         f.dem[1] = (float)dem[1];
         r.flags = f.flags = flags;
+        f.seg = 1;
+        f.pad = 0;
         r.adc = f.adc = adc;
         r.slot = f.slot = sl;
         if (v.adc) {
@@ -654,6 +745,18 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
         }
         if ((i + 1) % FIELD_CHUNK == 0 || i + 1 == n_events)  // the chunk is complete: its sample count
             for (int64_t k = i / FIELD_CHUNK * FIELD_CHUNK; k <= i; ++k) e64[(size_t)k].nslot = e32[(size_t)k].nslot = slot;
+        // segment lengths, once the chunk is complete: events of kind READ or TRAIN followed by
+        // events of the same kind within the chunk
+        if ((i + 1) % FIELD_CHUNK == 0 || i + 1 == n_events) {
+            const int64_t k0 = i / FIELD_CHUNK * FIELD_CHUNK;
+            for (int64_t k = i; k >= k0; --k) {
+                FieldEv32 &f = e32[(size_t)k];
+                const int32_t kind = f.flags & KIND_MASK;
+                f.seg = 1;
+                if ((kind == KIND_READ || kind == KIND_TRAIN) && k < i && (e32[(size_t)k + 1].flags & KIND_MASK) == kind)
+                    f.seg = e32[(size_t)k + 1].seg + 1;
+            }
+        }
     }
     cudaSetDevice(ctx->device);
     mrsim_fields *fh = new (std::nothrow) mrsim_fields();
