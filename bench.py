@@ -759,7 +759,7 @@ def run_kt(args):
 # holds: the map (9).  A pulse is the 3x3 rotation (9), a sample the demodulated value (4).
 # Transcendentals (sin/cos, exp, square root, division) are not counted.
 FIELD_OPS_COMPUTED, FIELD_OPS_TRANSVERSE, FIELD_OPS_MAP, FIELD_OPS_RF, FIELD_OPS_ADC = 81, 42, 9, 9, 4
-FIELD_ANCHOR = 16  # every 16th step of a run of equal intervals, and its last, is computed from the run's start
+FIELD_ANCHOR = 32  # every 32nd step of a run of equal intervals, and its last, is computed from the run's start
 
 
 def field_event_classes(events, g_transverse):

@@ -60,7 +60,7 @@ constexpr double TWO_PI = 6.283185307179586476925286766559;
 enum FieldFlags : int32_t {
     FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8, FF_RUN_START = 16, FF_RUN = 32, FF_SAME = 64
 };
-constexpr int64_t FIELD_ANCHOR = 16;
+constexpr int64_t FIELD_ANCHOR = 32;
 
 // The two kinds of event that make up most sequences, which the float32 kernel runs in loops of
 // their own: a sample step of a readout (the held map, then the sample) and a sub-pulse of a

@@ -119,9 +119,9 @@ def test_field_work_model(bench):
     assert bench.field_ops_per_spin(ev, gt) == (9 + 81) + (9 + 9) + (81 + 42 + 4) + (9 + 4)
     # without transverse components the third interval is still new (its G differs)
     assert bench.field_ops_per_spin(ev, None) == (9 + 81) + (9 + 9) + (81 + 4) + (9 + 4)
-    # a readout run of 40 equal intervals: the first computed, steps 16 and 32 and the last (40)
-    # anchored, the other 36 repeat the first
-    ro = W.make_events([(1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0)] * 40)
+    # a readout run of 70 equal intervals: the first computed, steps 32 and 64 and the last (70)
+    # anchored, the other 66 repeat the first
+    ro = W.make_events([(1e-5, 1e-3, 0, 0, 0, 0, 1, 0.0)] * 70)
     computed, repeat = bench.field_event_classes(ro, None)
-    assert np.flatnonzero(computed).tolist() == [0, 15, 31, 39] and np.count_nonzero(repeat) == 36
-    assert bench.field_ops_per_spin(ro, None) == 4 * 81 + 36 * 9 + 40 * 4
+    assert np.flatnonzero(computed).tolist() == [0, 31, 63, 69] and np.count_nonzero(repeat) == 66
+    assert bench.field_ops_per_spin(ro, None) == 4 * 81 + 66 * 9 + 70 * 4
