@@ -416,7 +416,7 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
  * lazy module loading (the CUDA default) that is also when the library's device code is loaded
  * on that device and the array is reserved there, i.e. the first call does take device memory
  * implicitly.  Make that first call at initialisation, e.g. with n = 0 (which does only this
- * set-up), and before any stream capture.  Every call shares the one array, which keeps the
+ * set-up).  Every call shares the one array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU (other streams, other host threads'
  * launches still running) race on it and must be serialised by the caller; host threads are
  * serialised inside the call.  spins_per_thread / threads_per_block: 0 = library default (which,
