@@ -990,7 +990,8 @@ def run_ours(args):
     ctx.stream_status(stream)
 
     # the float64 oracle on a spin sample runs on the host cores meanwhile (rank 0, plain lists)
-    extras = rank == 0 and not args.skip_extra and not n_coils and prec != M.FP32_KAHAN
+    # (one GPU only: a multi-GPU run holds every GPU while rank 0 would run them)
+    extras = world == 1 and not args.skip_extra and not n_coils and prec != M.FP32_KAHAN
     frac = args.oracle_fraction if args.oracle_fraction >= 0 else {"c1": 1.0, "c2": 1.0, "c3": 0.01}[args.workload]
     orun = None
     if extras and not args.no_cpu_baseline and not args.raster and not args.events and frac > 0:
