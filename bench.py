@@ -863,9 +863,10 @@ def run_fields(args):
         cb = cpu_baseline_fields(w, args.cpu_seconds)
         line["cpu_baseline"] = cb["baseline"]
         sub = cb["sample"]
-        ps = M.Phantom.from_workload_phantom(ctx, w.phantom.subset(sub))
-        M.set_b0_direction(ctx, ps, w.b0_dir[sub])
-        par = {"sample_spins": int(sub.size)}
+        # the sample through the timed launch shape: the whole phantom with M0 = 0 outside it
+        ps = M.Phantom.from_workload_phantom(ctx, masked_phantom(w.phantom, sub))
+        M.set_b0_direction(ctx, ps, w.b0_dir)
+        par = {"sample_spins": int(sub.size), "launch": "whole phantom, M0 = 0 outside the sample"}
         nr = float(np.linalg.norm(cb["ref"]))
         for name, pr in (("fp32", M.FP32), ("fp64", M.FP64)):
             got = M.simulate_fields(ctx, ps, F, pr)

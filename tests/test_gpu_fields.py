@@ -175,3 +175,29 @@ def test_fields_workload_c1_low_field(M, ctx, oracle_mod):
     f = M.Fields(ctx, w.sequence.events, W.GAMMA_BAR, w.g_transverse, w.b0_tesla)
     assert rel_l2(M.simulate_fields(ctx, p, f, M.FP64), ref) <= TOL64
     assert rel_l2(M.simulate_fields(ctx, p, f, M.FP32), ref) <= TOL32
+
+
+@pytest.mark.parametrize("n_spins", [262143, 60000])
+def test_fields_large_launch_masked(M, ctx, oracle_mod, n_spins):
+    """A launch of C2's spin count less one (1 024 blocks of the float32 kernel, more than one wave
+    of resident blocks, a ragged last block) and a one-wave launch: every spin outside a 240-spin
+    sample has M0 = 0 (such a spin stays at zero), so the signal is the sample's, against the
+    oracle on the sample; the sample includes the last spins of the phantom."""
+    rng = np.random.default_rng(920 + n_spins % 97)
+    ph, ev, gt = case(rng, n_spins, 300)
+    nd = directions(rng, n_spins, 0.4)
+    idx = np.sort(np.concatenate([rng.choice(n_spins - 64, 200, replace=False), np.arange(n_spins - 40, n_spins)]))
+    rho = np.zeros_like(ph.rho)
+    rho[idx] = ph.rho[idx]
+    masked = W.Phantom(ph.x, ph.y, ph.z, rho, ph.t1, ph.t2, ph.dw)
+    sub = ph.subset(idx)
+    ref, _ = oracle_mod.simulate_fields(sub, ev, W.GAMMA_BAR, nd[idx], gt, 1.0)
+    p = M.Phantom.from_workload_phantom(ctx, masked)
+    M.set_b0_direction(ctx, p, nd)
+    f = M.Fields(ctx, ev, W.GAMMA_BAR, gt, 1.0)
+    got32 = M.simulate_fields(ctx, p, f, M.FP32)
+    got64 = M.simulate_fields(ctx, p, f, M.FP64)
+    ctx.stream_status()
+    assert rel_l2(got32, ref) <= TOL32
+    assert rel_l2(got64, ref) <= phase_floor(sub, ev, gt, 1.0)
+
