@@ -256,11 +256,26 @@ __device__ __forceinline__ void factors(const AdjEvent &e, const SpinP<T> &p, co
     }
 }
 
+// a·b + c·d, a·b − c·d and a·b + c·d + e·f: float64 as written (the compiler forms the same
+// multiply-adds as from the expressions inline); double-float in one step each (the products'
+// residuals summed once, one renormalisation) instead of a renormalised value per operation
+template <typename T>
+__device__ __forceinline__ T dot2(T a, T b, T c, T d) { return a * b + c * d; }
+template <typename T>
+__device__ __forceinline__ T dot2m(T a, T b, T c, T d) { return a * b - c * d; }
+template <typename T>
+__device__ __forceinline__ T dot3(T a, T b, T c, T d, T e, T f) { return a * b + c * d + e * f; }
+__device__ __forceinline__ dev::dfl dot2(dev::dfl a, dev::dfl b, dev::dfl c, dev::dfl d) { return dev::vdot2(a, b, c, d); }
+__device__ __forceinline__ dev::dfl dot2m(dev::dfl a, dev::dfl b, dev::dfl c, dev::dfl d) { return dev::vdot2(a, b, c, -d); }
+__device__ __forceinline__ dev::dfl dot3(dev::dfl a, dev::dfl b, dev::dfl c, dev::dfl d, dev::dfl e, dev::dfl f) {
+    return dev::vdot3(a, b, c, d, e, f);
+}
+
 template <typename T>
 __device__ __forceinline__ void apply_rf(const T *R, T M[3]) {
-    const T x = R[0] * M[0] + R[1] * M[1] + R[2] * M[2];
-    const T y = R[3] * M[0] + R[4] * M[1] + R[5] * M[2];
-    const T z = R[6] * M[0] + R[7] * M[1] + R[8] * M[2];
+    const T x = dot3(R[0], M[0], R[1], M[1], R[2], M[2]);
+    const T y = dot3(R[3], M[0], R[4], M[1], R[5], M[2]);
+    const T z = dot3(R[6], M[0], R[7], M[1], R[8], M[2]);
     M[0] = x;
     M[1] = y;
     M[2] = z;
@@ -271,11 +286,11 @@ template <typename T>
 __device__ __forceinline__ void after_pulse(const AdjEvent &e, const SpinP<T> &p, const T *tab, T M[3]) {
     T wr, wi, e1;
     factors(e, p, tab, wr, wi, e1);
-    const T x = M[0] * wr - M[1] * wi;
-    const T y = M[0] * wi + M[1] * wr;
+    const T x = dot2m(M[0], wr, M[1], wi);
+    const T y = dot2(M[0], wi, M[1], wr);
     M[0] = x;
     M[1] = y;
-    M[2] = e1 * M[2] + p.rho * (T(1) - e1);
+    M[2] = dot2(e1, M[2], p.rho, T(1) - e1);
 }
 
 template <typename T>
@@ -404,20 +419,20 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
             // parameter gradients through P (λ is the adjoint after the event)
             const T mx = buf[i][3], my = buf[i][4];  // P·M_a, transverse part
             const T ndt = -dt_of(e, T(0));
-            g_r2 += ndt * (L[0] * mx + L[1] * my);
+            g_r2 += ndt * dot2(L[0], mx, L[1], my);
             g_r1 += ndt * e1 * (Ma[2] - p.rho) * L[2];
             g_rho += (T(1) - e1) * L[2];
             // λ_a = Pᵀ λ: conj(w)·λ on the transverse part, E1 on z
-            const T lax = L[0] * wr + L[1] * wi, lay = L[1] * wr - L[0] * wi, laz = e1 * L[2];
+            const T lax = dot2(L[0], wr, L[1], wi), lay = dot2m(L[1], wr, L[0], wi), laz = e1 * L[2];
             if (e.flags & A_RF) {
                 const RfE<T> &rf = rf_at<T>(a, e.rf);
                 if (rf.param >= 0) {
                     // dL/dα = λ_aᵀ·(dR/dα)·M_n = λ_aᵀ·G·M_a
                     const T *G = rf.G;
-                    const T dx = G[0] * Ma[0] + G[1] * Ma[1] + G[2] * Ma[2];
-                    const T dy = G[3] * Ma[0] + G[4] * Ma[1] + G[5] * Ma[2];
-                    const T dz = G[6] * Ma[0] + G[7] * Ma[1] + G[8] * Ma[2];
-                    const T g = lax * dx + lay * dy + laz * dz;
+                    const T dx = dot3(G[0], Ma[0], G[1], Ma[1], G[2], Ma[2]);
+                    const T dy = dot3(G[3], Ma[0], G[4], Ma[1], G[5], Ma[2]);
+                    const T dz = dot3(G[6], Ma[0], G[7], Ma[1], G[8], Ma[2]);
+                    const T g = dot3(lax, dx, lay, dy, laz, dz);
                     if constexpr (LOCAL) {
                         gl[rf.param] += g;
                     } else {  // reduced over the warp, then the block (shared atomics)
@@ -426,9 +441,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) adj_backward_kernel(const AdjArgs
                     }
                 }
                 // λ_n = Rᵀ λ_a
-                L[0] = rf.R[0] * lax + rf.R[3] * lay + rf.R[6] * laz;
-                L[1] = rf.R[1] * lax + rf.R[4] * lay + rf.R[7] * laz;
-                L[2] = rf.R[2] * lax + rf.R[5] * lay + rf.R[8] * laz;
+                L[0] = dot3(rf.R[0], lax, rf.R[3], lay, rf.R[6], laz);
+                L[1] = dot3(rf.R[1], lax, rf.R[4], lay, rf.R[7], laz);
+                L[2] = dot3(rf.R[2], lax, rf.R[5], lay, rf.R[8], laz);
             } else {
                 L[0] = lax;
                 L[1] = lay;

@@ -358,8 +358,8 @@ struct Spins {
     __device__ __forceinline__ void rot_w() {
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const P nu = vfma(v[q], nwi_of(q), vmul(u[q], wr[q]));
-            const P nv = vfma(v[q], wr[q], vmul(u[q], wi[q]));
+            const P nu = vdot2(v[q], nwi_of(q), u[q], wr[q]);
+            const P nv = vdot2(v[q], wr[q], u[q], wi[q]);
             u[q] = nu;
             v[q] = nv;
         }
@@ -397,8 +397,8 @@ struct Spins {
     __device__ __forceinline__ void rf_turn(P ca, P sa, P nsa) {
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const P nv = vfma(v[q], ca, vmul(mz[q], sa));
-            const P nz = vfma(v[q], nsa, vmul(mz[q], ca));
+            const P nv = vdot2(v[q], ca, mz[q], sa);
+            const P nz = vdot2(v[q], nsa, mz[q], ca);
             v[q] = nv;
             mz[q] = nz;
         }
@@ -432,8 +432,8 @@ struct Spins {
             splat(ns, (R)-op.f[3]);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const P nu = vfma(u[q], c, vmul(v[q], s));
-                const P nv = vfma(v[q], c, vmul(u[q], ns));
+                const P nu = vdot2(u[q], c, v[q], s);
+                const P nv = vdot2(v[q], c, u[q], ns);
                 u[q] = nu;
                 v[q] = nv;
             }
@@ -580,8 +580,8 @@ struct Spins {
             set_lanes(AR, ar);
             set_lanes(AI, ai);
             set_lanes(NAI, nai);
-            const P nu = vfma(v[q], NAI, vmul(u[q], AR));
-            const P nv = vfma(v[q], AR, vmul(u[q], AI));
+            const P nu = vdot2(v[q], NAI, u[q], AR);
+            const P nv = vdot2(v[q], AR, u[q], AI);
             u[q] = nu;
             v[q] = nv;
         }
@@ -688,8 +688,8 @@ struct Spins {
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const CwT w = cw[op.acls * SP + pi(q)];
-                u[q] = vfma(av[q], vneg(w.im), vmul(au[q], w.re));
-                v[q] = vfma(av[q], w.re, vmul(au[q], w.im));
+                u[q] = vdot2(av[q], vneg(w.im), au[q], w.re);
+                v[q] = vdot2(av[q], w.re, au[q], w.im);
             }
         }
     }
@@ -813,8 +813,8 @@ struct Spins {
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const CwT w = cw[op.acls * SP + pi(q)];
-                u[q] = vfma(av[q], vneg(w.im), vmul(au[q], w.re));
-                v[q] = vfma(av[q], w.re, vmul(au[q], w.im));
+                u[q] = vdot2(av[q], vneg(w.im), au[q], w.re);
+                v[q] = vdot2(av[q], w.re, au[q], w.im);
             }
         }
     }

@@ -61,6 +61,9 @@ __device__ __forceinline__ float lane_of(f2 a, int h) {
 __device__ __forceinline__ void splat(f2 &o, float x) { o = pk2(x, x); }
 __device__ __forceinline__ void set_lanes(f2 &o, const float (&x)[2]) { o = pk2(x[0], x[1]); }
 
+// a·b + c·d with c·d formed first (the rounding order of every rotation in the kernels)
+__device__ __forceinline__ f2 vdot2(f2 a, f2 b, f2 c, f2 d) { return vfma(a, b, vmul(c, d)); }
+
 // the same operations on one scalar lane (float64, and float32 with one spin per thread)
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
@@ -80,6 +83,8 @@ template <typename T>
 __device__ __forceinline__ void splat(T &o, T x) { o = x; }
 template <typename T>
 __device__ __forceinline__ void set_lanes(T &o, const T (&x)[1]) { o = x[0]; }
+__device__ __forceinline__ float vdot2(float a, float b, float c, float d) { return vfma(a, b, vmul(c, d)); }
+__device__ __forceinline__ double vdot2(double a, double b, double c, double d) { return vfma(a, b, vmul(c, d)); }
 
 }  // namespace dev
 }  // namespace mrsim
