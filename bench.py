@@ -64,6 +64,9 @@ OPS_ADC, OPS_RF, OPS_OTHER = 6, 10, 4
 # other event is a precession-relaxation with a fresh phase (12); each sample also costs 3/k for
 # the shared-memory transpose of its partial sums with k spins per thread.
 EV_ADC_REPEAT, EV_RF, EV_OTHER, EV_SAMPLE_TRANSPOSE = 7, 9, 12, 3
+# A recurring shaped pulse run as its train map: per occurrence the 3x3 map and offset (12) in place
+# of its sub-pulses; per kind, once per launch, four states stepped through its sub-pulses.
+EV_MAP = 12
 FP32_LANES = 128      # FP32 lanes per SM (unit count)
 SM_MAX_MHZ = 2070.0   # used only when no clock sample exists
 
@@ -103,6 +106,22 @@ def per_event_ops_per_spin(events, spins_per_thread: int) -> float:
     n_other = len(ev) - n_rf - n_adc_rep
     return (EV_RF * n_rf + EV_ADC_REPEAT * n_adc_rep + EV_OTHER * n_other
             + EV_SAMPLE_TRANSPOSE / max(int(spins_per_thread), 1) * int(np.count_nonzero(adc)))
+
+
+def train_map_kinds(M, events, gamma_hz_per_t) -> list:
+    """The compiled program's train maps: per kind, (sub-pulses, occurrences)."""
+    ops = M.debug_compile(events, gamma_hz_per_t)["ops"]
+    kinds = {}
+    for o in ops[(ops["kind"] == M.OP_RF_TRAIN) & ((ops["flags"] & M.F_TMAP) != 0)]:
+        kinds.setdefault(int(o["tab"]), [int(o["n"]), 0])[1] += 1
+    return [tuple(v) for v in kinds.values()]
+
+
+def map_adjusted(ops_per_spin: float, per_sub: float, kinds) -> float:
+    """A model's ops per spin when the recurring trains run as maps: each occurrence applies its
+    map (EV_MAP) instead of its n sub-pulses (per_sub each), and each kind's map is formed once by
+    stepping four states (the three unit states and the zero state) through its n sub-pulses."""
+    return ops_per_spin + sum(occ * (EV_MAP - per_sub * n) + 4 * per_sub * n for n, occ in kinds)
 
 
 # Device facts and measured rates, filled by measure_device() before any timed region.
@@ -481,8 +500,11 @@ def run_batch(args):
     ck = clocks.stop()
     ctx.stream_status(stream)
     ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
-    form_ops = sum(algorithmic_ops_per_spin(w.sequence.events) * w.phantom.n for w in ws)
-    ops = sum(per_event_ops_per_spin(w.sequence.events, shape[0]) * w.phantom.n for w in ws)
+    kinds = [train_map_kinds(M, w.sequence.events, w.sequence.gamma_hz_per_t) for w in ws]
+    form_ops = sum(map_adjusted(algorithmic_ops_per_spin(w.sequence.events), OPS_RF, km) * w.phantom.n
+                   for w, km in zip(ws, kinds))
+    ops = sum(map_adjusted(per_event_ops_per_spin(w.sequence.events, shape[0]), EV_RF, km) * w.phantom.n
+              for w, km in zip(ws, kinds))
     achieved = ops / (ms * 1e-3) / 1e9
     form_g = form_ops / (ms * 1e-3) / 1e9
     line = {
@@ -1025,15 +1047,19 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
     base_ev = (canonical if args.raster else w.sequence).events
-    form_ops = algorithmic_ops_per_spin(base_ev, n_coils) * w.phantom.n
+    # recurring shaped pulses run as train maps (not with receive coils, which step every train)
+    kinds = [] if n_coils else train_map_kinds(M, base_ev, w.sequence.gamma_hz_per_t)
+    form_ops = map_adjusted(algorithmic_ops_per_spin(base_ev, n_coils), OPS_RF, kinds) * w.phantom.n
     form_g = form_ops / (kern_ms * 1e-3) / 1e9
     sha = kernel_source_sha()
+    map_note = (f"; {sum(o for _, o in kinds)} recurring trains of {len(kinds)} kinds as maps: {EV_MAP} per "
+                f"occurrence instead of its sub-pulses, 4 x RF per sub-pulse per kind to form them") if kinds else ""
     if n_coils:  # the per-event model has no coil term: the formulation model is the algorithmic work
         ops, model = form_ops, "formulation model with receive coils (a sample costs 4 + 4 per coil)"
     else:
-        ops = per_event_ops_per_spin(base_ev, k_spins) * w.phantom.n
+        ops = map_adjusted(per_event_ops_per_spin(base_ev, k_spins), EV_RF, kinds) * w.phantom.n
         model = (f"per event: ADC repeating the previous (G, dt) {EV_ADC_REPEAT}, RF {EV_RF}, other {EV_OTHER}, "
-                 f"+ {EV_SAMPLE_TRANSPOSE}/k per sample with k = {k_spins} spins per thread")
+                 f"+ {EV_SAMPLE_TRANSPOSE}/k per sample with k = {k_spins} spins per thread" + map_note)
     achieved = ops / (kern_ms * 1e-3) / 1e9
     if prec == M.FP64:  # the same algorithmic lane-ops against the measured float64 rate
         roof = dict(fp64_roofline(achieved), kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps, op_model=model)

@@ -87,6 +87,27 @@ mrsim_status grow(mrsim_ctx *ctx, double **buf, size_t *cap, size_t need_doubles
     return MRSIM_OK;
 }
 
+// The train maps of a single-phantom launch (the program's recurring trains composed per spin),
+// allocated on the stream from the context's pool; the caller frees *own on the stream after its
+// kernel.  a.maps stays NULL (trains run sub-pulse by sub-pulse) when the program has no map kinds,
+// the phantom no spins, or maps are switched off.
+mrsim_status prepare_maps(mrsim_ctx *ctx, const mrsim_sequence *seq, int mode, FwdArgs &a, void *stream, void **own) {
+    *own = nullptr;
+    if (!ctx->train_maps || a.prog.n_tmap <= 0 || a.n_spins <= 0) return MRSIM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *m = nullptr;
+    cudaError_t e = ctx_malloc_maps(ctx, &m, train_map_bytes(mode, a.prog, a.n_pad), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "train maps");
+    const int rc = launch_train_maps(mode, a, seq->d_train64, m, stream);
+    if (rc != 0) {
+        cudaFreeAsync(m, st);
+        return cuda_fail(ctx, (cudaError_t)rc, "train maps");
+    }
+    a.maps = m;
+    *own = m;
+    return MRSIM_OK;
+}
+
 mrsim_status pack(mrsim_ctx *ctx, int64_t n, const double *const src[7], cudaStream_t st, mrsim_phantom **out) {
     mrsim_phantom *p = new (std::nothrow) mrsim_phantom();
     if (!p) return fail(ctx, MRSIM_ENOMEM, "host allocation failed");
@@ -190,6 +211,12 @@ mrsim_status mrsim_debug_fail_alloc(mrsim_ctx *ctx, int32_t after) {
     return MRSIM_OK;
 }
 
+mrsim_status mrsim_context_set_train_maps(mrsim_ctx *ctx, int32_t enable) {
+    if (!ctx) return MRSIM_EINVAL;
+    ctx->train_maps = enable != 0;
+    return MRSIM_OK;
+}
+
 mrsim_status mrsim_debug_wait_timeout(mrsim_ctx *ctx, int64_t limit_ns, void *stream) {
     if (!ctx) return MRSIM_EINVAL;
     if (limit_ns < 1000 || limit_ns > 1000000000) return fail(ctx, MRSIM_EINVAL, "limit_ns must be in [1e3, 1e9]");
@@ -249,6 +276,7 @@ void mrsim_context_destroy(mrsim_ctx *ctx) {
     cudaFree(ctx->d_sens);
     cudaFree(ctx->d_kt);
     cudaFree(ctx->d_snap);
+    if (ctx->map_pool) cudaMemPoolDestroy(ctx->map_pool);  // released once its last allocation is freed
     delete ctx;
 }
 
@@ -346,11 +374,12 @@ mrsim_status mrsim::compile_host(int64_t n_events, const mrsim_event *events, do
         const Compiled &h = c->host;
         const void *src[HostProgram::N_TABLES] = {h.ops32.data(), h.ops64.data(), h.pcls.data(), h.e1.data(),
                                                   h.e2.data(), h.demod.data(), c->demod32.data(),
-                                                  c->train32.data(), h.train.data()};
+                                                  c->train32.data(), h.train.data(), h.tmap.data()};
         const size_t bytes[HostProgram::N_TABLES] = {
             h.ops32.size() * sizeof(OpF32), h.ops64.size() * sizeof(OpF64), h.pcls.size() * sizeof(double),
             h.e1.size() * sizeof(double),   h.e2.size() * sizeof(double),    h.demod.size() * sizeof(double),
-            c->demod32.size() * sizeof(float), c->train32.size() * sizeof(float), h.train.size() * sizeof(double)};
+            c->demod32.size() * sizeof(float), c->train32.size() * sizeof(float), h.train.size() * sizeof(double),
+            h.tmap.size() * sizeof(int32_t)};
         size_t o = 0;
         for (int t = 0; t < HostProgram::N_TABLES; ++t) {
             c->off[t] = o;
@@ -452,6 +481,8 @@ mrsim_status mrsim_sequence_create(mrsim_ctx *ctx, const mrsim_compiled *c, mrsi
     p.n_train = (int32_t)(h.host.train.size() / 2);
     p.n_adc = h.host.n_adc;
     for (int a = 0; a < 4; ++a) p.kmax[a] = h.kmax[a];
+    p.tmap = (const int32_t *)at(HostProgram::TMAP);
+    p.n_tmap = (int32_t)(h.host.tmap.size() / 4);
     s->p32 = p;
     s->p32.ops = s->d_ops32;
     s->p32.train = s->d_train32;
@@ -573,9 +604,12 @@ mrsim_status mrsim_simulate_ex(mrsim_ctx *ctx, const mrsim_phantom *ph, const mr
     a.snap = snap_n > 0 ? dsnap : nullptr;
     a.signal = dsig;
     a.status = ctx->d_status;
+    void *maps = nullptr;
+    if ((rs = prepare_maps(ctx, seq, mode, a, stream, &maps)) != MRSIM_OK) return rs;
     int rc = mode == MODE_F64 ? launch_fwd_f64(a, L.k, L.threads, stream)
              : mode == MODE_DF ? launch_fwd_df(a, L.k, L.threads, stream)
                                : launch_fwd_f32(a, L.k, L.threads, stream);
+    if (maps) cudaFreeAsync(maps, st);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel");
     if (host_out) CK(cudaMemcpyAsync(o.state_out, dout, st_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy state out");
     if (host_snap) CK(cudaMemcpyAsync(o.snapshots, dsnap, snap_n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy snapshots");
@@ -838,6 +872,21 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
         if (e0) cudaEventDestroy(e0);
         return cuda_fail(ctx, ee, "event");
     }
+    // the train maps, once for every trial: the shapes are timed running the trains as the
+    // simulation will
+    void *tmaps = nullptr;
+    {
+        FwdArgs ma{};
+        ma.prog = P;
+        ma.params = ph->params;
+        ma.n_spins = ph->n;
+        ma.n_pad = ph->n_pad;
+        if ((rs = prepare_maps(ctx, seq, mode, ma, stream, &tmaps)) != MRSIM_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rs;
+        }
+    }
     // time one launch of the prefix in shape (k, t); < 0 if the shape cannot run
     const int32_t short_ops = P.n_ops;
     const int32_t long_ops = (int32_t)std::min<int64_t>((int64_t)short_ops * 3, (fp64 ? seq->p64 : seq->p32).n_ops);
@@ -849,6 +898,7 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
         a.n_pad = ph->n_pad;
         a.signal = ctx->d_sig;
         a.status = ctx->d_status;
+        a.maps = tmaps;
         cudaEventRecord(e0, st);
         const int rc = mode == MODE_F64 ? launch_fwd_f64(a, k, t, stream)
                        : mode == MODE_DF ? launch_fwd_df(a, k, t, stream)
@@ -891,6 +941,7 @@ mrsim_status mrsim_autotune(mrsim_ctx *ctx, const mrsim_phantom *ph, const mrsim
         if (c.ms < win.ms) win = c;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (tmaps) cudaFreeAsync(tmaps, st);
     mrsim_status ss = mrsim_stream_status(ctx, stream);
     if (ss != MRSIM_OK) return ss;
     if (win.k == 0) return fail(ctx, MRSIM_EUNSUPPORTED, "no launch shape fits this program on the device");
@@ -986,6 +1037,12 @@ mrsim_status batch_enqueue(mrsim_batch *b, const FwdArgs *d_descs, cudaStream_t 
     int rc = zero_signals(d_descs, (int)b->descs.size(), st);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "zero batch signals");
     CK(cudaMemsetAsync(b->d_head, 0, sizeof(int), st), "reset work queue");
+    for (size_t i = 0; i < b->descs.size(); ++i) {  // train maps of the phantoms that have some
+        const FwdArgs &d = b->descs[i];
+        if (!d.maps) continue;
+        rc = launch_train_maps(launch_mode(b->prec), d, b->seq[i]->d_train64, const_cast<void *>(d.maps), st);
+        if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "batch train maps");
+    }
     BatchArgs a{};
     a.descs = d_descs;
     a.items = b->d_items;
@@ -1040,6 +1097,28 @@ mrsim_status mrsim_batch_create(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *
         mrsim_batch_destroy(b);
         return st;
     };
+    // every phantom's train maps in one buffer, rebuilt by each launch (a phantom's device memory
+    // may change between launches)
+    const int bmode = launch_mode(prec);
+    if (ctx->train_maps) {
+        size_t total = 0;
+        std::vector<size_t> off(b->descs.size(), 0);
+        for (size_t i = 0; i < b->descs.size(); ++i) {
+            const FwdArgs &a = b->descs[i];
+            if (a.prog.n_tmap <= 0 || a.n_spins <= 0) continue;
+            off[i] = total;
+            total += (train_map_bytes(bmode, a.prog, a.n_pad) + 255) / 256 * 256;
+        }
+        if (total > 0) {
+            cudaError_t e = ctx_malloc(ctx, &b->d_maps, total);
+            if (e != cudaSuccess) {
+                mrsim_batch_destroy(b);
+                return cuda_fail(ctx, e, "batch train maps");
+            }
+            for (size_t i = 0; i < b->descs.size(); ++i)
+                if (b->descs[i].prog.n_tmap > 0 && b->descs[i].n_spins > 0) b->descs[i].maps = b->d_maps + off[i];
+        }
+    }
     if (n > 0) {
         cudaError_t e = ctx_malloc(ctx, &b->d_descs, b->descs.size() * sizeof(FwdArgs));
         if (e == cudaSuccess)
@@ -1219,6 +1298,7 @@ void mrsim_batch_destroy(mrsim_batch *b) {
     cudaFree(b->d_descs);
     cudaFree(b->d_items);
     cudaFree(b->d_head);
+    cudaFree(b->d_maps);
     delete b;
 }
 

@@ -769,6 +769,37 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         err = "too many ADC samples";
         return MRSIM_EINVAL;
     }
+    // Train maps: trains that recur TRAIN_MAP_MIN times or more with the same classes and table
+    // entries (the same shaped pulse in every TR) get a map kind, in order of first appearance.
+    // A train's effect depends only on these and on the spin, so one map per spin and kind stands
+    // for every occurrence.  Programs with learnable flips rewrite their table between launches:
+    // no maps there.
+    if (!rf_param) {
+        std::map<std::array<int32_t, 4>, int> count;
+        std::vector<std::array<int32_t, 4>> order;
+        for (const OpF32 &o : out.ops32) {
+            if (o.kind != OP_RF_TRAIN || !(o.flags & F_E1CLS) || !(o.flags & F_PCLS)) continue;
+            const std::array<int32_t, 4> key = {o.pcls, o.ecls, o.adc0, o.n};
+            if (count[key]++ == 0) order.push_back(key);
+        }
+        std::map<std::array<int32_t, 4>, int> kind;
+        for (const auto &key : order) {
+            if ((int)kind.size() == TRAIN_MAP_MAX) break;
+            if (count[key] < TRAIN_MAP_MIN) continue;
+            const int t = (int)kind.size();
+            kind.emplace(key, t);
+            out.tmap.insert(out.tmap.end(), key.begin(), key.end());
+        }
+        for (size_t i = 0; i < out.ops32.size() && !kind.empty(); ++i) {
+            OpF32 &a = out.ops32[i];
+            if (a.kind != OP_RF_TRAIN || !(a.flags & F_E1CLS) || !(a.flags & F_PCLS)) continue;
+            auto it = kind.find({a.pcls, a.ecls, a.adc0, a.n});
+            if (it == kind.end()) continue;
+            OpF64 &b = out.ops64[i];
+            a.flags = b.flags = (uint16_t)(a.flags | F_TMAP);
+            a.tab = b.tab = (int16_t)it->second;
+        }
+    }
     return MRSIM_OK;
 }
 

@@ -20,6 +20,7 @@ struct Compiled {
     int n_pcls = 0, n_e1 = 0, n_e2 = 0;
     int64_t n_adc = 0;
     int64_t n_snap = 0;  // snapshots (OP_SNAP operations) in the program
+    std::vector<int32_t> tmap;  // 4 per train-map kind: phasor class, T1 class, first table entry, sub-pulses
 };
 
 // Returns an mrsim_status; on failure `err` says why.

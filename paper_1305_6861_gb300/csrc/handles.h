@@ -47,6 +47,9 @@ struct mrsim_ctx {
     size_t kt_cap = 0;
     double *d_snap = nullptr;  // snapshots for host output
     size_t snap_cap = 0;
+    cudaMemPool_t map_pool = nullptr;  // train maps of single-phantom launches: allocated on the call's
+                                       // stream and freed after its kernel, so concurrent calls never share
+    bool train_maps = true;            // mrsim_context_set_train_maps
     int *d_bad = nullptr;
 };
 
@@ -66,6 +69,26 @@ inline cudaError_t ctx_malloc(mrsim_ctx *ctx, void **p, size_t bytes) {
         return cudaErrorMemoryAllocation;
     }
     return cudaMalloc(p, bytes);
+}
+// Stream-ordered allocation from the context's train-map pool (created on first use; it keeps its
+// memory between calls); honours the same failure-injection hook.
+inline cudaError_t ctx_malloc_maps(mrsim_ctx *ctx, void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (ctx->fail_alloc >= 0 && ctx->fail_alloc-- == 0) return cudaErrorMemoryAllocation;
+    if (!ctx->map_pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        cudaError_t e = cudaMemPoolCreate(&ctx->map_pool, &props);
+        if (e != cudaSuccess) {
+            ctx->map_pool = nullptr;
+            return e;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(ctx->map_pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return cudaMallocFromPoolAsync(p, bytes, ctx->map_pool, st);
 }
 template <class T>
 cudaError_t ctx_malloc(mrsim_ctx *ctx, T **p, size_t bytes) {
@@ -88,8 +111,8 @@ struct HostProgram {
     double gamma = 0.0;
     // every device table in one 256-byte-aligned image, uploaded with a single copy: operations
     // (float32, float64), phasor classes, T1 and T2 classes, demodulation (float64, float32),
-    // sub-pulse tables (float32, float64)
-    enum Table { OPS32, OPS64, PCLS, E1, E2, DEMOD, DEMOD32, TRAIN32, TRAIN64, N_TABLES };
+    // sub-pulse tables (float32, float64), train-map kinds
+    enum Table { OPS32, OPS64, PCLS, E1, E2, DEMOD, DEMOD32, TRAIN32, TRAIN64, TMAP, N_TABLES };
     std::vector<unsigned char> image;
     size_t off[N_TABLES] = {}, len[N_TABLES] = {};
 };
@@ -130,6 +153,7 @@ struct mrsim_batch {
     FwdArgs *d_descs = nullptr;
     BatchItem *d_items = nullptr;
     int *d_head = nullptr;  // work-queue counter
+    unsigned char *d_maps = nullptr;  // every phantom's train maps (descs[i].maps points into it)
     int k = 0, threads = 0, grid = 0;
     size_t smem = 0;
     int64_t spin_steps = 0;

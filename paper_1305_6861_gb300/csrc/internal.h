@@ -59,6 +59,7 @@ enum OpFlags : uint16_t {
     F_KZ = 4096,
     F_DT = 8192,
     F_RFTAB = 16384,  // RF, RF_FAST: (cos α, sin α) from sub-pulse table entry `tab` (a parametric pulse)
+    F_TMAP = 32768,   // RF_TRAIN: a recurring train; a launch given train maps applies map `tab` instead
 };
 
 // float32 program: 64 bytes.  Inline PREC payload: kx, ky, kz, Δt as (hi, lo) float pairs
@@ -101,6 +102,13 @@ constexpr int SAMPLE_WINDOW_F64 = 256;
 constexpr int RUN_MAX = 256;
 // Entries (cos α, sin α) of the de-duplicated sub-pulse table held in shared memory.
 constexpr int TRAIN_TABLE_MAX = 2048;
+// Train maps: a sub-pulse train that recurs at least TRAIN_MAP_MIN times with the same precession
+// class, T1 class and table entries is, for each spin, one affine map of its state (the composition
+// of its sub-pulses, Eq. 3.23), computed once per launch; at most TRAIN_MAP_MAX kinds per program.
+constexpr int TRAIN_MAP_MIN = 4;
+constexpr int TRAIN_MAP_MAX = 16;
+constexpr int TRAIN_MAP_ROWS = 12;  // A (3 x 3, row-major) and c (3): (u, v, Mz) <- A (u, v, Mz) + c
+
 // Ops staged in shared memory per bulk copy (two buffers).
 constexpr int CHUNK_F32 = 64;
 constexpr int CHUNK_F64 = 32;
@@ -123,6 +131,8 @@ struct Program {
     int32_t n_train;
     int64_t n_adc;
     float kmax[4];  // float32 program: max |k_hi| of the inline precessions per term (kx, ky, kz, Δt)
+    const int32_t *tmap;  // 4 per train-map kind: phasor class, T1 class, first table entry, sub-pulses
+    int32_t n_tmap;
 };
 
 struct FwdArgs {
@@ -136,6 +146,8 @@ struct FwdArgs {
     const void *sens;        // receive coils: n_coils x n_pad complex (float2 or double2), coil-major
     int32_t n_coils;         // 0 = no coil weighting
     double *snap;            // NULL or n_snap x n_spins x 3 (device), written by OP_SNAP (laboratory frame)
+    const void *maps;        // NULL (trains run sub-pulse by sub-pulse) or the train maps of this phantom and
+                             // program: n_tmap x TRAIN_MAP_ROWS rows of n_pad values in the launch's type
 };
 
 // One work item of the persistent batch kernel: tile `tile` of the phantom of descriptor `desc`.
@@ -169,6 +181,11 @@ int launch_fwd_df(const FwdArgs &a, int spins_per_thread, int threads, void *str
 // one block whose bounded mbarrier wait runs out after limit_ns and records MRSIM_ETIMEOUT in *status
 int launch_wait_probe(int *status, uint64_t limit_ns, void *stream);
 size_t fwd_smem_bytes(bool fp64, const Program &p, int spins_per_thread, int threads);
+// Train maps of a.prog for the spins of a.params (n_pad per row) into `maps`: float32, float64 or
+// double-float values by mode, built in double-float (float64 for mode MODE_F64) from the float64
+// sub-pulse table train64 (2 per entry: cos α, sin α).
+size_t train_map_bytes(int mode, const Program &p, int64_t n_pad);
+int launch_train_maps(int mode, const FwdArgs &a, const double *train64, void *maps, void *stream);
 // K-t formalism (kt_kernel.cu): one step per elementary sequence, with the pulse's phase terms
 // precomputed on the host.
 struct KtStepDev {

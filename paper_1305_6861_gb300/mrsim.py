@@ -44,7 +44,7 @@ EXPORTS = (
     "mrsim_compiled_upload_bytes", "mrsim_compiled_destroy", "mrsim_sequence_create", "mrsim_debug_wait_timeout",
     "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate", "mrsim_simulate_adjoint",
     "mrsim_sequence_num_pulses", "mrsim_simulate_fields", "mrsim_phantom_set_b0_direction", "mrsim_fields_create",
-    "mrsim_fields_num_adc", "mrsim_fields_destroy", "mrsim_adjoint_set_precision",
+    "mrsim_fields_num_adc", "mrsim_fields_destroy", "mrsim_adjoint_set_precision", "mrsim_context_set_train_maps",
 )
 
 
@@ -152,6 +152,7 @@ def lib():
             "mrsim_debug_wait_timeout": (ctypes.c_int, [vp, i64, vp]),
             "mrsim_set_log_callback": (None, [vp, vp]),
             "mrsim_debug_fail_alloc": (ctypes.c_int, [vp, i32]),
+            "mrsim_context_set_train_maps": (ctypes.c_int, [vp, i32]),
             "mrsim_measure_fma_rate": (ctypes.c_int, [vp, i32, dbl, vp, P(dbl), P(dbl)]),
         }
         for name, (res, args) in sig.items():
@@ -197,6 +198,10 @@ class Context:
 
     def stream_status(self, stream=None):
         self.check(lib().mrsim_stream_status(self.h, _stream(stream)))
+
+    def set_train_maps(self, enable: bool):
+        """Recurring shaped pulses as one map per spin (default) or sub-pulse by sub-pulse."""
+        self.check(lib().mrsim_context_set_train_maps(self.h, 1 if enable else 0))
 
     def close(self):
         if getattr(self, "h", None):
@@ -641,3 +646,4 @@ OP_END, OP_RF, OP_RF_FAST, OP_PREC, OP_RUN, OP_RF_TRAIN, OP_SNAP = 0, 1, 2, 3, 4
 F_ADC, F_PCLS, F_PLOAD, F_INLINE, F_E1CLS, F_E1LOAD, F_E1INL, F_E2CLS, F_ANCHOR, F_FRAME = (
     1, 2, 4, 8, 16, 32, 64, 128, 256, 512)
 F_KX, F_KY, F_KZ, F_DT = 1024, 2048, 4096, 8192
+F_RFTAB, F_TMAP = 16384, 32768

@@ -255,8 +255,9 @@ def test_compile_without_context(mrsim_lib):
     d = M.debug_compile(w.sequence.events, w.sequence.gamma_hz_per_t)
     n_adc, n_tr = len(d["demod"]), len(d["train"])
     assert c.n_adc == n_adc == w.sequence.n_adc
+    n_tmap = len({int(o["tab"]) for o in d["ops"] if o["kind"] == M.OP_RF_TRAIN and o["flags"] & M.F_TMAP})
     tables = [len(d["ops"]) * 64, len(d["ops"]) * 128, 8 * d["pcls"].size, 8 * d["e1"].size, 8 * d["e2"].size,
-              16 * n_adc, 8 * n_adc, 8 * n_tr, 16 * n_tr]  # one image, tables on 256-byte boundaries
+              16 * n_adc, 8 * n_adc, 8 * n_tr, 16 * n_tr, 16 * n_tmap]  # one image, tables on 256-byte boundaries
     assert c.upload_bytes == sum(-(-b // 256) * 256 for b in tables)
     c.close()
     c.close()  # idempotent
@@ -349,3 +350,28 @@ def test_log_callback_and_env(mrsim_lib):
     env = dict(os.environ, MRSIM_LOG="1")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and "mrsim: invalid argument: event 0: adc must be 0/1" in r.stderr
+
+
+def test_train_map_kinds(mrsim_lib):
+    """The compiler marks a shaped pulse that recurs (at least 4 times with the same sub-pulse
+    flips, precession class and T1 class) as a train-map kind: C2's two sinc pulses, 256
+    occurrences each, 125 fast sub-pulses each; C1 (hard pulses) has none; a train that occurs
+    once is not mapped."""
+    M = mrsim_lib
+
+    def kinds(events, gamma):
+        ops = M.debug_compile(events, gamma)["ops"]
+        out = {}
+        for o in ops[(ops["kind"] == M.OP_RF_TRAIN) & ((ops["flags"] & M.F_TMAP) != 0)]:
+            out.setdefault(int(o["tab"]), [int(o["n"]), 0])[1] += 1
+        return out
+
+    w2 = W.config2()
+    assert sorted(kinds(w2.sequence.events, w2.sequence.gamma_hz_per_t).values()) == [[125, 256], [125, 256]]
+    w1 = W.config1()
+    assert kinds(w1.sequence.events, w1.sequence.gamma_hz_per_t) == {}
+    one = W.spin_echo(16, 8, 0.5, 12e-3, 30e-3, 10e-6, n_rf=24)
+    ev = one.events[: len(one.events) // 16]  # a single TR: every train occurs once
+    assert kinds(ev, one.gamma_hz_per_t) == {}
+    assert len(kinds(one.events, one.gamma_hz_per_t)) >= 1
+
