@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc") if os.path.exists(os.path.join(CUDA_HOME, "bin", "nvcc")) else "nvcc"
 
-CU_SOURCES = ["capi.cu", "fwd_f32.cu", "fwd_f64.cu", "fwd_df.cu", "batch_static.cu", "adjoint.cu", "kt_kernel.cu", "rate_probe.cu", "fields_kernel.cu"]
+CU_SOURCES = ["capi.cu", "fwd_f32.cu", "fwd_f64.cu", "fwd_df.cu", "batch_static.cu", "adjoint.cu", "kt_kernel.cu", "rate_probe.cu", "fields_kernel.cu", "train_maps.cu"]
 CXX_SOURCES = ["compile.cpp"]
 
 

@@ -22,23 +22,6 @@ int launch_wait_probe(int *status, uint64_t limit_ns, void *stream) {
     return (int)cudaGetLastError();
 }
 
-size_t train_map_bytes(int mode, const Program &p, int64_t n_pad) {
-    return (size_t)p.n_tmap * TRAIN_MAP_ROWS * (size_t)n_pad * (mode == MODE_F32 ? sizeof(float) : sizeof(double));
-}
-
-int launch_train_maps(int mode, const FwdArgs &a, const double *train64, void *maps, void *stream) {
-    if (a.prog.n_tmap <= 0 || a.n_pad <= 0) return 0;
-    const dim3 grid((unsigned)((a.n_pad + 255) / 256), (unsigned)a.prog.n_tmap);
-    cudaStream_t st = (cudaStream_t)stream;
-    if (mode == MODE_F64)
-        dev::train_map_kernel<double, double><<<grid, 256, 0, st>>>(a, train64, static_cast<double *>(maps));
-    else if (mode == MODE_DF)
-        dev::train_map_kernel<dev::dfl, dev::dfl><<<grid, 256, 0, st>>>(a, train64, static_cast<dev::dfl *>(maps));
-    else
-        dev::train_map_kernel<dev::dfl, float><<<grid, 256, 0, st>>>(a, train64, static_cast<float *>(maps));
-    return (int)cudaGetLastError();
-}
-
 int launch_fwd_f64(const FwdArgs &a, int k, int threads, void *stream) {
     switch (k) {
     case 1: return dev::launch_one<double, 1, 256>(a, threads, stream);
