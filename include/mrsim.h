@@ -433,7 +433,10 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
  * launches still running) race on it and must be serialised by the caller; host threads are
  * serialised inside the call.  spins_per_thread / threads_per_block: 0 = library default (which,
  * as in mrsim_batch_create, falls back to 1 x 64 and then 1 x 32 when it does not fit).  The
- * caller's current device is the same after the call as before it.
+ * caller's current device is the same after the call as before it.  Train maps need device
+ * memory per spin, so this call runs every shaped pulse sub-pulse by sub-pulse, as
+ * mrsim_batch_launch does with maps switched off (mrsim_context_set_train_maps); with maps on, the
+ * two differ by the rounding the maps remove, within the float32 tolerance.
  * Asynchronous on `stream`; errors of the kernel surface through mrsim_stream_status. */
 #define MRSIM_STATIC_SCRATCH_BYTES (1u << 20)
 mrsim_status mrsim_simulate_batch_static(mrsim_ctx *ctx, int32_t n, const mrsim_phantom *const *phantoms,
