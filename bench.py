@@ -784,15 +784,56 @@ FIELD_OPS_COMPUTED, FIELD_OPS_TRANSVERSE, FIELD_OPS_MAP, FIELD_OPS_RF, FIELD_OPS
 FIELD_ANCHOR = 32  # every 32nd step of a run of equal intervals, and its last, is computed from the run's start
 
 
-def field_event_classes(events, g_transverse):
+FIELD_TRAIN_MAX = 256  # longest train the fields kernels map
+
+
+def field_train_maps(events, g_transverse):
+    """The fields records' train maps: trains (two or more consecutive pulsed events without
+    samples sharing one free interval, at most FIELD_TRAIN_MAX) keyed by interval and pulses; a
+    key that occurs 4 times or more is a map kind (first 16 by first occurrence).  Returns
+    (mapped, kinds): per event whether it belongs to a mapped train, and per kind (events,
+    occurrences)."""
+    n = len(events)
+    gt = np.zeros((n, 6)) if g_transverse is None else np.asarray(g_transverse, dtype=float)
+    key = np.concatenate([np.stack([events["dt"], events["gx"], events["gy"], events["gz"]], axis=1), gt], axis=1)
+    pulsed = (events["rf_flip"] != 0) & (events["dt"] > 0) & (events["adc"] == 0)
+    starts = {}
+    i = 0
+    while i < n:
+        if not pulsed[i]:
+            i += 1
+            continue
+        k = i + 1
+        while k < n and k - i < FIELD_TRAIN_MAX and pulsed[k] and np.array_equal(key[k], key[i]):
+            k += 1
+        if k - i >= 2:
+            tk = (tuple(key[i]), tuple(events["rf_flip"][i:k]), tuple(events["rf_phase"][i:k]))
+            starts.setdefault(tk, []).append((i, k))
+        i = k
+    mapped = np.zeros(n, dtype=bool)
+    kinds = []
+    for occ in sorted(starts.values(), key=lambda v: v[0][0]):
+        if len(kinds) == 16:
+            break
+        if len(occ) < 4:
+            continue
+        kinds.append((occ[0][1] - occ[0][0], len(occ)))
+        for i0, k in occ:
+            mapped[i0:k] = True
+    return mapped, kinds
+
+
+def field_event_classes(events, g_transverse, maps=True):
     """Which events compute their interval from the record (`computed`) and which apply the map the
     spin holds (`repeat`), as the field records mark them: a run is a sequence of equal free
     intervals (equal dt, G and transverse components) without pulses; its FIELD_ANCHOR-th steps
     and its last are computed from the run's start; any other interval equal to the last computed
-    one (not counting anchored steps) repeats it."""
+    one (not counting anchored steps) repeats it.  With train maps, the events of mapped trains are
+    neither (they run as their train's map) and leave the held map alone."""
     n = len(events)
     gt = np.zeros((n, 6)) if g_transverse is None else np.asarray(g_transverse, dtype=float)
     key = np.concatenate([np.stack([events["dt"], events["gx"], events["gy"], events["gz"]], axis=1), gt], axis=1)
+    mapped = field_train_maps(events, g_transverse)[0] if maps else np.zeros(n, dtype=bool)
     free = events["dt"] > 0
     runnable = free & (events["rf_flip"] == 0)
     run = np.zeros(n, dtype=np.int64)
@@ -808,7 +849,7 @@ def field_event_classes(events, g_transverse):
     repeat = np.zeros(n, dtype=bool)
     cached = None
     for i in range(n):
-        if not free[i]:
+        if not free[i] or mapped[i]:
             continue
         if anchor[i]:
             computed[i] = True
@@ -820,12 +861,18 @@ def field_event_classes(events, g_transverse):
     return computed, repeat
 
 
-def field_ops_per_spin(events, g_transverse) -> int:
-    computed, repeat = field_event_classes(events, g_transverse)
+def field_ops_per_spin(events, g_transverse, maps=True) -> int:
+    computed, repeat = field_event_classes(events, g_transverse, maps)
+    mapped, kinds = field_train_maps(events, g_transverse) if maps else (np.zeros(len(events), dtype=bool), [])
     tr = np.any(g_transverse != 0, axis=1) if g_transverse is not None else np.zeros(len(events), dtype=bool)
-    return int(FIELD_OPS_COMPUTED * np.count_nonzero(computed) + FIELD_OPS_TRANSVERSE * np.count_nonzero(computed & tr)
-               + FIELD_OPS_MAP * np.count_nonzero(repeat) + FIELD_OPS_RF * np.count_nonzero(events["rf_flip"] != 0)
-               + FIELD_OPS_ADC * np.count_nonzero(events["adc"]))
+    ops = (FIELD_OPS_COMPUTED * np.count_nonzero(computed) + FIELD_OPS_TRANSVERSE * np.count_nonzero(computed & tr)
+           + FIELD_OPS_MAP * np.count_nonzero(repeat) + FIELD_OPS_RF * np.count_nonzero((events["rf_flip"] != 0) & ~mapped)
+           + FIELD_OPS_ADC * np.count_nonzero(events["adc"]))
+    # mapped trains: the map per occurrence; per kind, the interval's turn and four states stepped
+    # through its events (pulse, then the turn)
+    ops += sum(occ * EV_MAP + FIELD_OPS_COMPUTED + FIELD_OPS_TRANSVERSE + 4 * (FIELD_OPS_RF + FIELD_OPS_MAP) * n
+               for n, occ in kinds)
+    return int(ops)
 
 
 def run_fields(args):

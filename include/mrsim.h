@@ -395,13 +395,20 @@ mrsim_status mrsim_phantom_set_b0_direction(mrsim_phantom *ph, const double *b0_
  *   g_transverse: NULL, or 6*n_events doubles, host memory: per event gtx (3) and gty (3) [T/m],
  *                 the transverse field components Bx = gtx.x, By = gty.x during the event
  *   b0_tesla:     |B0| [T] > 0; it must exceed the gradient field at every spin (u != 0)
- * The records (float64 and float32, 192 bytes each per event) are uploaded once. */
+ * The records (float64 and float32, 192 bytes each per event) are uploaded once.  With the
+ * context's train maps on at creation (mrsim_context_set_train_maps), a train (two or more
+ * consecutive pulsed events without samples sharing one free interval, up to 256) that recurs at
+ * least 4 times with the same pulses and interval runs, per spin, as one map composed at the
+ * start of each simulation (double-float; float64 for MRSIM_FP64), which then needs
+ * 12 x (map kinds) values per spin of device memory from the context's stream-ordered pool. */
 typedef struct mrsim_fields mrsim_fields;
 mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_event *events,
                                  const double *g_transverse, double gamma_hz_per_t, double b0_tesla,
                                  mrsim_fields **out);
 /* Samples of the prepared list (the signal's length; -1 for NULL). */
 int64_t mrsim_fields_num_adc(const mrsim_fields *f);
+/* Train-map kinds of the prepared list (0: every train runs event by event; -1 for NULL). */
+int32_t mrsim_fields_num_train_maps(const mrsim_fields *f);
 void mrsim_fields_destroy(mrsim_fields *f);
 /* Forward simulation with non-parallel fields: signal_out = 2*n_adc doubles, host or device
  * (device output: asynchronous on `stream`; host output synchronises).  float32 keeps the

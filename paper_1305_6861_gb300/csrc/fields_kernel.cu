@@ -31,11 +31,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <map>
 #include <cmath>
 #include <string>
 #include <vector>
 
 #include "../../include/mrsim.h"
+#include "dfloat.cuh"
 #include "handles.h"
 #include "internal.h"
 
@@ -58,8 +61,14 @@ constexpr double TWO_PI = 6.283185307179586476925286766559;
 // the repeated rounding reaches at most FIELD_ANCHOR - 1 steps and never the state a run hands on.
 // FF_SAME: the free interval equals the one whose map the spin holds; apply it.
 enum FieldFlags : int32_t {
-    FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8, FF_RUN_START = 16, FF_RUN = 32, FF_SAME = 64
+    FF_RF = 1, FF_TRANSVERSE = 2, FF_ADC = 4, FF_FREE = 8, FF_RUN_START = 16, FF_RUN = 32, FF_SAME = 64,
+    FF_TMAP = 128  // the first event of a mapped train: apply train map (flags >> 16) & 0xff; the train's
+                   // other events carry no flags
 };
+// Train maps: a train (two or more consecutive pulsed events without samples that share one free
+// interval) that recurs at least TRAIN_MAP_MIN times with the same pulses and interval runs, per
+// spin, as one affine map composed at set-up (pulse, then the interval's turn, event by event).
+constexpr int FIELD_TRAIN_MAX = 256;  // longest mapped train (its pulses are staged in shared memory)
 constexpr int64_t FIELD_ANCHOR = 32;
 
 // The two kinds of event that make up most sequences, which the float32 kernel runs in loops of
@@ -108,7 +117,30 @@ struct FieldArgs {
     const double *ndir;    // 3 per spin, or NULL: every spin's field along z
     double b0;
     double *signal;        // 2 per sample
+    const void *maps;      // train maps: kind x TRAIN_MAP_ROWS rows of n_pad values (float or double)
 };
+
+// The map kinds of an event list: the first occurrence (event, length) of each.
+struct FieldKinds {
+    int32_t n;
+    int32_t len[TRAIN_MAP_MAX];
+    int64_t first[TRAIN_MAP_MAX];
+};
+
+// train map kind t of spin s applied to (M0, M1, M2): M <- A M + c
+template <typename R, typename T>
+__device__ __forceinline__ void apply_train_map(const R *maps, int t, int64_t np, int64_t s, T &M0, T &M1, T &M2) {
+    const R *m = maps + (int64_t)t * TRAIN_MAP_ROWS * np + s;
+    T A[TRAIN_MAP_ROWS];
+#pragma unroll
+    for (int j = 0; j < TRAIN_MAP_ROWS; ++j) A[j] = (T)m[j * np];
+    const T t0 = A[2] * M2 + (A[1] * M1 + (A[0] * M0 + A[9]));
+    const T t1 = A[5] * M2 + (A[4] * M1 + (A[3] * M0 + A[10]));
+    const T t2 = A[8] * M2 + (A[7] * M1 + (A[6] * M0 + A[11]));
+    M0 = t0;
+    M1 = t1;
+    M2 = t2;
+}
 
 // Phase accumulator in cycles for products of (hi, lo) pairs: per product the integer part of
 // the leading product is removed exactly (|ah bh| < 2^22, the fractional part is exact), its
@@ -219,6 +251,8 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
         __syncthreads();
         for (int i = 0; i < nc; ++i) {
             const FieldEv64 &e = evs[i];
+            if ((e.flags & FF_TMAP) && s < np)
+                apply_train_map(static_cast<const double *>(a.maps), (e.flags >> 16) & 0xff, np, s, M0, M1, M2);
             if (e.flags & FF_RF) {
                 const double t0 = e.R[0] * M0 + e.R[1] * M1 + e.R[2] * M2;
                 const double t1 = e.R[3] * M0 + e.R[4] * M1 + e.R[5] * M2;
@@ -397,7 +431,9 @@ __device__ __forceinline__ void write_sample(float *win, int stride, int slot, f
 // (coalesced per k).  The events of a chunk run as segments: a run of readout samples (the host
 // marks its length) applies the held map in a loop unrolled by two, whose halves alternate between
 // the state and a second set of registers; a run of sub-pulses turns and maps each spin with no
-// copy; any other event takes the general path, its flags tested once for all K spins.  Samples:
+// copy; a run of events without effect (the events of a mapped train after its first) is passed
+// over in one step; any other event (a mapped train's first applies its train map) takes the
+// general path, its flags tested once for all K spins.  Samples:
 // each thread writes the sum over its spins of each sample of the chunk to its own column of a
 // shared window (no exchange between threads while the events run); after the chunk, each of the
 // 2·nslot rows (a sample's real or imaginary part) is summed over the T columns (64 entries per
@@ -432,6 +468,10 @@ __global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
             const FieldEv32 &e = evs[i];
             const int flags = e.flags;
             const int kind = flags & KIND_MASK;
+            if (flags == 0) {  // a run of events without effect (inside a mapped train, or empty)
+                i += e.seg;
+                continue;
+            }
             if (kind == KIND_READ) {
                 const int n = e.seg;
                 int slot = e.slot;
@@ -480,6 +520,15 @@ __global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
                 }
                 i += n;
             } else {
+                if (flags & FF_TMAP) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const int64_t si = ((int64_t)blockIdx.x * K + k) * T + t;
+                        if (si < a.n_pad)
+                            apply_train_map(static_cast<const float *>(a.maps), (flags >> 16) & 0xff, a.n_pad, si,
+                                            sp[k].M0, sp[k].M1, sp[k].M2);
+                    }
+                }
                 if (flags & FF_RF) {
                     float R[9];
 #pragma unroll
@@ -542,6 +591,84 @@ __global__ void __launch_bounds__(T, 512 / T) fields_kernel_f32(FieldArgs a) {
     }
 }
 
+__device__ __forceinline__ double fdot3(double a, double b, double c, double d, double e, double f) {
+    return a * b + c * d + e * f;
+}
+__device__ __forceinline__ dev::dfl fdot3(dev::dfl a, dev::dfl b, dev::dfl c, dev::dfl d, dev::dfl e, dev::dfl f) {
+    return dev::vdot3(a, b, c, d, e, f);
+}
+
+// Train maps (set-up): thread (s, t) forms, in float64, spin s's turn for the free interval of map
+// kind t (the same in every event of the train: the field, its direction, the phase, the
+// exponentials, as the float64 kernel forms them), then steps the three unit states (the columns
+// of A) and the zero state (c) through the train's events, pulse then turn, in C arithmetic
+// (double-float, or float64 for the float64 kernel); the pulses are staged per block in shared
+// memory.  Stored rounded to R.
+template <typename C, typename R>
+__global__ void __launch_bounds__(128) fields_map_kernel(FieldArgs a, const FieldEv64 *ev, FieldKinds k, R *maps) {
+    __shared__ C rp[FIELD_TRAIN_MAX * 9];
+    const int t = blockIdx.y;
+    const int64_t i0 = k.first[t];
+    const int n = k.len[t];
+    for (int q = threadIdx.x; q < 9 * n; q += blockDim.x) rp[q] = C(ev[i0 + q / 9].R[q % 9]);
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n_pad) return;
+    const bool live = s < a.n_spins;
+    const int64_t si = live ? s : 0;
+    const int64_t np = a.n_pad;
+    const double x = a.params[P_X * np + si], y = a.params[P_Y * np + si], z = a.params[P_Z * np + si];
+    const double dw = TWO_PI * a.params[P_DF * np + si];
+    const double m0 = live ? a.params[P_RHO * np + si] : 0.0;
+    const double r1 = a.params[P_R1 * np + si], r2 = a.params[P_R2 * np + si];
+    const double n0 = a.ndir ? a.ndir[3 * si] : 0.0, n1 = a.ndir ? a.ndir[3 * si + 1] : 0.0;
+    const double n2 = a.ndir ? a.ndir[3 * si + 2] : 1.0;
+    const FieldEv64 &e = ev[i0];
+    const double bz = e.g[0] * x + e.g[1] * y + e.g[2] * z;
+    const double bx = e.gt[0] * x + e.gt[1] * y + e.gt[2] * z;
+    const double by = e.gt[3] * x + e.gt[4] * y + e.gt[5] * z;
+    const double p = n0 * bx + n1 * by + n2 * bz;
+    const double qx = bx - p * n0, qy = by - p * n1, qz = bz - p * n2;
+    const double ux = a.b0 * n0 + bx, uy = a.b0 * n1 + by, uz = a.b0 * n2 + bz;
+    const double un = sqrt(ux * ux + uy * uy + uz * uz);
+    const double excess = p + (qx * qx + qy * qy + qz * qz) / (un + a.b0 + p);
+    const double inv = 1.0 / un;
+    double sn, cs;
+    sincos(e.gdt * excess + dw * e.dt, &sn, &cs);
+    double Ad[9], cd[3];
+    turn_map(ux * inv, uy * inv, uz * inv, cs, sn, expm1(-e.dt * r1), exp(-e.dt * r2), m0, Ad, cd);
+    C A[9], cc[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = C(Ad[q]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cc[q] = C(cd[q]);
+    C V[4][3] = {{C(1.0), C(0.0), C(0.0)}, {C(0.0), C(1.0), C(0.0)}, {C(0.0), C(0.0), C(1.0)}, {C(0.0), C(0.0), C(0.0)}};
+    for (int i = 0; i < n; ++i) {
+        const C *Rm = rp + 9 * i;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const C w0 = fdot3(Rm[0], V[v][0], Rm[1], V[v][1], Rm[2], V[v][2]);  // the pulse
+            const C w1 = fdot3(Rm[3], V[v][0], Rm[4], V[v][1], Rm[5], V[v][2]);
+            const C w2 = fdot3(Rm[6], V[v][0], Rm[7], V[v][1], Rm[8], V[v][2]);
+            V[v][0] = fdot3(A[0], w0, A[1], w1, A[2], w2);  // the interval's turn
+            V[v][1] = fdot3(A[3], w0, A[4], w1, A[5], w2);
+            V[v][2] = fdot3(A[6], w0, A[7], w1, A[8], w2);
+            if (v == 3) {
+                V[v][0] = V[v][0] + cc[0];
+                V[v][1] = V[v][1] + cc[1];
+                V[v][2] = V[v][2] + cc[2];
+            }
+        }
+    }
+    R *m = maps + (int64_t)t * TRAIN_MAP_ROWS * np + s;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) m[(3 * j + v) * np] = R(double(V[v][j]));
+        m[(9 + j) * np] = R(double(V[3][j]));
+    }
+}
+
 // lowest index of a direction that is not a finite unit vector (|n| - 1 beyond 1e-9)
 __global__ void check_dirs_kernel(int64_t n, const double *nd, int *bad) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
@@ -596,6 +723,7 @@ struct mrsim_fields {
     mrsim_ctx *ctx = nullptr;
     int64_t n_events = 0, n_adc = 0;
     double b0 = 0.0;
+    FieldKinds kinds{};  // train-map kinds (none when the context's train maps were off at creation)
     unsigned char *d_rec = nullptr;  // [float64 records | float32 records]
     size_t off32 = 0;
 };
@@ -685,6 +813,66 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     }
     for (int64_t i = n_events - 1; i >= 0; --i)
         if (run[i] > 0) len[i] = (i + 1 < n_events && run[i + 1] == run[i] + 1) ? len[i + 1] : run[i];
+    // Train maps: trains (>= 2 consecutive pulsed events without samples sharing one free interval,
+    // at most FIELD_TRAIN_MAX) keyed by their interval and pulses; a key that occurs
+    // TRAIN_MAP_MIN times or more becomes a map kind (in order of first occurrence, at most
+    // TRAIN_MAP_MAX).  tkind[i]: the kind of the mapped train that starts at event i (-1: none);
+    // inside[i]: event i belongs to a mapped train and is not its first.
+    std::vector<int32_t> tkind;
+    std::vector<char> inside;
+    FieldKinds kinds{};
+    try {
+        tkind.assign((size_t)n_events, -1);
+        inside.assign((size_t)n_events, 0);
+        if (ctx->train_maps) {
+            auto pulsed = [&](int64_t k) { return events[k].rf_flip != 0.0 && events[k].dt > 0.0 && !events[k].adc; };
+            auto bits = [](double d) {
+                uint64_t u;
+                std::memcpy(&u, &d, 8);
+                return u;
+            };
+            std::map<std::vector<uint64_t>, std::vector<int64_t>> starts;
+            std::vector<std::pair<int64_t, const std::vector<uint64_t> *>> order;
+            std::vector<int64_t> lens((size_t)n_events, 0);
+            for (int64_t i = 0; i < n_events;) {
+                if (!pulsed(i)) {
+                    ++i;
+                    continue;
+                }
+                int64_t k = i + 1;
+                while (k < n_events && k - i < FIELD_TRAIN_MAX && pulsed(k) && same_interval(i, k)) ++k;
+                if (k - i >= 2) {
+                    const mrsim_event &v = events[i];
+                    const double *gt = g_transverse ? g_transverse + 6 * i : zero6;
+                    std::vector<uint64_t> key = {bits(v.dt), bits(v.gx), bits(v.gy), bits(v.gz)};
+                    for (int q = 0; q < 6; ++q) key.push_back(bits(gt[q]));
+                    for (int64_t q = i; q < k; ++q) {
+                        key.push_back(bits(events[q].rf_flip));
+                        key.push_back(bits(events[q].rf_phase));
+                    }
+                    auto it = starts.emplace(std::move(key), std::vector<int64_t>()).first;
+                    if (it->second.empty()) order.emplace_back(i, &it->first);
+                    it->second.push_back(i);
+                    lens[(size_t)i] = k - i;
+                }
+                i = k;
+            }
+            for (const auto &o : order) {
+                if (kinds.n == TRAIN_MAP_MAX) break;
+                const std::vector<int64_t> &st = starts[*o.second];
+                if ((int)st.size() < TRAIN_MAP_MIN) continue;
+                const int t = kinds.n++;
+                kinds.first[t] = st[0];
+                kinds.len[t] = (int32_t)lens[(size_t)st[0]];
+                for (int64_t i0 : st) {
+                    tkind[(size_t)i0] = t;
+                    for (int64_t q = i0 + 1; q < i0 + kinds.len[t]; ++q) inside[(size_t)q] = 1;
+                }
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return ffail(ctx, MRSIM_ENOMEM, "host allocation failed");
+    }
     int64_t j = 0, cached = -1;  // cached: the event whose one-interval map the spins hold
     int slot = 0;
     for (int64_t i = 0; i < n_events; ++i) {
@@ -695,12 +883,15 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
         const bool free = v.dt > 0.0;
         const int64_t pos = run[(size_t)i];
         const bool anchor = pos > 1 && (pos % FIELD_ANCHOR == 0 || pos == len[(size_t)i]);
-        const bool same = free && !anchor && cached >= 0 && same_interval(cached, i);
-        if (free && !anchor && !same) cached = i;
+        const bool mapped = tkind[(size_t)i] >= 0 || inside[(size_t)i];  // a mapped train leaves the held map alone
+        const bool same = !mapped && free && !anchor && cached >= 0 && same_interval(cached, i);
+        if (!mapped && free && !anchor && !same) cached = i;
         const double span = anchor ? v.dt * (double)pos : v.dt;  // an anchored step: the run's interval so far
-        const int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
-                              (free ? FF_FREE : 0) | (pos == 1 ? FF_RUN_START : 0) | (anchor ? FF_RUN : 0) |
-                              (same ? FF_SAME : 0);
+        int32_t flags = (v.rf_flip != 0.0 ? FF_RF : 0) | (tr ? FF_TRANSVERSE : 0) | (v.adc ? FF_ADC : 0) |
+                        (free ? FF_FREE : 0) | (pos == 1 ? FF_RUN_START : 0) | (anchor ? FF_RUN : 0) |
+                        (same ? FF_SAME : 0);
+        if (tkind[(size_t)i] >= 0) flags = FF_TMAP | (tkind[(size_t)i] << 16);
+        else if (inside[(size_t)i]) flags = 0;
         double R[9];
         rf_matrix(v.rf_flip, v.rf_phase, R);
         const double g[3] = {v.gx, v.gy, v.gz};
@@ -755,6 +946,7 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
                 f.seg = 1;
                 if ((kind == KIND_READ || kind == KIND_TRAIN) && k < i && (e32[(size_t)k + 1].flags & KIND_MASK) == kind)
                     f.seg = e32[(size_t)k + 1].seg + 1;
+                if (f.flags == 0 && k < i && e32[(size_t)k + 1].flags == 0) f.seg = e32[(size_t)k + 1].seg + 1;
             }
         }
     }
@@ -765,6 +957,7 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
     fh->n_events = n_events;
     fh->n_adc = j;
     fh->b0 = b0_tesla;
+    fh->kinds = kinds;
     const size_t b64 = (size_t)n_events * sizeof(FieldEv64), b32 = (size_t)n_events * sizeof(FieldEv32);
     fh->off32 = (b64 + 255) / 256 * 256;
     if (n_events > 0) {
@@ -784,6 +977,8 @@ mrsim_status mrsim_fields_create(mrsim_ctx *ctx, int64_t n_events, const mrsim_e
 }
 
 int64_t mrsim_fields_num_adc(const mrsim_fields *f) { return f ? f->n_adc : -1; }
+
+int32_t mrsim_fields_num_train_maps(const mrsim_fields *f) { return f ? f->kinds.n : -1; }
 
 void mrsim_fields_destroy(mrsim_fields *f) {
     if (!f) return;
@@ -820,6 +1015,7 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
         sig = ctx->d_sig;
     }
     cudaError_t e = cudaSuccess;
+    void *maps = nullptr;
     if (n_adc > 0) e = cudaMemsetAsync(sig, 0, sig_bytes, st);
     if (e == cudaSuccess && ph->n > 0 && f->n_events > 0) {
         FieldArgs a{};
@@ -831,6 +1027,21 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
         a.ndir = ph->d_dir;
         a.b0 = f->b0;
         a.signal = sig;
+        if (f->kinds.n > 0) {  // the train maps of this phantom, from the context's pool
+            const size_t mb = (size_t)f->kinds.n * TRAIN_MAP_ROWS * (size_t)ph->n_pad * (f64 ? sizeof(double) : sizeof(float));
+            e = ctx_malloc_maps(ctx, &maps, mb, st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return ffail(ctx, MRSIM_ENOMEM, "fields train maps");
+            }
+            const dim3 mg((unsigned)((ph->n_pad + 127) / 128), (unsigned)f->kinds.n);
+            const FieldEv64 *ev64 = reinterpret_cast<const FieldEv64 *>(f->d_rec);
+            if (f64)
+                fields_map_kernel<double, double><<<mg, 128, 0, st>>>(a, ev64, f->kinds, static_cast<double *>(maps));
+            else
+                fields_map_kernel<dev::dfl, float><<<mg, 128, 0, st>>>(a, ev64, f->kinds, static_cast<float *>(maps));
+            a.maps = maps;
+        }
         if (f64) {
             const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
             fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
@@ -853,6 +1064,7 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
                 fields_kernel_f32<FIELD_K32, 128><<<(unsigned)blocks128, 128, 0, st>>>(a);
         }
         e = cudaGetLastError();
+        if (maps) cudaFreeAsync(maps, st);
     }
     if (e == cudaSuccess && host_sig) {
         e = cudaMemcpyAsync(signal_out, sig, sig_bytes, cudaMemcpyDeviceToHost, st);

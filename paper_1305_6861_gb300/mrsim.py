@@ -45,6 +45,7 @@ EXPORTS = (
     "mrsim_set_log_callback", "mrsim_debug_fail_alloc", "mrsim_measure_fma_rate", "mrsim_simulate_adjoint",
     "mrsim_sequence_num_pulses", "mrsim_simulate_fields", "mrsim_phantom_set_b0_direction", "mrsim_fields_create",
     "mrsim_fields_num_adc", "mrsim_fields_destroy", "mrsim_adjoint_set_precision", "mrsim_context_set_train_maps",
+    "mrsim_fields_num_train_maps",
 )
 
 
@@ -141,6 +142,7 @@ def lib():
             "mrsim_phantom_set_b0_direction": (ctypes.c_int, [vp, vp, vp]),
             "mrsim_fields_create": (ctypes.c_int, [vp, i64, vp, vp, dbl, dbl, P(vp)]),
             "mrsim_fields_num_adc": (i64, [vp]),
+            "mrsim_fields_num_train_maps": (i32, [vp]),
             "mrsim_fields_destroy": (None, [vp]),
             "mrsim_debug_compile": (ctypes.c_int, [i64, vp, dbl, P(ProgramDump)]),
             "mrsim_compile": (ctypes.c_int, [i64, vp, dbl, i64, vp, P(vp)]),
@@ -558,6 +560,7 @@ class Fields:
                                             float(b0_tesla), ctypes.byref(h)))
         self.h = h
         self.n_adc = int(lib().mrsim_fields_num_adc(h))
+        self.n_train_maps = int(lib().mrsim_fields_num_train_maps(h))
         self.n_events = int(ev.shape[0])
 
     def close(self):

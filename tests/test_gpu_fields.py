@@ -201,3 +201,33 @@ def test_fields_large_launch_masked(M, ctx, oracle_mod, n_spins):
     assert rel_l2(got32, ref) <= TOL32
     assert rel_l2(got64, ref) <= phase_floor(sub, ev, gt, 1.0)
 
+
+def test_fields_train_maps(M, ctx, oracle_mod):
+    """A spin echo whose sinc pulses recur every TR, with tilted static fields and Maxwell
+    concomitant components: its trains run as maps (pulse, then the interval's turn, composed per
+    spin at set-up) when the context's maps are on at creation, event by event when off; both
+    against the oracle at the usual bars."""
+    rng = np.random.default_rng(930)
+    seq = W.spin_echo(16, 8, 0.5, 12e-3, 30e-3, 10e-6, n_rf=24)
+    ev = seq.events
+    gt = W.concomitant_transverse(ev)
+    ph = W.random_phantom(2001, rng)
+    ph.dw[:] = 2 * math.pi * rng.uniform(-80, 80, ph.n)
+    nd = directions(rng, ph.n, 0.3)
+    ref, _ = oracle_mod.simulate_fields(ph, ev, W.GAMMA_BAR, nd, gt, 0.3)
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    M.set_b0_direction(ctx, p, nd)
+    floor = phase_floor(ph, ev, gt, 0.3)
+    try:
+        for maps in (True, False):
+            ctx.set_train_maps(maps)
+            f = M.Fields(ctx, ev, W.GAMMA_BAR, gt, 0.3)
+            assert (f.n_train_maps > 0) == maps
+            got64 = M.simulate_fields(ctx, p, f, M.FP64)
+            got32 = M.simulate_fields(ctx, p, f, M.FP32)
+            ctx.stream_status()
+            assert rel_l2(got64, ref) <= floor, (maps, rel_l2(got64, ref))
+            assert rel_l2(got32, ref) <= TOL32, (maps, rel_l2(got32, ref))
+    finally:
+        ctx.set_train_maps(True)
+
