@@ -1094,15 +1094,15 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the forward kernel; one launch per step) ----------
     base_ev = (canonical if args.raster else w.sequence).events
-    # recurring shaped pulses run as train maps (not with receive coils, which step every train)
-    kinds = [] if n_coils else train_map_kinds(M, base_ev, w.sequence.gamma_hz_per_t)
+    # recurring shaped pulses run as train maps
+    kinds = train_map_kinds(M, base_ev, w.sequence.gamma_hz_per_t)
     form_ops = map_adjusted(algorithmic_ops_per_spin(base_ev, n_coils), OPS_RF, kinds) * w.phantom.n
     form_g = form_ops / (kern_ms * 1e-3) / 1e9
     sha = kernel_source_sha()
     map_note = (f"; {sum(o for _, o in kinds)} recurring trains of {len(kinds)} kinds as maps: {EV_MAP} per "
                 f"occurrence instead of its sub-pulses, 4 x RF per sub-pulse per kind to form them") if kinds else ""
     if n_coils:  # the per-event model has no coil term: the formulation model is the algorithmic work
-        ops, model = form_ops, "formulation model with receive coils (a sample costs 4 + 4 per coil)"
+        ops, model = form_ops, "formulation model with receive coils (a sample costs 4 + 4 per coil)" + map_note
     else:
         ops = map_adjusted(per_event_ops_per_spin(base_ev, k_spins), EV_RF, kinds) * w.phantom.n
         model = (f"per event: ADC repeating the previous (G, dt) {EV_ADC_REPEAT}, RF {EV_RF}, other {EV_OTHER}, "

@@ -119,15 +119,15 @@ void mrsim_set_log_callback(mrsim_log_fn fn, void *user);
 mrsim_status mrsim_debug_fail_alloc(mrsim_ctx *ctx, int32_t after);
 /* Train maps (on by default).  A shaped pulse (Eq. 3.23) repeated with the same sub-pulse flips,
  * precession class and T1 class (the same pulse in every TR) composes, for each spin, to one
- * affine map of its state.  With maps on, mrsim_simulate[_ex], mrsim_autotune and the batch calls
- * build every spin's map once per launch (double-float arithmetic, float64 for MRSIM_FP64) and
+ * affine map of its state.  With maps on, mrsim_simulate[_ex], mrsim_simulate_coils,
+ * mrsim_autotune and the batch calls build every spin's map once per launch (double-float arithmetic, float64 for MRSIM_FP64) and
  * apply it in place of the train's sub-pulses.  The result is the same composition with one
  * rounding of the map in place of one rounding per sub-pulse.  Such a call then needs
  * 12 x (map kinds) values per spin of device memory: a single-phantom call takes it from a
  * per-context stream-ordered pool and frees it after its kernel; a batch holds it from creation.
  * enable = 0 runs every train sub-pulse by sub-pulse (and needs no such memory).
- * mrsim_simulate_batch_static, mrsim_simulate_coils and the adjoint never use maps.  Affects the
- * calls made after it; batches created before it keep their setting. */
+ * mrsim_simulate_batch_static and the adjoint never use maps.  Affects the calls made after it;
+ * batches created before it keep their setting. */
 mrsim_status mrsim_context_set_train_maps(mrsim_ctx *ctx, int32_t enable);
 /* Synchronise `stream` (cudaStream_t, NULL = legacy default stream) and report any device-side
  * status recorded by kernels of this context (e.g. MRSIM_ETIMEOUT); clears the status word. */

@@ -679,7 +679,10 @@ mrsim_status mrsim_simulate_coils(mrsim_ctx *ctx, const mrsim_phantom *ph, const
     a.status = ctx->d_status;
     a.sens = ctx->d_sens;
     a.n_coils = n_coils;
+    void *maps = nullptr;
+    if ((rs = prepare_maps(ctx, seq, fp64 ? MODE_F64 : MODE_F32, a, stream, &maps)) != MRSIM_OK) return rs;
     const int rc = fp64 ? launch_fwd_coils_f64(a, threads, stream) : launch_fwd_coils_f32(a, threads, stream);
+    if (maps) cudaFreeAsync(maps, st);
     if (rc != 0) return cuda_fail(ctx, (cudaError_t)rc, "launch forward kernel (coils)");
     if (host_sig) {
         CK(cudaMemcpyAsync(signal_out, dsig, sig_doubles * sizeof(double), cudaMemcpyDeviceToHost, st), "copy signal out");
