@@ -223,6 +223,10 @@ def test_fields_train_maps(M, ctx, oracle_mod):
             ctx.set_train_maps(maps)
             f = M.Fields(ctx, ev, W.GAMMA_BAR, gt, 0.3)
             assert (f.n_train_maps > 0) == maps
+            if maps:  # the benchmark's work model marks the same map kinds as the library
+                import bench
+
+                assert f.n_train_maps == len(bench.field_train_maps(ev, gt)[1])
             got64 = M.simulate_fields(ctx, p, f, M.FP64)
             got32 = M.simulate_fields(ctx, p, f, M.FP32)
             ctx.stream_status()
