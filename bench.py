@@ -465,7 +465,7 @@ def run_batch(args):
 
     torch.cuda.set_device(0)
     ws = W.config4()
-    prec = M.FP64 if args.precision == "fp64" else M.FP32
+    prec = {"fp64": M.FP64, "kahan": M.FP32_KAHAN}.get(args.precision, M.FP32)
     ctx = M.Context(0)
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", 0)
@@ -510,7 +510,7 @@ def run_batch(args):
     line = {
         "metric": METRIC, "value": spin_steps / (ms * 1e-3), "unit": "spin-steps/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == M.FP64 else "f32", "data": "synthetic",
+        "dtype": {M.FP64: "f64", M.FP32_KAHAN: "df32"}.get(prec, "f32"), "data": "synthetic",
         "config": {"workload": "c4_batch64", "n_phantoms": len(ws), "n_spins": sum(w.phantom.n for w in ws),
                    "spin_steps_per_step": spin_steps, "n_items": b.n_items,
                    "launch": {"spins_per_thread": shape[0], "threads_per_block": shape[1], "tune_s": tune_s,
@@ -523,7 +523,9 @@ def run_batch(args):
                      f"+ {EV_SAMPLE_TRANSPOSE}/k per sample with k = {shape[0]} spins per thread",
             formulation_model={"ops_per_spin_step": form_ops / spin_steps, "achieved": form_g,
                                "frac": form_g / (fp32_alu_peak_ops(sm_clock(ck)) / 1e9)}),
-        "gpu_launches": 2 * args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id(),
+        # per step: the signal clear, every mapped phantom's train-map set-up, the batch kernel
+        "gpu_launches": (2 + sum(1 for km in kinds if km)) * args.steps, "clocks": ck,
+        "measured_rates": measured_rates(), "source": source_id(),
     }
     if prec == M.FP32 and not args.skip_extra:
         # the float64 and the compensated (double-float) batch on the same phantoms: their times,
@@ -927,7 +929,8 @@ def run_fields(args):
                                                   op_model="cached-map formulation per event (a computed interval 81 (+42 "
                                                            "transverse), a repeated one 9, pulse 9, sample 4), "
                                                            "transcendentals not counted"),
-            "gpu_launches": args.steps, "clocks": ck, "measured_rates": measured_rates(), "source": source_id()}
+            "gpu_launches": (2 if F.n_train_maps else 1) * args.steps, "clocks": ck, "measured_rates": measured_rates(),
+            "source": source_id()}
     if not args.no_cpu_baseline:  # the oracle on a bounded spin sample, and the GPU on the same spins
         cb = cpu_baseline_fields(w, args.cpu_seconds)
         line["cpu_baseline"] = cb["baseline"]
@@ -1244,7 +1247,7 @@ def run_ours(args):
                        "parallelism": f"spin-sharded x{world}" if world > 1 else "1 GPU",
                        **({"stress_mode": RASTER_NOTE.format(r=args.raster * 1e6, n=canonical.n_events)}
                           if args.raster else {})},
-            "roofline": roof, "gpu_launches": args.steps, "clocks": ck, "wall_s_timed": t_wall,
+            "roofline": roof, "gpu_launches": (2 if kinds else 1) * args.steps, "clocks": ck, "wall_s_timed": t_wall,
             "measured_rates": measured_rates(),
             "peaks_file": {k: read_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
             "source": source_id(),
