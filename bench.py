@@ -1175,19 +1175,37 @@ def run_ours(args):
         if orun is not None:
             out["oracle_parity"] = oracle_parity_sample(ctx, M, w, orun, seq, shape, stream)
 
-        # end to end through the public API with host buffers (pinned), copies inside the region
+        if not args.no_cpu_baseline:  # the oracle alone on the host cores, on a bounded sample
+            cb, (sub, ref) = cpu_baseline(w, seconds=args.cpu_seconds)
+            out["cpu_baseline"] = cb
+            if orun is None:
+                out["oracle_parity"] = oracle_parity(ctx, M, w, sub, ref)
+    # end to end through the public API with host buffers (pinned), copies inside the region; with
+    # more than one GPU every rank runs it on its own spins and the signal is summed across ranks
+    # in every step, as in the timed steps
+    if not args.skip_extra and not n_coils and prec != M.FP32_KAHAN:
         pinned = [torch.from_numpy(a).pin_memory() for a in w.phantom.arrays()]
         host_arrays = [p.numpy() for p in pinned]
         ev_pinned = torch.from_numpy(w.sequence.events.view(np.uint8)).pin_memory().numpy().view(W.EVENT_DTYPE)
-        host_sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64).pin_memory().numpy().view(np.complex128)
+        host_sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64).pin_memory()
+        host_sig_c = host_sig.numpy().view(np.complex128)
+        dev_sig = torch.zeros(2 * seq.n_adc, dtype=torch.float64, device=dev)
         e2e_steps = max(3, min(args.steps, 20))
         serial_steps = e2e_steps if kern_ms < 200.0 else 3
         gamma = w.sequence.gamma_hz_per_t
 
+        def run_e2e(p, s):
+            if dist:  # device output, the sum over ranks, then the read-back
+                M.simulate(ctx, p, s, prec, stream=stream, out=dev_sig, **kw)
+                D.reduce_signal(dev_sig)
+                host_sig.copy_(dev_sig)
+            else:
+                M.simulate(ctx, p, s, prec, out=host_sig_c, **kw)
+
         def e2e_serial_step():
             p = M.Phantom(ctx, host_arrays)
             s = M.Sequence(ctx, ev_pinned, gamma)
-            M.simulate(ctx, p, s, prec, out=host_sig, **kw)
+            run_e2e(p, s)
             p.close()
             s.close()
 
@@ -1205,35 +1223,37 @@ def run_ours(args):
                     p = M.Phantom(ctx, host_arrays)
                     s = M.Sequence.from_compiled(ctx, comp)
                     comp.close()
-                    M.simulate(ctx, p, s, prec, out=host_sig, **kw)
+                    run_e2e(p, s)
                     p.close()
                     s.close()
 
         e2e_serial_step()
         e2e_pipelined(2)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(serial_steps):
-            e2e_serial_step()
-        torch.cuda.synchronize()
-        serial_s = (time.perf_counter() - t0) / serial_steps
+        serial_s = None
+        if not dist:
+            t0 = time.perf_counter()
+            for _ in range(serial_steps):
+                e2e_serial_step()
+            torch.cuda.synchronize()
+            serial_s = (time.perf_counter() - t0) / serial_steps
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         e2e_pipelined(e2e_steps)
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s = D.max_over_ranks((time.perf_counter() - t0) * 1e3, device=dev) / 1e3 / e2e_steps
         upload = M.Compiled(ev_pinned, gamma)
         h2d = int(7 * 8 * w.phantom.n + upload.upload_bytes)
         upload.close()
-        out["e2e"] = {"value": spin_steps / e2e_s, "unit": "spin-steps/s", "h2d_bytes_per_step": h2d,
+        out["e2e"] = {"value": world * spin_steps / e2e_s, "unit": "spin-steps/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": int(16 * seq.n_adc), "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
                       "pipeline": "the next step's host compile runs on a worker thread during this step's "
-                                  "uploads, kernel and read-back (first compile not overlapped)",
-                      "serial_ms_per_step": serial_s * 1e3, "serial_steps": serial_steps}
-        if not args.no_cpu_baseline:  # the oracle alone on the host cores, on a bounded sample
-            cb, (sub, ref) = cpu_baseline(w, seconds=args.cpu_seconds)
-            out["cpu_baseline"] = cb
-            if orun is None:
-                out["oracle_parity"] = oracle_parity(ctx, M, w, sub, ref)
+                                  "uploads, kernel and read-back (first compile not overlapped)"
+                                  + ("; per step the signal is summed across ranks before the read-back; slowest rank"
+                                     if dist else "")}
+        if serial_s is not None:
+            out["e2e"].update({"serial_ms_per_step": serial_s * 1e3, "serial_steps": serial_steps})
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "spin-steps/s", "n_gpus": world, "steps": args.steps,
