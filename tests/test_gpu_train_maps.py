@@ -121,3 +121,31 @@ def test_train_map_allocation_failure(M, ctx, oracle_mod):
     torch.cuda.synchronize()
     ctx.stream_status()
     assert rel_l2(out.cpu().numpy().view(np.complex128), oracle_mod.signal(ph, seq)) <= 2e-5
+
+
+def test_train_maps_with_snapshots_and_resume(M, ctx, oracle_mod):
+    """Snapshots inside and between the shaped pulses of a spin echo whose other pulses run as
+    train maps, and a simulation resumed from a state in the middle of the sequence: every
+    snapshot equals the oracle's state after that event, and the resumed signal the oracle's."""
+    ph, seq = list(cases())[0]
+    ev = seq.events
+    per_tr = len(ev) // 16
+    rf = np.flatnonzero(ev["rf_flip"] != 0)
+    snaps = np.array(sorted({int(rf[5]), per_tr + 3, int(rf[len(rf) // 2]), 9 * per_tr - 1, len(ev) - 1}))
+    p = M.Phantom.from_workload_phantom(ctx, ph)
+    s = M.Sequence(ctx, ev, seq.gamma_hz_per_t, snapshots=snaps)
+    out = np.zeros((len(snaps), ph.n, 3))
+    for prec, tol in ((M.FP64, 1e-12), (M.FP32, 1e-4)):
+        M.simulate(ctx, p, s, prec, snapshots=out)
+        ctx.stream_status()
+        for q, e in enumerate(snaps):
+            _, st = oracle_mod.simulate(ph, ev[: e + 1], seq.gamma_hz_per_t, want_signal=False, want_state=True)
+            assert np.max(np.abs(out[q] - st)) <= tol * max(1.0, np.abs(st).max()), (prec, q)
+    # resume: the second half from the state after the first half
+    half = 8 * per_tr
+    _, mid = oracle_mod.simulate(ph, ev[:half], seq.gamma_hz_per_t, want_signal=False, want_state=True)
+    ref2, _ = oracle_mod.simulate(ph, ev[half:], seq.gamma_hz_per_t, m_init=mid)
+    s2 = M.Sequence(ctx, ev[half:], seq.gamma_hz_per_t)
+    got2 = M.simulate(ctx, p, s2, M.FP64, state_in=mid.copy())
+    assert rel_l2(got2, ref2) <= max(1e-12, phase_floor(ph, ev[half:], seq.gamma_hz_per_t))
+
