@@ -18,10 +18,11 @@
 // (every sub-pulse of a shaped pulse after the first, every step of a readout) applies it with nine
 // FMAs instead of recomputing the field, its direction, the phase and the exponentials.
 //
-// Layout: one thread per spin (its state, direction and position in registers), 128 threads per
-// block; the event records are staged through shared memory in chunks of FIELD_CHUNK by the
-// whole block; each sample's spin sum is a warp butterfly, a shared-memory window per chunk and
-// float64 atomics across blocks.
+// Layout: one spin per thread (float64) or two (float32), state, direction and position in
+// registers; the event records are staged through shared memory in chunks of FIELD_CHUNK by the
+// whole block; each thread writes its spins' value of each sample to its own column of a shared
+// window, the block sums the window's rows after the chunk, and float64 atomics add them across
+// blocks.
 //
 // float32 path: the large part of the phase, γ/2π Δt p = Σ_j n_j (k_j . x) with the moments
 // k_j = γ/2π g_j Δt in cycles/m, is summed from float-float products (hi, lo pairs of the
@@ -197,39 +198,19 @@ __device__ __forceinline__ void apply_map(const T (&A)[9], const T (&c)[3], T &M
     M2 = t2;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+// float64 sample window: one column per thread, rows of FIELD_THREADS + 2 doubles (row r is
+// sample r/2 of the chunk, real or imaginary part)
+constexpr int F64_WIN_STRIDE = FIELD_THREADS + 2;
+constexpr size_t F64_WIN_BYTES = (size_t)2 * FIELD_CHUNK * F64_WIN_STRIDE * sizeof(double);
 
-// Shared staging of one chunk of records and the chunk's sample window; flush adds the window's
-// samples to the signal.
-template <typename Ev, typename W>
-__device__ __forceinline__ int stage_chunk(const Ev *src, int64_t c0, int64_t n_events, Ev *evs, W *win) {
-    const int nc = (int)min((int64_t)FIELD_CHUNK, n_events - c0);
-    const int4 *s4 = reinterpret_cast<const int4 *>(src + c0);
-    int4 *d4 = reinterpret_cast<int4 *>(evs);
-    const int words = nc * (int)(sizeof(Ev) / sizeof(int4));
-    for (int i = threadIdx.x; i < words; i += blockDim.x) d4[i] = s4[i];
-    for (int i = threadIdx.x; i < 2 * FIELD_CHUNK; i += blockDim.x) win[i] = W(0);
-    return nc;
-}
-
-template <typename Ev, typename W>
-__device__ __forceinline__ void flush_chunk(const Ev *evs, int nc, const W *win, double *signal) {
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-        if (evs[i].flags & FF_ADC) {
-            atomicAdd(&signal[2 * (int64_t)evs[i].adc], (double)win[2 * evs[i].slot]);
-            atomicAdd(&signal[2 * (int64_t)evs[i].adc + 1], (double)win[2 * evs[i].slot + 1]);
-        }
-    }
-}
-
+// One spin per thread.  Samples: each thread writes its spin's value of each sample of the chunk to
+// its own column of a shared window; after the chunk each row is summed over the columns by two
+// threads (64 entries each, four partial sums) and added to the signal, so a sample costs a thread
+// two stores instead of a ten-add warp butterfly on the float64 pipe.
 __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) {
+    static_assert(FIELD_THREADS == 128, "two threads per window row");
     __shared__ FieldEv64 evs[FIELD_CHUNK];
-    __shared__ double win[2 * FIELD_CHUNK];
+    extern __shared__ __align__(16) double wind[];  // 2 * FIELD_CHUNK rows of F64_WIN_STRIDE
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = s < a.n_spins;
     const int64_t si = live ? s : 0;
@@ -245,9 +226,16 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
     double S0 = M0, S1 = M1, S2 = M2;  // state at the start of the current run
     double A[9] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0}, cv[3] = {0.0, 0.0, 0.0};  // cached map
     const FieldEv64 *src = static_cast<const FieldEv64 *>(a.ev);
+    const int t = threadIdx.x, row = t / 2, part = t % 2;
     for (int64_t c0 = 0; c0 < a.n_events; c0 += FIELD_CHUNK) {
         __syncthreads();
-        const int nc = stage_chunk(src, c0, a.n_events, evs, win);
+        const int nc = (int)min((int64_t)FIELD_CHUNK, a.n_events - c0);
+        {
+            const int4 *s4 = reinterpret_cast<const int4 *>(src + c0);
+            int4 *d4 = reinterpret_cast<int4 *>(evs);
+            const int words = nc * (int)(sizeof(FieldEv64) / sizeof(int4));
+            for (int i = t; i < words; i += FIELD_THREADS) d4[i] = s4[i];
+        }
         __syncthreads();
         for (int i = 0; i < nc; ++i) {
             const FieldEv64 &e = evs[i];
@@ -299,19 +287,24 @@ __global__ void __launch_bounds__(FIELD_THREADS) fields_kernel_f64(FieldArgs a) 
                     for (int q = 0; q < 3; ++q) cv[q] = cb[q];
                 }
             }
-            if (e.flags & FF_ADC) {
-                double sr = M0 * e.dem[0] + M1 * e.dem[1];
-                double sim = M1 * e.dem[0] - M0 * e.dem[1];
-                sr = warp_sum(live ? sr : 0.0);
-                sim = warp_sum(live ? sim : 0.0);
-                if ((threadIdx.x & 31) == 0) {
-                    atomicAdd(&win[2 * e.slot], sr);
-                    atomicAdd(&win[2 * e.slot + 1], sim);
-                }
+            if (e.flags & FF_ADC) {  // a spin past the phantom's end has M = 0
+                double *w = wind + (2 * e.slot) * F64_WIN_STRIDE + t;
+                w[0] = M0 * e.dem[0] + M1 * e.dem[1];
+                w[F64_WIN_STRIDE] = M1 * e.dem[0] - M0 * e.dem[1];
             }
         }
         __syncthreads();
-        flush_chunk(evs, nc, win, a.signal);
+        const int nslot = evs[0].nslot, adc0 = evs[0].adc;
+        double v = 0.0;
+        if (row < 2 * nslot) {
+            const double *w = wind + row * F64_WIN_STRIDE + part;
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int q = 0; q < FIELD_THREADS / 2; ++q) acc[q & 3] += w[2 * q];
+            v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if (part == 0 && row < 2 * nslot) atomicAdd(&a.signal[2 * (int64_t)adc0 + row], v);
     }
 }
 
@@ -1044,7 +1037,8 @@ mrsim_status mrsim_simulate_fields(mrsim_ctx *ctx, const mrsim_phantom *ph, cons
         }
         if (f64) {
             const unsigned grid = (unsigned)((ph->n + FIELD_THREADS - 1) / FIELD_THREADS);
-            fields_kernel_f64<<<grid, FIELD_THREADS, 0, st>>>(a);
+            cudaFuncSetAttribute(fields_kernel_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F64_WIN_BYTES);
+            fields_kernel_f64<<<grid, FIELD_THREADS, F64_WIN_BYTES, st>>>(a);
         } else {
             // 64 or 128 threads per block, whichever fills the last wave of resident blocks better
             const int64_t blocks128 = (ph->n + FIELD_K32 * 128 - 1) / (FIELD_K32 * 128);
