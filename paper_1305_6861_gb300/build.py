@@ -52,7 +52,7 @@ def _compile(src: str, verbose: bool) -> str:
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", f"-I{CUDA_HOME}/include", "-c", src, "-o", obj]
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", f"-I{CUDA_HOME}/include", "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

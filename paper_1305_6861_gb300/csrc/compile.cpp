@@ -20,16 +20,27 @@ namespace mrsim {
 
 namespace {
 
+// One lowered event.  Members that no kind uses together share storage (56 bytes in all: every
+// pass of the compiler streams the item list, so its size sets the compile time); each member is
+// read only for the kinds that write it.
 struct Item {
-    enum Kind { RF, PREC, SAMPLE, END, SNAP } kind;
-    double k[3];    // gradient moment γ/2π·G·Δt [cycles/m]
-    double dt;      // interval [s]
-    double alpha, phi;
-    double tau;     // RF/END: time since the previous RF pulse [s]
-    int64_t j;      // SAMPLE: sample index; SNAP: snapshot index
-    double adc_phase;
+    double k[3];  // PREC, SAMPLE: gradient moment γ/2π·G·Δt [cycles/m]
+    union {
+        double dt;     // PREC, SAMPLE: interval [s]
+        double alpha;  // RF: flip angle
+    };
+    union {
+        int64_t j;   // SAMPLE: sample index; SNAP: snapshot index
+        double phi;  // RF: phase
+    };
+    union {
+        double adc_phase;  // SAMPLE: receiver phase
+        double tau;        // RF, END, SNAP: time since the previous RF pulse [s]
+    };
     int32_t param;  // RF: learnable-flip index of a parametric pulse, or -1
+    enum Kind : int32_t { RF, PREC, SAMPLE, END, SNAP } kind;
 };
+static_assert(sizeof(Item) == 56, "Item layout");
 
 using Key = std::array<uint64_t, 4>;
 
@@ -185,6 +196,10 @@ struct ClassOf {
 // terms the value equals the plain sum.
 struct CSum {
     double s = 0.0, c = 0.0;
+    void set(double x) {  // the first term: value() is the same as for add() to an empty sum
+        s = x;
+        c = 0.0;
+    }
     void add(double x) {
         const double t = s + x;
         c += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
@@ -238,7 +253,8 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     // sample whose event has that gradient absorbs the trailing part (one interval of constant
     // gradient; precession and relaxation compose), so a readout whose dwell is split into several
     // events still compiles to uniform samples.
-    // (moments and durations as compensated sums: components 0-2 the moment, 3 the duration)
+    // (moments and durations as compensated sums: components 0-2 the moment, 3 the duration;
+    // each sum holds a value only while its flag is set)
     bool have = false, hhave = false, thave = false;
     CSum pk[4], hk[4], tk[4];
     double tg[3] = {0, 0, 0};
@@ -246,16 +262,12 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     auto push_prec = [&](const CSum *sum) {
         const double k[3] = {sum[0].value(), sum[1].value(), sum[2].value()}, dt = sum[3].value();
         if (is_zero(k, dt)) return;
-        Item it{};
+        Item &it = items.emplace_back();
         it.kind = Item::PREC;
         std::memcpy(it.k, k, sizeof k);
         it.dt = dt;
-        items.push_back(it);
     };
-    auto reset = [&]() {
-        have = hhave = thave = false;
-        for (int c = 0; c < 4; ++c) pk[c] = hk[c] = tk[c] = CSum{};
-    };
+    auto reset = [&]() { have = hhave = thave = false; };
     auto flush = [&]() {
         if (have) push_prec(pk);
         reset();
@@ -284,39 +296,39 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
         }
         if (e.rf_flip != 0.0 || prm >= 0) {
             flush();
-            Item it{};
+            Item &it = items.emplace_back();
             it.kind = Item::RF;
             it.alpha = e.rf_flip;
             it.phi = e.rf_phase;
             it.tau = tau;
             it.param = prm;
-            items.push_back(it);
             tau = 0.0;
         }
         const double k[3] = {gamma_hz * e.gx * e.dt, gamma_hz * e.gy * e.dt, gamma_hz * e.gz * e.dt};
         if (e.adc) {
-            Item it{};
-            it.kind = Item::SAMPLE;
+            double sk[3], sdt;
             if (same_g(e)) {  // the trailing constant-gradient part joins the sample's interval
                 if (hhave) push_prec(hk);
                 for (int c = 0; c < 4; ++c) tk[c].add(c < 3 ? k[c] : e.dt);
-                for (int c = 0; c < 3; ++c) it.k[c] = tk[c].value();
-                it.dt = tk[3].value();
+                for (int c = 0; c < 3; ++c) sk[c] = tk[c].value();
+                sdt = tk[3].value();
                 reset();
             } else {
                 flush();
-                std::memcpy(it.k, k, sizeof k);
-                it.dt = e.dt;
+                std::memcpy(sk, k, sizeof k);
+                sdt = e.dt;
             }
+            Item &it = items.emplace_back();
+            it.kind = Item::SAMPLE;
+            std::memcpy(it.k, sk, sizeof sk);
+            it.dt = sdt;
             it.j = j++;
             it.adc_phase = e.adc_phase;
-            items.push_back(it);
         } else {
-            if (!same_g(e)) {  // a new trailing run starts here
-                for (int c = 0; c < 4; ++c) {
-                    hk[c] = pk[c];
-                    tk[c] = CSum{};
-                }
+            const bool fresh = !same_g(e);
+            if (fresh) {  // a new trailing run starts here
+                if (have)
+                    for (int c = 0; c < 4; ++c) hk[c] = pk[c];
                 hhave = have;
                 tg[0] = e.gx;
                 tg[1] = e.gy;
@@ -325,28 +337,32 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
             }
             for (int c = 0; c < 4; ++c) {
                 const double v = c < 3 ? k[c] : e.dt;
-                tk[c].add(v);
-                pk[c].add(v);
+                if (fresh)
+                    tk[c].set(v);
+                else
+                    tk[c].add(v);
+                if (have)
+                    pk[c].add(v);
+                else
+                    pk[c].set(v);
             }
             have = true;
         }
         tau += e.dt;
         if (snap_next < n_snap && snap_after[snap_next] == i) {  // state after event i
             flush();
-            Item it{};
+            Item &it = items.emplace_back();
             it.kind = Item::SNAP;
             it.j = snap_next++;
             it.tau = tau;
-            items.push_back(it);
             tau = 0.0;  // the snapshot applies the T1 recovery so far
         }
     }
     flush();
     {
-        Item it{};
+        Item &it = items.emplace_back();
         it.kind = Item::END;
         it.tau = tau;
-        items.push_back(it);
     }
     out.n_adc = j;
     out.n_snap = n_snap;
