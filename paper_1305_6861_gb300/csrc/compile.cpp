@@ -369,19 +369,22 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
 
     // ---- group sample runs and count class uses -------------------------------------------------
     std::vector<Group> &groups = lease.s.groups;
+    groups.resize(items.size());
+    size_t n_groups = 0;
     for (size_t i = 0; i < items.size();) {
         if (items[i].kind == Item::SAMPLE && !is_zero(items[i].k, items[i].dt)) {
             size_t e = i + 1;
             while (e < items.size() && items[e].kind == Item::SAMPLE && (int64_t)(e - i) < RUN_MAX &&
                    same_interval(items[e], items[i]))
                 ++e;
-            groups.push_back({i, (int64_t)(e - i)});
+            groups[n_groups++] = {i, (int64_t)(e - i)};
             i = e;
         } else {
-            groups.push_back({i, 1});
+            groups[n_groups++] = {i, 1};
             ++i;
         }
     }
+    groups.resize(n_groups);
     Uses<Key, KeyHash> puses;
     Uses<uint64_t> e1uses, e2uses;
     auto anchor_key = [&](const Item &it, int64_t cnt) {
@@ -480,8 +483,6 @@ int compile_sequence(const mrsim_event *ev, int64_t n, double gamma_hz, Compiled
     double psi = 0.0;
     int pcache = -1, e1cache = -1;
     out.demod.assign(2 * (size_t)out.n_adc, 0.0);
-    out.ops32.reserve(groups.size() + 1);
-    out.ops64.reserve(groups.size() + 1);
     auto new32 = [](uint8_t kind) {
         OpF32 o;
         std::memset(&o, 0, sizeof o);
