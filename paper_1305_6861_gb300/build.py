@@ -46,13 +46,16 @@ def up_to_date() -> bool:
 
 
 def _compile(src: str, verbose: bool) -> str:
+    # host code without multiply-add contraction (-ffp-contract=off): the host compiler's float64
+    # results are then the same on x86-64 and AArch64 hosts
     obj = os.path.join(BUILDDIR, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
-        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-c", src, "-o",
+               obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:
-        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", f"-I{CUDA_HOME}/include", "-c", src, "-o", obj]
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", f"-I{CUDA_HOME}/include", "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
