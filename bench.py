@@ -265,20 +265,37 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None}
 
 
-def traffic_for(kernel_src_sha: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+def traffic_for(kernel_src_sha: str, workload: str, prog_sha: str | None = None):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source
+    and (for the program-driven kernels) on a program of this structure."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             d = json.load(f)
         e = d.get(workload)
-        if e and e.get("kernel_source_sha") == kernel_src_sha:
+        if e and e.get("kernel_source_sha") == kernel_src_sha and e.get("program_sha") == prog_sha:
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
     return None
 
 
-FWD_SOURCES = ("fwd_kernel.cuh", "packed.cuh", "internal.h", "compile.cpp")
+def program_sha(M, sequences) -> str:
+    """Hash of the compiled programs' structure: operation kinds, flags, counts, class and table
+    indices, and the table sizes.  With the kernel source this fixes what a launch reads and
+    writes; the float payloads (moments, angles, phases) are left out."""
+    h = hashlib.sha256()
+    for seq in sequences:
+        p = M.debug_compile(seq.events, seq.gamma_hz_per_t)
+        ops = p["ops"]
+        for f in ("kind", "flags", "n", "adc0", "pcls", "ecls", "acls", "tab"):
+            h.update(np.ascontiguousarray(ops[f]).tobytes())
+        sizes = [len(ops)] + [len(p[t]) for t in ("pcls", "e1", "e2", "train", "demod")]
+        h.update(np.asarray(sizes, dtype=np.int64).tobytes())
+    return h.hexdigest()[:16]
+
+
+# the device code of the forward and batch kernels (the program they run is hashed on its own)
+FWD_SOURCES = ("fwd_kernel.cuh", "packed.cuh", "internal.h")
 KT_SOURCES = ("kt_kernel.cu", "packed.cuh", "internal.h")
 
 
@@ -517,7 +534,8 @@ def run_batch(args):
                               "mode": "persistent kernel + work queue, CUDA graph replay"},
                    "l2": "flushed between timed steps (256 MB write, outside the step events)"},
         "roofline": fp64_roofline(achieved) if prec == M.FP64 else fp32_roofline(
-            achieved, ck, traffic=traffic_for(kernel_source_sha(), "c4_batch64"), kernel_ms=ms,
+            achieved, ck, traffic=traffic_for(kernel_source_sha(), "c4_batch64", program_sha(M, [w.sequence for w in ws])),
+            kernel_ms=ms,
             ops_per_spin_step=ops / spin_steps,
             op_model=f"per event: ADC repeating the previous (G, dt) {EV_ADC_REPEAT}, RF {EV_RF}, other {EV_OTHER}, "
                      f"+ {EV_SAMPLE_TRANSPOSE}/k per sample with k = {shape[0]} spins per thread",
@@ -1115,7 +1133,8 @@ def run_ours(args):
         roof = dict(fp64_roofline(achieved), kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps, op_model=model)
     else:
         roof = fp32_roofline(
-            achieved, ck, traffic=traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else "")),
+            achieved, ck, traffic=traffic_for(sha, w.name + (f"_{n_coils}coils" if n_coils else ""),
+                                              program_sha(M, [w.sequence])),
             kernel_ms=kern_ms, ops_per_spin_step=ops / spin_steps, op_model=model,
             formulation_model={"ops_per_spin_step": form_ops / spin_steps, "achieved": form_g,
                                "frac": form_g / (fp32_alu_peak_ops(sm_clock(ck)) / 1e9),

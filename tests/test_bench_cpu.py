@@ -97,12 +97,34 @@ def test_algorithmic_work_model(bench):
 def test_traffic_records_follow_the_kernel_source(bench):
     rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     for name, e in rec.items():
-        assert bench.traffic_for(e["kernel_source_sha"], name) == e["dram_bytes_per_launch"]
-        assert bench.traffic_for("0" * 16, name) is None
+        ps = e.get("program_sha")
+        assert bench.traffic_for(e["kernel_source_sha"], name, ps) == e["dram_bytes_per_launch"]
+        assert bench.traffic_for("0" * 16, name, ps) is None
+        if ps is not None:  # a program-driven kernel's record also needs the program's structure
+            assert bench.traffic_for(e["kernel_source_sha"], name, "0" * 16) is None
+            assert bench.traffic_for(e["kernel_source_sha"], name) is None
         assert e["dram_bytes_per_launch"] == e["dram_read_bytes"] + e["dram_write_bytes"]
         assert "--clock-control none" in e["source"]
     # the hash ignores comments and whitespace only
     assert len(bench.kernel_source_sha()) == 16 and bench.kernel_source_sha() != bench.kernel_source_sha(bench.KT_SOURCES)
+
+
+def test_traffic_record_matches_the_committed_compiler(bench):
+    """The C2 record holds for the program the committed host compiler makes of C2, and the
+    program hash sees a structural change (one sample fewer) but not a change of payload (another
+    receiver phase)."""
+    from paper_1305_6861_gb300 import mrsim as M
+
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))["c2_se2d_256"]
+    seq = W.config2().sequence
+    assert bench.program_sha(M, [seq]) == rec["program_sha"]
+    assert bench.kernel_source_sha() == rec["kernel_source_sha"]
+    ev = seq.events.copy()
+    adc = np.nonzero(ev["adc"])[0]
+    ev["adc_phase"][adc] += 0.25
+    assert bench.program_sha(M, [W.Sequence(ev, seq.gamma_hz_per_t)]) == rec["program_sha"]
+    ev["adc"][adc[-1]] = 0
+    assert bench.program_sha(M, [W.Sequence(ev, seq.gamma_hz_per_t)]) != rec["program_sha"]
 
 
 def test_field_work_model(bench):
