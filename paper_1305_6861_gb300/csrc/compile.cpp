@@ -20,9 +20,9 @@ namespace mrsim {
 
 namespace {
 
-// One lowered event.  Members that no kind uses together share storage (56 bytes in all: every
-// pass of the compiler streams the item list, so its size sets the compile time); each member is
-// read only for the kinds that write it.
+// One lowered event.  Members that no kind uses together share storage, 56 bytes in all: every
+// pass of the compiler streams the item list, and much of the compile time is spent moving it.
+// Each member is read only for the kinds that write it.
 struct Item {
     double k[3];  // PREC, SAMPLE: gradient moment γ/2π·G·Δt [cycles/m]
     union {
