@@ -46,8 +46,8 @@ def up_to_date() -> bool:
 
 
 def _compile(src: str, verbose: bool) -> str:
-    # host code without multiply-add contraction (-ffp-contract=off): the host compiler's float64
-    # results are then the same on x86-64 and AArch64 hosts
+    # host code without multiply-add contraction (-ffp-contract=off): the host compiler's own float64
+    # operations then round the same way on x86-64 and AArch64 hosts (the libm calls aside)
     obj = os.path.join(BUILDDIR, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-c", src, "-o",
